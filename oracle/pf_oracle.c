@@ -1,0 +1,712 @@
+/*
+ * FP64 CPU oracle for the bounded-power-cell renderer of Power Foam
+ * (arxiv 2604.24994).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or
+ * load this file; only the tests, the smoke check and the benchmark's CPU
+ * baseline do.  It shares no code, header or constant with the CUDA library.
+ *
+ * Everything is the plain definition, in double precision, brute force:
+ *
+ *   ray        x(t) = o + t d, |d| = 1, through the pixel centre (u+.5, v+.5)
+ *              of a pinhole camera (x_cam = rot (x - o)).
+ *   power      pow(x, i) = |x - p_i|^2 - w_i                (Eq. pow_dist)
+ *   power cell P_i = { x : pow(x,i) <= pow(x,j) for all j }  (Eq. power_cell)
+ *   bound      B_i = { x : |x - p_i| <= R_i }                (Sec. 3.2)
+ *   dense half D_i = { x : nh_i . (x - p_i) <= off_i },  nh = n/|n|
+ *              (Sec. 3.3: the oriented face splits the cell; the outer half
+ *              has zero density)
+ *   segment    [ta, tb] = { t >= 0 : x(t) in B_i, P_i, D_i },  l = tb - ta
+ *   colour     c_i = rgb_i + sum_k W_k tex_ik with soft-Voronoi weights
+ *              W_k = softmax_k(-kappa |u - s_k|)               (Eq. svrad)
+ *              evaluated at the end of the dense segment that lies on the
+ *              face side, u = (e1.(x_s - p_i), e2.(x_s - p_i)) / R_i.
+ *   opacity    alpha = 1 - exp(-sigma l)
+ *   composite  segments sorted by entry distance ta (they are disjoint):
+ *              C = sum_k T_k alpha_k c_k, T_{k+1} = T_k (1 - alpha_k),
+ *              black background; T_final is returned separately.
+ *              (Sec. 3.1: the volume rendering integral is a sum over the
+ *              segments of the ray inside the cells.)
+ *
+ * The radical plane between i and j is  pow(x,i) = pow(x,j), i.e.
+ *     2 x.(p_j - p_i) = |p_j|^2 - |p_i|^2 + w_i - w_j
+ * (the definition of pow gives +w_i - w_j; the appendix's Eq.
+ * power_bisector prints the weights the other way round).
+ *
+ * The adjoint (orc_render_grad) differentiates exactly this, in FP64, by
+ * the implicit function theorem on whichever constraint is active at each
+ * segment end.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* parameters as double arrays (the float32 inputs widen exactly; finite
+ * differences perturb them in double) */
+typedef struct {
+    int64_t n;
+    const double *pos, *w, *R, *sigma, *rgb, *normal, *offset, *tex;
+} orc_scene;
+
+typedef struct {
+    double rot[9];
+    double origin[3];
+    double fx, fy, cx, cy;
+    int32_t width, height;
+} orc_camera;
+
+/* optional candidate lists: cell i is clipped against idx[beg[i]..end[i])
+ * only (ascending, i excluded).  A NULL list, or beg[i] < 0, means against
+ * every other site.  A candidate list must contain every j whose radical
+ * plane can cut B_i; the others can never bind, so the result is the same. */
+typedef struct {
+    const int64_t *beg, *end;
+    const int32_t *idx;
+} orc_cands;
+
+enum { ACT_SPHERE = -1, ACT_CAMERA = -2, ACT_DIPOLE = -3 };
+
+typedef struct {
+    int32_t cell;
+    double ta, tb;
+    int32_t act_a, act_b;
+} orc_seg;
+
+static double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+static void load3(const double *p, int64_t i, double *o) {
+    o[0] = p[3 * i];
+    o[1] = p[3 * i + 1];
+    o[2] = p[3 * i + 2];
+}
+
+/* pixel-centre ray of a pinhole camera */
+void orc_ray(const orc_camera *cam, double u, double v, double *o, double *d) {
+    double dc[3] = {(u + 0.5 - cam->cx) / cam->fx, (v + 0.5 - cam->cy) / cam->fy, 1.0};
+    double dw[3];
+    for (int r = 0; r < 3; r++)
+        dw[r] = cam->rot[0 * 3 + r] * dc[0] + cam->rot[1 * 3 + r] * dc[1] + cam->rot[2 * 3 + r] * dc[2];
+    double nn = sqrt(dot3(dw, dw));
+    for (int r = 0; r < 3; r++) {
+        d[r] = dw[r] / nn;
+        o[r] = cam->origin[r];
+    }
+}
+
+/* unit dipole normal */
+static void unit_normal(const orc_scene *s, int64_t i, double *nh, double *len) {
+    double n[3];
+    load3(s->normal, i, n);
+    double L = sqrt(dot3(n, n));
+    for (int r = 0; r < 3; r++) nh[r] = n[r] / L;
+    *len = L;
+}
+
+/*
+ * Segment of the ray inside cell i (brute force over every other site, or
+ * over the given candidates).  Returns 1 when non-empty.
+ */
+static int cell_segment(const orc_scene *s, const orc_cands *cd, int64_t i, const double *o, const double *d,
+                        orc_seg *out) {
+    double p[3], m[3];
+    load3(s->pos, i, p);
+    for (int r = 0; r < 3; r++) m[r] = o[r] - p[r];
+    double R = s->R[i];
+    /* sphere |m + t d|^2 = R^2:  t^2 + 2 b t + c = 0 */
+    double b = dot3(m, d);
+    double c = dot3(m, m) - R * R;
+    double disc = b * b - c;
+    if (disc < 0.0) return 0;
+    double sq = sqrt(disc);
+    /* numerically stable roots */
+    double q = (b >= 0.0) ? -(b + sq) : -(b - sq);
+    double t0, t1;
+    if (q == 0.0) {
+        t0 = t1 = 0.0;
+    } else {
+        double r1 = q, r2 = c / q;
+        t0 = r1 < r2 ? r1 : r2;
+        t1 = r1 < r2 ? r2 : r1;
+    }
+    double ta = t0, tb = t1;
+    int aa = ACT_SPHERE, ab = ACT_SPHERE;
+    if (ta < 0.0) {
+        ta = 0.0;
+        aa = ACT_CAMERA;
+    }
+    if (tb <= ta) return 0;
+    double wi = s->w[i];
+    /* radical planes:  x.a <= (|p_j|^2 - |p_i|^2 + w_i - w_j)/2  with a = p_j - p_i,
+     * written for x = o + t d as  t (d.a) <= h,  h = (|a|^2 + w_i - w_j)/2 - a.m */
+    int64_t jb = 0, je = s->n;
+    int use_list = (cd && cd->beg && cd->beg[i] >= 0);
+    if (use_list) {
+        jb = cd->beg[i];
+        je = cd->end[i];
+    }
+    for (int64_t jj = jb; jj < je; jj++) {
+        int64_t j = use_list ? (int64_t)cd->idx[jj] : jj;
+        if (j == i) continue;
+        double pj[3], a[3];
+        load3(s->pos, j, pj);
+        for (int r = 0; r < 3; r++) a[r] = pj[r] - p[r];
+        double h = 0.5 * (dot3(a, a) + wi - (double)s->w[j]) - dot3(a, m);
+        double den = dot3(d, a);
+        if (den > 0.0) {
+            double t = h / den;
+            if (t < tb) {
+                tb = t;
+                ab = (int)j;
+            }
+        } else if (den < 0.0) {
+            double t = h / den;
+            if (t > ta) {
+                ta = t;
+                aa = (int)j;
+            }
+        } else if (h < 0.0) {
+            return 0;
+        }
+        if (tb <= ta) return 0;
+    }
+    /* dense half:  nh.(x - p) <= off  ->  t (nh.d) <= off - nh.m */
+    double nh[3], nl;
+    unit_normal(s, i, nh, &nl);
+    double den = dot3(nh, d);
+    double h = (double)s->offset[i] - dot3(nh, m);
+    if (den > 0.0) {
+        double t = h / den;
+        if (t < tb) {
+            tb = t;
+            ab = ACT_DIPOLE;
+        }
+    } else if (den < 0.0) {
+        double t = h / den;
+        if (t > ta) {
+            ta = t;
+            aa = ACT_DIPOLE;
+        }
+    } else if (h < 0.0) {
+        return 0;
+    }
+    if (tb <= ta) return 0;
+    out->cell = (int32_t)i;
+    out->ta = ta;
+    out->tb = tb;
+    out->act_a = aa;
+    out->act_b = ab;
+    return 1;
+}
+
+/*
+ * Orthonormal frame (e1, e2) of the face with unit normal nh, by the
+ * branchless construction of Duff et al., "Building an Orthonormal Basis,
+ * Revisited" (JCGT 2017).  J1/J2 (optional) receive de/dnh as 3x3
+ * row-major matrices J[r][c] = d e_r / d nh_c, treating the three
+ * components of nh as independent.
+ */
+static void onb(const double *n, double *e1, double *e2, double *J1, double *J2) {
+    double sg = n[2] >= 0.0 ? 1.0 : -1.0;
+    double a = -1.0 / (sg + n[2]);
+    double b = n[0] * n[1] * a;
+    e1[0] = 1.0 + sg * n[0] * n[0] * a;
+    e1[1] = sg * b;
+    e1[2] = -sg * n[0];
+    e2[0] = b;
+    e2[1] = sg + n[1] * n[1] * a;
+    e2[2] = -n[1];
+    if (J1) {
+        double da = a * a; /* d a / d nz */
+        double db[3] = {n[1] * a, n[0] * a, n[0] * n[1] * da};
+        double J1v[9] = {2.0 * sg * n[0] * a, 0.0, sg * n[0] * n[0] * da,
+                         sg * db[0], sg * db[1], sg * db[2],
+                         -sg, 0.0, 0.0};
+        double J2v[9] = {db[0], db[1], db[2],
+                         0.0, 2.0 * n[1] * a, n[1] * n[1] * da,
+                         0.0, -1.0, 0.0};
+        memcpy(J1, J1v, sizeof J1v);
+        memcpy(J2, J2v, sizeof J2v);
+    }
+}
+
+void orc_onb(const double *n, double *e1, double *e2) { onb(n, e1, e2, NULL, NULL); }
+
+/* the four texture sites, in units of R on the face, site-major */
+static const double SITE[4][2] = {{-1.0 / 3.0, -1.0 / 3.0}, {1.0 / 3.0, -1.0 / 3.0}, {-1.0 / 3.0, 1.0 / 3.0}, {1.0 / 3.0, 1.0 / 3.0}};
+
+/* colour of cell i for the segment (Eq. svrad, see header) */
+static void cell_colour(const orc_scene *s, int64_t i, const double *o, const double *d, const orc_seg *sg,
+                        double kappa, double *col, double *Wout, double *uout, double *ts_out) {
+    double nh[3], nl;
+    unit_normal(s, i, nh, &nl);
+    double ts = (dot3(nh, d) > 0.0) ? sg->tb : sg->ta;
+    double p[3], y[3], e1[3], e2[3];
+    load3(s->pos, i, p);
+    for (int r = 0; r < 3; r++) y[r] = o[r] + ts * d[r] - p[r];
+    onb(nh, e1, e2, NULL, NULL);
+    double R = s->R[i];
+    double u[2] = {dot3(e1, y) / R, dot3(e2, y) / R};
+    double lg[4], mx = -INFINITY;
+    for (int k = 0; k < 4; k++) {
+        double dx = u[0] - SITE[k][0], dy = u[1] - SITE[k][1];
+        lg[k] = -kappa * sqrt(dx * dx + dy * dy);
+        if (lg[k] > mx) mx = lg[k];
+    }
+    double W[4], Z = 0.0;
+    for (int k = 0; k < 4; k++) {
+        W[k] = exp(lg[k] - mx);
+        Z += W[k];
+    }
+    for (int k = 0; k < 4; k++) W[k] /= Z;
+    for (int ch = 0; ch < 3; ch++) {
+        double v = s->rgb[3 * i + ch];
+        for (int k = 0; k < 4; k++) v += W[k] * (double)s->tex[12 * i + 3 * k + ch];
+        col[ch] = v;
+    }
+    if (Wout) memcpy(Wout, W, sizeof W);
+    if (uout) memcpy(uout, u, sizeof u);
+    if (ts_out) *ts_out = ts;
+}
+
+static int cmp_seg(const void *a, const void *b) {
+    const orc_seg *x = a, *y = b;
+    if (x->ta < y->ta) return -1;
+    if (x->ta > y->ta) return 1;
+    return (x->cell > y->cell) - (x->cell < y->cell);
+}
+
+/* all non-empty segments of one ray, sorted by entry distance */
+static int64_t ray_segments(const orc_scene *s, const orc_cands *cd, const double *o, const double *d, orc_seg **buf,
+                            int64_t *cap) {
+    int64_t n = 0;
+    for (int64_t i = 0; i < s->n; i++) {
+        orc_seg sg;
+        if (!cell_segment(s, cd, i, o, d, &sg)) continue;
+        if (n == *cap) {
+            *cap = *cap ? 2 * *cap : 64;
+            *buf = realloc(*buf, (size_t)*cap * sizeof(orc_seg));
+        }
+        (*buf)[n++] = sg;
+    }
+    qsort(*buf, (size_t)n, sizeof(orc_seg), cmp_seg);
+    return n;
+}
+
+/* exported for the tests: segments of an explicit ray */
+int64_t orc_ray_segments(const orc_scene *s, const orc_cands *cd, const double *o, const double *d, int64_t maxn,
+                         int32_t *cell, double *ta, double *tb, int32_t *act_a, int32_t *act_b) {
+    orc_seg *buf = NULL;
+    int64_t cap = 0;
+    int64_t n = ray_segments(s, cd, o, d, &buf, &cap);
+    for (int64_t k = 0; k < n && k < maxn; k++) {
+        cell[k] = buf[k].cell;
+        ta[k] = buf[k].ta;
+        tb[k] = buf[k].tb;
+        act_a[k] = buf[k].act_a;
+        act_b[k] = buf[k].act_b;
+    }
+    free(buf);
+    return n;
+}
+
+/* exported for the tests: colour of cell i for an explicit segment */
+void orc_cell_colour(const orc_scene *s, int64_t i, const double *o, const double *d, double ta, double tb,
+                     double kappa, double *col) {
+    orc_seg sg = {(int32_t)i, ta, tb, ACT_SPHERE, ACT_SPHERE};
+    cell_colour(s, i, o, d, &sg, kappa, col, NULL, NULL, NULL);
+}
+
+static void pixel_of(const orc_camera *cam, int64_t k, const int32_t *pix, double *u, double *v) {
+    if (pix) {
+        *u = pix[2 * k];
+        *v = pix[2 * k + 1];
+    } else {
+        *u = (double)(k % cam->width);
+        *v = (double)(k / cam->width);
+    }
+}
+
+/* composite one ray: C = sum_k T_k alpha_k c_k over its sorted segments */
+static int64_t render_ray(const orc_scene *s, const orc_cands *cd, const double *o, const double *d, double kappa,
+                          orc_seg **buf, int64_t *cap, double *C, double *Tout) {
+    int64_t n = ray_segments(s, cd, o, d, buf, cap);
+    double T = 1.0;
+    C[0] = C[1] = C[2] = 0.0;
+    for (int64_t q = 0; q < n; q++) {
+        int64_t i = (*buf)[q].cell;
+        double l = (*buf)[q].tb - (*buf)[q].ta;
+        double surv = exp(-s->sigma[i] * l);
+        double alpha = 1.0 - surv;
+        double col[3];
+        cell_colour(s, i, o, d, &(*buf)[q], kappa, col, NULL, NULL, NULL);
+        for (int ch = 0; ch < 3; ch++) C[ch] += T * alpha * col[ch];
+        T *= surv;
+    }
+    *Tout = T;
+    return n;
+}
+
+/* explicit rays: o [n][3], d [n][3] (unit) */
+int orc_render_rays(const orc_scene *s, const orc_cands *cd, int64_t nray, const double *o, const double *d,
+                    double kappa, double *out_rgb, double *out_T) {
+    orc_seg *buf = NULL;
+    int64_t cap = 0;
+    for (int64_t k = 0; k < nray; k++) render_ray(s, cd, &o[3 * k], &d[3 * k], kappa, &buf, &cap, &out_rgb[3 * k], &out_T[k]);
+    free(buf);
+    return 0;
+}
+
+/*
+ * Render npix pixels (pix = [npix][2] (u, v) or NULL for the whole image in
+ * row-major order).  out_rgb [npix][3], out_T [npix], out_nseg [npix] (nullable).
+ */
+int orc_render(const orc_scene *s, const orc_cands *cd, const orc_camera *cam, int64_t npix, const int32_t *pix,
+               double kappa, double *out_rgb, double *out_T, int32_t *out_nseg, int nthreads) {
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+#endif
+    {
+        orc_seg *buf = NULL;
+        int64_t cap = 0;
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+        for (int64_t k = 0; k < npix; k++) {
+            double u, v, o[3], d[3];
+            pixel_of(cam, k, pix, &u, &v);
+            orc_ray(cam, u, v, o, d);
+            double T, C[3];
+            int64_t n = render_ray(s, cd, o, d, kappa, &buf, &cap, C, &T);
+            for (int ch = 0; ch < 3; ch++) out_rgb[3 * k + ch] = C[ch];
+            out_T[k] = T;
+            if (out_nseg) out_nseg[k] = (int32_t)n;
+        }
+        free(buf);
+    }
+    return 0;
+}
+
+/* cells whose bounding sphere the given pixels' rays meet at t >= 0 (flag per cell) */
+int orc_hit_cells(const orc_scene *s, const orc_camera *cam, int64_t npix, const int32_t *pix, uint8_t *flag,
+                  int nthreads) {
+    memset(flag, 0, (size_t)s->n);
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+    for (int64_t i = 0; i < s->n; i++) {
+        double p[3], m[3];
+        load3(s->pos, i, p);
+        double R = s->R[i];
+        for (int64_t k = 0; k < npix; k++) {
+            double u, v, o[3], d[3];
+            pixel_of(cam, k, pix, &u, &v);
+            orc_ray(cam, u, v, o, d);
+            for (int r = 0; r < 3; r++) m[r] = o[r] - p[r];
+            double b = dot3(m, d), c = dot3(m, m) - R * R;
+            double disc = b * b - c;
+            /* widened: a ray passing within ~1e-6 R of the sphere also counts */
+            if (disc >= -1e-12 * R * R && -b + sqrt(fabs(disc)) >= -1e-6 * R) {
+                flag[i] = 1;
+                break;
+            }
+        }
+    }
+    return 0;
+}
+
+/*
+ * Accumulate d t_end / d(params) * g into the per-pixel contribution list,
+ * for the constraint `act` active at ray parameter t.
+ * Parameter columns (25 per cell): pos 0-2, w 3, R 4, sigma 5, rgb 6-8,
+ * normal 9-11, offset 12, tex 13-24.
+ */
+enum { P_POS = 0, P_W = 3, P_R = 4, P_SIG = 5, P_RGB = 6, P_N = 9, P_OFF = 12, P_TEX = 13, NPAR = 25 };
+
+typedef struct {
+    int32_t cell, col;
+    double v;
+} orc_contrib;
+
+typedef struct {
+    orc_contrib *c;
+    int64_t n, cap;
+} clist;
+
+static void push(clist *L, int32_t cell, int col, double v) {
+    if (v == 0.0) return;
+    if (L->n == L->cap) {
+        L->cap = L->cap ? 2 * L->cap : 256;
+        L->c = realloc(L->c, (size_t)L->cap * sizeof(orc_contrib));
+    }
+    L->c[L->n].cell = cell;
+    L->c[L->n].col = col;
+    L->c[L->n].v = v;
+    L->n++;
+}
+
+/* dL/dt for the end of a segment given by constraint act on cell i */
+static void route_t(const orc_scene *s, int64_t i, int act, double t, const double *o, const double *d, double g,
+                    clist *L) {
+    if (g == 0.0 || act == ACT_CAMERA) return;
+    double p[3], x[3], y[3];
+    load3(s->pos, i, p);
+    for (int r = 0; r < 3; r++) {
+        x[r] = o[r] + t * d[r];
+        y[r] = x[r] - p[r];
+    }
+    if (act == ACT_SPHERE) {
+        /* F = |x - p|^2 - R^2 = 0:  dt/dp = y/(y.d), dt/dR = R/(y.d) */
+        double yd = dot3(y, d);
+        for (int r = 0; r < 3; r++) push(L, (int32_t)i, P_POS + r, g * y[r] / yd);
+        push(L, (int32_t)i, P_R, g * (double)s->R[i] / yd);
+    } else if (act == ACT_DIPOLE) {
+        /* F = nh.(x - p) - off:  dt/dp = nh/(nh.d), dt/doff = 1/(nh.d), dt/dnh = -(x-p)/(nh.d) */
+        double nh[3], nl;
+        unit_normal(s, i, nh, &nl);
+        double nd = dot3(nh, d);
+        double gnh[3];
+        for (int r = 0; r < 3; r++) {
+            push(L, (int32_t)i, P_POS + r, g * nh[r] / nd);
+            gnh[r] = -g * y[r] / nd;
+        }
+        push(L, (int32_t)i, P_OFF, g / nd);
+        /* nh = n/|n|:  dL/dn = (I - nh nh^T) dL/dnh / |n| */
+        double pr = dot3(nh, gnh);
+        for (int r = 0; r < 3; r++) push(L, (int32_t)i, P_N + r, (gnh[r] - nh[r] * pr) / nl);
+    } else {
+        /* F = 2 x.(p_j - p_i) - |p_j|^2 + |p_i|^2 - w_i + w_j
+         * dF/dt = 2 d.(p_j - p_i), dF/dp_i = -2(x - p_i), dF/dp_j = 2(x - p_j),
+         * dF/dw_i = -1, dF/dw_j = 1  ->  dt/dtheta = -dF/dtheta / dF/dt */
+        int64_t j = act;
+        double pj[3], a[3];
+        load3(s->pos, j, pj);
+        for (int r = 0; r < 3; r++) a[r] = pj[r] - p[r];
+        double Ft = 2.0 * dot3(d, a);
+        for (int r = 0; r < 3; r++) {
+            push(L, (int32_t)i, P_POS + r, g * (2.0 * (x[r] - p[r])) / Ft);
+            push(L, (int32_t)j, P_POS + r, g * (-2.0 * (x[r] - pj[r])) / Ft);
+        }
+        push(L, (int32_t)i, P_W, g * 1.0 / Ft);
+        push(L, (int32_t)j, P_W, g * -1.0 / Ft);
+    }
+}
+
+/*
+ * Gradient of L with respect to every cell parameter, given dL/dC [npix][3]
+ * and dL/dT_final [npix] for the rendered pixels.  grad [n][25] is
+ * overwritten.  Contributions are summed in pixel order, so the result does
+ * not depend on the thread count.
+ */
+int orc_render_grad(const orc_scene *s, const orc_cands *cd, const orc_camera *cam, int64_t npix, const int32_t *pix,
+                    double kappa, const double *dL_dC, const double *dL_dT, double *grad, int nthreads) {
+    clist *lists = calloc((size_t)npix, sizeof(clist));
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+#endif
+    {
+        orc_seg *buf = NULL;
+        int64_t cap = 0;
+        double *alpha = NULL, *surv = NULL, *Tin = NULL, *col = NULL;
+        int64_t acap = 0;
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+        for (int64_t k = 0; k < npix; k++) {
+            double u, v, o[3], d[3];
+            pixel_of(cam, k, pix, &u, &v);
+            orc_ray(cam, u, v, o, d);
+            int64_t n = ray_segments(s, cd, o, d, &buf, &cap);
+            if (n > acap) {
+                acap = n;
+                alpha = realloc(alpha, (size_t)n * sizeof(double));
+                surv = realloc(surv, (size_t)n * sizeof(double));
+                Tin = realloc(Tin, (size_t)n * sizeof(double));
+                col = realloc(col, (size_t)n * 3 * sizeof(double));
+            }
+            double T = 1.0;
+            for (int64_t q = 0; q < n; q++) {
+                int64_t i = buf[q].cell;
+                double l = buf[q].tb - buf[q].ta;
+                surv[q] = exp(-(double)s->sigma[i] * l);
+                alpha[q] = 1.0 - surv[q];
+                Tin[q] = T;
+                cell_colour(s, i, o, d, &buf[q], kappa, &col[3 * q], NULL, NULL, NULL);
+                T *= surv[q];
+            }
+            double Tf = T;
+            const double *gC = &dL_dC[3 * k];
+            double gT = dL_dT[k];
+            clist *L = &lists[k];
+            /* S = sum over segments behind q of T_j alpha_j c_j */
+            double S[3] = {0, 0, 0};
+            for (int64_t q = n - 1; q >= 0; q--) {
+                int64_t i = buf[q].cell;
+                double sig = s->sigma[i];
+                double l = buf[q].tb - buf[q].ta;
+                double Tout = Tin[q] * surv[q];
+                /* x = sigma l, alpha = 1 - e^-x:
+                 * dL/dx = gC.(T_{q+1} c_q - S_q) - gT T_final */
+                double dLdx = -gT * Tf;
+                for (int ch = 0; ch < 3; ch++) dLdx += gC[ch] * (Tout * col[3 * q + ch] - S[ch]);
+                push(L, (int32_t)i, P_SIG, dLdx * l);
+                double gl = dLdx * sig;
+                /* colour: dL/dc = T alpha gC */
+                double wc = Tin[q] * alpha[q];
+                double gc[3] = {wc * gC[0], wc * gC[1], wc * gC[2]};
+                double W[4], uu[2], ts;
+                double cc[3];
+                cell_colour(s, i, o, d, &buf[q], kappa, cc, W, uu, &ts);
+                for (int ch = 0; ch < 3; ch++) push(L, (int32_t)i, P_RGB + ch, gc[ch]);
+                for (int kk = 0; kk < 4; kk++)
+                    for (int ch = 0; ch < 3; ch++) push(L, (int32_t)i, P_TEX + 3 * kk + ch, W[kk] * gc[ch]);
+                /* soft-Voronoi weights -> u */
+                double gW[4], sW = 0.0;
+                for (int kk = 0; kk < 4; kk++) {
+                    gW[kk] = 0.0;
+                    for (int ch = 0; ch < 3; ch++) gW[kk] += (double)s->tex[12 * i + 3 * kk + ch] * gc[ch];
+                    sW += W[kk] * gW[kk];
+                }
+                double gu[2] = {0.0, 0.0};
+                for (int kk = 0; kk < 4; kk++) {
+                    double glog = W[kk] * (gW[kk] - sW);          /* dL/dlogit */
+                    double dx = uu[0] - SITE[kk][0], dy = uu[1] - SITE[kk][1];
+                    double r = sqrt(dx * dx + dy * dy);
+                    if (r > 0.0) {
+                        double gr = -kappa * glog;                  /* logit = -kappa r */
+                        gu[0] += gr * dx / r;
+                        gu[1] += gr * dy / r;
+                    }
+                }
+                /* u = (e1.y_s, e2.y_s)/R, y_s = o + ts d - p */
+                double nh[3], nl, e1[3], e2[3], J1[9], J2[9], p[3], ys[3];
+                unit_normal(s, i, nh, &nl);
+                onb(nh, e1, e2, J1, J2);
+                load3(s->pos, i, p);
+                for (int r = 0; r < 3; r++) ys[r] = o[r] + ts * d[r] - p[r];
+                double R = s->R[i];
+                double gy[3];
+                for (int r = 0; r < 3; r++) gy[r] = (gu[0] * e1[r] + gu[1] * e2[r]) / R;
+                for (int r = 0; r < 3; r++) push(L, (int32_t)i, P_POS + r, -gy[r]);
+                push(L, (int32_t)i, P_R, -(gu[0] * uu[0] + gu[1] * uu[1]) / R);
+                /* through the frame: dL/de1 = gu0 y/R, dL/dnh = J1^T dL/de1 + J2^T dL/de2 */
+                double gnh[3] = {0, 0, 0};
+                for (int c = 0; c < 3; c++)
+                    for (int r = 0; r < 3; r++)
+                        gnh[c] += J1[3 * r + c] * gu[0] * ys[r] / R + J2[3 * r + c] * gu[1] * ys[r] / R;
+                double pr = dot3(nh, gnh);
+                for (int r = 0; r < 3; r++) push(L, (int32_t)i, P_N + r, (gnh[r] - nh[r] * pr) / nl);
+                /* the texture point moves with its segment end */
+                double gts = dot3(gy, d);
+                int on_b = (dot3(nh, d) > 0.0);
+                double gta = -gl + (on_b ? 0.0 : gts);
+                double gtb = gl + (on_b ? gts : 0.0);
+                route_t(s, i, buf[q].act_a, buf[q].ta, o, d, gta, L);
+                route_t(s, i, buf[q].act_b, buf[q].tb, o, d, gtb, L);
+                for (int ch = 0; ch < 3; ch++) S[ch] += Tin[q] * alpha[q] * col[3 * q + ch];
+            }
+        }
+        free(buf);
+        free(alpha);
+        free(surv);
+        free(Tin);
+        free(col);
+    }
+    memset(grad, 0, (size_t)s->n * NPAR * sizeof(double));
+    for (int64_t k = 0; k < npix; k++) {
+        for (int64_t q = 0; q < lists[k].n; q++) {
+            orc_contrib *c = &lists[k].c[q];
+            grad[(int64_t)c->cell * NPAR + c->col] += c->v;
+        }
+        free(lists[k].c);
+    }
+    free(lists);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------
+ * CPU binning: which 16x16 tiles each cell's bounding sphere can touch, and
+ * the painter key pow(o, p_i) (Sec. 3.2; Thm. power_painter orders cells by
+ * the power distance of the camera centre).
+ *
+ * The rectangle is the exact image-plane bounding box of the projected
+ * sphere (the tangent lines from the camera centre in the x-z and y-z
+ * planes), widened by 1e-6 px, and clipped to the image.  A sphere that
+ * reaches the plane z = 0 gets the whole image, minus any side of the view
+ * frustum it lies entirely outside of.  Every step is one IEEE operation
+ * in double precision, in the order written (the library evaluates the same
+ * rule), so the tile sets can be compared bit for bit.
+ * ------------------------------------------------------------------------ */
+#define ORC_TILE 16
+
+static double orc_ceil(double x) { return ceil(x); }
+static double orc_floor(double x) { return floor(x); }
+
+/* rect[4] = {tx0, ty0, tx1, ty1} (empty: tx0 > tx1), key = order-preserving bits of pow */
+void orc_bin_cell(const orc_camera *cam, const double *pos, const double *w, const double *R, int64_t i,
+                  int32_t *rect, uint64_t *key) {
+    double px = pos[3 * i], py = pos[3 * i + 1], pz = pos[3 * i + 2];
+    double dx = px - cam->origin[0];
+    double dy = py - cam->origin[1];
+    double dz = pz - cam->origin[2];
+    double pw = ((dx * dx + dy * dy) + dz * dz) - (double)w[i];
+    uint64_t bits;
+    memcpy(&bits, &pw, 8);
+    *key = (bits >> 63) ? ~bits : (bits | 0x8000000000000000ULL);
+
+    const double *M = cam->rot;
+    double X = (M[0] * dx + M[1] * dy) + M[2] * dz;
+    double Y = (M[3] * dx + M[4] * dy) + M[5] * dz;
+    double Z = (M[6] * dx + M[7] * dy) + M[8] * dz;
+    double r = R[i];
+    rect[0] = 1;
+    rect[1] = 1;
+    rect[2] = 0;
+    rect[3] = 0;
+    if (Z + r <= 0.0) return; /* entirely behind the camera */
+    double W = cam->width, H = cam->height;
+    double kl = (0.0 - cam->cx) / cam->fx, kr = (W - cam->cx) / cam->fx;
+    double ku = (0.0 - cam->cy) / cam->fy, kd = (H - cam->cy) / cam->fy;
+    /* outside a side plane of the frustum (x = k z through the camera centre) */
+    if (X - kr * Z > r * sqrt(1.0 + kr * kr)) return;
+    if (kl * Z - X > r * sqrt(1.0 + kl * kl)) return;
+    if (Y - kd * Z > r * sqrt(1.0 + kd * kd)) return;
+    if (ku * Z - Y > r * sqrt(1.0 + ku * ku)) return;
+    double ulo = -INFINITY, uhi = INFINITY, vlo = -INFINITY, vhi = INFINITY;
+    if (Z > r) {
+        double rr = r * r;
+        double zr = Z * Z - rr;
+        double sx = sqrt((X * X + Z * Z) - rr);
+        double sy = sqrt((Y * Y + Z * Z) - rr);
+        double kxl = (X * Z - r * sx) / zr, kxh = (X * Z + r * sx) / zr;
+        double kyl = (Y * Z - r * sy) / zr, kyh = (Y * Z + r * sy) / zr;
+        ulo = cam->fx * kxl + cam->cx;
+        uhi = cam->fx * kxh + cam->cx;
+        vlo = cam->fy * kyl + cam->cy;
+        vhi = cam->fy * kyh + cam->cy;
+    }
+    /* pixel centres u + 0.5 inside [ulo, uhi], widened by 1e-6 px */
+    double a0 = orc_ceil((ulo - 0.5) - 1e-6), a1 = orc_floor((uhi - 0.5) + 1e-6);
+    double b0 = orc_ceil((vlo - 0.5) - 1e-6), b1 = orc_floor((vhi - 0.5) + 1e-6);
+    if (a0 < 0.0) a0 = 0.0;
+    if (b0 < 0.0) b0 = 0.0;
+    if (a1 > W - 1.0) a1 = W - 1.0;
+    if (b1 > H - 1.0) b1 = H - 1.0;
+    if (a0 > a1 || b0 > b1) return;
+    rect[0] = (int32_t)a0 / ORC_TILE;
+    rect[1] = (int32_t)b0 / ORC_TILE;
+    rect[2] = (int32_t)a1 / ORC_TILE;
+    rect[3] = (int32_t)b1 / ORC_TILE;
+}
+
+int orc_bin(const orc_camera *cam, int64_t n, const double *pos, const double *w, const double *R, int32_t *rect,
+            uint64_t *key) {
+    for (int64_t i = 0; i < n; i++) orc_bin_cell(cam, pos, w, R, i, &rect[4 * i], &key[i]);
+    return 0;
+}

@@ -1,0 +1,514 @@
+"""Pins for the FP64 CPU oracle: each test checks it against something other
+than itself (closed forms, library routines, invariants of the paper's
+geometry, brute-force point classification, finite differences)."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import ACT_CAMERA, ACT_DIPOLE, ACT_SPHERE
+from tests.oracle_util import cam_at, cluster_scene, make_scene, random_dirs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def seg_dict(segs):
+    return {c: (ta, tb) for c, ta, tb, _, _ in segs}
+
+
+# ---------------------------------------------------------------- closed forms
+
+def test_isolated_cell_chord_closed_form():
+    """One cell, no neighbours, face outside the ball: the segment is the
+    sphere chord 2 sqrt(R^2 - b^2) and T = exp(-sigma chord) (Sec. 3.1/3.2)."""
+    R, sig = 0.3, 2.0
+    rgb = np.array([0.2, 0.5, 0.9])
+    orc = oracle.Oracle(make_scene([0, 0, 0], 0.04, R, sig, rgb))
+    for b in (0.0, 0.1, 0.25, 0.299):
+        o = np.array([[-2.0, b, 0.0]])
+        d = np.array([[1.0, 0.0, 0.0]])
+        c, T = orc.render_rays(o, d)
+        chord = 2 * math.sqrt(R * R - b * b)
+        assert T[0] == pytest.approx(math.exp(-sig * chord), rel=1e-13, abs=1e-15)
+        np.testing.assert_allclose(c[0], (1 - math.exp(-sig * chord)) * rgb, rtol=1e-12, atol=1e-15)
+    # through the centre the chord is the diameter
+    segs = orc.ray_segments([-2.0, 0, 0], [1.0, 0, 0])
+    assert segs[0][2] - segs[0][1] == pytest.approx(2 * R, rel=1e-14)
+    assert segs[0][3] == ACT_SPHERE and segs[0][4] == ACT_SPHERE
+    # a miss
+    c, T = orc.render_rays([[-2.0, 0.31, 0.0]], [[1.0, 0, 0]])
+    assert T[0] == 1.0 and np.all(c == 0)
+
+
+def test_camera_inside_cell_clips_at_zero():
+    """t >= 0: from inside the ball only the forward half-chord counts."""
+    R = 0.5
+    orc = oracle.Oracle(make_scene([0, 0, 0], 0.1, R, 1.0))
+    segs = orc.ray_segments([0.1, 0.0, 0.0], [1.0, 0.0, 0.0])
+    assert len(segs) == 1
+    c, ta, tb, aa, ab = segs[0]
+    assert ta == 0.0 and aa == ACT_CAMERA
+    assert tb == pytest.approx(0.4, rel=1e-14) and ab == ACT_SPHERE
+
+
+def test_two_cells_golden():
+    g = json.load(open(os.path.join(GOLDEN, "two_cells_on_axis.json")))
+    sc = make_scene([[0, 0, 0], [0.5, 0, 0]], [0.05, 0.03], [0.4, 0.4], [1.0, 2.0],
+                    [[1, 0, 0], [0, 1, 0]])
+    orc = oracle.Oracle(sc)
+    segs = orc.ray_segments([-1.0, 0, 0], [1.0, 0, 0])
+    assert len(segs) == len(g["segments"])
+    for (c, ta, tb, _, _), (ce, tae, tbe) in zip(segs, g["segments"]):
+        assert c == ce
+        assert ta == pytest.approx(tae, abs=1e-13)
+        assert tb == pytest.approx(tbe, abs=1e-13)
+    assert segs[0][4] == 1 and segs[1][3] == 0       # the shared face is the radical plane
+    rgb, T = orc.render_rays([[-1.0, 0, 0]], [[1.0, 0, 0]])
+    assert T[0] == pytest.approx(g["T"], rel=1e-12)
+    np.testing.assert_allclose(rgb[0], g["rgb"], rtol=1e-12, atol=1e-15)
+
+
+def test_radical_plane_position_general():
+    """Off-axis two-cell case: the shared boundary point satisfies
+    pow(x,i) = pow(x,j) (the definition, Eq. pow_dist), for random weights."""
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        D = rng.uniform(0.2, 0.6)
+        wi, wj = rng.uniform(0.01, 0.08, 2)
+        sc = make_scene([[0, 0, 0], [D, 0, 0]], [wi, wj], [0.7, 0.7])
+        orc = oracle.Oracle(sc)
+        o = np.array([-1.0, rng.uniform(-0.1, 0.1), rng.uniform(-0.1, 0.1)])
+        d = np.array([1.0, rng.uniform(-0.05, 0.05), rng.uniform(-0.05, 0.05)])
+        d /= np.linalg.norm(d)
+        segs = orc.ray_segments(o, d)
+        assert [s[0] for s in segs] == [0, 1]
+        t = segs[0][2]
+        assert segs[1][1] == pytest.approx(t, abs=1e-13)
+        x = o + t * d
+        pi = np.sum(x * x) - wi
+        pj = np.sum((x - [D, 0, 0]) ** 2) - wj
+        assert pi == pytest.approx(pj, abs=1e-13)
+
+
+# ------------------------------------------------- point classification checks
+
+def classify(sc, x):
+    """Plain definition at a point: the power cell (argmin over all sites of
+    |x - p|^2 - w), inside its ball, and on the dense side of its face."""
+    P = np.asarray(sc.pos, np.float64)
+    pw = np.sum((P - x) ** 2, axis=1) - np.asarray(sc.w, np.float64)
+    i = int(np.argmin(pw))
+    inside = np.sum((x - P[i]) ** 2) <= float(sc.R[i]) ** 2
+    n = np.asarray(sc.normal[i], np.float64)
+    n = n / np.linalg.norm(n)
+    dense = float(np.dot(n, x - P[i])) <= float(sc.offset[i])
+    return i, inside and dense
+
+
+@pytest.mark.parametrize("seed,equal_w", [(1, False), (2, False), (3, True), (4, True)])
+def test_segments_match_point_classification(seed, equal_w):
+    """Every point inside segment k lies in cell k's bounded dense region,
+    and every sampled point on the ray outside all segments lies in none."""
+    rng = np.random.default_rng(seed)
+    sc = cluster_scene(rng, n=14, equal_w=equal_w)
+    orc = oracle.Oracle(sc)
+    for _ in range(20):
+        o = rng.uniform(-1, 1, 3)
+        o = 1.2 * o / np.linalg.norm(o)
+        d = -o / np.linalg.norm(o) + rng.normal(0, 0.08, 3)
+        d /= np.linalg.norm(d)
+        segs = orc.ray_segments(o, d)
+        for c, ta, tb, _, _ in segs:
+            for f in (0.02, 0.3, 0.5, 0.7, 0.98):
+                x = o + (ta + f * (tb - ta)) * d
+                i, ins = classify(sc, x)
+                assert ins and i == c
+        ts = np.linspace(0, 3, 1500)
+        for t in ts:
+            if any(ta - 1e-9 <= t <= tb + 1e-9 for _, ta, tb, _, _ in segs):
+                continue
+            _, ins = classify(sc, o + t * d)
+            assert not ins
+
+
+def test_equal_weights_reduce_to_voronoi_kdtree():
+    """Equal weights: power cells are Voronoi cells (appendix), so the cell
+    of a point is scipy's nearest site."""
+    from scipy.spatial import cKDTree
+    rng = np.random.default_rng(11)
+    sc = cluster_scene(rng, n=30, spread=0.3, equal_w=True, dipole=False)
+    tree = cKDTree(np.asarray(sc.pos, np.float64))
+    orc = oracle.Oracle(sc)
+    checked = 0
+    for _ in range(40):
+        o = random_dirs(rng, 1)[0] * 1.5
+        d = -o / 1.5 + rng.normal(0, 0.1, 3)
+        d /= np.linalg.norm(d)
+        for c, ta, tb, _, _ in orc.ray_segments(o, d):
+            x = o + 0.5 * (ta + tb) * d
+            assert tree.query(x)[1] == c
+            checked += 1
+    assert checked > 50
+
+
+# ----------------------------------------------------------------- invariants
+
+def ball_union(sc, o, d):
+    """Union of the ray's chords through all balls (t >= 0), merged."""
+    P = np.asarray(sc.pos, np.float64)
+    R = np.asarray(sc.R, np.float64)
+    iv = []
+    for p, r in zip(P, R):
+        m = o - p
+        b = m @ d
+        disc = b * b - (m @ m - r * r)
+        if disc <= 0:
+            continue
+        t0, t1 = -b - math.sqrt(disc), -b + math.sqrt(disc)
+        t0 = max(t0, 0.0)
+        if t1 > t0:
+            iv.append([t0, t1])
+    iv.sort()
+    out = []
+    for a, b in iv:
+        if out and a <= out[-1][1]:
+            out[-1][1] = max(out[-1][1], b)
+        else:
+            out.append([a, b])
+    return out
+
+
+@pytest.mark.parametrize("seed", [21, 22, 23])
+def test_tied_scene_cells_tile_the_union_of_balls(seed):
+    """R_i^2 - w_i equal for all cells: the bounded cells partition the
+    union of the balls, so along any ray the segments neither overlap nor
+    leave gaps inside the union, and their lengths sum to its length."""
+    rng = np.random.default_rng(seed)
+    sc = cluster_scene(rng, n=25, spread=0.25, tied=True, dipole=False)
+    orc = oracle.Oracle(sc)
+    for _ in range(30):
+        o = random_dirs(rng, 1)[0] * 1.3
+        d = -o / 1.3 + rng.normal(0, 0.15, 3)
+        d /= np.linalg.norm(d)
+        segs = orc.ray_segments(o, d)
+        U = ball_union(sc, o, d)
+        tot = sum(tb - ta for _, ta, tb, _, _ in segs)
+        assert tot == pytest.approx(sum(b - a for a, b in U), abs=1e-12)
+        for k in range(len(segs) - 1):
+            gap = segs[k + 1][1] - segs[k][2]
+            assert gap >= -1e-12                       # no overlap
+            if gap > 1e-12:                            # a gap must be a gap of the union
+                mid = 0.5 * (segs[k][2] + segs[k + 1][1])
+                assert not any(a < mid < b for a, b in U)
+
+
+@pytest.mark.parametrize("seed", [31, 32])
+def test_untied_scene_segments_disjoint_and_bounded(seed):
+    """R = 1.5 r: segments still never overlap and never exceed the union."""
+    rng = np.random.default_rng(seed)
+    sc = cluster_scene(rng, n=25, spread=0.25, dipole=False)
+    orc = oracle.Oracle(sc)
+    for _ in range(30):
+        o = random_dirs(rng, 1)[0] * 1.3
+        d = -o / 1.3 + rng.normal(0, 0.15, 3)
+        d /= np.linalg.norm(d)
+        segs = orc.ray_segments(o, d)
+        for k in range(len(segs) - 1):
+            assert segs[k + 1][1] - segs[k][2] >= -1e-12
+        tot = sum(tb - ta for _, ta, tb, _, _ in segs)
+        assert tot <= sum(b - a for a, b in ball_union(sc, o, d)) + 1e-12
+
+
+@pytest.mark.parametrize("seed", [41, 42, 43])
+def test_power_painter_order(seed):
+    """Thm. power_painter: along any ray from the camera centre, the cells
+    are met in increasing order of pow(o, p_i)."""
+    rng = np.random.default_rng(seed)
+    sc = cluster_scene(rng, n=30, spread=0.25)
+    orc = oracle.Oracle(sc)
+    P = np.asarray(sc.pos, np.float64)
+    W = np.asarray(sc.w, np.float64)
+    n_pairs = 0
+    for q in range(40):
+        # some cameras inside the cluster
+        o = random_dirs(rng, 1)[0] * (1.3 if q % 2 else 0.1)
+        d = random_dirs(rng, 1)[0]
+        if q % 2:
+            d = -o / 1.3 + 0.15 * d
+            d /= np.linalg.norm(d)
+        segs = orc.ray_segments(o, d)
+        keys = [np.sum((o - P[c]) ** 2) - W[c] for c, *_ in segs]
+        for a, b in zip(keys, keys[1:]):
+            assert a < b
+            n_pairs += 1
+    assert n_pairs > 30
+
+
+def test_cech_lists_equal_brute_force_for_tied_scene():
+    """Sec. 3.2: with R = r, only overlapping balls can share a face, so
+    clipping against the Cech neighbours (all overlapping spheres) renders
+    the same image as clipping against every site."""
+    rng = np.random.default_rng(51)
+    sc = cluster_scene(rng, n=40, spread=0.3, tied=True)
+    P = np.asarray(sc.pos, np.float64)
+    R = np.asarray(sc.R, np.float64)
+    lists = {i: [j for j in range(len(P)) if j != i and np.linalg.norm(P[i] - P[j]) < R[i] + R[j]]
+             for i in range(len(P))}
+    cam = cam_at([1.2, 0.3, 0.2], 24, 24)
+    a = oracle.Oracle(sc)
+    rgb0, T0 = a.render(cam)
+    a.set_candidate_lists(lists)
+    rgb1, T1 = a.render(cam)
+    assert np.array_equal(rgb0, rgb1) and np.array_equal(T0, T1)
+    assert np.any(T0 < 1)
+
+
+def test_prune_matches_brute_force(tiny):
+    sc, cam = tiny
+    a = oracle.Oracle(sc)
+    pix = np.stack(np.meshgrid(np.arange(0, 128, 3), np.arange(0, 128, 3)), -1).reshape(-1, 2)
+    rgb0, T0 = a.render(cam, pix)
+    a.prune_for(cam, pix)
+    rgb1, T1 = a.render(cam, pix)
+    assert np.array_equal(rgb0, rgb1) and np.array_equal(T0, T1)
+
+
+# --------------------------------------------------------------------- dipole
+
+def test_dipole_limits_and_complement():
+    """Sec. 3.3: the face splits the cell; a face outside the ball (offset >=
+    R) leaves the whole cell dense, offset <= -R makes it empty, and the two
+    halves (n, o) and (-n, -o) add up to the whole cell."""
+    rng = np.random.default_rng(61)
+    base = cluster_scene(rng, n=12, spread=0.2, dipole=True)
+    whole = base.copy()
+    whole.offset = np.asarray(base.R, np.float64) * 1.0000001
+    flip = base.copy()
+    flip.normal = -np.asarray(base.normal)
+    flip.offset = -np.asarray(base.offset)
+    gone = base.copy()
+    gone.offset = -np.asarray(base.R, np.float64) * 1.0000001
+    big = base.copy()
+    big.offset = np.full(base.n, 1e3)
+    ob, of, ow, og, obig = (oracle.Oracle(s) for s in (base, flip, whole, gone, big))
+    for _ in range(30):
+        o = random_dirs(rng, 1)[0] * 1.2
+        d = -o / 1.2 + rng.normal(0, 0.1, 3)
+        d /= np.linalg.norm(d)
+        sw = seg_dict(ow.ray_segments(o, d))
+        assert sw == seg_dict(obig.ray_segments(o, d))
+        assert og.ray_segments(o, d) == []
+        sb = seg_dict(ob.ray_segments(o, d))
+        sf = seg_dict(of.ray_segments(o, d))
+        for c, (ta, tb) in sw.items():
+            lb = sb.get(c, (0, 0))
+            lf = sf.get(c, (0, 0))
+            assert (lb[1] - lb[0]) + (lf[1] - lf[0]) == pytest.approx(tb - ta, abs=1e-12)
+
+
+# -------------------------------------------------------------------- texture
+
+def test_onb_properties():
+    rng = np.random.default_rng(71)
+    for n in list(random_dirs(rng, 50)) + [np.array([0, 0, 1.0]), np.array([0, 0, -1.0])]:
+        e1, e2 = oracle.onb(n)
+        M = np.stack([e1, e2, n])
+        np.testing.assert_allclose(M @ M.T, np.eye(3), atol=1e-14)
+        np.testing.assert_allclose(np.cross(e1, e2), n, atol=1e-14)
+    e1, e2 = oracle.onb(np.array([0, 0, 1.0]))
+    np.testing.assert_allclose(e1, [1, 0, 0])
+    np.testing.assert_allclose(e2, [0, 1, 0])
+
+
+def face_scene(tex, R=1.0):
+    # cell at the origin, face = plane z = 0 through p, dense half z <= 0
+    return make_scene([0, 0, 0], 0.2, R, 1.0, [0.1, 0.2, 0.3], [0, 0, 1.0], 0.0, tex)
+
+
+def test_texture_closed_forms():
+    """Eq. svrad on the face: zero texture gives the base colour; equal site
+    values add a constant; at the face centre all four sites weigh 1/4; a
+    sharp kernel picks the nearest site.  Sites (+-1/3, +-1/3) R in the
+    (e1, e2) frame, site-major (k = 0: (-,-), 1: (+,-), 2: (-,+), 3: (+,+))."""
+    rng = np.random.default_rng(81)
+    tex = rng.normal(0, 0.2, 12)
+    o_down, d_down = np.array([0.3, -0.35, 5.0]), np.array([0.0, 0.0, -1.0])
+    # zero texture
+    c = oracle.Oracle(face_scene(np.zeros(12))).cell_colour(0, o_down, d_down, 5.0, 5.5)
+    np.testing.assert_allclose(c, [0.1, 0.2, 0.3], atol=1e-15)
+    # equal site values
+    v = np.array([0.05, -0.1, 0.2])
+    c = oracle.Oracle(face_scene(np.tile(v, 4))).cell_colour(0, o_down, d_down, 5.0, 5.5)
+    np.testing.assert_allclose(c, [0.15, 0.1, 0.5], atol=1e-14)
+    # face centre: ray straight down the axis, entry at the face
+    orc = oracle.Oracle(face_scene(tex))
+    segs = orc.ray_segments([0, 0, 5.0], d_down)
+    assert segs[0][3] == ACT_DIPOLE
+    c = orc.cell_colour(0, [0, 0, 5.0], d_down, segs[0][1], segs[0][2])
+    np.testing.assert_allclose(c, [0.1, 0.2, 0.3] + tex.reshape(4, 3).mean(0), atol=1e-14)
+    # sharp kernel: nearest site to u = (0.3, -0.35) is k = 1
+    sharp = oracle.Oracle(face_scene(tex), kappa=400.0)
+    segs = sharp.ray_segments(o_down, d_down)
+    c = sharp.cell_colour(0, o_down, d_down, segs[0][1], segs[0][2])
+    np.testing.assert_allclose(c, [0.1, 0.2, 0.3] + tex[3:6], atol=1e-12)
+    # the same face point seen from below (exit through the face)
+    segs = sharp.ray_segments([0.3, -0.35, -5.0], [0, 0, 1.0])
+    assert segs[0][4] == ACT_DIPOLE
+    c2 = sharp.cell_colour(0, [0.3, -0.35, -5.0], [0, 0, 1.0], segs[0][1], segs[0][2])
+    np.testing.assert_allclose(c2, c, atol=1e-14)
+
+
+# -------------------------------------------------------------------- marching
+
+def march(sc, o, d, h, tmax):
+    """Midpoint marching with point classification only (the plain
+    definition of the cells); texture-free colours."""
+    T = 1.0
+    C = np.zeros(3)
+    P = np.asarray(sc.pos, np.float64)
+    for k in range(int(tmax / h)):
+        x = o + (k + 0.5) * h * d
+        i, ins = classify(sc, x)
+        if not ins:
+            continue
+        a = 1 - math.exp(-float(sc.sigma[i]) * h)
+        C += T * a * np.asarray(sc.rgb[i], np.float64)
+        T *= 1 - a
+    return C, T
+
+
+def test_compositing_matches_marching_on_ten_cells():
+    """Sec. 3.1: the segment sum equals the volume rendering integral; a
+    fine march with point-wise cell classification converges to it."""
+    rng = np.random.default_rng(91)
+    sc = cluster_scene(rng, n=10, spread=0.12)
+    orc = oracle.Oracle(sc)
+    for _ in range(4):
+        o = random_dirs(rng, 1)[0] * 0.9
+        d = -o / 0.9 + rng.normal(0, 0.05, 3)
+        d /= np.linalg.norm(d)
+        c_ref, T_ref = orc.render_rays(o[None], d[None])
+        errs = []
+        for h in (4e-3, 1e-3, 2.5e-4):
+            c, T = march(sc, o, d, h, 2.0)
+            errs.append(max(abs(T - T_ref[0]), np.max(np.abs(c - c_ref[0]))))
+        assert errs[-1] < 2e-3
+        assert errs[-1] <= errs[0] + 1e-12
+
+
+# ------------------------------------------------------------------ gradients
+
+def fd_scene(seed):
+    rng = np.random.default_rng(seed)
+    return cluster_scene(rng, n=9, spread=0.12, r=(0.06, 0.12), tex_std=0.2)
+
+
+@pytest.mark.parametrize("seed", [101, 102])
+def test_adjoint_matches_central_differences(seed):
+    """The hand adjoint equals FP64 central differences of the forward for
+    every parameter group, on a scene where cells clip each other."""
+    sc = fd_scene(seed)
+    cam = cam_at([0.55, 0.25, 0.15], 10, 10, fov=40.0)
+    orc = oracle.Oracle(sc)
+    rng = np.random.default_rng(seed + 1)
+    npix = cam.width * cam.height
+    gC = rng.normal(size=(npix, 3))
+    gT = rng.normal(size=npix)
+    G = orc.render_grad(cam, gC, gT)
+
+    def loss():
+        c, T = orc.render(cam)
+        return float(np.sum(c * gC) + np.sum(T * gT))
+
+    scale = {"pos": 1e-3, "w": 1e-4, "R": 1e-3, "sigma": 1e-3, "rgb": 1e-3, "normal": 1e-3,
+             "offset": 1e-3, "tex": 1e-3}
+    checked = 0
+    for key, arr in orc.params.items():
+        g = G[key]
+        flat = arr.reshape(-1)
+        gflat = np.asarray(g).reshape(-1)
+        nz = np.nonzero(np.abs(gflat) > 1e-8)[0]
+        assert nz.size > 0, key
+        for j in rng.choice(nz, size=min(6, nz.size), replace=False):
+            h = scale[key] * 1e-3
+            old = flat[j]
+            flat[j] = old + h
+            lp = loss()
+            flat[j] = old - h
+            lm = loss()
+            flat[j] = old
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - gflat[j]) <= 1e-5 * max(1.0, abs(fd)), (key, j, fd, gflat[j])
+            checked += 1
+    assert checked >= 40
+
+
+def test_gradient_of_zero_upstream_is_zero():
+    sc = fd_scene(103)
+    cam = cam_at([0.55, 0.25, 0.15], 6, 6)
+    G = oracle.Oracle(sc).render_grad(cam, np.zeros((36, 3)), np.zeros(36))
+    assert all(np.all(v == 0) for v in G.values())
+
+
+# -------------------------------------------------------------------- binning
+
+def test_binning_is_conservative_and_keys_ordered(tiny):
+    """Every pixel whose ray meets a cell's ball (t >= 0) lies in a tile of
+    that cell's rectangle; keys order cells by pow(o, p_i)."""
+    sc, cam = tiny
+    orc = oracle.Oracle(sc)
+    rect, key = orc.bin(cam)
+    P = np.asarray(sc.pos, np.float64)
+    R = np.asarray(sc.R, np.float64)
+    us, vs = np.meshgrid(np.arange(cam.width), np.arange(cam.height))
+    dirs = []
+    for u, v in zip(us.ravel(), vs.ravel()):
+        dirs.append(orc.ray(cam, u, v)[1])
+    D = np.array(dirs)
+    o = np.asarray(cam.origin, np.float64)
+    m = o - P                                          # [N,3]
+    b = D @ m.T                                        # [px, N]
+    c = np.sum(m * m, 1) - R * R
+    disc = b * b - c[None, :]
+    hit = (disc > 0) & (-b + np.sqrt(np.maximum(disc, 0)) > 0)
+    px, cell = np.nonzero(hit)
+    tx = us.ravel()[px] // 16
+    ty = vs.ravel()[px] // 16
+    r = rect[cell]
+    assert np.all((r[:, 0] <= tx) & (tx <= r[:, 2]) & (r[:, 1] <= ty) & (ty <= r[:, 3]))
+    pw = np.sum((P - o) ** 2, 1) - np.asarray(sc.w, np.float64)
+    assert np.array_equal(np.argsort(key, kind="stable"), np.argsort(pw, kind="stable"))
+
+
+def test_binning_rect_is_tight():
+    """For a sphere in front of the camera the rectangle is the tile cover
+    of its projected extent: sampled silhouette points reach every edge."""
+    from paper_2604_24994_gb300.inputs import look_at
+    rng = np.random.default_rng(7)
+    cam = look_at([3.0, 0.5, 0.2], 320, 240)
+    n = 200
+    pos = rng.uniform(-0.8, 0.8, (n, 3))
+    R = rng.uniform(0.02, 0.3, n)
+    sc = make_scene(pos, R * R, R)
+    rect, _ = oracle.Oracle(sc).bin(cam)
+    sph = random_dirs(rng, 20000)
+    Mr = np.asarray(cam.rot)
+    for i in range(n):
+        pts = pos[i] + R[i] * sph
+        xc = (pts - cam.origin) @ Mr.T
+        u = cam.fx * xc[:, 0] / xc[:, 2] + cam.cx
+        v = cam.fy * xc[:, 1] / xc[:, 2] + cam.cy
+        pu = np.ceil(u.min() - 0.5), np.floor(u.max() - 0.5)
+        pv = np.ceil(v.min() - 0.5), np.floor(v.max() - 0.5)
+        lo = np.array([max(pu[0], 0), max(pv[0], 0)])
+        hi = np.array([min(pu[1], cam.width - 1), min(pv[1], cam.height - 1)])
+        if np.any(lo > hi):
+            continue
+        # sampled extent inside the rect, and the rect at most one pixel row/column wider
+        assert rect[i, 0] <= lo[0] // 16 and rect[i, 2] >= hi[0] // 16
+        assert rect[i, 1] <= lo[1] // 16 and rect[i, 3] >= hi[1] // 16
+        assert rect[i, 0] >= (lo[0] - 2) // 16 and rect[i, 2] <= (hi[0] + 2) // 16
+        assert rect[i, 1] >= (lo[1] - 2) // 16 and rect[i, 3] <= (hi[1] + 2) // 16
