@@ -1,0 +1,183 @@
+/*
+ * powerfoam.h - C ABI of the GB300 (sm_103a) tile rasterizer for bounded
+ * power-diagram cells (Power Foam, arxiv 2604.24994).
+ *
+ * Conventions for every entry point
+ *   - All scene, image and gradient pointers are DEVICE pointers owned by the
+ *     caller.  The library never allocates or frees device memory; scratch
+ *     lives in a caller-provided workspace whose size pf_plan_workspace_bytes
+ *     reports.  A plan (pf_plan) is a small host object (layout + cameras).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy stream).
+ *     Calls only enqueue work on it and return; results are valid once the
+ *     stream reaches them.  The exceptions say so (pf_bin_sort with a
+ *     non-NULL n_instances, the pf_serve_* calls).
+ *   - Nothing throws across the ABI.  Every call returns a pf_status;
+ *     pf_status_string names it, pf_last_error_message gives detail for the
+ *     calling thread's last failure.
+ *   - Float data is IEEE binary32, little endian, C-contiguous.
+ *
+ * Scene parameters (Sec. 3.2-3.4 of the paper), N cells:
+ *   pos    [N,3]  site p_i
+ *   w      [N]    power weight w_i (pow(x,i) = |x - p_i|^2 - w_i, Eq. pow_dist)
+ *   R      [N]    bound radius of cell i's sphere
+ *   sigma  [N]    density of the dense half of the cell
+ *   rgb    [N,3]  base colour
+ *   normal [N,3]  dipole normal n_i (any non-zero length; used as n/|n|)
+ *   offset [N]    the face is { x : n^.(x - p_i) = offset_i }; the dense
+ *                 half is n^.(x - p_i) <= offset_i (Sec. 3.3)
+ *   tex    [N,12] four texture sites x RGB, site-major, 16-byte aligned
+ *                 (the soft-Voronoi radiance on the face, Eq. svrad)
+ *   nbr    [N,K]  int32 neighbour ids (-1 padded): every site whose radical
+ *                 plane can cut cell i's sphere must be listed (a Cech list,
+ *                 Sec. 3.2, is enough); extra entries never change the result.
+ */
+#ifndef POWERFOAM_H
+#define POWERFOAM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PF_OK = 0,
+    PF_ERR_INVALID_ARG = 1, /* null pointer, bad size, bad camera */
+    PF_ERR_CAPACITY = 2,    /* instance capacity too small; required size reported */
+    PF_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+    PF_ERR_TIMEOUT = 4,     /* a bounded wait ran out */
+    PF_ERR_BUSY = 5,        /* admission refused (serving) */
+    PF_ERR_NOT_FOUND = 6    /* unknown request id (serving) */
+} pf_status;
+
+typedef struct {
+    const float *pos, *w, *R, *sigma, *rgb, *normal, *offset, *tex;
+    const int32_t *nbr;
+    int32_t n_cells; /* N >= 0 */
+    int32_t k_nbr;   /* K in [0, 64] */
+} pf_scene;
+
+/* Pinhole camera: x_cam = rot (x_world - origin), OpenCV axes (x right,
+ * y down, z forward); pixel (u, v) is the ray through (u + 0.5, v + 0.5). */
+typedef struct {
+    double rot[9]; /* row-major world->camera rotation */
+    double origin[3];
+    double fx, fy, cx, cy;
+    int32_t width, height; /* 1..16384 each */
+} pf_camera;
+
+/* Gradient outputs, same shapes as the scene parameters; the backward ADDS
+ * into them (zero them first for a fresh gradient). */
+typedef struct {
+    float *pos, *w, *R, *sigma, *rgb, *normal, *offset, *tex;
+} pf_scene_grad;
+
+typedef struct pf_plan pf_plan;
+
+/* Work counters of one forward pass (filled when stats are enabled). */
+typedef struct {
+    uint64_t instances; /* (cell, tile) pairs after binning */
+    uint64_t candidates; /* (pixel, listed cell) pairs examined */
+    uint64_t hits;       /* non-empty (pixel, cell) segments */
+    uint64_t planes;     /* radical-plane clips evaluated */
+    uint64_t refined;    /* segment ends recomputed in FP64 */
+    uint64_t sphere_pass; /* candidates that passed the sphere test */
+} pf_stats;
+
+const char *pf_status_string(pf_status s);
+/* Detail of the calling thread's last failed call ("" if none). */
+const char *pf_last_error_message(void);
+
+/*
+ * Plans.  A plan fixes N, K, the views (their cameras and resolutions) and
+ * the capacity of the (cell, tile) instance arrays.  Multi-view calls work
+ * on all views at once; images of view v start at pixel offset
+ * sum_{u<v} W_u H_u of the concatenated outputs.
+ * Ownership: *out is owned by the caller and freed with pf_plan_destroy.
+ */
+pf_status pf_plan_create(int32_t n_cells, int32_t k_nbr, const pf_camera *cams, int32_t n_views,
+                         uint64_t inst_capacity, pf_plan **out);
+void pf_plan_destroy(pf_plan *plan);
+/* Bytes of device workspace the plan needs (256-byte aligned base). */
+pf_status pf_plan_workspace_bytes(const pf_plan *plan, uint64_t *bytes);
+/* Total pixels over all views. */
+pf_status pf_plan_pixels(const pf_plan *plan, uint64_t *pixels);
+/* Replace the cameras; resolutions must equal the plan's.  The new values
+ * are read by the next pf_project on any stream. */
+pf_status pf_plan_set_cameras(pf_plan *plan, const pf_camera *cams, int32_t n_views);
+/* Count work in the next forward passes (adds to the counters; 0 disables). */
+pf_status pf_plan_enable_stats(pf_plan *plan, int32_t enable);
+/* Read the counters, then reset them (synchronises `stream`). */
+pf_status pf_plan_read_stats(pf_plan *plan, void *ws, pf_stats *out, void *stream);
+
+/*
+ * View-independent cell records (Sec. 3.2-3.4).  For every cell, in FP64:
+ * the unit normal and face frame, and the radical planes
+ *   x.(p_j - p_i) <= (|p_j|^2 - |p_i|^2 + w_i - w_j) / 2
+ * of its listed neighbours (the definition of pow gives +w_i - w_j; the
+ * appendix's Eq. power_bisector prints the weights the other way round),
+ * kept only where the plane reaches the bounding sphere (Sec. 3.2: other
+ * planes never cut the cell).  Run after any scene change.
+ */
+pf_status pf_prepare(const pf_scene *scene, pf_plan *plan, void *ws, void *stream);
+
+/*
+ * Per view and cell, in FP64: the camera-relative site offset (stored as a
+ * float pair), the painter key pow(o, p_i) (Thm. power_painter: ordering by
+ * power distance from the camera centre is a valid painter's order), and
+ * the exact screen bounding box of the sphere, as a 16x16 tile rectangle.
+ */
+pf_status pf_project(const pf_scene *scene, pf_plan *plan, void *ws, void *stream);
+
+/*
+ * Duplicate every (cell, tile) pair, group by tile and sort each tile's list
+ * by (key, cell index) (Sec. 3.2: a global sort by depth "similar to 3DGS",
+ * here by power distance).  If n_instances is non-NULL the call
+ * synchronises the stream and returns the instance count; then
+ * PF_ERR_CAPACITY means the plan's capacity was too small (*n_instances is
+ * the size needed; re-plan and repeat pf_prepare/pf_project/pf_bin_sort).
+ * With NULL it stays asynchronous; an overflow is then only visible through
+ * pf_plan_read_stats / a later synchronous call, and the lists are cut at
+ * capacity (memory-safe, images wrong).
+ */
+pf_status pf_bin_sort(pf_plan *plan, void *ws, uint64_t *n_instances, void *stream);
+
+/*
+ * Forward render (Sec. 3.1-3.4): per pixel, walk the tile's sorted list,
+ * cut the ray with each cell's sphere, radical planes and dense half,
+ * composite alpha = 1 - exp(-sigma l) and the soft-Voronoi face colour front
+ * to back over a black background; stop once T < 1e-6.
+ * Outputs (device, concatenated over views): rgb [P,3], T [P] (final
+ * transmittance) and last [P] (1 + list index of the last contributing
+ * cell; 0 if none).  T and last are the checkpoint pf_render_bwd replays.
+ */
+pf_status pf_render_fwd(const pf_scene *scene, pf_plan *plan, void *ws, float *rgb, float *T, uint32_t *last,
+                        void *stream);
+
+/*
+ * Adjoint of pf_render_fwd for upstream dL/drgb [P,3] and dL/dT [P]
+ * (dL_dT may be NULL for zero).  Replays each tile back to front from the
+ * checkpoint (T, last) and ADDS dL/d(parameter) into `grad` (every pointer
+ * non-NULL).  Requires the same plan/workspace state as the forward.
+ */
+pf_status pf_render_bwd(const pf_scene *scene, pf_plan *plan, void *ws, const float *dL_drgb, const float *dL_dT,
+                        const float *T, const uint32_t *last, const pf_scene_grad *grad, void *stream);
+
+/*
+ * Copy the binning results to HOST buffers (synchronises `stream`), for
+ * inspection and tests.  tile_start [T+1] (T = tiles over all views, view v
+ * first at its tile base, row-major tiles of 16x16 px): tile t's list is
+ * cells[tile_start[t] .. tile_start[t+1]), cell indices sorted by (key,
+ * index).  cells [capacity].  keys [V*N] painter keys (order-preserving bits
+ * of pow(o, p_i) in FP64) and rects [V*N][4] (tx0, ty0, tx1, ty1 with
+ * tx0 > tx1 when empty) may be NULL.
+ */
+pf_status pf_read_bins(pf_plan *plan, void *ws, uint32_t *tile_start, uint32_t *cells, uint64_t *keys,
+                       uint16_t *rects, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POWERFOAM_H */

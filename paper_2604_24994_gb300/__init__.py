@@ -1,0 +1,21 @@
+"""GB300 (sm_103a) tile rasterizer for bounded power-diagram cells
+(Power Foam, arxiv 2604.24994): forward render, hand-written adjoint and a
+continuous-batching server behind a C ABI (include/powerfoam.h).
+
+    from paper_2604_24994_gb300 import inputs, DeviceScene, Renderer, render
+"""
+from . import inputs  # noqa: F401
+
+__all__ = ["inputs", "DeviceScene", "Renderer", "RenderFunction", "render", "build_library"]
+
+
+def build_library(force: bool = False) -> str:
+    from .build import build
+    return build(force=force)
+
+
+def __getattr__(name):
+    if name in ("DeviceScene", "Renderer", "RenderFunction", "render", "Plan"):
+        from . import api
+        return getattr(api, name)
+    raise AttributeError(name)

@@ -1,0 +1,247 @@
+"""Python-level API over the C ABI: device scenes, plans with workspaces,
+forward/backward calls and a torch.autograd.Function.
+
+PyTorch provides device memory and streams only; every step of the
+rendering path runs in the library's kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import check, lib, ptr
+
+PARAMS = ("pos", "w", "R", "sigma", "rgb", "normal", "offset", "tex")
+
+
+class DeviceScene:
+    """Scene parameters as contiguous float32 CUDA tensors (+ int32 lists)."""
+
+    def __init__(self, params: dict, nbr: torch.Tensor):
+        self.params = params
+        self.nbr = nbr
+        self.n = int(params["pos"].shape[0])
+        self.k = int(nbr.shape[1]) if nbr.dim() == 2 else 0
+
+    @staticmethod
+    def from_numpy(scene, device="cuda", requires_grad=False) -> "DeviceScene":
+        params = {}
+        for k in PARAMS:
+            a = np.ascontiguousarray(getattr(scene, k), np.float32)
+            t = torch.from_numpy(a).to(device)
+            if requires_grad:
+                t.requires_grad_(True)
+            params[k] = t
+        nbr = torch.from_numpy(np.ascontiguousarray(scene.nbr, np.int32)).to(device)
+        return DeviceScene(params, nbr)
+
+    def struct(self, params: dict | None = None) -> _lib.Scene:
+        p = self.params if params is None else params
+        s = _lib.Scene()
+        for k in PARAMS:
+            t = p[k]
+            if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+                raise ValueError(f"scene parameter {k} must be a contiguous float32 CUDA tensor")
+            setattr(s, k, t.data_ptr() if t.numel() else None)
+        s.nbr = self.nbr.data_ptr() if self.nbr.numel() else None
+        s.n_cells = self.n
+        s.k_nbr = self.k
+        return s
+
+
+class Plan:
+    """A C plan (layout + cameras) with its device workspace."""
+
+    def __init__(self, n: int, k: int, cams, capacity: int, device="cuda"):
+        self.n, self.k = n, k
+        self.cams = list(cams)
+        self.capacity = int(capacity)
+        self.handle = C.c_void_p()
+        arr = _lib.camera_array(self.cams)
+        check(lib().pf_plan_create(n, k, arr, len(self.cams), self.capacity, C.byref(self.handle)),
+              "pf_plan_create")
+        b = C.c_uint64()
+        check(lib().pf_plan_workspace_bytes(self.handle, C.byref(b)), "pf_plan_workspace_bytes")
+        self.ws_bytes = int(b.value)
+        self.ws = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=device)
+        px = C.c_uint64()
+        check(lib().pf_plan_pixels(self.handle, C.byref(px)), "pf_plan_pixels")
+        self.pixels = int(px.value)
+
+    def set_cameras(self, cams):
+        cams = list(cams)
+        check(lib().pf_plan_set_cameras(self.handle, _lib.camera_array(cams), len(cams)), "pf_plan_set_cameras")
+        self.cams = cams
+
+    def __del__(self):
+        try:
+            if self.handle:
+                lib().pf_plan_destroy(self.handle)
+                self.handle = C.c_void_p()
+        except Exception:
+            pass
+
+    @property
+    def ws_ptr(self):
+        return self.ws.data_ptr()
+
+
+def _stream():
+    return _lib.stream_ptr(torch.cuda.current_stream())
+
+
+class Renderer:
+    """Renders a DeviceScene from a fixed set of cameras (one or many views,
+    any resolutions).  The instance capacity grows automatically."""
+
+    def __init__(self, n: int, k: int, cams, capacity: int | None = None, device="cuda"):
+        self.device = device
+        cams = list(cams)
+        if capacity is None:
+            px = sum(c.width * c.height for c in cams)
+            capacity = max(1 << 16, min(8 * n * len(cams) + px // 16, 0xE0000000))
+        self.plan = Plan(n, k, cams, capacity, device)
+        self.generation = 0
+        self.n_instances = 0
+
+    @property
+    def cams(self):
+        return self.plan.cams
+
+    def set_cameras(self, cams):
+        cams = list(cams)
+        if [(c.width, c.height) for c in cams] == [(c.width, c.height) for c in self.plan.cams]:
+            self.plan.set_cameras(cams)
+        else:
+            self.plan = Plan(self.plan.n, self.plan.k, cams, self.plan.capacity, self.device)
+        self.generation += 1
+
+    def bin(self, scene: DeviceScene, params: dict | None = None, sync: bool = True):
+        """pf_prepare + pf_project + pf_bin_sort (re-planning on overflow)."""
+        s = scene.struct(params)
+        st = _stream()
+        for _ in range(3):
+            P = self.plan
+            check(lib().pf_prepare(C.byref(s), P.handle, P.ws_ptr, st), "pf_prepare")
+            check(lib().pf_project(C.byref(s), P.handle, P.ws_ptr, st), "pf_project")
+            if not sync:
+                check(lib().pf_bin_sort(P.handle, P.ws_ptr, None, st), "pf_bin_sort")
+                break
+            n = C.c_uint64()
+            r = lib().pf_bin_sort(P.handle, P.ws_ptr, C.byref(n), st)
+            self.n_instances = int(n.value)
+            if r == _lib.PF_ERR_CAPACITY:
+                cap = min(int(n.value * 1.25) + 1024, 0xE0000000)
+                self.plan = Plan(P.n, P.k, P.cams, cap, self.device)
+                continue
+            check(r, "pf_bin_sort")
+            break
+        self.generation += 1
+        return self.generation
+
+    def _alloc_out(self):
+        P = self.plan
+        rgb = torch.empty((P.pixels, 3), dtype=torch.float32, device=self.device)
+        T = torch.empty(P.pixels, dtype=torch.float32, device=self.device)
+        last = torch.empty(P.pixels, dtype=torch.int32, device=self.device)
+        return rgb, T, last
+
+    def render_fwd(self, scene: DeviceScene, params: dict | None = None, out=None):
+        """pf_render_fwd on the current bins: flat rgb [P,3], T [P], last [P]."""
+        rgb, T, last = out if out is not None else self._alloc_out()
+        P = self.plan
+        check(lib().pf_render_fwd(C.byref(scene.struct(params)), P.handle, P.ws_ptr, rgb.data_ptr(), T.data_ptr(),
+                                  last.data_ptr(), _stream()), "pf_render_fwd")
+        return rgb, T, last
+
+    def forward(self, scene: DeviceScene, params: dict | None = None, sync: bool = True):
+        self.bin(scene, params, sync=sync)
+        return self.render_fwd(scene, params)
+
+    def backward(self, scene: DeviceScene, dL_drgb, dL_dT, T, last, params: dict | None = None, grads=None):
+        """pf_render_bwd: returns a dict of gradient tensors (added into
+        `grads` when given)."""
+        p = scene.params if params is None else params
+        if grads is None:
+            grads = {k: torch.zeros_like(p[k]) for k in PARAMS}
+        g = _lib.SceneGrad()
+        for k in PARAMS:
+            setattr(g, k, grads[k].data_ptr() if grads[k].numel() else None)
+        dL_drgb = dL_drgb.contiguous().float()
+        dL_dT = None if dL_dT is None else dL_dT.contiguous().float()
+        P = self.plan
+        check(lib().pf_render_bwd(C.byref(scene.struct(params)), P.handle, P.ws_ptr, dL_drgb.data_ptr(),
+                                  ptr(dL_dT), T.data_ptr(), last.data_ptr(), C.byref(g), _stream()),
+              "pf_render_bwd")
+        return grads
+
+    def stats(self):
+        s = _lib.Stats()
+        P = self.plan
+        check(lib().pf_plan_read_stats(P.handle, P.ws_ptr, C.byref(s), _stream()), "pf_plan_read_stats")
+        return {f: int(getattr(s, f)) for f, _ in _lib.Stats._fields_}
+
+    def enable_stats(self, on: bool = True):
+        check(lib().pf_plan_enable_stats(self.plan.handle, 1 if on else 0), "pf_plan_enable_stats")
+
+    def read_bins(self):
+        """Host copies of (tile_start [T+1], cells [capacity], keys [V*N], rects [V*N,4])."""
+        P = self.plan
+        T = sum(((c.width + 15) // 16) * ((c.height + 15) // 16) for c in P.cams)
+        ts = np.zeros(T + 1, np.uint32)
+        cells = np.zeros(max(P.capacity, 1), np.uint32)
+        keys = np.zeros(max(P.n * len(P.cams), 1), np.uint64)
+        rects = np.zeros((max(P.n * len(P.cams), 1), 4), np.uint16)
+        check(lib().pf_read_bins(P.handle, P.ws_ptr, ts.ctypes.data, cells.ctypes.data, keys.ctypes.data,
+                                 rects.ctypes.data, _stream()), "pf_read_bins")
+        return ts, cells, keys, rects
+
+    def split(self, flat):
+        """Per-view images from a flat per-pixel tensor."""
+        out = []
+        o = 0
+        for c in self.cams:
+            n = c.width * c.height
+            out.append(flat[o:o + n].view(c.height, c.width, *flat.shape[1:]))
+            o += n
+        return out
+
+
+class RenderFunction(torch.autograd.Function):
+    """(pos, w, R, sigma, rgb, normal, offset, tex) -> (rgb [P,3], T [P]).
+
+    The backward replays the forward's checkpoint (T, last) tile by tile,
+    back to front, through pf_render_bwd."""
+
+    @staticmethod
+    def forward(ctx, renderer: Renderer, scene: DeviceScene, *params):
+        pd = dict(zip(PARAMS, [p.detach() for p in params]))
+        gen = renderer.bin(scene, pd)
+        rgb, T, last = renderer.render_fwd(scene, pd)
+        ctx.renderer = renderer
+        ctx.scene = scene
+        ctx.gen = gen
+        ctx.save_for_backward(T, last, *params)
+        return rgb, T
+
+    @staticmethod
+    def backward(ctx, g_rgb, g_T):
+        T, last, *params = ctx.saved_tensors
+        r = ctx.renderer
+        pd = dict(zip(PARAMS, [p.detach() for p in params]))
+        if r.generation != ctx.gen:  # the workspace was reused: rebuild the same bins
+            r.bin(ctx.scene, pd)
+        if g_rgb is None:
+            g_rgb = torch.zeros((T.shape[0], 3), device=T.device)
+        grads = r.backward(ctx.scene, g_rgb, g_T, T, last, pd)
+        return (None, None, *[grads[k] for k in PARAMS])
+
+
+def render(renderer: Renderer, scene: DeviceScene, params: dict | None = None):
+    """Differentiable render of all the renderer's views: flat rgb [P,3], T [P]."""
+    p = scene.params if params is None else params
+    return RenderFunction.apply(renderer, scene, *[p[k] for k in PARAMS])

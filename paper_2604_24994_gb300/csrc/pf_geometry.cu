@@ -1,0 +1,210 @@
+// pf_prepare / pf_project kernels: FP64 geometry per cell and per (view, cell).
+#include <math_constants.h>
+
+#include "pf_internal.cuh"
+
+namespace pf {
+
+// ---------------------------------------------------------------------------
+// View-independent cell records.
+//
+// Per cell, in FP64: unit normal, face frame (e1, e2) / R, and the radical
+// planes of the listed neighbours.  The plane between i and j is
+//   (x - p_i).a <= g,  a = p_j - p_i,  g = (|a|^2 + w_i - w_j) / 2
+// (pow(x,i) <= pow(x,j) with pow = |x - p|^2 - w, Eq. pow_dist); it is
+// stored normalised, (a/|a|, g/|a|), so g/|a| is the signed distance of
+// the plane from p_i.  A plane at distance >= R_i never reaches the ball
+// and is dropped (Sec. 3.2: it cannot cut the cell); one at distance
+// < -R_i excludes the whole ball and marks the cell empty.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) prepare_kernel(pf_scene s, float *__restrict__ cellrec,
+                                                      int32_t *__restrict__ cellnp, float4 *__restrict__ planes,
+                                                      int2 *__restrict__ plane_nb) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s.n_cells) return;
+    const int K = s.k_nbr;
+    const double px = s.pos[3 * i], py = s.pos[3 * i + 1], pz = s.pos[3 * i + 2];
+    const double wi = s.w[i];
+    const double R = s.R[i];
+    const double nx0 = s.normal[3 * i], ny0 = s.normal[3 * i + 1], nz0 = s.normal[3 * i + 2];
+    const double nl = sqrt(nx0 * nx0 + ny0 * ny0 + nz0 * nz0);
+    const double nx = nx0 / nl, ny = ny0 / nl, nz = nz0 / nl;
+    // orthonormal face frame, branchless construction of Duff et al. (JCGT 2017)
+    const double sg = nz >= 0.0 ? 1.0 : -1.0;
+    const double ca = -1.0 / (sg + nz);
+    const double cb = nx * ny * ca;
+    const double iR = R > 0.0 ? 1.0 / R : 0.0;
+    const double e1x = (1.0 + sg * nx * nx * ca) * iR, e1y = sg * cb * iR, e1z = -sg * nx * iR;
+    const double e2x = cb * iR, e2y = (sg + ny * ny * ca) * iR, e2z = -ny * iR;
+
+    bool empty = !(R > 0.0) || !(nl > 0.0);
+    int cnt = 0;
+    for (int k = 0; k < K; k++) {
+        const int j = s.nbr[(int64_t)i * K + k];
+        if (j < 0 || j >= s.n_cells || j == i) continue;
+        const double ax = (double)s.pos[3 * j] - px, ay = (double)s.pos[3 * j + 1] - py,
+                     az = (double)s.pos[3 * j + 2] - pz;
+        const double wj = s.w[j];
+        const double L2 = ax * ax + ay * ay + az * az;
+        if (L2 == 0.0) {  // coincident sites: pow(x,i) <= pow(x,j) iff w_i >= w_j
+            if (wi < wj) empty = true;
+            continue;
+        }
+        const double L = sqrt(L2);
+        const double g = (L2 + wi - wj) / (2.0 * L);
+        if (g < -R * (1.0 + 1e-6)) empty = true;
+        if (g < R * (1.0 + 1e-6)) {
+            const double iL = 1.0 / L;
+            planes[(int64_t)i * K + cnt] = make_float4((float)(ax * iL), (float)(ay * iL), (float)(az * iL), (float)g);
+            plane_nb[(int64_t)i * K + cnt] = make_int2(j, __float_as_int((float)L));
+            cnt++;
+        }
+    }
+    cellnp[i] = cnt;
+    float4 *cr = reinterpret_cast<float4 *>(cellrec + (int64_t)i * CELLREC_F);
+    cr[0] = make_float4((float)nx, (float)ny, (float)nz, s.offset[i]);
+    cr[1] = make_float4((float)e1x, (float)e1y, (float)e1z, (float)R);
+    cr[2] = make_float4((float)e2x, (float)e2y, (float)e2z, s.sigma[i]);
+    cr[3] = make_float4(s.rgb[3 * i], s.rgb[3 * i + 1], s.rgb[3 * i + 2], __int_as_float(empty ? 1 : 0));
+    const float4 *tx = reinterpret_cast<const float4 *>(s.tex + (int64_t)i * 12);
+    cr[4] = tx[0];
+    cr[5] = tx[1];
+    cr[6] = tx[2];
+    cr[7] = make_float4((float)nl, (float)wi, 0.f, 0.f);
+}
+
+// ---------------------------------------------------------------------------
+// Per (view, cell) projection.
+//
+// Painter key: pow(o, p_i) = |p_i - o|^2 - w_i in FP64 (Thm. power_painter),
+// mapped to order-preserving unsigned bits.
+//
+// Tile rectangle: the exact image-plane bounding box of the sphere (p_i,
+// R_i), from the tangent lines through the camera centre in the camera's
+// x-z and y-z planes, widened by 1e-6 px, covering every pixel whose centre
+// lies inside it.  A sphere reaching z <= 0 gets the whole image unless it
+// lies entirely outside one side plane of the frustum; one entirely behind
+// is dropped.  Every operation is an explicitly rounded IEEE double
+// operation (no contraction), so a CPU evaluating the same rule in the same
+// order gets the same rectangles bit for bit.
+//
+// Site offset m = o - p_i is stored as a float pair (hi + lo ~ 48 bits) for
+// the renderer's compensated products; Rt^2 is a conservative radius^2 for
+// the cheap single-float sphere test (covers its rounding).
+// ---------------------------------------------------------------------------
+#define DADD __dadd_rn
+#define DSUB __dsub_rn
+#define DMUL __dmul_rn
+#define DDIV __ddiv_rn
+#define DSQRT __dsqrt_rn
+
+__global__ void __launch_bounds__(256) project_kernel(pf_scene s, const ViewDev *__restrict__ views, int nv,
+                                                      const float *__restrict__ cellrec, float *__restrict__ viewrec,
+                                                      ushort4 *__restrict__ rect_out,
+                                                      unsigned long long *__restrict__ key_out,
+                                                      uint32_t *__restrict__ cnt_out, int32_t *__restrict__ diff) {
+    const int64_t N = s.n_cells;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= N * nv) return;
+    const int v = (int)(idx / N);
+    const int64_t i = idx - (int64_t)v * N;
+    const ViewDev &V = views[v];
+    const double px = s.pos[3 * i], py = s.pos[3 * i + 1], pz = s.pos[3 * i + 2];
+    const double dx = DSUB(px, V.origin[0]);
+    const double dy = DSUB(py, V.origin[1]);
+    const double dz = DSUB(pz, V.origin[2]);
+    const double pw = DSUB(DADD(DADD(DMUL(dx, dx), DMUL(dy, dy)), DMUL(dz, dz)), (double)s.w[i]);
+    unsigned long long bits = (unsigned long long)__double_as_longlong(pw);
+    key_out[idx] = (bits >> 63) ? ~bits : (bits | 0x8000000000000000ull);
+
+    // camera-relative offset m = o - p as a float pair
+    {
+        const double mx = -dx, my = -dy, mz = -dz;
+        const float hx = __double2float_rn(mx), hy = __double2float_rn(my), hz = __double2float_rn(mz);
+        const float lx = __double2float_rn(mx - (double)hx), ly = __double2float_rn(my - (double)hy),
+                    lz = __double2float_rn(mz - (double)hz);
+        const double mlen = sqrt(mx * mx + my * my + mz * mz);
+        const double Rt = (double)s.R[i] * (1.0 + 0x1p-20) + mlen * 0x1p-20;
+        const float rt2 = __double2float_ru(Rt * Rt * (1.0 + 0x1p-20));
+        float4 *vr = reinterpret_cast<float4 *>(viewrec + idx * VIEWREC_F);
+        vr[0] = make_float4(hx, hy, hz, rt2);
+        vr[1] = make_float4(lx, ly, lz, 0.f);
+    }
+
+    ushort4 rc = make_ushort4(1, 1, 0, 0);
+    uint32_t count = 0;
+    const double *M = V.rot;
+    const double X = DADD(DADD(DMUL(M[0], dx), DMUL(M[1], dy)), DMUL(M[2], dz));
+    const double Y = DADD(DADD(DMUL(M[3], dx), DMUL(M[4], dy)), DMUL(M[5], dz));
+    const double Z = DADD(DADD(DMUL(M[6], dx), DMUL(M[7], dy)), DMUL(M[8], dz));
+    const double r = s.R[i];
+    bool vis = !(DADD(Z, r) <= 0.0);
+    const double W = V.width, H = V.height;
+    if (vis) {
+        const double kl = DDIV(DSUB(0.0, V.cx), V.fx), kr = DDIV(DSUB(W, V.cx), V.fx);
+        const double ku = DDIV(DSUB(0.0, V.cy), V.fy), kd = DDIV(DSUB(H, V.cy), V.fy);
+        if (DSUB(X, DMUL(kr, Z)) > DMUL(r, DSQRT(DADD(1.0, DMUL(kr, kr))))) vis = false;
+        if (DSUB(DMUL(kl, Z), X) > DMUL(r, DSQRT(DADD(1.0, DMUL(kl, kl))))) vis = false;
+        if (DSUB(Y, DMUL(kd, Z)) > DMUL(r, DSQRT(DADD(1.0, DMUL(kd, kd))))) vis = false;
+        if (DSUB(DMUL(ku, Z), Y) > DMUL(r, DSQRT(DADD(1.0, DMUL(ku, ku))))) vis = false;
+    }
+    if (vis) {
+        double ulo = -CUDART_INF, uhi = CUDART_INF, vlo = -CUDART_INF, vhi = CUDART_INF;
+        if (Z > r) {
+            const double rr = DMUL(r, r);
+            const double zr = DSUB(DMUL(Z, Z), rr);
+            const double sx = DSQRT(DSUB(DADD(DMUL(X, X), DMUL(Z, Z)), rr));
+            const double sy = DSQRT(DSUB(DADD(DMUL(Y, Y), DMUL(Z, Z)), rr));
+            const double kxl = DDIV(DSUB(DMUL(X, Z), DMUL(r, sx)), zr);
+            const double kxh = DDIV(DADD(DMUL(X, Z), DMUL(r, sx)), zr);
+            const double kyl = DDIV(DSUB(DMUL(Y, Z), DMUL(r, sy)), zr);
+            const double kyh = DDIV(DADD(DMUL(Y, Z), DMUL(r, sy)), zr);
+            ulo = DADD(DMUL(V.fx, kxl), V.cx);
+            uhi = DADD(DMUL(V.fx, kxh), V.cx);
+            vlo = DADD(DMUL(V.fy, kyl), V.cy);
+            vhi = DADD(DMUL(V.fy, kyh), V.cy);
+        }
+        double a0 = ceil(DSUB(DSUB(ulo, 0.5), 1e-6)), a1 = floor(DADD(DSUB(uhi, 0.5), 1e-6));
+        double b0 = ceil(DSUB(DSUB(vlo, 0.5), 1e-6)), b1 = floor(DADD(DSUB(vhi, 0.5), 1e-6));
+        if (a0 < 0.0) a0 = 0.0;
+        if (b0 < 0.0) b0 = 0.0;
+        if (a1 > W - 1.0) a1 = W - 1.0;
+        if (b1 > H - 1.0) b1 = H - 1.0;
+        if (!(a0 > a1 || b0 > b1)) {
+            const int x0 = (int)a0 / TILE, y0 = (int)b0 / TILE, x1 = (int)a1 / TILE, y1 = (int)b1 / TILE;
+            rc = make_ushort4((unsigned short)x0, (unsigned short)y0, (unsigned short)x1, (unsigned short)y1);
+            count = (uint32_t)(x1 - x0 + 1) * (uint32_t)(y1 - y0 + 1);
+            // 2D difference grid: +1 at (x0,y0), -1 at (x1+1,y0) and (x0,y1+1), +1 at (x1+1,y1+1)
+            const int gw = V.tiles_x + 1;
+            int32_t *g = diff + V.diff_base;
+            atomicAdd(&g[y0 * gw + x0], 1);
+            atomicAdd(&g[y0 * gw + x1 + 1], -1);
+            atomicAdd(&g[(y1 + 1) * gw + x0], -1);
+            atomicAdd(&g[(y1 + 1) * gw + x1 + 1], 1);
+        }
+    }
+    rect_out[idx] = rc;
+    cnt_out[idx] = count;
+}
+
+cudaError_t launch_prepare(const pf_scene &s, const Plan &p, const WS &w, cudaStream_t st) {
+    if (p.n == 0) return cudaSuccess;
+    const int threads = 256;
+    const int blocks = (p.n + threads - 1) / threads;
+    prepare_kernel<<<blocks, threads, 0, st>>>(s, w.cellrec, w.cellnp, w.planes, w.plane_nb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_project(const pf_scene &s, const Plan &p, const WS &w, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(w.diff, 0, sizeof(int32_t) * (size_t)p.total_diff, st);
+    if (e != cudaSuccess) return e;
+    const int64_t total = (int64_t)p.n * p.nv;
+    if (total == 0) return cudaSuccess;
+    const int threads = 256;
+    const int64_t blocks = (total + threads - 1) / threads;
+    project_kernel<<<(unsigned)blocks, threads, 0, st>>>(s, w.views, p.nv, w.cellrec, w.viewrec, w.rect, w.key,
+                                                         w.cnt, w.diff);
+    return cudaGetLastError();
+}
+
+}  // namespace pf

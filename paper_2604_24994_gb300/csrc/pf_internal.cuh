@@ -1,0 +1,133 @@
+// Internal definitions shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "powerfoam.h"
+
+namespace pf {
+
+constexpr int TILE = 16;               // tile edge in pixels
+constexpr int TILE_PIX = TILE * TILE;  // one thread per pixel
+constexpr int BATCH = 32;              // cells staged per shared-memory batch
+constexpr int MAX_K = 64;              // neighbour list width limit
+constexpr int CELLREC_F = 32;          // floats per view-independent cell record
+constexpr int VIEWREC_F = 8;           // floats per (view, cell) record
+constexpr int ACC_F = 32;              // gradient accumulator floats per cell
+constexpr float T_EPS = 1e-6f;         // forward stops once T drops below this
+constexpr float X_CAP = 60.0f;         // sigma * l is capped (alpha = 1 - e^-60)
+constexpr float KAPPA = 6.0f;          // soft-Voronoi sharpness, units of 1/R
+constexpr float SITE = 1.0f / 3.0f;    // texture sites at (+-1/3, +-1/3) R
+
+// Cell record layout (floats), one 128-byte line per cell.
+enum : int {
+    CR_N = 0,     // [0..2] unit normal, [3] offset
+    CR_OFF = 3,
+    CR_E1 = 4,    // [4..6] e1 / R,     [7] R
+    CR_R = 7,
+    CR_E2 = 8,    // [8..10] e2 / R,    [11] sigma
+    CR_SIG = 11,
+    CR_RGB = 12,  // [12..14] rgb,      [15] flags (bit 0: empty)
+    CR_FLAGS = 15,
+    CR_TEX = 16,  // [16..27] texture, site-major
+    CR_NLEN = 28, // [28] |n|
+    CR_W = 29     // [29] w
+};
+
+// Gradient accumulator layout (floats per cell).
+enum : int {
+    G_P = 0,     // [0..2] position
+    G_W = 3,     // [3] weight
+    G_R = 4,     // [4] bound radius
+    G_SIG = 5,   // [5] density
+    G_N = 6,     // [6..8] unit normal (projected to n in the finalize pass)
+    G_OFF = 9,   // [9] offset
+    G_TEX = 10,  // [10..21] texture (rgb is their sum)
+    G_NB_A = 22, // [22..25] entry-side neighbour (p_j, w_j)
+    G_NB_B = 26, // [26..29] exit-side neighbour
+    G_USED = 22
+};
+
+// Per-view constants on the device.
+struct ViewDev {
+    double rot[9];
+    double origin[3];
+    double fx, fy, cx, cy;
+    double ifx, ify;          // 1/fx, 1/fy
+    int32_t width, height;
+    int32_t tiles_x, tiles_y;
+    int64_t tile_base;        // first global tile id of this view
+    int64_t pix_base;         // first pixel of this view in the outputs
+    int64_t diff_base;        // offset of this view's (tx+1)(ty+1) difference grid
+};
+
+struct Counters {
+    unsigned long long total_inst;  // instances required
+    unsigned int overflow;          // 1 if total_inst > capacity
+    unsigned int pad;
+    unsigned long long stats[8];    // pf_stats fields after `instances`
+};
+
+// Workspace layout (byte offsets into the caller's buffer).
+struct Layout {
+    uint64_t views, cellrec, cellnp, planes, plane_nb, viewrec, rect, key, cnt, celloff, diff, tile_start,
+        tile_cursor, scan_tmp, inst_key, inst_cell, inst_sorted, sort_tmp_key, sort_tmp_cell, counters, acc,
+        total;
+    uint64_t scan_tmp_elems;
+};
+
+struct Plan;
+
+// Device pointers for one call, resolved from the layout.
+struct WS {
+    ViewDev *views;
+    float *cellrec;        // [N][32]
+    int32_t *cellnp;       // [N] relevant planes
+    float4 *planes;        // [N][K] (unit a, plane distance g/|a|)
+    int2 *plane_nb;        // [N][K] (neighbour j, |a| as float bits)
+    float *viewrec;        // [V][N][8]: m_hi.xyz, Rt^2, m_lo.xyz, pad
+    ushort4 *rect;         // [V][N] tile rect (x0, y0, x1, y1), empty: x0 > x1
+    unsigned long long *key;  // [V][N]
+    uint32_t *cnt;         // [V][N] instances of the cell in the view
+    uint32_t *celloff;     // [V][N] exclusive scan of cnt
+    int32_t *diff;         // 2D difference grids of all views
+    uint32_t *tile_start;  // [T+1]
+    uint32_t *tile_cursor; // [T]
+    uint32_t *scan_tmp;
+    unsigned long long *inst_key;  // [cap]
+    uint32_t *inst_cell;   // [cap]
+    uint32_t *inst_sorted; // [cap]
+    unsigned long long *sort_tmp_key;
+    uint32_t *sort_tmp_cell;
+    Counters *counters;
+    float *acc;            // [N][32]
+};
+
+struct Plan {
+    int32_t n, k, nv;
+    uint64_t cap;
+    int64_t total_tiles, total_pixels, total_diff;
+    ViewDev *views_host;   // host copy, uploaded by pf_project
+    Layout L;
+    int stats;
+    WS ws(void *base) const;
+};
+
+// ------------------------------------------------------------------ helpers
+__host__ __device__ inline uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
+
+void set_error(const char *fmt, ...);
+pf_status cuda_status(cudaError_t e, const char *what);
+
+// kernels launched from the C API (defined in the .cu files)
+cudaError_t launch_prepare(const pf_scene &s, const Plan &p, const WS &w, cudaStream_t st);
+cudaError_t launch_project(const pf_scene &s, const Plan &p, const WS &w, cudaStream_t st);
+cudaError_t launch_bin_sort(const Plan &p, const WS &w, cudaStream_t st);
+cudaError_t launch_render_fwd(const pf_scene &s, const Plan &p, const WS &w, float *rgb, float *T, uint32_t *last,
+                              cudaStream_t st);
+cudaError_t launch_render_bwd(const pf_scene &s, const Plan &p, const WS &w, const float *dL_drgb,
+                              const float *dL_dT, const float *T, const uint32_t *last, const pf_scene_grad &g,
+                              cudaStream_t st);
+
+}  // namespace pf

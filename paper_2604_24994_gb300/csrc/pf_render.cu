@@ -1,0 +1,824 @@
+// pf_render_fwd / pf_render_bwd: per-pixel ray/cell segments, front-to-back
+// compositing, and the back-to-front adjoint replay.
+//
+// One CTA per 16x16 tile, one thread per pixel; each warp covers an 8x4
+// pixel block.  The tile's sorted cell list is staged into shared memory in
+// batches of 32 cells with cp.async (16-byte granules): the 128-byte cell
+// record, the 32-byte view record and the cell's relevant radical planes.
+//
+// Segment of the ray x(t) = o + t d in cell i (Sec. 3.2-3.3), in the local
+// frame of the ray's closest approach to p_i:  with m = o - p_i and
+// v = m x d, the offset q = d x v satisfies |q| = |v| and x - p_i = q + s d,
+// s = t + m.d.  Then
+//   sphere:   s in [-sqrt(D), sqrt(D)],  D = R^2 - |v|^2
+//   camera:   s >= m.d                   (t >= 0)
+//   plane k:  s (d.a) <= g - q.a         (unit a, g = plane distance)
+//   face:     s (d.n) <= off - q.n       (dense half)
+// v is computed from the FP64 offset m (a float pair) and the FP64 ray
+// direction (a float pair) with error-free products, so q is accurate to a
+// few float ulps of |q| <= R no matter how far the camera is.  Segment ends
+// whose float error bound could move sigma * l by more than REFINE_EPS are
+// recomputed in FP64 from the original parameters (a near-tangent sphere or
+// a near-parallel plane / face).
+#include "pf_internal.cuh"
+
+namespace pf {
+
+constexpr float REFINE_EPS = 4e-6f;   // sigma * |error of a segment end| budget
+constexpr float PLANE_ERR = 6e-7f;    // bound on |error| of a plane/face end, in units of (R + |s|)
+constexpr float SPHERE_ERR = 6e-7f;   // bound on |error of D|, in units of R^2
+
+struct SceneRefs {          // original parameters, for FP64 refinement
+    const float *pos, *w, *R, *normal, *offset;
+};
+
+struct Seg {
+    float sa, sb;           // entry / exit in the local frame
+    float dena, denb;       // d.a of the active plane or face at each end
+    int ka, kb;             // active constraint: plane slot >= 0, or K_*
+    float3 q;               // closest-approach offset from p_i
+    float dnd;              // d . n (selects the texture end)
+    int refined;            // ends recomputed in FP64
+};
+
+enum : int { K_SPHERE = -1, K_CAMERA = -2, K_FACE = -3 };
+
+__device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+    return f3(fmaf(a.y, b.z, -a.z * b.y), fmaf(a.z, b.x, -a.x * b.z), fmaf(a.x, b.y, -a.y * b.x));
+}
+
+// One component of (m x d) = m1 d2 - m2 d1 for float pairs m = mh + ml,
+// d = dh + dl: exact products of the high parts plus first-order terms.
+__device__ __forceinline__ float cross_c(float mh1, float ml1, float dh2, float dl2, float mh2, float ml2, float dh1,
+                                         float dl1) {
+    const float p1 = mh1 * dh2;
+    const float e1 = fmaf(mh1, dh2, -p1);
+    const float p2 = mh2 * dh1;
+    const float e2 = fmaf(mh2, dh1, -p2);
+    const float hi = p1 - p2;
+    float lo = e1 - e2;
+    lo = fmaf(mh1, dl2, lo);
+    lo = fmaf(ml1, dh2, lo);
+    lo = fmaf(-mh2, dl1, lo);
+    lo = fmaf(-ml2, dh1, lo);
+    return hi + lo;
+}
+
+struct Ray {
+    float3 dh, dl;          // unit direction as a float pair
+};
+
+__device__ __forceinline__ Ray pixel_ray(const ViewDev &V, int u, int v) {
+    const double xc = ((double)u + 0.5 - V.cx) * V.ifx;
+    const double yc = ((double)v + 0.5 - V.cy) * V.ify;
+    const double *M = V.rot;
+    double dx = M[0] * xc + M[3] * yc + M[6];
+    double dy = M[1] * xc + M[4] * yc + M[7];
+    double dz = M[2] * xc + M[5] * yc + M[8];
+    const double n2 = dx * dx + dy * dy + dz * dz;
+    double r = (double)rsqrtf((float)n2);
+    r = r * (1.5 - 0.5 * n2 * r * r);
+    r = r * (1.5 - 0.5 * n2 * r * r);
+    dx *= r;
+    dy *= r;
+    dz *= r;
+    Ray R;
+    R.dh = f3((float)dx, (float)dy, (float)dz);
+    R.dl = f3((float)(dx - (double)R.dh.x), (float)(dy - (double)R.dh.y), (float)(dz - (double)R.dh.z));
+    return R;
+}
+
+// FP64 recomputation of one segment end.  kind: K_SPHERE (sign = -1 entry,
+// +1 exit), K_FACE, or a plane with neighbour j.
+__device__ __noinline__ float refine_end(const SceneRefs &S, const ViewDev &V, int i, int kind, int j, float sign,
+                                         Ray ray) {
+    const double dx = (double)ray.dh.x + (double)ray.dl.x, dy = (double)ray.dh.y + (double)ray.dl.y,
+                 dz = (double)ray.dh.z + (double)ray.dl.z;
+    const double px = S.pos[3 * i], py = S.pos[3 * i + 1], pz = S.pos[3 * i + 2];
+    const double mx = V.origin[0] - px, my = V.origin[1] - py, mz = V.origin[2] - pz;
+    const double b = mx * dx + my * dy + mz * dz;
+    const double qx = mx - b * dx, qy = my - b * dy, qz = mz - b * dz;
+    if (kind == K_SPHERE) {
+        const double R = S.R[i];
+        const double D = R * R - (qx * qx + qy * qy + qz * qz);
+        return (float)(sign * sqrt(D > 0.0 ? D : 0.0));
+    }
+    double ax, ay, az, g;
+    if (kind == K_FACE) {
+        const double nx = S.normal[3 * i], ny = S.normal[3 * i + 1], nz = S.normal[3 * i + 2];
+        const double nl = sqrt(nx * nx + ny * ny + nz * nz);
+        ax = nx / nl;
+        ay = ny / nl;
+        az = nz / nl;
+        g = S.offset[i];
+    } else {
+        ax = (double)S.pos[3 * j] - px;
+        ay = (double)S.pos[3 * j + 1] - py;
+        az = (double)S.pos[3 * j + 2] - pz;
+        g = 0.5 * (ax * ax + ay * ay + az * az + (double)S.w[i] - (double)S.w[j]);
+    }
+    const double num = g - (qx * ax + qy * ay + qz * az);
+    const double den = dx * ax + dy * ay + dz * az;
+    return (float)(num / den);
+}
+
+__device__ __noinline__ double refine_D(const SceneRefs &S, const ViewDev &V, int i, Ray ray) {
+    const double dx = (double)ray.dh.x + (double)ray.dl.x, dy = (double)ray.dh.y + (double)ray.dl.y,
+                 dz = (double)ray.dh.z + (double)ray.dl.z;
+    const double mx = V.origin[0] - (double)S.pos[3 * i], my = V.origin[1] - (double)S.pos[3 * i + 1],
+                 mz = V.origin[2] - (double)S.pos[3 * i + 2];
+    const double b = mx * dx + my * dy + mz * dz;
+    const double qx = mx - b * dx, qy = my - b * dy, qz = mz - b * dz;
+    const double R = S.R[i];
+    return R * R - (qx * qx + qy * qy + qz * qz);
+}
+
+__device__ __noinline__ float refine_face_dot(const SceneRefs &S, int i, Ray ray) {
+    const double dx = (double)ray.dh.x + (double)ray.dl.x, dy = (double)ray.dh.y + (double)ray.dl.y,
+                 dz = (double)ray.dh.z + (double)ray.dl.z;
+    const double nx = S.normal[3 * i], ny = S.normal[3 * i + 1], nz = S.normal[3 * i + 2];
+    const double dn = dx * nx + dy * ny + dz * nz;
+    return dn > 0.0 ? 1.0f : (dn < 0.0 ? -1.0f : 0.0f);
+}
+
+// The ray's segment in one cell.  cr: cell record, vr: view record,
+// pl: the cell's planes, nb: their neighbour ids (global, for refinement).
+__device__ __forceinline__ bool cell_segment(const float *__restrict__ cr, const float *__restrict__ vr,
+                                             const float4 *__restrict__ pl, int np,
+                                             const int2 *__restrict__ nb_glob, const SceneRefs &S,
+                                             const ViewDev &V, int cell, Ray ray, Seg &sg, bool &cand) {
+    const float3 mh = f3(vr[0], vr[1], vr[2]);
+    const float3 v0 = cross3(mh, ray.dh);
+    cand = dot3(v0, v0) <= vr[3];
+    if (!cand) return false;
+    const float3 ml = f3(vr[4], vr[5], vr[6]);
+    const float3 dh = ray.dh, dl = ray.dl;
+    const float3 v = f3(cross_c(mh.y, ml.y, dh.z, dl.z, mh.z, ml.z, dh.y, dl.y),
+                        cross_c(mh.z, ml.z, dh.x, dl.x, mh.x, ml.x, dh.z, dl.z),
+                        cross_c(mh.x, ml.x, dh.y, dl.y, mh.y, ml.y, dh.x, dl.x));
+    const float R = cr[CR_R];
+    const float sig = cr[CR_SIG];
+    float D = fmaf(R, R, -dot3(v, v));
+    sg.refined = 0;
+    // near-tangent sphere: decide and measure D in FP64
+    const float dthr = SPHERE_ERR * R * R * fmaxf(sig, 1.0f) * (1.0f / (2.0f * REFINE_EPS));
+    const float dthr2 = SPHERE_ERR * R * R;
+    if (fabsf(D) < fmaxf(dthr * dthr, dthr2)) {
+        D = (float)refine_D(S, V, cell, ray);
+        sg.refined = 1;
+    }
+    if (!(D > 0.0f)) return false;
+    const float sq = sqrtf(D);
+    const float3 q = cross3(dh, v);
+    const float b = dot3(mh, dh);
+    float sa = -sq, sb = sq, dena = 0.f, denb = 0.f;
+    int ka = K_SPHERE, kb = K_SPHERE;
+    if (b > sa) {
+        sa = b;
+        ka = K_CAMERA;
+    }
+    bool empty = false;
+    for (int k = 0; k < np; k++) {
+        const float4 P = pl[k];
+        const float3 a = f3(P.x, P.y, P.z);
+        const float num = P.w - dot3(q, a);
+        const float den = dot3(dh, a);
+        if (den > 0.0f) {
+            const float s = __fdividef(num, den);
+            if (s < sb) { sb = s; kb = k; denb = den; }
+        } else if (den < 0.0f) {
+            const float s = __fdividef(num, den);
+            if (s > sa) { sa = s; ka = k; dena = den; }
+        } else if (num < 0.0f) {
+            empty = true;
+        }
+    }
+    {
+        const float3 n = f3(cr[CR_N], cr[CR_N + 1], cr[CR_N + 2]);
+        const float num = cr[CR_OFF] - dot3(q, n);
+        const float den = dot3(dh, n);
+        sg.dnd = den;
+        if (den > 0.0f) {
+            const float s = __fdividef(num, den);
+            if (s < sb) { sb = s; kb = K_FACE; denb = den; }
+        } else if (den < 0.0f) {
+            const float s = __fdividef(num, den);
+            if (s > sa) { sa = s; ka = K_FACE; dena = den; }
+        } else if (num < 0.0f) {
+            empty = true;
+        }
+        if (fabsf(den) < 0x1p-20f) sg.dnd = refine_face_dot(S, cell, ray);
+    }
+    if (empty || !(sb > sa)) return false;
+    // near-parallel plane or face at an end: recompute that end in FP64
+    const float lim = PLANE_ERR * fmaxf(sig, 1.0f) * (1.0f / REFINE_EPS);
+    if (ka >= 0 || ka == K_FACE) {
+        if (fabsf(dena) < lim * (R + fabsf(sa))) {
+            sa = refine_end(S, V, cell, ka, ka >= 0 ? nb_glob[ka].x : -1, -1.f, ray);
+            sg.refined++;
+        }
+    }
+    if (kb >= 0 || kb == K_FACE) {
+        if (fabsf(denb) < lim * (R + fabsf(sb))) {
+            sb = refine_end(S, V, cell, kb, kb >= 0 ? nb_glob[kb].x : -1, 1.f, ray);
+            sg.refined++;
+        }
+    }
+    if (!(sb > sa)) return false;
+    sg.sa = sa;
+    sg.sb = sb;
+    sg.ka = ka;
+    sg.kb = kb;
+    sg.dena = dena;
+    sg.denb = denb;
+    sg.q = q;
+    return true;
+}
+
+// Soft-Voronoi face colour (Eq. svrad): weights of the four sites at the
+// texture point y = q + s d (the dense segment's end on the face side).
+struct Tex {
+    float3 ys;
+    float u1, u2;
+    float ax[2], ay[2];     // u - site offsets: ax[0] = u1 + 1/3, ax[1] = u1 - 1/3
+    float r[4], W[4];
+};
+
+__device__ __forceinline__ float3 face_colour(const float *__restrict__ cr, const Seg &sg, const Ray &ray, Tex &tx) {
+    const float ss = sg.dnd > 0.0f ? sg.sb : sg.sa;
+    tx.ys = f3(fmaf(ss, ray.dh.x, sg.q.x), fmaf(ss, ray.dh.y, sg.q.y), fmaf(ss, ray.dh.z, sg.q.z));
+    tx.u1 = dot3(f3(cr[CR_E1], cr[CR_E1 + 1], cr[CR_E1 + 2]), tx.ys);
+    tx.u2 = dot3(f3(cr[CR_E2], cr[CR_E2 + 1], cr[CR_E2 + 2]), tx.ys);
+    tx.ax[0] = tx.u1 + SITE;
+    tx.ax[1] = tx.u1 - SITE;
+    tx.ay[0] = tx.u2 + SITE;
+    tx.ay[1] = tx.u2 - SITE;
+    float Z = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const float ax = tx.ax[k & 1], ay = tx.ay[k >> 1];
+        tx.r[k] = sqrtf(fmaf(ax, ax, ay * ay));
+        tx.W[k] = __expf(-KAPPA * tx.r[k]);
+        Z += tx.W[k];
+    }
+    const float iz = __fdividef(1.0f, Z);
+    float3 c = f3(cr[CR_RGB], cr[CR_RGB + 1], cr[CR_RGB + 2]);
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        tx.W[k] *= iz;
+        c.x = fmaf(tx.W[k], cr[CR_TEX + 3 * k], c.x);
+        c.y = fmaf(tx.W[k], cr[CR_TEX + 3 * k + 1], c.y);
+        c.z = fmaf(tx.W[k], cr[CR_TEX + 3 * k + 2], c.z);
+    }
+    return c;
+}
+
+// ------------------------------------------------------------ batch staging
+struct Smem {
+    int ids[BATCH];
+    int poff[BATCH + 1];
+};
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(src));
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Stage list entries [base, base + nb) of the tile into shared memory.
+__device__ __forceinline__ void stage_batch(Smem &sm, float *s_cr, float *s_vr, float4 *s_pl, int2 *s_nb,
+                                            const uint32_t *__restrict__ list, int nb, const WS &w, int64_t vbase,
+                                            int K) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (warp == 0) {
+        int c = 0, np = 0;
+        if (lane < nb) {
+            c = (int)list[lane];
+            np = w.cellnp[c];
+            sm.ids[lane] = c;
+        }
+        int incl = np;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        sm.poff[lane + 1] = incl;
+        if (lane == 0) sm.poff[0] = 0;
+    }
+    __syncthreads();
+    for (int q = tid; q < nb * 10; q += TILE_PIX) {
+        const int j = q / 10, part = q - j * 10;
+        const int c = sm.ids[j];
+        if (part < 8)
+            cp_async16(s_cr + j * CELLREC_F + part * 4, w.cellrec + (int64_t)c * CELLREC_F + part * 4);
+        else
+            cp_async16(s_vr + j * VIEWREC_F + (part - 8) * 4, w.viewrec + (vbase + c) * VIEWREC_F + (part - 8) * 4);
+    }
+    for (int j = warp; j < nb; j += TILE_PIX / 32) {
+        const int c = sm.ids[j];
+        const int o = sm.poff[j], np = sm.poff[j + 1] - o;
+        for (int k = lane; k < np; k += 32) {
+            cp_async16(s_pl + o + k, w.planes + (int64_t)c * K + k);
+            if (s_nb) *(reinterpret_cast<long long *>(s_nb + o + k)) =
+                *(reinterpret_cast<const long long *>(w.plane_nb + (int64_t)c * K + k));
+        }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+}
+
+__device__ __forceinline__ int find_view(const ViewDev *views, int nv, int64_t tile) {
+    int lo = 0, hi = nv - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (views[mid].tile_base <= tile) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+struct RenderArgs {
+    WS w;
+    SceneRefs S;
+    int nv, n, K;
+    unsigned long long cap;
+};
+
+__device__ __forceinline__ void tile_pixel(const ViewDev &V, int64_t lt, int &px, int &py) {
+    const int tx = (int)(lt % V.tiles_x), ty = (int)(lt / V.tiles_x);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    px = tx * TILE + (warp & 1) * 8 + (lane & 7);
+    py = ty * TILE + (warp >> 1) * 4 + (lane >> 3);
+}
+
+// ---------------------------------------------------------------- forward
+template <bool STATS>
+__global__ void __launch_bounds__(TILE_PIX) render_fwd_kernel(RenderArgs A, float *__restrict__ rgb_out,
+                                                              float *__restrict__ T_out,
+                                                              uint32_t *__restrict__ last_out) {
+    extern __shared__ float4 smem4[];
+    __shared__ Smem sm;
+    float *s_cr = reinterpret_cast<float *>(smem4);
+    float *s_vr = s_cr + BATCH * CELLREC_F;
+    float4 *s_pl = reinterpret_cast<float4 *>(s_vr + BATCH * VIEWREC_F);
+
+    const int64_t tile = blockIdx.x;
+    const int v = find_view(A.w.views, A.nv, tile);
+    const ViewDev &V = A.w.views[v];
+    int px, py;
+    tile_pixel(V, tile - V.tile_base, px, py);
+    const bool inside = px < V.width && py < V.height;
+    Ray ray = pixel_ray(V, inside ? px : 0, inside ? py : 0);
+
+    unsigned long long s = A.w.tile_start[tile], e = A.w.tile_start[tile + 1];
+    const bool overflow = A.w.counters->overflow != 0;
+    if (s > A.cap) s = A.cap;
+    if (e > A.cap) e = A.cap;
+    if (overflow) e = s;
+    const int64_t vbase = (int64_t)v * A.n;
+
+    float T = 1.0f;
+    float3 C = f3(0.f, 0.f, 0.f);
+    uint32_t last = 0;
+    bool done = !inside;
+    unsigned long long st_cand = 0, st_hit = 0, st_pl = 0, st_ref = 0, st_pass = 0;
+
+    for (unsigned long long base = s; base < e; base += BATCH) {
+        const int nb = (int)min((unsigned long long)BATCH, e - base);
+        __syncthreads();
+        stage_batch(sm, s_cr, s_vr, s_pl, nullptr, A.w.inst_sorted + base, nb, A.w, vbase, A.K);
+        for (int j = 0; j < nb; j++) {
+            if (__all_sync(0xffffffffu, done)) break;
+            if (done) continue;
+            const int cell = sm.ids[j];
+            const float *cr = s_cr + j * CELLREC_F;
+            Seg sg;
+            bool cand;
+            const int o = sm.poff[j], np = sm.poff[j + 1] - o;
+            const bool hit = cell_segment(cr, s_vr + j * VIEWREC_F, s_pl + o, np,
+                                          A.w.plane_nb + (int64_t)cell * A.K, A.S, V, cell, ray, sg, cand);
+            if (STATS) {
+                st_cand++;
+                st_pass += cand;
+                st_pl += cand ? np : 0;
+                st_ref += cand ? sg.refined : 0;
+                st_hit += hit;
+            }
+            if (!hit) continue;
+            Tex tx;
+            const float3 c = face_colour(cr, sg, ray, tx);
+            const float x = fminf(cr[CR_SIG] * (sg.sb - sg.sa), X_CAP);
+            const float ex = __expf(-x);
+            const float wgt = T * (1.0f - ex);
+            C.x = fmaf(wgt, c.x, C.x);
+            C.y = fmaf(wgt, c.y, C.y);
+            C.z = fmaf(wgt, c.z, C.z);
+            T *= ex;
+            last = (uint32_t)(base - s) + j + 1;
+            if (T < T_EPS) done = true;
+        }
+        if (__syncthreads_count(!done) == 0) break;
+    }
+    if (inside) {
+        const int64_t pix = V.pix_base + (int64_t)py * V.width + px;
+        rgb_out[3 * pix] = C.x;
+        rgb_out[3 * pix + 1] = C.y;
+        rgb_out[3 * pix + 2] = C.z;
+        T_out[pix] = T;
+        last_out[pix] = last;
+    }
+    if (STATS) {
+        unsigned long long *st = A.w.counters->stats;
+        for (int o = 16; o > 0; o >>= 1) {
+            st_cand += __shfl_xor_sync(0xffffffffu, st_cand, o);
+            st_hit += __shfl_xor_sync(0xffffffffu, st_hit, o);
+            st_pl += __shfl_xor_sync(0xffffffffu, st_pl, o);
+            st_ref += __shfl_xor_sync(0xffffffffu, st_ref, o);
+            st_pass += __shfl_xor_sync(0xffffffffu, st_pass, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(&st[0], st_cand);
+            atomicAdd(&st[1], st_hit);
+            atomicAdd(&st[2], st_pl);
+            atomicAdd(&st[3], st_ref);
+            atomicAdd(&st[4], st_pass);
+        }
+    }
+}
+
+// --------------------------------------------------------------- backward
+// Sum v[0..31] over the warp with each lane ending up holding one index:
+// after five exchange rounds lane l holds sum_lanes v[l] (31 shuffles).
+__device__ __forceinline__ float warp_transpose_sum(float (&v)[32], int lane) {
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+        const bool up = lane & 16;
+        const float keep = up ? v[k + 16] : v[k];
+        const float give = up ? v[k] : v[k + 16];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, give, 16);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        const bool up = lane & 8;
+        const float keep = up ? v[k + 8] : v[k];
+        const float give = up ? v[k] : v[k + 8];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, give, 8);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const bool up = lane & 4;
+        const float keep = up ? v[k + 4] : v[k];
+        const float give = up ? v[k] : v[k + 4];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, give, 4);
+    }
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        const bool up = lane & 2;
+        const float keep = up ? v[k + 2] : v[k];
+        const float give = up ? v[k] : v[k + 2];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, give, 2);
+    }
+    {
+        const bool up = lane & 1;
+        const float keep = up ? v[1] : v[0];
+        const float give = up ? v[0] : v[1];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, give, 1);
+    }
+    return v[0];
+}
+
+// dL/dt of one segment end -> gradients of its active constraint.
+// y = q + s d is the end point relative to p_i.
+__device__ __forceinline__ void route_end(float gt, int kind, float s, float den, const Seg &sg, const Ray &ray,
+                                          const float *cr, const float4 *pl, const int2 *nb, float3 &gm, float (&v)[32],
+                                          float (&nbv)[4], int &nbj) {
+    nbj = -1;
+    if (gt == 0.0f || kind == K_CAMERA) return;
+    const float3 d = ray.dh;
+    const float3 y = f3(fmaf(s, d.x, sg.q.x), fmaf(s, d.y, sg.q.y), fmaf(s, d.z, sg.q.z));
+    if (kind == K_SPHERE) {
+        // |y|^2 = R^2:  dt/dm = -y / (y.d),  dt/dR = R / (y.d),  y.d = s
+        const float is = gt / s;
+        gm.x -= is * y.x;
+        gm.y -= is * y.y;
+        gm.z -= is * y.z;
+        v[G_R] += is * cr[CR_R];
+        return;
+    }
+    const float id = gt / den;
+    if (kind == K_FACE) {
+        // n.y = off:  dt/dm = -n/(d.n), dt/dn = -y/(d.n), dt/doff = 1/(d.n)
+        gm.x -= id * cr[CR_N];
+        gm.y -= id * cr[CR_N + 1];
+        gm.z -= id * cr[CR_N + 2];
+        v[G_N] -= id * y.x;
+        v[G_N + 1] -= id * y.y;
+        v[G_N + 2] -= id * y.z;
+        v[G_OFF] += id;
+        return;
+    }
+    // plane (unit a, distance g) of neighbour j:  a.y = g
+    const float4 P = pl[kind];
+    const float3 a = f3(P.x, P.y, P.z);
+    const int2 J = nb[kind];
+    const float L = __int_as_float(J.y);
+    gm.x -= id * a.x;
+    gm.y -= id * a.y;
+    gm.z -= id * a.z;
+    // dL/da_unit = -id y, dL/dg = id;  a_unit = A/L, g = (L^2 + w_i - w_j)/(2L), A = p_j - p_i
+    const float3 ga = f3(-id * y.x, -id * y.y, -id * y.z);
+    const float gg = id;
+    const float pa = dot3(a, ga);
+    const float iL = 1.0f / L;
+    const float cg = gg * (1.0f - P.w * iL);
+    const float3 dA = f3((ga.x - a.x * pa) * iL + cg * a.x, (ga.y - a.y * pa) * iL + cg * a.y,
+                         (ga.z - a.z * pa) * iL + cg * a.z);
+    v[G_P] -= dA.x;
+    v[G_P + 1] -= dA.y;
+    v[G_P + 2] -= dA.z;
+    v[G_W] += 0.5f * gg * iL;
+    nbv[0] = dA.x;
+    nbv[1] = dA.y;
+    nbv[2] = dA.z;
+    nbv[3] = -0.5f * gg * iL;
+    nbj = J.x;
+}
+
+__global__ void __launch_bounds__(TILE_PIX) render_bwd_kernel(RenderArgs A, const float *__restrict__ dL_drgb,
+                                                              const float *__restrict__ dL_dT,
+                                                              const float *__restrict__ T_in,
+                                                              const uint32_t *__restrict__ last_in) {
+    extern __shared__ float4 smem4[];
+    __shared__ Smem sm;
+    __shared__ int s_maxlast;
+    float *s_cr = reinterpret_cast<float *>(smem4);
+    float *s_vr = s_cr + BATCH * CELLREC_F;
+    float4 *s_pl = reinterpret_cast<float4 *>(s_vr + BATCH * VIEWREC_F);
+    int2 *s_nb = reinterpret_cast<int2 *>(s_pl + BATCH * A.K);
+
+    const int lane = threadIdx.x & 31;
+    const int64_t tile = blockIdx.x;
+    const int v = find_view(A.w.views, A.nv, tile);
+    const ViewDev &V = A.w.views[v];
+    int px, py;
+    tile_pixel(V, tile - V.tile_base, px, py);
+    const bool inside = px < V.width && py < V.height;
+    Ray ray = pixel_ray(V, inside ? px : 0, inside ? py : 0);
+    unsigned long long s = A.w.tile_start[tile], e = A.w.tile_start[tile + 1];
+    if (s > A.cap) s = A.cap;
+    if (e > A.cap) e = A.cap;
+    if (A.w.counters->overflow) e = s;
+    const int64_t vbase = (int64_t)v * A.n;
+
+    float3 g = f3(0.f, 0.f, 0.f);
+    float gT = 0.f, Tf = 1.f;
+    int last = 0;
+    if (inside) {
+        const int64_t pix = V.pix_base + (int64_t)py * V.width + px;
+        g = f3(dL_drgb[3 * pix], dL_drgb[3 * pix + 1], dL_drgb[3 * pix + 2]);
+        gT = dL_dT ? dL_dT[pix] : 0.f;
+        Tf = T_in[pix];
+        last = (int)last_in[pix];
+        if ((unsigned long long)last > e - s) last = (int)(e - s);
+    }
+    if (threadIdx.x == 0) s_maxlast = 0;
+    __syncthreads();
+    atomicMax(&s_maxlast, last);
+    __syncthreads();
+    const int maxlast = s_maxlast;
+
+    float Tafter = Tf;
+    float3 accC = f3(0.f, 0.f, 0.f);
+    float *acc = A.w.acc;
+
+    for (int hi = maxlast; hi > 0; hi -= BATCH) {
+        const int lo = hi > BATCH ? hi - BATCH : 0;
+        const int nb = hi - lo;
+        __syncthreads();
+        stage_batch(sm, s_cr, s_vr, s_pl, s_nb, A.w.inst_sorted + s + lo, nb, A.w, vbase, A.K);
+        for (int j = nb - 1; j >= 0; j--) {
+            const int idx = lo + j;
+            if (!__any_sync(0xffffffffu, idx < last)) continue;
+            const int cell = sm.ids[j];
+            const float *cr = s_cr + j * CELLREC_F;
+            const int o = sm.poff[j], np = sm.poff[j + 1] - o;
+            Seg sg;
+            bool cand;
+            bool hit = false;
+            if (idx < last)
+                hit = cell_segment(cr, s_vr + j * VIEWREC_F, s_pl + o, np, A.w.plane_nb + (int64_t)cell * A.K,
+                                   A.S, V, cell, ray, sg, cand);
+            if (!__any_sync(0xffffffffu, hit)) continue;
+            float vv[32];
+#pragma unroll
+            for (int q = 0; q < 32; q++) vv[q] = 0.f;
+            float nba[4] = {0.f, 0.f, 0.f, 0.f}, nbb[4] = {0.f, 0.f, 0.f, 0.f};
+            int ja = -1, jb = -1;
+            if (hit) {
+                Tex tx;
+                const float3 c = face_colour(cr, sg, ray, tx);
+                const float sig = cr[CR_SIG];
+                const float l = sg.sb - sg.sa;
+                const float xr = sig * l;
+                const float x = fminf(xr, X_CAP);
+                const float ex = __expf(-x);
+                const float alpha = 1.0f - ex;
+                const float Tbefore = Tafter * __expf(x);
+                // x = sigma l, alpha = 1 - e^-x:  dL/dx = g.(T_{k+1} c - S_k) - gT T_final
+                float dLdx = g.x * (Tafter * c.x - accC.x) + g.y * (Tafter * c.y - accC.y) +
+                             g.z * (Tafter * c.z - accC.z) - gT * Tf;
+                if (xr > X_CAP) dLdx = 0.f;
+                vv[G_SIG] = dLdx * l;
+                const float gl = dLdx * sig;
+                const float wc = Tbefore * alpha;
+                const float3 gc = f3(wc * g.x, wc * g.y, wc * g.z);
+                // texture values and soft-Voronoi weights
+                float gW[4], sW = 0.f;
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    vv[G_TEX + 3 * k] = tx.W[k] * gc.x;
+                    vv[G_TEX + 3 * k + 1] = tx.W[k] * gc.y;
+                    vv[G_TEX + 3 * k + 2] = tx.W[k] * gc.z;
+                    gW[k] = cr[CR_TEX + 3 * k] * gc.x + cr[CR_TEX + 3 * k + 1] * gc.y + cr[CR_TEX + 3 * k + 2] * gc.z;
+                    sW += tx.W[k] * gW[k];
+                }
+                float gu1 = 0.f, gu2 = 0.f;
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const float gr = -KAPPA * tx.W[k] * (gW[k] - sW);
+                    if (tx.r[k] > 0.f) {
+                        const float ir = gr / tx.r[k];
+                        gu1 = fmaf(ir, tx.ax[k & 1], gu1);
+                        gu2 = fmaf(ir, tx.ay[k >> 1], gu2);
+                    }
+                }
+                // u = (e1.y, e2.y)/R with e/R stored:  dL/dy, dL/dR, dL/dn via the frame
+                const float3 E1 = f3(cr[CR_E1], cr[CR_E1 + 1], cr[CR_E1 + 2]);
+                const float3 E2 = f3(cr[CR_E2], cr[CR_E2 + 1], cr[CR_E2 + 2]);
+                const float R = cr[CR_R];
+                const float3 gy = f3(gu1 * E1.x + gu2 * E2.x, gu1 * E1.y + gu2 * E2.y, gu1 * E1.z + gu2 * E2.z);
+                vv[G_R] += -(gu1 * tx.u1 + gu2 * tx.u2) / R;
+                {
+                    // dL/de1 = gu1 y / R, dL/de2 = gu2 y / R (frame of Duff et al., JCGT 2017)
+                    const float iR = 1.0f / R;
+                    const float3 g1 = f3(gu1 * tx.ys.x * iR, gu1 * tx.ys.y * iR, gu1 * tx.ys.z * iR);
+                    const float3 g2 = f3(gu2 * tx.ys.x * iR, gu2 * tx.ys.y * iR, gu2 * tx.ys.z * iR);
+                    const float nx = cr[CR_N], ny = cr[CR_N + 1], nz = cr[CR_N + 2];
+                    const float sgn = nz >= 0.f ? 1.f : -1.f;
+                    const float ca = -1.0f / (sgn + nz);
+                    const float da = ca * ca;
+                    const float db0 = ny * ca, db1 = nx * ca, db2 = nx * ny * da;
+                    // e1 = (1 + s x^2 a, s b, -s x), e2 = (b, s + y^2 a, -y), b = x y a
+                    vv[G_N] += g1.x * (2.f * sgn * nx * ca) + g1.y * sgn * db0 + g1.z * (-sgn) + g2.x * db0;
+                    vv[G_N + 1] += g1.y * sgn * db1 + g2.x * db1 + g2.y * (2.f * ny * ca) + g2.z * (-1.f);
+                    vv[G_N + 2] += g1.x * (sgn * nx * nx * da) + g1.y * sgn * db2 + g2.x * db2 + g2.y * (ny * ny * da);
+                }
+                // the texture point moves with its segment end: y_s = m + t_s d
+                float3 gm = gy;
+                const float gts = dot3(gy, ray.dh);
+                const bool onb = sg.dnd > 0.f;
+                const float gta = -gl + (onb ? 0.f : gts);
+                const float gtb = gl + (onb ? gts : 0.f);
+                const int2 *nbp = s_nb + o;
+                const float4 *plp = s_pl + o;
+                route_end(gta, sg.ka, sg.sa, sg.dena, sg, ray, cr, plp, nbp, gm, vv, nba, ja);
+                route_end(gtb, sg.kb, sg.sb, sg.denb, sg, ray, cr, plp, nbp, gm, vv, nbb, jb);
+                // m = o - p
+                vv[G_P] -= gm.x;
+                vv[G_P + 1] -= gm.y;
+                vv[G_P + 2] -= gm.z;
+                accC.x = fmaf(wc, c.x, accC.x);
+                accC.y = fmaf(wc, c.y, accC.y);
+                accC.z = fmaf(wc, c.z, accC.z);
+                Tafter = Tbefore;
+            }
+            // neighbour gradients: fold into the warp sum when the warp agrees on j
+            const unsigned ma = __ballot_sync(0xffffffffu, ja >= 0);
+            const int ref_a = ma ? __shfl_sync(0xffffffffu, ja, __ffs(ma) - 1) : -1;
+            const unsigned mb = __ballot_sync(0xffffffffu, jb >= 0);
+            const int ref_b = mb ? __shfl_sync(0xffffffffu, jb, __ffs(mb) - 1) : -1;
+            if (ja >= 0 && ja != ref_a) {
+                float *d = acc + (int64_t)ja * ACC_F;
+                atomicAdd(d + G_P, nba[0]);
+                atomicAdd(d + G_P + 1, nba[1]);
+                atomicAdd(d + G_P + 2, nba[2]);
+                atomicAdd(d + G_W, nba[3]);
+            } else if (ja >= 0) {
+#pragma unroll
+                for (int q = 0; q < 4; q++) vv[G_NB_A + q] = nba[q];
+            }
+            if (jb >= 0 && jb != ref_b) {
+                float *d = acc + (int64_t)jb * ACC_F;
+                atomicAdd(d + G_P, nbb[0]);
+                atomicAdd(d + G_P + 1, nbb[1]);
+                atomicAdd(d + G_P + 2, nbb[2]);
+                atomicAdd(d + G_W, nbb[3]);
+            } else if (jb >= 0) {
+#pragma unroll
+                for (int q = 0; q < 4; q++) vv[G_NB_B + q] = nbb[q];
+            }
+            const float sum = warp_transpose_sum(vv, lane);
+            if (lane < G_USED) {
+                atomicAdd(acc + (int64_t)cell * ACC_F + lane, sum);
+            } else if (lane < G_NB_B) {
+                if (ref_a >= 0) atomicAdd(acc + (int64_t)ref_a * ACC_F + (lane - G_NB_A), sum);
+            } else if (lane < G_NB_B + 4) {
+                if (ref_b >= 0) atomicAdd(acc + (int64_t)ref_b * ACC_F + (lane - G_NB_B), sum);
+            }
+        }
+    }
+}
+
+// Accumulators -> parameter gradients.  n = |n| n^:  dL/dn = (I - n^ n^T) dL/dn^ / |n|;
+// rgb enters the colour with weight 1, the texture sites with weights summing to 1.
+__global__ void __launch_bounds__(256) finalize_kernel(int n, const float *__restrict__ acc,
+                                                       const float *__restrict__ cellrec, pf_scene_grad G) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float *a = acc + (int64_t)i * ACC_F;
+    const float *cr = cellrec + (int64_t)i * CELLREC_F;
+    G.pos[3 * i] += a[G_P];
+    G.pos[3 * i + 1] += a[G_P + 1];
+    G.pos[3 * i + 2] += a[G_P + 2];
+    G.w[i] += a[G_W];
+    G.R[i] += a[G_R];
+    G.sigma[i] += a[G_SIG];
+    const float nx = cr[CR_N], ny = cr[CR_N + 1], nz = cr[CR_N + 2], nl = cr[CR_NLEN];
+    const float gx = a[G_N], gy = a[G_N + 1], gz = a[G_N + 2];
+    const float pr = nx * gx + ny * gy + nz * gz;
+    const float inl = nl > 0.f ? 1.0f / nl : 0.f;
+    G.normal[3 * i] += (gx - nx * pr) * inl;
+    G.normal[3 * i + 1] += (gy - ny * pr) * inl;
+    G.normal[3 * i + 2] += (gz - nz * pr) * inl;
+    G.offset[i] += a[G_OFF];
+    float r0 = 0.f, r1 = 0.f, r2 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const float t0 = a[G_TEX + 3 * k], t1 = a[G_TEX + 3 * k + 1], t2 = a[G_TEX + 3 * k + 2];
+        G.tex[12 * i + 3 * k] += t0;
+        G.tex[12 * i + 3 * k + 1] += t1;
+        G.tex[12 * i + 3 * k + 2] += t2;
+        r0 += t0;
+        r1 += t1;
+        r2 += t2;
+    }
+    G.rgb[3 * i] += r0;
+    G.rgb[3 * i + 1] += r1;
+    G.rgb[3 * i + 2] += r2;
+}
+
+static RenderArgs make_args(const pf_scene &s, const Plan &p, const WS &w) {
+    RenderArgs A;
+    A.w = w;
+    A.S.pos = s.pos;
+    A.S.w = s.w;
+    A.S.R = s.R;
+    A.S.normal = s.normal;
+    A.S.offset = s.offset;
+    A.nv = p.nv;
+    A.n = p.n;
+    A.K = p.k;
+    A.cap = p.cap;
+    return A;
+}
+
+static size_t fwd_smem(int K) {
+    return (size_t)BATCH * (CELLREC_F + VIEWREC_F) * 4 + (size_t)BATCH * (K > 0 ? K : 1) * 16;
+}
+static size_t bwd_smem(int K) { return fwd_smem(K) + (size_t)BATCH * (K > 0 ? K : 1) * 8; }
+
+cudaError_t launch_render_fwd(const pf_scene &s, const Plan &p, const WS &w, float *rgb, float *T, uint32_t *last,
+                              cudaStream_t st) {
+    if (p.total_tiles == 0) return cudaSuccess;
+    RenderArgs A = make_args(s, p, w);
+    const size_t smem = fwd_smem(p.k);
+    if (p.stats) {
+        cudaFuncSetAttribute(render_fwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        render_fwd_kernel<true><<<(unsigned)p.total_tiles, TILE_PIX, smem, st>>>(A, rgb, T, last);
+    } else {
+        cudaFuncSetAttribute(render_fwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        render_fwd_kernel<false><<<(unsigned)p.total_tiles, TILE_PIX, smem, st>>>(A, rgb, T, last);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_render_bwd(const pf_scene &s, const Plan &p, const WS &w, const float *dL_drgb,
+                              const float *dL_dT, const float *T, const uint32_t *last, const pf_scene_grad &g,
+                              cudaStream_t st) {
+    if (p.n == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(w.acc, 0, sizeof(float) * ACC_F * (size_t)p.n, st);
+    if (e != cudaSuccess) return e;
+    if (p.total_tiles > 0) {
+        RenderArgs A = make_args(s, p, w);
+        const size_t smem = bwd_smem(p.k);
+        cudaFuncSetAttribute(render_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        render_bwd_kernel<<<(unsigned)p.total_tiles, TILE_PIX, smem, st>>>(A, dL_drgb, dL_dT, T, last);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    finalize_kernel<<<(p.n + 255) / 256, 256, 0, st>>>(p.n, w.acc, w.cellrec, g);
+    return cudaGetLastError();
+}
+
+}  // namespace pf

@@ -44,3 +44,14 @@ def cluster_scene(rng, n=10, spread=0.15, r=(0.05, 0.12), bound=1.5, tied=False,
 
 def cam_at(o, w=16, h=16, fov=60.0):
     return look_at(o, w, h, fov)
+
+
+def f32(scene):
+    """The same scene with float32 parameters (what the CUDA path consumes;
+    the oracle widens them exactly), and all-pairs neighbour lists if none."""
+    s = scene.copy()
+    for k in s.PARAMS:
+        setattr(s, k, np.ascontiguousarray(np.asarray(getattr(s, k)), np.float32))
+    if s.nbr.shape[1] == 0 and s.n > 1:
+        s.nbr = np.array([[j for j in range(s.n) if j != i] for i in range(s.n)], np.int32)
+    return s

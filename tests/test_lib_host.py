@@ -1,0 +1,116 @@
+"""Host-only checks of the C ABI library: it builds, loads without a GPU,
+exports every entry point include/powerfoam.h declares, and its plan calls
+validate arguments (no compute call is made here)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2604_24994_gb300 import build as pfbuild
+from paper_2604_24994_gb300 import inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(pf_[a-z_0-9]+)\s*\(", src, flags=re.M))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    pfbuild.build()
+    from paper_2604_24994_gb300 import _lib
+    return _lib.lib()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings(lib):
+    from paper_2604_24994_gb300 import _lib
+    for s in range(7):
+        assert lib.pf_status_string(s)
+    assert lib.pf_status_string(_lib.PF_ERR_CAPACITY) == b"instance capacity exceeded"
+
+
+def test_plan_layout_and_validation(lib):
+    from paper_2604_24994_gb300 import _lib
+    cams = [inputs.look_at((3, 0, 0), 100, 75), inputs.look_at((0, 3, 0), 64, 64)]
+    arr = _lib.camera_array(cams)
+    h = C.c_void_p()
+    assert lib.pf_plan_create(1000, 16, arr, 2, 5000, C.byref(h)) == 0
+    b = C.c_uint64()
+    px = C.c_uint64()
+    assert lib.pf_plan_workspace_bytes(h, C.byref(b)) == 0
+    assert lib.pf_plan_pixels(h, C.byref(px)) == 0
+    assert px.value == 100 * 75 + 64 * 64
+    # 7 x 5 + 4 x 4 tiles; workspace grows with capacity
+    assert b.value > 1000 * (128 + 16 * 24)
+    h2 = C.c_void_p()
+    assert lib.pf_plan_create(1000, 16, arr, 2, 50000, C.byref(h2)) == 0
+    b2 = C.c_uint64()
+    lib.pf_plan_workspace_bytes(h2, C.byref(b2))
+    assert b2.value - b.value >= 45000 * 28 - 5 * 256  # 28 B per instance, 256-byte aligned regions
+    # camera resolution cannot change under a plan
+    bad = _lib.camera_array([inputs.look_at((3, 0, 0), 101, 75), cams[1]])
+    assert lib.pf_plan_set_cameras(h, bad, 2) == _lib.PF_ERR_INVALID_ARG
+    assert b"resolution" in lib.pf_last_error_message()
+    assert lib.pf_plan_set_cameras(h, _lib.camera_array(cams[::-1][::-1]), 2) == 0
+    lib.pf_plan_destroy(h)
+    lib.pf_plan_destroy(h2)
+    lib.pf_plan_destroy(None)
+
+
+@pytest.mark.parametrize("mut", ["width0", "fx0", "nan", "k65", "nviews0"])
+def test_plan_rejects_bad_arguments(lib, mut):
+    from paper_2604_24994_gb300 import _lib
+    cam = inputs.look_at((3, 0, 0), 32, 32)
+    k, nv = 8, 1
+    if mut == "width0":
+        cam.width = 0
+    elif mut == "fx0":
+        cam.fx = 0.0
+    elif mut == "nan":
+        cam.origin = np.array([np.nan, 0, 0])
+    elif mut == "k65":
+        k = 65
+    elif mut == "nviews0":
+        nv = 0
+    h = C.c_void_p()
+    assert lib.pf_plan_create(10, k, _lib.camera_array([cam]), nv, 100, C.byref(h)) == _lib.PF_ERR_INVALID_ARG
+
+
+def test_calls_reject_null_workspace(lib):
+    from paper_2604_24994_gb300 import _lib
+    h = C.c_void_p()
+    assert lib.pf_plan_create(10, 4, _lib.camera_array([inputs.look_at((3, 0, 0), 32, 32)]), 1, 100,
+                              C.byref(h)) == 0
+    s = _lib.Scene()
+    s.n_cells, s.k_nbr = 10, 4
+    assert lib.pf_prepare(C.byref(s), h, None, None) == _lib.PF_ERR_INVALID_ARG
+    assert lib.pf_bin_sort(h, None, None, None) == _lib.PF_ERR_INVALID_ARG
+    # scene size must match the plan
+    s.n_cells = 11
+    assert lib.pf_project(C.byref(s), h, C.c_void_p(256), None) == _lib.PF_ERR_INVALID_ARG
+    lib.pf_plan_destroy(h)
+
+
+def test_product_path_refuses_to_run_without_library(monkeypatch, tmp_path):
+    from paper_2604_24994_gb300 import _lib
+    monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(_lib, "_lib", None)
+    with pytest.raises(RuntimeError, match="CUDA library missing"):
+        _lib.lib()
