@@ -1,0 +1,332 @@
+"""Benchmark: 1080p forward and forward+backward frames/s of the bounded
+power-cell rasterizer on a synthetic 1M-cell capture-shaped scene, with the
+render kernel's roofline fraction, an end-to-end number through host
+buffers, and the FP64 CPU oracle timed on a pixel sample beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: one process per GPU (torchrun); every rank renders its own
+views (independent frames, no data-path collective): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "1080p fwd & fwd+bwd frames/s at 1M cells; serve p50/p99 ms; % roofline"
+UNIT = "frames/s"
+WORKLOAD = "capture-shaped scene, 1,000,000 cells (70% Gaussian mixture in the unit ball, 30% log-uniform shell to r=20), r=0.35*d8, R=1.5r, 32 neighbours; one 1920x1080 pinhole view (fov_y 60 deg) from (3,0,0)"
+
+# FP32 flop constants of the forward, per event (FMA = 2 flops), counted
+# from the kernel source: see DESIGN.md "Roofline of the render kernel".
+FLOPS_PER_CANDIDATE = 17        # cheap sphere test (m x d, |v|^2, compare)
+FLOPS_PER_PASS = 90             # compensated cross product, D, q, b, end set-up
+FLOPS_PER_PLANE = 16            # q.a, d.a, num, divide, compare
+FLOPS_PER_HIT = 150             # face clip, texture (4 sites), alpha, composite
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for n, v in zip(names, r[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+            except Exception:
+                pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_workload(rank: int = 0, small: bool = False):
+    """The 1080p / 1M-cell capture workload, or (small=True) the same recipe
+    at 400k cells and 1280x720 for profiler captures."""
+    from paper_2604_24994_gb300 import inputs
+    t0 = time.time()
+    sc = inputs.capture_scene(400_000 if small else 1_000_000, seed=0, K=32)
+    cam = inputs.capture_camera(1280, 720) if small else inputs.capture_camera()
+    if rank:  # every rank renders its own view of the same scene
+        ang = 2 * math.pi * rank / 8
+        cam = inputs.look_at((3 * math.cos(ang), 3 * math.sin(ang), 0.0), 1920, 1080)
+    return sc, cam, time.time() - t0
+
+
+def cpu_baseline(sc, cam, seconds: float = 15.0):
+    """The oracle as it stands, on a bounded pixel sample of the frame."""
+    import oracle
+    orc = oracle.Oracle(sc)
+    rng = np.random.default_rng(0)
+    n = 16
+    done = 0
+    t_spent = 0.0
+    while t_spent < seconds and done < 4096:
+        pix = np.stack([rng.integers(0, cam.width, n), rng.integers(0, cam.height, n)], 1).astype(np.int32)
+        t0 = time.time()
+        orc.prune_for(cam, pix)
+        orc.render(cam, pix)
+        t_spent += time.time() - t0
+        done += n
+        n = min(2 * n, 256)
+    per_px = t_spent / done
+    fps = 1.0 / (per_px * cam.width * cam.height)
+    return {"value": fps, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{done} random pixels of the 1920x1080 frame ({t_spent:.1f} s, exact prune, "
+                      f"OpenMP over pixels); frames/s = 1 / (time per pixel x 2,073,600)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    sc, cam, _ = make_workload(0)
+    import oracle
+    orc = oracle.Oracle(sc)
+    rng = np.random.default_rng(1)
+    per = []
+    for step in range(args.warmup + args.steps):
+        pix = np.stack([rng.integers(0, cam.width, 64), rng.integers(0, cam.height, 64)], 1).astype(np.int32)
+        t0 = time.time()
+        orc.prune_for(cam, pix)
+        orc.render(cam, pix)
+        dt = time.time() - t0
+        if step >= args.warmup:
+            per.append(dt / 64)
+    per_px = float(np.mean(per))
+    fps = 1.0 / (per_px * cam.width * cam.height)
+    line = {"impl": "reference", "metric": METRIC, "value": fps, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_px * cam.width * cam.height * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "parallelism": "replicas"},
+            "cpu_baseline": {"value": fps, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"each step 64 random pixels of the 1920x1080 frame; frames/s "
+                                       f"extrapolated as 1 / (time per pixel x 2,073,600)"},
+            "e2e": {"value": fps, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2604_24994_gb300 import DeviceScene, Renderer, build
+    build.build()
+
+    sc, cam, gen_s = make_workload(rank, small=args.workload == "small")
+    ds = DeviceScene.from_numpy(sc, "cuda")
+    r = Renderer(ds.n, ds.k, [cam])
+    stream = torch.cuda.current_stream()
+
+    # size the instance capacity (synchronous once), then count work once
+    r.bin(ds, sync=True)
+    n_inst = r.n_instances
+    r.enable_stats(True)
+    rgb, T, last = r.render_fwd(ds)
+    stats = r.stats()
+    r.enable_stats(False)
+
+    # target image for the fwd+bwd step: the same scene with sites moved by N(0, 0.002)
+    from paper_2604_24994_gb300 import inputs
+    tsc = inputs.perturbed_sites(sc, 0.002, seed=1)
+    tds = DeviceScene.from_numpy(tsc, "cuda")
+    rt = Renderer(tds.n, tds.k, [cam])
+    target, _, _ = rt.forward(tds)
+    target = target.clone()
+    del rt, tds
+
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def fwd_step(times=None):
+        # a new view of a resident scene: project + bin/sort + render
+        from paper_2604_24994_gb300._lib import check, lib
+        import ctypes as C
+        P = r.plan
+        s = ds.struct()
+        check(lib().pf_project(C.byref(s), P.handle, P.ws_ptr, stream.cuda_stream), "project")
+        check(lib().pf_bin_sort(P.handle, P.ws_ptr, None, stream.cuda_stream), "bin_sort")
+        if times is not None:
+            a, b = ev(), ev()
+            a.record(stream)
+        out = r.render_fwd(ds, out=(rgb, T, last))
+        if times is not None:
+            b.record(stream)
+            times.append((a, b))
+        return out
+
+    def train_step():
+        r.bin(ds, sync=False)  # prepare + project + bin/sort
+        c, t, l = r.render_fwd(ds, out=(rgb, T, last))
+        g = 2.0 * (c - target)
+        r.backward(ds, g, None, t, l, grads=grads)
+        return g
+
+    grads = {k: torch.zeros_like(v) for k, v in ds.params.items()}
+    # library kernels per forward step: project, tile counts, 2 scans x 3, expand, sort, render
+    kernels_fwd = 1 + 1 + 6 + 1 + 1 + 1
+
+    def timed(fn, k, warm, per_kernel=None):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        tot = 0.0
+        for _ in range(k):
+            flush.zero_()                      # L2 flush between steps (not timed)
+            a, b = ev(), ev()
+            a.record(stream)
+            fn(per_kernel) if per_kernel is not None else fn()
+            b.record(stream)
+            b.synchronize()
+            tot += a.elapsed_time(b)
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        return tot / k
+
+    K, W = args.steps, args.warmup
+    with ClockSampler(local) as clk:
+        kt = []
+        ms_fwd = timed(fwd_step, K, W, kt)
+        ms_render = float(np.mean([a.elapsed_time(b) for a, b in kt]))
+        ms_train = timed(train_step, K, W)
+    clocks = clk.summary()
+
+    # end to end through the public API with host buffers: camera in, image out
+    host_rgb = torch.empty((r.plan.pixels, 3), dtype=torch.float32, pin_memory=True)
+    host_T = torch.empty(r.plan.pixels, dtype=torch.float32, pin_memory=True)
+
+    def e2e_step():
+        r.set_cameras([cam])                     # host camera -> plan (copied by pf_project)
+        fwd_step()
+        host_rgb.copy_(rgb, non_blocking=True)
+        host_T.copy_(T, non_blocking=True)
+
+    ms_e2e = timed(e2e_step, K, W)
+
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_fwd, ms_train, ms_e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_fwd, ms_train, ms_e2e = [float(x) for x in t.cpu()]
+    if rank != 0:
+        return
+
+    pk = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    peak_tflops = 152 * 128 * 2 * sm_max * 1e6 / 1e12     # FP32 FMA lanes x 2 flops x clock
+    flops = (stats["candidates"] * FLOPS_PER_CANDIDATE + stats["sphere_pass"] * FLOPS_PER_PASS
+             + stats["planes"] * FLOPS_PER_PLANE + stats["hits"] * FLOPS_PER_HIT)
+    achieved = flops / (ms_render * 1e-3) / 1e12
+    cpu = cpu_baseline(sc, cam, seconds=args.cpu_seconds) if args.cpu_seconds > 0 else None
+    line = {
+        "metric": METRIC, "value": ws * 1000.0 / ms_fwd, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
+        "ms_per_step": ms_fwd, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (FP64 geometry)", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "resolution": "1920x1080", "cells": ds.n, "neighbours": ds.k,
+                   "instances": n_inst, "parallelism": f"replicas x{ws}",
+                   "l2": "256 MiB buffer written between timed steps (not timed)",
+                   "fwd_step": "pf_project + pf_bin_sort + pf_render_fwd (scene resident and prepared)",
+                   "fwd_bwd_step": "pf_prepare + pf_project + pf_bin_sort + pf_render_fwd + L2 loss grad + pf_render_bwd",
+                   "scene_generation_s": round(gen_s, 1)},
+        "fwd_fps": ws * 1000.0 / ms_fwd, "fwd_bwd_fps": ws * 1000.0 / ms_train, "ms_fwd_bwd": ms_train,
+        "ms_render_fwd_kernel": ms_render,
+        "work": stats,
+        "roofline": {"bound": "alu", "kernel": "render_fwd_kernel", "achieved": achieved, "peak": peak_tflops,
+                     "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
+                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz (unit counts and max clock)"},
+        "e2e": {"value": ws * 1000.0 / ms_e2e, "unit": UNIT, "h2d_bytes_per_step": 184,
+                "d2h_bytes_per_step": r.plan.pixels * 16},
+        "gpu_launches": K * kernels_fwd,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--workload", default="full", choices=["full", "small"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -33,6 +33,7 @@ Scene layout (all float32 except nbr):
 from __future__ import annotations
 
 import dataclasses
+import itertools
 import math
 
 import numpy as np
@@ -176,55 +177,89 @@ def _plane_dist(pi, wi, pj, wj):
 
 
 def build_neighbours(pos: np.ndarray, w: np.ndarray, R: np.ndarray, K: int,
-                     workers: int = -1):
+                     workers: int = -1, n_groups: int = 16):
     """Rank neighbours by radical-plane distance, keep K, clip R for
-    completeness.  Returns (nbr int32 [N,K], R_clipped float32, n_clipped)."""
+    completeness.  Returns (nbr int32 [N,K], R_clipped float32, n_clipped).
+
+    Exact: the K+1 smallest t_ij over all sites.  Candidates are the
+    Euclidean nearest sites; then, per group of sites of similar weight
+    (largest weight W_g), every site closer than
+        tau_i + sqrt(tau_i^2 - w_i + W_g)
+    is added, where tau_i is the (K+1)-th smallest t among the first
+    candidates (a site j with t_ij < tau_i must lie inside that radius)."""
     from scipy.spatial import cKDTree
 
     N = pos.shape[0]
     P = pos.astype(np.float64)
     W = w.astype(np.float64)
     Rn = R.astype(np.float64).copy()
-    wmax = float(W.max()) if N else 0.0
     nbr = np.full((N, K), -1, np.int32)
-    tK1 = np.full(N, np.inf)
     if N <= 1 or K == 0:
         return nbr, R.astype(np.float32), 0
+    kq = min(N, K + 9)
     tree = cKDTree(P)
-    todo = np.arange(N)
-    kq = min(N, max(2 * K + 2, K + 18))
-    while todo.size:
-        kq = min(kq, N)
-        chunk_done = []
-        for s in range(0, todo.size, 200_000):
-            idx = todo[s:s + 200_000]
-            dist, js = tree.query(P[idx], k=kq, workers=workers)
-            dist = dist.reshape(len(idx), kq)
-            js = js.reshape(len(idx), kq)
-            t, _ = _plane_dist(P[idx][:, None, :], W[idx][:, None], P[js], W[js])
-            t[js == idx[:, None]] = np.inf          # self
-            # deterministic order: by t, then by index
-            order = np.lexsort((js, t), axis=1)
-            ts = np.take_along_axis(t, order, 1)
-            jsort = np.take_along_axis(js, order, 1)
-            take = min(K, kq - 1)
-            sel = jsort[:, :take]
-            selt = ts[:, :take]
-            sel = np.where(np.isfinite(selt), sel, -1)
-            nbr[idx, :take] = sel
-            kth = ts[:, take] if kq - 1 > take else np.full(len(idx), np.inf)
-            tK1[idx] = kth
-            if kq >= N:
-                ok = np.ones(len(idx), bool)
-            else:
-                dmax = dist[:, -1]
-                # any unseen j has |a| >= dmax, so t_ij >= (dmax^2 + w_i - wmax) / (2 dmax)
-                lb = (dmax * dmax + W[idx] - wmax) / (2.0 * dmax)
-                ok = lb >= kth
-            chunk_done.append(idx[ok])
-        done = np.concatenate(chunk_done) if chunk_done else np.zeros(0, int)
-        todo = np.setdiff1d(todo, done)
-        kq *= 2
+    best_t = np.full((N, K + 1), np.inf)
+    best_j = np.full((N, K + 1), -1, np.int64)
+    dmax = np.zeros(N)
+    CH = 250_000
+    for s0 in range(0, N, CH):
+        idx = np.arange(s0, min(N, s0 + CH))
+        dist, js = tree.query(P[idx], k=kq, workers=workers)
+        dist = dist.reshape(len(idx), kq)
+        js = js.reshape(len(idx), kq)
+        t, _ = _plane_dist(P[idx][:, None, :], W[idx][:, None], P[js], W[js])
+        t[js == idx[:, None]] = np.inf
+        order = np.lexsort((js, t), axis=1)[:, :K + 1]
+        m = min(K + 1, kq)
+        best_t[idx, :m] = np.take_along_axis(t, order, 1)[:, :m]
+        best_j[idx, :m] = np.take_along_axis(js, order, 1)[:, :m]
+        dmax[idx] = dist[:, -1] if kq < N else np.inf
+    tau = best_t[:, K]
+    # weight groups, each with its own tree and largest weight
+    order_w = np.argsort(W, kind="stable")
+    extra_i, extra_j = [], []
+    for g in np.array_split(order_w, max(1, min(n_groups, N))):
+        if g.size == 0:
+            continue
+        Wg = float(W[g].max())
+        disc = tau * tau - W + Wg
+        rho = tau + np.sqrt(np.maximum(disc, 0.0))
+        need = np.nonzero(np.isfinite(tau) & (disc >= 0) & (rho > dmax))[0]
+        if need.size == 0:
+            continue
+        tg = cKDTree(P[g])
+        cnt = tg.query_ball_point(P[need], rho[need], return_length=True, workers=workers)
+        need = need[cnt > 0]
+        if need.size == 0:
+            continue
+        lists = tg.query_ball_point(P[need], rho[need], workers=workers)
+        lens = np.fromiter((len(l) for l in lists), np.int64, len(lists))
+        flat = np.fromiter(itertools.chain.from_iterable(lists), np.int64, int(lens.sum()))
+        ci = np.repeat(need, lens)
+        js = g[flat]
+        L = np.linalg.norm(P[js] - P[ci], axis=1)
+        keep = (L > dmax[ci]) & (js != ci)
+        extra_i.append(ci[keep])
+        extra_j.append(js[keep])
+    if extra_i and sum(a.size for a in extra_i):
+        ei = np.concatenate(extra_i)
+        ej = np.concatenate(extra_j)
+        et, _ = _plane_dist(P[ei], W[ei], P[ej], W[ej])
+        cells = np.unique(ei)
+        # merge each affected cell's current best with its extra candidates
+        bi = np.repeat(cells, K + 1)
+        ai = np.concatenate([bi, ei])
+        at = np.concatenate([best_t[cells].reshape(-1), et])
+        aj = np.concatenate([best_j[cells].reshape(-1), ej])
+        o = np.lexsort((aj, at, ai))
+        ai, at, aj = ai[o], at[o], aj[o]
+        start = np.searchsorted(ai, cells)
+        rank = np.arange(ai.size) - np.repeat(start, np.diff(np.append(start, ai.size)))
+        sel = rank < K + 1
+        best_t[ai[sel], rank[sel]] = at[sel]
+        best_j[ai[sel], rank[sel]] = aj[sel]
+    nbr[:] = np.where(np.isfinite(best_t[:, :K]), best_j[:, :K], -1).astype(np.int32)
+    tK1 = best_t[:, K]
     clip = tK1 < Rn
     Rn[clip] = np.maximum(tK1[clip], 0.0)
     Rf = Rn.astype(np.float32)
