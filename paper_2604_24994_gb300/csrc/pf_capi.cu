@@ -52,7 +52,7 @@ WS Plan::ws(void *base) const {
     return w;
 }
 
-static bool camera_ok(const pf_camera &c) {
+bool camera_ok(const pf_camera &c) {
     if (c.width < 1 || c.height < 1 || c.width > 16384 || c.height > 16384) return false;
     if (!(c.fx > 0) || !(c.fy > 0)) return false;
     for (int i = 0; i < 9; i++)
@@ -62,7 +62,7 @@ static bool camera_ok(const pf_camera &c) {
     return isfinite(c.cx) && isfinite(c.cy) && isfinite(c.fx) && isfinite(c.fy);
 }
 
-static void fill_views(Plan *p, const pf_camera *cams) {
+void fill_views(Plan *p, const pf_camera *cams) {
     int64_t tb = 0, pb = 0, db = 0;
     for (int v = 0; v < p->nv; v++) {
         ViewDev &d = p->views_host[v];
@@ -91,7 +91,7 @@ static void fill_views(Plan *p, const pf_camera *cams) {
     p->total_diff = db;
 }
 
-static void make_layout(Plan *p) {
+void make_layout(Plan *p) {
     Layout &L = p->L;
     uint64_t o = 0;
     auto take = [&](uint64_t bytes) {
@@ -127,7 +127,7 @@ static void make_layout(Plan *p) {
     L.total = o;
 }
 
-static bool scene_ok(const pf_scene *s, const Plan *p) {
+bool scene_ok(const pf_scene *s, const Plan *p) {
     if (!s) return false;
     if (s->n_cells != p->n || s->k_nbr != p->k) {
         set_error("scene has N=%d K=%d but the plan N=%d K=%d", s->n_cells, s->k_nbr, p->n, p->k);

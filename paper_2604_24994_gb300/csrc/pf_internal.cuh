@@ -119,6 +119,10 @@ __host__ __device__ inline uint64_t align_up(uint64_t x, uint64_t a) { return (x
 
 void set_error(const char *fmt, ...);
 pf_status cuda_status(cudaError_t e, const char *what);
+bool camera_ok(const pf_camera &c);
+bool scene_ok(const pf_scene *s, const Plan *p);
+void fill_views(Plan *p, const pf_camera *cams);  // per-view constants and offsets
+void make_layout(Plan *p);                        // workspace offsets
 
 // kernels launched from the C API (defined in the .cu files)
 cudaError_t launch_prepare(const pf_scene &s, const Plan &p, const WS &w, cudaStream_t st);

@@ -1,0 +1,118 @@
+// pf_render_fwd_static: one small view rendered with no caller workspace and
+// no device allocation.  The scratch that pf_prepare / pf_project /
+// pf_bin_sort / pf_render_fwd normally take from the caller's workspace
+// lives here in one file-scope __device__ array instead.
+//
+// Who needs this: code that must not allocate device memory at all, for
+// example a host that hands its whole memory budget to another allocator,
+// a real-time loop where an allocation (or the caching allocator growing)
+// is not allowed, or a caller in a context that forbids cudaMalloc (such as
+// an ongoing stream capture).  Such a caller still owns and passes its
+// scene, camera and output buffers.
+//
+// Costs and rules:
+//   - The array is PF_STATIC_SCRATCH_BYTES (about 6.5 MiB).  Every GPU that
+//     loads this library reserves it until the process exits.
+//   - The first call on a device looks up the array's device address with
+//     cudaGetSymbolAddress (host code cannot use the array's name as a
+//     device pointer).  Make that first call before any stream capture.
+//   - All calls share the one array and it keeps the previous call's data.
+//     Everything that has to start at zero is cleared on every call.  Calls
+//     that overlap on the GPU (other streams, other threads) race on it:
+//     serialise them.
+//   - The call synchronises `stream` once (to check the instance count).
+#include <mutex>
+
+#include "pf_internal.cuh"
+
+namespace pf {
+
+constexpr size_t STATIC_SCRATCH_BYTES = PF_STATIC_SCRATCH_BYTES;
+
+static __device__ __align__(256) unsigned char g_static_scratch[STATIC_SCRATCH_BYTES];
+
+static std::mutex g_static_mu;
+static void *g_static_ptr[128];
+
+// Device address of the array on the current device (looked up once per device).
+static pf_status static_scratch(void **out) {
+    int dev = 0;
+    pf_status s = cuda_status(cudaGetDevice(&dev), "pf_render_fwd_static: cudaGetDevice");
+    if (s) return s;
+    if (dev < 0 || dev >= 128) {
+        set_error("pf_render_fwd_static: device %d out of range", dev);
+        return PF_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void *p = nullptr;
+        s = cuda_status(cudaGetSymbolAddress(&p, g_static_scratch), "pf_render_fwd_static: cudaGetSymbolAddress");
+        if (s) return s;
+        g_static_ptr[dev] = p;
+    }
+    *out = g_static_ptr[dev];
+    return PF_OK;
+}
+
+}  // namespace pf
+
+using namespace pf;
+
+extern "C" pf_status pf_render_fwd_static(const pf_scene *scene, const pf_camera *cam, float *rgb, float *T,
+                                          uint32_t *last, void *stream) {
+    set_error("%s", "");
+    if (!scene || !cam || !rgb || !T || !last) {
+        set_error("pf_render_fwd_static: null argument");
+        return PF_ERR_INVALID_ARG;
+    }
+    if (scene->n_cells < 0 || scene->n_cells > PF_STATIC_MAX_CELLS || scene->k_nbr < 0 ||
+        scene->k_nbr > PF_STATIC_MAX_K) {
+        set_error("pf_render_fwd_static: %d cells / %d neighbours exceed the limits %d / %d", scene->n_cells,
+                  scene->k_nbr, PF_STATIC_MAX_CELLS, PF_STATIC_MAX_K);
+        return PF_ERR_INVALID_ARG;
+    }
+    if (!camera_ok(*cam) || cam->width > PF_STATIC_MAX_SIDE || cam->height > PF_STATIC_MAX_SIDE) {
+        set_error("pf_render_fwd_static: camera invalid or larger than %dx%d", PF_STATIC_MAX_SIDE,
+                  PF_STATIC_MAX_SIDE);
+        return PF_ERR_INVALID_ARG;
+    }
+    // a plan on the stack: no heap, no device allocation
+    ViewDev view_host;
+    Plan p;
+    p.n = scene->n_cells;
+    p.k = scene->k_nbr;
+    p.nv = 1;
+    p.cap = PF_STATIC_MAX_INSTANCES;
+    p.stats = 0;
+    p.views_host = &view_host;
+    fill_views(&p, cam);
+    make_layout(&p);
+    if (!scene_ok(scene, &p)) return PF_ERR_INVALID_ARG;
+    if (p.L.total > STATIC_SCRATCH_BYTES) {
+        set_error("pf_render_fwd_static: layout %llu bytes exceeds the static scratch", (unsigned long long)p.L.total);
+        return PF_ERR_CAPACITY;
+    }
+    void *base = nullptr;
+    pf_status s = static_scratch(&base);
+    if (s) return s;
+    WS w = p.ws(base);
+    cudaStream_t st = (cudaStream_t)stream;
+    // the view constants: pageable copy, done before cudaMemcpyAsync returns
+    s = cuda_status(cudaMemcpyAsync(w.views, &view_host, sizeof view_host, cudaMemcpyHostToDevice, st),
+                    "pf_render_fwd_static: views");
+    if (!s) s = cuda_status(launch_prepare(*scene, p, w, st), "pf_render_fwd_static: prepare");
+    if (!s) s = cuda_status(launch_project(*scene, p, w, st), "pf_render_fwd_static: project");
+    if (!s) s = cuda_status(launch_bin_sort(p, w, st), "pf_render_fwd_static: bin_sort");
+    if (s) return s;
+    Counters c;
+    s = cuda_status(cudaMemcpyAsync(&c, w.counters, sizeof c, cudaMemcpyDeviceToHost, st),
+                    "pf_render_fwd_static: counters");
+    if (!s) s = cuda_status(cudaStreamSynchronize(st), "pf_render_fwd_static: sync");
+    if (s) return s;
+    if (c.overflow) {
+        set_error("pf_render_fwd_static: %llu (cell, tile) instances exceed the limit %d",
+                  (unsigned long long)c.total_inst, PF_STATIC_MAX_INSTANCES);
+        return PF_ERR_CAPACITY;
+    }
+    return cuda_status(launch_render_fwd(*scene, p, w, rgb, T, last, st), "pf_render_fwd_static: render");
+}
