@@ -29,6 +29,8 @@ METRIC = "1080p fwd & fwd+bwd frames/s at 1M cells; serve p50/p99 ms; % roofline
 UNIT = "frames/s"
 WORKLOAD = "capture-shaped scene, 1,000,000 cells (70% Gaussian mixture in the unit ball, 30% log-uniform shell to r=20), r=0.35*d8, R=1.5r, 32 neighbours; one 1920x1080 pinhole view (fov_y 60 deg) from (3,0,0)"
 
+WORKLOAD_SMALL = "profiling case: the same recipe at 400,000 cells, one 1280x720 view from (3,0,0)"
+
 # FP32 flop constants of the forward, per event (FMA = 2 flops), counted
 # from the kernel source: see DESIGN.md "Roofline of the render kernel".
 FLOPS_PER_CANDIDATE = 17        # cheap sphere test (m x d, |v|^2, compare)
@@ -292,7 +294,8 @@ def run_ours(args):
         "metric": METRIC, "value": ws * 1000.0 / ms_fwd, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
         "ms_per_step": ms_fwd, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 (FP64 geometry)", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "resolution": "1920x1080", "cells": ds.n, "neighbours": ds.k,
+        "config": {"workload": WORKLOAD if args.workload == "full" else WORKLOAD_SMALL,
+                   "resolution": f"{cam.width}x{cam.height}", "cells": ds.n, "neighbours": ds.k,
                    "instances": n_inst, "parallelism": f"replicas x{ws}",
                    "l2": "256 MiB buffer written between timed steps (not timed)",
                    "fwd_step": "pf_project + pf_bin_sort + pf_render_fwd (scene resident and prepared)",

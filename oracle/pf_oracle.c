@@ -637,9 +637,10 @@ int orc_render_grad(const orc_scene *s, const orc_cands *cd, const orc_camera *c
  *
  * The rectangle is the exact image-plane bounding box of the projected
  * sphere (the tangent lines from the camera centre in the x-z and y-z
- * planes), widened by 1e-6 px, and clipped to the image.  A sphere that
- * reaches the plane z = 0 gets the whole image, minus any side of the view
- * frustum it lies entirely outside of.  Every step is one IEEE operation
+ * planes, slopes (X Z -+ r sqrt(X^2 + Z^2 - r^2)) / (Z^2 - r^2)), widened by
+ * 1e-6 px, and clipped to the image.  A sphere that reaches the plane
+ * z = 0 gets the whole image unless it lies entirely outside a side plane
+ * of the view frustum.  Every step is one IEEE operation
  * in double precision, in the order written (the library evaluates the same
  * rule), so the tile sets can be compared bit for bit.
  * ------------------------------------------------------------------------ */
@@ -671,25 +672,28 @@ void orc_bin_cell(const orc_camera *cam, const double *pos, const double *w, con
     rect[3] = 0;
     if (Z + r <= 0.0) return; /* entirely behind the camera */
     double W = cam->width, H = cam->height;
-    double kl = (0.0 - cam->cx) / cam->fx, kr = (W - cam->cx) / cam->fx;
-    double ku = (0.0 - cam->cy) / cam->fy, kd = (H - cam->cy) / cam->fy;
-    /* outside a side plane of the frustum (x = k z through the camera centre) */
-    if (X - kr * Z > r * sqrt(1.0 + kr * kr)) return;
-    if (kl * Z - X > r * sqrt(1.0 + kl * kl)) return;
-    if (Y - kd * Z > r * sqrt(1.0 + kd * kd)) return;
-    if (ku * Z - Y > r * sqrt(1.0 + ku * ku)) return;
     double ulo = -INFINITY, uhi = INFINITY, vlo = -INFINITY, vhi = INFINITY;
     if (Z > r) {
+        /* tangent lines from the camera centre to the sphere's x-z and y-z circles */
         double rr = r * r;
-        double zr = Z * Z - rr;
+        double izr = 1.0 / (Z * Z - rr);
         double sx = sqrt((X * X + Z * Z) - rr);
         double sy = sqrt((Y * Y + Z * Z) - rr);
-        double kxl = (X * Z - r * sx) / zr, kxh = (X * Z + r * sx) / zr;
-        double kyl = (Y * Z - r * sy) / zr, kyh = (Y * Z + r * sy) / zr;
+        double kxl = (X * Z - r * sx) * izr, kxh = (X * Z + r * sx) * izr;
+        double kyl = (Y * Z - r * sy) * izr, kyh = (Y * Z + r * sy) * izr;
         ulo = cam->fx * kxl + cam->cx;
         uhi = cam->fx * kxh + cam->cx;
         vlo = cam->fy * kyl + cam->cy;
         vhi = cam->fy * kyh + cam->cy;
+    } else {
+        /* reaches z <= 0: whole image unless entirely outside a side plane
+         * x = k z of the frustum (through the camera centre) */
+        double kl = (0.0 - cam->cx) / cam->fx, kr = (W - cam->cx) / cam->fx;
+        double ku = (0.0 - cam->cy) / cam->fy, kd = (H - cam->cy) / cam->fy;
+        if (X - kr * Z > r * sqrt(1.0 + kr * kr)) return;
+        if (kl * Z - X > r * sqrt(1.0 + kl * kl)) return;
+        if (Y - kd * Z > r * sqrt(1.0 + kd * kd)) return;
+        if (ku * Z - Y > r * sqrt(1.0 + ku * ku)) return;
     }
     /* pixel centres u + 0.5 inside [ulo, uhi], widened by 1e-6 px */
     double a0 = orc_ceil((ulo - 0.5) - 1e-6), a1 = orc_floor((uhi - 0.5) + 1e-6);

@@ -9,7 +9,8 @@
 //      finds its cell by binary search, its tile inside the cell's
 //      rectangle, and takes a slot in the tile's bucket;
 //   4. one CTA per tile sorts the bucket by (key, cell): a bitonic network
-//      in shared memory, or in global memory for oversized buckets.
+//      in shared memory (24 KB for up to 2048 entries, 192 KB for up to
+//      16384), or in global memory for larger buckets.
 // The result does not depend on the order of the atomic slot grabs: the
 // composite key (key, cell) is unique.
 #include "pf_internal.cuh"
@@ -18,8 +19,6 @@ namespace pf {
 
 constexpr int SCAN_T = 1024;         // threads per scan block
 constexpr int SCAN_E = 2 * SCAN_T;   // elements per scan block
-constexpr int SORT_T = 256;
-constexpr int SORT_SMEM_N = 4096;    // bucket size sorted in shared memory
 
 // --------------------------------------------------------------- tile counts
 __global__ void tile_counts_kernel(const ViewDev *__restrict__ views, int32_t *__restrict__ diff,
@@ -239,41 +238,74 @@ __device__ void bitonic_sort(KeyArr keys, CellArr cells, int n) {
     }
 }
 
-__global__ void __launch_bounds__(SORT_T) sort_tiles_kernel(const uint32_t *__restrict__ tile_start,
-                                                            unsigned long long cap, unsigned long long *inst_key,
-                                                            uint32_t *inst_cell, uint32_t *__restrict__ inst_sorted,
-                                                            unsigned long long *tmp_key, uint32_t *tmp_cell) {
+// One CTA per tile.  Variant <LO, CAP>: buckets with LO < n <= CAP are
+// sorted in shared memory; with GLOBAL, buckets above CAP are sorted in
+// place in the global scratch arrays.
+template <int LO, int CAP, int NT, bool GLOBAL>
+__global__ void __launch_bounds__(NT) sort_tiles_kernel(const uint32_t *__restrict__ tile_start,
+                                                        unsigned long long cap, const unsigned long long *inst_key,
+                                                        const uint32_t *inst_cell, uint32_t *__restrict__ inst_sorted,
+                                                        unsigned long long *tmp_key, uint32_t *tmp_cell) {
     extern __shared__ unsigned long long sk[];
-    uint32_t *sc = reinterpret_cast<uint32_t *>(sk + SORT_SMEM_N);
+    uint32_t *sc = reinterpret_cast<uint32_t *>(sk + CAP);
     const int64_t t = blockIdx.x;
     unsigned long long s = tile_start[t], e = tile_start[t + 1];
     if (s > cap) s = cap;
     if (e > cap) e = cap;
-    const int n = (int)(e - s);
-    if (n <= 0) return;
+    const int64_t n = (int64_t)(e - s);
+    if (n <= LO || n <= 0) return;
     if (n == 1) {
         if (threadIdx.x == 0) inst_sorted[s] = inst_cell[s];
         return;
     }
-    if (n <= SORT_SMEM_N) {
-        for (int q = threadIdx.x; q < n; q += SORT_T) {
+    if (n <= CAP) {
+        for (int q = threadIdx.x; q < n; q += NT) {
             sk[q] = inst_key[s + q];
             sc[q] = inst_cell[s + q];
         }
         __syncthreads();
-        bitonic_sort(sk, sc, n);
-        for (int q = threadIdx.x; q < n; q += SORT_T) inst_sorted[s + q] = sc[q];
-    } else {
+        bitonic_sort(sk, sc, (int)n);
+        for (int q = threadIdx.x; q < n; q += NT) inst_sorted[s + q] = sc[q];
+    } else if (GLOBAL) {
         unsigned long long *gk = tmp_key + s;
         uint32_t *gc = tmp_cell + s;
-        for (int q = threadIdx.x; q < n; q += SORT_T) {
+        for (int64_t q = threadIdx.x; q < n; q += NT) {
             gk[q] = inst_key[s + q];
             gc[q] = inst_cell[s + q];
         }
         __syncthreads();
-        bitonic_sort(gk, gc, n);
-        for (int q = threadIdx.x; q < n; q += SORT_T) inst_sorted[s + q] = gc[q];
+        bitonic_sort(gk, gc, (int)n);
+        for (int64_t q = threadIdx.x; q < n; q += NT) inst_sorted[s + q] = gc[q];
     }
+}
+
+// Render order: tiles by decreasing list length (bucketed by length / 4),
+// so that persistent render CTAs start with the heaviest tiles.
+__global__ void __launch_bounds__(1024) tile_order_kernel(const uint32_t *__restrict__ tile_start, int64_t T,
+                                                          unsigned long long cap, uint32_t *__restrict__ order) {
+    constexpr int NB = 1024;
+    __shared__ uint32_t hist[NB];
+    for (int b = threadIdx.x; b < NB; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    auto bucket = [&](int64_t t) {
+        unsigned long long s = tile_start[t], e = tile_start[t + 1];
+        if (s > cap) s = cap;
+        if (e > cap) e = cap;
+        const unsigned long long c = (e - s) >> 2;
+        return NB - 1 - (int)(c < NB - 1 ? c : NB - 1);
+    };
+    for (int64_t t = threadIdx.x; t < T; t += blockDim.x) atomicAdd(&hist[bucket(t)], 1u);
+    __syncthreads();
+    if (threadIdx.x == 0) {  // 1024 buckets: a serial scan is cheap
+        uint32_t acc = 0;
+        for (int b = 0; b < NB; b++) {
+            const uint32_t x = hist[b];
+            hist[b] = acc;
+            acc += x;
+        }
+    }
+    __syncthreads();
+    for (int64_t t = threadIdx.x; t < T; t += blockDim.x) order[atomicAdd(&hist[bucket(t)], 1u)] = (uint32_t)t;
 }
 
 cudaError_t launch_bin_sort(const Plan &p, const WS &w, cudaStream_t st) {
@@ -307,14 +339,21 @@ cudaError_t launch_bin_sort(const Plan &p, const WS &w, cudaStream_t st) {
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (T > 0) {
-        const size_t smem = SORT_SMEM_N * (sizeof(unsigned long long) + sizeof(uint32_t));
-        static bool attr_set = false;
-        if (!attr_set) {
-            cudaFuncSetAttribute(sort_tiles_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            attr_set = true;
-        }
-        sort_tiles_kernel<<<(unsigned)T, SORT_T, smem, st>>>(w.tile_start, p.cap, w.inst_key, w.inst_cell,
-                                                             w.inst_sorted, w.sort_tmp_key, w.sort_tmp_cell);
+        tile_order_kernel<<<1, 1024, 0, st>>>(w.tile_start, T, p.cap, w.tile_order);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (T > 0) {
+        // small buckets (<= 2048) in 24 KB of shared memory, large ones in 192 KB
+        constexpr int SMALL = 2048, LARGE = 16384;
+        auto ks = sort_tiles_kernel<0, SMALL, 256, false>;
+        auto kl = sort_tiles_kernel<SMALL, LARGE, 512, true>;
+        const size_t ss = (size_t)SMALL * 12, sl = (size_t)LARGE * 12;
+        cudaFuncSetAttribute(kl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sl);
+        ks<<<(unsigned)T, 256, ss, st>>>(w.tile_start, p.cap, w.inst_key, w.inst_cell, w.inst_sorted, w.sort_tmp_key,
+                                        w.sort_tmp_cell);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        kl<<<(unsigned)T, 512, sl, st>>>(w.tile_start, p.cap, w.inst_key, w.inst_cell, w.inst_sorted, w.sort_tmp_key,
+                                        w.sort_tmp_cell);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;

@@ -2,6 +2,7 @@
 #include <stdarg.h>
 #include <stdio.h>
 #include <stdlib.h>
+#include <math.h>
 #include <string.h>
 
 #include <new>
@@ -41,6 +42,7 @@ WS Plan::ws(void *base) const {
     w.diff = (int32_t *)(b + L.diff);
     w.tile_start = (uint32_t *)(b + L.tile_start);
     w.tile_cursor = (uint32_t *)(b + L.tile_cursor);
+    w.tile_order = (uint32_t *)(b + L.tile_order);
     w.scan_tmp = (uint32_t *)(b + L.scan_tmp);
     w.inst_key = (unsigned long long *)(b + L.inst_key);
     w.inst_cell = (uint32_t *)(b + L.inst_cell);
@@ -75,6 +77,16 @@ void fill_views(Plan *p, const pf_camera *cams) {
         d.cy = c.cy;
         d.ifx = 1.0 / c.fx;
         d.ify = 1.0 / c.fy;
+        // frustum side planes through the camera centre (host IEEE double,
+        // no contraction: the CPU binning evaluates the same expressions)
+        d.kl = (0.0 - c.cx) / c.fx;
+        d.kr = ((double)c.width - c.cx) / c.fx;
+        d.ku = (0.0 - c.cy) / c.fy;
+        d.kd = ((double)c.height - c.cy) / c.fy;
+        d.skl = sqrt(1.0 + d.kl * d.kl);
+        d.skr = sqrt(1.0 + d.kr * d.kr);
+        d.sku = sqrt(1.0 + d.ku * d.ku);
+        d.skd = sqrt(1.0 + d.kd * d.kd);
         d.width = c.width;
         d.height = c.height;
         d.tiles_x = (c.width + TILE - 1) / TILE;
@@ -114,6 +126,7 @@ void make_layout(Plan *p) {
     L.diff = take((uint64_t)p->total_diff * 4);
     L.tile_start = take((T + 1) * 4);
     L.tile_cursor = take(T * 4);
+    L.tile_order = take(T * 4);
     uint64_t m = nv * n > T ? nv * n : T;
     L.scan_tmp_elems = m / 2048 + 2;
     L.scan_tmp = take(L.scan_tmp_elems * 4);

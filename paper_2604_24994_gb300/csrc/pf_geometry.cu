@@ -17,60 +17,84 @@ namespace pf {
 // and is dropped (Sec. 3.2: it cannot cut the cell); one at distance
 // < -R_i excludes the whole ball and marks the cell empty.
 // ---------------------------------------------------------------------------
+// FP64 1/sqrt(x): float estimate refined by two Newton steps (relative
+// error ~1e-15; avoids the FP64 divide and square root sequences).
+__device__ __forceinline__ double rsqrt64(double x) {
+    double r = (double)rsqrtf((float)x);
+    r = r * (1.5 - 0.5 * x * r * r);
+    r = r * (1.5 - 0.5 * x * r * r);
+    return r;
+}
+
 __global__ void __launch_bounds__(256) prepare_kernel(pf_scene s, float *__restrict__ cellrec,
                                                       int32_t *__restrict__ cellnp, float4 *__restrict__ planes,
                                                       int2 *__restrict__ plane_nb) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.n_cells) return;
     const int K = s.k_nbr;
-    const double px = s.pos[3 * i], py = s.pos[3 * i + 1], pz = s.pos[3 * i + 2];
-    const double wi = s.w[i];
-    const double R = s.R[i];
+    const float pxf = s.pos[3 * i], pyf = s.pos[3 * i + 1], pzf = s.pos[3 * i + 2];
+    const double px = pxf, py = pyf, pz = pzf;
+    const float wif = s.w[i];
+    const double wi = wif;
+    const float Rf = s.R[i];
+    const double R = Rf;
     const double nx0 = s.normal[3 * i], ny0 = s.normal[3 * i + 1], nz0 = s.normal[3 * i + 2];
-    const double nl = sqrt(nx0 * nx0 + ny0 * ny0 + nz0 * nz0);
-    const double nx = nx0 / nl, ny = ny0 / nl, nz = nz0 / nl;
-    // orthonormal face frame, branchless construction of Duff et al. (JCGT 2017)
-    const double sg = nz >= 0.0 ? 1.0 : -1.0;
-    const double ca = -1.0 / (sg + nz);
-    const double cb = nx * ny * ca;
-    const double iR = R > 0.0 ? 1.0 / R : 0.0;
-    const double e1x = (1.0 + sg * nx * nx * ca) * iR, e1y = sg * cb * iR, e1z = -sg * nx * iR;
-    const double e2x = cb * iR, e2y = (sg + ny * ny * ca) * iR, e2z = -ny * iR;
+    const double n2 = nx0 * nx0 + ny0 * ny0 + nz0 * nz0;
+    const double inl = n2 > 0.0 ? rsqrt64(n2) : 0.0;
+    const float nx = (float)(nx0 * inl), ny = (float)(ny0 * inl), nz = (float)(nz0 * inl);
+    // orthonormal face frame from the unit normal, branchless construction of
+    // Duff et al. (JCGT 2017); divided by R so that u = (e1.y, e2.y) / R
+    const float sg = nz >= 0.0f ? 1.0f : -1.0f;
+    const float ca = -1.0f / (sg + nz);
+    const float cb = nx * ny * ca;
+    const float iR = Rf > 0.0f ? 1.0f / Rf : 0.0f;
+    const float e1x = (1.0f + sg * nx * nx * ca) * iR, e1y = sg * cb * iR, e1z = -sg * nx * iR;
+    const float e2x = cb * iR, e2y = (sg + ny * ny * ca) * iR, e2z = -ny * iR;
 
-    bool empty = !(R > 0.0) || !(nl > 0.0);
+    bool empty = !(R > 0.0) || !(n2 > 0.0);
     int cnt = 0;
     for (int k = 0; k < K; k++) {
         const int j = s.nbr[(int64_t)i * K + k];
         if (j < 0 || j >= s.n_cells || j == i) continue;
-        const double ax = (double)s.pos[3 * j] - px, ay = (double)s.pos[3 * j + 1] - py,
-                     az = (double)s.pos[3 * j + 2] - pz;
-        const double wj = s.w[j];
+        const float qx = s.pos[3 * j], qy = s.pos[3 * j + 1], qz = s.pos[3 * j + 2];
+        const float wjf = s.w[j];
+        // float pre-test with a wide margin: only planes that may reach the
+        // ball (distance (|a|^2 + w_i - w_j) / (2|a|) < R) go on to FP64
+        {
+            const float ax = qx - pxf, ay = qy - pyf, az = qz - pzf;
+            const float L2 = ax * ax + ay * ay + az * az;
+            const float num = L2 + wif - wjf;
+            const float mag = L2 + fabsf(wif) + fabsf(wjf);
+            const float Lf = sqrtf(L2);
+            if (L2 > 0.0f && num > 2.0f * Lf * Rf * 1.001f + 1e-4f * mag) continue;
+        }
+        const double ax = (double)qx - px, ay = (double)qy - py, az = (double)qz - pz;
+        const double wj = wjf;
         const double L2 = ax * ax + ay * ay + az * az;
         if (L2 == 0.0) {  // coincident sites: pow(x,i) <= pow(x,j) iff w_i >= w_j
             if (wi < wj) empty = true;
             continue;
         }
-        const double L = sqrt(L2);
-        const double g = (L2 + wi - wj) / (2.0 * L);
+        const double iL = rsqrt64(L2);
+        const double g = 0.5 * (L2 + wi - wj) * iL;  // plane distance from p_i
         if (g < -R * (1.0 + 1e-6)) empty = true;
         if (g < R * (1.0 + 1e-6)) {
-            const double iL = 1.0 / L;
             planes[(int64_t)i * K + cnt] = make_float4((float)(ax * iL), (float)(ay * iL), (float)(az * iL), (float)g);
-            plane_nb[(int64_t)i * K + cnt] = make_int2(j, __float_as_int((float)L));
+            plane_nb[(int64_t)i * K + cnt] = make_int2(j, __float_as_int((float)(L2 * iL)));
             cnt++;
         }
     }
     cellnp[i] = cnt;
     float4 *cr = reinterpret_cast<float4 *>(cellrec + (int64_t)i * CELLREC_F);
-    cr[0] = make_float4((float)nx, (float)ny, (float)nz, s.offset[i]);
-    cr[1] = make_float4((float)e1x, (float)e1y, (float)e1z, (float)R);
-    cr[2] = make_float4((float)e2x, (float)e2y, (float)e2z, s.sigma[i]);
+    cr[0] = make_float4(nx, ny, nz, s.offset[i]);
+    cr[1] = make_float4(e1x, e1y, e1z, Rf);
+    cr[2] = make_float4(e2x, e2y, e2z, s.sigma[i]);
     cr[3] = make_float4(s.rgb[3 * i], s.rgb[3 * i + 1], s.rgb[3 * i + 2], __int_as_float(empty ? 1 : 0));
     const float4 *tx = reinterpret_cast<const float4 *>(s.tex + (int64_t)i * 12);
     cr[4] = tx[0];
     cr[5] = tx[1];
     cr[6] = tx[2];
-    cr[7] = make_float4((float)nl, (float)wi, 0.f, 0.f);
+    cr[7] = make_float4((float)(n2 * inl), wif, 0.f, 0.f);
 }
 
 // ---------------------------------------------------------------------------
@@ -140,30 +164,29 @@ __global__ void __launch_bounds__(256) project_kernel(pf_scene s, const ViewDev 
     const double r = s.R[i];
     bool vis = !(DADD(Z, r) <= 0.0);
     const double W = V.width, H = V.height;
-    if (vis) {
-        const double kl = DDIV(DSUB(0.0, V.cx), V.fx), kr = DDIV(DSUB(W, V.cx), V.fx);
-        const double ku = DDIV(DSUB(0.0, V.cy), V.fy), kd = DDIV(DSUB(H, V.cy), V.fy);
-        if (DSUB(X, DMUL(kr, Z)) > DMUL(r, DSQRT(DADD(1.0, DMUL(kr, kr))))) vis = false;
-        if (DSUB(DMUL(kl, Z), X) > DMUL(r, DSQRT(DADD(1.0, DMUL(kl, kl))))) vis = false;
-        if (DSUB(Y, DMUL(kd, Z)) > DMUL(r, DSQRT(DADD(1.0, DMUL(kd, kd))))) vis = false;
-        if (DSUB(DMUL(ku, Z), Y) > DMUL(r, DSQRT(DADD(1.0, DMUL(ku, ku))))) vis = false;
+    double ulo = -CUDART_INF, uhi = CUDART_INF, vlo = -CUDART_INF, vhi = CUDART_INF;
+    if (vis && Z > r) {
+        // tangent lines from the camera centre to the sphere's x-z and y-z circles
+        const double rr = DMUL(r, r);
+        const double izr = DDIV(1.0, DSUB(DMUL(Z, Z), rr));
+        const double sx = DSQRT(DSUB(DADD(DMUL(X, X), DMUL(Z, Z)), rr));
+        const double sy = DSQRT(DSUB(DADD(DMUL(Y, Y), DMUL(Z, Z)), rr));
+        const double kxl = DMUL(DSUB(DMUL(X, Z), DMUL(r, sx)), izr);
+        const double kxh = DMUL(DADD(DMUL(X, Z), DMUL(r, sx)), izr);
+        const double kyl = DMUL(DSUB(DMUL(Y, Z), DMUL(r, sy)), izr);
+        const double kyh = DMUL(DADD(DMUL(Y, Z), DMUL(r, sy)), izr);
+        ulo = DADD(DMUL(V.fx, kxl), V.cx);
+        uhi = DADD(DMUL(V.fx, kxh), V.cx);
+        vlo = DADD(DMUL(V.fy, kyl), V.cy);
+        vhi = DADD(DMUL(V.fy, kyh), V.cy);
+    } else if (vis) {
+        // reaches z <= 0: whole image unless outside a side plane x = k z
+        if (DSUB(X, DMUL(V.kr, Z)) > DMUL(r, V.skr)) vis = false;
+        if (DSUB(DMUL(V.kl, Z), X) > DMUL(r, V.skl)) vis = false;
+        if (DSUB(Y, DMUL(V.kd, Z)) > DMUL(r, V.skd)) vis = false;
+        if (DSUB(DMUL(V.ku, Z), Y) > DMUL(r, V.sku)) vis = false;
     }
     if (vis) {
-        double ulo = -CUDART_INF, uhi = CUDART_INF, vlo = -CUDART_INF, vhi = CUDART_INF;
-        if (Z > r) {
-            const double rr = DMUL(r, r);
-            const double zr = DSUB(DMUL(Z, Z), rr);
-            const double sx = DSQRT(DSUB(DADD(DMUL(X, X), DMUL(Z, Z)), rr));
-            const double sy = DSQRT(DSUB(DADD(DMUL(Y, Y), DMUL(Z, Z)), rr));
-            const double kxl = DDIV(DSUB(DMUL(X, Z), DMUL(r, sx)), zr);
-            const double kxh = DDIV(DADD(DMUL(X, Z), DMUL(r, sx)), zr);
-            const double kyl = DDIV(DSUB(DMUL(Y, Z), DMUL(r, sy)), zr);
-            const double kyh = DDIV(DADD(DMUL(Y, Z), DMUL(r, sy)), zr);
-            ulo = DADD(DMUL(V.fx, kxl), V.cx);
-            uhi = DADD(DMUL(V.fx, kxh), V.cx);
-            vlo = DADD(DMUL(V.fy, kyl), V.cy);
-            vhi = DADD(DMUL(V.fy, kyh), V.cy);
-        }
         double a0 = ceil(DSUB(DSUB(ulo, 0.5), 1e-6)), a1 = floor(DADD(DSUB(uhi, 0.5), 1e-6));
         double b0 = ceil(DSUB(DSUB(vlo, 0.5), 1e-6)), b1 = floor(DADD(DSUB(vhi, 0.5), 1e-6));
         if (a0 < 0.0) a0 = 0.0;

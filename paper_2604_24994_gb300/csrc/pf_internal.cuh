@@ -55,6 +55,8 @@ struct ViewDev {
     double origin[3];
     double fx, fy, cx, cy;
     double ifx, ify;          // 1/fx, 1/fy
+    double kl, kr, ku, kd;    // image-edge slopes x/z, y/z of the frustum side planes
+    double skl, skr, sku, skd; // sqrt(1 + k^2) of each
     int32_t width, height;
     int32_t tiles_x, tiles_y;
     int64_t tile_base;        // first global tile id of this view
@@ -65,6 +67,8 @@ struct ViewDev {
 struct Counters {
     unsigned long long total_inst;  // instances required
     unsigned int overflow;          // 1 if total_inst > capacity
+    unsigned int q_fwd;             // next entry of tile_order for the forward's CTAs
+    unsigned int q_bwd;             // same for the backward
     unsigned int pad;
     unsigned long long stats[8];    // pf_stats fields after `instances`
 };
@@ -72,8 +76,8 @@ struct Counters {
 // Workspace layout (byte offsets into the caller's buffer).
 struct Layout {
     uint64_t views, cellrec, cellnp, planes, plane_nb, viewrec, rect, key, cnt, celloff, diff, tile_start,
-        tile_cursor, scan_tmp, inst_key, inst_cell, inst_sorted, sort_tmp_key, sort_tmp_cell, counters, acc,
-        total;
+        tile_cursor, tile_order, scan_tmp, inst_key, inst_cell, inst_sorted, sort_tmp_key, sort_tmp_cell, counters,
+        acc, total;
     uint64_t scan_tmp_elems;
 };
 
@@ -94,6 +98,7 @@ struct WS {
     int32_t *diff;         // 2D difference grids of all views
     uint32_t *tile_start;  // [T+1]
     uint32_t *tile_cursor; // [T]
+    uint32_t *tile_order;  // [T] tiles by decreasing list length (render order)
     uint32_t *scan_tmp;
     unsigned long long *inst_key;  // [cap]
     uint32_t *inst_cell;   // [cap]

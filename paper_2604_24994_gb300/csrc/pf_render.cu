@@ -163,7 +163,7 @@ __device__ __forceinline__ bool cell_segment(const float *__restrict__ cr, const
     float D = fmaf(R, R, -dot3(v, v));
     sg.refined = 0;
     // near-tangent sphere: decide and measure D in FP64
-    const float dthr = SPHERE_ERR * R * R * fmaxf(sig, 1.0f) * (1.0f / (2.0f * REFINE_EPS));
+    const float dthr = SPHERE_ERR * R * R * sig * (1.0f / (2.0f * REFINE_EPS));
     const float dthr2 = SPHERE_ERR * R * R;
     if (fabsf(D) < fmaxf(dthr * dthr, dthr2)) {
         D = (float)refine_D(S, V, cell, ray);
@@ -213,7 +213,7 @@ __device__ __forceinline__ bool cell_segment(const float *__restrict__ cr, const
     }
     if (empty || !(sb > sa)) return false;
     // near-parallel plane or face at an end: recompute that end in FP64
-    const float lim = PLANE_ERR * fmaxf(sig, 1.0f) * (1.0f / REFINE_EPS);
+    const float lim = PLANE_ERR * sig * (1.0f / REFINE_EPS);
     if (ka >= 0 || ka == K_FACE) {
         if (fabsf(dena) < lim * (R + fabsf(sa))) {
             sa = refine_end(S, V, cell, ka, ka >= 0 ? nb_glob[ka].x : -1, -1.f, ray);
@@ -355,16 +355,26 @@ __device__ __forceinline__ void tile_pixel(const ViewDev &V, int64_t lt, int &px
 
 // ---------------------------------------------------------------- forward
 template <bool STATS>
-__global__ void __launch_bounds__(TILE_PIX) render_fwd_kernel(RenderArgs A, float *__restrict__ rgb_out,
-                                                              float *__restrict__ T_out,
-                                                              uint32_t *__restrict__ last_out) {
+__global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, int64_t n_tiles,
+                                                                 float *__restrict__ rgb_out,
+                                                                 float *__restrict__ T_out,
+                                                                 uint32_t *__restrict__ last_out) {
     extern __shared__ float4 smem4[];
     __shared__ Smem sm;
+    __shared__ int64_t s_q;
     float *s_cr = reinterpret_cast<float *>(smem4);
     float *s_vr = s_cr + BATCH * CELLREC_F;
     float4 *s_pl = reinterpret_cast<float4 *>(s_vr + BATCH * VIEWREC_F);
+    unsigned long long st_cand = 0, st_hit = 0, st_pl = 0, st_ref = 0, st_pass = 0;
+    const bool overflow = A.w.counters->overflow != 0;
 
-    const int64_t tile = blockIdx.x;
+    // persistent CTAs take tiles from the queue, heaviest lists first
+    for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_q = atomicAdd(&A.w.counters->q_fwd, 1u);
+    __syncthreads();
+    if (s_q >= n_tiles) break;
+    const int64_t tile = A.w.tile_order[s_q];
     const int v = find_view(A.w.views, A.nv, tile);
     const ViewDev &V = A.w.views[v];
     int px, py;
@@ -373,7 +383,6 @@ __global__ void __launch_bounds__(TILE_PIX) render_fwd_kernel(RenderArgs A, floa
     Ray ray = pixel_ray(V, inside ? px : 0, inside ? py : 0);
 
     unsigned long long s = A.w.tile_start[tile], e = A.w.tile_start[tile + 1];
-    const bool overflow = A.w.counters->overflow != 0;
     if (s > A.cap) s = A.cap;
     if (e > A.cap) e = A.cap;
     if (overflow) e = s;
@@ -383,7 +392,6 @@ __global__ void __launch_bounds__(TILE_PIX) render_fwd_kernel(RenderArgs A, floa
     float3 C = f3(0.f, 0.f, 0.f);
     uint32_t last = 0;
     bool done = !inside;
-    unsigned long long st_cand = 0, st_hit = 0, st_pl = 0, st_ref = 0, st_pass = 0;
 
     for (unsigned long long base = s; base < e; base += BATCH) {
         const int nb = (int)min((unsigned long long)BATCH, e - base);
@@ -429,6 +437,7 @@ __global__ void __launch_bounds__(TILE_PIX) render_fwd_kernel(RenderArgs A, floa
         T_out[pix] = T;
         last_out[pix] = last;
     }
+    }  // tile queue
     if (STATS) {
         unsigned long long *st = A.w.counters->stats;
         for (int o = 16; o > 0; o >>= 1) {
@@ -546,20 +555,31 @@ __device__ __forceinline__ void route_end(float gt, int kind, float s, float den
     nbj = J.x;
 }
 
-__global__ void __launch_bounds__(TILE_PIX) render_bwd_kernel(RenderArgs A, const float *__restrict__ dL_drgb,
-                                                              const float *__restrict__ dL_dT,
-                                                              const float *__restrict__ T_in,
-                                                              const uint32_t *__restrict__ last_in) {
+__global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, int64_t n_tiles,
+                                                                 const float *__restrict__ dL_drgb,
+                                                                 const float *__restrict__ dL_dT,
+                                                                 const float *__restrict__ T_in,
+                                                                 const uint32_t *__restrict__ last_in) {
     extern __shared__ float4 smem4[];
     __shared__ Smem sm;
     __shared__ int s_maxlast;
+    __shared__ int64_t s_q;
     float *s_cr = reinterpret_cast<float *>(smem4);
     float *s_vr = s_cr + BATCH * CELLREC_F;
     float4 *s_pl = reinterpret_cast<float4 *>(s_vr + BATCH * VIEWREC_F);
     int2 *s_nb = reinterpret_cast<int2 *>(s_pl + BATCH * A.K);
-
     const int lane = threadIdx.x & 31;
-    const int64_t tile = blockIdx.x;
+    const bool overflow = A.w.counters->overflow != 0;
+
+    for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_q = atomicAdd(&A.w.counters->q_bwd, 1u);
+        s_maxlast = 0;
+    }
+    __syncthreads();
+    if (s_q >= n_tiles) break;
+    const int64_t tile = A.w.tile_order[s_q];
     const int v = find_view(A.w.views, A.nv, tile);
     const ViewDev &V = A.w.views[v];
     int px, py;
@@ -569,7 +589,7 @@ __global__ void __launch_bounds__(TILE_PIX) render_bwd_kernel(RenderArgs A, cons
     unsigned long long s = A.w.tile_start[tile], e = A.w.tile_start[tile + 1];
     if (s > A.cap) s = A.cap;
     if (e > A.cap) e = A.cap;
-    if (A.w.counters->overflow) e = s;
+    if (overflow) e = s;
     const int64_t vbase = (int64_t)v * A.n;
 
     float3 g = f3(0.f, 0.f, 0.f);
@@ -583,8 +603,6 @@ __global__ void __launch_bounds__(TILE_PIX) render_bwd_kernel(RenderArgs A, cons
         last = (int)last_in[pix];
         if ((unsigned long long)last > e - s) last = (int)(e - s);
     }
-    if (threadIdx.x == 0) s_maxlast = 0;
-    __syncthreads();
     atomicMax(&s_maxlast, last);
     __syncthreads();
     const int maxlast = s_maxlast;
@@ -729,6 +747,7 @@ __global__ void __launch_bounds__(TILE_PIX) render_bwd_kernel(RenderArgs A, cons
             }
         }
     }
+    }  // tile queue
 }
 
 // Accumulators -> parameter gradients.  n = |n| n^:  dL/dn = (I - n^ n^T) dL/dn^ / |n|;
@@ -784,6 +803,18 @@ static RenderArgs make_args(const pf_scene &s, const Plan &p, const WS &w) {
     return A;
 }
 
+// Enough CTAs to fill every SM at the kernel's occupancy, at most one per tile.
+template <typename Kernel>
+static unsigned persistent_grid(Kernel k, size_t smem, int64_t tiles) {
+    int dev = 0, sms = 1, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, TILE_PIX, smem);
+    if (per_sm < 1) per_sm = 1;
+    const int64_t g = (int64_t)sms * per_sm;
+    return (unsigned)(g < tiles ? g : tiles);
+}
+
 static size_t fwd_smem(int K) {
     return (size_t)BATCH * (CELLREC_F + VIEWREC_F) * 4 + (size_t)BATCH * (K > 0 ? K : 1) * 16;
 }
@@ -794,12 +825,16 @@ cudaError_t launch_render_fwd(const pf_scene &s, const Plan &p, const WS &w, flo
     if (p.total_tiles == 0) return cudaSuccess;
     RenderArgs A = make_args(s, p, w);
     const size_t smem = fwd_smem(p.k);
+    cudaError_t e = cudaMemsetAsync(&w.counters->q_fwd, 0, sizeof(unsigned int), st);
+    if (e != cudaSuccess) return e;
     if (p.stats) {
-        cudaFuncSetAttribute(render_fwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        render_fwd_kernel<true><<<(unsigned)p.total_tiles, TILE_PIX, smem, st>>>(A, rgb, T, last);
+        auto k = render_fwd_kernel<true>;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k<<<persistent_grid(k, smem, p.total_tiles), TILE_PIX, smem, st>>>(A, p.total_tiles, rgb, T, last);
     } else {
-        cudaFuncSetAttribute(render_fwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        render_fwd_kernel<false><<<(unsigned)p.total_tiles, TILE_PIX, smem, st>>>(A, rgb, T, last);
+        auto k = render_fwd_kernel<false>;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k<<<persistent_grid(k, smem, p.total_tiles), TILE_PIX, smem, st>>>(A, p.total_tiles, rgb, T, last);
     }
     return cudaGetLastError();
 }
@@ -813,8 +848,11 @@ cudaError_t launch_render_bwd(const pf_scene &s, const Plan &p, const WS &w, con
     if (p.total_tiles > 0) {
         RenderArgs A = make_args(s, p, w);
         const size_t smem = bwd_smem(p.k);
+        e = cudaMemsetAsync(&w.counters->q_bwd, 0, sizeof(unsigned int), st);
+        if (e != cudaSuccess) return e;
         cudaFuncSetAttribute(render_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        render_bwd_kernel<<<(unsigned)p.total_tiles, TILE_PIX, smem, st>>>(A, dL_drgb, dL_dT, T, last);
+        render_bwd_kernel<<<persistent_grid(render_bwd_kernel, smem, p.total_tiles), TILE_PIX, smem, st>>>(
+            A, p.total_tiles, dL_drgb, dL_dT, T, last);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     finalize_kernel<<<(p.n + 255) / 256, 256, 0, st>>>(p.n, w.acc, w.cellrec, g);
