@@ -229,11 +229,15 @@ def run_ours(args):
         c, t, l = r.render_fwd(ds, out=(rgb, T, last))
         g = 2.0 * (c - target)
         r.backward(ds, g, None, t, l, grads=grads)
+        if ws > 1:  # data parallel over views: sum the per-view gradients (the one exchange step)
+            for v in grads.values():
+                torch.distributed.all_reduce(v)
         return g
 
     grads = {k: torch.zeros_like(v) for k, v in ds.params.items()}
-    # library kernels per forward step: project, tile counts, 2 scans x 3, expand, sort, render
-    kernels_fwd = 1 + 1 + 6 + 1 + 1 + 1
+    # library kernels per forward step: project, tile counts, 2 scans x 3, expand, tile order,
+    # 2 tile sorts (shared-memory sizes), render
+    kernels_fwd = 1 + 1 + 6 + 1 + 1 + 2 + 1
 
     def timed(fn, k, warm, per_kernel=None):
         for _ in range(warm):
@@ -290,12 +294,13 @@ def run_ours(args):
              + stats["planes"] * FLOPS_PER_PLANE + stats["hits"] * FLOPS_PER_HIT)
     achieved = flops / (ms_render * 1e-3) / 1e12
     cpu = cpu_baseline(sc, cam, seconds=args.cpu_seconds) if args.cpu_seconds > 0 else None
+    n_cells, n_nbr = ds.n, ds.k
     line = {
         "metric": METRIC, "value": ws * 1000.0 / ms_fwd, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
         "ms_per_step": ms_fwd, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 (FP64 geometry)", "data": "synthetic",
         "config": {"workload": WORKLOAD if args.workload == "full" else WORKLOAD_SMALL,
-                   "resolution": f"{cam.width}x{cam.height}", "cells": ds.n, "neighbours": ds.k,
+                   "resolution": f"{cam.width}x{cam.height}", "cells": n_cells, "neighbours": n_nbr,
                    "instances": n_inst, "parallelism": f"replicas x{ws}",
                    "l2": "256 MiB buffer written between timed steps (not timed)",
                    "fwd_step": "pf_project + pf_bin_sort + pf_render_fwd (scene resident and prepared)",
@@ -313,7 +318,97 @@ def run_ours(args):
         "clocks": clocks,
         "cpu_baseline": cpu,
     }
+    del r, ds, flush, grads, target, host_rgb, host_T, rgb, T, last
+    torch.cuda.empty_cache()
+    line["serve"] = None if args.no_serve else serve_bench(args, local)
     print(json.dumps(line), flush=True)
+
+
+SERVE_SIZES = [(640, 360), (1280, 720), (1920, 1080), (3840, 2160)]
+SERVE_PROBS = [0.3, 0.3, 0.3, 0.1]
+
+
+def serve_bench(args, local: int):
+    """Serving workload: a 2M-cell capture-shaped scene stays resident;
+    requests arrive Poisson at `rate`/s with resolutions drawn from
+    SERVE_SIZES; admission by a 40 GB tile/sort memory budget.  Both the
+    continuous-batching server and the plain one-view-per-launch renderer
+    (one request per batch, one in flight, no graphs) run the same arrival
+    trace; then each runs a closed-loop burst to saturation."""
+    import torch
+    from paper_2604_24994_gb300 import DeviceScene, inputs
+    from paper_2604_24994_gb300.serve import Server
+
+    t0 = time.time()
+    n_cells = 2_000_000 if args.workload == "full" else 400_000
+    sc = inputs.capture_scene(n_cells, seed=0, K=32)
+    gen_s = time.time() - t0
+    ds = DeviceScene.from_numpy(sc, "cuda")
+    rng = np.random.default_rng(0)
+    dur = args.serve_seconds
+    rate = args.serve_rate
+    n_req = int(rate * dur * 1.2) + 64
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+    arrivals = arrivals[arrivals < dur]
+    cams = inputs.random_sphere_cameras(rng, len(arrivals) + 400, 2.0, 6.0, SERVE_SIZES, SERVE_PROBS)
+    ring = {}
+    for (w, h) in SERVE_SIZES:  # output buffers, reused round-robin
+        ring[(w, h)] = [(torch.empty((w * h, 3), device="cuda"), torch.empty(w * h, device="cuda"))
+                        for _ in range(12 if w < 3840 else 4)]
+    ctr = {k: 0 for k in ring}
+
+    def outputs(cam):
+        k = (cam.width, cam.height)
+        o = ring[k][ctr[k] % len(ring[k])]
+        ctr[k] += 1
+        return o
+
+    budget = int(args.serve_budget_gb * (1 << 30))
+
+    def run(opts, open_loop: bool):
+        srv = Server(ds, budget, **opts)
+        # warm-up: every resolution alone and in a batch (graph capture, first launches)
+        ids = [srv.submit(c, *outputs(c)) for c in cams[-40:]]
+        for i in ids:
+            srv.wait(i, 600000)
+        srv.reset_stats()
+        ids = []
+        if open_loop:
+            start = time.perf_counter()
+            for a, cam in zip(arrivals, cams):
+                delay = start + a - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                st, rid = srv.try_submit(cam, *outputs(cam))
+                if st == 0:
+                    ids.append(rid)
+        else:  # closed loop: a burst that keeps every slot busy
+            for cam in cams[:300]:
+                ids.append(srv.submit(cam, *outputs(cam)))
+        for i in ids:
+            srv.wait(i, 600000)
+        rep = srv.report()
+        srv.close()
+        return rep
+
+    q = int(2 * rate)  # at most two seconds of backlog are admitted; the rest is rejected (counted)
+    batched = dict(max_batch_views=8, slots=3, use_graphs=True, max_queue=q)
+    plain = dict(max_batch_views=1, slots=1, use_graphs=False, max_queue=q)
+    out = {"workload": f"{n_cells:,}-cell capture-shaped scene resident; Poisson {rate}/s for {dur} s "
+                       f"({len(arrivals)} requests); resolutions 640x360/1280x720/1920x1080/3840x2160 with "
+                       f"p=.3/.3/.3/.1; cameras on spheres of radius 2-6 looking at the origin; "
+                       f"{args.serve_budget_gb:.0f} GB tile/sort budget",
+           "scene_generation_s": round(gen_s, 1)}
+    keep = ("p50_ms", "p99_ms", "mean_ms", "requests_per_s", "mpix_per_s", "mean_batch_views", "completed",
+            "rejected", "graph_replays")
+    for name, opts in (("batched", batched), ("plain", plain)):
+        rep_open = run(opts, True)
+        rep_sat = run(opts, False)
+        out[name] = {"open_loop": {k: rep_open[k] for k in keep},
+                     "saturation": {k: rep_sat[k] for k in ("requests_per_s", "mpix_per_s", "p50_ms", "p99_ms",
+                                                            "mean_batch_views")},
+                     "opts": opts}
+    return out
 
 
 def main():
@@ -324,6 +419,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--workload", default="full", choices=["full", "small"])
+    ap.add_argument("--serve-seconds", type=float, default=20.0)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-budget-gb", type=float, default=40.0)
+    ap.add_argument("--no-serve", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

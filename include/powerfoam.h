@@ -177,6 +177,60 @@ pf_status pf_read_bins(pf_plan *plan, void *ws, uint32_t *tile_start, uint32_t *
                        uint16_t *rects, void *stream);
 
 /*
+ * Serving: continuous batching of render requests over one resident scene.
+ *
+ * The caller provides a device pool (the memory budget, 256-byte aligned).
+ * The server keeps the scene's cell records there (prepared once), and
+ * splits the rest into `slots` equal regions, one per batch in flight, each
+ * with its own CUDA stream.  A worker thread admits queued requests in
+ * arrival order into a free slot while the batch's per-view records, tile
+ * arrays and instance buffers fit the slot (the admission test is memory),
+ * up to max_batch_views.  A batch is projected, binned and rendered as one
+ * multi-view plan with one persistent render launch; requests that arrive
+ * while other batches run are admitted as slots free up, so their work
+ * overlaps on the GPU.  With use_graphs the launch sequence of each batch
+ * shape is captured once per slot and replayed.  Results are the same as
+ * rendering each view alone with pf_render_fwd.
+ *
+ * The scene pointers and the pool must stay valid until pf_serve_destroy.
+ * Output buffers (device rgb [W*H,3], T [W*H]) belong to the caller and are
+ * written when the request completes.  No call blocks longer than the
+ * timeout it is given; pf_serve_destroy waits at most 10 s for batches in
+ * flight and drops requests not yet started.
+ */
+typedef struct {
+    int32_t max_batch_views; /* views per batch, 1..256 */
+    int32_t slots;           /* batches in flight, 1..16 */
+    int32_t use_graphs;      /* capture and replay each batch shape */
+    int32_t max_queue;       /* queued requests before submit returns PF_ERR_BUSY */
+} pf_serve_opts;
+
+typedef struct {
+    uint64_t submitted, completed, rejected, batches, graph_replays, requeued;
+    double p50_ms, p99_ms, mean_ms, max_ms; /* submit -> result written */
+    double elapsed_s;                        /* first submit -> last completion */
+    double requests_per_s, mpix_per_s, mean_batch_views;
+} pf_serve_report;
+
+typedef struct pf_server pf_server;
+
+/* Prepares the scene (synchronously) and starts the worker.  Errors:
+ * PF_ERR_INVALID_ARG, PF_ERR_CAPACITY (pool too small for the scene). */
+pf_status pf_serve_create(const pf_scene *scene, void *pool, uint64_t pool_bytes, const pf_serve_opts *opts,
+                          pf_server **out);
+/* Non-blocking.  PF_ERR_CAPACITY if the view cannot fit a slot even alone,
+ * PF_ERR_BUSY if the queue is full (the request is not taken). */
+pf_status pf_serve_submit(pf_server *srv, const pf_camera *cam, float *rgb, float *T, uint64_t *req_id);
+/* Waits up to timeout_ms (0: just check).  *done = 1 when the outputs are
+ * written (the id is then released), 0 if not yet (PF_ERR_TIMEOUT when a
+ * timeout was given), -1 with an error status if the request failed.
+ * PF_ERR_NOT_FOUND for unknown or released ids. */
+pf_status pf_serve_poll(pf_server *srv, uint64_t req_id, int32_t timeout_ms, int32_t *done);
+pf_status pf_serve_stats(pf_server *srv, pf_serve_report *out);
+pf_status pf_serve_reset_stats(pf_server *srv);
+void pf_serve_destroy(pf_server *srv);
+
+/*
  * Forward render of one small view WITHOUT a workspace and without any
  * device allocation (no cudaMalloc, cudaFree or allocating library call).
  * The paper has no counterpart: this exists for callers that cannot

@@ -51,7 +51,31 @@ WS Plan::ws(void *base) const {
     w.sort_tmp_cell = (uint32_t *)(b + L.sort_tmp_cell);
     w.counters = (Counters *)(b + L.counters);
     w.acc = (float *)(b + L.acc);
+    if (external_scene) {
+        const SceneLayout S = make_scene_layout(n, k);
+        char *sb = (char *)scene_ws;
+        w.cellrec = (float *)(sb + S.cellrec);
+        w.cellnp = (int32_t *)(sb + S.cellnp);
+        w.planes = (float4 *)(sb + S.planes);
+        w.plane_nb = (int2 *)(sb + S.plane_nb);
+    }
     return w;
+}
+
+SceneLayout make_scene_layout(int32_t n, int32_t k) {
+    SceneLayout S;
+    uint64_t o = 0;
+    auto take = [&](uint64_t bytes) {
+        uint64_t at = o;
+        o = align_up(o + bytes, 256);
+        return at;
+    };
+    S.cellrec = take((uint64_t)n * CELLREC_F * 4);
+    S.cellnp = take((uint64_t)n * 4);
+    S.planes = take((uint64_t)n * k * 16);
+    S.plane_nb = take((uint64_t)n * k * 8);
+    S.total = o;
+    return S;
 }
 
 bool camera_ok(const pf_camera &c) {
@@ -94,6 +118,9 @@ void fill_views(Plan *p, const pf_camera *cams) {
         d.tile_base = tb;
         d.pix_base = pb;
         d.diff_base = db;
+        d.out_rgb = nullptr;
+        d.out_T = nullptr;
+        d.out_last = nullptr;
         tb += (int64_t)d.tiles_x * d.tiles_y;
         pb += (int64_t)c.width * c.height;
         db += (int64_t)(d.tiles_x + 1) * (d.tiles_y + 1);
@@ -114,10 +141,11 @@ void make_layout(Plan *p) {
     uint64_t n = (uint64_t)p->n, k = (uint64_t)p->k, nv = (uint64_t)p->nv, cap = p->cap;
     uint64_t T = (uint64_t)p->total_tiles;
     L.views = take(nv * sizeof(ViewDev));
-    L.cellrec = take(n * CELLREC_F * 4);
-    L.cellnp = take(n * 4);
-    L.planes = take(n * k * 16);
-    L.plane_nb = take(n * k * 8);
+    const uint64_t ns = p->external_scene ? 0 : n;
+    L.cellrec = take(ns * CELLREC_F * 4);
+    L.cellnp = take(ns * 4);
+    L.planes = take(ns * k * 16);
+    L.plane_nb = take(ns * k * 8);
     L.viewrec = take(nv * n * VIEWREC_F * 4);
     L.rect = take(nv * n * 8);
     L.key = take(nv * n * 8);
@@ -136,7 +164,7 @@ void make_layout(Plan *p) {
     L.sort_tmp_key = take(cap * 8);
     L.sort_tmp_cell = take(cap * 4);
     L.counters = take(sizeof(Counters));
-    L.acc = take(n * ACC_F * 4);
+    L.acc = take((p->fwd_only ? 0 : n) * ACC_F * 4);
     L.total = o;
 }
 

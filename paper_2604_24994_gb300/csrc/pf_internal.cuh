@@ -62,6 +62,9 @@ struct ViewDev {
     int64_t tile_base;        // first global tile id of this view
     int64_t pix_base;         // first pixel of this view in the outputs
     int64_t diff_base;        // offset of this view's (tx+1)(ty+1) difference grid
+    float *out_rgb;           // optional per-view outputs [H*W*3], [H*W], [H*W]
+    float *out_T;             // (NULL: write into the concatenated outputs;
+    uint32_t *out_last;       //  out_last NULL with out_rgb set: not written)
 };
 
 struct Counters {
@@ -116,8 +119,20 @@ struct Plan {
     ViewDev *views_host;   // host copy, uploaded by pf_project
     Layout L;
     int stats;
+    // Optional: the view-independent cell records (cellrec, cellnp, planes,
+    // plane_nb) live in a separate, shared buffer laid out by make_scene_layout
+    // (the server prepares a resident scene once); then L omits them.
+    void *scene_ws = nullptr;
+    bool external_scene = false;
+    bool fwd_only = false;   // omit the gradient accumulators
     WS ws(void *base) const;
 };
+
+// Offsets of the view-independent records in a scene-only buffer.
+struct SceneLayout {
+    uint64_t cellrec, cellnp, planes, plane_nb, total;
+};
+SceneLayout make_scene_layout(int32_t n, int32_t k);
 
 // ------------------------------------------------------------------ helpers
 __host__ __device__ inline uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }

@@ -145,6 +145,12 @@ __device__ __noinline__ float refine_face_dot(const SceneRefs &S, int i, Ray ray
 
 // The ray's segment in one cell.  cr: cell record, vr: view record,
 // pl: the cell's planes, nb: their neighbour ids (global, for refinement).
+// GRAD (the backward) also recomputes D in FP64 whenever D < GRAD_D R^2:
+// the sphere end's derivatives scale with 1/sqrt(D), so near-tangent
+// gradients need D to more digits than the forward's value does.
+constexpr float GRAD_D = 1e-3f;
+
+template <bool GRAD>
 __device__ __forceinline__ bool cell_segment(const float *__restrict__ cr, const float *__restrict__ vr,
                                              const float4 *__restrict__ pl, int np,
                                              const int2 *__restrict__ nb_glob, const SceneRefs &S,
@@ -164,7 +170,7 @@ __device__ __forceinline__ bool cell_segment(const float *__restrict__ cr, const
     sg.refined = 0;
     // near-tangent sphere: decide and measure D in FP64
     const float dthr = SPHERE_ERR * R * R * sig * (1.0f / (2.0f * REFINE_EPS));
-    const float dthr2 = SPHERE_ERR * R * R;
+    const float dthr2 = (GRAD ? GRAD_D : SPHERE_ERR) * R * R;
     if (fabsf(D) < fmaxf(dthr * dthr, dthr2)) {
         D = (float)refine_D(S, V, cell, ray);
         sg.refined = 1;
@@ -405,7 +411,7 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, i
             Seg sg;
             bool cand;
             const int o = sm.poff[j], np = sm.poff[j + 1] - o;
-            const bool hit = cell_segment(cr, s_vr + j * VIEWREC_F, s_pl + o, np,
+            const bool hit = cell_segment<false>(cr, s_vr + j * VIEWREC_F, s_pl + o, np,
                                           A.w.plane_nb + (int64_t)cell * A.K, A.S, V, cell, ray, sg, cand);
             if (STATS) {
                 st_cand++;
@@ -430,12 +436,21 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, i
         if (__syncthreads_count(!done) == 0) break;
     }
     if (inside) {
-        const int64_t pix = V.pix_base + (int64_t)py * V.width + px;
-        rgb_out[3 * pix] = C.x;
-        rgb_out[3 * pix + 1] = C.y;
-        rgb_out[3 * pix + 2] = C.z;
-        T_out[pix] = T;
-        last_out[pix] = last;
+        const int64_t lp = (int64_t)py * V.width + px;
+        if (V.out_rgb) {  // per-view outputs (serving)
+            V.out_rgb[3 * lp] = C.x;
+            V.out_rgb[3 * lp + 1] = C.y;
+            V.out_rgb[3 * lp + 2] = C.z;
+            if (V.out_T) V.out_T[lp] = T;
+            if (V.out_last) V.out_last[lp] = last;
+        } else {
+            const int64_t pix = V.pix_base + lp;
+            rgb_out[3 * pix] = C.x;
+            rgb_out[3 * pix + 1] = C.y;
+            rgb_out[3 * pix + 2] = C.z;
+            T_out[pix] = T;
+            last_out[pix] = last;
+        }
     }
     }  // tile queue
     if (STATS) {
@@ -626,7 +641,7 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
             bool cand;
             bool hit = false;
             if (idx < last)
-                hit = cell_segment(cr, s_vr + j * VIEWREC_F, s_pl + o, np, A.w.plane_nb + (int64_t)cell * A.K,
+                hit = cell_segment<true>(cr, s_vr + j * VIEWREC_F, s_pl + o, np, A.w.plane_nb + (int64_t)cell * A.K,
                                    A.S, V, cell, ray, sg, cand);
             if (!__any_sync(0xffffffffu, hit)) continue;
             float vv[32];

@@ -1,0 +1,121 @@
+"""Serving (continuous batching): results are the same alone and in the mix,
+admission is by memory, back-pressure and bounded waits report errors on
+the host (no GPU fault is involved)."""
+import numpy as np
+import pytest
+
+from paper_2604_24994_gb300 import inputs
+from tests.gpu_util import RGB_TOL, T_TOL
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def scene():
+    from paper_2604_24994_gb300 import DeviceScene, build
+    build.build()
+    sc = inputs.capture_scene(60_000, seed=3, K=32)
+    return sc, DeviceScene.from_numpy(sc, "cuda")
+
+
+def mixed_cameras(n, seed):
+    rng = np.random.default_rng(seed)
+    sizes = [(64, 48), (96, 96), (200, 120), (37, 53), (160, 90)]
+    return inputs.random_sphere_cameras(rng, n, 1.5, 4.0, sizes, [0.2] * 5)
+
+
+def alone(ds, cam):
+    import torch
+    from paper_2604_24994_gb300 import Renderer
+    r = Renderer(ds.n, ds.k, [cam])
+    rgb, T, _ = r.forward(ds)
+    torch.cuda.synchronize()
+    return rgb.cpu().numpy(), T.cpu().numpy()
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+def test_results_same_alone_and_in_the_mix(scene, graphs):
+    import torch
+    from paper_2604_24994_gb300.serve import Server
+    sc, ds = scene
+    cams = mixed_cameras(14, seed=1)
+    srv = Server(ds, 1 << 30, max_batch_views=4, slots=2, use_graphs=graphs)
+    for rnd in range(2):  # the second round replays captured batch shapes
+        outs = []
+        ids = []
+        for cam in cams:
+            rgb = torch.full((cam.n_pixels, 3), float("nan"), device="cuda")
+            T = torch.full((cam.n_pixels,), float("nan"), device="cuda")
+            outs.append((rgb, T))
+            ids.append(srv.submit(cam, rgb, T))
+        for rid in ids:
+            srv.wait(rid, 60000)
+        for cam, (rgb, T) in zip(cams, outs):
+            rgb0, T0 = alone(ds, cam)
+            assert np.abs(rgb.cpu().numpy() - rgb0).max() < RGB_TOL
+            assert np.abs(T.cpu().numpy() - T0).max() < T_TOL
+    rep = srv.report()
+    assert rep["completed"] == 2 * len(cams) and rep["p99_ms"] >= rep["p50_ms"] > 0
+    assert rep["mean_batch_views"] >= 1.0
+    if graphs:
+        assert rep["graph_replays"] > 0
+    srv.close()
+
+
+def test_admission_by_memory_and_back_pressure(scene):
+    import torch
+    from paper_2604_24994_gb300 import _lib
+    from paper_2604_24994_gb300.serve import Server
+    sc, ds = scene
+    # a pool just big enough for the scene records and a small slot
+    scene_bytes = ds.n * (128 + 4 + ds.k * 24) + 4096
+    srv = Server(ds, scene_bytes + 6 * ds.n * 56 + (4 << 20), max_batch_views=2, slots=1, max_queue=3)
+    big = inputs.look_at((3, 0, 0), 4096, 4096)
+    st, _ = srv.try_submit(big, torch.empty(3, device="cuda"), torch.empty(1, device="cuda"))
+    assert st == _lib.PF_ERR_CAPACITY  # cannot fit a slot even alone
+    cam = inputs.look_at((3, 0, 0), 32, 32)
+    outs = [(torch.empty((1024, 3), device="cuda"), torch.empty(1024, device="cuda")) for _ in range(64)]
+    codes = [srv.try_submit(cam, r, t)[0] for r, t in outs]
+    assert _lib.PF_ERR_BUSY in codes  # the queue holds at most 3
+    assert codes[0] == _lib.PF_OK
+    srv.close()
+
+
+def test_poll_unknown_and_timeout_semantics(scene):
+    import torch
+    from paper_2604_24994_gb300 import _lib
+    from paper_2604_24994_gb300.serve import Server
+    sc, ds = scene
+    srv = Server(ds, 1 << 29, max_batch_views=2, slots=1)
+    with pytest.raises(_lib.PFError) as e:
+        srv.poll(123456)
+    assert e.value.status == _lib.PF_ERR_NOT_FOUND
+    cam = inputs.look_at((3, 0, 0), 48, 48)
+    rgb = torch.empty((cam.n_pixels, 3), device="cuda")
+    T = torch.empty(cam.n_pixels, device="cuda")
+    rid = srv.submit(cam, rgb, T)
+    assert srv.poll(rid, 0) in (0, 1)  # non-blocking check
+    srv.wait(rid, 60000)
+    with pytest.raises(_lib.PFError):
+        srv.poll(rid)  # released after completion
+    srv.close()
+
+
+def test_destroy_with_work_in_flight_returns(scene):
+    import time
+
+    import torch
+    from paper_2604_24994_gb300.serve import Server
+    sc, ds = scene
+    srv = Server(ds, 1 << 30, max_batch_views=4, slots=2)
+    cams = mixed_cameras(40, seed=2)
+    keep = []
+    for cam in cams:
+        rgb = torch.empty((cam.n_pixels, 3), device="cuda")
+        T = torch.empty(cam.n_pixels, device="cuda")
+        keep.append((rgb, T))
+        srv.submit(cam, rgb, T)
+    t0 = time.time()
+    srv.close()
+    assert time.time() - t0 < 15.0
+    torch.cuda.synchronize()
