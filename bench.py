@@ -31,12 +31,17 @@ WORKLOAD = "capture-shaped scene, 1,000,000 cells (70% Gaussian mixture in the u
 
 WORKLOAD_SMALL = "profiling case: the same recipe at 400,000 cells, one 1280x720 view from (3,0,0)"
 
-# FP32 flop constants of the forward, per event (FMA = 2 flops), counted
-# from the kernel source: see DESIGN.md "Roofline of the render kernel".
-FLOPS_PER_CANDIDATE = 17        # cheap sphere test (m x d, |v|^2, compare)
-FLOPS_PER_PASS = 90             # compensated cross product, D, q, b, end set-up
-FLOPS_PER_PLANE = 16            # q.a, d.a, num, divide, compare
-FLOPS_PER_HIT = 150             # face clip, texture (4 sites), alpha, composite
+# Algorithmic FP32 flops of the forward per counted event (FMA = 2, add /
+# mul / compare / sqrt / exp / reciprocal = 1), counted operation by
+# operation from the render kernel's source; the design doc lists the terms.
+FLOPS_PER_CANDIDATE = 15        # cheap sphere test: m x d (9), |v|^2 (5), compare (1)
+FLOPS_PER_PASS = 107            # compensated m x d (51), D (7), tangent check (9), sqrt (1),
+                                # q = d x v (9), m.d (5), camera end (2), face clip (14),
+                                # emptiness (1), refinement checks (8)
+FLOPS_PER_PLANE = 14            # q.a (5), g - q.a (1), d.a (5), sign test, divide, compare (3)
+FLOPS_PER_HIT = 92              # face point (6), face coordinates (10), site offsets (4),
+                                # four sites x (|u - s| 3, sqrt, scale, exp, sum) (28),
+                                # normalise (5), colour (24), compositing (15)
 
 
 def peaks():
