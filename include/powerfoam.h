@@ -260,7 +260,7 @@ void pf_serve_destroy(pf_server *srv);
 #define PF_STATIC_MAX_K 32
 #define PF_STATIC_MAX_SIDE 256
 #define PF_STATIC_MAX_INSTANCES 65536
-#define PF_STATIC_SCRATCH_BYTES (6u * 1024u * 1024u + 512u * 1024u)
+#define PF_STATIC_SCRATCH_BYTES (8u * 1024u * 1024u + 512u * 1024u)
 pf_status pf_render_fwd_static(const pf_scene *scene, const pf_camera *cam, float *rgb, float *T, uint32_t *last,
                                void *stream);
 

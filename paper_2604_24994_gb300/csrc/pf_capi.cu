@@ -33,6 +33,7 @@ WS Plan::ws(void *base) const {
     w.cellrec = (float *)(b + L.cellrec);
     w.cellnp = (int32_t *)(b + L.cellnp);
     w.planes = (float4 *)(b + L.planes);
+    w.planes_lo = (float4 *)(b + L.planes_lo);
     w.plane_nb = (int2 *)(b + L.plane_nb);
     w.viewrec = (float *)(b + L.viewrec);
     w.rect = (ushort4 *)(b + L.rect);
@@ -57,6 +58,7 @@ WS Plan::ws(void *base) const {
         w.cellrec = (float *)(sb + S.cellrec);
         w.cellnp = (int32_t *)(sb + S.cellnp);
         w.planes = (float4 *)(sb + S.planes);
+        w.planes_lo = (float4 *)(sb + S.planes_lo);
         w.plane_nb = (int2 *)(sb + S.plane_nb);
     }
     return w;
@@ -74,6 +76,7 @@ SceneLayout make_scene_layout(int32_t n, int32_t k) {
     S.cellnp = take((uint64_t)n * 4);
     S.planes = take((uint64_t)n * k * 16);
     S.plane_nb = take((uint64_t)n * k * 8);
+    S.planes_lo = take((uint64_t)n * k * 16);
     S.total = o;
     return S;
 }
@@ -146,6 +149,7 @@ void make_layout(Plan *p) {
     L.cellnp = take(ns * 4);
     L.planes = take(ns * k * 16);
     L.plane_nb = take(ns * k * 8);
+    L.planes_lo = take(ns * k * 16);
     L.viewrec = take(nv * n * VIEWREC_F * 4);
     L.rect = take(nv * n * 8);
     L.key = take(nv * n * 8);

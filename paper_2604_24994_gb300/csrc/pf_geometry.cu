@@ -28,7 +28,7 @@ __device__ __forceinline__ double rsqrt64(double x) {
 
 __global__ void __launch_bounds__(256) prepare_kernel(pf_scene s, float *__restrict__ cellrec,
                                                       int32_t *__restrict__ cellnp, float4 *__restrict__ planes,
-                                                      int2 *__restrict__ plane_nb) {
+                                                      float4 *__restrict__ planes_lo, int2 *__restrict__ plane_nb) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.n_cells) return;
     const int K = s.k_nbr;
@@ -41,7 +41,8 @@ __global__ void __launch_bounds__(256) prepare_kernel(pf_scene s, float *__restr
     const double nx0 = s.normal[3 * i], ny0 = s.normal[3 * i + 1], nz0 = s.normal[3 * i + 2];
     const double n2 = nx0 * nx0 + ny0 * ny0 + nz0 * nz0;
     const double inl = n2 > 0.0 ? rsqrt64(n2) : 0.0;
-    const float nx = (float)(nx0 * inl), ny = (float)(ny0 * inl), nz = (float)(nz0 * inl);
+    const double nxd = nx0 * inl, nyd = ny0 * inl, nzd = nz0 * inl;
+    const float nx = (float)nxd, ny = (float)nyd, nz = (float)nzd;
     // orthonormal face frame from the unit normal, branchless construction of
     // Duff et al. (JCGT 2017); divided by R so that u = (e1.y, e2.y) / R
     const float sg = nz >= 0.0f ? 1.0f : -1.0f;
@@ -79,7 +80,11 @@ __global__ void __launch_bounds__(256) prepare_kernel(pf_scene s, float *__restr
         const double g = 0.5 * (L2 + wi - wj) * iL;  // plane distance from p_i
         if (g < -R * (1.0 + 1e-6)) empty = true;
         if (g < R * (1.0 + 1e-6)) {
-            planes[(int64_t)i * K + cnt] = make_float4((float)(ax * iL), (float)(ay * iL), (float)(az * iL), (float)g);
+            const double ux = ax * iL, uy = ay * iL, uz = az * iL;
+            const float4 hi = make_float4((float)ux, (float)uy, (float)uz, (float)g);
+            planes[(int64_t)i * K + cnt] = hi;
+            planes_lo[(int64_t)i * K + cnt] = make_float4((float)(ux - (double)hi.x), (float)(uy - (double)hi.y),
+                                                          (float)(uz - (double)hi.z), (float)(g - (double)hi.w));
             plane_nb[(int64_t)i * K + cnt] = make_int2(j, __float_as_int((float)(L2 * iL)));
             cnt++;
         }
@@ -94,7 +99,8 @@ __global__ void __launch_bounds__(256) prepare_kernel(pf_scene s, float *__restr
     cr[4] = tx[0];
     cr[5] = tx[1];
     cr[6] = tx[2];
-    cr[7] = make_float4((float)(n2 * inl), wif, 0.f, 0.f);
+    cr[7] = make_float4((float)(nxd - (double)nx), (float)(nyd - (double)ny), (float)(nzd - (double)nz),
+                        (float)(n2 * inl));
 }
 
 // ---------------------------------------------------------------------------
@@ -214,7 +220,7 @@ cudaError_t launch_prepare(const pf_scene &s, const Plan &p, const WS &w, cudaSt
     if (p.n == 0) return cudaSuccess;
     const int threads = 256;
     const int blocks = (p.n + threads - 1) / threads;
-    prepare_kernel<<<blocks, threads, 0, st>>>(s, w.cellrec, w.cellnp, w.planes, w.plane_nb);
+    prepare_kernel<<<blocks, threads, 0, st>>>(s, w.cellrec, w.cellnp, w.planes, w.planes_lo, w.plane_nb);
     return cudaGetLastError();
 }
 

@@ -31,8 +31,8 @@ enum : int {
     CR_RGB = 12,  // [12..14] rgb,      [15] flags (bit 0: empty)
     CR_FLAGS = 15,
     CR_TEX = 16,  // [16..27] texture, site-major
-    CR_NLEN = 28, // [28] |n|
-    CR_W = 29     // [29] w
+    CR_NLO = 28,  // [28..30] low part of the unit normal (FP64 = hi + lo)
+    CR_NLEN = 31  // [31] |n|
 };
 
 // Gradient accumulator layout (floats per cell).
@@ -80,7 +80,7 @@ struct Counters {
 struct Layout {
     uint64_t views, cellrec, cellnp, planes, plane_nb, viewrec, rect, key, cnt, celloff, diff, tile_start,
         tile_cursor, tile_order, scan_tmp, inst_key, inst_cell, inst_sorted, sort_tmp_key, sort_tmp_cell, counters,
-        acc, total;
+        acc, planes_lo, total;
     uint64_t scan_tmp_elems;
 };
 
@@ -91,7 +91,8 @@ struct WS {
     ViewDev *views;
     float *cellrec;        // [N][32]
     int32_t *cellnp;       // [N] relevant planes
-    float4 *planes;        // [N][K] (unit a, plane distance g/|a|)
+    float4 *planes;        // [N][K] (unit a, plane distance g/|a|), float
+    float4 *planes_lo;     // [N][K] low parts: FP64 plane = planes + planes_lo
     int2 *plane_nb;        // [N][K] (neighbour j, |a| as float bits)
     float *viewrec;        // [V][N][8]: m_hi.xyz, Rt^2, m_lo.xyz, pad
     ushort4 *rect;         // [V][N] tile rect (x0, y0, x1, y1), empty: x0 > x1
@@ -130,7 +131,7 @@ struct Plan {
 
 // Offsets of the view-independent records in a scene-only buffer.
 struct SceneLayout {
-    uint64_t cellrec, cellnp, planes, plane_nb, total;
+    uint64_t cellrec, cellnp, planes, plane_nb, planes_lo, total;
 };
 SceneLayout make_scene_layout(int32_t n, int32_t k);
 

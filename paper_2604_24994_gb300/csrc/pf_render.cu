@@ -24,13 +24,9 @@
 
 namespace pf {
 
-constexpr float REFINE_EPS = 4e-6f;   // sigma * |error of a segment end| budget
+constexpr float REFINE_EPS = 6e-6f;   // sigma * |error of a segment end| budget
 constexpr float PLANE_ERR = 6e-7f;    // bound on |error| of a plane/face end, in units of (R + |s|)
 constexpr float SPHERE_ERR = 6e-7f;   // bound on |error of D|, in units of R^2
-
-struct SceneRefs {          // original parameters, for FP64 refinement
-    const float *pos, *w, *R, *normal, *offset;
-};
 
 struct Seg {
     float sa, sb;           // entry / exit in the local frame
@@ -90,56 +86,49 @@ __device__ __forceinline__ Ray pixel_ray(const ViewDev &V, int u, int v) {
     return R;
 }
 
-// FP64 recomputation of one segment end.  kind: K_SPHERE (sign = -1 entry,
-// +1 exit), K_FACE, or a plane with neighbour j.
-__device__ __noinline__ float refine_end(const SceneRefs &S, const ViewDev &V, int i, int kind, int j, float sign,
-                                         Ray ray) {
+// FP64 recomputation of segment ends, from float pairs already at hand (the
+// view record's m = hi + lo, the ray's d = hi + lo, a plane's hi + lo parts
+// written by prepare): no global gathers, no FP64 divide or sqrt sequence.
+// q = m - (m.d) d is the closest-approach offset in FP64.
+__device__ __forceinline__ double rcp64(double x) {
+    double r = (double)(1.0f / (float)x);
+    r = r * (2.0 - x * r);
+    r = r * (2.0 - x * r);
+    return r;
+}
+
+// A plane (or the face) end: s = (g - q.a) / (d.a); `fallback` if d.a == 0.
+__device__ __noinline__ float refine_plane64(const float *vr, float4 hi, float4 lo, Ray ray, float fallback) {
     const double dx = (double)ray.dh.x + (double)ray.dl.x, dy = (double)ray.dh.y + (double)ray.dl.y,
                  dz = (double)ray.dh.z + (double)ray.dl.z;
-    const double px = S.pos[3 * i], py = S.pos[3 * i + 1], pz = S.pos[3 * i + 2];
-    const double mx = V.origin[0] - px, my = V.origin[1] - py, mz = V.origin[2] - pz;
+    const double mx = (double)vr[0] + (double)vr[4], my = (double)vr[1] + (double)vr[5],
+                 mz = (double)vr[2] + (double)vr[6];
     const double b = mx * dx + my * dy + mz * dz;
     const double qx = mx - b * dx, qy = my - b * dy, qz = mz - b * dz;
-    if (kind == K_SPHERE) {
-        const double R = S.R[i];
-        const double D = R * R - (qx * qx + qy * qy + qz * qz);
-        return (float)(sign * sqrt(D > 0.0 ? D : 0.0));
-    }
-    double ax, ay, az, g;
-    if (kind == K_FACE) {
-        const double nx = S.normal[3 * i], ny = S.normal[3 * i + 1], nz = S.normal[3 * i + 2];
-        const double nl = sqrt(nx * nx + ny * ny + nz * nz);
-        ax = nx / nl;
-        ay = ny / nl;
-        az = nz / nl;
-        g = S.offset[i];
-    } else {
-        ax = (double)S.pos[3 * j] - px;
-        ay = (double)S.pos[3 * j + 1] - py;
-        az = (double)S.pos[3 * j + 2] - pz;
-        g = 0.5 * (ax * ax + ay * ay + az * az + (double)S.w[i] - (double)S.w[j]);
-    }
+    const double ax = (double)hi.x + (double)lo.x, ay = (double)hi.y + (double)lo.y, az = (double)hi.z + (double)lo.z;
+    const double g = (double)hi.w + (double)lo.w;
     const double num = g - (qx * ax + qy * ay + qz * az);
     const double den = dx * ax + dy * ay + dz * az;
-    return (float)(num / den);
+    if (den == 0.0) return fallback;
+    return (float)(num * rcp64(den));
 }
 
-__device__ __noinline__ double refine_D(const SceneRefs &S, const ViewDev &V, int i, Ray ray) {
+// The sphere's D = R^2 - |q|^2.
+__device__ __noinline__ float refine_D64(const float *vr, float R, Ray ray) {
     const double dx = (double)ray.dh.x + (double)ray.dl.x, dy = (double)ray.dh.y + (double)ray.dl.y,
                  dz = (double)ray.dh.z + (double)ray.dl.z;
-    const double mx = V.origin[0] - (double)S.pos[3 * i], my = V.origin[1] - (double)S.pos[3 * i + 1],
-                 mz = V.origin[2] - (double)S.pos[3 * i + 2];
+    const double mx = (double)vr[0] + (double)vr[4], my = (double)vr[1] + (double)vr[5],
+                 mz = (double)vr[2] + (double)vr[6];
     const double b = mx * dx + my * dy + mz * dz;
     const double qx = mx - b * dx, qy = my - b * dy, qz = mz - b * dz;
-    const double R = S.R[i];
-    return R * R - (qx * qx + qy * qy + qz * qz);
+    return (float)((double)R * (double)R - (qx * qx + qy * qy + qz * qz));
 }
 
-__device__ __noinline__ float refine_face_dot(const SceneRefs &S, int i, Ray ray) {
-    const double dx = (double)ray.dh.x + (double)ray.dl.x, dy = (double)ray.dh.y + (double)ray.dl.y,
-                 dz = (double)ray.dh.z + (double)ray.dl.z;
-    const double nx = S.normal[3 * i], ny = S.normal[3 * i + 1], nz = S.normal[3 * i + 2];
-    const double dn = dx * nx + dy * ny + dz * nz;
+// Sign of d.n in FP64 (the side of the face the texture point is taken on).
+__device__ __noinline__ float face_side64(const float *cr, Ray ray) {
+    const double dn = ((double)ray.dh.x + (double)ray.dl.x) * ((double)cr[CR_N] + (double)cr[CR_NLO]) +
+                      ((double)ray.dh.y + (double)ray.dl.y) * ((double)cr[CR_N + 1] + (double)cr[CR_NLO + 1]) +
+                      ((double)ray.dh.z + (double)ray.dl.z) * ((double)cr[CR_N + 2] + (double)cr[CR_NLO + 2]);
     return dn > 0.0 ? 1.0f : (dn < 0.0 ? -1.0f : 0.0f);
 }
 
@@ -153,8 +142,7 @@ constexpr float GRAD_D = 1e-3f;
 template <bool GRAD>
 __device__ __forceinline__ bool cell_segment(const float *__restrict__ cr, const float *__restrict__ vr,
                                              const float4 *__restrict__ pl, int np,
-                                             const int2 *__restrict__ nb_glob, const SceneRefs &S,
-                                             const ViewDev &V, int cell, Ray ray, Seg &sg, bool &cand) {
+                                             const float4 *__restrict__ lo_glob, Ray ray, Seg &sg, bool &cand) {
     const float3 mh = f3(vr[0], vr[1], vr[2]);
     const float3 v0 = cross3(mh, ray.dh);
     cand = dot3(v0, v0) <= vr[3];
@@ -172,7 +160,7 @@ __device__ __forceinline__ bool cell_segment(const float *__restrict__ cr, const
     const float dthr = SPHERE_ERR * R * R * sig * (1.0f / (2.0f * REFINE_EPS));
     const float dthr2 = (GRAD ? GRAD_D : SPHERE_ERR) * R * R;
     if (fabsf(D) < fmaxf(dthr * dthr, dthr2)) {
-        D = (float)refine_D(S, V, cell, ray);
+        D = refine_D64(vr, R, ray);
         sg.refined = 1;
     }
     if (!(D > 0.0f)) return false;
@@ -215,20 +203,24 @@ __device__ __forceinline__ bool cell_segment(const float *__restrict__ cr, const
         } else if (num < 0.0f) {
             empty = true;
         }
-        if (fabsf(den) < 0x1p-20f) sg.dnd = refine_face_dot(S, cell, ray);
+        if (fabsf(den) < 0x1p-20f) sg.dnd = face_side64(cr, ray);
     }
     if (empty || !(sb > sa)) return false;
     // near-parallel plane or face at an end: recompute that end in FP64
     const float lim = PLANE_ERR * sig * (1.0f / REFINE_EPS);
     if (ka >= 0 || ka == K_FACE) {
         if (fabsf(dena) < lim * (R + fabsf(sa))) {
-            sa = refine_end(S, V, cell, ka, ka >= 0 ? nb_glob[ka].x : -1, -1.f, ray);
+            sa = ka >= 0 ? refine_plane64(vr, pl[ka], lo_glob[ka], ray, sa)
+                         : refine_plane64(vr, make_float4(cr[CR_N], cr[CR_N + 1], cr[CR_N + 2], cr[CR_OFF]),
+                                          make_float4(cr[CR_NLO], cr[CR_NLO + 1], cr[CR_NLO + 2], 0.f), ray, sa);
             sg.refined++;
         }
     }
     if (kb >= 0 || kb == K_FACE) {
         if (fabsf(denb) < lim * (R + fabsf(sb))) {
-            sb = refine_end(S, V, cell, kb, kb >= 0 ? nb_glob[kb].x : -1, 1.f, ray);
+            sb = kb >= 0 ? refine_plane64(vr, pl[kb], lo_glob[kb], ray, sb)
+                         : refine_plane64(vr, make_float4(cr[CR_N], cr[CR_N + 1], cr[CR_N + 2], cr[CR_OFF]),
+                                          make_float4(cr[CR_NLO], cr[CR_NLO + 1], cr[CR_NLO + 2], 0.f), ray, sb);
             sg.refined++;
         }
     }
@@ -282,58 +274,93 @@ __device__ __forceinline__ float3 face_colour(const float *__restrict__ cr, cons
 }
 
 // ------------------------------------------------------------ batch staging
-struct Smem {
-    int ids[BATCH];
-    int poff[BATCH + 1];
+// Tile lists are staged in batches of 32 cells, double buffered: while the
+// warps work on batch k, the copies of batch k+1 are in flight (cp.async,
+// 16-byte granules: the 128-byte cell record, the 32-byte view record and
+// the cell's planes, plus the planes' neighbour ids for the backward).
+struct Stage {
+    char *base;        // dynamic shared memory
+    int K;
+    bool with_nb;
+    // per buffer: cell records [BATCH][CELLREC_F], view records [BATCH][VIEWREC_F],
+    // planes [BATCH * K], plane neighbours [BATCH * K]; then ids [2][BATCH], poff [2][BATCH + 1]
+    __device__ __forceinline__ size_t kk() const { return K > 0 ? (size_t)K : 1; }
+    __device__ __forceinline__ size_t buf_bytes() const {
+        return (size_t)BATCH * (CELLREC_F + VIEWREC_F) * 4 + BATCH * kk() * (with_nb ? 24 : 16);
+    }
+    __device__ __forceinline__ float *cr(int b) const { return reinterpret_cast<float *>(base + b * buf_bytes()); }
+    __device__ __forceinline__ float *vr(int b) const { return cr(b) + BATCH * CELLREC_F; }
+    __device__ __forceinline__ float4 *pl(int b) const { return reinterpret_cast<float4 *>(vr(b) + BATCH * VIEWREC_F); }
+    __device__ __forceinline__ int2 *nb(int b) const { return reinterpret_cast<int2 *>(pl(b) + BATCH * kk()); }
+    __device__ __forceinline__ int *ids(int b) const {
+        return reinterpret_cast<int *>(base + 2 * buf_bytes()) + b * BATCH;
+    }
+    __device__ __forceinline__ int *poff(int b) const {
+        return reinterpret_cast<int *>(base + 2 * buf_bytes()) + 2 * BATCH + b * (BATCH + 1);
+    }
 };
 
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(src));
 }
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(src));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
-// Stage list entries [base, base + nb) of the tile into shared memory.
-__device__ __forceinline__ void stage_batch(Smem &sm, float *s_cr, float *s_vr, float4 *s_pl, int2 *s_nb,
-                                            const uint32_t *__restrict__ list, int nb, const WS &w, int64_t vbase,
-                                            int K) {
+// Start the copies of list entries [0, nb) into buffer `buf`.  Every warp
+// reads the 32 ids and plane counts itself (no barrier before the copies);
+// warp 0 also publishes them for the consumers.
+__device__ __forceinline__ void issue_batch(const Stage &sg, int buf, const uint32_t *__restrict__ list, int nb,
+                                            const WS &w, int64_t vbase, int K, bool with_nb) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (warp == 0) {
-        int c = 0, np = 0;
-        if (lane < nb) {
-            c = (int)list[lane];
-            np = w.cellnp[c];
-            sm.ids[lane] = c;
-        }
-        int incl = np;
+    int id = 0, np = 0;
+    if (lane < nb) {
+        id = (int)list[lane];
+        np = w.cellnp[id];
+    }
+    int incl = np;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (warp == 0) {
+        sg.ids(buf)[lane] = id;
+        sg.poff(buf)[lane + 1] = incl;
+        if (lane == 0) sg.poff(buf)[0] = 0;
+    }
+    // records: nb x (8 + 2) chunks over all threads (uniform trip count: the
+    // shuffles need every lane)
+    const int nrec = nb * 10;
+    for (int q0 = 0; q0 < nrec; q0 += TILE_PIX) {
+        const int q = q0 + tid;
+        const int j = (q < nrec ? q : 0) / 10, part = q - j * 10;
+        const int c = __shfl_sync(0xffffffffu, id, j);
+        if (q < nrec) {
+            if (part < 8)
+                cp_async16(sg.cr(buf) + j * CELLREC_F + part * 4, w.cellrec + (int64_t)c * CELLREC_F + part * 4);
+            else
+                cp_async16(sg.vr(buf) + j * VIEWREC_F + (part - 8) * 4,
+                           w.viewrec + (vbase + c) * VIEWREC_F + (part - 8) * 4);
         }
-        sm.poff[lane + 1] = incl;
-        if (lane == 0) sm.poff[0] = 0;
     }
-    __syncthreads();
-    for (int q = tid; q < nb * 10; q += TILE_PIX) {
-        const int j = q / 10, part = q - j * 10;
-        const int c = sm.ids[j];
-        if (part < 8)
-            cp_async16(s_cr + j * CELLREC_F + part * 4, w.cellrec + (int64_t)c * CELLREC_F + part * 4);
-        else
-            cp_async16(s_vr + j * VIEWREC_F + (part - 8) * 4, w.viewrec + (vbase + c) * VIEWREC_F + (part - 8) * 4);
-    }
+    // planes: warp w copies the planes of cells w, w + 8, ...
     for (int j = warp; j < nb; j += TILE_PIX / 32) {
-        const int c = sm.ids[j];
-        const int o = sm.poff[j], np = sm.poff[j + 1] - o;
-        for (int k = lane; k < np; k += 32) {
-            cp_async16(s_pl + o + k, w.planes + (int64_t)c * K + k);
-            if (s_nb) *(reinterpret_cast<long long *>(s_nb + o + k)) =
-                *(reinterpret_cast<const long long *>(w.plane_nb + (int64_t)c * K + k));
+        const int c = __shfl_sync(0xffffffffu, id, j);
+        const int end = __shfl_sync(0xffffffffu, incl, j);
+        const int cnt = __shfl_sync(0xffffffffu, np, j);
+        const int o = end - cnt;
+        for (int k = lane; k < cnt; k += 32) {
+            cp_async16(sg.pl(buf) + o + k, w.planes + (int64_t)c * K + k);
+            if (with_nb) cp_async8(sg.nb(buf) + o + k, w.plane_nb + (int64_t)c * K + k);
         }
     }
-    cp_async_wait_all();
-    __syncthreads();
+    cp_async_commit();
 }
 
 __device__ __forceinline__ int find_view(const ViewDev *views, int nv, int64_t tile) {
@@ -347,16 +374,74 @@ __device__ __forceinline__ int find_view(const ViewDev *views, int nv, int64_t t
 
 struct RenderArgs {
     WS w;
-    SceneRefs S;
     int nv, n, K;
     unsigned long long cap;
 };
 
-__device__ __forceinline__ void tile_pixel(const ViewDev &V, int64_t lt, int &px, int &py) {
+__device__ __forceinline__ void tile_pixel(const ViewDev &V, int64_t lt, int &px, int &py, int &wx, int &wy) {
     const int tx = (int)(lt % V.tiles_x), ty = (int)(lt / V.tiles_x);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    px = tx * TILE + (warp & 1) * 8 + (lane & 7);
-    py = ty * TILE + (warp >> 1) * 4 + (lane >> 3);
+    wx = tx * TILE + (warp & 1) * 8;   // the warp's 8x4 block
+    wy = ty * TILE + (warp >> 1) * 4;
+    px = wx + (lane & 7);
+    py = wy + (lane >> 3);
+}
+
+// The warp's view cone: centre ray through the middle of its 8x4 block and
+// the tangent of the largest angle to any of its 32 pixel rays.
+struct Cone {
+    float3 dc;
+    float tan_t;
+};
+
+__device__ __forceinline__ Cone warp_cone(const ViewDev &V, int wx, int wy, const Ray &ray) {
+    Cone c;
+    const Ray r0 = pixel_ray(V, wx + 4, wy + 2);   // near the block's centre; the cone is measured from it
+    c.dc = r0.dh;
+    const float3 d = ray.dh;
+    const float3 x = cross3(d, c.dc);
+    const float sn = sqrtf(dot3(x, x));
+    const float cs = dot3(d, c.dc);
+    float t = sn / fmaxf(cs, 1e-3f);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t = fmaxf(t, __shfl_xor_sync(0xffffffffu, t, o));
+    c.tan_t = t * 1.001f + 1e-5f;
+    return c;
+}
+
+// Ballot of the batch's cells whose bounding sphere can meet the warp's
+// cone: lane j tests cell j (conservative: a sphere near or behind the
+// camera plane always counts).
+__device__ __forceinline__ unsigned warp_mask(const Stage &sg, int buf, int nb, const Cone &cone) {
+    const int lane = threadIdx.x & 31;
+    bool ov = false;
+    if (lane < nb) {
+        const float *vr = sg.vr(buf) + lane * VIEWREC_F;
+        const float R = sg.cr(buf)[lane * CELLREC_F + CR_R];
+        const float3 m = f3(vr[0], vr[1], vr[2]);      // o - p
+        const float tc = -dot3(m, cone.dc);              // site depth along the centre ray
+        const float3 u = cross3(m, cone.dc);
+        const float mm = sqrtf(dot3(m, m));
+        const float rho = sqrtf(dot3(u, u));
+        const float lim = fmaf(fmaxf(tc, 0.0f), cone.tan_t, R * (1.0f + cone.tan_t * cone.tan_t)) + 1e-5f * (mm + R);
+        ov = (tc <= R * 1.01f + 1e-5f * mm) || (rho <= lim);
+        ov = ov && (tc + R >= -1e-5f * mm);
+    }
+    return __ballot_sync(0xffffffffu, ov);
+}
+
+__host__ __device__ inline size_t stage_bytes(int K, bool with_nb) {
+    const size_t k = K > 0 ? (size_t)K : 1;
+    const size_t buf = (size_t)BATCH * (CELLREC_F + VIEWREC_F) * 4 + BATCH * k * (with_nb ? 24 : 16);
+    return 2 * buf + (2 * BATCH + 2 * (BATCH + 1)) * 4;
+}
+
+__device__ __forceinline__ Stage make_stage(float4 *smem, int K, bool with_nb) {
+    Stage sg;
+    sg.base = reinterpret_cast<char *>(smem);
+    sg.K = K;
+    sg.with_nb = with_nb;
+    return sg;
 }
 
 // ---------------------------------------------------------------- forward
@@ -366,11 +451,8 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, i
                                                                  float *__restrict__ T_out,
                                                                  uint32_t *__restrict__ last_out) {
     extern __shared__ float4 smem4[];
-    __shared__ Smem sm;
     __shared__ int64_t s_q;
-    float *s_cr = reinterpret_cast<float *>(smem4);
-    float *s_vr = s_cr + BATCH * CELLREC_F;
-    float4 *s_pl = reinterpret_cast<float4 *>(s_vr + BATCH * VIEWREC_F);
+    const Stage sg = make_stage(smem4, A.K, false);
     unsigned long long st_cand = 0, st_hit = 0, st_pl = 0, st_ref = 0, st_pass = 0;
     const bool overflow = A.w.counters->overflow != 0;
 
@@ -383,58 +465,73 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, i
     const int64_t tile = A.w.tile_order[s_q];
     const int v = find_view(A.w.views, A.nv, tile);
     const ViewDev &V = A.w.views[v];
-    int px, py;
-    tile_pixel(V, tile - V.tile_base, px, py);
+    int px, py, wx, wy;
+    tile_pixel(V, tile - V.tile_base, px, py, wx, wy);
     const bool inside = px < V.width && py < V.height;
-    Ray ray = pixel_ray(V, inside ? px : 0, inside ? py : 0);
+    const Ray ray = pixel_ray(V, px, py);
+    const Cone cone = warp_cone(V, wx, wy, ray);
 
     unsigned long long s = A.w.tile_start[tile], e = A.w.tile_start[tile + 1];
     if (s > A.cap) s = A.cap;
     if (e > A.cap) e = A.cap;
     if (overflow) e = s;
     const int64_t vbase = (int64_t)v * A.n;
+    const int n = (int)(e - s);
+    const int nbat = (n + BATCH - 1) / BATCH;
 
     float T = 1.0f;
     float3 C = f3(0.f, 0.f, 0.f);
     uint32_t last = 0;
     bool done = !inside;
 
-    for (unsigned long long base = s; base < e; base += BATCH) {
-        const int nb = (int)min((unsigned long long)BATCH, e - base);
+    if (nbat > 0) issue_batch(sg, 0, A.w.inst_sorted + s, min(BATCH, n), A.w, vbase, A.K, false);
+    for (int k = 0; k < nbat; k++) {
+        // every warp is done with batch k-1, whose buffer batch k+1 reuses
+        if (__syncthreads_count(!done) == 0) break;
+        if (k + 1 < nbat) {
+            issue_batch(sg, (k + 1) & 1, A.w.inst_sorted + s + (k + 1) * BATCH, min(BATCH, n - (k + 1) * BATCH),
+                        A.w, vbase, A.K, false);
+            cp_async_wait_one();
+        } else {
+            cp_async_wait_all();
+        }
         __syncthreads();
-        stage_batch(sm, s_cr, s_vr, s_pl, nullptr, A.w.inst_sorted + base, nb, A.w, vbase, A.K);
-        for (int j = 0; j < nb; j++) {
+        const int buf = k & 1, nb = min(BATCH, n - k * BATCH);
+        unsigned mask = warp_mask(sg, buf, nb, cone);
+        while (mask) {
+            const int j = __ffs(mask) - 1;
+            mask &= mask - 1;
             if (__all_sync(0xffffffffu, done)) break;
             if (done) continue;
-            const int cell = sm.ids[j];
-            const float *cr = s_cr + j * CELLREC_F;
-            Seg sg;
+            const int cell = sg.ids(buf)[j];
+            const float *cr = sg.cr(buf) + j * CELLREC_F;
+            Seg seg;
             bool cand;
-            const int o = sm.poff[j], np = sm.poff[j + 1] - o;
-            const bool hit = cell_segment<false>(cr, s_vr + j * VIEWREC_F, s_pl + o, np,
-                                          A.w.plane_nb + (int64_t)cell * A.K, A.S, V, cell, ray, sg, cand);
+            const int o = sg.poff(buf)[j], np = sg.poff(buf)[j + 1] - o;
+            const bool hit = cell_segment<false>(cr, sg.vr(buf) + j * VIEWREC_F, sg.pl(buf) + o, np,
+                                                 A.w.planes_lo + (int64_t)cell * A.K, ray, seg, cand);
             if (STATS) {
                 st_cand++;
                 st_pass += cand;
                 st_pl += cand ? np : 0;
-                st_ref += cand ? sg.refined : 0;
+                st_ref += cand ? seg.refined : 0;
                 st_hit += hit;
             }
             if (!hit) continue;
             Tex tx;
-            const float3 c = face_colour(cr, sg, ray, tx);
-            const float x = fminf(cr[CR_SIG] * (sg.sb - sg.sa), X_CAP);
+            const float3 c = face_colour(cr, seg, ray, tx);
+            const float x = fminf(cr[CR_SIG] * (seg.sb - seg.sa), X_CAP);
             const float ex = __expf(-x);
             const float wgt = T * (1.0f - ex);
             C.x = fmaf(wgt, c.x, C.x);
             C.y = fmaf(wgt, c.y, C.y);
             C.z = fmaf(wgt, c.z, C.z);
             T *= ex;
-            last = (uint32_t)(base - s) + j + 1;
+            last = (uint32_t)(k * BATCH + j + 1);
             if (T < T_EPS) done = true;
         }
-        if (__syncthreads_count(!done) == 0) break;
     }
+    cp_async_wait_all();  // a batch may still be in flight after an early exit
     if (inside) {
         const int64_t lp = (int64_t)py * V.width + px;
         if (V.out_rgb) {  // per-view outputs (serving)
@@ -576,13 +673,9 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
                                                                  const float *__restrict__ T_in,
                                                                  const uint32_t *__restrict__ last_in) {
     extern __shared__ float4 smem4[];
-    __shared__ Smem sm;
     __shared__ int s_maxlast;
     __shared__ int64_t s_q;
-    float *s_cr = reinterpret_cast<float *>(smem4);
-    float *s_vr = s_cr + BATCH * CELLREC_F;
-    float4 *s_pl = reinterpret_cast<float4 *>(s_vr + BATCH * VIEWREC_F);
-    int2 *s_nb = reinterpret_cast<int2 *>(s_pl + BATCH * A.K);
+    const Stage stg = make_stage(smem4, A.K, true);
     const int lane = threadIdx.x & 31;
     const bool overflow = A.w.counters->overflow != 0;
 
@@ -597,10 +690,11 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
     const int64_t tile = A.w.tile_order[s_q];
     const int v = find_view(A.w.views, A.nv, tile);
     const ViewDev &V = A.w.views[v];
-    int px, py;
-    tile_pixel(V, tile - V.tile_base, px, py);
+    int px, py, wx, wy;
+    tile_pixel(V, tile - V.tile_base, px, py, wx, wy);
     const bool inside = px < V.width && py < V.height;
-    Ray ray = pixel_ray(V, inside ? px : 0, inside ? py : 0);
+    const Ray ray = pixel_ray(V, px, py);
+    const Cone cone = warp_cone(V, wx, wy, ray);
     unsigned long long s = A.w.tile_start[tile], e = A.w.tile_start[tile + 1];
     if (s > A.cap) s = A.cap;
     if (e > A.cap) e = A.cap;
@@ -625,24 +719,44 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
     float Tafter = Tf;
     float3 accC = f3(0.f, 0.f, 0.f);
     float *acc = A.w.acc;
+    const uint32_t *list = A.w.inst_sorted + s;
 
-    for (int hi = maxlast; hi > 0; hi -= BATCH) {
-        const int lo = hi > BATCH ? hi - BATCH : 0;
-        const int nb = hi - lo;
+    // batches of the list prefix [0, maxlast) in the forward's partition,
+    // walked back to front; batch b-1 is copied while batch b is replayed
+    const int nbat = (maxlast + BATCH - 1) / BATCH;
+    if (nbat > 0)
+        issue_batch(stg, (nbat - 1) & 1, list + (nbat - 1) * BATCH, maxlast - (nbat - 1) * BATCH, A.w, vbase, A.K,
+                    true);
+    for (int b = nbat - 1; b >= 0; b--) {
+        __syncthreads();  // batch b+1, whose buffer batch b-1 reuses, is done
+        if (b > 0) {
+            issue_batch(stg, (b - 1) & 1, list + (b - 1) * BATCH, BATCH, A.w, vbase, A.K, true);
+            cp_async_wait_one();
+        } else {
+            cp_async_wait_all();
+        }
         __syncthreads();
-        stage_batch(sm, s_cr, s_vr, s_pl, s_nb, A.w.inst_sorted + s + lo, nb, A.w, vbase, A.K);
-        for (int j = nb - 1; j >= 0; j--) {
+        const int buf = b & 1, lo = b * BATCH, nb = min(BATCH, maxlast - lo);
+        unsigned mask = warp_mask(stg, buf, nb, cone);
+        const float *s_cr = stg.cr(buf);
+        const float *s_vr = stg.vr(buf);
+        const float4 *s_pl = stg.pl(buf);
+        const int2 *s_nb = stg.nb(buf);
+        const int *poff = stg.poff(buf);
+        while (mask) {
+            const int j = 31 - __clz(mask);
+            mask &= ~(1u << j);
             const int idx = lo + j;
             if (!__any_sync(0xffffffffu, idx < last)) continue;
-            const int cell = sm.ids[j];
+            const int cell = stg.ids(buf)[j];
             const float *cr = s_cr + j * CELLREC_F;
-            const int o = sm.poff[j], np = sm.poff[j + 1] - o;
+            const int o = poff[j], np = poff[j + 1] - o;
             Seg sg;
             bool cand;
             bool hit = false;
             if (idx < last)
-                hit = cell_segment<true>(cr, s_vr + j * VIEWREC_F, s_pl + o, np, A.w.plane_nb + (int64_t)cell * A.K,
-                                   A.S, V, cell, ray, sg, cand);
+                hit = cell_segment<true>(cr, s_vr + j * VIEWREC_F, s_pl + o, np, A.w.planes_lo + (int64_t)cell * A.K,
+                                         ray, sg, cand);
             if (!__any_sync(0xffffffffu, hit)) continue;
             float vv[32];
 #pragma unroll
@@ -762,6 +876,7 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
             }
         }
     }
+    cp_async_wait_all();
     }  // tile queue
 }
 
@@ -806,11 +921,6 @@ __global__ void __launch_bounds__(256) finalize_kernel(int n, const float *__res
 static RenderArgs make_args(const pf_scene &s, const Plan &p, const WS &w) {
     RenderArgs A;
     A.w = w;
-    A.S.pos = s.pos;
-    A.S.w = s.w;
-    A.S.R = s.R;
-    A.S.normal = s.normal;
-    A.S.offset = s.offset;
     A.nv = p.nv;
     A.n = p.n;
     A.K = p.k;
@@ -830,10 +940,8 @@ static unsigned persistent_grid(Kernel k, size_t smem, int64_t tiles) {
     return (unsigned)(g < tiles ? g : tiles);
 }
 
-static size_t fwd_smem(int K) {
-    return (size_t)BATCH * (CELLREC_F + VIEWREC_F) * 4 + (size_t)BATCH * (K > 0 ? K : 1) * 16;
-}
-static size_t bwd_smem(int K) { return fwd_smem(K) + (size_t)BATCH * (K > 0 ? K : 1) * 8; }
+static size_t fwd_smem(int K) { return stage_bytes(K, false); }
+static size_t bwd_smem(int K) { return stage_bytes(K, true); }
 
 cudaError_t launch_render_fwd(const pf_scene &s, const Plan &p, const WS &w, float *rgb, float *T, uint32_t *last,
                               cudaStream_t st) {

@@ -11,7 +11,7 @@
 // scene, camera and output buffers.
 //
 // Costs and rules:
-//   - The array is PF_STATIC_SCRATCH_BYTES (about 6.5 MiB).  Every GPU that
+//   - The array is PF_STATIC_SCRATCH_BYTES (8.5 MiB).  Every GPU that
 //     loads this library reserves it until the process exits.
 //   - The first call on a device looks up the array's device address with
 //     cudaGetSymbolAddress (host code cannot use the array's name as a

@@ -68,7 +68,7 @@ def test_admission_by_memory_and_back_pressure(scene):
     from paper_2604_24994_gb300.serve import Server
     sc, ds = scene
     # a pool just big enough for the scene records and a small slot
-    scene_bytes = ds.n * (128 + 4 + ds.k * 24) + 4096
+    scene_bytes = ds.n * (128 + 4 + ds.k * 40) + 4096
     srv = Server(ds, scene_bytes + 6 * ds.n * 56 + (4 << 20), max_batch_views=2, slots=1, max_queue=3)
     big = inputs.look_at((3, 0, 0), 4096, 4096)
     st, _ = srv.try_submit(big, torch.empty(3, device="cuda"), torch.empty(1, device="cuda"))
