@@ -83,6 +83,11 @@ typedef struct {
     uint64_t planes;     /* radical-plane clips evaluated */
     uint64_t refined;    /* segment ends recomputed in FP64 */
     uint64_t sphere_pass; /* candidates that passed the sphere test */
+    /* the same events counted once per warp (32 pixels) that had at least
+     * one of them: their ratio to the per-pixel counts is the SIMD use */
+    uint64_t warp_candidates;
+    uint64_t warp_passes;
+    uint64_t warp_hits;
 } pf_stats;
 
 const char *pf_status_string(pf_status s);

@@ -42,7 +42,8 @@ class SceneGrad(C.Structure):
 
 
 class Stats(C.Structure):
-    _fields_ = [(k, C.c_uint64) for k in ("instances", "candidates", "hits", "planes", "refined", "sphere_pass")]
+    _fields_ = [(k, C.c_uint64) for k in ("instances", "candidates", "hits", "planes", "refined", "sphere_pass",
+                                                     "warp_candidates", "warp_passes", "warp_hits")]
 
 
 def _sig(lib):

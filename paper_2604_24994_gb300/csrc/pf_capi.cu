@@ -303,6 +303,9 @@ pf_status pf_plan_read_stats(pf_plan *p, void *ws, pf_stats *out, void *stream) 
     out->planes = c.stats[2];
     out->refined = c.stats[3];
     out->sphere_pass = c.stats[4];
+    out->warp_candidates = c.stats[5];
+    out->warp_passes = c.stats[6];
+    out->warp_hits = c.stats[7];
     return PF_OK;
 }
 

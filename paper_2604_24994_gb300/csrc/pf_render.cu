@@ -41,6 +41,12 @@ enum : int { K_SPHERE = -1, K_CAMERA = -2, K_FACE = -3 };
 
 __device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
 __device__ __forceinline__ float dot3(float3 a, float3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
+// 1/x to about 1 ulp; +-0 gives +-inf (subnormals count as zero)
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 __device__ __forceinline__ float3 cross3(float3 a, float3 b) {
     return f3(fmaf(a.y, b.z, -a.z * b.y), fmaf(a.z, b.x, -a.x * b.z), fmaf(a.x, b.y, -a.y * b.x));
 }
@@ -173,22 +179,28 @@ __device__ __forceinline__ bool cell_segment(const float *__restrict__ cr, const
         sa = b;
         ka = K_CAMERA;
     }
-    bool empty = false;
+    // Radical planes, branch free: a plane bounds s from below when d.a < 0
+    // (sign bit, so -0 counts as below) and from above otherwise.  With
+    // d.a = +-0 the quotient is +-inf or NaN: it moves no end unless num < 0
+    // (the ray runs outside the plane), which empties the segment.
+#pragma unroll 2
     for (int k = 0; k < np; k++) {
         const float4 P = pl[k];
         const float3 a = f3(P.x, P.y, P.z);
         const float num = P.w - dot3(q, a);
         const float den = dot3(dh, a);
-        if (den > 0.0f) {
-            const float s = __fdividef(num, den);
-            if (s < sb) { sb = s; kb = k; denb = den; }
-        } else if (den < 0.0f) {
-            const float s = __fdividef(num, den);
-            if (s > sa) { sa = s; ka = k; dena = den; }
-        } else if (num < 0.0f) {
-            empty = true;
-        }
+        const float t = num * rcp_approx(den);
+        const bool ent = __float_as_int(den) < 0;
+        const bool ua = ent && t > sa;
+        const bool ub = !ent && t < sb;
+        sa = ua ? t : sa;
+        ka = ua ? k : ka;
+        sb = ub ? t : sb;
+        kb = ub ? k : kb;
     }
+    if (ka >= 0) dena = dot3(dh, f3(pl[ka].x, pl[ka].y, pl[ka].z));
+    if (kb >= 0) denb = dot3(dh, f3(pl[kb].x, pl[kb].y, pl[kb].z));
+    bool empty = false;
     {
         const float3 n = f3(cr[CR_N], cr[CR_N + 1], cr[CR_N + 2]);
         const float num = cr[CR_OFF] - dot3(q, n);
@@ -454,6 +466,7 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, i
     __shared__ int64_t s_q;
     const Stage sg = make_stage(smem4, A.K, false);
     unsigned long long st_cand = 0, st_hit = 0, st_pl = 0, st_ref = 0, st_pass = 0;
+    unsigned long long st_wcand = 0, st_wpass = 0, st_whit = 0;  // per warp (lane 0 counts)
     const bool overflow = A.w.counters->overflow != 0;
 
     // persistent CTAs take tiles from the queue, heaviest lists first
@@ -516,6 +529,11 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, i
                 st_pl += cand ? np : 0;
                 st_ref += cand ? seg.refined : 0;
                 st_hit += hit;
+                const bool l0 = (threadIdx.x & 31) == __ffs(__activemask()) - 1;
+                const unsigned pm = __ballot_sync(__activemask(), cand), hm = __ballot_sync(__activemask(), hit);
+                st_wcand += l0;
+                st_wpass += l0 && pm;
+                st_whit += l0 && hm;
             }
             if (!hit) continue;
             Tex tx;
@@ -558,6 +576,9 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, i
             st_pl += __shfl_xor_sync(0xffffffffu, st_pl, o);
             st_ref += __shfl_xor_sync(0xffffffffu, st_ref, o);
             st_pass += __shfl_xor_sync(0xffffffffu, st_pass, o);
+            st_wcand += __shfl_xor_sync(0xffffffffu, st_wcand, o);
+            st_wpass += __shfl_xor_sync(0xffffffffu, st_wpass, o);
+            st_whit += __shfl_xor_sync(0xffffffffu, st_whit, o);
         }
         if ((threadIdx.x & 31) == 0) {
             atomicAdd(&st[0], st_cand);
@@ -565,6 +586,9 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, i
             atomicAdd(&st[2], st_pl);
             atomicAdd(&st[3], st_ref);
             atomicAdd(&st[4], st_pass);
+            atomicAdd(&st[5], st_wcand);
+            atomicAdd(&st[6], st_wpass);
+            atomicAdd(&st[7], st_whit);
         }
     }
 }
