@@ -47,21 +47,27 @@ __device__ __forceinline__ float rcp_approx(float x) {
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
+// sqrt(x) to a few ulp for x >= 0 (one hardware approximation, no
+// correctly-rounded fix-up sequence)
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 __device__ __forceinline__ float3 cross3(float3 a, float3 b) {
     return f3(fmaf(a.y, b.z, -a.z * b.y), fmaf(a.z, b.x, -a.x * b.z), fmaf(a.x, b.y, -a.y * b.x));
 }
 
 // One component of (m x d) = m1 d2 - m2 d1 for float pairs m = mh + ml,
-// d = dh + dl: exact products of the high parts plus first-order terms.
+// d = dh + dl.  p2 = mh2 dh1 rounded, e2 its exact rounding error (FMA);
+// fma(mh1, dh2, -p2) rounds the exact mh1 dh2 - p2 once, an error of half
+// an ulp of the (small) result; then the first-order terms of the low parts.
 __device__ __forceinline__ float cross_c(float mh1, float ml1, float dh2, float dl2, float mh2, float ml2, float dh1,
                                          float dl1) {
-    const float p1 = mh1 * dh2;
-    const float e1 = fmaf(mh1, dh2, -p1);
     const float p2 = mh2 * dh1;
     const float e2 = fmaf(mh2, dh1, -p2);
-    const float hi = p1 - p2;
-    float lo = e1 - e2;
-    lo = fmaf(mh1, dl2, lo);
+    const float hi = fmaf(mh1, dh2, -p2);
+    float lo = fmaf(mh1, dl2, -e2);
     lo = fmaf(ml1, dh2, lo);
     lo = fmaf(-mh2, dl1, lo);
     lo = fmaf(-ml2, dh1, lo);
@@ -170,7 +176,7 @@ __device__ __forceinline__ bool cell_segment(const float *__restrict__ cr, const
         sg.refined = 1;
     }
     if (!(D > 0.0f)) return false;
-    const float sq = sqrtf(D);
+    const float sq = sqrt_approx(D);
     const float3 q = cross3(dh, v);
     const float b = dot3(mh, dh);
     float sa = -sq, sb = sq, dena = 0.f, denb = 0.f;
@@ -200,24 +206,25 @@ __device__ __forceinline__ bool cell_segment(const float *__restrict__ cr, const
     }
     if (ka >= 0) dena = dot3(dh, f3(pl[ka].x, pl[ka].y, pl[ka].z));
     if (kb >= 0) denb = dot3(dh, f3(pl[kb].x, pl[kb].y, pl[kb].z));
-    bool empty = false;
     {
+        // the dipole's dense half n.y <= offset, the same way
         const float3 n = f3(cr[CR_N], cr[CR_N + 1], cr[CR_N + 2]);
         const float num = cr[CR_OFF] - dot3(q, n);
         const float den = dot3(dh, n);
+        const float t = num * rcp_approx(den);
+        const bool ent = __float_as_int(den) < 0;
+        const bool ua = ent && t > sa;
+        const bool ub = !ent && t < sb;
+        sa = ua ? t : sa;
+        ka = ua ? K_FACE : ka;
+        dena = ua ? den : dena;
+        sb = ub ? t : sb;
+        kb = ub ? K_FACE : kb;
+        denb = ub ? den : denb;
         sg.dnd = den;
-        if (den > 0.0f) {
-            const float s = __fdividef(num, den);
-            if (s < sb) { sb = s; kb = K_FACE; denb = den; }
-        } else if (den < 0.0f) {
-            const float s = __fdividef(num, den);
-            if (s > sa) { sa = s; ka = K_FACE; dena = den; }
-        } else if (num < 0.0f) {
-            empty = true;
-        }
         if (fabsf(den) < 0x1p-20f) sg.dnd = face_side64(cr, ray);
     }
-    if (empty || !(sb > sa)) return false;
+    if (!(sb > sa)) return false;
     // near-parallel plane or face at an end: recompute that end in FP64
     const float lim = PLANE_ERR * sig * (1.0f / REFINE_EPS);
     if (ka >= 0 || ka == K_FACE) {
@@ -269,7 +276,7 @@ __device__ __forceinline__ float3 face_colour(const float *__restrict__ cr, cons
 #pragma unroll
     for (int k = 0; k < 4; k++) {
         const float ax = tx.ax[k & 1], ay = tx.ay[k >> 1];
-        tx.r[k] = sqrtf(fmaf(ax, ax, ay * ay));
+        tx.r[k] = sqrt_approx(fmaf(ax, ax, ay * ay));
         tx.W[k] = __expf(-KAPPA * tx.r[k]);
         Z += tx.W[k];
     }
@@ -645,14 +652,14 @@ __device__ __forceinline__ void route_end(float gt, int kind, float s, float den
     const float3 y = f3(fmaf(s, d.x, sg.q.x), fmaf(s, d.y, sg.q.y), fmaf(s, d.z, sg.q.z));
     if (kind == K_SPHERE) {
         // |y|^2 = R^2:  dt/dm = -y / (y.d),  dt/dR = R / (y.d),  y.d = s
-        const float is = gt / s;
+        const float is = gt * rcp_approx(s);
         gm.x -= is * y.x;
         gm.y -= is * y.y;
         gm.z -= is * y.z;
         v[G_R] += is * cr[CR_R];
         return;
     }
-    const float id = gt / den;
+    const float id = gt * rcp_approx(den);
     if (kind == K_FACE) {
         // n.y = off:  dt/dm = -n/(d.n), dt/dn = -y/(d.n), dt/doff = 1/(d.n)
         gm.x -= id * cr[CR_N];
@@ -676,7 +683,7 @@ __device__ __forceinline__ void route_end(float gt, int kind, float s, float den
     const float3 ga = f3(-id * y.x, -id * y.y, -id * y.z);
     const float gg = id;
     const float pa = dot3(a, ga);
-    const float iL = 1.0f / L;
+    const float iL = rcp_approx(L);
     const float cg = gg * (1.0f - P.w * iL);
     const float3 dA = f3((ga.x - a.x * pa) * iL + cg * a.x, (ga.y - a.y * pa) * iL + cg * a.y,
                          (ga.z - a.z * pa) * iL + cg * a.z);
@@ -820,7 +827,7 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
                 for (int k = 0; k < 4; k++) {
                     const float gr = -KAPPA * tx.W[k] * (gW[k] - sW);
                     if (tx.r[k] > 0.f) {
-                        const float ir = gr / tx.r[k];
+                        const float ir = gr * rcp_approx(tx.r[k]);
                         gu1 = fmaf(ir, tx.ax[k & 1], gu1);
                         gu2 = fmaf(ir, tx.ay[k >> 1], gu2);
                     }
@@ -830,15 +837,15 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
                 const float3 E2 = f3(cr[CR_E2], cr[CR_E2 + 1], cr[CR_E2 + 2]);
                 const float R = cr[CR_R];
                 const float3 gy = f3(gu1 * E1.x + gu2 * E2.x, gu1 * E1.y + gu2 * E2.y, gu1 * E1.z + gu2 * E2.z);
-                vv[G_R] += -(gu1 * tx.u1 + gu2 * tx.u2) / R;
+                const float iR = rcp_approx(R);
+                vv[G_R] -= (gu1 * tx.u1 + gu2 * tx.u2) * iR;
                 {
                     // dL/de1 = gu1 y / R, dL/de2 = gu2 y / R (frame of Duff et al., JCGT 2017)
-                    const float iR = 1.0f / R;
                     const float3 g1 = f3(gu1 * tx.ys.x * iR, gu1 * tx.ys.y * iR, gu1 * tx.ys.z * iR);
                     const float3 g2 = f3(gu2 * tx.ys.x * iR, gu2 * tx.ys.y * iR, gu2 * tx.ys.z * iR);
                     const float nx = cr[CR_N], ny = cr[CR_N + 1], nz = cr[CR_N + 2];
                     const float sgn = nz >= 0.f ? 1.f : -1.f;
-                    const float ca = -1.0f / (sgn + nz);
+                    const float ca = -rcp_approx(sgn + nz);
                     const float da = ca * ca;
                     const float db0 = ny * ca, db1 = nx * ca, db2 = nx * ny * da;
                     // e1 = (1 + s x^2 a, s b, -s x), e2 = (b, s + y^2 a, -y), b = x y a
