@@ -120,7 +120,8 @@ __global__ void __launch_bounds__(256) prepare_kernel(pf_scene s, float *__restr
 //
 // Site offset m = o - p_i is stored as a float pair (hi + lo ~ 48 bits) for
 // the renderer's compensated products; Rt^2 is a conservative radius^2 for
-// the cheap single-float sphere test (covers its rounding).
+// the cheap single-float sphere test (covers its rounding); the last slot
+// holds the cell's near-tangent threshold on |D|.
 // ---------------------------------------------------------------------------
 #define DADD __dadd_rn
 #define DSUB __dsub_rn
@@ -158,7 +159,7 @@ __global__ void __launch_bounds__(256) project_kernel(pf_scene s, const ViewDev 
         const float rt2 = __double2float_ru(Rt * Rt * (1.0 + 0x1p-20));
         float4 *vr = reinterpret_cast<float4 *>(viewrec + idx * VIEWREC_F);
         vr[0] = make_float4(hx, hy, hz, rt2);
-        vr[1] = make_float4(lx, ly, lz, 0.f);
+        vr[1] = make_float4(lx, ly, lz, sphere_refine_threshold(s.R[i], s.sigma[i]));
     }
 
     ushort4 rc = make_ushort4(1, 1, 0, 0);

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math_constants.h>
 #include <stdint.h>
 
 #include "powerfoam.h"
@@ -13,12 +14,28 @@ constexpr int TILE_PIX = TILE * TILE;  // one thread per pixel
 constexpr int BATCH = 32;              // cells staged per shared-memory batch
 constexpr int MAX_K = 64;              // neighbour list width limit
 constexpr int CELLREC_F = 32;          // floats per view-independent cell record
-constexpr int VIEWREC_F = 8;           // floats per (view, cell) record
+constexpr int VIEWREC_F = 8;           // floats per (view, cell) record: m hi, Rt^2, m lo, D threshold
 constexpr int ACC_F = 32;              // gradient accumulator floats per cell
 constexpr float T_EPS = 1e-6f;         // forward stops once T drops below this
 constexpr float X_CAP = 60.0f;         // sigma * l is capped (alpha = 1 - e^-60)
 constexpr float KAPPA = 6.0f;          // soft-Voronoi sharpness, units of 1/R
 constexpr float SITE = 1.0f / 3.0f;    // texture sites at (+-1/3, +-1/3) R
+
+// Precision budget of the render's float segment ends (the rest of the
+// budget for the forward's 1e-5 in T): an end whose float error bound could
+// move sigma * l by more than REFINE_EPS is recomputed at higher precision.
+constexpr float REFINE_EPS = 6e-6f;    // sigma * |error of a segment end| budget
+constexpr float PLANE_ERR = 6e-7f;     // bound on |error| of a plane/face end, in units of (R + |s|)
+constexpr float SPHERE_ERR = 6e-7f;    // bound on |error of D|, in units of R^2
+
+// |D| below which the sphere's D = R^2 - |v|^2 is recomputed: where the
+// chord 2 sqrt(D) moves sigma * l by more than REFINE_EPS for an error
+// SPHERE_ERR R^2 in D, and never above the error itself.
+__host__ __device__ inline float sphere_refine_threshold(float R, float sigma) {
+    const float dthr = SPHERE_ERR * R * R * sigma * (1.0f / (2.0f * REFINE_EPS));
+    const float t = SPHERE_ERR * R * R;
+    return dthr * dthr > t ? dthr * dthr : t;
+}
 
 // Cell record layout (floats), one 128-byte line per cell.
 enum : int {

@@ -24,9 +24,6 @@
 
 namespace pf {
 
-constexpr float REFINE_EPS = 6e-6f;   // sigma * |error of a segment end| budget
-constexpr float PLANE_ERR = 6e-7f;    // bound on |error| of a plane/face end, in units of (R + |s|)
-constexpr float SPHERE_ERR = 6e-7f;   // bound on |error of D|, in units of R^2
 
 struct Seg {
     float sa, sb;           // entry / exit in the local frame
@@ -155,11 +152,13 @@ template <bool GRAD>
 __device__ __forceinline__ bool cell_segment(const float *__restrict__ cr, const float *__restrict__ vr,
                                              const float4 *__restrict__ pl, int np,
                                              const float4 *__restrict__ lo_glob, Ray ray, Seg &sg, bool &cand) {
-    const float3 mh = f3(vr[0], vr[1], vr[2]);
+    const float4 V0 = reinterpret_cast<const float4 *>(vr)[0];
+    const float3 mh = f3(V0.x, V0.y, V0.z);
     const float3 v0 = cross3(mh, ray.dh);
-    cand = dot3(v0, v0) <= vr[3];
+    cand = dot3(v0, v0) <= V0.w;
     if (!cand) return false;
-    const float3 ml = f3(vr[4], vr[5], vr[6]);
+    const float4 V1 = reinterpret_cast<const float4 *>(vr)[1];
+    const float3 ml = f3(V1.x, V1.y, V1.z);
     const float3 dh = ray.dh, dl = ray.dl;
     const float3 v = f3(cross_c(mh.y, ml.y, dh.z, dl.z, mh.z, ml.z, dh.y, dl.y),
                         cross_c(mh.z, ml.z, dh.x, dl.x, mh.x, ml.x, dh.z, dl.z),
@@ -169,9 +168,7 @@ __device__ __forceinline__ bool cell_segment(const float *__restrict__ cr, const
     float D = fmaf(R, R, -dot3(v, v));
     sg.refined = 0;
     // near-tangent sphere: decide and measure D in FP64
-    const float dthr = SPHERE_ERR * R * R * sig * (1.0f / (2.0f * REFINE_EPS));
-    const float dthr2 = (GRAD ? GRAD_D : SPHERE_ERR) * R * R;
-    if (fabsf(D) < fmaxf(dthr * dthr, dthr2)) {
+    if (fabsf(D) < (GRAD ? fmaxf(V1.w, GRAD_D * R * R) : V1.w)) {
         D = refine_D64(vr, R, ray);
         sg.refined = 1;
     }
@@ -179,7 +176,7 @@ __device__ __forceinline__ bool cell_segment(const float *__restrict__ cr, const
     const float sq = sqrt_approx(D);
     const float3 q = cross3(dh, v);
     const float b = dot3(mh, dh);
-    float sa = -sq, sb = sq, dena = 0.f, denb = 0.f;
+    float sa = -sq, sb = sq;
     int ka = K_SPHERE, kb = K_SPHERE;
     if (b > sa) {
         sa = b;
@@ -204,8 +201,11 @@ __device__ __forceinline__ bool cell_segment(const float *__restrict__ cr, const
         sb = ub ? t : sb;
         kb = ub ? k : kb;
     }
-    if (ka >= 0) dena = dot3(dh, f3(pl[ka].x, pl[ka].y, pl[ka].z));
-    if (kb >= 0) denb = dot3(dh, f3(pl[kb].x, pl[kb].y, pl[kb].z));
+    // d.a of the planes at the ends (+inf for sphere / camera ends); a cell
+    // without planes reads some other slot of the batch and discards it
+    const float4 Pa = pl[max(ka, 0)], Pb = pl[max(kb, 0)];
+    float dena = ka >= 0 ? dot3(dh, f3(Pa.x, Pa.y, Pa.z)) : CUDART_INF_F;
+    float denb = kb >= 0 ? dot3(dh, f3(Pb.x, Pb.y, Pb.z)) : CUDART_INF_F;
     {
         // the dipole's dense half n.y <= offset, the same way
         const float3 n = f3(cr[CR_N], cr[CR_N + 1], cr[CR_N + 2]);
@@ -227,16 +227,15 @@ __device__ __forceinline__ bool cell_segment(const float *__restrict__ cr, const
     if (!(sb > sa)) return false;
     // near-parallel plane or face at an end: recompute that end in FP64
     const float lim = PLANE_ERR * sig * (1.0f / REFINE_EPS);
-    if (ka >= 0 || ka == K_FACE) {
-        if (fabsf(dena) < lim * (R + fabsf(sa))) {
+    const bool ra = fabsf(dena) < lim * (R + fabsf(sa)), rb = fabsf(denb) < lim * (R + fabsf(sb));
+    if (ra || rb) {
+        if (ra) {
             sa = ka >= 0 ? refine_plane64(vr, pl[ka], lo_glob[ka], ray, sa)
                          : refine_plane64(vr, make_float4(cr[CR_N], cr[CR_N + 1], cr[CR_N + 2], cr[CR_OFF]),
                                           make_float4(cr[CR_NLO], cr[CR_NLO + 1], cr[CR_NLO + 2], 0.f), ray, sa);
             sg.refined++;
         }
-    }
-    if (kb >= 0 || kb == K_FACE) {
-        if (fabsf(denb) < lim * (R + fabsf(sb))) {
+        if (rb) {
             sb = kb >= 0 ? refine_plane64(vr, pl[kb], lo_glob[kb], ray, sb)
                          : refine_plane64(vr, make_float4(cr[CR_N], cr[CR_N + 1], cr[CR_N + 2], cr[CR_OFF]),
                                           make_float4(cr[CR_NLO], cr[CR_NLO + 1], cr[CR_NLO + 2], 0.f), ray, sb);
@@ -641,61 +640,58 @@ __device__ __forceinline__ float warp_transpose_sum(float (&v)[32], int lane) {
     return v[0];
 }
 
-// dL/dt of one segment end -> gradients of its active constraint.
-// y = q + s d is the end point relative to p_i.
+// dL/ds of one segment end -> gradients of its active constraint, the same
+// instructions for every kind (the lanes of a warp meet different kinds).
+// y = q + s d is the end point relative to p_i; the constraint c(y) = rhs
+// has normal nrm with d.nrm = dn, so ds/dm = -nrm/dn and ds/d(rhs) = 1/dn:
+//   sphere |y|^2 = R^2:  nrm = y, dn = y.d = s,  rhs = R^2/2 (ds/dR = R/s)
+//   face   n.y = off:    nrm = n, dn = d.n,      ds/dn = -y/dn
+//   plane  a.y = g:      nrm = a, dn = d.a,      ds/da = -y/dn
+//   camera (s = m.d):    no parameter of cell i; contributes nothing here.
+// Lanes whose end is not of a kind see that kind's terms multiplied by 0,
+// with their operands replaced by finite stand-ins first.
 __device__ __forceinline__ void route_end(float gt, int kind, float s, float den, const Seg &sg, const Ray &ray,
                                           const float *cr, const float4 *pl, const int2 *nb, float3 &gm, float (&v)[32],
                                           float (&nbv)[4], int &nbj) {
-    nbj = -1;
-    if (gt == 0.0f || kind == K_CAMERA) return;
+    const bool sph = kind == K_SPHERE, face = kind == K_FACE, plane = kind >= 0;
     const float3 d = ray.dh;
     const float3 y = f3(fmaf(s, d.x, sg.q.x), fmaf(s, d.y, sg.q.y), fmaf(s, d.z, sg.q.z));
-    if (kind == K_SPHERE) {
-        // |y|^2 = R^2:  dt/dm = -y / (y.d),  dt/dR = R / (y.d),  y.d = s
-        const float is = gt * rcp_approx(s);
-        gm.x -= is * y.x;
-        gm.y -= is * y.y;
-        gm.z -= is * y.z;
-        v[G_R] += is * cr[CR_R];
-        return;
-    }
-    const float id = gt * rcp_approx(den);
-    if (kind == K_FACE) {
-        // n.y = off:  dt/dm = -n/(d.n), dt/dn = -y/(d.n), dt/doff = 1/(d.n)
-        gm.x -= id * cr[CR_N];
-        gm.y -= id * cr[CR_N + 1];
-        gm.z -= id * cr[CR_N + 2];
-        v[G_N] -= id * y.x;
-        v[G_N + 1] -= id * y.y;
-        v[G_N + 2] -= id * y.z;
-        v[G_OFF] += id;
-        return;
-    }
-    // plane (unit a, distance g) of neighbour j:  a.y = g
-    const float4 P = pl[kind];
+    float4 P = pl[max(kind, 0)];
+    const int2 J = nb[max(kind, 0)];
+    if (!plane) P = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float L = plane ? __int_as_float(J.y) : 1.0f;
+    const float3 nf = f3(cr[CR_N], cr[CR_N + 1], cr[CR_N + 2]);
+    const float3 nrm = sph ? y : (face ? nf : f3(P.x, P.y, P.z));
+    const float dn = sph ? s : den;
+    const float id = (sph || face || plane) ? gt * rcp_approx(dn) : 0.0f;
+    gm.x -= id * nrm.x;
+    gm.y -= id * nrm.y;
+    gm.z -= id * nrm.z;
+    v[G_R] += (sph ? id : 0.0f) * cr[CR_R];
+    const float fid = face ? id : 0.0f;
+    v[G_N] -= fid * y.x;
+    v[G_N + 1] -= fid * y.y;
+    v[G_N + 2] -= fid * y.z;
+    v[G_OFF] += fid;
+    // plane of neighbour j: dL/da_unit = -id y, dL/dg = id, with a_unit = A/L,
+    // g = (L^2 + w_i - w_j)/(2L), A = p_j - p_i
+    const float pid = plane ? id : 0.0f;
     const float3 a = f3(P.x, P.y, P.z);
-    const int2 J = nb[kind];
-    const float L = __int_as_float(J.y);
-    gm.x -= id * a.x;
-    gm.y -= id * a.y;
-    gm.z -= id * a.z;
-    // dL/da_unit = -id y, dL/dg = id;  a_unit = A/L, g = (L^2 + w_i - w_j)/(2L), A = p_j - p_i
-    const float3 ga = f3(-id * y.x, -id * y.y, -id * y.z);
-    const float gg = id;
+    const float3 ga = f3(-pid * y.x, -pid * y.y, -pid * y.z);
     const float pa = dot3(a, ga);
     const float iL = rcp_approx(L);
-    const float cg = gg * (1.0f - P.w * iL);
+    const float cg = pid * (1.0f - P.w * iL);
     const float3 dA = f3((ga.x - a.x * pa) * iL + cg * a.x, (ga.y - a.y * pa) * iL + cg * a.y,
                          (ga.z - a.z * pa) * iL + cg * a.z);
     v[G_P] -= dA.x;
     v[G_P + 1] -= dA.y;
     v[G_P + 2] -= dA.z;
-    v[G_W] += 0.5f * gg * iL;
+    v[G_W] += 0.5f * pid * iL;
     nbv[0] = dA.x;
     nbv[1] = dA.y;
     nbv[2] = dA.z;
-    nbv[3] = -0.5f * gg * iL;
-    nbj = J.x;
+    nbv[3] = -0.5f * pid * iL;
+    nbj = plane ? J.x : -1;
 }
 
 __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, int64_t n_tiles,
@@ -789,12 +785,23 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
                 hit = cell_segment<true>(cr, s_vr + j * VIEWREC_F, s_pl + o, np, A.w.planes_lo + (int64_t)cell * A.K,
                                          ray, sg, cand);
             if (!__any_sync(0xffffffffu, hit)) continue;
+            // Every lane runs the adjoint of this cell.  A lane without a hit
+            // runs it on neutral inputs (an empty segment with camera ends at
+            // the site, zero dL/dx and colour weight), so all its values are 0.
+            if (!hit) {
+                sg.sa = 0.f;
+                sg.sb = 0.f;
+                sg.ka = K_CAMERA;
+                sg.kb = K_CAMERA;
+                sg.dena = 1.f;
+                sg.denb = 1.f;
+                sg.q = f3(0.f, 0.f, 0.f);
+                sg.dnd = 1.f;
+            }
             float vv[32];
-#pragma unroll
-            for (int q = 0; q < 32; q++) vv[q] = 0.f;
-            float nba[4] = {0.f, 0.f, 0.f, 0.f}, nbb[4] = {0.f, 0.f, 0.f, 0.f};
-            int ja = -1, jb = -1;
-            if (hit) {
+            float nba[4], nbb[4];
+            int ja, jb;
+            {
                 Tex tx;
                 const float3 c = face_colour(cr, sg, ray, tx);
                 const float sig = cr[CR_SIG];
@@ -807,10 +814,10 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
                 // x = sigma l, alpha = 1 - e^-x:  dL/dx = g.(T_{k+1} c - S_k) - gT T_final
                 float dLdx = g.x * (Tafter * c.x - accC.x) + g.y * (Tafter * c.y - accC.y) +
                              g.z * (Tafter * c.z - accC.z) - gT * Tf;
-                if (xr > X_CAP) dLdx = 0.f;
+                if (xr > X_CAP || !hit) dLdx = 0.f;
                 vv[G_SIG] = dLdx * l;
                 const float gl = dLdx * sig;
-                const float wc = Tbefore * alpha;
+                const float wc = hit ? Tbefore * alpha : 0.0f;
                 const float3 gc = f3(wc * g.x, wc * g.y, wc * g.z);
                 // texture values and soft-Voronoi weights
                 float gW[4], sW = 0.f;
@@ -826,11 +833,9 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
 #pragma unroll
                 for (int k = 0; k < 4; k++) {
                     const float gr = -KAPPA * tx.W[k] * (gW[k] - sW);
-                    if (tx.r[k] > 0.f) {
-                        const float ir = gr * rcp_approx(tx.r[k]);
-                        gu1 = fmaf(ir, tx.ax[k & 1], gu1);
-                        gu2 = fmaf(ir, tx.ay[k >> 1], gu2);
-                    }
+                    const float ir = tx.r[k] > 0.f ? gr * rcp_approx(tx.r[k]) : 0.0f;
+                    gu1 = fmaf(ir, tx.ax[k & 1], gu1);
+                    gu2 = fmaf(ir, tx.ay[k >> 1], gu2);
                 }
                 // u = (e1.y, e2.y)/R with e/R stored:  dL/dy, dL/dR, dL/dn via the frame
                 const float3 E1 = f3(cr[CR_E1], cr[CR_E1 + 1], cr[CR_E1 + 2]);
@@ -838,7 +843,7 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
                 const float R = cr[CR_R];
                 const float3 gy = f3(gu1 * E1.x + gu2 * E2.x, gu1 * E1.y + gu2 * E2.y, gu1 * E1.z + gu2 * E2.z);
                 const float iR = rcp_approx(R);
-                vv[G_R] -= (gu1 * tx.u1 + gu2 * tx.u2) * iR;
+                vv[G_R] = -(gu1 * tx.u1 + gu2 * tx.u2) * iR;
                 {
                     // dL/de1 = gu1 y / R, dL/de2 = gu2 y / R (frame of Duff et al., JCGT 2017)
                     const float3 g1 = f3(gu1 * tx.ys.x * iR, gu1 * tx.ys.y * iR, gu1 * tx.ys.z * iR);
@@ -849,10 +854,15 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
                     const float da = ca * ca;
                     const float db0 = ny * ca, db1 = nx * ca, db2 = nx * ny * da;
                     // e1 = (1 + s x^2 a, s b, -s x), e2 = (b, s + y^2 a, -y), b = x y a
-                    vv[G_N] += g1.x * (2.f * sgn * nx * ca) + g1.y * sgn * db0 + g1.z * (-sgn) + g2.x * db0;
-                    vv[G_N + 1] += g1.y * sgn * db1 + g2.x * db1 + g2.y * (2.f * ny * ca) + g2.z * (-1.f);
-                    vv[G_N + 2] += g1.x * (sgn * nx * nx * da) + g1.y * sgn * db2 + g2.x * db2 + g2.y * (ny * ny * da);
+                    vv[G_N] = g1.x * (2.f * sgn * nx * ca) + g1.y * sgn * db0 + g1.z * (-sgn) + g2.x * db0;
+                    vv[G_N + 1] = g1.y * sgn * db1 + g2.x * db1 + g2.y * (2.f * ny * ca) + g2.z * (-1.f);
+                    vv[G_N + 2] = g1.x * (sgn * nx * nx * da) + g1.y * sgn * db2 + g2.x * db2 + g2.y * (ny * ny * da);
                 }
+                vv[G_P] = 0.f;
+                vv[G_P + 1] = 0.f;
+                vv[G_P + 2] = 0.f;
+                vv[G_W] = 0.f;
+                vv[G_OFF] = 0.f;
                 // the texture point moves with its segment end: y_s = m + t_s d
                 float3 gm = gy;
                 const float gts = dot3(gy, ray.dh);
@@ -870,32 +880,34 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
                 accC.x = fmaf(wc, c.x, accC.x);
                 accC.y = fmaf(wc, c.y, accC.y);
                 accC.z = fmaf(wc, c.z, accC.z);
-                Tafter = Tbefore;
+                if (hit) Tafter = Tbefore;
             }
             // neighbour gradients: fold into the warp sum when the warp agrees on j
             const unsigned ma = __ballot_sync(0xffffffffu, ja >= 0);
             const int ref_a = ma ? __shfl_sync(0xffffffffu, ja, __ffs(ma) - 1) : -1;
             const unsigned mb = __ballot_sync(0xffffffffu, jb >= 0);
             const int ref_b = mb ? __shfl_sync(0xffffffffu, jb, __ffs(mb) - 1) : -1;
-            if (ja >= 0 && ja != ref_a) {
+            const bool fold_a = ja >= 0 && ja == ref_a, fold_b = jb >= 0 && jb == ref_b;
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                vv[G_NB_A + q] = fold_a ? nba[q] : 0.f;
+                vv[G_NB_B + q] = fold_b ? nbb[q] : 0.f;
+            }
+            vv[30] = 0.f;
+            vv[31] = 0.f;
+            if (ja >= 0 && !fold_a) {
                 float *d = acc + (int64_t)ja * ACC_F;
                 atomicAdd(d + G_P, nba[0]);
                 atomicAdd(d + G_P + 1, nba[1]);
                 atomicAdd(d + G_P + 2, nba[2]);
                 atomicAdd(d + G_W, nba[3]);
-            } else if (ja >= 0) {
-#pragma unroll
-                for (int q = 0; q < 4; q++) vv[G_NB_A + q] = nba[q];
             }
-            if (jb >= 0 && jb != ref_b) {
+            if (jb >= 0 && !fold_b) {
                 float *d = acc + (int64_t)jb * ACC_F;
                 atomicAdd(d + G_P, nbb[0]);
                 atomicAdd(d + G_P + 1, nbb[1]);
                 atomicAdd(d + G_P + 2, nbb[2]);
                 atomicAdd(d + G_W, nbb[3]);
-            } else if (jb >= 0) {
-#pragma unroll
-                for (int q = 0; q < 4; q++) vv[G_NB_B + q] = nbb[q];
             }
             const float sum = warp_transpose_sum(vv, lane);
             if (lane < G_USED) {
