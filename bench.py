@@ -267,9 +267,12 @@ def run_ours(args):
     K, W = args.steps, args.warmup
     with ClockSampler(local) as clk:
         kt = []
+        r.record_hits(False)   # rendering only: nothing for a backward to replay
         ms_fwd = timed(fwd_step, K, W, kt)
         ms_render = float(np.mean([a.elapsed_time(b) for a, b in kt]))
+        r.record_hits(True)    # training: the forward records the hits the backward replays
         ms_train = timed(train_step, K, W)
+        r.record_hits(False)
     clocks = clk.summary()
 
     # end to end through the public API with host buffers: camera in, image out

@@ -111,6 +111,16 @@ pf_status pf_plan_pixels(const pf_plan *plan, uint64_t *pixels);
 /* Replace the cameras; resolutions must equal the plan's.  The new values
  * are read by the next pf_project on any stream. */
 pf_status pf_plan_set_cameras(pf_plan *plan, const pf_camera *cams, int32_t n_views);
+/* Hit recording (default on).  While on, pf_render_fwd also writes, for
+ * every pixel and every batch of 32 entries of its tile's list, a 32-bit
+ * mask of the entries whose segment was non-empty (4 bytes per pixel and
+ * batch, in the workspace); the next pf_render_bwd on the same bins then
+ * replays only those (cell, pixel) pairs instead of re-testing every listed
+ * cell.  Turn it off for forward-only rendering (it saves one store per
+ * warp and batch); the backward then re-tests.  The masks are dropped by
+ * pf_prepare, pf_project and pf_bin_sort, and not written by a forward that
+ * counts stats. */
+pf_status pf_plan_set_record_hits(pf_plan *plan, int32_t enable);
 /* Count work in the next forward passes (adds to the counters; 0 disables). */
 pf_status pf_plan_enable_stats(pf_plan *plan, int32_t enable);
 /* Read the counters, then reset them (synchronises `stream`). */
@@ -164,7 +174,10 @@ pf_status pf_render_fwd(const pf_scene *scene, pf_plan *plan, void *ws, float *r
  * Adjoint of pf_render_fwd for upstream dL/drgb [P,3] and dL/dT [P]
  * (dL_dT may be NULL for zero).  Replays each tile back to front from the
  * checkpoint (T, last) and ADDS dL/d(parameter) into `grad` (every pointer
- * non-NULL).  Requires the same plan/workspace state as the forward.
+ * non-NULL).  Requires the same plan/workspace state as the forward (the
+ * same scene, bins and views).  If the forward recorded hit masks on these
+ * bins (pf_plan_set_record_hits) only the recorded (cell, pixel) pairs are
+ * replayed; otherwise every listed cell is re-tested up to `last`.
  */
 pf_status pf_render_bwd(const pf_scene *scene, pf_plan *plan, void *ws, const float *dL_drgb, const float *dL_dT,
                         const float *T, const uint32_t *last, const pf_scene_grad *grad, void *stream);

@@ -104,9 +104,17 @@ class Renderer:
         if capacity is None:
             px = sum(c.width * c.height for c in cams)
             capacity = max(1 << 16, min(8 * n * len(cams) + px // 16, 0xE0000000))
-        self.plan = Plan(n, k, cams, capacity, device)
+        self._record = True
+        self._stats = False
+        self.plan = self._make_plan(n, k, cams, capacity)
         self.generation = 0
         self.n_instances = 0
+
+    def _make_plan(self, n, k, cams, capacity):
+        P = Plan(n, k, cams, capacity, self.device)
+        check(lib().pf_plan_set_record_hits(P.handle, 1 if self._record else 0), "pf_plan_set_record_hits")
+        check(lib().pf_plan_enable_stats(P.handle, 1 if self._stats else 0), "pf_plan_enable_stats")
+        return P
 
     @property
     def cams(self):
@@ -117,7 +125,7 @@ class Renderer:
         if [(c.width, c.height) for c in cams] == [(c.width, c.height) for c in self.plan.cams]:
             self.plan.set_cameras(cams)
         else:
-            self.plan = Plan(self.plan.n, self.plan.k, cams, self.plan.capacity, self.device)
+            self.plan = self._make_plan(self.plan.n, self.plan.k, cams, self.plan.capacity)
         self.generation += 1
 
     def bin(self, scene: DeviceScene, params: dict | None = None, sync: bool = True):
@@ -136,7 +144,7 @@ class Renderer:
             self.n_instances = int(n.value)
             if r == _lib.PF_ERR_CAPACITY:
                 cap = min(int(n.value * 1.25) + 1024, 0xE0000000)
-                self.plan = Plan(P.n, P.k, P.cams, cap, self.device)
+                self.plan = self._make_plan(P.n, P.k, P.cams, cap)
                 continue
             check(r, "pf_bin_sort")
             break
@@ -185,7 +193,13 @@ class Renderer:
         check(lib().pf_plan_read_stats(P.handle, P.ws_ptr, C.byref(s), _stream()), "pf_plan_read_stats")
         return {f: int(getattr(s, f)) for f, _ in _lib.Stats._fields_}
 
+    def record_hits(self, on: bool = True):
+        """Hit recording in the forward (default on); off for rendering only."""
+        self._record = bool(on)
+        check(lib().pf_plan_set_record_hits(self.plan.handle, 1 if on else 0), "pf_plan_set_record_hits")
+
     def enable_stats(self, on: bool = True):
+        self._stats = bool(on)
         check(lib().pf_plan_enable_stats(self.plan.handle, 1 if on else 0), "pf_plan_enable_stats")
 
     def read_bins(self):

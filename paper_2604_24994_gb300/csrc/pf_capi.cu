@@ -52,6 +52,7 @@ WS Plan::ws(void *base) const {
     w.sort_tmp_cell = (uint32_t *)(b + L.sort_tmp_cell);
     w.counters = (Counters *)(b + L.counters);
     w.acc = (float *)(b + L.acc);
+    w.hitmask = fwd_only ? nullptr : (uint32_t *)(b + L.hitmask);
     if (external_scene) {
         const SceneLayout S = make_scene_layout(n, k);
         char *sb = (char *)scene_ws;
@@ -169,6 +170,7 @@ void make_layout(Plan *p) {
     L.sort_tmp_cell = take(cap * 4);
     L.counters = take(sizeof(Counters));
     L.acc = take((p->fwd_only ? 0 : n) * ACC_F * 4);
+    L.hitmask = take(p->fwd_only ? 0 : (uint64_t)(TILE_PIX / 32) * mask_batches(*p) * 32 * 4);
     L.total = o;
 }
 
@@ -280,6 +282,12 @@ pf_status pf_plan_set_cameras(pf_plan *p, const pf_camera *cams, int32_t n_views
     return PF_OK;
 }
 
+pf_status pf_plan_set_record_hits(pf_plan *p, int32_t enable) {
+    if (!p) return PF_ERR_INVALID_ARG;
+    p->record_hits = enable != 0;
+    return PF_OK;
+}
+
 pf_status pf_plan_enable_stats(pf_plan *p, int32_t enable) {
     if (!p) return PF_ERR_INVALID_ARG;
     p->stats = enable ? 1 : 0;
@@ -312,6 +320,7 @@ pf_status pf_plan_read_stats(pf_plan *p, void *ws, pf_stats *out, void *stream) 
 pf_status pf_prepare(const pf_scene *scene, pf_plan *p, void *ws, void *stream) {
     g_err[0] = 0;
     if (!p || !ws || !scene_ok(scene, p)) return PF_ERR_INVALID_ARG;
+    p->masks_valid = false;
     WS w = p->ws(ws);
     return cuda_status(launch_prepare(*scene, *p, w, (cudaStream_t)stream), "pf_prepare");
 }
@@ -319,6 +328,7 @@ pf_status pf_prepare(const pf_scene *scene, pf_plan *p, void *ws, void *stream) 
 pf_status pf_project(const pf_scene *scene, pf_plan *p, void *ws, void *stream) {
     g_err[0] = 0;
     if (!p || !ws || !scene_ok(scene, p)) return PF_ERR_INVALID_ARG;
+    p->masks_valid = false;
     WS w = p->ws(ws);
     cudaStream_t st = (cudaStream_t)stream;
     pf_status s = cuda_status(
@@ -330,6 +340,7 @@ pf_status pf_project(const pf_scene *scene, pf_plan *p, void *ws, void *stream) 
 pf_status pf_bin_sort(pf_plan *p, void *ws, uint64_t *n_instances, void *stream) {
     g_err[0] = 0;
     if (!p || !ws) return PF_ERR_INVALID_ARG;
+    p->masks_valid = false;
     WS w = p->ws(ws);
     cudaStream_t st = (cudaStream_t)stream;
     pf_status s = cuda_status(launch_bin_sort(*p, w, st), "pf_bin_sort");
@@ -353,7 +364,11 @@ pf_status pf_render_fwd(const pf_scene *scene, pf_plan *p, void *ws, float *rgb,
     g_err[0] = 0;
     if (!p || !ws || !scene_ok(scene, p) || !rgb || !T || !last) return PF_ERR_INVALID_ARG;
     WS w = p->ws(ws);
-    return cuda_status(launch_render_fwd(*scene, *p, w, rgb, T, last, (cudaStream_t)stream), "pf_render_fwd");
+    const bool record = p->record_hits && !p->stats && w.hitmask != nullptr;
+    pf_status s =
+        cuda_status(launch_render_fwd(*scene, *p, w, rgb, T, last, record, (cudaStream_t)stream), "pf_render_fwd");
+    p->masks_valid = !s && record;
+    return s;
 }
 
 pf_status pf_render_bwd(const pf_scene *scene, pf_plan *p, void *ws, const float *dL_drgb, const float *dL_dT,
@@ -365,8 +380,9 @@ pf_status pf_render_bwd(const pf_scene *scene, pf_plan *p, void *ws, const float
         return PF_ERR_INVALID_ARG;
     }
     WS w = p->ws(ws);
-    return cuda_status(launch_render_bwd(*scene, *p, w, dL_drgb, dL_dT, T, last, *g, (cudaStream_t)stream),
-                       "pf_render_bwd");
+    return cuda_status(
+        launch_render_bwd(*scene, *p, w, dL_drgb, dL_dT, T, last, *g, p->masks_valid, (cudaStream_t)stream),
+        "pf_render_bwd");
 }
 
 pf_status pf_read_bins(pf_plan *p, void *ws, uint32_t *tile_start, uint32_t *cells, uint64_t *keys,

@@ -97,7 +97,7 @@ struct Counters {
 struct Layout {
     uint64_t views, cellrec, cellnp, planes, plane_nb, viewrec, rect, key, cnt, celloff, diff, tile_start,
         tile_cursor, tile_order, scan_tmp, inst_key, inst_cell, inst_sorted, sort_tmp_key, sort_tmp_cell, counters,
-        acc, planes_lo, total;
+        acc, planes_lo, hitmask, total;
     uint64_t scan_tmp_elems;
 };
 
@@ -128,6 +128,8 @@ struct WS {
     uint32_t *sort_tmp_cell;
     Counters *counters;
     float *acc;            // [N][32]
+    uint32_t *hitmask;     // [8][batch slots][32] per warp of a tile, batch of its list and
+                           // pixel: bit j set if the forward's segment in cell j was non-empty
 };
 
 struct Plan {
@@ -142,9 +144,17 @@ struct Plan {
     // (the server prepares a resident scene once); then L omits them.
     void *scene_ws = nullptr;
     bool external_scene = false;
-    bool fwd_only = false;   // omit the gradient accumulators
+    bool fwd_only = false;   // omit the gradient accumulators and hit masks
+    // hit masks in the workspace belong to the current bins: set by
+    // pf_render_fwd, cleared by anything that changes the bins
+    bool masks_valid = false;
+    bool record_hits = true;   // pf_plan_set_record_hits
     WS ws(void *base) const;
 };
+
+// Hit-mask batch slots per warp: every batch of every tile list gets one
+// (see hitmask_slot in the renderer).
+inline int64_t mask_batches(const Plan &p) { return (int64_t)(p.cap / BATCH) + p.total_tiles + 1; }
 
 // Offsets of the view-independent records in a scene-only buffer.
 struct SceneLayout {
@@ -167,9 +177,9 @@ cudaError_t launch_prepare(const pf_scene &s, const Plan &p, const WS &w, cudaSt
 cudaError_t launch_project(const pf_scene &s, const Plan &p, const WS &w, cudaStream_t st);
 cudaError_t launch_bin_sort(const Plan &p, const WS &w, cudaStream_t st);
 cudaError_t launch_render_fwd(const pf_scene &s, const Plan &p, const WS &w, float *rgb, float *T, uint32_t *last,
-                              cudaStream_t st);
+                              bool record, cudaStream_t st);
 cudaError_t launch_render_bwd(const pf_scene &s, const Plan &p, const WS &w, const float *dL_drgb,
                               const float *dL_dT, const float *T, const uint32_t *last, const pf_scene_grad &g,
-                              cudaStream_t st);
+                              bool use_masks, cudaStream_t st);
 
 }  // namespace pf

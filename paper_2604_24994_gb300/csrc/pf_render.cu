@@ -394,7 +394,17 @@ struct RenderArgs {
     WS w;
     int nv, n, K;
     unsigned long long cap;
+    int64_t mask_batches;   // batch slots per warp in the hit-mask array
 };
+
+// Hit masks: one 32-bit word per (warp of the tile, batch, pixel of the
+// warp).  Batch k of the tile whose list starts at instance s gets the
+// unique slot floor(s / 32) + tile + k (a list of n entries has at most
+// ceil(n / 32) batches, so consecutive tiles' slots never overlap).
+__device__ __forceinline__ int64_t hitmask_slot(const RenderArgs &A, int64_t tile, unsigned long long s, int k,
+                                                int warp) {
+    return ((int64_t)warp * A.mask_batches + (int64_t)(s / BATCH) + tile + k) * 32;
+}
 
 __device__ __forceinline__ void tile_pixel(const ViewDev &V, int64_t lt, int &px, int &py, int &wx, int &wy) {
     const int tx = (int)(lt % V.tiles_x), ty = (int)(lt / V.tiles_x);
@@ -463,14 +473,17 @@ __device__ __forceinline__ Stage make_stage(float4 *smem, int K, bool with_nb) {
 }
 
 // ---------------------------------------------------------------- forward
-template <bool STATS>
+// STATS: count work (see pf_stats); REC: record the hit masks the backward
+// replays (only with a hit-mask region in the workspace).
+template <bool STATS, bool REC>
 __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, int64_t n_tiles,
                                                                  float *__restrict__ rgb_out,
                                                                  float *__restrict__ T_out,
                                                                  uint32_t *__restrict__ last_out) {
     extern __shared__ float4 smem4[];
-    __shared__ int64_t s_q;
+    __shared__ int64_t s_q, s_slot;
     const Stage sg = make_stage(smem4, A.K, false);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned long long st_cand = 0, st_hit = 0, st_pl = 0, st_ref = 0, st_pass = 0;
     unsigned long long st_wcand = 0, st_wpass = 0, st_whit = 0;  // per warp (lane 0 counts)
     const bool overflow = A.w.counters->overflow != 0;
@@ -496,6 +509,7 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, i
     if (overflow) e = s;
     const int64_t vbase = (int64_t)v * A.n;
     const int n = (int)(e - s);
+    if (threadIdx.x == 0) s_slot = (int64_t)(s / BATCH) + tile;
     const int nbat = (n + BATCH - 1) / BATCH;
 
     float T = 1.0f;
@@ -517,6 +531,7 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, i
         __syncthreads();
         const int buf = k & 1, nb = min(BATCH, n - k * BATCH);
         unsigned mask = warp_mask(sg, buf, nb, cone);
+        unsigned my_hits = 0;  // bit j: this pixel's segment in cell j of the batch is non-empty
         while (mask) {
             const int j = __ffs(mask) - 1;
             mask &= mask - 1;
@@ -552,8 +567,11 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, i
             C.z = fmaf(wgt, c.z, C.z);
             T *= ex;
             last = (uint32_t)(k * BATCH + j + 1);
+            if (REC) my_hits |= 1u << j;
             if (T < T_EPS) done = true;
         }
+        // the backward replays only the (cell, pixel) pairs recorded here
+        if (REC) A.w.hitmask[((int64_t)(threadIdx.x >> 5) * A.mask_batches + s_slot + k) * 32 + (threadIdx.x & 31)] = my_hits;
     }
     cp_async_wait_all();  // a batch may still be in flight after an early exit
     if (inside) {
@@ -694,6 +712,9 @@ __device__ __forceinline__ void route_end(float gt, int kind, float s, float den
     nbj = plane ? J.x : -1;
 }
 
+// MASKS: replay only the (cell, lane) pairs the forward recorded as hits
+// (the hit masks of the current bins); otherwise re-test every listed cell.
+template <bool MASKS>
 __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, int64_t n_tiles,
                                                                  const float *__restrict__ dL_drgb,
                                                                  const float *__restrict__ dL_dT,
@@ -703,7 +724,7 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
     __shared__ int s_maxlast;
     __shared__ int64_t s_q;
     const Stage stg = make_stage(smem4, A.K, true);
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool overflow = A.w.counters->overflow != 0;
 
     for (;;) {
@@ -755,6 +776,8 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
         issue_batch(stg, (nbat - 1) & 1, list + (nbat - 1) * BATCH, maxlast - (nbat - 1) * BATCH, A.w, vbase, A.K,
                     true);
     for (int b = nbat - 1; b >= 0; b--) {
+        // bit j: the forward found this pixel's segment in cell j non-empty
+        const unsigned my_hits = MASKS ? A.w.hitmask[hitmask_slot(A, tile, s, b, warp) + lane] : 0u;
         __syncthreads();  // batch b+1, whose buffer batch b-1 reuses, is done
         if (b > 0) {
             issue_batch(stg, (b - 1) & 1, list + (b - 1) * BATCH, BATCH, A.w, vbase, A.K, true);
@@ -764,7 +787,7 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
         }
         __syncthreads();
         const int buf = b & 1, lo = b * BATCH, nb = min(BATCH, maxlast - lo);
-        unsigned mask = warp_mask(stg, buf, nb, cone);
+        unsigned mask = MASKS ? __reduce_or_sync(0xffffffffu, my_hits) : warp_mask(stg, buf, nb, cone);
         const float *s_cr = stg.cr(buf);
         const float *s_vr = stg.vr(buf);
         const float4 *s_pl = stg.pl(buf);
@@ -774,14 +797,15 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
             const int j = 31 - __clz(mask);
             mask &= ~(1u << j);
             const int idx = lo + j;
-            if (!__any_sync(0xffffffffu, idx < last)) continue;
+            const bool mine = MASKS ? ((my_hits >> j) & 1u) != 0 : idx < last;
+            if (!MASKS && !__any_sync(0xffffffffu, mine)) continue;
             const int cell = stg.ids(buf)[j];
             const float *cr = s_cr + j * CELLREC_F;
             const int o = poff[j], np = poff[j + 1] - o;
             Seg sg;
             bool cand;
             bool hit = false;
-            if (idx < last)
+            if (mine)
                 hit = cell_segment<true>(cr, s_vr + j * VIEWREC_F, s_pl + o, np, A.w.planes_lo + (int64_t)cell * A.K,
                                          ray, sg, cand);
             if (!__any_sync(0xffffffffu, hit)) continue;
@@ -968,6 +992,7 @@ static RenderArgs make_args(const pf_scene &s, const Plan &p, const WS &w) {
     A.n = p.n;
     A.K = p.k;
     A.cap = p.cap;
+    A.mask_batches = mask_batches(p);
     return A;
 }
 
@@ -987,27 +1012,22 @@ static size_t fwd_smem(int K) { return stage_bytes(K, false); }
 static size_t bwd_smem(int K) { return stage_bytes(K, true); }
 
 cudaError_t launch_render_fwd(const pf_scene &s, const Plan &p, const WS &w, float *rgb, float *T, uint32_t *last,
-                              cudaStream_t st) {
+                              bool record, cudaStream_t st) {
     if (p.total_tiles == 0) return cudaSuccess;
     RenderArgs A = make_args(s, p, w);
     const size_t smem = fwd_smem(p.k);
     cudaError_t e = cudaMemsetAsync(&w.counters->q_fwd, 0, sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
-    if (p.stats) {
-        auto k = render_fwd_kernel<true>;
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k<<<persistent_grid(k, smem, p.total_tiles), TILE_PIX, smem, st>>>(A, p.total_tiles, rgb, T, last);
-    } else {
-        auto k = render_fwd_kernel<false>;
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k<<<persistent_grid(k, smem, p.total_tiles), TILE_PIX, smem, st>>>(A, p.total_tiles, rgb, T, last);
-    }
+    auto k = p.stats ? render_fwd_kernel<true, false>
+                     : (record ? render_fwd_kernel<false, true> : render_fwd_kernel<false, false>);
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<persistent_grid(k, smem, p.total_tiles), TILE_PIX, smem, st>>>(A, p.total_tiles, rgb, T, last);
     return cudaGetLastError();
 }
 
 cudaError_t launch_render_bwd(const pf_scene &s, const Plan &p, const WS &w, const float *dL_drgb,
                               const float *dL_dT, const float *T, const uint32_t *last, const pf_scene_grad &g,
-                              cudaStream_t st) {
+                              bool use_masks, cudaStream_t st) {
     if (p.n == 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(w.acc, 0, sizeof(float) * ACC_F * (size_t)p.n, st);
     if (e != cudaSuccess) return e;
@@ -1016,9 +1036,10 @@ cudaError_t launch_render_bwd(const pf_scene &s, const Plan &p, const WS &w, con
         const size_t smem = bwd_smem(p.k);
         e = cudaMemsetAsync(&w.counters->q_bwd, 0, sizeof(unsigned int), st);
         if (e != cudaSuccess) return e;
-        cudaFuncSetAttribute(render_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        render_bwd_kernel<<<persistent_grid(render_bwd_kernel, smem, p.total_tiles), TILE_PIX, smem, st>>>(
-            A, p.total_tiles, dL_drgb, dL_dT, T, last);
+        auto kern = use_masks && w.hitmask ? render_bwd_kernel<true> : render_bwd_kernel<false>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kern<<<persistent_grid(kern, smem, p.total_tiles), TILE_PIX, smem, st>>>(A, p.total_tiles, dL_drgb, dL_dT, T,
+                                                                                 last);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     finalize_kernel<<<(p.n + 255) / 256, 256, 0, st>>>(p.n, w.acc, w.cellrec, g);

@@ -158,7 +158,7 @@ static cudaError_t enqueue_batch(Server &S, Slot &sl, const Plan &p) {
     cudaError_t e = cudaMemcpyAsync(w.views, sl.views_pinned, sizeof(ViewDev) * p.nv, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = launch_project(S.scene, p, w, st);
     if (e == cudaSuccess) e = launch_bin_sort(p, w, st);
-    if (e == cudaSuccess) e = launch_render_fwd(S.scene, p, w, nullptr, nullptr, nullptr, st);
+    if (e == cudaSuccess) e = launch_render_fwd(S.scene, p, w, nullptr, nullptr, nullptr, false, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(sl.ctr_pinned, w.counters, sizeof(Counters), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaLaunchHostFunc(st, batch_done, &sl);
     return e;

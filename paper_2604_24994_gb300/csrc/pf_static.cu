@@ -84,6 +84,7 @@ extern "C" pf_status pf_render_fwd_static(const pf_scene *scene, const pf_camera
     p.nv = 1;
     p.cap = PF_STATIC_MAX_INSTANCES;
     p.stats = 0;
+    p.fwd_only = true;
     p.views_host = &view_host;
     fill_views(&p, cam);
     make_layout(&p);
@@ -114,5 +115,5 @@ extern "C" pf_status pf_render_fwd_static(const pf_scene *scene, const pf_camera
                   (unsigned long long)c.total_inst, PF_STATIC_MAX_INSTANCES);
         return PF_ERR_CAPACITY;
     }
-    return cuda_status(launch_render_fwd(*scene, p, w, rgb, T, last, st), "pf_render_fwd_static: render");
+    return cuda_status(launch_render_fwd(*scene, p, w, rgb, T, last, false, st), "pf_render_fwd_static: render");
 }

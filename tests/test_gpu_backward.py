@@ -89,3 +89,39 @@ def test_autograd_function_matches_direct_backward(tiny):
     Go = oracle.Oracle(sc).render_grad(cam, gC, gT)
     G = {k: ds.params[k].grad.cpu().numpy().astype(np.float64) for k in PARAMS}
     check_grads(G, Go)
+
+
+def test_hit_mask_replay_matches_full_retest():
+    """The backward replays only the (cell, lane) pairs the forward recorded
+    as hits; once the bins are rebuilt (the recorded masks are dropped) it
+    re-tests every listed cell instead.  Both replays give the same
+    gradients up to the order of the atomic sums, and both match the oracle."""
+    import torch
+    from paper_2604_24994_gb300 import DeviceScene, Renderer
+    sc = inputs.capture_scene(20_000, seed=5, K=32)
+    cam = inputs.look_at((2.2, 0.4, 0.3), 96, 72)
+    ds = DeviceScene.from_numpy(sc, "cuda")
+    r = Renderer(ds.n, ds.k, [cam])
+    rgb, T, last = r.forward(ds)
+    rng = np.random.default_rng(3)
+    gC = torch.from_numpy(rng.normal(size=(cam.n_pixels, 3))).float().cuda()
+    gT = torch.from_numpy(rng.normal(size=cam.n_pixels)).float().cuda()
+    g_mask = r.backward(ds, gC, gT, T, last)
+    r.bin(ds)  # same scene and view: identical bins, but no recorded hits
+    g_full = r.backward(ds, gC, gT, T, last)
+    r.record_hits(False)  # a forward that records nothing: the backward re-tests
+    rgb2, T2, last2 = r.render_fwd(ds)
+    g_off = r.backward(ds, gC, gT, T2, last2)
+    torch.cuda.synchronize()
+    assert torch.equal(rgb, rgb2) and torch.equal(T, T2) and torch.equal(last, last2)
+    for k in PARAMS:
+        a = g_mask[k].double().cpu().numpy()
+        for other in (g_full, g_off):
+            b = other[k].double().cpu().numpy()
+            assert rel_l2(a, b) < 1e-5, (k, rel_l2(a, b))
+    # the oracle's adjoint of the same image (sampled pixels would not do:
+    # the gradients are sums over every pixel)
+    orc = oracle.Oracle(sc)
+    orc.prune_for(cam)
+    Go = orc.render_grad(cam, gC.cpu().numpy().astype(np.float64), gT.cpu().numpy().astype(np.float64))
+    check_grads({k: v.double().cpu().numpy() for k, v in g_mask.items()}, Go)
