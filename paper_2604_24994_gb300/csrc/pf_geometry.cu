@@ -15,7 +15,9 @@ namespace pf {
 // stored normalised, (a/|a|, g/|a|), so g/|a| is the signed distance of
 // the plane from p_i.  A plane at distance >= R_i never reaches the ball
 // and is dropped (Sec. 3.2: it cannot cut the cell); one at distance
-// < -R_i excludes the whole ball and marks the cell empty.
+// < -R_i excludes the whole ball and marks the cell empty.  Planes whose
+// facet is shown empty by a single other plane or the dipole face are
+// dropped as well (drop_implied_planes).
 // ---------------------------------------------------------------------------
 // FP64 1/sqrt(x): float estimate refined by two Newton steps (relative
 // error ~1e-15; avoids the FP64 divide and square root sequences).
@@ -24,6 +26,47 @@ __device__ __forceinline__ double rsqrt64(double x) {
     r = r * (1.5 - 0.5 * x * r * r);
     r = r * (1.5 - 0.5 * x * r * r);
     return r;
+}
+
+// Drop the planes that another constraint implies inside the ball B (radius
+// R about p_i).  Plane k's disk B.(plane k) lies entirely outside the
+// half-space H_j of a witness j (a plane or the dipole's dense half) when
+//   min over the disk of a_j.y - g_j = g_k (a_j.a_k) - rho_k |a_j x a_k| - g_j > 0,
+// rho_k = sqrt(R^2 - g_k^2).  Then the convex set B n H_j misses plane k, so
+// it lies on one side of it; the point y = -R a_j of B n H_j shows which:
+// if a_k.y < g_k, B n H_j is inside H_k and plane k changes no segment.
+// Both tests keep a margin of 1e-5 R above the float error.  Witnesses are
+// the planes still kept (earlier survivors, later ones not yet examined), so
+// a dropped plane is always implied through a chain ending at a kept one.
+// Planes are compacted in place; returns the new count.
+__device__ int drop_implied_planes(float4 *__restrict__ P, float4 *__restrict__ PL, int2 *__restrict__ NB, int cnt,
+                                   float4 face, float R) {
+    const float tol = 1e-5f * R;
+    int kept = 0;
+    for (int k = 0; k < cnt; k++) {
+        const float4 ak = P[k];
+        const float rho = sqrtf(fmaxf(R * R - ak.w * ak.w, 0.0f));
+        bool implied = false;
+        for (int j = -1; j < cnt && !implied; j++) {
+            if (j >= kept && j <= k) continue;   // slots [kept, k) are vacated, k is the plane itself
+            const float4 aj = j < 0 ? face : P[j];
+            const float c = ak.x * aj.x + ak.y * aj.y + ak.z * aj.z;
+            // sin of the angle from the cross product (accurate for near-parallel normals)
+            const float cx = ak.y * aj.z - ak.z * aj.y, cy = ak.z * aj.x - ak.x * aj.z, cz = ak.x * aj.y - ak.y * aj.x;
+            const float sn = sqrtf(cx * cx + cy * cy + cz * cz);
+            const float gap = ak.w * c - rho * sn - aj.w;
+            implied = gap > tol && -R * c < ak.w - tol;
+        }
+        if (!implied) {
+            if (kept != k) {
+                P[kept] = ak;
+                PL[kept] = PL[k];
+                NB[kept] = NB[k];
+            }
+            kept++;
+        }
+    }
+    return kept;
 }
 
 __global__ void __launch_bounds__(256) prepare_kernel(pf_scene s, float *__restrict__ cellrec,
@@ -89,6 +132,8 @@ __global__ void __launch_bounds__(256) prepare_kernel(pf_scene s, float *__restr
             cnt++;
         }
     }
+    if (!empty) cnt = drop_implied_planes(planes + (int64_t)i * K, planes_lo + (int64_t)i * K,
+                                          plane_nb + (int64_t)i * K, cnt, make_float4(nx, ny, nz, s.offset[i]), Rf);
     cellnp[i] = cnt;
     float4 *cr = reinterpret_cast<float4 *>(cellrec + (int64_t)i * CELLREC_F);
     cr[0] = make_float4(nx, ny, nz, s.offset[i]);

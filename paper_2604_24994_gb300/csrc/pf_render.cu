@@ -148,10 +148,18 @@ __device__ __noinline__ float face_side64(const float *cr, Ray ray) {
 // gradients need D to more digits than the forward's value does.
 constexpr float GRAD_D = 1e-3f;
 
+// The ray against the cell's bounding sphere: the cheap candidate test
+// (cand), then the exact chord in the closest-approach frame.
+struct Chord {
+    float3 q;      // closest-approach offset from p_i (x - p_i = q + s d)
+    float sq;      // half chord: the sphere spans s in [-sq, sq]
+    float b;       // s of the camera (the segment starts at s >= b)
+    int refined;   // D recomputed in FP64
+};
+
 template <bool GRAD>
-__device__ __forceinline__ bool cell_segment(const float *__restrict__ cr, const float *__restrict__ vr,
-                                             const float4 *__restrict__ pl, int np,
-                                             const float4 *__restrict__ lo_glob, Ray ray, Seg &sg, bool &cand) {
+__device__ __forceinline__ bool sphere_chord(const float *__restrict__ cr, const float *__restrict__ vr,
+                                             const Ray &ray, Chord &ch, bool &cand) {
     const float4 V0 = reinterpret_cast<const float4 *>(vr)[0];
     const float3 mh = f3(V0.x, V0.y, V0.z);
     const float3 v0 = cross3(mh, ray.dh);
@@ -164,24 +172,37 @@ __device__ __forceinline__ bool cell_segment(const float *__restrict__ cr, const
                         cross_c(mh.z, ml.z, dh.x, dl.x, mh.x, ml.x, dh.z, dl.z),
                         cross_c(mh.x, ml.x, dh.y, dl.y, mh.y, ml.y, dh.x, dl.x));
     const float R = cr[CR_R];
-    const float sig = cr[CR_SIG];
     float D = fmaf(R, R, -dot3(v, v));
-    sg.refined = 0;
+    ch.refined = 0;
     // near-tangent sphere: decide and measure D in FP64
     if (fabsf(D) < (GRAD ? fmaxf(V1.w, GRAD_D * R * R) : V1.w)) {
         D = refine_D64(vr, R, ray);
-        sg.refined = 1;
+        ch.refined = 1;
     }
     if (!(D > 0.0f)) return false;
-    const float sq = sqrt_approx(D);
-    const float3 q = cross3(dh, v);
-    const float b = dot3(mh, dh);
-    float sa = -sq, sb = sq;
+    ch.sq = sqrt_approx(D);
+    ch.q = cross3(dh, v);
+    ch.b = dot3(mh, dh);
+    return true;
+}
+
+// Clip the chord with the cell's radical planes pl[0..np), the dipole face,
+// then refine near-parallel ends.  False if the segment is empty.
+template <bool GRAD>
+__device__ __forceinline__ bool clip_chord(const float *__restrict__ cr, const float *__restrict__ vr,
+                                           const float4 *__restrict__ pl, int np,
+                                           const float4 *__restrict__ lo_glob, const Ray &ray, const Chord &ch,
+                                           Seg &sg) {
+    const float3 dh = ray.dh, q = ch.q;
+    const float R = cr[CR_R];
+    const float sig = cr[CR_SIG];
+    float sa = -ch.sq, sb = ch.sq;
     int ka = K_SPHERE, kb = K_SPHERE;
-    if (b > sa) {
-        sa = b;
+    if (ch.b > sa) {
+        sa = ch.b;
         ka = K_CAMERA;
     }
+    sg.refined = ch.refined;
     // Radical planes, branch free: a plane bounds s from below when d.a < 0
     // (sign bit, so -0 counts as below) and from above otherwise.  With
     // d.a = +-0 the quotient is +-inf or NaN: it moves no end unless num < 0
@@ -536,24 +557,33 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, i
             const int j = __ffs(mask) - 1;
             mask &= mask - 1;
             if (__all_sync(0xffffffffu, done)) break;
-            if (done) continue;
-            const int cell = sg.ids(buf)[j];
             const float *cr = sg.cr(buf) + j * CELLREC_F;
+            const float *vr = sg.vr(buf) + j * VIEWREC_F;
+            Chord ch;
+            bool cand = false, pass = false;
+            if (!done) pass = sphere_chord<false>(cr, vr, ray, ch, cand);
+            const unsigned pm = __ballot_sync(0xffffffffu, pass);
+            bool hit = false;
             Seg seg;
-            bool cand;
-            const int o = sg.poff(buf)[j], np = sg.poff(buf)[j + 1] - o;
-            const bool hit = cell_segment<false>(cr, sg.vr(buf) + j * VIEWREC_F, sg.pl(buf) + o, np,
-                                                 A.w.planes_lo + (int64_t)cell * A.K, ray, seg, cand);
-            if (STATS) {
+            int np = 0;
+            if (pm) {
+                const int o = sg.poff(buf)[j];
+                np = sg.poff(buf)[j + 1] - o;
+                if (pass)
+                    hit = clip_chord<false>(cr, vr, sg.pl(buf) + o, np, A.w.planes_lo + (int64_t)sg.ids(buf)[j] * A.K,
+                                            ray, ch, seg);
+            }
+            if (STATS && !done) {
+                const unsigned act = __ballot_sync(__activemask(), true);
+                const bool l0 = lane == __ffs(act) - 1;
+                const unsigned cm = __ballot_sync(act, cand), hm = __ballot_sync(act, hit);
                 st_cand++;
                 st_pass += cand;
-                st_pl += cand ? np : 0;
-                st_ref += cand ? seg.refined : 0;
+                st_pl += pass ? np : 0;
+                st_ref += pass ? (hit ? seg.refined : ch.refined) : 0;
                 st_hit += hit;
-                const bool l0 = (threadIdx.x & 31) == __ffs(__activemask()) - 1;
-                const unsigned pm = __ballot_sync(__activemask(), cand), hm = __ballot_sync(__activemask(), hit);
                 st_wcand += l0;
-                st_wpass += l0 && pm;
+                st_wpass += l0 && cm;
                 st_whit += l0 && hm;
             }
             if (!hit) continue;
@@ -801,13 +831,14 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
             if (!MASKS && !__any_sync(0xffffffffu, mine)) continue;
             const int cell = stg.ids(buf)[j];
             const float *cr = s_cr + j * CELLREC_F;
+            const float *vr = s_vr + j * VIEWREC_F;
             const int o = poff[j], np = poff[j + 1] - o;
             Seg sg;
+            Chord ch;
             bool cand;
             bool hit = false;
-            if (mine)
-                hit = cell_segment<true>(cr, s_vr + j * VIEWREC_F, s_pl + o, np, A.w.planes_lo + (int64_t)cell * A.K,
-                                         ray, sg, cand);
+            if (mine && sphere_chord<true>(cr, vr, ray, ch, cand))
+                hit = clip_chord<true>(cr, vr, s_pl + o, np, A.w.planes_lo + (int64_t)cell * A.K, ray, ch, sg);
             if (!__any_sync(0xffffffffu, hit)) continue;
             // Every lane runs the adjoint of this cell.  A lane without a hit
             // runs it on neutral inputs (an empty segment with camera ends at
