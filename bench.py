@@ -44,6 +44,34 @@ FLOPS_PER_HIT = 92              # face point (6), face coordinates (10), site of
                                 # normalise (5), colour (24), compositing (15)
 
 
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "render_fwd_dram_1080p_1M.md")
+TRAFFIC_SOURCES = ("paper_2604_24994_gb300/csrc/pf_render.cu", "paper_2604_24994_gb300/csrc/pf_internal.cuh",
+                   "include/powerfoam.h")
+
+
+def render_source_digest():
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic():
+    """DRAM bytes (read + write) of one render_fwd_kernel launch on this
+    workload from the committed ncu summary, or None when the kernel's
+    sources changed since those counters were taken."""
+    try:
+        txt = open(TRAFFIC_PROFILE).read()
+    except OSError:
+        return None
+    fields = dict(line.split(":", 1) for line in txt.splitlines() if line.startswith(("source_sha256:", "dram_bytes_per_launch:")))
+    if fields.get("source_sha256", "").strip() != render_source_digest():
+        return None
+    return int(fields["dram_bytes_per_launch"].strip())
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -318,7 +346,8 @@ def run_ours(args):
         "ms_render_fwd_kernel": ms_render,
         "work": stats,
         "roofline": {"bound": "alu", "kernel": "render_fwd_kernel", "achieved": achieved, "peak": peak_tflops,
-                     "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+                     "traffic": measured_traffic() if args.workload == "full" else None,
                      "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz (unit counts and max clock)"},
         "e2e": {"value": ws * 1000.0 / ms_e2e, "unit": UNIT, "h2d_bytes_per_step": 184,
                 "d2h_bytes_per_step": r.plan.pixels * 16},
