@@ -63,9 +63,18 @@ __device__ int drop_implied_planes(float4 *__restrict__ P, float4 *__restrict__ 
     return kept;
 }
 
-__global__ void __launch_bounds__(256) prepare_kernel(pf_scene s, float *__restrict__ cellrec,
-                                                      int32_t *__restrict__ cellnp, float4 *__restrict__ planes,
-                                                      float4 *__restrict__ planes_lo, int2 *__restrict__ plane_nb) {
+// (p, w) of every cell in one 16-byte word, so that each neighbour gather
+// in prepare_kernel is a single load.
+__global__ void __launch_bounds__(256) pack_sites_kernel(pf_scene s, float4 *__restrict__ pw) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s.n_cells) return;
+    pw[i] = make_float4(s.pos[3 * i], s.pos[3 * i + 1], s.pos[3 * i + 2], s.w[i]);
+}
+
+__global__ void __launch_bounds__(256) prepare_kernel(pf_scene s, const float4 *__restrict__ pw,
+                                                      float *__restrict__ cellrec, int32_t *__restrict__ cellnp,
+                                                      float4 *__restrict__ planes, float4 *__restrict__ planes_lo,
+                                                      int2 *__restrict__ plane_nb) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.n_cells) return;
     const int K = s.k_nbr;
@@ -93,8 +102,9 @@ __global__ void __launch_bounds__(256) prepare_kernel(pf_scene s, float *__restr
     for (int k = 0; k < K; k++) {
         const int j = s.nbr[(int64_t)i * K + k];
         if (j < 0 || j >= s.n_cells || j == i) continue;
-        const float qx = s.pos[3 * j], qy = s.pos[3 * j + 1], qz = s.pos[3 * j + 2];
-        const float wjf = s.w[j];
+        const float4 pj = pw[j];
+        const float qx = pj.x, qy = pj.y, qz = pj.z;
+        const float wjf = pj.w;
         // float pre-test with a wide margin: only planes that may reach the
         // ball (distance (|a|^2 + w_i - w_j) / (2|a|) < R) go on
         {
@@ -259,7 +269,8 @@ cudaError_t launch_prepare(const pf_scene &s, const Plan &p, const WS &w, cudaSt
     if (p.n == 0) return cudaSuccess;
     const int threads = 256;
     const int blocks = (p.n + threads - 1) / threads;
-    prepare_kernel<<<blocks, threads, 0, st>>>(s, w.cellrec, w.cellnp, w.planes, w.planes_lo, w.plane_nb);
+    pack_sites_kernel<<<blocks, threads, 0, st>>>(s, w.pw);
+    prepare_kernel<<<blocks, threads, 0, st>>>(s, w.pw, w.cellrec, w.cellnp, w.planes, w.planes_lo, w.plane_nb);
     return cudaGetLastError();
 }
 
