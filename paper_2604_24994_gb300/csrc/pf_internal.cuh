@@ -97,7 +97,7 @@ struct Counters {
 struct Layout {
     uint64_t views, cellrec, cellnp, planes, plane_nb, viewrec, rect, key, cnt, celloff, diff, tile_start,
         tile_cursor, tile_order, scan_tmp, inst_key, inst_cell, inst_sorted, sort_tmp_key, sort_tmp_cell, counters,
-        acc, planes_lo, hitmask, pw, total;
+        acc, planes_lo, hitmask, hitkind, pw, total;
     uint64_t scan_tmp_elems;
 };
 
@@ -129,6 +129,8 @@ struct WS {
     Counters *counters;
     float *acc;            // [N][32]
     float4 *pw;            // [N] (p, w) packed for prepare's neighbour gathers (scratch)
+    uint16_t *hitkind;     // [8][batch slots][32 cells][32 pixels]: the active constraints
+                           // (entry, exit) of each recorded hit, 7 bits each, kind + 3
     uint32_t *hitmask;     // [8][batch slots][32] per warp of a tile, batch of its list and
                            // pixel: bit j set if the forward's segment in cell j was non-empty
 };

@@ -274,6 +274,61 @@ __device__ __forceinline__ bool clip_chord(const float *__restrict__ cr, const f
     return true;
 }
 
+// The segment of a recorded hit from its active constraints (ka, kb): the
+// same float expressions as clip_chord for those two constraints and the
+// face, then the same refinement, so the ends equal the forward's.
+template <bool GRAD>
+__device__ __forceinline__ bool segment_from_kinds(const float *__restrict__ cr, const float *__restrict__ vr,
+                                                   const float4 *__restrict__ pl,
+                                                   const float4 *__restrict__ lo_glob, const Ray &ray,
+                                                   const Chord &ch, int ka, int kb, Seg &sg) {
+    const float3 dh = ray.dh, q = ch.q;
+    const float R = cr[CR_R];
+    const float sig = cr[CR_SIG];
+    sg.refined = ch.refined;
+    const float3 n = f3(cr[CR_N], cr[CR_N + 1], cr[CR_N + 2]);
+    const float fnum = cr[CR_OFF] - dot3(q, n);
+    const float fden = dot3(dh, n);
+    const float tf = fnum * rcp_approx(fden);
+    sg.dnd = fden;
+    if (fabsf(fden) < 0x1p-20f) sg.dnd = face_side64(cr, ray);
+    const float4 Pa = pl[max(ka, 0)], Pb = pl[max(kb, 0)];
+    const float dpa = dot3(dh, f3(Pa.x, Pa.y, Pa.z)), dpb = dot3(dh, f3(Pb.x, Pb.y, Pb.z));
+    const float tpa = (Pa.w - dot3(q, f3(Pa.x, Pa.y, Pa.z))) * rcp_approx(dpa);
+    const float tpb = (Pb.w - dot3(q, f3(Pb.x, Pb.y, Pb.z))) * rcp_approx(dpb);
+    float sa = ka >= 0 ? tpa : (ka == K_FACE ? tf : (ka == K_CAMERA ? ch.b : -ch.sq));
+    float sb = kb >= 0 ? tpb : (kb == K_FACE ? tf : ch.sq);
+    const float dena = ka >= 0 ? dpa : (ka == K_FACE ? fden : CUDART_INF_F);
+    const float denb = kb >= 0 ? dpb : (kb == K_FACE ? fden : CUDART_INF_F);
+    if (!(sb > sa)) return false;
+    // near-parallel plane or face at an end: recompute that end in FP64
+    const float lim = PLANE_ERR * sig * (1.0f / REFINE_EPS);
+    const bool ra = fabsf(dena) < lim * (R + fabsf(sa)), rb = fabsf(denb) < lim * (R + fabsf(sb));
+    if (ra || rb) {
+        if (ra) {
+            sa = ka >= 0 ? refine_plane64(vr, pl[ka], lo_glob[ka], ray, sa)
+                         : refine_plane64(vr, make_float4(cr[CR_N], cr[CR_N + 1], cr[CR_N + 2], cr[CR_OFF]),
+                                          make_float4(cr[CR_NLO], cr[CR_NLO + 1], cr[CR_NLO + 2], 0.f), ray, sa);
+            sg.refined++;
+        }
+        if (rb) {
+            sb = kb >= 0 ? refine_plane64(vr, pl[kb], lo_glob[kb], ray, sb)
+                         : refine_plane64(vr, make_float4(cr[CR_N], cr[CR_N + 1], cr[CR_N + 2], cr[CR_OFF]),
+                                          make_float4(cr[CR_NLO], cr[CR_NLO + 1], cr[CR_NLO + 2], 0.f), ray, sb);
+            sg.refined++;
+        }
+    }
+    if (!(sb > sa)) return false;
+    sg.sa = sa;
+    sg.sb = sb;
+    sg.ka = ka;
+    sg.kb = kb;
+    sg.dena = dena;
+    sg.denb = denb;
+    sg.q = q;
+    return true;
+}
+
 // Soft-Voronoi face colour (Eq. svrad): weights of the four sites at the
 // texture point y = q + s d (the dense segment's end on the face side).
 struct Tex {
@@ -587,6 +642,9 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, i
                 st_whit += l0 && hm;
             }
             if (!hit) continue;
+            if (REC)
+                A.w.hitkind[(((int64_t)warp * A.mask_batches + s_slot + k) * 32 + j) * 32 + lane] =
+                    (uint16_t)((seg.ka + 3) | ((seg.kb + 3) << 7));
             Tex tx;
             const float3 c = face_colour(cr, seg, ray, tx);
             const float x = fminf(cr[CR_SIG] * (seg.sb - seg.sa), X_CAP);
@@ -837,8 +895,16 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
             Chord ch;
             bool cand;
             bool hit = false;
-            if (mine && sphere_chord<true>(cr, vr, ray, ch, cand))
+            if (MASKS) {
+                // the forward recorded this hit's active constraints: no plane loop
+                unsigned kk = 0;
+                if (mine) kk = A.w.hitkind[(hitmask_slot(A, tile, s, b, warp) + j) * 32 + lane];
+                if (mine && sphere_chord<true>(cr, vr, ray, ch, cand))
+                    hit = segment_from_kinds<true>(cr, vr, s_pl + o, A.w.planes_lo + (int64_t)cell * A.K, ray, ch,
+                                                   (int)(kk & 127u) - 3, (int)(kk >> 7) - 3, sg);
+            } else if (mine && sphere_chord<true>(cr, vr, ray, ch, cand)) {
                 hit = clip_chord<true>(cr, vr, s_pl + o, np, A.w.planes_lo + (int64_t)cell * A.K, ray, ch, sg);
+            }
             if (!__any_sync(0xffffffffu, hit)) continue;
             // Every lane runs the adjoint of this cell.  A lane without a hit
             // runs it on neutral inputs (an empty segment with camera ends at
