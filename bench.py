@@ -144,11 +144,12 @@ def make_workload(rank: int = 0, small: bool = False):
     at 400k cells and 1280x720 for profiler captures."""
     from paper_2604_24994_gb300 import inputs
     t0 = time.time()
+    from paper_2604_24994_gb300.dataparallel import ring_view
     sc = inputs.capture_scene(400_000 if small else 1_000_000, seed=0, K=32)
-    cam = inputs.capture_camera(1280, 720) if small else inputs.capture_camera()
+    w, h = (1280, 720) if small else (1920, 1080)
+    cam = inputs.capture_camera(w, h)
     if rank:  # every rank renders its own view of the same scene
-        ang = 2 * math.pi * rank / 8
-        cam = inputs.look_at((3 * math.cos(ang), 3 * math.sin(ang), 0.0), 1920, 1080)
+        cam = ring_view(rank, w, h)
     return sc, cam, time.time() - t0
 
 
@@ -213,6 +214,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2604_24994_gb300 import DeviceScene, Renderer, build
+    from paper_2604_24994_gb300.dataparallel import sum_gradients
     build.build()
 
     sc, cam, gen_s = make_workload(rank, small=args.workload == "small")
@@ -263,8 +265,7 @@ def run_ours(args):
         g = 2.0 * (c - target)
         r.backward(ds, g, None, t, l, grads=grads)
         if ws > 1:  # data parallel over views: sum the per-view gradients (the one exchange step)
-            for v in grads.values():
-                torch.distributed.all_reduce(v)
+            sum_gradients(grads)
         return g
 
     grads = {k: torch.zeros_like(v) for k, v in ds.params.items()}
