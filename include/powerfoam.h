@@ -127,9 +127,8 @@ pf_status pf_plan_enable_stats(pf_plan *plan, int32_t enable);
 pf_status pf_plan_read_stats(pf_plan *plan, void *ws, pf_stats *out, void *stream);
 
 /*
- * View-independent cell records (Sec. 3.2-3.4).  For every cell, in
- * float-float (about 46 bits): the unit normal and face frame, and the
- * radical planes
+ * View-independent cell records (Sec. 3.2-3.4).  For every cell, in FP64:
+ * the unit normal and face frame, and the radical planes
  *   x.(p_j - p_i) <= (|p_j|^2 - |p_i|^2 + w_i - w_j) / 2
  * of its listed neighbours (the definition of pow gives +w_i - w_j; the
  * appendix's Eq. power_bisector prints the weights the other way round),

@@ -1,4 +1,4 @@
-// pf_prepare / pf_project kernels: float-float geometry per cell, FP64 per (view, cell).
+// pf_prepare / pf_project kernels: FP64 geometry per cell and per (view, cell).
 #include <math_constants.h>
 
 #include "pf_internal.cuh"
@@ -8,8 +8,7 @@ namespace pf {
 // ---------------------------------------------------------------------------
 // View-independent cell records.
 //
-// Per cell, in float-float (about 46 bits; FP64 runs at 1/64 of the FP32
-// rate on GB300): unit normal, face frame (e1, e2) / R, and the radical
+// Per cell, in FP64: unit normal, face frame (e1, e2) / R, and the radical
 // planes of the listed neighbours, each stored as float + low part.  The
 // plane between i and j is
 //   (x - p_i).a <= g,  a = p_j - p_i,  g = (|a|^2 + w_i - w_j) / 2
@@ -21,6 +20,15 @@ namespace pf {
 // facet is shown empty by a single other plane or the dipole face are
 // dropped as well (drop_implied_planes).
 // ---------------------------------------------------------------------------
+
+// FP64 1/sqrt(x): float estimate refined by two Newton steps (relative
+// error ~1e-15; avoids the FP64 divide and square root sequences).
+__device__ __forceinline__ double rsqrt64(double x) {
+    double r = (double)rsqrtf((float)x);
+    r = r * (1.5 - 0.5 * x * r * r);
+    r = r * (1.5 - 0.5 * x * r * r);
+    return r;
+}
 
 // Drop the planes that another constraint implies inside the ball B (radius
 // R about p_i).  Plane k's disk B.(plane k) lies entirely outside the
@@ -79,14 +87,16 @@ __global__ void __launch_bounds__(256) prepare_kernel(pf_scene s, const float4 *
     if (i >= s.n_cells) return;
     const int K = s.k_nbr;
     const float pxf = s.pos[3 * i], pyf = s.pos[3 * i + 1], pzf = s.pos[3 * i + 2];
+    const double px = pxf, py = pyf, pz = pzf;
     const float wif = s.w[i];
+    const double wi = wif;
     const float Rf = s.R[i];
-    // unit normal in float-float: n / |n| with 1/|n| from ff_rsqrt
-    const float nx0 = s.normal[3 * i], ny0 = s.normal[3 * i + 1], nz0 = s.normal[3 * i + 2];
-    const ff n2 = ff_sumsq3(ff{nx0, 0.f}, ff{ny0, 0.f}, ff{nz0, 0.f});
-    const ff inl = n2.h > 0.0f ? ff_rsqrt(n2) : ff{0.f, 0.f};
-    const ff nxd = ff_mul(inl, ff{nx0, 0.f}), nyd = ff_mul(inl, ff{ny0, 0.f}), nzd = ff_mul(inl, ff{nz0, 0.f});
-    const float nx = nxd.h, ny = nyd.h, nz = nzd.h;
+    const double R = Rf;
+    const double nx0 = s.normal[3 * i], ny0 = s.normal[3 * i + 1], nz0 = s.normal[3 * i + 2];
+    const double n2 = nx0 * nx0 + ny0 * ny0 + nz0 * nz0;
+    const double inl = n2 > 0.0 ? rsqrt64(n2) : 0.0;
+    const double nxd = nx0 * inl, nyd = ny0 * inl, nzd = nz0 * inl;
+    const float nx = (float)nxd, ny = (float)nyd, nz = (float)nzd;
     // orthonormal face frame from the unit normal, branchless construction of
     // Duff et al. (JCGT 2017); divided by R so that u = (e1.y, e2.y) / R
     const float sg = nz >= 0.0f ? 1.0f : -1.0f;
@@ -96,8 +106,7 @@ __global__ void __launch_bounds__(256) prepare_kernel(pf_scene s, const float4 *
     const float e1x = (1.0f + sg * nx * nx * ca) * iR, e1y = sg * cb * iR, e1z = -sg * nx * iR;
     const float e2x = cb * iR, e2y = (sg + ny * ny * ca) * iR, e2z = -ny * iR;
 
-    bool empty = !(Rf > 0.0f) || !(n2.h > 0.0f);
-    const float Rhi = Rf * (1.0f + 1e-6f);
+    bool empty = !(R > 0.0) || !(n2 > 0.0);
     int cnt = 0;
     for (int k = 0; k < K; k++) {
         const int j = s.nbr[(int64_t)i * K + k];
@@ -106,7 +115,7 @@ __global__ void __launch_bounds__(256) prepare_kernel(pf_scene s, const float4 *
         const float qx = pj.x, qy = pj.y, qz = pj.z;
         const float wjf = pj.w;
         // float pre-test with a wide margin: only planes that may reach the
-        // ball (distance (|a|^2 + w_i - w_j) / (2|a|) < R) go on
+        // ball (distance (|a|^2 + w_i - w_j) / (2|a|) < R) go on to FP64
         {
             const float ax = qx - pxf, ay = qy - pyf, az = qz - pzf;
             const float L2 = ax * ax + ay * ay + az * az;
@@ -115,24 +124,23 @@ __global__ void __launch_bounds__(256) prepare_kernel(pf_scene s, const float4 *
             const float Lf = sqrtf(L2);
             if (L2 > 0.0f && num > 2.0f * Lf * Rf * 1.001f + 1e-4f * mag) continue;
         }
-        // a = p_j - p_i exactly as float pairs, then |a|^2, 1/|a| and the
-        // plane distance g = (|a|^2 + w_i - w_j) / (2|a|) in float-float
-        const ff ax = two_sum(qx, -pxf), ay = two_sum(qy, -pyf), az = two_sum(qz, -pzf);
-        const ff L2 = ff_sumsq3(ax, ay, az);
-        if (L2.h == 0.0f) {  // coincident sites: pow(x,i) <= pow(x,j) iff w_i >= w_j
-            if (wif < wjf) empty = true;
+        const double ax = (double)qx - px, ay = (double)qy - py, az = (double)qz - pz;
+        const double wj = wjf;
+        const double L2 = ax * ax + ay * ay + az * az;
+        if (L2 == 0.0) {  // coincident sites: pow(x,i) <= pow(x,j) iff w_i >= w_j
+            if (wi < wj) empty = true;
             continue;
         }
-        const ff iL = ff_rsqrt(L2);
-        ff g = ff_mul(ff_add(L2, two_sum(wif, -wjf)), iL);
-        g.h *= 0.5f;
-        g.l *= 0.5f;
-        if (g.h < -Rhi) empty = true;
-        if (g.h < Rhi) {
-            const ff ux = ff_mul(ax, iL), uy = ff_mul(ay, iL), uz = ff_mul(az, iL);
-            planes[(int64_t)i * K + cnt] = make_float4(ux.h, uy.h, uz.h, g.h);
-            planes_lo[(int64_t)i * K + cnt] = make_float4(ux.l, uy.l, uz.l, g.l);
-            plane_nb[(int64_t)i * K + cnt] = make_int2(j, __float_as_int(ff_mul(L2, iL).h));
+        const double iL = rsqrt64(L2);
+        const double g = 0.5 * (L2 + wi - wj) * iL;  // plane distance from p_i
+        if (g < -R * (1.0 + 1e-6)) empty = true;
+        if (g < R * (1.0 + 1e-6)) {
+            const double ux = ax * iL, uy = ay * iL, uz = az * iL;
+            const float4 hi = make_float4((float)ux, (float)uy, (float)uz, (float)g);
+            planes[(int64_t)i * K + cnt] = hi;
+            planes_lo[(int64_t)i * K + cnt] = make_float4((float)(ux - (double)hi.x), (float)(uy - (double)hi.y),
+                                                          (float)(uz - (double)hi.z), (float)(g - (double)hi.w));
+            plane_nb[(int64_t)i * K + cnt] = make_int2(j, __float_as_int((float)(L2 * iL)));
             cnt++;
         }
     }
@@ -148,7 +156,8 @@ __global__ void __launch_bounds__(256) prepare_kernel(pf_scene s, const float4 *
     cr[4] = tx[0];
     cr[5] = tx[1];
     cr[6] = tx[2];
-    cr[7] = make_float4(nxd.l, nyd.l, nzd.l, ff_mul(n2, inl).h);
+    cr[7] = make_float4((float)(nxd - (double)nx), (float)(nyd - (double)ny), (float)(nzd - (double)nz),
+                        (float)(n2 * inl));
 }
 
 // ---------------------------------------------------------------------------

@@ -155,52 +155,6 @@ struct Plan {
     WS ws(void *base) const;
 };
 
-// ---- float-float arithmetic (device): a value is hi + lo with |lo| <=
-// ulp(hi)/2, about 46-48 significant bits on the FP32 pipe.  The error-free
-// transformations are Knuth's TwoSum and the FMA form of Dekker's
-// TwoProduct; the _rn intrinsics keep the compiler from contracting them.
-struct ff {
-    float h, l;
-};
-__device__ __forceinline__ ff two_prod(float a, float b) {
-    const float p = __fmul_rn(a, b);
-    return {p, fmaf(a, b, -p)};
-}
-__device__ __forceinline__ ff two_sum(float a, float b) {
-    const float s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
-}
-__device__ __forceinline__ ff ff_add(ff a, ff b) {
-    const ff s = two_sum(a.h, b.h);
-    return two_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
-}
-__device__ __forceinline__ ff ff_mul(ff a, ff b) {
-    const ff p = two_prod(a.h, b.h);
-    return two_sum(p.h, fmaf(a.h, b.l, fmaf(a.l, b.h, p.l)));
-}
-// a^2 + b^2 + c^2 of floats, exact products
-__device__ __forceinline__ ff ff_sumsq3(ff a, ff b, ff c) {
-    const ff x = two_prod(a.h, a.h), y = two_prod(b.h, b.h), z = two_prod(c.h, c.h);
-    ff s = ff_add(ff_add(x, y), z);
-    // first-order low-part terms 2 (a.h a.l + b.h b.l + c.h c.l)
-    const float t = 2.0f * fmaf(a.h, a.l, fmaf(b.h, b.l, __fmul_rn(c.h, c.l)));
-    return two_sum(s.h, __fadd_rn(s.l, t));
-}
-// 1/sqrt(x), x > 0: the float estimate, then two Newton steps r += r (1 - x r^2) / 2
-// in float-float (the residual 1 - x r^2 is small, so its float part suffices)
-__device__ __forceinline__ ff ff_rsqrt(ff x) {
-    ff r = {rsqrtf(x.h), 0.0f};
-#pragma unroll
-    for (int it = 0; it < 2; it++) {
-        const ff xr2 = ff_mul(x, ff_mul(r, r));
-        const float e = __fsub_rn(__fsub_rn(1.0f, xr2.h), xr2.l);
-        const ff c = two_prod(r.h, __fmul_rn(0.5f, e));
-        r = ff_add(r, c);
-    }
-    return r;
-}
-
 // Hit-mask batch slots per warp: every batch of every tile list gets one
 // (see hitmask_slot in the renderer).
 inline int64_t mask_batches(const Plan &p) { return (int64_t)(p.cap / BATCH) + p.total_tiles + 1; }
