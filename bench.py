@@ -449,6 +449,75 @@ def serve_bench(args, local: int):
     return out
 
 
+def run_large(args):
+    """The large differentiable workload: 5M cells (capture recipe), 48
+    neighbours, four 3840x2160 views on a ring, forward+backward with the
+    per-pixel (T, last) checkpoint.  Times the step with the forward's hit
+    records (the default) and with the checkpoint alone (recording off: the
+    backward re-tests every listed cell), reports peak device memory, the
+    bytes of the hit records, and what storing every segment instead of
+    replaying would need.  Prints one JSON line (not the benchmark line)."""
+    import torch
+    from paper_2604_24994_gb300 import DeviceScene, Renderer, build, inputs
+    from paper_2604_24994_gb300.dataparallel import ring_view
+    build.build()
+    t0 = time.time()
+    sc = inputs.capture_scene(5_000_000, seed=0, K=48)
+    gen_s = time.time() - t0
+    cams = [ring_view(v, 3840, 2160, radius=3.0, n_ring=4) for v in range(4)]
+    ds = DeviceScene.from_numpy(sc, "cuda")
+    del sc
+    r = Renderer(ds.n, ds.k, cams)
+    r.bin(ds, sync=True)
+    r.enable_stats(True)
+    r.render_fwd(ds)
+    stats = r.stats()
+    r.enable_stats(False)
+    px = r.plan.pixels
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    target = torch.rand((px, 3), device="cuda", generator=gen)
+    rgb = torch.empty((px, 3), device="cuda")
+    T = torch.empty(px, device="cuda")
+    last = torch.empty(px, dtype=torch.int32, device="cuda")
+    grads = {k: torch.zeros_like(v) for k, v in ds.params.items()}
+    stream = torch.cuda.current_stream()
+
+    def step():
+        r.bin(ds, sync=False)
+        c, t, l = r.render_fwd(ds, out=(rgb, T, last))
+        r.backward(ds, 2.0 * (c - target), None, t, l, grads=grads)
+
+    out = {}
+    for name, rec in (("checkpoint+hit_records", True), ("checkpoint_only", False)):
+        r.record_hits(rec)
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        torch.cuda.reset_peak_memory_stats()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            step()
+        b.record(stream)
+        b.synchronize()
+        out[name] = {"ms_fwd_bwd": a.elapsed_time(b) / args.steps,
+                     "peak_allocated_gb": torch.cuda.max_memory_allocated() / 1e9}
+    # bytes of the hit records in the workspace (8 warps x batch slots x 32 pixels x (4 + 32 x 2) B)
+    P = r.plan
+    tiles = sum(((c.width + 15) // 16) * ((c.height + 15) // 16) for c in cams)
+    slots = P.capacity // 32 + tiles + 1
+    hit_rec_gb = 8 * slots * 32 * (4 + 64) / 1e9
+    hits = stats["hits"]
+    line = {"workload": "5,000,000 cells (capture recipe), 48 neighbours, 4 views 3840x2160 on a ring of radius 3",
+            "pixels": px, "instances": stats["instances"], "hits": hits, "hits_per_pixel": hits / px,
+            "workspace_gb": P.ws_bytes / 1e9, "hit_records_gb": hit_rec_gb,
+            "checkpoint_bytes_per_pixel": 8,
+            "no_checkpoint_estimate_gb": hits * 32 / 1e9,
+            "no_checkpoint_note": "every hit's (T before, colour, entry, exit, kinds, cell) at 32 B instead of replaying",
+            "steps": args.steps, "warmup": args.warmup, "scene_generation_s": round(gen_s, 1), **out}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -456,7 +525,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="full", choices=["full", "small"])
+    ap.add_argument("--workload", default="full", choices=["full", "small", "large"])
     ap.add_argument("--serve-seconds", type=float, default=20.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-budget-gb", type=float, default=40.0)
@@ -464,6 +533,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "large":
+        run_large(args)
     else:
         run_ours(args)
 

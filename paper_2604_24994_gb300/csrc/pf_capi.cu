@@ -54,6 +54,7 @@ WS Plan::ws(void *base) const {
     w.acc = (float *)(b + L.acc);
     w.hitmask = fwd_only ? nullptr : (uint32_t *)(b + L.hitmask);
     w.hitkind = fwd_only ? nullptr : (uint16_t *)(b + L.hitkind);
+    w.hitcount = fwd_only ? nullptr : (uint32_t *)(b + L.hitcount);
     w.pw = (float4 *)(b + L.pw);
     if (external_scene) {
         const SceneLayout S = make_scene_layout(n, k);
@@ -173,7 +174,8 @@ void make_layout(Plan *p) {
     L.counters = take(sizeof(Counters));
     L.acc = take((p->fwd_only ? 0 : n) * ACC_F * 4);
     L.hitmask = take(p->fwd_only ? 0 : (uint64_t)(TILE_PIX / 32) * mask_batches(*p) * 32 * 4);
-    L.hitkind = take(p->fwd_only ? 0 : (uint64_t)(TILE_PIX / 32) * mask_batches(*p) * 32 * 32 * 2);
+    L.hitkind = take(p->fwd_only ? 0 : (uint64_t)p->total_pixels * HIT_CAP * 2);
+    L.hitcount = take(p->fwd_only ? 0 : (uint64_t)p->total_pixels * 4);
     L.pw = take(n * 16);
     L.total = o;
 }

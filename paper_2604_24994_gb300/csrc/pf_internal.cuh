@@ -16,6 +16,7 @@ constexpr int MAX_K = 64;              // neighbour list width limit
 constexpr int CELLREC_F = 32;          // floats per view-independent cell record
 constexpr int VIEWREC_F = 8;           // floats per (view, cell) record: m hi, Rt^2, m lo, D threshold
 constexpr int ACC_F = 32;              // gradient accumulator floats per cell
+constexpr int HIT_CAP = 256;           // recorded hits per pixel (later ones are re-clipped)
 constexpr float T_EPS = 1e-6f;         // forward stops once T drops below this
 constexpr float X_CAP = 60.0f;         // sigma * l is capped (alpha = 1 - e^-60)
 constexpr float KAPPA = 6.0f;          // soft-Voronoi sharpness, units of 1/R
@@ -97,7 +98,7 @@ struct Counters {
 struct Layout {
     uint64_t views, cellrec, cellnp, planes, plane_nb, viewrec, rect, key, cnt, celloff, diff, tile_start,
         tile_cursor, tile_order, scan_tmp, inst_key, inst_cell, inst_sorted, sort_tmp_key, sort_tmp_cell, counters,
-        acc, planes_lo, hitmask, hitkind, pw, total;
+        acc, planes_lo, hitmask, hitkind, hitcount, pw, total;
     uint64_t scan_tmp_elems;
 };
 
@@ -129,8 +130,9 @@ struct WS {
     Counters *counters;
     float *acc;            // [N][32]
     float4 *pw;            // [N] (p, w) packed for prepare's neighbour gathers (scratch)
-    uint16_t *hitkind;     // [8][batch slots][32 cells][32 pixels]: the active constraints
-                           // (entry, exit) of each recorded hit, 7 bits each, kind + 3
+    uint16_t *hitkind;     // [pixels][HIT_CAP]: active constraints (entry, exit) of the pixel's
+                           // first HIT_CAP hits in list order, 7 bits each, kind + 3
+    uint32_t *hitcount;    // [pixels] hits the forward composited
     uint32_t *hitmask;     // [8][batch slots][32] per warp of a tile, batch of its list and
                            // pixel: bit j set if the forward's segment in cell j was non-empty
 };

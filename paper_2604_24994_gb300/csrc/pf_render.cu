@@ -107,7 +107,9 @@ __device__ __forceinline__ double rcp64(double x) {
 }
 
 // A plane (or the face) end: s = (g - q.a) / (d.a); `fallback` if d.a == 0.
-__device__ __noinline__ float refine_plane64(const float *vr, float4 hi, float4 lo, Ray ray, float fallback) {
+// `den` receives d.a in FP64, rounded once (the adjoint divides by it).
+__device__ __noinline__ float refine_plane64(const float *vr, float4 hi, float4 lo, Ray ray, float fallback,
+                                             float &den_out) {
     const double dx = (double)ray.dh.x + (double)ray.dl.x, dy = (double)ray.dh.y + (double)ray.dl.y,
                  dz = (double)ray.dh.z + (double)ray.dl.z;
     const double mx = (double)vr[0] + (double)vr[4], my = (double)vr[1] + (double)vr[5],
@@ -118,6 +120,7 @@ __device__ __noinline__ float refine_plane64(const float *vr, float4 hi, float4 
     const double g = (double)hi.w + (double)lo.w;
     const double num = g - (qx * ax + qy * ay + qz * az);
     const double den = dx * ax + dy * ay + dz * az;
+    den_out = (float)den;
     if (den == 0.0) return fallback;
     return (float)(num * rcp64(den));
 }
@@ -145,8 +148,11 @@ __device__ __noinline__ float face_side64(const float *cr, Ray ray) {
 // pl: the cell's planes, nb: their neighbour ids (global, for refinement).
 // GRAD (the backward) also recomputes D in FP64 whenever D < GRAD_D R^2:
 // the sphere end's derivatives scale with 1/sqrt(D), so near-tangent
-// gradients need D to more digits than the forward's value does.
+// gradients need D to more digits than the forward's value does.  For the
+// same reason it recomputes a plane or face end, and takes its d.a from
+// FP64, whenever |d.a| < GRAD_DEN (the end's derivatives scale with 1/(d.a)).
 constexpr float GRAD_D = 1e-3f;
+constexpr float GRAD_DEN = 2e-3f;
 
 // The ray against the cell's bounding sphere: the cheap candidate test
 // (cand), then the exact chord in the closest-approach frame.
@@ -248,18 +254,25 @@ __device__ __forceinline__ bool clip_chord(const float *__restrict__ cr, const f
     if (!(sb > sa)) return false;
     // near-parallel plane or face at an end: recompute that end in FP64
     const float lim = PLANE_ERR * sig * (1.0f / REFINE_EPS);
-    const bool ra = fabsf(dena) < lim * (R + fabsf(sa)), rb = fabsf(denb) < lim * (R + fabsf(sb));
+    // the adjoint divides by d.a: the backward also recomputes every end with
+    // |d.a| < GRAD_DEN, so that 1/(d.a) has a relative error below ~1e-4
+    const bool ra = fabsf(dena) < (GRAD ? fmaxf(lim * (R + fabsf(sa)), GRAD_DEN) : lim * (R + fabsf(sa)));
+    const bool rb = fabsf(denb) < (GRAD ? fmaxf(lim * (R + fabsf(sb)), GRAD_DEN) : lim * (R + fabsf(sb)));
     if (ra || rb) {
+        // and takes d.a from FP64 at the ends it recomputes
+        float d64;
         if (ra) {
-            sa = ka >= 0 ? refine_plane64(vr, pl[ka], lo_glob[ka], ray, sa)
+            sa = ka >= 0 ? refine_plane64(vr, pl[ka], lo_glob[ka], ray, sa, d64)
                          : refine_plane64(vr, make_float4(cr[CR_N], cr[CR_N + 1], cr[CR_N + 2], cr[CR_OFF]),
-                                          make_float4(cr[CR_NLO], cr[CR_NLO + 1], cr[CR_NLO + 2], 0.f), ray, sa);
+                                          make_float4(cr[CR_NLO], cr[CR_NLO + 1], cr[CR_NLO + 2], 0.f), ray, sa, d64);
+            if (GRAD) dena = d64;
             sg.refined++;
         }
         if (rb) {
-            sb = kb >= 0 ? refine_plane64(vr, pl[kb], lo_glob[kb], ray, sb)
+            sb = kb >= 0 ? refine_plane64(vr, pl[kb], lo_glob[kb], ray, sb, d64)
                          : refine_plane64(vr, make_float4(cr[CR_N], cr[CR_N + 1], cr[CR_N + 2], cr[CR_OFF]),
-                                          make_float4(cr[CR_NLO], cr[CR_NLO + 1], cr[CR_NLO + 2], 0.f), ray, sb);
+                                          make_float4(cr[CR_NLO], cr[CR_NLO + 1], cr[CR_NLO + 2], 0.f), ray, sb, d64);
+            if (GRAD) denb = d64;
             sg.refined++;
         }
     }
@@ -298,23 +311,30 @@ __device__ __forceinline__ bool segment_from_kinds(const float *__restrict__ cr,
     const float tpb = (Pb.w - dot3(q, f3(Pb.x, Pb.y, Pb.z))) * rcp_approx(dpb);
     float sa = ka >= 0 ? tpa : (ka == K_FACE ? tf : (ka == K_CAMERA ? ch.b : -ch.sq));
     float sb = kb >= 0 ? tpb : (kb == K_FACE ? tf : ch.sq);
-    const float dena = ka >= 0 ? dpa : (ka == K_FACE ? fden : CUDART_INF_F);
-    const float denb = kb >= 0 ? dpb : (kb == K_FACE ? fden : CUDART_INF_F);
+    float dena = ka >= 0 ? dpa : (ka == K_FACE ? fden : CUDART_INF_F);
+    float denb = kb >= 0 ? dpb : (kb == K_FACE ? fden : CUDART_INF_F);
     if (!(sb > sa)) return false;
     // near-parallel plane or face at an end: recompute that end in FP64
     const float lim = PLANE_ERR * sig * (1.0f / REFINE_EPS);
-    const bool ra = fabsf(dena) < lim * (R + fabsf(sa)), rb = fabsf(denb) < lim * (R + fabsf(sb));
+    // the adjoint divides by d.a: the backward also recomputes every end with
+    // |d.a| < GRAD_DEN, so that 1/(d.a) has a relative error below ~1e-4
+    const bool ra = fabsf(dena) < (GRAD ? fmaxf(lim * (R + fabsf(sa)), GRAD_DEN) : lim * (R + fabsf(sa)));
+    const bool rb = fabsf(denb) < (GRAD ? fmaxf(lim * (R + fabsf(sb)), GRAD_DEN) : lim * (R + fabsf(sb)));
     if (ra || rb) {
+        // and takes d.a from FP64 at the ends it recomputes
+        float d64;
         if (ra) {
-            sa = ka >= 0 ? refine_plane64(vr, pl[ka], lo_glob[ka], ray, sa)
+            sa = ka >= 0 ? refine_plane64(vr, pl[ka], lo_glob[ka], ray, sa, d64)
                          : refine_plane64(vr, make_float4(cr[CR_N], cr[CR_N + 1], cr[CR_N + 2], cr[CR_OFF]),
-                                          make_float4(cr[CR_NLO], cr[CR_NLO + 1], cr[CR_NLO + 2], 0.f), ray, sa);
+                                          make_float4(cr[CR_NLO], cr[CR_NLO + 1], cr[CR_NLO + 2], 0.f), ray, sa, d64);
+            if (GRAD) dena = d64;
             sg.refined++;
         }
         if (rb) {
-            sb = kb >= 0 ? refine_plane64(vr, pl[kb], lo_glob[kb], ray, sb)
+            sb = kb >= 0 ? refine_plane64(vr, pl[kb], lo_glob[kb], ray, sb, d64)
                          : refine_plane64(vr, make_float4(cr[CR_N], cr[CR_N + 1], cr[CR_N + 2], cr[CR_OFF]),
-                                          make_float4(cr[CR_NLO], cr[CR_NLO + 1], cr[CR_NLO + 2], 0.f), ray, sb);
+                                          make_float4(cr[CR_NLO], cr[CR_NLO + 1], cr[CR_NLO + 2], 0.f), ray, sb, d64);
+            if (GRAD) denb = d64;
             sg.refined++;
         }
     }
@@ -559,7 +579,7 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, i
     extern __shared__ float4 smem4[];
     __shared__ int64_t s_q, s_slot;
     const Stage sg = make_stage(smem4, A.K, false);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     unsigned long long st_cand = 0, st_hit = 0, st_pl = 0, st_ref = 0, st_pass = 0;
     unsigned long long st_wcand = 0, st_wpass = 0, st_whit = 0;  // per warp (lane 0 counts)
     const bool overflow = A.w.counters->overflow != 0;
@@ -591,6 +611,7 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, i
     float T = 1.0f;
     float3 C = f3(0.f, 0.f, 0.f);
     uint32_t last = 0;
+    int nhit = 0;  // hits so far (hit recording)
     bool done = !inside;
 
     if (nbat > 0) issue_batch(sg, 0, A.w.inst_sorted + s, min(BATCH, n), A.w, vbase, A.K, false);
@@ -642,9 +663,12 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, i
                 st_whit += l0 && hm;
             }
             if (!hit) continue;
-            if (REC)
-                A.w.hitkind[(((int64_t)warp * A.mask_batches + s_slot + k) * 32 + j) * 32 + lane] =
-                    (uint16_t)((seg.ka + 3) | ((seg.kb + 3) << 7));
+            if (REC) {
+                if (nhit < HIT_CAP)
+                    A.w.hitkind[(V.pix_base + (int64_t)py * V.width + px) * HIT_CAP + nhit] =
+                        (uint16_t)((seg.ka + 3) | ((seg.kb + 3) << 7));
+                nhit++;
+            }
             Tex tx;
             const float3 c = face_colour(cr, seg, ray, tx);
             const float x = fminf(cr[CR_SIG] * (seg.sb - seg.sa), X_CAP);
@@ -677,6 +701,7 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, i
             rgb_out[3 * pix + 2] = C.z;
             T_out[pix] = T;
             last_out[pix] = last;
+            if (REC) A.w.hitcount[pix] = (uint32_t)nhit;
         }
     }
     }  // tile queue
@@ -840,13 +865,15 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
     float3 g = f3(0.f, 0.f, 0.f);
     float gT = 0.f, Tf = 1.f;
     int last = 0;
+    int nrec = 0;  // the forward's hit count; hits are met in reverse order
+    const int64_t pix = inside ? V.pix_base + (int64_t)py * V.width + px : 0;
     if (inside) {
-        const int64_t pix = V.pix_base + (int64_t)py * V.width + px;
         g = f3(dL_drgb[3 * pix], dL_drgb[3 * pix + 1], dL_drgb[3 * pix + 2]);
         gT = dL_dT ? dL_dT[pix] : 0.f;
         Tf = T_in[pix];
         last = (int)last_in[pix];
         if ((unsigned long long)last > e - s) last = (int)(e - s);
+        if (MASKS) nrec = (int)A.w.hitcount[pix];
     }
     atomicMax(&s_maxlast, last);
     __syncthreads();
@@ -897,11 +924,16 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
             bool hit = false;
             if (MASKS) {
                 // the forward recorded this hit's active constraints: no plane loop
-                unsigned kk = 0;
-                if (mine) kk = A.w.hitkind[(hitmask_slot(A, tile, s, b, warp) + j) * 32 + lane];
-                if (mine && sphere_chord<true>(cr, vr, ray, ch, cand))
-                    hit = segment_from_kinds<true>(cr, vr, s_pl + o, A.w.planes_lo + (int64_t)cell * A.K, ray, ch,
-                                                   (int)(kk & 127u) - 3, (int)(kk >> 7) - 3, sg);
+                unsigned kk = 0xffffu;
+                if (mine && --nrec < HIT_CAP) kk = A.w.hitkind[pix * HIT_CAP + nrec];
+                if (mine && sphere_chord<true>(cr, vr, ray, ch, cand)) {
+                    if (kk != 0xffffu)
+                        hit = segment_from_kinds<true>(cr, vr, s_pl + o, A.w.planes_lo + (int64_t)cell * A.K, ray,
+                                                       ch, (int)(kk & 127u) - 3, (int)(kk >> 7) - 3, sg);
+                    else  // beyond the recorded hits of this pixel: clip against every plane
+                        hit = clip_chord<true>(cr, vr, s_pl + o, np, A.w.planes_lo + (int64_t)cell * A.K, ray, ch,
+                                               sg);
+                }
             } else if (mine && sphere_chord<true>(cr, vr, ray, ch, cand)) {
                 hit = clip_chord<true>(cr, vr, s_pl + o, np, A.w.planes_lo + (int64_t)cell * A.K, ray, ch, sg);
             }

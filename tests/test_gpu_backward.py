@@ -125,3 +125,47 @@ def test_hit_mask_replay_matches_full_retest():
     orc.prune_for(cam)
     Go = orc.render_grad(cam, gC.cpu().numpy().astype(np.float64), gT.cpu().numpy().astype(np.float64))
     check_grads({k: v.double().cpu().numpy() for k, v in g_mask.items()}, Go)
+
+
+def test_replay_beyond_the_recorded_hits_per_pixel():
+    """A chain of 300 faint cells along the view axis gives every ray more
+    hits than the forward records per pixel (HIT_CAP = 256); the backward
+    re-clips the later ones.  Same gradients as a backward with no recorded
+    hits at all, and as the oracle."""
+    import torch
+    from paper_2604_24994_gb300 import DeviceScene, Renderer
+    n = 300
+    x = np.linspace(-3.0, 3.0, n)
+    pos = np.stack([x, 0.001 * np.sin(7 * x), 0.001 * np.cos(5 * x)], 1)
+    spacing = 6.0 / (n - 1)
+    r = np.full(n, 0.6 * spacing)
+    w = r ** 2
+    R = np.full(n, 40 * spacing)            # balls much wider than the slabs
+    nbr, R, _ = inputs.build_neighbours(pos, w, R, 16)
+    rng = np.random.default_rng(4)
+    normal = rng.normal(size=(n, 3))
+    sc = inputs.Scene(pos=pos.astype(np.float32), w=w.astype(np.float32), R=R.astype(np.float32),
+                      sigma=np.full(n, 0.1, np.float32), rgb=rng.uniform(size=(n, 3)).astype(np.float32),
+                      normal=normal.astype(np.float32), offset=np.full(n, 0.5 * spacing, np.float32),
+                      tex=rng.normal(0, 0.1, size=(n, 12)).astype(np.float32), nbr=nbr)
+    cam = inputs.look_at((4.0, 0.0, 0.0), 24, 16, fov_y_deg=0.1)
+    ds = DeviceScene.from_numpy(sc, "cuda")
+    rd = Renderer(ds.n, ds.k, [cam])
+    rd.enable_stats(True)
+    rgb, T, last = rd.forward(ds)
+    st = rd.stats()
+    rd.enable_stats(False)
+    assert st["hits"] / cam.n_pixels > 280          # well past the recorded 256 per pixel
+    rgb, T, last = rd.forward(ds)                  # a forward that records hits
+    gC = torch.from_numpy(rng.normal(size=(cam.n_pixels, 3))).float().cuda()
+    gT = torch.from_numpy(rng.normal(size=cam.n_pixels)).float().cuda()
+    g_rec = rd.backward(ds, gC, gT, T, last)
+    rd.record_hits(False)
+    rgb2, T2, last2 = rd.render_fwd(ds)
+    g_off = rd.backward(ds, gC, gT, T2, last2)
+    torch.cuda.synchronize()
+    for k in PARAMS:
+        a, b = g_rec[k].double().cpu().numpy(), g_off[k].double().cpu().numpy()
+        assert rel_l2(a, b) < 1e-5, (k, rel_l2(a, b))
+    Go = oracle.Oracle(sc).render_grad(cam, gC.cpu().numpy().astype(np.float64), gT.cpu().numpy().astype(np.float64))
+    check_grads({k: v.double().cpu().numpy() for k, v in g_rec.items()}, Go)
