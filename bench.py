@@ -452,10 +452,10 @@ def serve_bench(args, local: int):
 def run_large(args):
     """The large differentiable workload: 5M cells (capture recipe), 48
     neighbours, four 3840x2160 views on a ring, forward+backward with the
-    per-pixel (T, last) checkpoint.  Times the step with the forward's hit
-    records (the default) and with the checkpoint alone (recording off: the
-    backward re-tests every listed cell), reports peak device memory, the
-    bytes of the hit records, and what storing every segment instead of
+    per-pixel (T, last) checkpoint.  Times the step and reports peak device
+    memory for the default plan (checkpoint + the forward's hit records) and
+    for a plan laid out without hit records (checkpoint only: the backward
+    re-tests every listed cell), plus what storing every segment instead of
     replaying would need.  Prints one JSON line (not the benchmark line)."""
     import torch
     from paper_2604_24994_gb300 import DeviceScene, Renderer, build, inputs
@@ -467,33 +467,38 @@ def run_large(args):
     cams = [ring_view(v, 3840, 2160, radius=3.0, n_ring=4) for v in range(4)]
     ds = DeviceScene.from_numpy(sc, "cuda")
     del sc
-    r = Renderer(ds.n, ds.k, cams)
+    # size the instance capacity once, then lay plans out at that size
+    r = Renderer(ds.n, ds.k, cams, hit_records=False)
     r.bin(ds, sync=True)
+    cap = int(r.n_instances * 1.02) + 4096
     r.enable_stats(True)
     r.render_fwd(ds)
     stats = r.stats()
-    r.enable_stats(False)
-    px = r.plan.pixels
+    del r
+    torch.cuda.empty_cache()
+    px = sum(c.width * c.height for c in cams)
     gen = torch.Generator(device="cuda").manual_seed(0)
     target = torch.rand((px, 3), device="cuda", generator=gen)
-    rgb = torch.empty((px, 3), device="cuda")
-    T = torch.empty(px, device="cuda")
-    last = torch.empty(px, dtype=torch.int32, device="cuda")
-    grads = {k: torch.zeros_like(v) for k, v in ds.params.items()}
     stream = torch.cuda.current_stream()
-
-    def step():
-        r.bin(ds, sync=False)
-        c, t, l = r.render_fwd(ds, out=(rgb, T, last))
-        r.backward(ds, 2.0 * (c - target), None, t, l, grads=grads)
-
     out = {}
     for name, rec in (("checkpoint+hit_records", True), ("checkpoint_only", False)):
-        r.record_hits(rec)
+        torch.cuda.empty_cache()
+        torch.cuda.reset_peak_memory_stats()
+        base = torch.cuda.memory_allocated()
+        r = Renderer(ds.n, ds.k, cams, capacity=cap, hit_records=rec)
+        rgb = torch.empty((px, 3), device="cuda")
+        T = torch.empty(px, device="cuda")
+        last = torch.empty(px, dtype=torch.int32, device="cuda")
+        grads = {k: torch.zeros_like(v) for k, v in ds.params.items()}
+
+        def step():
+            r.bin(ds, sync=False)
+            c, t, l = r.render_fwd(ds, out=(rgb, T, last))
+            r.backward(ds, 2.0 * (c - target), None, t, l, grads=grads)
+
         for _ in range(args.warmup):
             step()
         torch.cuda.synchronize()
-        torch.cuda.reset_peak_memory_stats()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         for _ in range(args.steps):
@@ -501,19 +506,18 @@ def run_large(args):
         b.record(stream)
         b.synchronize()
         out[name] = {"ms_fwd_bwd": a.elapsed_time(b) / args.steps,
-                     "peak_allocated_gb": torch.cuda.max_memory_allocated() / 1e9}
-    # bytes of the hit records in the workspace (8 warps x batch slots x 32 pixels x (4 + 32 x 2) B)
-    P = r.plan
-    tiles = sum(((c.width + 15) // 16) * ((c.height + 15) // 16) for c in cams)
-    slots = P.capacity // 32 + tiles + 1
-    hit_rec_gb = 8 * slots * 32 * (4 + 64) / 1e9
+                     "workspace_gb": r.plan.ws_bytes / 1e9,
+                     "peak_allocated_gb": torch.cuda.max_memory_allocated() / 1e9,
+                     "peak_above_scene_gb": (torch.cuda.max_memory_allocated() - base) / 1e9}
+        del r, rgb, T, last, grads
     hits = stats["hits"]
     line = {"workload": "5,000,000 cells (capture recipe), 48 neighbours, 4 views 3840x2160 on a ring of radius 3",
-            "pixels": px, "instances": stats["instances"], "hits": hits, "hits_per_pixel": hits / px,
-            "workspace_gb": P.ws_bytes / 1e9, "hit_records_gb": hit_rec_gb,
+            "pixels": px, "instances": stats["instances"], "capacity": cap, "hits": hits,
+            "hits_per_pixel": hits / px, "scene_params_gb": sum(v.numel() * v.element_size()
+                                                               for v in ds.params.values()) / 1e9,
             "checkpoint_bytes_per_pixel": 8,
             "no_checkpoint_estimate_gb": hits * 32 / 1e9,
-            "no_checkpoint_note": "every hit's (T before, colour, entry, exit, kinds, cell) at 32 B instead of replaying",
+            "no_checkpoint_note": "not built: every hit's (T before, colour, entry, exit, kinds, cell) at 32 B",
             "steps": args.steps, "warmup": args.warmup, "scene_generation_s": round(gen_s, 1), **out}
     print(json.dumps(line), flush=True)
 

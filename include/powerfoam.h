@@ -113,14 +113,21 @@ pf_status pf_plan_pixels(const pf_plan *plan, uint64_t *pixels);
 pf_status pf_plan_set_cameras(pf_plan *plan, const pf_camera *cams, int32_t n_views);
 /* Hit recording (default on).  While on, pf_render_fwd also writes, for
  * every pixel and every batch of 32 entries of its tile's list, a 32-bit
- * mask of the entries whose segment was non-empty (4 bytes per pixel and
- * batch, in the workspace); the next pf_render_bwd on the same bins then
- * replays only those (cell, pixel) pairs instead of re-testing every listed
- * cell.  Turn it off for forward-only rendering (it saves one store per
+ * mask of the entries whose segment was non-empty, and the active
+ * constraints (entry, exit) of the pixel's first 256 hits (in the
+ * workspace); the next pf_render_bwd on the same bins then replays only
+ * those (cell, pixel) pairs, without the plane loop for the recorded ones,
+ * instead of re-testing every listed cell.  Turn it off for forward-only rendering (it saves one store per
  * warp and batch); the backward then re-tests.  The masks are dropped by
  * pf_prepare, pf_project and pf_bin_sort, and not written by a forward that
  * counts stats. */
 pf_status pf_plan_set_record_hits(pf_plan *plan, int32_t enable);
+/* Lay the plan's workspace out without the hit records (8 x (capacity/32 +
+ * tiles + 1) x 128 bytes of masks, 516 bytes per pixel of records and
+ * counts): a smaller workspace whose backward always re-tests.  Call it
+ * before querying pf_plan_workspace_bytes and allocating; recording can then
+ * no longer be enabled (PF_ERR_INVALID_ARG). */
+pf_status pf_plan_omit_hit_records(pf_plan *plan);
 /* Count work in the next forward passes (adds to the counters; 0 disables). */
 pf_status pf_plan_enable_stats(pf_plan *plan, int32_t enable);
 /* Read the counters, then reset them (synchronises `stream`). */

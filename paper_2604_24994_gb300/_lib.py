@@ -59,6 +59,7 @@ def _sig(lib):
         "pf_plan_set_cameras": ([V, P(Camera), I32], st),
         "pf_plan_enable_stats": ([V, I32], st),
         "pf_plan_set_record_hits": ([V, I32], st),
+        "pf_plan_omit_hit_records": ([V], st),
         "pf_plan_read_stats": ([V, V, P(Stats), V], st),
         "pf_prepare": ([P(Scene), V, V, V], st),
         "pf_project": ([P(Scene), V, V, V], st),

@@ -56,7 +56,7 @@ class DeviceScene:
 class Plan:
     """A C plan (layout + cameras) with its device workspace."""
 
-    def __init__(self, n: int, k: int, cams, capacity: int, device="cuda"):
+    def __init__(self, n: int, k: int, cams, capacity: int, device="cuda", hit_records: bool = True):
         self.n, self.k = n, k
         self.cams = list(cams)
         self.capacity = int(capacity)
@@ -64,6 +64,8 @@ class Plan:
         arr = _lib.camera_array(self.cams)
         check(lib().pf_plan_create(n, k, arr, len(self.cams), self.capacity, C.byref(self.handle)),
               "pf_plan_create")
+        if not hit_records:
+            check(lib().pf_plan_omit_hit_records(self.handle), "pf_plan_omit_hit_records")
         b = C.c_uint64()
         check(lib().pf_plan_workspace_bytes(self.handle, C.byref(b)), "pf_plan_workspace_bytes")
         self.ws_bytes = int(b.value)
@@ -98,20 +100,24 @@ class Renderer:
     """Renders a DeviceScene from a fixed set of cameras (one or many views,
     any resolutions).  The instance capacity grows automatically."""
 
-    def __init__(self, n: int, k: int, cams, capacity: int | None = None, device="cuda"):
+    def __init__(self, n: int, k: int, cams, capacity: int | None = None, device="cuda",
+                 hit_records: bool = True):
+        """hit_records=False lays the workspace out without the forward's hit
+        records (smaller; the backward then always re-tests)."""
         self.device = device
+        self._hit_records = hit_records
         cams = list(cams)
         if capacity is None:
             px = sum(c.width * c.height for c in cams)
             capacity = max(1 << 16, min(8 * n * len(cams) + px // 16, 0xE0000000))
-        self._record = True
+        self._record = hit_records
         self._stats = False
         self.plan = self._make_plan(n, k, cams, capacity)
         self.generation = 0
         self.n_instances = 0
 
     def _make_plan(self, n, k, cams, capacity):
-        P = Plan(n, k, cams, capacity, self.device)
+        P = Plan(n, k, cams, capacity, self.device, hit_records=self._hit_records)
         check(lib().pf_plan_set_record_hits(P.handle, 1 if self._record else 0), "pf_plan_set_record_hits")
         check(lib().pf_plan_enable_stats(P.handle, 1 if self._stats else 0), "pf_plan_enable_stats")
         return P

@@ -52,9 +52,10 @@ WS Plan::ws(void *base) const {
     w.sort_tmp_cell = (uint32_t *)(b + L.sort_tmp_cell);
     w.counters = (Counters *)(b + L.counters);
     w.acc = (float *)(b + L.acc);
-    w.hitmask = fwd_only ? nullptr : (uint32_t *)(b + L.hitmask);
-    w.hitkind = fwd_only ? nullptr : (uint16_t *)(b + L.hitkind);
-    w.hitcount = fwd_only ? nullptr : (uint32_t *)(b + L.hitcount);
+    const bool rec = !fwd_only && !no_hit_records;
+    w.hitmask = rec ? (uint32_t *)(b + L.hitmask) : nullptr;
+    w.hitkind = rec ? (uint16_t *)(b + L.hitkind) : nullptr;
+    w.hitcount = rec ? (uint32_t *)(b + L.hitcount) : nullptr;
     w.pw = (float4 *)(b + L.pw);
     if (external_scene) {
         const SceneLayout S = make_scene_layout(n, k);
@@ -173,10 +174,12 @@ void make_layout(Plan *p) {
     L.sort_tmp_cell = take(cap * 4);
     L.counters = take(sizeof(Counters));
     L.acc = take((p->fwd_only ? 0 : n) * ACC_F * 4);
-    L.hitmask = take(p->fwd_only ? 0 : (uint64_t)(TILE_PIX / 32) * mask_batches(*p) * 32 * 4);
-    L.hitkind = take(p->fwd_only ? 0 : (uint64_t)p->total_pixels * HIT_CAP * 2);
-    L.hitcount = take(p->fwd_only ? 0 : (uint64_t)p->total_pixels * 4);
     L.pw = take(n * 16);
+    // hit records last, so that dropping them moves no other region
+    const bool rec = !p->fwd_only && !p->no_hit_records;
+    L.hitmask = take(rec ? (uint64_t)(TILE_PIX / 32) * mask_batches(*p) * 32 * 4 : 0);
+    L.hitkind = take(rec ? (uint64_t)p->total_pixels * HIT_CAP * 2 : 0);
+    L.hitcount = take(rec ? (uint64_t)p->total_pixels * 4 : 0);
     L.total = o;
 }
 
@@ -290,7 +293,20 @@ pf_status pf_plan_set_cameras(pf_plan *p, const pf_camera *cams, int32_t n_views
 
 pf_status pf_plan_set_record_hits(pf_plan *p, int32_t enable) {
     if (!p) return PF_ERR_INVALID_ARG;
+    if (enable && p->no_hit_records) {
+        set_error("pf_plan_set_record_hits: the plan's workspace has no hit records (pf_plan_omit_hit_records)");
+        return PF_ERR_INVALID_ARG;
+    }
     p->record_hits = enable != 0;
+    return PF_OK;
+}
+
+pf_status pf_plan_omit_hit_records(pf_plan *p) {
+    if (!p) return PF_ERR_INVALID_ARG;
+    p->no_hit_records = true;
+    p->record_hits = false;
+    p->masks_valid = false;
+    make_layout(p);
     return PF_OK;
 }
 

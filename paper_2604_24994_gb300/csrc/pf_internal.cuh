@@ -154,6 +154,7 @@ struct Plan {
     // pf_render_fwd, cleared by anything that changes the bins
     bool masks_valid = false;
     bool record_hits = true;   // pf_plan_set_record_hits
+    bool no_hit_records = false;  // pf_plan_omit_hit_records: the layout has no hit-record regions
     WS ws(void *base) const;
 };
 

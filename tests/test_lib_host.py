@@ -39,6 +39,28 @@ def test_exports_every_declared_symbol(lib):
     assert not missing, missing
 
 
+def test_plan_without_hit_records(lib):
+    from paper_2604_24994_gb300 import _lib
+    cams = [inputs.look_at((3, 0, 0), 100, 75), inputs.look_at((0, 3, 0), 64, 64)]
+    arr = _lib.camera_array(cams)
+    h = C.c_void_p()
+    assert lib.pf_plan_create(1000, 16, arr, 2, 5000, C.byref(h)) == 0
+    full, small = C.c_uint64(), C.c_uint64()
+    lib.pf_plan_workspace_bytes(h, C.byref(full))
+    assert lib.pf_plan_set_record_hits(h, 0) == 0 and lib.pf_plan_set_record_hits(h, 1) == 0
+    assert lib.pf_plan_omit_hit_records(h) == 0
+    lib.pf_plan_workspace_bytes(h, C.byref(small))
+    # 8 warps x (capacity/32 + tiles + 1) batch slots x 32 pixels x 4 B of masks, then per pixel
+    # 256 x 2 B of constraint records and a 4 B hit count (each region 256-byte aligned)
+    tiles = 7 * 5 + 4 * 4
+    px = 100 * 75 + 64 * 64
+    rec = 8 * (5000 // 32 + tiles + 1) * 32 * 4 + px * 256 * 2 + px * 4
+    assert rec <= full.value - small.value <= rec + 3 * 256
+    assert lib.pf_plan_set_record_hits(h, 1) == _lib.PF_ERR_INVALID_ARG
+    assert lib.pf_plan_set_record_hits(h, 0) == 0
+    lib.pf_plan_destroy(h)
+
+
 def test_status_strings(lib):
     from paper_2604_24994_gb300 import _lib
     for s in range(7):
