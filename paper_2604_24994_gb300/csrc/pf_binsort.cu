@@ -205,11 +205,12 @@ template <typename KeyArr, typename CellArr>
 __device__ void bitonic_sort(KeyArr keys, CellArr cells, int n) {
     int P = 1;
     while (P < n) P <<= 1;
-    for (int size = 2; size <= P; size <<= 1) {
-        const int half = size >> 1;
+    for (int lh = 0; (2 << lh) <= P; lh++) {   // merge blocks of size 2^(lh+1)
+        const int half = 1 << lh, size = 2 << lh;
         for (int q = threadIdx.x; q < P / 2; q += blockDim.x) {
-            const int i = (q / half) * size + (q % half);
-            const int j = (q / half) * size + size - 1 - (q % half);
+            const int blk = (q >> lh) << (lh + 1), r = q & (half - 1);
+            const int i = blk + r;
+            const int j = blk + size - 1 - r;
             if (j < n) {
                 const unsigned long long ki = keys[i], kj = keys[j];
                 const uint32_t ci = cells[i], cj = cells[j];
@@ -220,9 +221,10 @@ __device__ void bitonic_sort(KeyArr keys, CellArr cells, int n) {
             }
         }
         __syncthreads();
-        for (int stride = half >> 1; stride > 0; stride >>= 1) {
+        for (int ls = lh - 1; ls >= 0; ls--) {
+            const int stride = 1 << ls;
             for (int q = threadIdx.x; q < P / 2; q += blockDim.x) {
-                const int i = (q / stride) * 2 * stride + (q % stride);
+                const int i = ((q >> ls) << (ls + 1)) + (q & (stride - 1));
                 const int j = i + stride;
                 if (j < n) {
                     const unsigned long long ki = keys[i], kj = keys[j];
@@ -242,13 +244,10 @@ __device__ void bitonic_sort(KeyArr keys, CellArr cells, int n) {
 // sorted in shared memory; with GLOBAL, buckets above CAP are sorted in
 // place in the global scratch arrays.
 template <int LO, int CAP, int NT, bool GLOBAL>
-__global__ void __launch_bounds__(NT) sort_tiles_kernel(const uint32_t *__restrict__ tile_start,
-                                                        unsigned long long cap, const unsigned long long *inst_key,
-                                                        const uint32_t *inst_cell, uint32_t *__restrict__ inst_sorted,
-                                                        unsigned long long *tmp_key, uint32_t *tmp_cell) {
-    extern __shared__ unsigned long long sk[];
-    uint32_t *sc = reinterpret_cast<uint32_t *>(sk + CAP);
-    const int64_t t = blockIdx.x;
+__device__ __forceinline__ void sort_tile(int64_t t, const uint32_t *__restrict__ tile_start, unsigned long long cap,
+                                          const unsigned long long *inst_key, const uint32_t *inst_cell,
+                                          uint32_t *__restrict__ inst_sorted, unsigned long long *tmp_key,
+                                          uint32_t *tmp_cell, unsigned long long *sk, uint32_t *sc) {
     unsigned long long s = tile_start[t], e = tile_start[t + 1];
     if (s > cap) s = cap;
     if (e > cap) e = cap;
@@ -276,6 +275,49 @@ __global__ void __launch_bounds__(NT) sort_tiles_kernel(const uint32_t *__restri
         __syncthreads();
         bitonic_sort(gk, gc, (int)n);
         for (int64_t q = threadIdx.x; q < n; q += NT) inst_sorted[s + q] = gc[q];
+    }
+}
+
+// One CTA per tile for the lists of at most CAP entries.
+template <int CAP, int NT>
+__global__ void __launch_bounds__(NT) sort_small_tiles_kernel(const uint32_t *__restrict__ tile_start,
+                                                              unsigned long long cap,
+                                                              const unsigned long long *inst_key,
+                                                              const uint32_t *inst_cell,
+                                                              uint32_t *__restrict__ inst_sorted) {
+    extern __shared__ unsigned long long sk[];
+    uint32_t *sc = reinterpret_cast<uint32_t *>(sk + CAP);
+    unsigned long long s = tile_start[blockIdx.x], e = tile_start[blockIdx.x + 1];
+    if (s > cap) s = cap;
+    if (e > cap) e = cap;
+    if (e - s > (unsigned long long)CAP) return;  // the persistent kernel sorts it
+    sort_tile<0, CAP, NT, false>(blockIdx.x, tile_start, cap, inst_key, inst_cell, inst_sorted, nullptr, nullptr,
+                                 sk, sc);
+}
+
+// Persistent CTAs over the render order (tiles by decreasing list length,
+// bucketed by length / 4): every list longer than LO comes before any list
+// shorter than LO, so a CTA stops at the first such list.  Lists up to CAP
+// are sorted in shared memory, longer ones in the global scratch arrays.
+template <int LO, int CAP, int NT>
+__global__ void __launch_bounds__(NT) sort_large_tiles_kernel(const uint32_t *__restrict__ order, int64_t T,
+                                                              const uint32_t *__restrict__ tile_start,
+                                                              unsigned long long cap,
+                                                              const unsigned long long *inst_key,
+                                                              const uint32_t *inst_cell,
+                                                              uint32_t *__restrict__ inst_sorted,
+                                                              unsigned long long *tmp_key, uint32_t *tmp_cell) {
+    extern __shared__ unsigned long long sk[];
+    uint32_t *sc = reinterpret_cast<uint32_t *>(sk + CAP);
+    for (int64_t i = blockIdx.x; i < T; i += gridDim.x) {
+        const int64_t t = order[i];
+        unsigned long long s = tile_start[t], e = tile_start[t + 1];
+        if (s > cap) s = cap;
+        if (e > cap) e = cap;
+        if (e - s < (unsigned long long)LO) break;  // the same for every thread of the CTA
+        sort_tile<LO, CAP, NT, true>(t, tile_start, cap, inst_key, inst_cell, inst_sorted, tmp_key, tmp_cell, sk,
+                                     sc);
+        __syncthreads();  // shared memory is reused by the next list
     }
 }
 
@@ -345,15 +387,18 @@ cudaError_t launch_bin_sort(const Plan &p, const WS &w, cudaStream_t st) {
     if (T > 0) {
         // small buckets (<= 2048) in 24 KB of shared memory, large ones in 192 KB
         constexpr int SMALL = 2048, LARGE = 16384;
-        auto ks = sort_tiles_kernel<0, SMALL, 256, false>;
-        auto kl = sort_tiles_kernel<SMALL, LARGE, 512, true>;
+        auto ks = sort_small_tiles_kernel<SMALL, 256>;
+        auto kl = sort_large_tiles_kernel<SMALL, LARGE, 512>;
         const size_t ss = (size_t)SMALL * 12, sl = (size_t)LARGE * 12;
         cudaFuncSetAttribute(kl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sl);
-        ks<<<(unsigned)T, 256, ss, st>>>(w.tile_start, p.cap, w.inst_key, w.inst_cell, w.inst_sorted, w.sort_tmp_key,
-                                        w.sort_tmp_cell);
+        ks<<<(unsigned)T, 256, ss, st>>>(w.tile_start, p.cap, w.inst_key, w.inst_cell, w.inst_sorted);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        kl<<<(unsigned)T, 512, sl, st>>>(w.tile_start, p.cap, w.inst_key, w.inst_cell, w.inst_sorted, w.sort_tmp_key,
-                                        w.sort_tmp_cell);
+        int dev = 0, sms = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        kl<<<(unsigned)(T < sms ? T : sms), 512, sl, st>>>(w.tile_order, T, w.tile_start, p.cap, w.inst_key,
+                                                            w.inst_cell, w.inst_sorted, w.sort_tmp_key,
+                                                            w.sort_tmp_cell);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
