@@ -76,6 +76,8 @@ def lib():
             _lib.orc_ray_segments.argtypes = [P(_Scene), P(_Cands), P(d), P(d), C.c_int64, P(C.c_int32),
                                               P(d), P(d), P(C.c_int32), P(C.c_int32)]
             _lib.orc_ray_segments.restype = C.c_int64
+            _lib.orc_cell_contrib.argtypes = [P(_Scene), P(_Cands), P(_Camera), C.c_int64, P(C.c_int32), P(d), P(d),
+                                         C.c_int]
             _lib.orc_render_rays.argtypes = [P(_Scene), P(_Cands), C.c_int64, P(d), P(d), d, P(d), P(d)]
             _lib.orc_cell_colour.argtypes = [P(_Scene), C.c_int64, P(d), P(d), d, d, d, P(d)]
             _lib.orc_ray.argtypes = [P(_Camera), d, d, P(d), P(d)]
@@ -245,6 +247,17 @@ class Oracle:
                          _ptr(rgb, C.c_double), _ptr(T, C.c_double), _ptr(nseg, C.c_int32),
                          self.nthreads)
         return (rgb, T, nseg) if return_nseg else (rgb, T)
+
+    def contrib(self, cam, pix=None):
+        """Per-cell contributions [N] over the pixels (float64): sum of
+        T alpha (L_sparse) and of T alpha max(nh . d, 0)^2 (L_normal)."""
+        pixa, npix = self._pix(cam, pix)
+        sp = np.zeros(self.n, np.float64)
+        nm = np.zeros(self.n, np.float64)
+        lib().orc_cell_contrib(C.byref(self._s), C.byref(self._cs) if self._cs else None, C.byref(camera_struct(cam)),
+                          npix, _ptr(pixa, C.c_int32) if pixa is not None else None, _ptr(sp, C.c_double),
+                          _ptr(nm, C.c_double), self.nthreads)
+        return sp, nm
 
     def render_grad(self, cam, dL_dC, dL_dT, pix=None) -> dict:
         """dL/d(parameters) (float64 dict keyed like the scene) for upstream

@@ -391,6 +391,61 @@ int orc_render(const orc_scene *s, const orc_cands *cd, const orc_camera *cam, i
     return 0;
 }
 
+/*
+ * Per-cell contributions over npix pixels (Sec. 4 training terms): with
+ * T_k the transmittance in front of the cell's segment k on a ray and
+ * alpha_k its opacity,
+ *   sparse[i] = sum over rays of T_k alpha_k                   (L_sparse)
+ *   normal[i] = sum over rays of T_k alpha_k max(nh_i . d, 0)^2 (L_normal)
+ * accumulated over the same composited segments as orc_render.
+ */
+int orc_cell_contrib(const orc_scene *s, const orc_cands *cd, const orc_camera *cam, int64_t npix, const int32_t *pix,
+                double *sparse, double *normal, int nthreads) {
+    memset(sparse, 0, sizeof(double) * (size_t)s->n);
+    memset(normal, 0, sizeof(double) * (size_t)s->n);
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+#endif
+    {
+        orc_seg *buf = NULL;
+        int64_t cap = 0;
+        double *ls = calloc((size_t)s->n, sizeof(double)), *ln = calloc((size_t)s->n, sizeof(double));
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+        for (int64_t k = 0; k < npix; k++) {
+            double u, v, o[3], d[3];
+            pixel_of(cam, k, pix, &u, &v);
+            orc_ray(cam, u, v, o, d);
+            int64_t n = ray_segments(s, cd, o, d, &buf, &cap);
+            double T = 1.0;
+            for (int64_t q = 0; q < n; q++) {
+                int64_t i = buf[q].cell;
+                double surv = exp(-s->sigma[i] * (buf[q].tb - buf[q].ta));
+                double w = T * (1.0 - surv);
+                double nh[3], len;
+                unit_normal(s, i, nh, &len);
+                double nd = dot3(nh, d);
+                ls[i] += w;
+                ln[i] += w * (nd > 0.0 ? nd * nd : 0.0);
+                T *= surv;
+            }
+        }
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+        for (int64_t i = 0; i < s->n; i++) {
+            sparse[i] += ls[i];
+            normal[i] += ln[i];
+        }
+        free(ls);
+        free(ln);
+        free(buf);
+    }
+    return 0;
+}
+
 /* cells whose bounding sphere the given pixels' rays meet at t >= 0 (flag per cell) */
 int orc_hit_cells(const orc_scene *s, const orc_camera *cam, int64_t npix, const int32_t *pix, uint8_t *flag,
                   int nthreads) {

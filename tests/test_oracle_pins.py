@@ -512,3 +512,57 @@ def test_binning_rect_is_tight():
         assert rect[i, 1] <= lo[1] // 16 and rect[i, 3] >= hi[1] // 16
         assert rect[i, 0] >= (lo[0] - 2) // 16 and rect[i, 2] <= (hi[0] + 2) // 16
         assert rect[i, 1] >= (lo[1] - 2) // 16 and rect[i, 3] <= (hi[1] + 2) // 16
+
+
+# ------------------------------------------ per-cell contributions (Sec. 4)
+
+def test_contributions_telescope_to_one_minus_T(tiny):
+    """Per ray, sum_k T_k alpha_k = 1 - T_final (the product telescopes), so
+    the per-cell L_sparse terms sum to sum over pixels of (1 - T); the
+    L_normal terms lie between 0 and the L_sparse ones."""
+    sc, cam = tiny
+    orc = oracle.Oracle(sc)
+    sp, nm = orc.contrib(cam)
+    _, T = orc.render(cam)
+    assert sp.sum() == pytest.approx((1 - T).sum(), rel=1e-12)
+    assert np.all(nm >= 0) and np.all(nm <= sp * (1 + 1e-12))
+    assert (sp > 0).sum() > 100
+
+
+def test_contributions_of_an_isolated_cell_closed_form():
+    """One cell, no neighbours, face outside the ball: each pixel adds
+    w = 1 - exp(-sigma chord) to L_sparse, chord = 2 sqrt(R^2 - b^2) with b
+    the ray's distance to the site, and w max(nh.d, 0)^2 to L_normal.
+    Flipping the normal (the face stays outside the ball, so nothing else
+    changes) moves the dot product to the other side: the two L_normal sum
+    to sum w (nh.d)^2."""
+    R, sig = 0.3, 2.0
+    nrm = np.array([0.3, -0.5, 0.8])
+    cam = cam_at((0.4, -2.0, 0.3), 24, 20, 30.0)
+    orc = oracle.Oracle(make_scene([0, 0, 0], 0.04, R, sig, normal=nrm))
+    sp, nm = orc.contrib(cam)
+    nh = nrm / np.linalg.norm(nrm)
+    ws, wn, wq = 0.0, 0.0, 0.0
+    for v in range(cam.height):
+        for u in range(cam.width):
+            o, d = orc.ray(cam, u, v)
+            tc = -np.dot(o, d)                      # closest approach to the site at the origin
+            b2 = np.dot(o + tc * d, o + tc * d)
+            if b2 >= R * R:
+                continue
+            half = math.sqrt(R * R - b2)
+            ta, tb = max(tc - half, 0.0), tc + half
+            if tb <= ta:
+                continue
+            w = 1 - math.exp(-sig * (tb - ta))
+            nd = float(np.dot(nh, d))
+            ws += w
+            wn += w * max(nd, 0.0) ** 2
+            wq += w * nd * nd
+    assert ws > 1.0
+    assert sp[0] == pytest.approx(ws, rel=1e-12)
+    assert nm[0] == pytest.approx(wn, rel=1e-12)
+    flipped = oracle.Oracle(make_scene([0, 0, 0], 0.04, R, sig, normal=-nrm))
+    sp2, nm2 = flipped.contrib(cam)
+    assert sp2[0] == pytest.approx(sp[0], rel=1e-14)
+    assert nm[0] + nm2[0] == pytest.approx(wq, rel=1e-12)
