@@ -304,6 +304,21 @@ def run_ours(args):
         r.record_hits(False)
     clocks = clk.summary()
 
+    # the forward with the per-cell contributions (T alpha, T alpha max(n.d,0)^2) added
+    contrib = (torch.zeros(ds.n, device="cuda"), torch.zeros(ds.n, device="cuda"))
+    ct = []
+    for it in range(W + K):
+        flush.zero_()
+        a, b = ev(), ev()
+        a.record(stream)
+        r.render_fwd(ds, out=(rgb, T, last), contrib=contrib)
+        b.record(stream)
+        b.synchronize()
+        if it >= W:
+            ct.append(a.elapsed_time(b))
+    ms_render_contrib = float(np.mean(ct))
+    del contrib
+
     # end to end through the public API with host buffers: camera in, image out
     host_rgb = torch.empty((r.plan.pixels, 3), dtype=torch.float32, pin_memory=True)
     host_T = torch.empty(r.plan.pixels, dtype=torch.float32, pin_memory=True)
@@ -345,6 +360,7 @@ def run_ours(args):
                    "scene_generation_s": round(gen_s, 1)},
         "fwd_fps": ws * 1000.0 / ms_fwd, "fwd_bwd_fps": ws * 1000.0 / ms_train, "ms_fwd_bwd": ms_train,
         "ms_render_fwd_kernel": ms_render,
+        "ms_render_fwd_contrib_kernel": ms_render_contrib,
         "work": stats,
         "roofline": {"bound": "alu", "kernel": "render_fwd_kernel", "achieved": achieved, "peak": peak_tflops,
                      "unit": "TFLOP/s", "frac": achieved / peak_tflops,

@@ -179,6 +179,20 @@ pf_status pf_render_fwd(const pf_scene *scene, pf_plan *plan, void *ws, float *r
                         void *stream);
 
 /*
+ * pf_render_fwd that also ADDS each cell's contributions over the views'
+ * pixels (the per-primitive terms of Sec. 4's training): with T the
+ * transmittance in front of the cell's segment on a ray and alpha its
+ * opacity,
+ *   contrib_sparse[i] += sum over rays of T alpha           (L_sparse, pruning EMA)
+ *   contrib_normal[i] += sum over rays of T alpha max(nh_i . d, 0)^2   (L_normal)
+ * Arrays [N] on the device, zeroed by the caller for a fresh sum.  Segments
+ * behind a pixel's early termination (T < 1e-6) are not counted.  Records
+ * hits like pf_render_fwd; does not count stats.
+ */
+pf_status pf_render_fwd_contrib(const pf_scene *scene, pf_plan *plan, void *ws, float *rgb, float *T, uint32_t *last,
+                                float *contrib_sparse, float *contrib_normal, void *stream);
+
+/*
  * Adjoint of pf_render_fwd for upstream dL/drgb [P,3] and dL/dT [P]
  * (dL_dT may be NULL for zero).  Replays each tile back to front from the
  * checkpoint (T, last) and ADDS dL/d(parameter) into `grad` (every pointer

@@ -164,12 +164,24 @@ class Renderer:
         last = torch.empty(P.pixels, dtype=torch.int32, device=self.device)
         return rgb, T, last
 
-    def render_fwd(self, scene: DeviceScene, params: dict | None = None, out=None):
-        """pf_render_fwd on the current bins: flat rgb [P,3], T [P], last [P]."""
+    def render_fwd(self, scene: DeviceScene, params: dict | None = None, out=None, contrib=None):
+        """pf_render_fwd on the current bins: flat rgb [P,3], T [P], last [P].
+        With contrib=(sparse [N], normal [N]) (float32 device tensors) it is
+        pf_render_fwd_contrib, which also adds the per-cell contributions
+        (sum of T alpha, and of T alpha max(n.d, 0)^2) into them."""
         rgb, T, last = out if out is not None else self._alloc_out()
         P = self.plan
-        check(lib().pf_render_fwd(C.byref(scene.struct(params)), P.handle, P.ws_ptr, rgb.data_ptr(), T.data_ptr(),
-                                  last.data_ptr(), _stream()), "pf_render_fwd")
+        if contrib is None:
+            check(lib().pf_render_fwd(C.byref(scene.struct(params)), P.handle, P.ws_ptr, rgb.data_ptr(),
+                                      T.data_ptr(), last.data_ptr(), _stream()), "pf_render_fwd")
+        else:
+            cs, cn = contrib
+            for t in (cs, cn):
+                if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous() and t.numel() == P.n):
+                    raise ValueError("contribution arrays must be contiguous float32 CUDA tensors of N cells")
+            check(lib().pf_render_fwd_contrib(C.byref(scene.struct(params)), P.handle, P.ws_ptr, rgb.data_ptr(),
+                                              T.data_ptr(), last.data_ptr(), cs.data_ptr(), cn.data_ptr(),
+                                              _stream()), "pf_render_fwd_contrib")
         return rgb, T, last
 
     def forward(self, scene: DeviceScene, params: dict | None = None, sync: bool = True):

@@ -393,6 +393,23 @@ pf_status pf_render_fwd(const pf_scene *scene, pf_plan *p, void *ws, float *rgb,
     return s;
 }
 
+pf_status pf_render_fwd_contrib(const pf_scene *scene, pf_plan *p, void *ws, float *rgb, float *T, uint32_t *last,
+                                float *contrib_sparse, float *contrib_normal, void *stream) {
+    g_err[0] = 0;
+    if (!p || !ws || !scene_ok(scene, p) || !rgb || !T || !last) return PF_ERR_INVALID_ARG;
+    if (p->n > 0 && (!contrib_sparse || !contrib_normal)) {
+        set_error("pf_render_fwd_contrib: null contribution array");
+        return PF_ERR_INVALID_ARG;
+    }
+    WS w = p->ws(ws);
+    const bool record = p->record_hits && w.hitmask != nullptr;
+    pf_status s = cuda_status(launch_render_fwd(*scene, *p, w, rgb, T, last, record, (cudaStream_t)stream,
+                                                p->n > 0 ? contrib_sparse : nullptr, p->n > 0 ? contrib_normal : nullptr),
+                              "pf_render_fwd_contrib");
+    p->masks_valid = !s && record;
+    return s;
+}
+
 pf_status pf_render_bwd(const pf_scene *scene, pf_plan *p, void *ws, const float *dL_drgb, const float *dL_dT,
                         const float *T, const uint32_t *last, const pf_scene_grad *g, void *stream) {
     g_err[0] = 0;

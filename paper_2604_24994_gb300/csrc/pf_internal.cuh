@@ -183,7 +183,8 @@ cudaError_t launch_prepare(const pf_scene &s, const Plan &p, const WS &w, cudaSt
 cudaError_t launch_project(const pf_scene &s, const Plan &p, const WS &w, cudaStream_t st);
 cudaError_t launch_bin_sort(const Plan &p, const WS &w, cudaStream_t st);
 cudaError_t launch_render_fwd(const pf_scene &s, const Plan &p, const WS &w, float *rgb, float *T, uint32_t *last,
-                              bool record, cudaStream_t st);
+                              bool record, cudaStream_t st, float *contrib_sparse = nullptr,
+                              float *contrib_normal = nullptr);
 cudaError_t launch_render_bwd(const pf_scene &s, const Plan &p, const WS &w, const float *dL_drgb,
                               const float *dL_dT, const float *T, const uint32_t *last, const pf_scene_grad &g,
                               bool use_masks, cudaStream_t st);

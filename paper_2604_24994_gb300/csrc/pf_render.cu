@@ -491,6 +491,8 @@ struct RenderArgs {
     int nv, n, K;
     unsigned long long cap;
     int64_t mask_batches;   // batch slots per warp in the hit-mask array
+    float *contrib_sparse;  // [N] sum of T alpha per cell (pf_render_fwd_contrib), or null
+    float *contrib_normal;  // [N] sum of T alpha max(nh.d, 0)^2 per cell, or null
 };
 
 // Hit masks: one 32-bit word per (warp of the tile, batch, pixel of the
@@ -570,8 +572,10 @@ __device__ __forceinline__ Stage make_stage(float4 *smem, int K, bool with_nb) {
 
 // ---------------------------------------------------------------- forward
 // STATS: count work (see pf_stats); REC: record the hit masks the backward
-// replays (only with a hit-mask region in the workspace).
-template <bool STATS, bool REC>
+// replays (only with a hit-mask region in the workspace); CONTRIB: add each
+// cell's contributions (Sec. 4: T alpha for L_sparse and the pruning EMA,
+// T alpha max(nh.d, 0)^2 for L_normal) over the frame's pixels.
+template <bool STATS, bool REC, bool CONTRIB>
 __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, int64_t n_tiles,
                                                                  float *__restrict__ rgb_out,
                                                                  float *__restrict__ T_out,
@@ -661,6 +665,23 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, i
                 st_wcand += l0;
                 st_wpass += l0 && cm;
                 st_whit += l0 && hm;
+            }
+            if (CONTRIB && __any_sync(0xffffffffu, hit)) {
+                // T alpha and T alpha max(nh.d, 0)^2 of the hit lanes, summed
+                // over the warp in 2^-24 fixed point (integer warp reduction:
+                // 32 terms <= 1 stay below 2^29), one atomic per value and cell
+                unsigned qw = 0u, qn = 0u;
+                if (hit) {
+                    const float cw = T * (1.0f - __expf(-fminf(cr[CR_SIG] * (seg.sb - seg.sa), X_CAP)));
+                    const float nd = dot3(f3(cr[CR_N], cr[CR_N + 1], cr[CR_N + 2]), ray.dh);
+                    qw = __float2uint_rn(cw * 0x1p24f);
+                    qn = __float2uint_rn((nd > 0.0f ? cw * nd * nd : 0.0f) * 0x1p24f);
+                }
+                qw = __reduce_add_sync(0xffffffffu, qw);
+                qn = __reduce_add_sync(0xffffffffu, qn);
+                if (lane < 2)
+                    atomicAdd((lane ? A.contrib_normal : A.contrib_sparse) + sg.ids(buf)[j],
+                              (float)(lane ? qn : qw) * 0x1p-24f);
             }
             if (!hit) continue;
             if (REC) {
@@ -1122,6 +1143,8 @@ static RenderArgs make_args(const pf_scene &s, const Plan &p, const WS &w) {
     A.K = p.k;
     A.cap = p.cap;
     A.mask_batches = mask_batches(p);
+    A.contrib_sparse = nullptr;
+    A.contrib_normal = nullptr;
     return A;
 }
 
@@ -1141,14 +1164,18 @@ static size_t fwd_smem(int K) { return stage_bytes(K, false); }
 static size_t bwd_smem(int K) { return stage_bytes(K, true); }
 
 cudaError_t launch_render_fwd(const pf_scene &s, const Plan &p, const WS &w, float *rgb, float *T, uint32_t *last,
-                              bool record, cudaStream_t st) {
+                              bool record, cudaStream_t st, float *contrib_sparse, float *contrib_normal) {
     if (p.total_tiles == 0) return cudaSuccess;
     RenderArgs A = make_args(s, p, w);
+    A.contrib_sparse = contrib_sparse;
+    A.contrib_normal = contrib_normal;
+    const bool contrib = contrib_sparse != nullptr;
     const size_t smem = fwd_smem(p.k);
     cudaError_t e = cudaMemsetAsync(&w.counters->q_fwd, 0, sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
-    auto k = p.stats ? render_fwd_kernel<true, false>
-                     : (record ? render_fwd_kernel<false, true> : render_fwd_kernel<false, false>);
+    auto k = contrib ? (record ? render_fwd_kernel<false, true, true> : render_fwd_kernel<false, false, true>)
+                     : p.stats ? render_fwd_kernel<true, false, false>
+                               : (record ? render_fwd_kernel<false, true, false> : render_fwd_kernel<false, false, false>);
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<persistent_grid(k, smem, p.total_tiles), TILE_PIX, smem, st>>>(A, p.total_tiles, rgb, T, last);
     return cudaGetLastError();

@@ -1,0 +1,72 @@
+"""Per-cell contributions (Sec. 4's L_sparse / L_normal / pruning terms) from
+pf_render_fwd_contrib against the FP64 oracle, and their telescoping
+identity at a larger size."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_24994_gb300 import inputs
+from tests.oracle_util import cluster_scene, f32
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2604_24994_gb300 import build
+    build.build()
+
+
+def gpu_contrib(sc, cams):
+    import torch
+    from paper_2604_24994_gb300 import DeviceScene, Renderer
+    ds = DeviceScene.from_numpy(sc, "cuda")
+    r = Renderer(ds.n, ds.k, cams)
+    r.bin(ds)
+    cs = torch.zeros(ds.n, device="cuda")
+    cn = torch.zeros(ds.n, device="cuda")
+    rgb, T, last = r.render_fwd(ds, contrib=(cs, cn))
+    rgb2, T2, last2 = r.render_fwd(ds)
+    torch.cuda.synchronize()
+    # the contributions change nothing else
+    assert torch.equal(rgb, rgb2) and torch.equal(T, T2) and torch.equal(last, last2)
+    return cs.double().cpu().numpy(), cn.double().cpu().numpy(), T.double().cpu().numpy()
+
+
+def check(got, ref, what):
+    # per cell: the per-pixel terms agree to ~1e-5; segments behind a pixel's
+    # early termination (T < 1e-6) are not counted by the GPU
+    err = np.abs(got - ref)
+    bound = 2e-4 * np.abs(ref) + 2e-5
+    assert np.all(err <= bound), (what, float(err.max()), int(np.argmax(err - bound)))
+
+
+def test_contributions_tiny_full_frame(tiny):
+    sc, cam = tiny
+    cs, cn, _ = gpu_contrib(sc, [cam])
+    sp, nm = oracle.Oracle(sc).contrib(cam)
+    assert (sp > 0).sum() > 100
+    check(cs, sp, "sparse")
+    check(cn, nm, "normal")
+
+
+def test_contributions_dense_cluster_two_views():
+    rng = np.random.default_rng(21)
+    sc = f32(cluster_scene(rng, n=60, spread=0.2, r=(0.05, 0.1), tex_std=0.2))
+    cams = [inputs.look_at((0.8, 0.3, 0.2), 40, 32, fov_y_deg=45), inputs.look_at((-0.6, 0.4, 0.5), 24, 36)]
+    cs, cn, _ = gpu_contrib(sc, cams)
+    orc = oracle.Oracle(sc)
+    sp = sum(orc.contrib(c)[0] for c in cams)
+    nm = sum(orc.contrib(c)[1] for c in cams)
+    check(cs, sp, "sparse")
+    check(cn, nm, "normal")
+
+
+def test_contributions_telescope_at_capture_scale():
+    """Per pixel sum_k T_k alpha_k = 1 - T_final, so the cells' L_sparse
+    terms sum to sum over pixels of (1 - T) of the same render."""
+    sc = inputs.capture_scene(100_000, seed=2, K=32)
+    cam = inputs.capture_camera(640, 360)
+    cs, cn, T = gpu_contrib(sc, [cam])
+    assert cs.sum() == pytest.approx((1.0 - T).sum(), rel=2e-5)
+    assert np.all(cn >= 0) and np.all(cn <= cs * (1 + 1e-5) + 1e-7)
