@@ -566,3 +566,43 @@ def test_contributions_of_an_isolated_cell_closed_form():
     sp2, nm2 = flipped.contrib(cam)
     assert sp2[0] == pytest.approx(sp[0], rel=1e-14)
     assert nm[0] + nm2[0] == pytest.approx(wq, rel=1e-12)
+
+
+# --------------------------------------- connectivity loss (Sec. 4, L_connect)
+
+def test_connect_two_spheres_closed_form():
+    """Two spheres at distance d with radii a, b: each lists the other, so
+    L = 2 (a + b - d)^2 while they overlap and 0 once they do not."""
+    from oracle.connect import connect
+    for d, a, b in ((1.0, 0.7, 0.6), (0.5, 0.1, 0.3), (2.0, 0.5, 0.5)):
+        pos = np.array([[0.0, 0.0, 0.0], [d, 0.0, 0.0]])
+        loss, gp, gR = connect(pos, [a, b], [[1], [0]])
+        o = max(a + b - d, 0.0)
+        np.testing.assert_allclose(loss, [o * o, o * o], rtol=1e-15)
+        np.testing.assert_allclose(gR, [4 * o, 4 * o], rtol=1e-15)
+        # moving sphere 0 towards sphere 1 (+x) deepens the overlap
+        np.testing.assert_allclose(gp[0], [4 * o, 0, 0], rtol=1e-15, atol=0)
+        np.testing.assert_allclose(gp[1], [-4 * o, 0, 0], rtol=1e-15, atol=0)
+
+
+def test_connect_gradient_matches_central_differences():
+    from oracle.connect import connect
+    rng = np.random.default_rng(5)
+    n = 12
+    pos = rng.uniform(-0.5, 0.5, (n, 3))
+    R = rng.uniform(0.2, 0.5, n)
+    nbr = np.array([[j for j in range(n) if j != i][:6] for i in range(n)])
+    _, gp, gR = connect(pos, R, nbr)
+    h = 1e-6
+    for i in range(n):
+        for c in range(3):
+            p1, p2 = pos.copy(), pos.copy()
+            p1[i, c] += h
+            p2[i, c] -= h
+            fd = (connect(p1, R, nbr)[0].sum() - connect(p2, R, nbr)[0].sum()) / (2 * h)
+            assert fd == pytest.approx(gp[i, c], rel=1e-6, abs=1e-9)
+        r1, r2 = R.copy(), R.copy()
+        r1[i] += h
+        r2[i] -= h
+        fd = (connect(pos, r1, nbr)[0].sum() - connect(pos, r2, nbr)[0].sum()) / (2 * h)
+        assert fd == pytest.approx(gR[i], rel=1e-6, abs=1e-9)
