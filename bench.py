@@ -318,6 +318,18 @@ def run_ours(args):
             ct.append(a.elapsed_time(b))
     ms_render_contrib = float(np.mean(ct))
     del contrib
+    # the connectivity loss and its gradient over the neighbour lists
+    from paper_2604_24994_gb300.api import connect_loss
+    cc = []
+    for it in range(W + K):
+        a, b = ev(), ev()
+        a.record(stream)
+        connect_loss(ds)
+        b.record(stream)
+        b.synchronize()
+        if it >= W:
+            cc.append(a.elapsed_time(b))
+    ms_connect = float(np.mean(cc))
 
     # end to end through the public API with host buffers: camera in, image out
     host_rgb = torch.empty((r.plan.pixels, 3), dtype=torch.float32, pin_memory=True)
@@ -361,6 +373,7 @@ def run_ours(args):
         "fwd_fps": ws * 1000.0 / ms_fwd, "fwd_bwd_fps": ws * 1000.0 / ms_train, "ms_fwd_bwd": ms_train,
         "ms_render_fwd_kernel": ms_render,
         "ms_render_fwd_contrib_kernel": ms_render_contrib,
+        "ms_connect_loss_and_grad": ms_connect,
         "work": stats,
         "roofline": {"bound": "alu", "kernel": "render_fwd_kernel", "achieved": achieved, "peak": peak_tflops,
                      "unit": "TFLOP/s", "frac": achieved / peak_tflops,

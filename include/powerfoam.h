@@ -205,6 +205,17 @@ pf_status pf_render_bwd(const pf_scene *scene, pf_plan *plan, void *ws, const fl
                         const float *T, const uint32_t *last, const pf_scene_grad *grad, void *stream);
 
 /*
+ * Connectivity loss of Sec. 4 / appendix (L_connect) over the neighbour
+ * lists, which stand in for the Cech adjacency (pairs whose bounding spheres
+ * do not overlap add nothing):
+ *   loss[i] = sum_{j in nbr(i)} max(R_i + R_j - |p_i - p_j|, 0)^2     (written)
+ * With grad_pos [N,3] and grad_R [N] (both or neither) it ADDS the gradient
+ * of sum_i loss[i] with respect to the sites and the bound radii.  Uses only
+ * pos, R, nbr, n_cells and k_nbr of the scene; device pointers; no plan.
+ */
+pf_status pf_connect(const pf_scene *scene, float *loss, float *grad_pos, float *grad_R, void *stream);
+
+/*
  * Copy the binning results to HOST buffers (synchronises `stream`), for
  * inspection and tests.  tile_start [T+1] (T = tiles over all views, view v
  * first at its tile base, row-major tiles of 16x16 px): tile t's list is

@@ -66,6 +66,7 @@ def _sig(lib):
         "pf_bin_sort": ([V, V, P(U64), V], st),
         "pf_render_fwd": ([P(Scene), V, V, V, V, V, V], st),
         "pf_render_fwd_contrib": ([P(Scene), V, V, V, V, V, V, V, V], st),
+        "pf_connect": ([P(Scene), V, V, V, V], st),
         "pf_render_bwd": ([P(Scene), V, V, V, V, V, V, P(SceneGrad), V], st),
         "pf_read_bins": ([V, V, V, V, V, V, V], st),
     }

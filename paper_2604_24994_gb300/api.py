@@ -53,6 +53,19 @@ class DeviceScene:
         return s
 
 
+def connect_loss(scene: DeviceScene, grad: bool = True):
+    """pf_connect: the per-cell connectivity loss [N] (Sec. 4, L_connect over
+    the neighbour lists) and, if grad, the gradients (dL/dpos [N,3], dL/dR [N])
+    of its sum; otherwise (loss, None, None)."""
+    p = scene.params
+    loss = torch.empty(scene.n, dtype=torch.float32, device=p["pos"].device)
+    gp = torch.zeros_like(p["pos"]) if grad else None
+    gR = torch.zeros_like(p["R"]) if grad else None
+    check(lib().pf_connect(C.byref(scene.struct()), loss.data_ptr(), gp.data_ptr() if grad else None,
+                           gR.data_ptr() if grad else None, _stream()), "pf_connect")
+    return loss, gp, gR
+
+
 class Plan:
     """A C plan (layout + cameras) with its device workspace."""
 

@@ -424,6 +424,19 @@ pf_status pf_render_bwd(const pf_scene *scene, pf_plan *p, void *ws, const float
         "pf_render_bwd");
 }
 
+pf_status pf_connect(const pf_scene *scene, float *loss, float *grad_pos, float *grad_R, void *stream) {
+    g_err[0] = 0;
+    if (!scene || !loss || scene->n_cells < 0 || scene->k_nbr < 0 || (!grad_pos) != (!grad_R)) {
+        set_error("pf_connect: invalid argument");
+        return PF_ERR_INVALID_ARG;
+    }
+    if (scene->n_cells > 0 && (!scene->pos || !scene->R || (scene->k_nbr > 0 && !scene->nbr))) {
+        set_error("pf_connect: null scene pointer");
+        return PF_ERR_INVALID_ARG;
+    }
+    return cuda_status(launch_connect(*scene, loss, grad_pos, grad_R, (cudaStream_t)stream), "pf_connect");
+}
+
 pf_status pf_read_bins(pf_plan *p, void *ws, uint32_t *tile_start, uint32_t *cells, uint64_t *keys,
                        uint16_t *rects, void *stream) {
     g_err[0] = 0;

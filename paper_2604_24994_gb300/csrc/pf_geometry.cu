@@ -274,6 +274,55 @@ __global__ void __launch_bounds__(256) project_kernel(pf_scene s, const ViewDev 
     cnt_out[idx] = count;
 }
 
+// Connectivity loss (Sec. 4, L_connect) over the neighbour lists: per cell
+// sum_j max(R_i + R_j - |p_i - p_j|, 0)^2, and, when asked, the gradient of
+// the sum over cells: with o = R_i + R_j - d > 0, dR_i = dR_j = 2 o and
+// dp_i = -dp_j = 2 o (p_j - p_i) / d.  One thread per cell; the neighbour
+// side goes through atomics.
+__global__ void __launch_bounds__(256) connect_kernel(pf_scene s, float *__restrict__ loss, float *__restrict__ gpos,
+                                                      float *__restrict__ gR) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s.n_cells) return;
+    const int K = s.k_nbr;
+    const float px = s.pos[3 * i], py = s.pos[3 * i + 1], pz = s.pos[3 * i + 2], Ri = s.R[i];
+    float li = 0.f, gx = 0.f, gy = 0.f, gz = 0.f, gr = 0.f;
+    for (int k = 0; k < K; k++) {
+        const int j = s.nbr[(int64_t)i * K + k];
+        if (j < 0 || j >= s.n_cells || j == i) continue;
+        const float ax = s.pos[3 * j] - px, ay = s.pos[3 * j + 1] - py, az = s.pos[3 * j + 2] - pz;
+        const float d = sqrtf(ax * ax + ay * ay + az * az);
+        const float o = Ri + s.R[j] - d;
+        if (!(o > 0.0f)) continue;
+        li += o * o;
+        if (gpos) {
+            gr += 2.0f * o;
+            atomicAdd(gR + j, 2.0f * o);
+            if (d > 0.0f) {
+                const float f = 2.0f * o / d;
+                gx += f * ax;
+                gy += f * ay;
+                gz += f * az;
+                atomicAdd(gpos + 3 * j, -f * ax);
+                atomicAdd(gpos + 3 * j + 1, -f * ay);
+                atomicAdd(gpos + 3 * j + 2, -f * az);
+            }
+        }
+    }
+    loss[i] = li;
+    if (gpos) {
+        atomicAdd(gR + i, gr);
+        atomicAdd(gpos + 3 * i, gx);
+        atomicAdd(gpos + 3 * i + 1, gy);
+        atomicAdd(gpos + 3 * i + 2, gz);
+    }
+}
+
+cudaError_t launch_connect(const pf_scene &s, float *loss, float *gpos, float *gR, cudaStream_t st) {
+    if (s.n_cells == 0) return cudaSuccess;
+    connect_kernel<<<(s.n_cells + 255) / 256, 256, 0, st>>>(s, loss, gpos, gR);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_prepare(const pf_scene &s, const Plan &p, const WS &w, cudaStream_t st) {
     if (p.n == 0) return cudaSuccess;
     const int threads = 256;

@@ -180,6 +180,7 @@ void make_layout(Plan *p);                        // workspace offsets
 
 // kernels launched from the C API (defined in the .cu files)
 cudaError_t launch_prepare(const pf_scene &s, const Plan &p, const WS &w, cudaStream_t st);
+cudaError_t launch_connect(const pf_scene &s, float *loss, float *gpos, float *gR, cudaStream_t st);
 cudaError_t launch_project(const pf_scene &s, const Plan &p, const WS &w, cudaStream_t st);
 cudaError_t launch_bin_sort(const Plan &p, const WS &w, cudaStream_t st);
 cudaError_t launch_render_fwd(const pf_scene &s, const Plan &p, const WS &w, float *rgb, float *T, uint32_t *last,

@@ -70,3 +70,23 @@ def test_contributions_telescope_at_capture_scale():
     cs, cn, T = gpu_contrib(sc, [cam])
     assert cs.sum() == pytest.approx((1.0 - T).sum(), rel=2e-5)
     assert np.all(cn >= 0) and np.all(cn <= cs * (1 + 1e-5) + 1e-7)
+
+
+def test_connect_loss_matches_oracle():
+    """pf_connect (Sec. 4's L_connect over the neighbour lists) against the
+    FP64 loops of oracle.connect: per-cell loss and the gradient of the sum."""
+    import torch
+    from oracle.connect import connect
+    from paper_2604_24994_gb300 import DeviceScene, connect_loss
+    sc = inputs.capture_scene(5_000, seed=7, K=16)
+    ds = DeviceScene.from_numpy(sc, "cuda")
+    loss, gp, gR = connect_loss(ds)
+    torch.cuda.synchronize()
+    l0, gp0, gR0 = connect(sc.pos, sc.R, sc.nbr)
+    assert (l0 > 0).sum() > 1000
+    np.testing.assert_allclose(loss.double().cpu().numpy(), l0, rtol=2e-4, atol=1e-9 * l0.max())
+    for got, ref in ((gp, gp0), (gR, gR0)):
+        g = got.double().cpu().numpy()
+        assert np.linalg.norm(g - ref) <= 1e-4 * np.linalg.norm(ref)
+    loss2, none1, none2 = connect_loss(ds, grad=False)
+    assert none1 is None and torch.equal(loss, loss2)
