@@ -896,6 +896,10 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
         if ((unsigned long long)last > e - s) last = (int)(e - s);
         if (MASKS) nrec = (int)A.w.hitcount[pix];
     }
+    // the record of the next hit this lane meets (ordinal nrec - 1), loaded
+    // one hit ahead so that its latency hides behind the current one
+    unsigned kk_next = 0xffffu;
+    if (MASKS && nrec > 0 && nrec - 1 < HIT_CAP) kk_next = A.w.hitkind[pix * HIT_CAP + nrec - 1];
     atomicMax(&s_maxlast, last);
     __syncthreads();
     const int maxlast = s_maxlast;
@@ -946,7 +950,11 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
             if (MASKS) {
                 // the forward recorded this hit's active constraints: no plane loop
                 unsigned kk = 0xffffu;
-                if (mine && --nrec < HIT_CAP) kk = A.w.hitkind[pix * HIT_CAP + nrec];
+                if (mine) {
+                    kk = kk_next;
+                    --nrec;
+                    kk_next = nrec > 0 && nrec - 1 < HIT_CAP ? A.w.hitkind[pix * HIT_CAP + nrec - 1] : 0xffffu;
+                }
                 if (mine && sphere_chord<true>(cr, vr, ray, ch, cand)) {
                     if (kk != 0xffffu)
                         hit = segment_from_kinds<true>(cr, vr, s_pl + o, A.w.planes_lo + (int64_t)cell * A.K, ray,
