@@ -146,6 +146,25 @@ __global__ void __launch_bounds__(256) prepare_kernel(pf_scene s, const float4 *
     }
     if (!empty) cnt = drop_implied_planes(planes + (int64_t)i * K, planes_lo + (int64_t)i * K,
                                           plane_nb + (int64_t)i * K, cnt, make_float4(nx, ny, nz, s.offset[i]), Rf);
+    // nearest planes first: they cut the most of the ball, so a warp whose
+    // segments all become empty stops the plane loop earliest
+    {
+        float4 *P = planes + (int64_t)i * K, *PL = planes_lo + (int64_t)i * K;
+        int2 *NB = plane_nb + (int64_t)i * K;
+        for (int a = 1; a < cnt; a++) {
+            const float4 p = P[a], pl = PL[a];
+            const int2 nb = NB[a];
+            int b = a - 1;
+            for (; b >= 0 && P[b].w > p.w; b--) {
+                P[b + 1] = P[b];
+                PL[b + 1] = PL[b];
+                NB[b + 1] = NB[b];
+            }
+            P[b + 1] = p;
+            PL[b + 1] = pl;
+            NB[b + 1] = nb;
+        }
+    }
     cellnp[i] = cnt;
     float4 *cr = reinterpret_cast<float4 *>(cellrec + (int64_t)i * CELLREC_F);
     cr[0] = make_float4(nx, ny, nz, s.offset[i]);

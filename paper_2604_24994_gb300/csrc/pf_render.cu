@@ -32,6 +32,7 @@ struct Seg {
     float3 q;               // closest-approach offset from p_i
     float dnd;              // d . n (selects the texture end)
     int refined;            // ends recomputed in FP64
+    int nplanes;            // radical planes evaluated (the warp may stop early)
 };
 
 enum : int { K_SPHERE = -1, K_CAMERA = -2, K_FACE = -3 };
@@ -198,7 +199,7 @@ template <bool GRAD>
 __device__ __forceinline__ bool clip_chord(const float *__restrict__ cr, const float *__restrict__ vr,
                                            const float4 *__restrict__ pl, int np,
                                            const float4 *__restrict__ lo_glob, const Ray &ray, const Chord &ch,
-                                           Seg &sg) {
+                                           Seg &sg, unsigned lanes = 0u) {
     const float3 dh = ray.dh, q = ch.q;
     const float R = cr[CR_R];
     const float sig = cr[CR_SIG];
@@ -209,48 +210,59 @@ __device__ __forceinline__ bool clip_chord(const float *__restrict__ cr, const f
         ka = K_CAMERA;
     }
     sg.refined = ch.refined;
-    // Radical planes, branch free: a plane bounds s from below when d.a < 0
-    // (sign bit, so -0 counts as below) and from above otherwise.  With
-    // d.a = +-0 the quotient is +-inf or NaN: it moves no end unless num < 0
-    // (the ray runs outside the plane), which empties the segment.
-#pragma unroll 2
-    for (int k = 0; k < np; k++) {
-        const float4 P = pl[k];
-        const float3 a = f3(P.x, P.y, P.z);
-        const float num = P.w - dot3(q, a);
-        const float den = dot3(dh, a);
-        const float t = num * rcp_approx(den);
-        const bool ent = __float_as_int(den) < 0;
-        const bool ua = ent && t > sa;
-        const bool ub = !ent && t < sb;
-        sa = ua ? t : sa;
-        ka = ua ? k : ka;
-        sb = ub ? t : sb;
-        kb = ub ? k : kb;
-    }
-    // d.a of the planes at the ends (+inf for sphere / camera ends); a cell
-    // without planes reads some other slot of the batch and discards it
-    const float4 Pa = pl[max(ka, 0)], Pb = pl[max(kb, 0)];
-    float dena = ka >= 0 ? dot3(dh, f3(Pa.x, Pa.y, Pa.z)) : CUDART_INF_F;
-    float denb = kb >= 0 ? dot3(dh, f3(Pb.x, Pb.y, Pb.z)) : CUDART_INF_F;
+    // the dipole's dense half n.y <= offset first (it removes about half of
+    // the ball): a bound from below when d.n < 0 (sign bit, so -0 counts as
+    // below), from above otherwise; d.n = +-0 gives +-inf or NaN, which moves
+    // no end unless the ray runs outside the half (num < 0): then it empties
+    // the segment
+    float fden;
     {
-        // the dipole's dense half n.y <= offset, the same way
         const float3 n = f3(cr[CR_N], cr[CR_N + 1], cr[CR_N + 2]);
         const float num = cr[CR_OFF] - dot3(q, n);
-        const float den = dot3(dh, n);
-        const float t = num * rcp_approx(den);
-        const bool ent = __float_as_int(den) < 0;
+        fden = dot3(dh, n);
+        const float t = num * rcp_approx(fden);
+        const bool ent = __float_as_int(fden) < 0;
         const bool ua = ent && t > sa;
         const bool ub = !ent && t < sb;
         sa = ua ? t : sa;
         ka = ua ? K_FACE : ka;
-        dena = ua ? den : dena;
         sb = ub ? t : sb;
         kb = ub ? K_FACE : kb;
-        denb = ub ? den : denb;
-        sg.dnd = den;
-        if (fabsf(den) < 0x1p-20f) sg.dnd = face_side64(cr, ray);
+        sg.dnd = fden;
+        if (fabsf(fden) < 0x1p-20f) sg.dnd = face_side64(cr, ray);
     }
+    // Radical planes the same way, branch free, nearest first (prepare sorts
+    // them by distance).  With `lanes` (the lanes that run this call) the
+    // warp stops once every one of them has an empty segment.
+    int k = 0;
+    for (; k < np; k += 2) {
+#pragma unroll
+        for (int u = 0; u < 2; u++) {
+            if (u == 1 && k + 1 >= np) break;
+            const float4 P = pl[k + u];
+            const float3 a = f3(P.x, P.y, P.z);
+            const float num = P.w - dot3(q, a);
+            const float den = dot3(dh, a);
+            const float t = num * rcp_approx(den);
+            const bool ent = __float_as_int(den) < 0;
+            const bool ua = ent && t > sa;
+            const bool ub = !ent && t < sb;
+            sa = ua ? t : sa;
+            ka = ua ? k + u : ka;
+            sb = ub ? t : sb;
+            kb = ub ? k + u : kb;
+        }
+        if (lanes && !__any_sync(lanes, sb > sa)) {
+            k += 2;
+            break;
+        }
+    }
+    sg.nplanes = min(k, np);
+    // d.a of the constraints at the ends (+inf for sphere / camera ends); a
+    // cell without planes reads some other slot of the batch and discards it
+    const float4 Pa = pl[max(ka, 0)], Pb = pl[max(kb, 0)];
+    float dena = ka >= 0 ? dot3(dh, f3(Pa.x, Pa.y, Pa.z)) : (ka == K_FACE ? fden : CUDART_INF_F);
+    float denb = kb >= 0 ? dot3(dh, f3(Pb.x, Pb.y, Pb.z)) : (kb == K_FACE ? fden : CUDART_INF_F);
     if (!(sb > sa)) return false;
     // near-parallel plane or face at an end: recompute that end in FP64
     const float lim = PLANE_ERR * sig * (1.0f / REFINE_EPS);
@@ -651,7 +663,7 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, i
                 np = sg.poff(buf)[j + 1] - o;
                 if (pass)
                     hit = clip_chord<false>(cr, vr, sg.pl(buf) + o, np, A.w.planes_lo + (int64_t)sg.ids(buf)[j] * A.K,
-                                            ray, ch, seg);
+                                            ray, ch, seg, pm);
             }
             if (STATS && !done) {
                 const unsigned act = __ballot_sync(__activemask(), true);
@@ -659,7 +671,7 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, i
                 const unsigned cm = __ballot_sync(act, cand), hm = __ballot_sync(act, hit);
                 st_cand++;
                 st_pass += cand;
-                st_pl += pass ? np : 0;
+                st_pl += pass ? seg.nplanes : 0;
                 st_ref += pass ? (hit ? seg.refined : ch.refined) : 0;
                 st_hit += hit;
                 st_wcand += l0;
