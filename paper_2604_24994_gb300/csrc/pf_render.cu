@@ -234,7 +234,7 @@ __device__ __forceinline__ bool clip_chord(const float *__restrict__ cr, const f
     // Radical planes the same way, branch free, nearest first (prepare sorts
     // them by distance).  With `lanes` (the lanes that run this call) the
     // warp stops once every one of them has an empty segment.
-    int k = 0;
+    int k = (lanes && !__any_sync(lanes, sb > sa)) ? np : 0;  // the face alone may empty them all
     for (; k < np; k += 2) {
 #pragma unroll
         for (int u = 0; u < 2; u++) {
