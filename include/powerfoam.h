@@ -80,7 +80,11 @@ typedef struct {
     uint64_t instances; /* (cell, tile) pairs after binning */
     uint64_t candidates; /* (pixel, listed cell) pairs examined */
     uint64_t hits;       /* non-empty (pixel, cell) segments */
-    uint64_t planes;     /* radical-plane clips evaluated */
+    uint64_t planes;     /* radical-plane clips each ray needs on its own: per
+                          * sphere pass, the planes up to the one that empties
+                          * its segment (all of them if none does); the warp
+                          * evaluates more, since it stops only when every
+                          * lane's segment is empty */
     uint64_t refined;    /* segment ends recomputed in FP64 */
     uint64_t sphere_pass; /* candidates that passed the sphere test */
     /* the same events counted once per warp (32 pixels) that had at least

@@ -194,8 +194,10 @@ __device__ __forceinline__ bool sphere_chord(const float *__restrict__ cr, const
 }
 
 // Clip the chord with the cell's radical planes pl[0..np), the dipole face,
-// then refine near-parallel ends.  False if the segment is empty.
-template <bool GRAD>
+// then refine near-parallel ends.  False if the segment is empty.  NEED sets
+// sg.nplanes to the planes this ray needs on its own (up to the one that
+// empties its segment) instead of the planes the warp evaluated.
+template <bool GRAD, bool NEED = false>
 __device__ __forceinline__ bool clip_chord(const float *__restrict__ cr, const float *__restrict__ vr,
                                            const float4 *__restrict__ pl, int np,
                                            const float4 *__restrict__ lo_glob, const Ray &ray, const Chord &ch,
@@ -234,11 +236,12 @@ __device__ __forceinline__ bool clip_chord(const float *__restrict__ cr, const f
     // Radical planes the same way, branch free, nearest first (prepare sorts
     // them by distance).  With `lanes` (the lanes that run this call) the
     // warp stops once every one of them has an empty segment.
+    int need = (NEED && !(sb > sa)) ? 0 : np;
     int k = (lanes && !__any_sync(lanes, sb > sa)) ? np : 0;  // the face alone may empty them all
-    for (; k < np; k += 2) {
+    for (; k < np; k += 4) {
 #pragma unroll
-        for (int u = 0; u < 2; u++) {
-            if (u == 1 && k + 1 >= np) break;
+        for (int u = 0; u < 4; u++) {
+            if (u >= 1 && k + u >= np) break;
             const float4 P = pl[k + u];
             const float3 a = f3(P.x, P.y, P.z);
             const float num = P.w - dot3(q, a);
@@ -251,13 +254,14 @@ __device__ __forceinline__ bool clip_chord(const float *__restrict__ cr, const f
             ka = ua ? k + u : ka;
             sb = ub ? t : sb;
             kb = ub ? k + u : kb;
+            if (NEED && need == np && !(sb > sa)) need = k + u + 1;
         }
         if (lanes && !__any_sync(lanes, sb > sa)) {
-            k += 2;
+            k += 4;
             break;
         }
     }
-    sg.nplanes = min(k, np);
+    sg.nplanes = NEED ? need : min(k, np);
     // d.a of the constraints at the ends (+inf for sphere / camera ends); a
     // cell without planes reads some other slot of the batch and discards it
     const float4 Pa = pl[max(ka, 0)], Pb = pl[max(kb, 0)];
@@ -662,8 +666,8 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, i
                 const int o = sg.poff(buf)[j];
                 np = sg.poff(buf)[j + 1] - o;
                 if (pass)
-                    hit = clip_chord<false>(cr, vr, sg.pl(buf) + o, np, A.w.planes_lo + (int64_t)sg.ids(buf)[j] * A.K,
-                                            ray, ch, seg, pm);
+                    hit = clip_chord<false, STATS>(cr, vr, sg.pl(buf) + o, np,
+                                                   A.w.planes_lo + (int64_t)sg.ids(buf)[j] * A.K, ray, ch, seg, pm);
             }
             if (STATS && !done) {
                 const unsigned act = __ballot_sync(__activemask(), true);
