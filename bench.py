@@ -330,6 +330,21 @@ def run_ours(args):
         if it >= W:
             cc.append(a.elapsed_time(b))
     ms_connect = float(np.mean(cc))
+    # the neighbour lists of the same scene built on the GPU (pf_build_neighbours)
+    from paper_2604_24994_gb300.api import build_neighbours
+    pw, Rin = ds.params["pos"], ds.params["R"]
+    nt = []
+    for it in range(W + K):
+        a, b = ev(), ev()
+        a.record(stream)
+        nb_gpu, R_gpu, _ = build_neighbours(pw, ds.params["w"], Rin, ds.k)
+        b.record(stream)
+        b.synchronize()
+        if it >= W:
+            nt.append(a.elapsed_time(b))
+    ms_neighbours = float(np.mean(nt))
+    nbr_same = bool(torch.equal(nb_gpu.cpu(), torch.from_numpy(sc.nbr)))
+    del nb_gpu, R_gpu
 
     # end to end through the public API with host buffers: camera in, image out
     host_rgb = torch.empty((r.plan.pixels, 3), dtype=torch.float32, pin_memory=True)
@@ -374,6 +389,8 @@ def run_ours(args):
         "ms_render_fwd_kernel": ms_render,
         "ms_render_fwd_contrib_kernel": ms_render_contrib,
         "ms_connect_loss_and_grad": ms_connect,
+        "ms_build_neighbours": ms_neighbours,
+        "neighbours_equal_input_lists": nbr_same,
         "work": stats,
         "roofline": {"bound": "alu", "kernel": "render_fwd_kernel", "achieved": achieved, "peak": peak_tflops,
                      "unit": "TFLOP/s", "frac": achieved / peak_tflops,

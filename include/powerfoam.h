@@ -319,6 +319,36 @@ void pf_serve_destroy(pf_server *srv);
 pf_status pf_render_fwd_static(const pf_scene *scene, const pf_camera *cam, float *rgb, float *T, uint32_t *last,
                                void *stream);
 
+/*
+ * Neighbour lists on the GPU, the step before rendering that the paper does
+ * with GPU collision detection over the bounding spheres (Sec. 3.3, the Cech
+ * graph).  For cell i, with t_ij the signed distance from p_i of the radical
+ * plane between sites i and j (Sec. 3.2, Eq. power bisector),
+ *   t_ij = (|p_j - p_i|^2 + w_i - w_j) / (2 |p_j - p_i|)   (no plane if p_j == p_i),
+ * nbr[i] lists the K sites j != i with the smallest t_ij, ascending, equal
+ * values by ascending j, -1 after the last one when fewer than K exist; and
+ * R_out[i] = R_in[i], except R_out[i] = the largest float <= max(t_(K+1), 0)
+ * when the (K+1)-th smallest t_(K+1) < R_in[i] (so that no site left out can
+ * cut the cell's sphere; t is evaluated in FP64 from the float inputs exactly
+ * as written above: dx*dx + dy*dy, + dz*dz; sqrt; ((L^2 + w_i) - w_j) / (2L)).
+ *
+ * pos [N][3], w [N], R_in [N]: device, float32, finite.  nbr [N][K] int32
+ * and R_out [N] float32: device, written (R_out may be R_in).  n_clipped and
+ * status: device uint32, optional (NULL): the number of clipped radii, and 0
+ * or 1 if a tree walk ran out of stack or steps (the lists may then be incomplete;
+ * not expected below PF_NEIGHBOURS_MAX_CELLS).  ws: device workspace of at
+ * least pf_neighbours_workspace_bytes(N) bytes (about 116 bytes per cell),
+ * owned by the caller.  0 <= N <= PF_NEIGHBOURS_MAX_CELLS, 0 <= K <= 64,
+ * otherwise PF_ERR_INVALID_ARG; a small workspace gives PF_ERR_CAPACITY.
+ * Asynchronous on `stream`, no allocation, no host synchronisation (stream
+ * capture is allowed).
+ */
+#define PF_NEIGHBOURS_MAX_CELLS (1 << 28)
+uint64_t pf_neighbours_workspace_bytes(int32_t n_cells);
+pf_status pf_build_neighbours(const float *pos, const float *w, const float *R_in, int32_t n_cells, int32_t k_nbr,
+                              int32_t *nbr, float *R_out, uint32_t *n_clipped, uint32_t *status, void *ws,
+                              uint64_t ws_bytes, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

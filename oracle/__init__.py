@@ -86,7 +86,33 @@ def lib():
                                            C.c_int]
             _lib.orc_bin.argtypes = [P(_Camera), C.c_int64, P(d), P(d), P(d),
                                      P(C.c_int32), P(C.c_uint64)]
+            f = C.c_float
+            _lib.orc_neighbours.argtypes = [P(f), P(f), P(f), C.c_int64, C.c_int32, C.c_int64, P(C.c_int64),
+                                            P(C.c_int32), P(f), C.c_int]
         return _lib
+
+
+def neighbours(pos, w, R, k: int, cells=None, nthreads: int = 0):
+    """Brute-force neighbour lists (orc_neighbours): for each cell in `cells`
+    (default: all), the k sites with the smallest radical-plane distance
+    t_ij (ties by j, -1 padded) and the clipped bound radius.  Returns
+    (nbr int32 [m, k], R float32 [m])."""
+    pos = np.ascontiguousarray(pos, np.float32)
+    w = np.ascontiguousarray(w, np.float32)
+    R = np.ascontiguousarray(R, np.float32)
+    n = pos.shape[0]
+    if cells is None:
+        m, cp = n, None
+    else:
+        cells = np.ascontiguousarray(cells, np.int64)
+        m, cp = cells.shape[0], _ptr(cells, C.c_int64)
+    nbr = np.empty((m, k), np.int32)
+    Ro = np.empty(m, np.float32)
+    rc = lib().orc_neighbours(_ptr(pos, C.c_float), _ptr(w, C.c_float), _ptr(R, C.c_float), n, k, m, cp,
+                              _ptr(nbr, C.c_int32), _ptr(Ro, C.c_float), nthreads)
+    if rc != 0:
+        raise ValueError("orc_neighbours: invalid k")
+    return nbr, Ro
 
 
 def _ptr(a, ct):

@@ -769,3 +769,71 @@ int orc_bin(const orc_camera *cam, int64_t n, const double *pos, const double *w
     for (int64_t i = 0; i < n; i++) orc_bin_cell(cam, pos, w, R, i, &rect[4 * i], &key[i]);
     return 0;
 }
+
+/*
+ * Neighbour lists (the radical planes of Sec. 3.2, Eq. power_bisector, read
+ * as above): the signed distance from p_i of the plane between sites i and j
+ * is t_ij = (|a|^2 + w_i - w_j) / (2|a|), a = p_j - p_i (no plane when
+ * a = 0).  For each listed cell i: the K sites j != i with the smallest
+ * t_ij, ascending, equal values by ascending j, -1 after the last; and the
+ * bound radius, clipped to the largest float <= max(t_(K+1), 0) when the
+ * (K+1)-th smallest value t_(K+1) is below R_i (every site left out then
+ * has its plane outside the sphere).  Brute force over all sites; t in
+ * double from the float inputs as written, left to right, no contraction.
+ * cells: NULL for all n cells in order, else ncells indices; nbr
+ * [ncells][k], R_out [ncells].
+ */
+int orc_neighbours(const float *pos, const float *w, const float *R, int64_t n, int32_t k, int64_t ncells,
+                   const int64_t *cells, int32_t *nbr, float *R_out, int nthreads) {
+    if (k < 0) return -1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+#endif
+    {
+        double *bt = malloc(((size_t)k + 1) * sizeof(double));
+        int64_t *bj = malloc(((size_t)k + 1) * sizeof(int64_t));
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 16)
+#endif
+        for (int64_t q = 0; q < ncells; q++) {
+            const int64_t i = cells ? cells[q] : q;
+            int m = 0;
+            for (int64_t j = 0; j < n; j++) {
+                if (j == i) continue;
+                double dx = (double)pos[3 * j] - (double)pos[3 * i];
+                double dy = (double)pos[3 * j + 1] - (double)pos[3 * i + 1];
+                double dz = (double)pos[3 * j + 2] - (double)pos[3 * i + 2];
+                double L2 = dx * dx + dy * dy + dz * dz;
+                if (!(L2 > 0.0)) continue;
+                double L = sqrt(L2);
+                double t = (L2 + (double)w[i] - (double)w[j]) / (2.0 * L);
+                if (!(t < INFINITY)) continue;
+                /* keep the k+1 smallest (t, j) in ascending order */
+                if (m == k + 1 && !(t < bt[k] || (t == bt[k] && j < bj[k]))) continue;
+                int p = m < k + 1 ? m++ : k;
+                while (p > 0 && (bt[p - 1] > t || (bt[p - 1] == t && bj[p - 1] > j))) {
+                    bt[p] = bt[p - 1];
+                    bj[p] = bj[p - 1];
+                    p--;
+                }
+                bt[p] = t;
+                bj[p] = j;
+            }
+            for (int r = 0; r < k; r++) nbr[q * k + r] = r < m ? (int32_t)bj[r] : -1;
+            double tk1 = m == k + 1 ? bt[k] : INFINITY;
+            float Ri = R[i];
+            if (tk1 < (double)Ri) {
+                double x = tk1 > 0.0 ? tk1 : 0.0;
+                float f = (float)x;
+                if ((double)f > x) f = nextafterf(f, 0.0f);
+                R_out[q] = f;
+            } else {
+                R_out[q] = Ri;
+            }
+        }
+        free(bt);
+        free(bj);
+    }
+    return 0;
+}

@@ -6,7 +6,8 @@ continuous-batching server behind a C ABI (include/powerfoam.h).
 """
 from . import inputs  # noqa: F401
 
-__all__ = ["inputs", "DeviceScene", "Renderer", "RenderFunction", "render", "connect_loss", "build_library"]
+__all__ = ["inputs", "DeviceScene", "Renderer", "RenderFunction", "render", "connect_loss", "build_neighbours",
+           "build_library"]
 
 
 def build_library(force: bool = False) -> str:
@@ -15,7 +16,7 @@ def build_library(force: bool = False) -> str:
 
 
 def __getattr__(name):
-    if name in ("DeviceScene", "Renderer", "RenderFunction", "render", "Plan", "connect_loss"):
+    if name in ("DeviceScene", "Renderer", "RenderFunction", "render", "Plan", "connect_loss", "build_neighbours"):
         from . import api
         return getattr(api, name)
     raise AttributeError(name)

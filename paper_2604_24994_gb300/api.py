@@ -66,6 +66,32 @@ def connect_loss(scene: DeviceScene, grad: bool = True):
     return loss, gp, gR
 
 
+def build_neighbours(pos, w, R, k: int, out_R=None):
+    """pf_build_neighbours: per cell the k sites with the smallest
+    radical-plane distance t_ij = (|p_j - p_i|^2 + w_i - w_j) / (2|p_j - p_i|)
+    (Sec. 3.2; ties by j, -1 padded) and R clipped below t_(k+1).  pos [N,3],
+    w [N], R [N]: float32 CUDA tensors.  Returns (nbr int32 [N,k], R_out
+    float32 [N] (out_R if given; it may be R), n_clipped int)."""
+    n = int(pos.shape[0])
+    dev = pos.device
+    for t in (pos, w, R):
+        if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
+            raise ValueError("build_neighbours: float32 contiguous CUDA tensors expected")
+    nbr = torch.empty((n, k), dtype=torch.int32, device=dev)
+    R_out = torch.empty_like(R) if out_R is None else out_R
+    ws_bytes = int(lib().pf_neighbours_workspace_bytes(n))
+    ws = torch.empty(max(ws_bytes, 256), dtype=torch.uint8, device=dev)
+    info = torch.zeros(2, dtype=torch.int32, device=dev)  # n_clipped, status
+    check(lib().pf_build_neighbours(pos.data_ptr(), w.data_ptr(), R.data_ptr(), n, k,
+                                    nbr.data_ptr() if k > 0 else None, R_out.data_ptr(), info.data_ptr(),
+                                    info.data_ptr() + 4, ws.data_ptr(), ws_bytes, _stream()),
+          "pf_build_neighbours")
+    ncl, status = (int(x) for x in info.cpu())
+    if status:
+        raise RuntimeError("pf_build_neighbours: a tree walk ran out of stack or steps")
+    return nbr, R_out, ncl
+
+
 class Plan:
     """A C plan (layout + cameras) with its device workspace."""
 

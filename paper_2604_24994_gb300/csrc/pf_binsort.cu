@@ -136,8 +136,8 @@ __global__ void __launch_bounds__(SCAN_T) scan_add_kernel(uint32_t *__restrict__
         if (base + q < n) a[base + q] += add;
 }
 
-static cudaError_t exclusive_scan(uint32_t *a, int64_t n, uint32_t *tmp, unsigned long long *total,
-                                  unsigned int *overflow, unsigned long long cap, cudaStream_t st) {
+cudaError_t exclusive_scan(uint32_t *a, int64_t n, uint32_t *tmp, unsigned long long *total,
+                           unsigned int *overflow, unsigned long long cap, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     const int64_t nb = (n + SCAN_E - 1) / SCAN_E;
     scan_blocks_kernel<<<(unsigned)nb, SCAN_T, 0, st>>>(a, n, tmp);

@@ -606,3 +606,125 @@ def test_connect_gradient_matches_central_differences():
         r2[i] -= h
         fd = (connect(pos, r1, nbr)[0].sum() - connect(pos, r2, nbr)[0].sum()) / (2 * h)
         assert fd == pytest.approx(gR[i], rel=1e-6, abs=1e-9)
+
+
+# ------------------------------------------------------------ neighbour lists
+
+def _lattice(m, h):
+    g = np.stack(np.meshgrid(*[np.arange(m)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    return (g * h).astype(np.float32), g
+
+
+def test_neighbours_on_a_lattice_closed_form():
+    """Equal weights: the radical plane is the bisector, t_ij = |p_j - p_i|/2
+    (Sec. 3.2 with w_i = w_j).  On a cubic lattice of step h the centre's
+    nearest planes are its 6 face neighbours (h/2), then 12 edge neighbours
+    (h/sqrt 2), then 8 corners (h sqrt(3)/2); equal values go by index and
+    R is clipped to the next shell."""
+    h = 0.125
+    pos, g = _lattice(5, h)
+    n = len(pos)
+    w = np.full(n, 0.01, np.float32)
+    R = np.full(n, 0.3, np.float32)
+    c = int(np.nonzero((g == 2).all(1))[0][0])
+    off = np.abs(g - 2).sum(1)
+    cheb = np.abs(g - 2).max(1)
+    faces = np.sort(np.nonzero((off == 1))[0])
+    edges = np.sort(np.nonzero((off == 2) & (cheb == 1))[0])
+    for k, want, next_t in ((6, faces, h / math.sqrt(2)), (18, np.concatenate([faces, edges]),
+                                                           h * math.sqrt(3) / 2)):
+        nbr, Ro = oracle.neighbours(pos, w, R, k, cells=[c])
+        assert list(nbr[0]) == list(want)
+        # the clipped radius is the next shell's distance, rounded down to float
+        assert Ro[0] <= next_t and next_t - Ro[0] < 1e-7
+    # K beyond the shells that fit under R: no clip
+    nbr, Ro = oracle.neighbours(pos, w, np.full(n, 0.05, np.float32), 6, cells=[c])
+    assert Ro[0] == np.float32(0.05)
+
+
+def test_neighbour_distance_is_where_the_power_distances_meet():
+    """t_ij is the point on the ray from p_i to p_j where pow(x, i) =
+    pow(x, j) (Eq. pow_dist; found here by root bracketing, not by the
+    closed form): a heavier neighbour's plane moves towards p_i and comes
+    first in the list."""
+    from scipy.optimize import brentq
+    rng = np.random.default_rng(7)
+    pos = rng.uniform(-1, 1, (40, 3)).astype(np.float32)
+    w = rng.uniform(0.0, 0.2, 40).astype(np.float32)
+    R = np.full(40, 10.0, np.float32)
+    nbr, _ = oracle.neighbours(pos, w, R, 39, cells=[0])
+    P = pos.astype(np.float64)
+    W = w.astype(np.float64)
+
+    def t_root(j):
+        a = P[j] - P[0]
+        L = np.linalg.norm(a)
+        u = a / L
+        f = lambda s: (s * s - W[0]) - (np.sum((P[0] + s * u - P[j]) ** 2) - W[j])
+        return brentq(f, -10.0, 10.0, xtol=1e-15, rtol=1e-15)
+
+    ts = np.array([t_root(j) for j in nbr[0]])
+    assert (np.diff(ts) > -1e-12).all()
+    assert sorted(nbr[0]) == list(range(1, 40))
+
+
+def test_neighbours_match_the_input_generators_kd_tree_build():
+    """The brute-force oracle and the input module's KD-tree builder (a
+    different search: Euclidean candidates plus a per-weight-group radius)
+    give the same lists and radii on uniform and capture-shaped sites."""
+    from paper_2604_24994_gb300 import inputs
+    rng = np.random.default_rng(3)
+    for pos, r, k in ((rng.uniform(-1, 1, (3000, 3)), rng.uniform(0.02, 0.08, 3000), 16),
+                      (None, None, 32)):
+        if pos is None:
+            sc = inputs.capture_scene(3000, seed=4, K=4)
+            pos, r = sc.pos.astype(np.float64), np.sqrt(sc.w.astype(np.float64))
+        pos = pos.astype(np.float32)
+        w = (r * r).astype(np.float32)
+        R = (1.5 * r).astype(np.float32)
+        nb_k, R_k, ncl = inputs.build_neighbours(pos, w, R, k)
+        nb_o, R_o = oracle.neighbours(pos, w, R, k)
+        np.testing.assert_array_equal(nb_o, nb_k)
+        np.testing.assert_array_equal(R_o.view(np.int32), R_k.view(np.int32))
+        assert ncl == int((R_o != R).sum())
+
+
+def test_neighbour_lists_are_complete_and_ordered():
+    """Invariants at any size: every listed site's plane is no farther than
+    any unlisted one, and no unlisted site's plane cuts the clipped sphere
+    (t_ij >= R_i); duplicate sites have no plane and never appear."""
+    rng = np.random.default_rng(11)
+    pos = rng.uniform(-1, 1, (400, 3)).astype(np.float32)
+    pos[300:] = pos[:100]  # 100 duplicated sites
+    w = rng.uniform(0.0, 0.01, 400).astype(np.float32)
+    R = np.full(400, 0.5, np.float32)
+    k = 12
+    nbr, Ro = oracle.neighbours(pos, w, R, k)
+    P = pos.astype(np.float64)
+    for i in range(400):
+        a = P - P[i]
+        L = np.sqrt((a * a).sum(1))
+        with np.errstate(divide="ignore", invalid="ignore"):
+            t = (L * L + w[i] - w.astype(np.float64)) / (2 * L)
+        t[L == 0] = np.inf
+        listed = nbr[i][nbr[i] >= 0]
+        assert i not in listed and not (L[listed] == 0).any()
+        rest = np.setdiff1d(np.nonzero(np.isfinite(t))[0], listed)
+        if len(listed) and len(rest):
+            assert t[listed].max() <= t[rest].min() + 1e-12
+        assert (t[rest] >= Ro[i] - 1e-6).all()
+
+
+def test_neighbours_degenerate_sizes():
+    """One site: nothing to list, R kept.  Fewer sites than K: all of them,
+    then -1, R kept.  K = 0: an empty list, R still clipped by the nearest
+    plane."""
+    pos = np.array([[0, 0, 0], [1, 0, 0], [0, 2, 0]], np.float32)
+    w = np.zeros(3, np.float32)
+    R = np.full(3, 5.0, np.float32)
+    nbr, Ro = oracle.neighbours(pos[:1], w[:1], R[:1], 4)
+    assert list(nbr[0]) == [-1] * 4 and Ro[0] == 5.0
+    nbr, Ro = oracle.neighbours(pos, w, R, 4)
+    assert list(nbr[0]) == [1, 2, -1, -1] and Ro[0] == 5.0
+    nbr, Ro = oracle.neighbours(pos, w, R, 0)
+    assert nbr.shape == (3, 0) and Ro[0] == np.float32(0.5) and Ro[2] == np.float32(1.0)
