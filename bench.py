@@ -330,6 +330,29 @@ def run_ours(args):
         if it >= W:
             cc.append(a.elapsed_time(b))
     ms_connect = float(np.mean(cc))
+    # a 180-degree equidistant fisheye view of the same scene through the same kernels
+    from paper_2604_24994_gb300 import inputs as _inputs
+    fcam = _inputs.fisheye_look_at(tuple(np.asarray(cam.origin)), cam.width, cam.height, fov_deg=180.0)
+    rf = Renderer(ds.n, ds.k, [fcam], hit_records=False)
+    rf.bin(ds, sync=True)                      # prepare once, size the instance capacity
+    fo = rf.render_fwd(ds)
+    from paper_2604_24994_gb300._lib import check, lib
+    import ctypes as C
+    sst = ds.struct()
+    ft = []
+    for it in range(W + K):
+        flush.zero_()
+        a, b = ev(), ev()
+        a.record(stream)
+        check(lib().pf_project(C.byref(sst), rf.plan.handle, rf.plan.ws_ptr, stream.cuda_stream), "project")
+        check(lib().pf_bin_sort(rf.plan.handle, rf.plan.ws_ptr, None, stream.cuda_stream), "bin_sort")
+        rf.render_fwd(ds, out=fo)
+        b.record(stream)
+        b.synchronize()
+        if it >= W:
+            ft.append(a.elapsed_time(b))
+    ms_fisheye = float(np.mean(ft))
+    del rf, fo
     # the neighbour lists of the same scene built on the GPU (pf_build_neighbours)
     from paper_2604_24994_gb300.api import build_neighbours
     pw, Rin = ds.params["pos"], ds.params["R"]
@@ -384,11 +407,13 @@ def run_ours(args):
                    "l2": "256 MiB buffer written between timed steps (not timed)",
                    "fwd_step": "pf_project + pf_bin_sort + pf_render_fwd (scene resident and prepared)",
                    "fwd_bwd_step": "pf_prepare + pf_project + pf_bin_sort + pf_render_fwd + L2 loss grad + pf_render_bwd",
+                   "fisheye_step": "the forward step for a 180-degree equidistant fisheye of the same size and position",
                    "scene_generation_s": round(gen_s, 1)},
         "fwd_fps": ws * 1000.0 / ms_fwd, "fwd_bwd_fps": ws * 1000.0 / ms_train, "ms_fwd_bwd": ms_train,
         "ms_render_fwd_kernel": ms_render,
         "ms_render_fwd_contrib_kernel": ms_render_contrib,
         "ms_connect_loss_and_grad": ms_connect,
+        "fisheye_fwd_fps": 1000.0 / ms_fisheye,
         "ms_build_neighbours": ms_neighbours,
         "neighbours_equal_input_lists": nbr_same,
         "work": stats,

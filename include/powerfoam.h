@@ -58,13 +58,23 @@ typedef struct {
     int32_t k_nbr;   /* K in [0, 64] */
 } pf_scene;
 
-/* Pinhole camera: x_cam = rot (x_world - origin), OpenCV axes (x right,
- * y down, z forward); pixel (u, v) is the ray through (u + 0.5, v + 0.5). */
+/* Camera: x_cam = rot (x_world - origin), OpenCV axes (x right, y down,
+ * z forward); pixel (u, v) is the ray through its centre (u + 0.5, v + 0.5).
+ * model PF_PINHOLE (0): the ray through ((u+.5-cx)/fx, (v+.5-cy)/fy, 1).
+ * model PF_FISHEYE (1), equidistant (non-pinhole rasterization, appendix D):
+ * a = ((u+.5-cx)/fx, (v+.5-cy)/fy) is the ray's angle theta = |a| from the
+ * optical axis, towards a/|a|: direction (sin(theta) a/|a|, cos(theta)).
+ * Pixels with theta > pi have no ray: rgb 0, T 1, last 0.  The painter
+ * order (power distance from the camera centre) is exact for every ray
+ * through the centre, so both models render losslessly. */
+#define PF_PINHOLE 0
+#define PF_FISHEYE 1
 typedef struct {
     double rot[9]; /* row-major world->camera rotation */
     double origin[3];
-    double fx, fy, cx, cy;
+    double fx, fy, cx, cy;  /* fx, fy > 0 */
     int32_t width, height; /* 1..16384 each */
+    int32_t model;         /* PF_PINHOLE or PF_FISHEYE */
 } pf_camera;
 
 /* Gradient outputs, same shapes as the scene parameters; the backward ADDS

@@ -54,7 +54,7 @@ class _Scene(C.Structure):
 class _Camera(C.Structure):
     _fields_ = [("rot", C.c_double * 9), ("origin", C.c_double * 3), ("fx", C.c_double),
                 ("fy", C.c_double), ("cx", C.c_double), ("cy", C.c_double),
-                ("width", C.c_int32), ("height", C.c_int32)]
+                ("width", C.c_int32), ("height", C.c_int32), ("model", C.c_int32)]
 
 
 class _Cands(C.Structure):
@@ -81,6 +81,7 @@ def lib():
             _lib.orc_render_rays.argtypes = [P(_Scene), P(_Cands), C.c_int64, P(d), P(d), d, P(d), P(d)]
             _lib.orc_cell_colour.argtypes = [P(_Scene), C.c_int64, P(d), P(d), d, d, d, P(d)]
             _lib.orc_ray.argtypes = [P(_Camera), d, d, P(d), P(d)]
+            _lib.orc_ray.restype = C.c_int
             _lib.orc_onb.argtypes = [P(d), P(d), P(d)]
             _lib.orc_hit_cells.argtypes = [P(_Scene), P(_Camera), C.c_int64, P(C.c_int32), P(C.c_uint8),
                                            C.c_int]
@@ -125,6 +126,7 @@ def camera_struct(cam) -> _Camera:
     c.origin[:] = [float(x) for x in np.asarray(cam.origin, np.float64)]
     c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
     c.width, c.height = int(cam.width), int(cam.height)
+    c.model = int(getattr(cam, "model", 0))
     return c
 
 
@@ -303,11 +305,13 @@ class Oracle:
         return out
 
     def ray(self, cam, u, v):
+        """(origin, unit direction) of pixel (u, v); None where the pixel has
+        no ray (a fisheye pixel beyond theta = pi)."""
         o = np.zeros(3)
         d = np.zeros(3)
-        lib().orc_ray(C.byref(camera_struct(cam)), float(u), float(v), _ptr(o, C.c_double),
-                      _ptr(d, C.c_double))
-        return o, d
+        ok = lib().orc_ray(C.byref(camera_struct(cam)), float(u), float(v), _ptr(o, C.c_double),
+                           _ptr(d, C.c_double))
+        return (o, d) if ok else None
 
     def ray_segments(self, o, d, maxn: int = 100000):
         """Non-empty segments of the ray o + t d, sorted by entry distance:

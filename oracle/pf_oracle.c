@@ -52,11 +52,16 @@ typedef struct {
     const double *pos, *w, *R, *sigma, *rgb, *normal, *offset, *tex;
 } orc_scene;
 
+/* model 0: pinhole.  model 1: equidistant fisheye (non-pinhole rasterization,
+ * appendix D): the pixel centre's offset a = ((u+.5-cx)/fx, (v+.5-cy)/fy)
+ * is the direction's angle from the optical axis, theta = |a|, towards
+ * a/|a|; pixels with theta > pi have no ray. */
 typedef struct {
     double rot[9];
     double origin[3];
     double fx, fy, cx, cy;
     int32_t width, height;
+    int32_t model;
 } orc_camera;
 
 /* optional candidate lists: cell i is clipped against idx[beg[i]..end[i])
@@ -84,9 +89,17 @@ static void load3(const double *p, int64_t i, double *o) {
     o[2] = p[3 * i + 2];
 }
 
-/* pixel-centre ray of a pinhole camera */
-void orc_ray(const orc_camera *cam, double u, double v, double *o, double *d) {
+/* pixel-centre ray; 0 if the pixel has none (fisheye beyond theta = pi) */
+int orc_ray(const orc_camera *cam, double u, double v, double *o, double *d) {
     double dc[3] = {(u + 0.5 - cam->cx) / cam->fx, (v + 0.5 - cam->cy) / cam->fy, 1.0};
+    if (cam->model == 1) {
+        double th = sqrt(dc[0] * dc[0] + dc[1] * dc[1]);
+        if (th > 3.14159265358979323846) return 0;
+        double f = th > 0.0 ? sin(th) / th : 1.0;
+        dc[0] *= f;
+        dc[1] *= f;
+        dc[2] = cos(th);
+    }
     double dw[3];
     for (int r = 0; r < 3; r++)
         dw[r] = cam->rot[0 * 3 + r] * dc[0] + cam->rot[1 * 3 + r] * dc[1] + cam->rot[2 * 3 + r] * dc[2];
@@ -95,6 +108,7 @@ void orc_ray(const orc_camera *cam, double u, double v, double *o, double *d) {
         d[r] = dw[r] / nn;
         o[r] = cam->origin[r];
     }
+    return 1;
 }
 
 /* unit dipole normal */
@@ -379,9 +393,9 @@ int orc_render(const orc_scene *s, const orc_cands *cd, const orc_camera *cam, i
         for (int64_t k = 0; k < npix; k++) {
             double u, v, o[3], d[3];
             pixel_of(cam, k, pix, &u, &v);
-            orc_ray(cam, u, v, o, d);
-            double T, C[3];
-            int64_t n = render_ray(s, cd, o, d, kappa, &buf, &cap, C, &T);
+            double T = 1.0, C[3] = {0.0, 0.0, 0.0};
+            int64_t n = 0;
+            if (orc_ray(cam, u, v, o, d)) n = render_ray(s, cd, o, d, kappa, &buf, &cap, C, &T);
             for (int ch = 0; ch < 3; ch++) out_rgb[3 * k + ch] = C[ch];
             out_T[k] = T;
             if (out_nseg) out_nseg[k] = (int32_t)n;
@@ -417,7 +431,7 @@ int orc_cell_contrib(const orc_scene *s, const orc_cands *cd, const orc_camera *
         for (int64_t k = 0; k < npix; k++) {
             double u, v, o[3], d[3];
             pixel_of(cam, k, pix, &u, &v);
-            orc_ray(cam, u, v, o, d);
+            if (!orc_ray(cam, u, v, o, d)) continue;
             int64_t n = ray_segments(s, cd, o, d, &buf, &cap);
             double T = 1.0;
             for (int64_t q = 0; q < n; q++) {
@@ -461,7 +475,7 @@ int orc_hit_cells(const orc_scene *s, const orc_camera *cam, int64_t npix, const
         for (int64_t k = 0; k < npix; k++) {
             double u, v, o[3], d[3];
             pixel_of(cam, k, pix, &u, &v);
-            orc_ray(cam, u, v, o, d);
+            if (!orc_ray(cam, u, v, o, d)) continue;
             for (int r = 0; r < 3; r++) m[r] = o[r] - p[r];
             double b = dot3(m, d), c = dot3(m, m) - R * R;
             double disc = b * b - c;
@@ -576,7 +590,7 @@ int orc_render_grad(const orc_scene *s, const orc_cands *cd, const orc_camera *c
         for (int64_t k = 0; k < npix; k++) {
             double u, v, o[3], d[3];
             pixel_of(cam, k, pix, &u, &v);
-            orc_ray(cam, u, v, o, d);
+            if (!orc_ray(cam, u, v, o, d)) continue;
             int64_t n = ray_segments(s, cd, o, d, &buf, &cap);
             if (n > acap) {
                 acap = n;

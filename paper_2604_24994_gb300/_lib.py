@@ -34,7 +34,8 @@ class Scene(C.Structure):
 
 class Camera(C.Structure):
     _fields_ = [("rot", C.c_double * 9), ("origin", C.c_double * 3), ("fx", C.c_double), ("fy", C.c_double),
-                ("cx", C.c_double), ("cy", C.c_double), ("width", C.c_int32), ("height", C.c_int32)]
+                ("cx", C.c_double), ("cy", C.c_double), ("width", C.c_int32), ("height", C.c_int32),
+                ("model", C.c_int32)]
 
 
 class SceneGrad(C.Structure):
@@ -105,6 +106,7 @@ def camera_struct(cam) -> Camera:
     c.origin[:] = [float(x) for x in np.asarray(cam.origin, np.float64).reshape(3)]
     c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
     c.width, c.height = int(cam.width), int(cam.height)
+    c.model = int(getattr(cam, "model", 0))
     return c
 
 

@@ -89,6 +89,7 @@ SceneLayout make_scene_layout(int32_t n, int32_t k) {
 bool camera_ok(const pf_camera &c) {
     if (c.width < 1 || c.height < 1 || c.width > 16384 || c.height > 16384) return false;
     if (!(c.fx > 0) || !(c.fy > 0)) return false;
+    if (c.model != PF_PINHOLE && c.model != PF_FISHEYE) return false;
     for (int i = 0; i < 9; i++)
         if (!isfinite(c.rot[i])) return false;
     for (int i = 0; i < 3; i++)
@@ -121,6 +122,7 @@ void fill_views(Plan *p, const pf_camera *cams) {
         d.skd = sqrt(1.0 + d.kd * d.kd);
         d.width = c.width;
         d.height = c.height;
+        d.model = c.model;
         d.tiles_x = (c.width + TILE - 1) / TILE;
         d.tiles_y = (c.height + TILE - 1) / TILE;
         d.tile_base = tb;

@@ -248,7 +248,54 @@ __global__ void __launch_bounds__(256) project_kernel(pf_scene s, const ViewDev 
     bool vis = !(DADD(Z, r) <= 0.0);
     const double W = V.width, H = V.height;
     double ulo = -CUDART_INF, uhi = CUDART_INF, vlo = -CUDART_INF, vhi = CUDART_INF;
-    if (vis && Z > r) {
+    if (V.model == PF_FISHEYE) {
+        // equidistant fisheye: the directions that meet the sphere form a cap
+        // of angular radius asin(r/|c|) around c; its pixels lie in the box
+        // of the annular sector theta in [thc - b, thc + b], phi in
+        // [phc - dphi, phc + dphi] (image offsets theta (cos phi, sin phi)
+        // scaled by fx, fy), or of the disc of radius thc + b when the cap
+        // holds the optical axis.  Conservative; the renderer tests each ray.
+        vis = true;
+        const double L = sqrt(X * X + Y * Y + Z * Z);
+        if (L > r) {
+            const double b = asin(r / L) * (1.0 + 1e-12) + 1e-12;
+            const double rho = sqrt(X * X + Y * Y);
+            const double thc = atan2(rho, Z);
+            const double th0 = thc - b, th1 = fmin(thc + b, CUDART_PI);
+            double xl, xh, yl, yh;
+            const double st = sin(thc);
+            if (th0 <= 0.0 || thc + b >= CUDART_PI || !(r / L < st * (1.0 - 1e-12))) {
+                // the cap holds a pole, or spans every azimuth: a disc
+                xl = yl = -th1;
+                xh = yh = th1;
+            } else {
+                const double dphi = asin(fmin(r / L / st, 1.0)) * (1.0 + 1e-12) + 1e-12;
+                const double phc = atan2(Y, X);
+                const double p0 = phc - dphi, p1 = phc + dphi;
+                double c0, s0, c1, s1;
+                sincos(p0, &s0, &c0);
+                sincos(p1, &s1, &c1);
+                xl = fmin(fmin(th0 * c0, th1 * c0), fmin(th0 * c1, th1 * c1));
+                xh = fmax(fmax(th0 * c0, th1 * c0), fmax(th0 * c1, th1 * c1));
+                yl = fmin(fmin(th0 * s0, th1 * s0), fmin(th0 * s1, th1 * s1));
+                yh = fmax(fmax(th0 * s0, th1 * s0), fmax(th0 * s1, th1 * s1));
+                // the outer arc's extremes where it crosses an axis direction
+                for (int q = -4; q <= 4; q++) {
+                    const double psi = q * (0.5 * CUDART_PI);
+                    if (psi < p0 || psi > p1) continue;
+                    const int m = ((q % 4) + 4) % 4;
+                    if (m == 0) xh = fmax(xh, th1);
+                    if (m == 1) yh = fmax(yh, th1);
+                    if (m == 2) xl = fmin(xl, -th1);
+                    if (m == 3) yl = fmin(yl, -th1);
+                }
+            }
+            ulo = V.cx + V.fx * xl;
+            uhi = V.cx + V.fx * xh;
+            vlo = V.cy + V.fy * yl;
+            vhi = V.cy + V.fy * yh;
+        }
+    } else if (vis && Z > r) {
         // tangent lines from the camera centre to the sphere's x-z and y-z circles
         const double rr = DMUL(r, r);
         const double izr = DDIV(1.0, DSUB(DMUL(Z, Z), rr));

@@ -77,6 +77,8 @@ struct ViewDev {
     double skl, skr, sku, skd; // sqrt(1 + k^2) of each
     int32_t width, height;
     int32_t tiles_x, tiles_y;
+    int32_t model;            // PF_PINHOLE or PF_FISHEYE
+    int32_t pad_;
     int64_t tile_base;        // first global tile id of this view
     int64_t pix_base;         // first pixel of this view in the outputs
     int64_t diff_base;        // offset of this view's (tx+1)(ty+1) difference grid

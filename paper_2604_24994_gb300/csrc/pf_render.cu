@@ -76,13 +76,39 @@ struct Ray {
     float3 dh, dl;          // unit direction as a float pair
 };
 
-__device__ __forceinline__ Ray pixel_ray(const ViewDev &V, int u, int v) {
+// Does pixel (u, v) have a ray?  (A fisheye pixel beyond theta = pi has none.)
+__device__ __forceinline__ bool pixel_has_ray(const ViewDev &V, int u, int v) {
+    if (V.model != PF_FISHEYE) return true;
     const double xc = ((double)u + 0.5 - V.cx) * V.ifx;
     const double yc = ((double)v + 0.5 - V.cy) * V.ify;
+    return sqrt(xc * xc + yc * yc) <= CUDART_PI;
+}
+
+// Equidistant fisheye: the offset (xc, yc) is the angle from the axis
+// (clamped at pi; pixels beyond have no ray and are never composited).  Out
+// of line: the pinhole path never calls it.
+__device__ __noinline__ double3 fisheye_dir(double xc, double yc) {
+    const double th = fmin(sqrt(xc * xc + yc * yc), CUDART_PI);
+    double sn, cs;
+    sincos(th, &sn, &cs);
+    const double f = th > 0.0 ? sn / th : 1.0;
+    return make_double3(xc * f, yc * f, cs);
+}
+
+__device__ __forceinline__ Ray pixel_ray(const ViewDev &V, int u, int v) {
+    double xc = ((double)u + 0.5 - V.cx) * V.ifx;
+    double yc = ((double)v + 0.5 - V.cy) * V.ify;
+    double zc = 1.0;
+    if (V.model == PF_FISHEYE) {
+        const double3 c = fisheye_dir(xc, yc);
+        xc = c.x;
+        yc = c.y;
+        zc = c.z;
+    }
     const double *M = V.rot;
-    double dx = M[0] * xc + M[3] * yc + M[6];
-    double dy = M[1] * xc + M[4] * yc + M[7];
-    double dz = M[2] * xc + M[5] * yc + M[8];
+    double dx = M[0] * xc + M[3] * yc + M[6] * zc;
+    double dy = M[1] * xc + M[4] * yc + M[7] * zc;
+    double dz = M[2] * xc + M[5] * yc + M[8] * zc;
     const double n2 = dx * dx + dy * dy + dz * dz;
     double r = (double)rsqrtf((float)n2);
     r = r * (1.5 - 0.5 * n2 * r * r);
@@ -618,6 +644,7 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, i
     const bool inside = px < V.width && py < V.height;
     const Ray ray = pixel_ray(V, px, py);
     const Cone cone = warp_cone(V, wx, wy, ray);
+    const bool has_ray = pixel_has_ray(V, px, py);
 
     unsigned long long s = A.w.tile_start[tile], e = A.w.tile_start[tile + 1];
     if (s > A.cap) s = A.cap;
@@ -632,7 +659,7 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, i
     float3 C = f3(0.f, 0.f, 0.f);
     uint32_t last = 0;
     int nhit = 0;  // hits so far (hit recording)
-    bool done = !inside;
+    bool done = !inside || !has_ray;
 
     if (nbat > 0) issue_batch(sg, 0, A.w.inst_sorted + s, min(BATCH, n), A.w, vbase, A.K, false);
     for (int k = 0; k < nbat; k++) {

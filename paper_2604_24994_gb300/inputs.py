@@ -81,8 +81,11 @@ class Scene:
 
 @dataclasses.dataclass
 class Camera:
-    """Pinhole camera: x_cam = rot @ (x_world - origin); OpenCV axes
-    (x right, y down, z forward); pixel (u, v) has its centre at (u+.5, v+.5)."""
+    """Camera: x_cam = rot @ (x_world - origin); OpenCV axes (x right, y
+    down, z forward); pixel (u, v) has its centre at (u+.5, v+.5).
+    model 0: pinhole.  model 1: equidistant fisheye, the centre's offset
+    ((u+.5-cx)/fx, (v+.5-cy)/fy) is the ray's angle from the optical axis
+    (radians) towards that offset; beyond pi the pixel has no ray."""
     rot: np.ndarray        # [3,3] float64, world -> camera
     origin: np.ndarray     # [3] float64
     fx: float
@@ -91,6 +94,7 @@ class Camera:
     cy: float
     width: int
     height: int
+    model: int = 0
 
     @property
     def n_pixels(self) -> int:
@@ -127,6 +131,16 @@ def look_at(origin, width: int, height: int, fov_y_deg: float = 60.0,
     f = 0.5 * height / math.tan(math.radians(fov_y_deg) / 2)
     return Camera(rot=rot, origin=o, fx=f, fy=f, cx=width / 2.0, cy=height / 2.0,
                   width=int(width), height=int(height))
+
+
+def fisheye_look_at(origin, width: int, height: int, fov_deg: float = 180.0,
+                    target=(0.0, 0.0, 0.0), up=(0.0, 0.0, 1.0)) -> Camera:
+    """Equidistant fisheye at `origin` looking at `target`: the circle
+    inscribed in the image spans `fov_deg`; square pixels, principal point
+    at the image centre."""
+    c = look_at(origin, width, height, 60.0, target, up)
+    f = 0.5 * min(width, height) / math.radians(fov_deg / 2)
+    return dataclasses.replace(c, fx=f, fy=f, model=1)
 
 
 def ring_cameras(n_views: int, radius: float, width: int, height: int,

@@ -728,3 +728,64 @@ def test_neighbours_degenerate_sizes():
     assert list(nbr[0]) == [1, 2, -1, -1] and Ro[0] == 5.0
     nbr, Ro = oracle.neighbours(pos, w, R, 0)
     assert nbr.shape == (3, 0) and Ro[0] == np.float32(0.5) and Ro[2] == np.float32(1.0)
+
+
+# ------------------------------------------------------------- fisheye rays
+
+def test_fisheye_ray_angle_is_the_pixel_radius():
+    """Equidistant fisheye (appendix D's non-pinhole rasterization): the
+    ray's angle from the optical axis equals the pixel's distance from the
+    principal point over f (measured with arccos, not the sine/cosine the
+    oracle builds the ray from), its azimuth follows the pixel offset, and
+    pixels beyond pi have no ray."""
+    from paper_2604_24994_gb300 import inputs
+    cam = inputs.fisheye_look_at((3.0, 0.5, -0.2), 301, 200, fov_deg=300.0)
+    orc = oracle.Oracle(make_scene([0, 0, 0], 0.01, 0.1, 1.0, [0, 0, 0]))
+    rot = np.asarray(cam.rot)
+    rng = np.random.default_rng(1)
+    n_none = 0
+    for u, v in zip(rng.integers(0, 301, 200), rng.integers(0, 200, 200)):
+        a = np.array([(u + 0.5 - cam.cx) / cam.fx, (v + 0.5 - cam.cy) / cam.fy])
+        th = np.linalg.norm(a)
+        r = orc.ray(cam, u, v)
+        if th > math.pi:
+            assert r is None
+            n_none += 1
+            continue
+        o, d = r
+        dc = rot @ d                          # camera axes
+        assert abs(np.linalg.norm(d) - 1) < 1e-14
+        assert math.acos(np.clip(dc[2], -1, 1)) == pytest.approx(th, abs=1e-7)
+        if th > 1e-3:
+            # the image-plane part of the direction points along the pixel offset
+            assert abs(dc[0] * a[1] - dc[1] * a[0]) < 1e-12 * (1 + th)
+            assert dc[0] * a[0] + dc[1] * a[1] > 0
+    assert n_none > 0
+    # the principal point looks down the axis
+    o, d = orc.ray(cam, cam.cx - 0.5, cam.cy - 0.5)
+    np.testing.assert_allclose(rot @ d, [0, 0, 1], atol=1e-15)
+
+
+def test_fisheye_renders_the_same_rays_as_a_pinhole(tiny):
+    """Rendering is per ray: a fisheye pixel and a pinhole pixel that see the
+    same direction get the same colour and transmittance (the paper's
+    lossless non-pinhole claim), and a fisheye pixel without a ray is empty
+    (T = 1, black)."""
+    import dataclasses
+    from paper_2604_24994_gb300 import inputs
+    sc, _ = tiny
+    orc = oracle.Oracle(sc)
+    fe = inputs.fisheye_look_at((2.2, 0.4, 0.3), 96, 96, fov_deg=120.0)
+    rot = np.asarray(fe.rot)
+    for (u, v) in ((48, 48), (30, 61), (80, 20), (10, 50)):
+        d = rot @ orc.ray(fe, u, v)[1]       # camera axes
+        f = 400.0
+        ph = dataclasses.replace(fe, model=0, fx=f, fy=f, cx=0.5 - f * d[0] / d[2],
+                                 cy=0.5 - f * d[1] / d[2])
+        c1, T1 = orc.render(fe, pix=np.array([[u, v]]))
+        c2, T2 = orc.render(ph, pix=np.array([[0, 0]]))
+        np.testing.assert_allclose(c1, c2, atol=1e-10)
+        np.testing.assert_allclose(T1, T2, atol=1e-10)
+    wide = inputs.fisheye_look_at((2.2, 0.4, 0.3), 64, 32, fov_deg=350.0)
+    c, T = orc.render(wide, pix=np.array([[0, 0], [63, 31]]))
+    assert np.all(T == 1.0) and np.all(c == 0.0)
