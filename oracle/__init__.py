@@ -32,7 +32,8 @@ _lib = None
 
 KAPPA = 6.0          # soft-Voronoi sharpness on the face, in units of 1/R
 PARAM_COLS = {"pos": (0, 3), "w": (3, 1), "R": (4, 1), "sigma": (5, 1), "rgb": (6, 3),
-              "normal": (9, 3), "offset": (12, 1), "tex": (13, 12)}
+              "normal": (9, 3), "offset": (12, 1), "tex": (13, 12), "disp": (25, 4)}
+NPAR = 29
 ACT_SPHERE, ACT_CAMERA, ACT_DIPOLE = -1, -2, -3
 
 
@@ -48,7 +49,8 @@ def build(force: bool = False) -> str:
 
 class _Scene(C.Structure):
     _fields_ = [("n", C.c_int64)] + [(k, C.POINTER(C.c_double)) for k in
-                                     ("pos", "w", "R", "sigma", "rgb", "normal", "offset", "tex")]
+                                     ("pos", "w", "R", "sigma", "rgb", "normal", "offset", "tex", "disp")] + \
+               [("kappa_disp", C.c_double)]
 
 
 class _Camera(C.Structure):
@@ -135,17 +137,24 @@ class Oracle:
     widened to float64 (exactly, for float32 inputs); `params` holds them and
     may be edited in place (finite differences do)."""
 
-    def __init__(self, scene, kappa: float = KAPPA, nthreads: int = 0):
+    def __init__(self, scene, kappa: float = KAPPA, nthreads: int = 0, disp=None):
+        """`disp` [N,4] (or the scene's `disp` attribute): displacement of
+        each face at its four texture sites (Eq. svdisp); None for none."""
         self.kappa = float(kappa)
         self.nthreads = int(nthreads)
         self._arrs = {k: np.ascontiguousarray(np.asarray(getattr(scene, k), np.float64))
                       for k in ("pos", "w", "R", "sigma", "rgb", "normal", "offset", "tex")}
+        if disp is None:
+            disp = getattr(scene, "disp", None)
+        if disp is not None:
+            self._arrs["disp"] = np.ascontiguousarray(np.asarray(disp, np.float64).reshape(-1, 4))
         self.params = self._arrs
         self.n = int(self._arrs["pos"].shape[0])
         s = _Scene()
         s.n = self.n
         for k, a in self._arrs.items():
             setattr(s, k, _ptr(a, C.c_double))
+        s.kappa_disp = self.kappa
         self._s = s
         self._cands = None      # (beg, end, idx) arrays, kept alive
         self._cs = None
@@ -293,7 +302,7 @@ class Oracle:
         pixa, npix = self._pix(cam, pix)
         gC = np.ascontiguousarray(np.asarray(dL_dC, np.float64).reshape(npix, 3))
         gT = np.ascontiguousarray(np.asarray(dL_dT, np.float64).reshape(npix))
-        g = np.zeros((self.n, 25), np.float64)
+        g = np.zeros((self.n, NPAR), np.float64)
         lib().orc_render_grad(C.byref(self._s), C.byref(self._cs) if self._cs else None,
                               C.byref(camera_struct(cam)), npix,
                               _ptr(pixa, C.c_int32) if pixa is not None else None, self.kappa,
@@ -301,6 +310,8 @@ class Oracle:
                               self.nthreads)
         out = {}
         for k, (c0, w) in PARAM_COLS.items():
+            if k == "disp" and "disp" not in self._arrs:
+                continue
             out[k] = g[:, c0:c0 + w] if w > 1 else g[:, c0].copy()
         return out
 

@@ -50,6 +50,10 @@
 typedef struct {
     int64_t n;
     const double *pos, *w, *R, *sigma, *rgb, *normal, *offset, *tex;
+    /* optional (NULL: none): displacement of the face at the four texture
+     * sites, [n][4] (Eq. svdisp), with soft-Voronoi sharpness kappa_disp */
+    const double *disp;
+    double kappa_disp;
 } orc_scene;
 
 /* model 0: pinhole.  model 1: equidistant fisheye (non-pinhole rasterization,
@@ -119,6 +123,9 @@ static void unit_normal(const orc_scene *s, int64_t i, double *nh, double *len) 
     for (int r = 0; r < 3; r++) nh[r] = n[r] / L;
     *len = L;
 }
+
+static double face_disp(const orc_scene *s, int64_t i, const double *o, const double *d, double *W, double *u,
+                        double *tbar);
 
 /*
  * Segment of the ray inside cell i (brute force over every other site, or
@@ -192,6 +199,7 @@ static int cell_segment(const orc_scene *s, const orc_cands *cd, int64_t i, cons
     unit_normal(s, i, nh, &nl);
     double den = dot3(nh, d);
     double h = (double)s->offset[i] - dot3(nh, m);
+    if (s->disp) h += face_disp(s, i, o, d, NULL, NULL, NULL);
     if (den > 0.0) {
         double t = h / den;
         if (t < tb) {
@@ -251,6 +259,53 @@ void orc_onb(const double *n, double *e1, double *e2) { onb(n, e1, e2, NULL, NUL
 
 /* the four texture sites, in units of R on the face, site-major */
 static const double SITE[4][2] = {{-1.0 / 3.0, -1.0 / 3.0}, {1.0 / 3.0, -1.0 / 3.0}, {-1.0 / 3.0, 1.0 / 3.0}, {1.0 / 3.0, 1.0 / 3.0}};
+
+/*
+ * Displacement of the face for one ray (Eq. svdisp, with the one-step plane
+ * shift): the ray crosses the base face nh.(x - p) = off at
+ * tbar = (off - nh.m)/(nh.d), m = o - p; there, u = (e1.y, e2.y)/R with
+ * y = m + tbar d, and delta = sum_k W_k disp_k with the soft-Voronoi weights
+ * W_k = softmax_k(-kappa_disp |u - s_k|) over the four texture sites.  The
+ * ray then meets the displaced face nh.(x - p) = off + delta.  A ray
+ * parallel to the face (nh.d = 0) has no crossing: delta = 0.
+ */
+static double face_disp(const orc_scene *s, int64_t i, const double *o, const double *d, double *W, double *u,
+                        double *tbar) {
+    double nh[3], nl, p[3], m[3], y[3], e1[3], e2[3];
+    unit_normal(s, i, nh, &nl);
+    double den = dot3(nh, d);
+    if (!s->disp || den == 0.0) {
+        if (W)
+            for (int k = 0; k < 4; k++) W[k] = 0.0;
+        if (tbar) *tbar = 0.0;
+        return 0.0;
+    }
+    load3(s->pos, i, p);
+    for (int r = 0; r < 3; r++) m[r] = o[r] - p[r];
+    double tb = ((double)s->offset[i] - dot3(nh, m)) / den;
+    for (int r = 0; r < 3; r++) y[r] = m[r] + tb * d[r];
+    onb(nh, e1, e2, NULL, NULL);
+    double R = s->R[i];
+    double uu[2] = {dot3(e1, y) / R, dot3(e2, y) / R};
+    double lg[4], mx = -INFINITY, Wk[4], Z = 0.0, delta = 0.0;
+    for (int k = 0; k < 4; k++) {
+        double dx = uu[0] - SITE[k][0], dy = uu[1] - SITE[k][1];
+        lg[k] = -s->kappa_disp * sqrt(dx * dx + dy * dy);
+        if (lg[k] > mx) mx = lg[k];
+    }
+    for (int k = 0; k < 4; k++) {
+        Wk[k] = exp(lg[k] - mx);
+        Z += Wk[k];
+    }
+    for (int k = 0; k < 4; k++) {
+        Wk[k] /= Z;
+        delta += Wk[k] * s->disp[4 * i + k];
+    }
+    if (W) memcpy(W, Wk, sizeof Wk);
+    if (u) memcpy(u, uu, sizeof uu);
+    if (tbar) *tbar = tb;
+    return delta;
+}
 
 /* colour of cell i for the segment (Eq. svrad, see header) */
 static void cell_colour(const orc_scene *s, int64_t i, const double *o, const double *d, const orc_seg *sg,
@@ -495,7 +550,7 @@ int orc_hit_cells(const orc_scene *s, const orc_camera *cam, int64_t npix, const
  * Parameter columns (25 per cell): pos 0-2, w 3, R 4, sigma 5, rgb 6-8,
  * normal 9-11, offset 12, tex 13-24.
  */
-enum { P_POS = 0, P_W = 3, P_R = 4, P_SIG = 5, P_RGB = 6, P_N = 9, P_OFF = 12, P_TEX = 13, NPAR = 25 };
+enum { P_POS = 0, P_W = 3, P_R = 4, P_SIG = 5, P_RGB = 6, P_N = 9, P_OFF = 12, P_TEX = 13, P_DISP = 25, NPAR = 29 };
 
 typedef struct {
     int32_t cell, col;
@@ -519,6 +574,62 @@ static void push(clist *L, int32_t cell, int col, double v) {
     L->n++;
 }
 
+/*
+ * dL/dt for a segment end on the face of cell i at t:
+ * F = nh.(x - p) - off - delta = 0 gives dt/dp = nh/(nh.d),
+ * dt/doff = dt/ddelta = 1/(nh.d), dt/dnh = -(x - p)/(nh.d) at fixed delta.
+ * With displacement, delta (see face_disp) depends on disp_k through W_k,
+ * and on p, R and nh through u at the base crossing tbar, which itself
+ * moves like a face end without displacement.
+ */
+static void route_face(const orc_scene *s, int64_t i, double t, const double *o, const double *d, double g,
+                       clist *L, int with_disp) {
+    double nh[3], nl, p[3], y[3];
+    unit_normal(s, i, nh, &nl);
+    load3(s->pos, i, p);
+    for (int r = 0; r < 3; r++) y[r] = o[r] + t * d[r] - p[r];
+    double nd = dot3(nh, d);
+    double gnh[3];
+    for (int r = 0; r < 3; r++) {
+        push(L, (int32_t)i, P_POS + r, g * nh[r] / nd);
+        gnh[r] = -g * y[r] / nd;
+    }
+    push(L, (int32_t)i, P_OFF, g / nd);
+    if (with_disp && s->disp && nd != 0.0) {
+        double W[4], u[2], tb;
+        double delta = face_disp(s, i, o, d, W, u, &tb);
+        double gd = g / nd; /* dL/ddelta */
+        double gu[2] = {0.0, 0.0};
+        for (int k = 0; k < 4; k++) {
+            push(L, (int32_t)i, P_DISP + k, gd * W[k]);
+            /* d delta / d u = sum_k W_k (disp_k - delta) d lg_k / du,  lg_k = -kappa |u - s_k| */
+            double dx = u[0] - SITE[k][0], dy = u[1] - SITE[k][1];
+            double rr = sqrt(dx * dx + dy * dy);
+            if (rr > 0.0) {
+                double c = gd * W[k] * (s->disp[4 * i + k] - delta) * (-s->kappa_disp) / rr;
+                gu[0] += c * dx;
+                gu[1] += c * dy;
+            }
+        }
+        /* u = (e1.yb, e2.yb)/R, yb = o + tbar d - p */
+        double e1[3], e2[3], J1[9], J2[9], yb[3], gy[3];
+        onb(nh, e1, e2, J1, J2);
+        double R = s->R[i];
+        for (int r = 0; r < 3; r++) yb[r] = o[r] + tb * d[r] - p[r];
+        for (int r = 0; r < 3; r++) gy[r] = (gu[0] * e1[r] + gu[1] * e2[r]) / R;
+        for (int r = 0; r < 3; r++) push(L, (int32_t)i, P_POS + r, -gy[r]);
+        push(L, (int32_t)i, P_R, -(gu[0] * u[0] + gu[1] * u[1]) / R);
+        for (int c = 0; c < 3; c++)
+            for (int r = 0; r < 3; r++)
+                gnh[c] += J1[3 * r + c] * gu[0] * yb[r] / R + J2[3 * r + c] * gu[1] * yb[r] / R;
+        /* the base crossing moves with the base face */
+        route_face(s, i, tb, o, d, dot3(gy, d), L, 0);
+    }
+    /* nh = n/|n|:  dL/dn = (I - nh nh^T) dL/dnh / |n| */
+    double pr = dot3(nh, gnh);
+    for (int r = 0; r < 3; r++) push(L, (int32_t)i, P_N + r, (gnh[r] - nh[r] * pr) / nl);
+}
+
 /* dL/dt for the end of a segment given by constraint act on cell i */
 static void route_t(const orc_scene *s, int64_t i, int act, double t, const double *o, const double *d, double g,
                     clist *L) {
@@ -535,19 +646,7 @@ static void route_t(const orc_scene *s, int64_t i, int act, double t, const doub
         for (int r = 0; r < 3; r++) push(L, (int32_t)i, P_POS + r, g * y[r] / yd);
         push(L, (int32_t)i, P_R, g * (double)s->R[i] / yd);
     } else if (act == ACT_DIPOLE) {
-        /* F = nh.(x - p) - off:  dt/dp = nh/(nh.d), dt/doff = 1/(nh.d), dt/dnh = -(x-p)/(nh.d) */
-        double nh[3], nl;
-        unit_normal(s, i, nh, &nl);
-        double nd = dot3(nh, d);
-        double gnh[3];
-        for (int r = 0; r < 3; r++) {
-            push(L, (int32_t)i, P_POS + r, g * nh[r] / nd);
-            gnh[r] = -g * y[r] / nd;
-        }
-        push(L, (int32_t)i, P_OFF, g / nd);
-        /* nh = n/|n|:  dL/dn = (I - nh nh^T) dL/dnh / |n| */
-        double pr = dot3(nh, gnh);
-        for (int r = 0; r < 3; r++) push(L, (int32_t)i, P_N + r, (gnh[r] - nh[r] * pr) / nl);
+        route_face(s, i, t, o, d, g, L, 1);
     } else {
         /* F = 2 x.(p_j - p_i) - |p_j|^2 + |p_i|^2 - w_i + w_j
          * dF/dt = 2 d.(p_j - p_i), dF/dp_i = -2(x - p_i), dF/dp_j = 2(x - p_j),
@@ -568,7 +667,7 @@ static void route_t(const orc_scene *s, int64_t i, int act, double t, const doub
 
 /*
  * Gradient of L with respect to every cell parameter, given dL/dC [npix][3]
- * and dL/dT_final [npix] for the rendered pixels.  grad [n][25] is
+ * and dL/dT_final [npix] for the rendered pixels.  grad [n][29] is
  * overwritten.  Contributions are summed in pixel order, so the result does
  * not depend on the thread count.
  */

@@ -789,3 +789,98 @@ def test_fisheye_renders_the_same_rays_as_a_pinhole(tiny):
     wide = inputs.fisheye_look_at((2.2, 0.4, 0.3), 64, 32, fov_deg=350.0)
     c, T = orc.render(wide, pix=np.array([[0, 0], [63, 31]]))
     assert np.all(T == 1.0) and np.all(c == 0.0)
+
+
+# ----------------------------------------------------- face displacement
+
+def test_zero_displacement_is_the_base_render(tiny):
+    sc, cam = tiny
+    pix = np.stack(np.meshgrid(np.arange(0, 128, 7), np.arange(0, 128, 5)), -1).reshape(-1, 2)
+    c0, T0 = oracle.Oracle(sc).render(cam, pix=pix)
+    c1, T1 = oracle.Oracle(sc, disp=np.zeros((sc.n, 4))).render(cam, pix=pix)
+    assert np.array_equal(c0, c1) and np.array_equal(T0, T1)
+
+
+def test_flat_displacement_is_an_offset_shift():
+    """Eq. svdisp with every site displaced by the same c: the soft-Voronoi
+    weights sum to one, so the face moves by c everywhere, exactly like an
+    offset of off + c, images and gradients alike (the displacement's
+    gradient summed over the sites is the offset's)."""
+    rng = np.random.default_rng(21)
+    sc = cluster_scene(rng, n=9, spread=0.12, r=(0.06, 0.12), tex_std=0.2)
+    c = rng.uniform(-0.03, 0.03, sc.n)
+    cam = cam_at([0.55, 0.25, 0.15], 12, 10, fov=40.0)
+    shifted = sc.copy()
+    shifted.offset = sc.offset + c
+    od = oracle.Oracle(sc, disp=np.repeat(c[:, None], 4, 1))
+    os_ = oracle.Oracle(shifted)
+    c1, T1 = od.render(cam)
+    c2, T2 = os_.render(cam)
+    np.testing.assert_allclose(c1, c2, atol=1e-12)
+    np.testing.assert_allclose(T1, T2, atol=1e-12)
+    npix = cam.width * cam.height
+    gC = rng.normal(size=(npix, 3))
+    gT = rng.normal(size=npix)
+    G1 = od.render_grad(cam, gC, gT)
+    G2 = os_.render_grad(cam, gC, gT)
+    np.testing.assert_allclose(G1["disp"].sum(1), G2["offset"], atol=1e-9)
+    for k in ("pos", "w", "R", "sigma", "rgb", "normal", "offset", "tex"):
+        np.testing.assert_allclose(G1[k], G2[k], atol=1e-9, err_msg=k)
+
+
+def test_displacement_at_the_face_centre_is_the_mean():
+    """A ray along the normal through the face centre crosses the base face
+    at u = 0, equidistant from the four sites at (+-1/3, +-1/3) R: by symmetry
+    each weighs 1/4, the face moves by the mean displacement, and the dense
+    segment of an isolated cell runs from the sphere to that height."""
+    R, sig, off = 0.5, 3.0, 0.1
+    disp = np.array([[0.05, -0.02, 0.07, 0.0]])
+    sc = make_scene([0, 0, 0], 0.04, R, sig, [0.3, 0.6, 0.9], normal=[0, 0, 1], offset=off)
+    orc = oracle.Oracle(sc, disp=disp)
+    c, T = orc.render_rays(np.array([[0.0, 0.0, -3.0]]), np.array([[0.0, 0.0, 1.0]]))
+    length = (off + disp.mean()) - (-R)
+    assert T[0] == pytest.approx(math.exp(-sig * length), rel=1e-13)
+    segs = orc.ray_segments([0.0, 0, -3.0], [0.0, 0, 1.0])
+    assert segs[0][2] == pytest.approx(3.0 + off + disp.mean(), abs=1e-14)
+    assert segs[0][4] == ACT_DIPOLE
+
+
+@pytest.mark.parametrize("seed", [111, 112])
+def test_displacement_adjoint_matches_central_differences(seed):
+    """The adjoint with displacement (Eq. svdisp: the face end moves with
+    delta, delta with the site displacements and with u at the base
+    crossing) equals FP64 central differences for every parameter group."""
+    sc = fd_scene(seed)
+    rng = np.random.default_rng(seed + 7)
+    disp = rng.uniform(-0.04, 0.04, (sc.n, 4))
+    cam = cam_at([0.55, 0.25, 0.15], 10, 10, fov=40.0)
+    orc = oracle.Oracle(sc, disp=disp)
+    npix = cam.width * cam.height
+    gC = rng.normal(size=(npix, 3))
+    gT = rng.normal(size=npix)
+    G = orc.render_grad(cam, gC, gT)
+
+    def loss():
+        c, T = orc.render(cam)
+        return float(np.sum(c * gC) + np.sum(T * gT))
+
+    scale = {"pos": 1e-3, "w": 1e-4, "R": 1e-3, "sigma": 1e-3, "rgb": 1e-3, "normal": 1e-3,
+             "offset": 1e-3, "tex": 1e-3, "disp": 1e-3}
+    checked = 0
+    for key, arr in orc.params.items():
+        flat = arr.reshape(-1)
+        gflat = np.asarray(G[key]).reshape(-1)
+        nz = np.nonzero(np.abs(gflat) > 1e-8)[0]
+        assert nz.size > 0, key
+        for j in rng.choice(nz, size=min(6, nz.size), replace=False):
+            h = scale[key] * 1e-3
+            old = flat[j]
+            flat[j] = old + h
+            lp = loss()
+            flat[j] = old - h
+            lm = loss()
+            flat[j] = old
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - gflat[j]) <= 1e-5 * max(1.0, abs(fd)), (key, j, fd, gflat[j])
+            checked += 1
+    assert checked >= 45
