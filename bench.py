@@ -353,6 +353,29 @@ def run_ours(args):
             ft.append(a.elapsed_time(b))
     ms_fisheye = float(np.mean(ft))
     del rf, fo
+    # the same forward step with every face displaced (Eq. svdisp), up to 0.2 R at each texture site
+    drng = np.random.default_rng(5)
+    dsp = torch.from_numpy((drng.uniform(-0.2, 0.2, (ds.n, 4)) * sc.R[:, None]).astype(np.float32)).cuda()
+    dparams = dict(ds.params, disp=dsp)
+    dst = ds.struct(dparams)
+    rd = Renderer(ds.n, ds.k, [cam], hit_records=False)
+    rd.bin(ds, sync=True)
+    do = rd.render_fwd(ds, params=dparams)
+    dt = []
+    for it in range(W + K):
+        flush.zero_()
+        a, b = ev(), ev()
+        a.record(stream)
+        check(lib().pf_project(C.byref(dst), rd.plan.handle, rd.plan.ws_ptr, stream.cuda_stream), "project")
+        check(lib().pf_bin_sort(rd.plan.handle, rd.plan.ws_ptr, None, stream.cuda_stream), "bin_sort")
+        check(lib().pf_render_fwd(C.byref(dst), rd.plan.handle, rd.plan.ws_ptr, do[0].data_ptr(), do[1].data_ptr(),
+                                  do[2].data_ptr(), stream.cuda_stream), "render_fwd")
+        b.record(stream)
+        b.synchronize()
+        if it >= W:
+            dt.append(a.elapsed_time(b))
+    ms_disp = float(np.mean(dt))
+    del rd, do, dsp, dparams
     # the neighbour lists of the same scene built on the GPU (pf_build_neighbours)
     from paper_2604_24994_gb300.api import build_neighbours
     pw, Rin = ds.params["pos"], ds.params["R"]
@@ -408,12 +431,14 @@ def run_ours(args):
                    "fwd_step": "pf_project + pf_bin_sort + pf_render_fwd (scene resident and prepared)",
                    "fwd_bwd_step": "pf_prepare + pf_project + pf_bin_sort + pf_render_fwd + L2 loss grad + pf_render_bwd",
                    "fisheye_step": "the forward step for a 180-degree equidistant fisheye of the same size and position",
+                   "displaced_step": "the forward step with every face displaced by up to 0.2 R at its four sites",
                    "scene_generation_s": round(gen_s, 1)},
         "fwd_fps": ws * 1000.0 / ms_fwd, "fwd_bwd_fps": ws * 1000.0 / ms_train, "ms_fwd_bwd": ms_train,
         "ms_render_fwd_kernel": ms_render,
         "ms_render_fwd_contrib_kernel": ms_render_contrib,
         "ms_connect_loss_and_grad": ms_connect,
         "fisheye_fwd_fps": 1000.0 / ms_fisheye,
+        "displaced_fwd_fps": 1000.0 / ms_disp,
         "ms_build_neighbours": ms_neighbours,
         "neighbours_equal_input_lists": nbr_same,
         "work": stats,

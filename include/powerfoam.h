@@ -56,6 +56,16 @@ typedef struct {
     const int32_t *nbr;
     int32_t n_cells; /* N >= 0 */
     int32_t k_nbr;   /* K in [0, 64] */
+    /* Optional face displacement [N][4] (NULL: none; 16-byte aligned):
+     * disp[i][k] moves the face of cell i along its normal at texture site
+     * k.  A ray crossing the base face at face coordinates u sees the face
+     * moved by delta = sum_k W_k(u) disp[i][k], with the soft-Voronoi
+     * weights of the texture (Eq. svdisp, one-step plane shift); a ray
+     * parallel to the face sees no displacement.  Used by the plain forward
+     * (pf_render_fwd, pf_render_fwd_static, the server); the forward does
+     * not record hits then, and pf_render_fwd_contrib, stats passes and
+     * pf_render_bwd return PF_ERR_INVALID_ARG for a displaced scene. */
+    const float *disp;
 } pf_scene;
 
 /* Camera: x_cam = rot (x_world - origin), OpenCV axes (x right, y down,

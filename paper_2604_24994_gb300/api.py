@@ -28,7 +28,9 @@ class DeviceScene:
         self.k = int(nbr.shape[1]) if nbr.dim() == 2 else 0
 
     @staticmethod
-    def from_numpy(scene, device="cuda", requires_grad=False) -> "DeviceScene":
+    def from_numpy(scene, device="cuda", requires_grad=False, disp=None) -> "DeviceScene":
+        """`disp` [N,4] (or the scene's `disp` attribute): face displacement
+        at the four texture sites (Eq. svdisp); forward rendering only."""
         params = {}
         for k in PARAMS:
             a = np.ascontiguousarray(getattr(scene, k), np.float32)
@@ -36,6 +38,10 @@ class DeviceScene:
             if requires_grad:
                 t.requires_grad_(True)
             params[k] = t
+        if disp is None:
+            disp = getattr(scene, "disp", None)
+        if disp is not None:
+            params["disp"] = torch.from_numpy(np.ascontiguousarray(disp, np.float32).reshape(-1, 4)).to(device)
         nbr = torch.from_numpy(np.ascontiguousarray(scene.nbr, np.int32)).to(device)
         return DeviceScene(params, nbr)
 
@@ -50,6 +56,11 @@ class DeviceScene:
         s.nbr = self.nbr.data_ptr() if self.nbr.numel() else None
         s.n_cells = self.n
         s.k_nbr = self.k
+        d = p.get("disp")
+        if d is not None:
+            if not (d.is_cuda and d.dtype == torch.float32 and d.is_contiguous() and d.numel() == 4 * self.n):
+                raise ValueError("disp must be a contiguous float32 CUDA tensor [N,4]")
+            s.disp = d.data_ptr() if d.numel() else None
         return s
 
 

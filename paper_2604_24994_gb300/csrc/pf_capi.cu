@@ -197,8 +197,8 @@ bool scene_ok(const pf_scene *s, const Plan *p) {
         set_error("null scene pointer");
         return false;
     }
-    if (((uintptr_t)s->tex & 15) != 0) {
-        set_error("tex must be 16-byte aligned");
+    if (((uintptr_t)s->tex & 15) != 0 || ((uintptr_t)s->disp & 15) != 0) {
+        set_error("tex and disp must be 16-byte aligned");
         return false;
     }
     return true;
@@ -388,7 +388,12 @@ pf_status pf_render_fwd(const pf_scene *scene, pf_plan *p, void *ws, float *rgb,
     g_err[0] = 0;
     if (!p || !ws || !scene_ok(scene, p) || !rgb || !T || !last) return PF_ERR_INVALID_ARG;
     WS w = p->ws(ws);
-    const bool record = p->record_hits && !p->stats && w.hitmask != nullptr;
+    if (scene->disp && p->stats && p->n > 0) {
+        set_error("pf_render_fwd: no stats pass for a displaced scene");
+        return PF_ERR_INVALID_ARG;
+    }
+    // a displaced scene has no adjoint on the GPU: nothing to record for one
+    const bool record = p->record_hits && !p->stats && w.hitmask != nullptr && !scene->disp;
     pf_status s =
         cuda_status(launch_render_fwd(*scene, *p, w, rgb, T, last, record, (cudaStream_t)stream), "pf_render_fwd");
     p->masks_valid = !s && record;
@@ -401,6 +406,10 @@ pf_status pf_render_fwd_contrib(const pf_scene *scene, pf_plan *p, void *ws, flo
     if (!p || !ws || !scene_ok(scene, p) || !rgb || !T || !last) return PF_ERR_INVALID_ARG;
     if (p->n > 0 && (!contrib_sparse || !contrib_normal)) {
         set_error("pf_render_fwd_contrib: null contribution array");
+        return PF_ERR_INVALID_ARG;
+    }
+    if (scene->disp && p->n > 0) {
+        set_error("pf_render_fwd_contrib: not available for a displaced scene");
         return PF_ERR_INVALID_ARG;
     }
     WS w = p->ws(ws);
@@ -418,6 +427,10 @@ pf_status pf_render_bwd(const pf_scene *scene, pf_plan *p, void *ws, const float
     if (!p || !ws || !scene_ok(scene, p) || !dL_drgb || !T || !last || !g) return PF_ERR_INVALID_ARG;
     if (p->n > 0 && (!g->pos || !g->w || !g->R || !g->sigma || !g->rgb || !g->normal || !g->offset || !g->tex)) {
         set_error("pf_render_bwd: null gradient pointer");
+        return PF_ERR_INVALID_ARG;
+    }
+    if (scene->disp && p->n > 0) {
+        set_error("pf_render_bwd: no adjoint for a displaced scene");
         return PF_ERR_INVALID_ARG;
     }
     WS w = p->ws(ws);

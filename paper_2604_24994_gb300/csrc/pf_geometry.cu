@@ -18,7 +18,8 @@ namespace pf {
 // and is dropped (Sec. 3.2: it cannot cut the cell); one at distance
 // < -R_i excludes the whole ball and marks the cell empty.  Planes whose
 // facet is shown empty by a single other plane or the dipole face are
-// dropped as well (drop_implied_planes).
+// dropped as well (drop_implied_planes; a displaced face is taken at its
+// highest, the offset plus the largest site displacement).
 // ---------------------------------------------------------------------------
 
 // FP64 1/sqrt(x): float estimate refined by two Newton steps (relative
@@ -144,8 +145,13 @@ __global__ void __launch_bounds__(256) prepare_kernel(pf_scene s, const float4 *
             cnt++;
         }
     }
+    // the face as a witness at its widest: a displaced face (Eq. svdisp) moves
+    // by a convex combination of the site displacements, at most their maximum
+    float face_off = s.offset[i];
+    if (s.disp)
+        face_off += fmaxf(fmaxf(s.disp[4 * i], s.disp[4 * i + 1]), fmaxf(s.disp[4 * i + 2], s.disp[4 * i + 3]));
     if (!empty) cnt = drop_implied_planes(planes + (int64_t)i * K, planes_lo + (int64_t)i * K,
-                                          plane_nb + (int64_t)i * K, cnt, make_float4(nx, ny, nz, s.offset[i]), Rf);
+                                          plane_nb + (int64_t)i * K, cnt, make_float4(nx, ny, nz, face_off), Rf);
     // nearest planes first: they cut the most of the ball, so a warp whose
     // segments all become empty stops the plane loop earliest
     {

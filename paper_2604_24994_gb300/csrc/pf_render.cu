@@ -219,15 +219,45 @@ __device__ __forceinline__ bool sphere_chord(const float *__restrict__ cr, const
     return true;
 }
 
+// Displacement of the face for this ray (Eq. svdisp, one-step plane shift):
+// the ray crosses the base face at s = num / fden from its closest approach,
+// at y = q + s d from the site; there u = (e1.y, e2.y) / R, and the face
+// moves by delta = sum_k W_k disp_k with the texture's soft-Voronoi weights.
+// A ray parallel to the face sees no displacement.  u is scaled back to
+// 1e6 where a near-parallel crossing lies farther: the weights there are
+// already the limit of the ray's direction.
+__device__ __forceinline__ float face_delta(const float *__restrict__ cr, float3 q, float3 dh, float num,
+                                            float fden, float4 dk) {
+    if (!(fabsf(fden) > 0.0f)) return 0.0f;
+    const float s = num / fden;
+    const float3 y = f3(fmaf(s, dh.x, q.x), fmaf(s, dh.y, q.y), fmaf(s, dh.z, q.z));
+    float u0 = dot3(f3(cr[CR_E1], cr[CR_E1 + 1], cr[CR_E1 + 2]), y);
+    float u1 = dot3(f3(cr[CR_E2], cr[CR_E2 + 1], cr[CR_E2 + 2]), y);
+    const float um = fmaxf(fabsf(u0), fabsf(u1));
+    if (um > 1e6f) {
+        const float sc = 1e6f / um;
+        u0 *= sc;
+        u1 *= sc;
+    }
+    // sites (-,-), (+,-), (-,+), (+,+) at a third of R, as the texture's
+    const float a0 = u0 + SITE, a1 = u0 - SITE, b0 = u1 + SITE, b1 = u1 - SITE;
+    const float l0 = -KAPPA * sqrtf(a0 * a0 + b0 * b0), l1 = -KAPPA * sqrtf(a1 * a1 + b0 * b0);
+    const float l2 = -KAPPA * sqrtf(a0 * a0 + b1 * b1), l3 = -KAPPA * sqrtf(a1 * a1 + b1 * b1);
+    const float mx = fmaxf(fmaxf(l0, l1), fmaxf(l2, l3));
+    const float w0 = __expf(l0 - mx), w1 = __expf(l1 - mx), w2 = __expf(l2 - mx), w3 = __expf(l3 - mx);
+    return (w0 * dk.x + w1 * dk.y + w2 * dk.z + w3 * dk.w) / (w0 + w1 + w2 + w3);
+}
+
 // Clip the chord with the cell's radical planes pl[0..np), the dipole face,
 // then refine near-parallel ends.  False if the segment is empty.  NEED sets
 // sg.nplanes to the planes this ray needs on its own (up to the one that
-// empties its segment) instead of the planes the warp evaluated.
-template <bool GRAD, bool NEED = false>
+// empties its segment) instead of the planes the warp evaluated.  DISP
+// moves the face by the ray's displacement (face_delta, from dk).
+template <bool GRAD, bool NEED = false, bool DISP = false>
 __device__ __forceinline__ bool clip_chord(const float *__restrict__ cr, const float *__restrict__ vr,
                                            const float4 *__restrict__ pl, int np,
                                            const float4 *__restrict__ lo_glob, const Ray &ray, const Chord &ch,
-                                           Seg &sg, unsigned lanes = 0u) {
+                                           Seg &sg, unsigned lanes = 0u, float4 dk = float4{0.f, 0.f, 0.f, 0.f}) {
     const float3 dh = ray.dh, q = ch.q;
     const float R = cr[CR_R];
     const float sig = cr[CR_SIG];
@@ -244,10 +274,16 @@ __device__ __forceinline__ bool clip_chord(const float *__restrict__ cr, const f
     // no end unless the ray runs outside the half (num < 0): then it empties
     // the segment
     float fden;
+    float foff = cr[CR_OFF];
     {
         const float3 n = f3(cr[CR_N], cr[CR_N + 1], cr[CR_N + 2]);
-        const float num = cr[CR_OFF] - dot3(q, n);
+        float num = foff - dot3(q, n);
         fden = dot3(dh, n);
+        if (DISP) {
+            const float dl = face_delta(cr, q, dh, num, fden, dk);
+            foff += dl;
+            num += dl;
+        }
         const float t = num * rcp_approx(fden);
         const bool ent = __float_as_int(fden) < 0;
         const bool ua = ent && t > sa;
@@ -305,14 +341,14 @@ __device__ __forceinline__ bool clip_chord(const float *__restrict__ cr, const f
         float d64;
         if (ra) {
             sa = ka >= 0 ? refine_plane64(vr, pl[ka], lo_glob[ka], ray, sa, d64)
-                         : refine_plane64(vr, make_float4(cr[CR_N], cr[CR_N + 1], cr[CR_N + 2], cr[CR_OFF]),
+                         : refine_plane64(vr, make_float4(cr[CR_N], cr[CR_N + 1], cr[CR_N + 2], foff),
                                           make_float4(cr[CR_NLO], cr[CR_NLO + 1], cr[CR_NLO + 2], 0.f), ray, sa, d64);
             if (GRAD) dena = d64;
             sg.refined++;
         }
         if (rb) {
             sb = kb >= 0 ? refine_plane64(vr, pl[kb], lo_glob[kb], ray, sb, d64)
-                         : refine_plane64(vr, make_float4(cr[CR_N], cr[CR_N + 1], cr[CR_N + 2], cr[CR_OFF]),
+                         : refine_plane64(vr, make_float4(cr[CR_N], cr[CR_N + 1], cr[CR_N + 2], foff),
                                           make_float4(cr[CR_NLO], cr[CR_NLO + 1], cr[CR_NLO + 2], 0.f), ray, sb, d64);
             if (GRAD) denb = d64;
             sg.refined++;
@@ -342,7 +378,8 @@ __device__ __forceinline__ bool segment_from_kinds(const float *__restrict__ cr,
     const float sig = cr[CR_SIG];
     sg.refined = ch.refined;
     const float3 n = f3(cr[CR_N], cr[CR_N + 1], cr[CR_N + 2]);
-    const float fnum = cr[CR_OFF] - dot3(q, n);
+    const float foff = cr[CR_OFF];  // (replays never see a displaced face)
+    const float fnum = foff - dot3(q, n);
     const float fden = dot3(dh, n);
     const float tf = fnum * rcp_approx(fden);
     sg.dnd = fden;
@@ -367,14 +404,14 @@ __device__ __forceinline__ bool segment_from_kinds(const float *__restrict__ cr,
         float d64;
         if (ra) {
             sa = ka >= 0 ? refine_plane64(vr, pl[ka], lo_glob[ka], ray, sa, d64)
-                         : refine_plane64(vr, make_float4(cr[CR_N], cr[CR_N + 1], cr[CR_N + 2], cr[CR_OFF]),
+                         : refine_plane64(vr, make_float4(cr[CR_N], cr[CR_N + 1], cr[CR_N + 2], foff),
                                           make_float4(cr[CR_NLO], cr[CR_NLO + 1], cr[CR_NLO + 2], 0.f), ray, sa, d64);
             if (GRAD) dena = d64;
             sg.refined++;
         }
         if (rb) {
             sb = kb >= 0 ? refine_plane64(vr, pl[kb], lo_glob[kb], ray, sb, d64)
-                         : refine_plane64(vr, make_float4(cr[CR_N], cr[CR_N + 1], cr[CR_N + 2], cr[CR_OFF]),
+                         : refine_plane64(vr, make_float4(cr[CR_N], cr[CR_N + 1], cr[CR_N + 2], foff),
                                           make_float4(cr[CR_NLO], cr[CR_NLO + 1], cr[CR_NLO + 2], 0.f), ray, sb, d64);
             if (GRAD) denb = d64;
             sg.refined++;
@@ -454,6 +491,11 @@ struct Stage {
     __device__ __forceinline__ int *poff(int b) const {
         return reinterpret_cast<int *>(base + 2 * buf_bytes()) + 2 * BATCH + b * (BATCH + 1);
     }
+    // face displacements [2][BATCH] (displaced scenes only), 16-byte aligned
+    __device__ __forceinline__ float4 *dsp(int b) const {
+        return reinterpret_cast<float4 *>(base + ((2 * buf_bytes() + (4 * BATCH + 2) * 4 + 15) & ~(size_t)15)) +
+               b * BATCH;
+    }
 };
 
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
@@ -472,7 +514,8 @@ __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wai
 // reads the 32 ids and plane counts itself (no barrier before the copies);
 // warp 0 also publishes them for the consumers.
 __device__ __forceinline__ void issue_batch(const Stage &sg, int buf, const uint32_t *__restrict__ list, int nb,
-                                            const WS &w, int64_t vbase, int K, bool with_nb) {
+                                            const WS &w, int64_t vbase, int K, bool with_nb,
+                                            const float *__restrict__ disp = nullptr) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     int id = 0, np = 0;
     if (lane < nb) {
@@ -490,19 +533,22 @@ __device__ __forceinline__ void issue_batch(const Stage &sg, int buf, const uint
         sg.poff(buf)[lane + 1] = incl;
         if (lane == 0) sg.poff(buf)[0] = 0;
     }
-    // records: nb x (8 + 2) chunks over all threads (uniform trip count: the
-    // shuffles need every lane)
-    const int nrec = nb * 10;
+    // records: nb x (8 + 2 (+ 1 displacement)) chunks over all threads
+    // (uniform trip count: the shuffles need every lane)
+    const int parts = disp ? 11 : 10;
+    const int nrec = nb * parts;
     for (int q0 = 0; q0 < nrec; q0 += TILE_PIX) {
         const int q = q0 + tid;
-        const int j = (q < nrec ? q : 0) / 10, part = q - j * 10;
+        const int j = (q < nrec ? q : 0) / parts, part = q - j * parts;
         const int c = __shfl_sync(0xffffffffu, id, j);
         if (q < nrec) {
             if (part < 8)
                 cp_async16(sg.cr(buf) + j * CELLREC_F + part * 4, w.cellrec + (int64_t)c * CELLREC_F + part * 4);
-            else
+            else if (part < 10)
                 cp_async16(sg.vr(buf) + j * VIEWREC_F + (part - 8) * 4,
                            w.viewrec + (vbase + c) * VIEWREC_F + (part - 8) * 4);
+            else
+                cp_async16(sg.dsp(buf) + j, disp + (int64_t)c * 4);
         }
     }
     // planes: warp w copies the planes of cells w, w + 8, ...
@@ -535,6 +581,7 @@ struct RenderArgs {
     int64_t mask_batches;   // batch slots per warp in the hit-mask array
     float *contrib_sparse;  // [N] sum of T alpha per cell (pf_render_fwd_contrib), or null
     float *contrib_normal;  // [N] sum of T alpha max(nh.d, 0)^2 per cell, or null
+    const float *disp;      // [N][4] face displacement at the texture sites, or null
 };
 
 // Hit masks: one 32-bit word per (warp of the tile, batch, pixel of the
@@ -598,10 +645,11 @@ __device__ __forceinline__ unsigned warp_mask(const Stage &sg, int buf, int nb, 
     return __ballot_sync(0xffffffffu, ov);
 }
 
-__host__ __device__ inline size_t stage_bytes(int K, bool with_nb) {
+__host__ __device__ inline size_t stage_bytes(int K, bool with_nb, bool with_disp = false) {
     const size_t k = K > 0 ? (size_t)K : 1;
     const size_t buf = (size_t)BATCH * (CELLREC_F + VIEWREC_F) * 4 + BATCH * k * (with_nb ? 24 : 16);
-    return 2 * buf + (2 * BATCH + 2 * (BATCH + 1)) * 4;
+    const size_t ids = 2 * buf + (2 * BATCH + 2 * (BATCH + 1)) * 4;
+    return with_disp ? ((ids + 15) & ~(size_t)15) + 2 * BATCH * 16 : ids;
 }
 
 __device__ __forceinline__ Stage make_stage(float4 *smem, int K, bool with_nb) {
@@ -617,7 +665,7 @@ __device__ __forceinline__ Stage make_stage(float4 *smem, int K, bool with_nb) {
 // replays (only with a hit-mask region in the workspace); CONTRIB: add each
 // cell's contributions (Sec. 4: T alpha for L_sparse and the pruning EMA,
 // T alpha max(nh.d, 0)^2 for L_normal) over the frame's pixels.
-template <bool STATS, bool REC, bool CONTRIB>
+template <bool STATS, bool REC, bool CONTRIB, bool DISP = false>
 __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, int64_t n_tiles,
                                                                  float *__restrict__ rgb_out,
                                                                  float *__restrict__ T_out,
@@ -661,13 +709,14 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, i
     int nhit = 0;  // hits so far (hit recording)
     bool done = !inside || !has_ray;
 
-    if (nbat > 0) issue_batch(sg, 0, A.w.inst_sorted + s, min(BATCH, n), A.w, vbase, A.K, false);
+    const float *disp = DISP ? A.disp : nullptr;
+    if (nbat > 0) issue_batch(sg, 0, A.w.inst_sorted + s, min(BATCH, n), A.w, vbase, A.K, false, disp);
     for (int k = 0; k < nbat; k++) {
         // every warp is done with batch k-1, whose buffer batch k+1 reuses
         if (__syncthreads_count(!done) == 0) break;
         if (k + 1 < nbat) {
             issue_batch(sg, (k + 1) & 1, A.w.inst_sorted + s + (k + 1) * BATCH, min(BATCH, n - (k + 1) * BATCH),
-                        A.w, vbase, A.K, false);
+                        A.w, vbase, A.K, false, disp);
             cp_async_wait_one();
         } else {
             cp_async_wait_all();
@@ -693,8 +742,9 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, i
                 const int o = sg.poff(buf)[j];
                 np = sg.poff(buf)[j + 1] - o;
                 if (pass)
-                    hit = clip_chord<false, STATS>(cr, vr, sg.pl(buf) + o, np,
-                                                   A.w.planes_lo + (int64_t)sg.ids(buf)[j] * A.K, ray, ch, seg, pm);
+                    hit = clip_chord<false, STATS, DISP>(cr, vr, sg.pl(buf) + o, np,
+                                                         A.w.planes_lo + (int64_t)sg.ids(buf)[j] * A.K, ray, ch, seg,
+                                                         pm, DISP ? sg.dsp(buf)[j] : float4{0.f, 0.f, 0.f, 0.f});
             }
             if (STATS && !done) {
                 const unsigned act = __ballot_sync(__activemask(), true);
@@ -1196,6 +1246,7 @@ static RenderArgs make_args(const pf_scene &s, const Plan &p, const WS &w) {
     A.mask_batches = mask_batches(p);
     A.contrib_sparse = nullptr;
     A.contrib_normal = nullptr;
+    A.disp = s.disp;
     return A;
 }
 
@@ -1221,12 +1272,15 @@ cudaError_t launch_render_fwd(const pf_scene &s, const Plan &p, const WS &w, flo
     A.contrib_sparse = contrib_sparse;
     A.contrib_normal = contrib_normal;
     const bool contrib = contrib_sparse != nullptr;
-    const size_t smem = fwd_smem(p.k);
+    const bool disp = s.disp != nullptr;
+    if (disp && (contrib || p.stats || record)) return cudaErrorNotSupported;  // the C API refuses these first
+    const size_t smem = disp ? stage_bytes(p.k, false, true) : fwd_smem(p.k);
     cudaError_t e = cudaMemsetAsync(&w.counters->q_fwd, 0, sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
-    auto k = contrib ? (record ? render_fwd_kernel<false, true, true> : render_fwd_kernel<false, false, true>)
-                     : p.stats ? render_fwd_kernel<true, false, false>
-                               : (record ? render_fwd_kernel<false, true, false> : render_fwd_kernel<false, false, false>);
+    auto k = disp      ? render_fwd_kernel<false, false, false, true>
+             : contrib ? (record ? render_fwd_kernel<false, true, true> : render_fwd_kernel<false, false, true>)
+             : p.stats ? render_fwd_kernel<true, false, false>
+                       : (record ? render_fwd_kernel<false, true, false> : render_fwd_kernel<false, false, false>);
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<persistent_grid(k, smem, p.total_tiles), TILE_PIX, smem, st>>>(A, p.total_tiles, rgb, T, last);
     return cudaGetLastError();
