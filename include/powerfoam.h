@@ -61,10 +61,11 @@ typedef struct {
      * k.  A ray crossing the base face at face coordinates u sees the face
      * moved by delta = sum_k W_k(u) disp[i][k], with the soft-Voronoi
      * weights of the texture (Eq. svdisp, one-step plane shift); a ray
-     * parallel to the face sees no displacement.  Used by the plain forward
-     * (pf_render_fwd, pf_render_fwd_static, the server); the forward does
-     * not record hits then, and pf_render_fwd_contrib, stats passes and
-     * pf_render_bwd return PF_ERR_INVALID_ARG for a displaced scene. */
+     * parallel to the face sees no displacement.  pf_render_fwd (also
+     * recording hits), pf_render_fwd_static, the server and pf_render_bwd
+     * (which then adds dL/ddisp into pf_scene_grad.disp) honour it;
+     * pf_render_fwd_contrib and stats passes return PF_ERR_INVALID_ARG for a
+     * displaced scene. */
     const float *disp;
 } pf_scene;
 
@@ -91,6 +92,7 @@ typedef struct {
  * into them (zero them first for a fresh gradient). */
 typedef struct {
     float *pos, *w, *R, *sigma, *rgb, *normal, *offset, *tex;
+    float *disp; /* [N][4], required when the scene has a displacement, else ignored */
 } pf_scene_grad;
 
 typedef struct pf_plan pf_plan;

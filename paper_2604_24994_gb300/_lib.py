@@ -39,7 +39,7 @@ class Camera(C.Structure):
 
 
 class SceneGrad(C.Structure):
-    _fields_ = [(k, C.c_void_p) for k in ("pos", "w", "R", "sigma", "rgb", "normal", "offset", "tex")]
+    _fields_ = [(k, C.c_void_p) for k in ("pos", "w", "R", "sigma", "rgb", "normal", "offset", "tex", "disp")]
 
 
 class Stats(C.Structure):

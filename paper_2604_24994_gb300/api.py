@@ -242,10 +242,11 @@ class Renderer:
         """pf_render_bwd: returns a dict of gradient tensors (added into
         `grads` when given)."""
         p = scene.params if params is None else params
+        keys = PARAMS + (("disp",) if p.get("disp") is not None else ())
         if grads is None:
-            grads = {k: torch.zeros_like(p[k]) for k in PARAMS}
+            grads = {k: torch.zeros_like(p[k]) for k in keys}
         g = _lib.SceneGrad()
-        for k in PARAMS:
+        for k in keys:
             setattr(g, k, grads[k].data_ptr() if grads[k].numel() else None)
         dL_drgb = dL_drgb.contiguous().float()
         dL_dT = None if dL_dT is None else dL_dT.contiguous().float()

@@ -392,8 +392,7 @@ pf_status pf_render_fwd(const pf_scene *scene, pf_plan *p, void *ws, float *rgb,
         set_error("pf_render_fwd: no stats pass for a displaced scene");
         return PF_ERR_INVALID_ARG;
     }
-    // a displaced scene has no adjoint on the GPU: nothing to record for one
-    const bool record = p->record_hits && !p->stats && w.hitmask != nullptr && !scene->disp;
+    const bool record = p->record_hits && !p->stats && w.hitmask != nullptr;
     pf_status s =
         cuda_status(launch_render_fwd(*scene, *p, w, rgb, T, last, record, (cudaStream_t)stream), "pf_render_fwd");
     p->masks_valid = !s && record;
@@ -429,8 +428,8 @@ pf_status pf_render_bwd(const pf_scene *scene, pf_plan *p, void *ws, const float
         set_error("pf_render_bwd: null gradient pointer");
         return PF_ERR_INVALID_ARG;
     }
-    if (scene->disp && p->n > 0) {
-        set_error("pf_render_bwd: no adjoint for a displaced scene");
+    if (scene->disp && p->n > 0 && !g->disp) {
+        set_error("pf_render_bwd: a displaced scene needs grad->disp");
         return PF_ERR_INVALID_ARG;
     }
     WS w = p->ws(ws);

@@ -219,33 +219,61 @@ __device__ __forceinline__ bool sphere_chord(const float *__restrict__ cr, const
     return true;
 }
 
+// Face coordinates of a point y (relative to the site) and the soft-Voronoi
+// weights of the four texture sites there.
+struct Tex {
+    float3 ys;
+    float u1, u2;
+    float ax[2], ay[2];     // u - site offsets: ax[0] = u1 + 1/3, ax[1] = u1 - 1/3
+    float r[4], W[4];
+};
+
 // Displacement of the face for this ray (Eq. svdisp, one-step plane shift):
 // the ray crosses the base face at s = num / fden from its closest approach,
 // at y = q + s d from the site; there u = (e1.y, e2.y) / R, and the face
 // moves by delta = sum_k W_k disp_k with the texture's soft-Voronoi weights.
-// A ray parallel to the face sees no displacement.  u is scaled back to
-// 1e6 where a near-parallel crossing lies farther: the weights there are
-// already the limit of the ray's direction.
+// A ray parallel to the face sees no displacement.  s is kept within 1e6 R:
+// the weights of a farther crossing are already the limit of the ray's
+// direction.  With `tx` the crossing's coordinates and weights are returned
+// (for the adjoint).
 __device__ __forceinline__ float face_delta(const float *__restrict__ cr, float3 q, float3 dh, float num,
-                                            float fden, float4 dk) {
-    if (!(fabsf(fden) > 0.0f)) return 0.0f;
-    const float s = num / fden;
-    const float3 y = f3(fmaf(s, dh.x, q.x), fmaf(s, dh.y, q.y), fmaf(s, dh.z, q.z));
-    float u0 = dot3(f3(cr[CR_E1], cr[CR_E1 + 1], cr[CR_E1 + 2]), y);
-    float u1 = dot3(f3(cr[CR_E2], cr[CR_E2 + 1], cr[CR_E2 + 2]), y);
-    const float um = fmaxf(fabsf(u0), fabsf(u1));
-    if (um > 1e6f) {
-        const float sc = 1e6f / um;
-        u0 *= sc;
-        u1 *= sc;
+                                            float fden, float4 dk, Tex *tx = nullptr) {
+    if (!(fabsf(fden) > 0.0f)) {
+        if (tx) *tx = Tex{};
+        return 0.0f;
     }
+    const float big = 1e6f * cr[CR_R];
+    const float s = fminf(fmaxf(num / fden, -big), big);
+    const float3 y = f3(fmaf(s, dh.x, q.x), fmaf(s, dh.y, q.y), fmaf(s, dh.z, q.z));
+    const float u0 = dot3(f3(cr[CR_E1], cr[CR_E1 + 1], cr[CR_E1 + 2]), y);
+    const float u1 = dot3(f3(cr[CR_E2], cr[CR_E2 + 1], cr[CR_E2 + 2]), y);
     // sites (-,-), (+,-), (-,+), (+,+) at a third of R, as the texture's
     const float a0 = u0 + SITE, a1 = u0 - SITE, b0 = u1 + SITE, b1 = u1 - SITE;
-    const float l0 = -KAPPA * sqrtf(a0 * a0 + b0 * b0), l1 = -KAPPA * sqrtf(a1 * a1 + b0 * b0);
-    const float l2 = -KAPPA * sqrtf(a0 * a0 + b1 * b1), l3 = -KAPPA * sqrtf(a1 * a1 + b1 * b1);
+    const float r0 = sqrtf(a0 * a0 + b0 * b0), r1 = sqrtf(a1 * a1 + b0 * b0);
+    const float r2 = sqrtf(a0 * a0 + b1 * b1), r3 = sqrtf(a1 * a1 + b1 * b1);
+    const float l0 = -KAPPA * r0, l1 = -KAPPA * r1, l2 = -KAPPA * r2, l3 = -KAPPA * r3;
     const float mx = fmaxf(fmaxf(l0, l1), fmaxf(l2, l3));
     const float w0 = __expf(l0 - mx), w1 = __expf(l1 - mx), w2 = __expf(l2 - mx), w3 = __expf(l3 - mx);
-    return (w0 * dk.x + w1 * dk.y + w2 * dk.z + w3 * dk.w) / (w0 + w1 + w2 + w3);
+    const float z = w0 + w1 + w2 + w3;
+    if (tx) {
+        const float iz = 1.0f / z;
+        tx->ys = y;
+        tx->u1 = u0;
+        tx->u2 = u1;
+        tx->ax[0] = a0;
+        tx->ax[1] = a1;
+        tx->ay[0] = b0;
+        tx->ay[1] = b1;
+        tx->r[0] = r0;
+        tx->r[1] = r1;
+        tx->r[2] = r2;
+        tx->r[3] = r3;
+        tx->W[0] = w0 * iz;
+        tx->W[1] = w1 * iz;
+        tx->W[2] = w2 * iz;
+        tx->W[3] = w3 * iz;
+    }
+    return (w0 * dk.x + w1 * dk.y + w2 * dk.z + w3 * dk.w) / z;
 }
 
 // Clip the chord with the cell's radical planes pl[0..np), the dipole face,
@@ -368,19 +396,25 @@ __device__ __forceinline__ bool clip_chord(const float *__restrict__ cr, const f
 // The segment of a recorded hit from its active constraints (ka, kb): the
 // same float expressions as clip_chord for those two constraints and the
 // face, then the same refinement, so the ends equal the forward's.
-template <bool GRAD>
+template <bool GRAD, bool DISP = false>
 __device__ __forceinline__ bool segment_from_kinds(const float *__restrict__ cr, const float *__restrict__ vr,
                                                    const float4 *__restrict__ pl,
                                                    const float4 *__restrict__ lo_glob, const Ray &ray,
-                                                   const Chord &ch, int ka, int kb, Seg &sg) {
+                                                   const Chord &ch, int ka, int kb, Seg &sg,
+                                                   float4 dk = float4{0.f, 0.f, 0.f, 0.f}) {
     const float3 dh = ray.dh, q = ch.q;
     const float R = cr[CR_R];
     const float sig = cr[CR_SIG];
     sg.refined = ch.refined;
     const float3 n = f3(cr[CR_N], cr[CR_N + 1], cr[CR_N + 2]);
-    const float foff = cr[CR_OFF];  // (replays never see a displaced face)
-    const float fnum = foff - dot3(q, n);
+    float foff = cr[CR_OFF];
+    float fnum = foff - dot3(q, n);
     const float fden = dot3(dh, n);
+    if (DISP) {  // the forward's displaced face, the same expressions
+        const float dl = face_delta(cr, q, dh, fnum, fden, dk);
+        foff += dl;
+        fnum += dl;
+    }
     const float tf = fnum * rcp_approx(fden);
     sg.dnd = fden;
     if (fabsf(fden) < 0x1p-20f) sg.dnd = face_side64(cr, ray);
@@ -430,13 +464,6 @@ __device__ __forceinline__ bool segment_from_kinds(const float *__restrict__ cr,
 
 // Soft-Voronoi face colour (Eq. svrad): weights of the four sites at the
 // texture point y = q + s d (the dense segment's end on the face side).
-struct Tex {
-    float3 ys;
-    float u1, u2;
-    float ax[2], ay[2];     // u - site offsets: ax[0] = u1 + 1/3, ax[1] = u1 - 1/3
-    float r[4], W[4];
-};
-
 __device__ __forceinline__ float3 face_colour(const float *__restrict__ cr, const Seg &sg, const Ray &ray, Tex &tx) {
     const float ss = sg.dnd > 0.0f ? sg.sb : sg.sa;
     tx.ys = f3(fmaf(ss, ray.dh.x, sg.q.x), fmaf(ss, ray.dh.y, sg.q.y), fmaf(ss, ray.dh.z, sg.q.z));
@@ -582,6 +609,7 @@ struct RenderArgs {
     float *contrib_sparse;  // [N] sum of T alpha per cell (pf_render_fwd_contrib), or null
     float *contrib_normal;  // [N] sum of T alpha max(nh.d, 0)^2 per cell, or null
     const float *disp;      // [N][4] face displacement at the texture sites, or null
+    float *gdisp;           // [N][4] its gradient (the backward adds into it), or null
 };
 
 // Hit masks: one 32-bit word per (warp of the tile, batch, pixel of the
@@ -885,6 +913,22 @@ __device__ __forceinline__ float warp_transpose_sum(float (&v)[32], int lane) {
     return v[0];
 }
 
+// dL/dn through the face frame (Duff et al., JCGT 2017) for u = (e1.y, e2.y)/R
+// with dL/du = (c1, c2) R: dL/de1 = c1 y, dL/de2 = c2 y, and
+// e1 = (1 + s x^2 a, s b, -s x), e2 = (b, s + y^2 a, -y), b = x y a.
+__device__ __forceinline__ float3 frame_grad(const float *__restrict__ cr, float c1, float c2, float3 y) {
+    const float3 g1 = f3(c1 * y.x, c1 * y.y, c1 * y.z);
+    const float3 g2 = f3(c2 * y.x, c2 * y.y, c2 * y.z);
+    const float nx = cr[CR_N], ny = cr[CR_N + 1], nz = cr[CR_N + 2];
+    const float sgn = nz >= 0.f ? 1.f : -1.f;
+    const float ca = -rcp_approx(sgn + nz);
+    const float da = ca * ca;
+    const float db0 = ny * ca, db1 = nx * ca, db2 = nx * ny * da;
+    return f3(g1.x * (2.f * sgn * nx * ca) + g1.y * sgn * db0 + g1.z * (-sgn) + g2.x * db0,
+              g1.y * sgn * db1 + g2.x * db1 + g2.y * (2.f * ny * ca) + g2.z * (-1.f),
+              g1.x * (sgn * nx * nx * da) + g1.y * sgn * db2 + g2.x * db2 + g2.y * (ny * ny * da));
+}
+
 // dL/ds of one segment end -> gradients of its active constraint, the same
 // instructions for every kind (the lanes of a warp meet different kinds).
 // y = q + s d is the end point relative to p_i; the constraint c(y) = rhs
@@ -941,7 +985,7 @@ __device__ __forceinline__ void route_end(float gt, int kind, float s, float den
 
 // MASKS: replay only the (cell, lane) pairs the forward recorded as hits
 // (the hit masks of the current bins); otherwise re-test every listed cell.
-template <bool MASKS>
+template <bool MASKS, bool DISP = false>
 __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, int64_t n_tiles,
                                                                  const float *__restrict__ dL_drgb,
                                                                  const float *__restrict__ dL_dT,
@@ -1007,13 +1051,14 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
     const int nbat = (maxlast + BATCH - 1) / BATCH;
     if (nbat > 0)
         issue_batch(stg, (nbat - 1) & 1, list + (nbat - 1) * BATCH, maxlast - (nbat - 1) * BATCH, A.w, vbase, A.K,
-                    true);
+                    true, DISP ? A.disp : nullptr);
     for (int b = nbat - 1; b >= 0; b--) {
         // bit j: the forward found this pixel's segment in cell j non-empty
         const unsigned my_hits = MASKS ? A.w.hitmask[hitmask_slot(A, tile, s, b, warp) + lane] : 0u;
         __syncthreads();  // batch b+1, whose buffer batch b-1 reuses, is done
         if (b > 0) {
-            issue_batch(stg, (b - 1) & 1, list + (b - 1) * BATCH, BATCH, A.w, vbase, A.K, true);
+            issue_batch(stg, (b - 1) & 1, list + (b - 1) * BATCH, BATCH, A.w, vbase, A.K, true,
+                        DISP ? A.disp : nullptr);
             cp_async_wait_one();
         } else {
             cp_async_wait_all();
@@ -1035,6 +1080,7 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
             const int cell = stg.ids(buf)[j];
             const float *cr = s_cr + j * CELLREC_F;
             const float *vr = s_vr + j * VIEWREC_F;
+            const float4 dk = DISP ? stg.dsp(buf)[j] : float4{0.f, 0.f, 0.f, 0.f};
             const int o = poff[j], np = poff[j + 1] - o;
             Seg sg;
             Chord ch;
@@ -1050,14 +1096,16 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
                 }
                 if (mine && sphere_chord<true>(cr, vr, ray, ch, cand)) {
                     if (kk != 0xffffu)
-                        hit = segment_from_kinds<true>(cr, vr, s_pl + o, A.w.planes_lo + (int64_t)cell * A.K, ray,
-                                                       ch, (int)(kk & 127u) - 3, (int)(kk >> 7) - 3, sg);
+                        hit = segment_from_kinds<true, DISP>(cr, vr, s_pl + o, A.w.planes_lo + (int64_t)cell * A.K,
+                                                             ray, ch, (int)(kk & 127u) - 3, (int)(kk >> 7) - 3, sg,
+                                                             dk);
                     else  // beyond the recorded hits of this pixel: clip against every plane
-                        hit = clip_chord<true>(cr, vr, s_pl + o, np, A.w.planes_lo + (int64_t)cell * A.K, ray, ch,
-                                               sg);
+                        hit = clip_chord<true, false, DISP>(cr, vr, s_pl + o, np,
+                                                            A.w.planes_lo + (int64_t)cell * A.K, ray, ch, sg, 0u, dk);
                 }
             } else if (mine && sphere_chord<true>(cr, vr, ray, ch, cand)) {
-                hit = clip_chord<true>(cr, vr, s_pl + o, np, A.w.planes_lo + (int64_t)cell * A.K, ray, ch, sg);
+                hit = clip_chord<true, false, DISP>(cr, vr, s_pl + o, np, A.w.planes_lo + (int64_t)cell * A.K, ray,
+                                                    ch, sg, 0u, dk);
             }
             if (!__any_sync(0xffffffffu, hit)) continue;
             // Every lane runs the adjoint of this cell.  A lane without a hit
@@ -1120,18 +1168,10 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
                 const float iR = rcp_approx(R);
                 vv[G_R] = -(gu1 * tx.u1 + gu2 * tx.u2) * iR;
                 {
-                    // dL/de1 = gu1 y / R, dL/de2 = gu2 y / R (frame of Duff et al., JCGT 2017)
-                    const float3 g1 = f3(gu1 * tx.ys.x * iR, gu1 * tx.ys.y * iR, gu1 * tx.ys.z * iR);
-                    const float3 g2 = f3(gu2 * tx.ys.x * iR, gu2 * tx.ys.y * iR, gu2 * tx.ys.z * iR);
-                    const float nx = cr[CR_N], ny = cr[CR_N + 1], nz = cr[CR_N + 2];
-                    const float sgn = nz >= 0.f ? 1.f : -1.f;
-                    const float ca = -rcp_approx(sgn + nz);
-                    const float da = ca * ca;
-                    const float db0 = ny * ca, db1 = nx * ca, db2 = nx * ny * da;
-                    // e1 = (1 + s x^2 a, s b, -s x), e2 = (b, s + y^2 a, -y), b = x y a
-                    vv[G_N] = g1.x * (2.f * sgn * nx * ca) + g1.y * sgn * db0 + g1.z * (-sgn) + g2.x * db0;
-                    vv[G_N + 1] = g1.y * sgn * db1 + g2.x * db1 + g2.y * (2.f * ny * ca) + g2.z * (-1.f);
-                    vv[G_N + 2] = g1.x * (sgn * nx * nx * da) + g1.y * sgn * db2 + g2.x * db2 + g2.y * (ny * ny * da);
+                    const float3 gn = frame_grad(cr, gu1 * iR, gu2 * iR, tx.ys);
+                    vv[G_N] = gn.x;
+                    vv[G_N + 1] = gn.y;
+                    vv[G_N + 2] = gn.z;
                 }
                 vv[G_P] = 0.f;
                 vv[G_P + 1] = 0.f;
@@ -1148,6 +1188,49 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
                 const float4 *plp = s_pl + o;
                 route_end(gta, sg.ka, sg.sa, sg.dena, sg, ray, cr, plp, nbp, gm, vv, nba, ja);
                 route_end(gtb, sg.kb, sg.sb, sg.denb, sg, ray, cr, plp, nbp, gm, vv, nbb, jb);
+                if (DISP) {
+                    // the displaced face end moves with delta like with the offset
+                    // (ds/d delta = 1/(d.n)); delta moves with the site displacements
+                    // through W, and with u at the base crossing, whose point
+                    // yb = q + sb d rides the base face (Eq. svdisp)
+                    const float3 nf = f3(cr[CR_N], cr[CR_N + 1], cr[CR_N + 2]);
+                    const bool fa = sg.ka == K_FACE, fb = sg.kb == K_FACE;
+                    const float fden = dot3(ray.dh, nf);
+                    Tex fd;
+                    const float dl = face_delta(cr, sg.q, ray.dh, cr[CR_OFF] - dot3(sg.q, nf), fden, dk, &fd);
+                    const float gd = (fa || fb) ? ((fa ? gta : 0.f) + (fb ? gtb : 0.f)) *
+                                                      rcp_approx(fa ? sg.dena : sg.denb)
+                                                : 0.f;
+                    const float dks[4] = {dk.x, dk.y, dk.z, dk.w};
+                    float gdk[4], gv1 = 0.f, gv2 = 0.f;
+#pragma unroll
+                    for (int k = 0; k < 4; k++) {
+                        gdk[k] = gd * fd.W[k];
+                        const float gr = -KAPPA * gd * fd.W[k] * (dks[k] - dl);
+                        const float ir = fd.r[k] > 0.f ? gr * rcp_approx(fd.r[k]) : 0.0f;
+                        gv1 = fmaf(ir, fd.ax[k & 1], gv1);
+                        gv2 = fmaf(ir, fd.ay[k >> 1], gv2);
+                    }
+                    const float3 gyb = f3(gv1 * E1.x + gv2 * E2.x, gv1 * E1.y + gv2 * E2.y, gv1 * E1.z + gv2 * E2.z);
+                    vv[G_R] -= (gv1 * fd.u1 + gv2 * fd.u2) * iR;
+                    const float3 gn = frame_grad(cr, gv1 * iR, gv2 * iR, fd.ys);
+                    const float id2 = fabsf(fden) > 0.f ? dot3(gyb, ray.dh) * rcp_approx(fden) : 0.f;
+                    vv[G_N] += gn.x - id2 * fd.ys.x;
+                    vv[G_N + 1] += gn.y - id2 * fd.ys.y;
+                    vv[G_N + 2] += gn.z - id2 * fd.ys.z;
+                    vv[G_OFF] += id2;
+                    gm.x += gyb.x - id2 * nf.x;
+                    gm.y += gyb.y - id2 * nf.y;
+                    gm.z += gyb.z - id2 * nf.z;
+                    // the four site displacements: summed over the warp, one atomic each
+#pragma unroll
+                    for (int k = 0; k < 4; k++) {
+                        float v = gdk[k];
+#pragma unroll
+                        for (int o2 = 16; o2 > 0; o2 >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o2);
+                        if (lane == 0 && A.gdisp) atomicAdd(A.gdisp + 4 * (int64_t)cell + k, v);
+                    }
+                }
                 // m = o - p
                 vv[G_P] -= gm.x;
                 vv[G_P + 1] -= gm.y;
@@ -1247,6 +1330,7 @@ static RenderArgs make_args(const pf_scene &s, const Plan &p, const WS &w) {
     A.contrib_sparse = nullptr;
     A.contrib_normal = nullptr;
     A.disp = s.disp;
+    A.gdisp = nullptr;
     return A;
 }
 
@@ -1273,11 +1357,11 @@ cudaError_t launch_render_fwd(const pf_scene &s, const Plan &p, const WS &w, flo
     A.contrib_normal = contrib_normal;
     const bool contrib = contrib_sparse != nullptr;
     const bool disp = s.disp != nullptr;
-    if (disp && (contrib || p.stats || record)) return cudaErrorNotSupported;  // the C API refuses these first
+    if (disp && (contrib || p.stats)) return cudaErrorNotSupported;  // the C API refuses these first
     const size_t smem = disp ? stage_bytes(p.k, false, true) : fwd_smem(p.k);
     cudaError_t e = cudaMemsetAsync(&w.counters->q_fwd, 0, sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
-    auto k = disp      ? render_fwd_kernel<false, false, false, true>
+    auto k = disp      ? (record ? render_fwd_kernel<false, true, false, true> : render_fwd_kernel<false, false, false, true>)
              : contrib ? (record ? render_fwd_kernel<false, true, true> : render_fwd_kernel<false, false, true>)
              : p.stats ? render_fwd_kernel<true, false, false>
                        : (record ? render_fwd_kernel<false, true, false> : render_fwd_kernel<false, false, false>);
@@ -1294,10 +1378,14 @@ cudaError_t launch_render_bwd(const pf_scene &s, const Plan &p, const WS &w, con
     if (e != cudaSuccess) return e;
     if (p.total_tiles > 0) {
         RenderArgs A = make_args(s, p, w);
-        const size_t smem = bwd_smem(p.k);
+        A.gdisp = g.disp;
+        const bool disp = s.disp != nullptr;
+        const size_t smem = disp ? stage_bytes(p.k, true, true) : bwd_smem(p.k);
         e = cudaMemsetAsync(&w.counters->q_bwd, 0, sizeof(unsigned int), st);
         if (e != cudaSuccess) return e;
-        auto kern = use_masks && w.hitmask ? render_bwd_kernel<true> : render_bwd_kernel<false>;
+        const bool m = use_masks && w.hitmask;
+        auto kern = disp ? (m ? render_bwd_kernel<true, true> : render_bwd_kernel<false, true>)
+                         : (m ? render_bwd_kernel<true> : render_bwd_kernel<false>);
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         kern<<<persistent_grid(kern, smem, p.total_tiles), TILE_PIX, smem, st>>>(A, p.total_tiles, dL_drgb, dL_dT, T,
                                                                                  last);
