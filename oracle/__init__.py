@@ -32,8 +32,8 @@ _lib = None
 
 KAPPA = 6.0          # soft-Voronoi sharpness on the face, in units of 1/R
 PARAM_COLS = {"pos": (0, 3), "w": (3, 1), "R": (4, 1), "sigma": (5, 1), "rgb": (6, 3),
-              "normal": (9, 3), "offset": (12, 1), "tex": (13, 12), "disp": (25, 4)}
-NPAR = 29
+              "normal": (9, 3), "offset": (12, 1), "tex": (13, 12), "disp": (25, 4), "sites": (29, 8)}
+NPAR = 37
 ACT_SPHERE, ACT_CAMERA, ACT_DIPOLE = -1, -2, -3
 
 
@@ -50,7 +50,7 @@ def build(force: bool = False) -> str:
 class _Scene(C.Structure):
     _fields_ = [("n", C.c_int64)] + [(k, C.POINTER(C.c_double)) for k in
                                      ("pos", "w", "R", "sigma", "rgb", "normal", "offset", "tex", "disp")] + \
-               [("kappa_disp", C.c_double)]
+               [("kappa_disp", C.c_double), ("sites", C.POINTER(C.c_double))]
 
 
 class _Camera(C.Structure):
@@ -137,9 +137,11 @@ class Oracle:
     widened to float64 (exactly, for float32 inputs); `params` holds them and
     may be edited in place (finite differences do)."""
 
-    def __init__(self, scene, kappa: float = KAPPA, nthreads: int = 0, disp=None):
+    def __init__(self, scene, kappa: float = KAPPA, nthreads: int = 0, disp=None, sites=None):
         """`disp` [N,4] (or the scene's `disp` attribute): displacement of
-        each face at its four texture sites (Eq. svdisp); None for none."""
+        each face at its four texture sites (Eq. svdisp); None for none.
+        `sites` [N,4,2] (or the scene's `sites`): learned positions of those
+        sites in units of R; None for the fixed (+-1/3, +-1/3)."""
         self.kappa = float(kappa)
         self.nthreads = int(nthreads)
         self._arrs = {k: np.ascontiguousarray(np.asarray(getattr(scene, k), np.float64))
@@ -148,6 +150,10 @@ class Oracle:
             disp = getattr(scene, "disp", None)
         if disp is not None:
             self._arrs["disp"] = np.ascontiguousarray(np.asarray(disp, np.float64).reshape(-1, 4))
+        if sites is None:
+            sites = getattr(scene, "sites", None)
+        if sites is not None:
+            self._arrs["sites"] = np.ascontiguousarray(np.asarray(sites, np.float64).reshape(-1, 4, 2))
         self.params = self._arrs
         self.n = int(self._arrs["pos"].shape[0])
         s = _Scene()
@@ -310,9 +316,11 @@ class Oracle:
                               self.nthreads)
         out = {}
         for k, (c0, w) in PARAM_COLS.items():
-            if k == "disp" and "disp" not in self._arrs:
+            if k in ("disp", "sites") and k not in self._arrs:
                 continue
             out[k] = g[:, c0:c0 + w] if w > 1 else g[:, c0].copy()
+            if k == "sites":
+                out[k] = out[k].reshape(-1, 4, 2)
         return out
 
     def ray(self, cam, u, v):

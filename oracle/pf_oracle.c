@@ -54,6 +54,10 @@ typedef struct {
      * sites, [n][4] (Eq. svdisp), with soft-Voronoi sharpness kappa_disp */
     const double *disp;
     double kappa_disp;
+    /* optional (NULL: the fixed sites (+-1/3, +-1/3)): positions of the four
+     * texture / detail sites on the face, [n][4][2], in units of R, in the
+     * site order of tex and disp (Sec. 3.4: learnable detail sites) */
+    const double *sites;
 } orc_scene;
 
 /* model 0: pinhole.  model 1: equidistant fisheye (non-pinhole rasterization,
@@ -260,6 +264,12 @@ void orc_onb(const double *n, double *e1, double *e2) { onb(n, e1, e2, NULL, NUL
 /* the four texture sites, in units of R on the face, site-major */
 static const double SITE[4][2] = {{-1.0 / 3.0, -1.0 / 3.0}, {1.0 / 3.0, -1.0 / 3.0}, {-1.0 / 3.0, 1.0 / 3.0}, {1.0 / 3.0, 1.0 / 3.0}};
 
+/* site k of cell i: the scene's learned position, else the fixed one */
+static double site_x(const orc_scene *s, int64_t i, int k) { return s->sites ? s->sites[8 * i + 2 * k] : SITE[k][0]; }
+static double site_y(const orc_scene *s, int64_t i, int k) {
+    return s->sites ? s->sites[8 * i + 2 * k + 1] : SITE[k][1];
+}
+
 /*
  * Displacement of the face for one ray (Eq. svdisp, with the one-step plane
  * shift): the ray crosses the base face nh.(x - p) = off at
@@ -289,7 +299,7 @@ static double face_disp(const orc_scene *s, int64_t i, const double *o, const do
     double uu[2] = {dot3(e1, y) / R, dot3(e2, y) / R};
     double lg[4], mx = -INFINITY, Wk[4], Z = 0.0, delta = 0.0;
     for (int k = 0; k < 4; k++) {
-        double dx = uu[0] - SITE[k][0], dy = uu[1] - SITE[k][1];
+        double dx = uu[0] - site_x(s, i, k), dy = uu[1] - site_y(s, i, k);
         lg[k] = -s->kappa_disp * sqrt(dx * dx + dy * dy);
         if (lg[k] > mx) mx = lg[k];
     }
@@ -321,7 +331,7 @@ static void cell_colour(const orc_scene *s, int64_t i, const double *o, const do
     double u[2] = {dot3(e1, y) / R, dot3(e2, y) / R};
     double lg[4], mx = -INFINITY;
     for (int k = 0; k < 4; k++) {
-        double dx = u[0] - SITE[k][0], dy = u[1] - SITE[k][1];
+        double dx = u[0] - site_x(s, i, k), dy = u[1] - site_y(s, i, k);
         lg[k] = -kappa * sqrt(dx * dx + dy * dy);
         if (lg[k] > mx) mx = lg[k];
     }
@@ -550,7 +560,8 @@ int orc_hit_cells(const orc_scene *s, const orc_camera *cam, int64_t npix, const
  * Parameter columns (25 per cell): pos 0-2, w 3, R 4, sigma 5, rgb 6-8,
  * normal 9-11, offset 12, tex 13-24.
  */
-enum { P_POS = 0, P_W = 3, P_R = 4, P_SIG = 5, P_RGB = 6, P_N = 9, P_OFF = 12, P_TEX = 13, P_DISP = 25, NPAR = 29 };
+enum { P_POS = 0, P_W = 3, P_R = 4, P_SIG = 5, P_RGB = 6, P_N = 9, P_OFF = 12, P_TEX = 13, P_DISP = 25, P_SITE = 29,
+       NPAR = 37 };
 
 typedef struct {
     int32_t cell, col;
@@ -603,12 +614,17 @@ static void route_face(const orc_scene *s, int64_t i, double t, const double *o,
         for (int k = 0; k < 4; k++) {
             push(L, (int32_t)i, P_DISP + k, gd * W[k]);
             /* d delta / d u = sum_k W_k (disp_k - delta) d lg_k / du,  lg_k = -kappa |u - s_k| */
-            double dx = u[0] - SITE[k][0], dy = u[1] - SITE[k][1];
+            double dx = u[0] - site_x(s, i, k), dy = u[1] - site_y(s, i, k);
             double rr = sqrt(dx * dx + dy * dy);
             if (rr > 0.0) {
                 double c = gd * W[k] * (s->disp[4 * i + k] - delta) * (-s->kappa_disp) / rr;
                 gu[0] += c * dx;
                 gu[1] += c * dy;
+                /* the logit depends on u - s_k: the site moves opposite to u */
+                if (s->sites) {
+                    push(L, (int32_t)i, P_SITE + 2 * k, -c * dx);
+                    push(L, (int32_t)i, P_SITE + 2 * k + 1, -c * dy);
+                }
             }
         }
         /* u = (e1.yb, e2.yb)/R, yb = o + tbar d - p */
@@ -667,7 +683,7 @@ static void route_t(const orc_scene *s, int64_t i, int act, double t, const doub
 
 /*
  * Gradient of L with respect to every cell parameter, given dL/dC [npix][3]
- * and dL/dT_final [npix] for the rendered pixels.  grad [n][29] is
+ * and dL/dT_final [npix] for the rendered pixels.  grad [n][37] is
  * overwritten.  Contributions are summed in pixel order, so the result does
  * not depend on the thread count.
  */
@@ -744,12 +760,16 @@ int orc_render_grad(const orc_scene *s, const orc_cands *cd, const orc_camera *c
                 double gu[2] = {0.0, 0.0};
                 for (int kk = 0; kk < 4; kk++) {
                     double glog = W[kk] * (gW[kk] - sW);          /* dL/dlogit */
-                    double dx = uu[0] - SITE[kk][0], dy = uu[1] - SITE[kk][1];
+                    double dx = uu[0] - site_x(s, i, kk), dy = uu[1] - site_y(s, i, kk);
                     double r = sqrt(dx * dx + dy * dy);
                     if (r > 0.0) {
                         double gr = -kappa * glog;                  /* logit = -kappa r */
                         gu[0] += gr * dx / r;
                         gu[1] += gr * dy / r;
+                        if (s->sites) {                             /* r = |u - s_k| */
+                            push(L, (int32_t)i, P_SITE + 2 * kk, -gr * dx / r);
+                            push(L, (int32_t)i, P_SITE + 2 * kk + 1, -gr * dy / r);
+                        }
                     }
                 }
                 /* u = (e1.y_s, e2.y_s)/R, y_s = o + ts d - p */

@@ -884,3 +884,84 @@ def test_displacement_adjoint_matches_central_differences(seed):
             assert abs(fd - gflat[j]) <= 1e-5 * max(1.0, abs(fd)), (key, j, fd, gflat[j])
             checked += 1
     assert checked >= 45
+
+
+# ------------------------------------------------------- learned detail sites
+
+def default_sites(n):
+    return np.tile(np.array([[-1, -1], [1, -1], [-1, 1], [1, 1]], np.float64) / 3.0, (n, 1, 1))
+
+
+def test_explicit_default_sites_are_the_fixed_ones(tiny):
+    sc, cam = tiny
+    pix = np.stack(np.meshgrid(np.arange(0, 128, 9), np.arange(0, 128, 7)), -1).reshape(-1, 2)
+    disp = np.random.default_rng(2).uniform(-0.01, 0.01, (sc.n, 4))
+    a = oracle.Oracle(sc, disp=disp)
+    b = oracle.Oracle(sc, disp=disp, sites=default_sites(sc.n))
+    ca, Ta = a.render(cam, pix=pix)
+    cb, Tb = b.render(cam, pix=pix)
+    assert np.array_equal(ca, cb) and np.array_equal(Ta, Tb)
+
+
+def test_sites_around_the_crossing_weigh_equally():
+    """Sec. 3.4 with learned sites: four sites placed symmetrically around
+    the point where the ray crosses the face weigh 1/4 each, so the colour is
+    the base colour plus the mean site colour and the face moves by the mean
+    displacement, wherever the crossing lies on the face."""
+    R, sig, off = 0.5, 3.0, 0.1
+    rgb = np.array([0.2, 0.3, 0.4])
+    tex = np.random.default_rng(5).uniform(-0.2, 0.2, 12)
+    disp = np.array([[0.04, -0.01, 0.02, 0.03]])
+    sc = make_scene([0, 0, 0], 0.04, R, sig, rgb, normal=[0, 0, 1], offset=off, tex=tex)
+    x0, y0 = 0.12, -0.07                                  # the ray's crossing, world units
+    c0 = np.array([x0, y0]) / R                           # in face units (e1 = x, e2 = y for n = z)
+    a = 0.21
+    sites = (c0 + a * np.array([[-1, -1], [1, -1], [-1, 1], [1, 1]]))[None]
+    orc = oracle.Oracle(sc, disp=disp, sites=sites)
+    c, T = orc.render_rays(np.array([[x0, y0, -3.0]]), np.array([[0.0, 0.0, 1.0]]))
+    length = (off + disp.mean()) - (-math.sqrt(R * R - x0 * x0 - y0 * y0))
+    alpha = 1 - math.exp(-sig * length)
+    assert T[0] == pytest.approx(1 - alpha, rel=1e-13)
+    np.testing.assert_allclose(c[0], alpha * (rgb + tex.reshape(4, 3).mean(0)), atol=1e-13)
+
+
+@pytest.mark.parametrize("seed", [121, 122])
+def test_site_adjoint_matches_central_differences(seed):
+    """Gradients for learned site positions (through the texture weights and
+    the displacement weights) equal FP64 central differences, with every
+    other parameter group checked again alongside."""
+    sc = fd_scene(seed)
+    rng = np.random.default_rng(seed + 3)
+    disp = rng.uniform(-0.04, 0.04, (sc.n, 4))
+    sites = default_sites(sc.n) + rng.uniform(-0.15, 0.15, (sc.n, 4, 2))
+    cam = cam_at([0.55, 0.25, 0.15], 10, 10, fov=40.0)
+    orc = oracle.Oracle(sc, disp=disp, sites=sites)
+    npix = cam.width * cam.height
+    gC = rng.normal(size=(npix, 3))
+    gT = rng.normal(size=npix)
+    G = orc.render_grad(cam, gC, gT)
+
+    def loss():
+        c, T = orc.render(cam)
+        return float(np.sum(c * gC) + np.sum(T * gT))
+
+    scale = {"pos": 1e-3, "w": 1e-4, "R": 1e-3, "sigma": 1e-3, "rgb": 1e-3, "normal": 1e-3,
+             "offset": 1e-3, "tex": 1e-3, "disp": 1e-3, "sites": 1e-3}
+    checked = 0
+    for key, arr in orc.params.items():
+        flat = arr.reshape(-1)
+        gflat = np.asarray(G[key]).reshape(-1)
+        nz = np.nonzero(np.abs(gflat) > 1e-8)[0]
+        assert nz.size > 0, key
+        for j in rng.choice(nz, size=min(6 if key != "sites" else 12, nz.size), replace=False):
+            h = scale[key] * 1e-3
+            old = flat[j]
+            flat[j] = old + h
+            lp = loss()
+            flat[j] = old - h
+            lm = loss()
+            flat[j] = old
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - gflat[j]) <= 1e-5 * max(1.0, abs(fd)), (key, j, fd, gflat[j])
+            checked += 1
+    assert checked >= 55
