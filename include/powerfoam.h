@@ -67,6 +67,14 @@ typedef struct {
      * pf_render_fwd_contrib and stats passes return PF_ERR_INVALID_ARG for a
      * displaced scene. */
     const float *disp;
+    /* Optional learned detail-site positions [N][4][2] (NULL: the fixed
+     * sites (-1/3,-1/3), (1/3,-1/3), (-1/3,1/3), (1/3,1/3); 16-byte
+     * aligned), in units of R in the face frame, in the site order of tex
+     * and disp (Sec. 3.4: the detail sites are learnable).  They place both
+     * the texture's and the displacement's soft-Voronoi weights; the same
+     * entry points as disp honour them, and pf_render_bwd adds dL/dsites
+     * into pf_scene_grad.sites. */
+    const float *sites;
 } pf_scene;
 
 /* Camera: x_cam = rot (x_world - origin), OpenCV axes (x right, y down,
@@ -92,7 +100,8 @@ typedef struct {
  * into them (zero them first for a fresh gradient). */
 typedef struct {
     float *pos, *w, *R, *sigma, *rgb, *normal, *offset, *tex;
-    float *disp; /* [N][4], required when the scene has a displacement, else ignored */
+    float *disp;  /* [N][4], required when the scene has a displacement, else ignored */
+    float *sites; /* [N][4][2], required when the scene has learned sites, else ignored */
 } pf_scene_grad;
 
 typedef struct pf_plan pf_plan;

@@ -28,9 +28,10 @@ class DeviceScene:
         self.k = int(nbr.shape[1]) if nbr.dim() == 2 else 0
 
     @staticmethod
-    def from_numpy(scene, device="cuda", requires_grad=False, disp=None) -> "DeviceScene":
+    def from_numpy(scene, device="cuda", requires_grad=False, disp=None, sites=None) -> "DeviceScene":
         """`disp` [N,4] (or the scene's `disp` attribute): face displacement
-        at the four texture sites (Eq. svdisp); forward rendering only."""
+        at the four texture sites (Eq. svdisp).  `sites` [N,4,2] (or the
+        scene's `sites`): learned positions of those sites, in units of R."""
         params = {}
         for k in PARAMS:
             a = np.ascontiguousarray(getattr(scene, k), np.float32)
@@ -42,6 +43,10 @@ class DeviceScene:
             disp = getattr(scene, "disp", None)
         if disp is not None:
             params["disp"] = torch.from_numpy(np.ascontiguousarray(disp, np.float32).reshape(-1, 4)).to(device)
+        if sites is None:
+            sites = getattr(scene, "sites", None)
+        if sites is not None:
+            params["sites"] = torch.from_numpy(np.ascontiguousarray(sites, np.float32).reshape(-1, 4, 2)).to(device)
         nbr = torch.from_numpy(np.ascontiguousarray(scene.nbr, np.int32)).to(device)
         return DeviceScene(params, nbr)
 
@@ -56,11 +61,12 @@ class DeviceScene:
         s.nbr = self.nbr.data_ptr() if self.nbr.numel() else None
         s.n_cells = self.n
         s.k_nbr = self.k
-        d = p.get("disp")
-        if d is not None:
-            if not (d.is_cuda and d.dtype == torch.float32 and d.is_contiguous() and d.numel() == 4 * self.n):
-                raise ValueError("disp must be a contiguous float32 CUDA tensor [N,4]")
-            s.disp = d.data_ptr() if d.numel() else None
+        for k, width in (("disp", 4), ("sites", 8)):
+            d = p.get(k)
+            if d is not None:
+                if not (d.is_cuda and d.dtype == torch.float32 and d.is_contiguous() and d.numel() == width * self.n):
+                    raise ValueError(f"{k} must be a contiguous float32 CUDA tensor with {width} values per cell")
+                setattr(s, k, d.data_ptr() if d.numel() else None)
         return s
 
 
@@ -242,7 +248,7 @@ class Renderer:
         """pf_render_bwd: returns a dict of gradient tensors (added into
         `grads` when given)."""
         p = scene.params if params is None else params
-        keys = PARAMS + (("disp",) if p.get("disp") is not None else ())
+        keys = PARAMS + tuple(k for k in ("disp", "sites") if p.get(k) is not None)
         if grads is None:
             grads = {k: torch.zeros_like(p[k]) for k in keys}
         g = _lib.SceneGrad()

@@ -197,8 +197,8 @@ bool scene_ok(const pf_scene *s, const Plan *p) {
         set_error("null scene pointer");
         return false;
     }
-    if (((uintptr_t)s->tex & 15) != 0 || ((uintptr_t)s->disp & 15) != 0) {
-        set_error("tex and disp must be 16-byte aligned");
+    if (((uintptr_t)s->tex & 15) != 0 || ((uintptr_t)s->disp & 15) != 0 || ((uintptr_t)s->sites & 15) != 0) {
+        set_error("tex, disp and sites must be 16-byte aligned");
         return false;
     }
     return true;
@@ -388,8 +388,8 @@ pf_status pf_render_fwd(const pf_scene *scene, pf_plan *p, void *ws, float *rgb,
     g_err[0] = 0;
     if (!p || !ws || !scene_ok(scene, p) || !rgb || !T || !last) return PF_ERR_INVALID_ARG;
     WS w = p->ws(ws);
-    if (scene->disp && p->stats && p->n > 0) {
-        set_error("pf_render_fwd: no stats pass for a displaced scene");
+    if ((scene->disp || scene->sites) && p->stats && p->n > 0) {
+        set_error("pf_render_fwd: no stats pass for a displaced scene or learned sites");
         return PF_ERR_INVALID_ARG;
     }
     const bool record = p->record_hits && !p->stats && w.hitmask != nullptr;
@@ -407,8 +407,8 @@ pf_status pf_render_fwd_contrib(const pf_scene *scene, pf_plan *p, void *ws, flo
         set_error("pf_render_fwd_contrib: null contribution array");
         return PF_ERR_INVALID_ARG;
     }
-    if (scene->disp && p->n > 0) {
-        set_error("pf_render_fwd_contrib: not available for a displaced scene");
+    if ((scene->disp || scene->sites) && p->n > 0) {
+        set_error("pf_render_fwd_contrib: not available for a displaced scene or learned sites");
         return PF_ERR_INVALID_ARG;
     }
     WS w = p->ws(ws);
@@ -430,6 +430,10 @@ pf_status pf_render_bwd(const pf_scene *scene, pf_plan *p, void *ws, const float
     }
     if (scene->disp && p->n > 0 && !g->disp) {
         set_error("pf_render_bwd: a displaced scene needs grad->disp");
+        return PF_ERR_INVALID_ARG;
+    }
+    if (scene->sites && p->n > 0 && !g->sites) {
+        set_error("pf_render_bwd: learned sites need grad->sites");
         return PF_ERR_INVALID_ARG;
     }
     WS w = p->ws(ws);

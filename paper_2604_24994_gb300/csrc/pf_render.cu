@@ -235,9 +235,11 @@ struct Tex {
 // A ray parallel to the face sees no displacement.  s is kept within 1e6 R:
 // the weights of a farther crossing are already the limit of the ray's
 // direction.  With `tx` the crossing's coordinates and weights are returned
-// (for the adjoint).
+// (for the adjoint; its ax / ay hold u minus the fixed sites only).  `st`:
+// the cell's learned site positions [4][2] in units of R, or null.
 __device__ __forceinline__ float face_delta(const float *__restrict__ cr, float3 q, float3 dh, float num,
-                                            float fden, float4 dk, Tex *tx = nullptr) {
+                                            float fden, float4 dk, Tex *tx = nullptr,
+                                            const float *__restrict__ st = nullptr) {
     if (!(fabsf(fden) > 0.0f)) {
         if (tx) *tx = Tex{};
         return 0.0f;
@@ -247,10 +249,21 @@ __device__ __forceinline__ float face_delta(const float *__restrict__ cr, float3
     const float3 y = f3(fmaf(s, dh.x, q.x), fmaf(s, dh.y, q.y), fmaf(s, dh.z, q.z));
     const float u0 = dot3(f3(cr[CR_E1], cr[CR_E1 + 1], cr[CR_E1 + 2]), y);
     const float u1 = dot3(f3(cr[CR_E2], cr[CR_E2 + 1], cr[CR_E2 + 2]), y);
-    // sites (-,-), (+,-), (-,+), (+,+) at a third of R, as the texture's
+    // the texture's sites: learned positions `st`, else (-,-), (+,-), (-,+),
+    // (+,+) at a third of R
     const float a0 = u0 + SITE, a1 = u0 - SITE, b0 = u1 + SITE, b1 = u1 - SITE;
-    const float r0 = sqrtf(a0 * a0 + b0 * b0), r1 = sqrtf(a1 * a1 + b0 * b0);
-    const float r2 = sqrtf(a0 * a0 + b1 * b1), r3 = sqrtf(a1 * a1 + b1 * b1);
+    float r0, r1, r2, r3;
+    if (st) {
+        r0 = sqrtf((u0 - st[0]) * (u0 - st[0]) + (u1 - st[1]) * (u1 - st[1]));
+        r1 = sqrtf((u0 - st[2]) * (u0 - st[2]) + (u1 - st[3]) * (u1 - st[3]));
+        r2 = sqrtf((u0 - st[4]) * (u0 - st[4]) + (u1 - st[5]) * (u1 - st[5]));
+        r3 = sqrtf((u0 - st[6]) * (u0 - st[6]) + (u1 - st[7]) * (u1 - st[7]));
+    } else {
+        r0 = sqrtf(a0 * a0 + b0 * b0);
+        r1 = sqrtf(a1 * a1 + b0 * b0);
+        r2 = sqrtf(a0 * a0 + b1 * b1);
+        r3 = sqrtf(a1 * a1 + b1 * b1);
+    }
     const float l0 = -KAPPA * r0, l1 = -KAPPA * r1, l2 = -KAPPA * r2, l3 = -KAPPA * r3;
     const float mx = fmaxf(fmaxf(l0, l1), fmaxf(l2, l3));
     const float w0 = __expf(l0 - mx), w1 = __expf(l1 - mx), w2 = __expf(l2 - mx), w3 = __expf(l3 - mx);
@@ -279,13 +292,15 @@ __device__ __forceinline__ float face_delta(const float *__restrict__ cr, float3
 // Clip the chord with the cell's radical planes pl[0..np), the dipole face,
 // then refine near-parallel ends.  False if the segment is empty.  NEED sets
 // sg.nplanes to the planes this ray needs on its own (up to the one that
-// empties its segment) instead of the planes the warp evaluated.  DISP
-// moves the face by the ray's displacement (face_delta, from dk).
-template <bool GRAD, bool NEED = false, bool DISP = false>
+// empties its segment) instead of the planes the warp evaluated.  EXT:
+// an extended face model; with has_disp the face moves by the ray's
+// displacement (face_delta, from dk and the sites st).
+template <bool GRAD, bool NEED = false, bool EXT = false>
 __device__ __forceinline__ bool clip_chord(const float *__restrict__ cr, const float *__restrict__ vr,
                                            const float4 *__restrict__ pl, int np,
                                            const float4 *__restrict__ lo_glob, const Ray &ray, const Chord &ch,
-                                           Seg &sg, unsigned lanes = 0u, float4 dk = float4{0.f, 0.f, 0.f, 0.f}) {
+                                           Seg &sg, unsigned lanes = 0u, float4 dk = float4{0.f, 0.f, 0.f, 0.f},
+                                           const float *__restrict__ st = nullptr, bool has_disp = false) {
     const float3 dh = ray.dh, q = ch.q;
     const float R = cr[CR_R];
     const float sig = cr[CR_SIG];
@@ -307,8 +322,8 @@ __device__ __forceinline__ bool clip_chord(const float *__restrict__ cr, const f
         const float3 n = f3(cr[CR_N], cr[CR_N + 1], cr[CR_N + 2]);
         float num = foff - dot3(q, n);
         fden = dot3(dh, n);
-        if (DISP) {
-            const float dl = face_delta(cr, q, dh, num, fden, dk);
+        if (EXT && has_disp) {
+            const float dl = face_delta(cr, q, dh, num, fden, dk, nullptr, st);
             foff += dl;
             num += dl;
         }
@@ -396,12 +411,13 @@ __device__ __forceinline__ bool clip_chord(const float *__restrict__ cr, const f
 // The segment of a recorded hit from its active constraints (ka, kb): the
 // same float expressions as clip_chord for those two constraints and the
 // face, then the same refinement, so the ends equal the forward's.
-template <bool GRAD, bool DISP = false>
+template <bool GRAD, bool EXT = false>
 __device__ __forceinline__ bool segment_from_kinds(const float *__restrict__ cr, const float *__restrict__ vr,
                                                    const float4 *__restrict__ pl,
                                                    const float4 *__restrict__ lo_glob, const Ray &ray,
                                                    const Chord &ch, int ka, int kb, Seg &sg,
-                                                   float4 dk = float4{0.f, 0.f, 0.f, 0.f}) {
+                                                   float4 dk = float4{0.f, 0.f, 0.f, 0.f},
+                                                   const float *__restrict__ st = nullptr, bool has_disp = false) {
     const float3 dh = ray.dh, q = ch.q;
     const float R = cr[CR_R];
     const float sig = cr[CR_SIG];
@@ -410,8 +426,8 @@ __device__ __forceinline__ bool segment_from_kinds(const float *__restrict__ cr,
     float foff = cr[CR_OFF];
     float fnum = foff - dot3(q, n);
     const float fden = dot3(dh, n);
-    if (DISP) {  // the forward's displaced face, the same expressions
-        const float dl = face_delta(cr, q, dh, fnum, fden, dk);
+    if (EXT && has_disp) {  // the forward's displaced face, the same expressions
+        const float dl = face_delta(cr, q, dh, fnum, fden, dk, nullptr, st);
         foff += dl;
         fnum += dl;
     }
@@ -464,7 +480,10 @@ __device__ __forceinline__ bool segment_from_kinds(const float *__restrict__ cr,
 
 // Soft-Voronoi face colour (Eq. svrad): weights of the four sites at the
 // texture point y = q + s d (the dense segment's end on the face side).
-__device__ __forceinline__ float3 face_colour(const float *__restrict__ cr, const Seg &sg, const Ray &ray, Tex &tx) {
+// Colour at the texture point; `st`: the cell's learned site positions, or
+// null for the fixed ones (then tx.ax / tx.ay hold u minus the sites).
+__device__ __forceinline__ float3 face_colour(const float *__restrict__ cr, const Seg &sg, const Ray &ray, Tex &tx,
+                                              const float *__restrict__ st = nullptr) {
     const float ss = sg.dnd > 0.0f ? sg.sb : sg.sa;
     tx.ys = f3(fmaf(ss, ray.dh.x, sg.q.x), fmaf(ss, ray.dh.y, sg.q.y), fmaf(ss, ray.dh.z, sg.q.z));
     tx.u1 = dot3(f3(cr[CR_E1], cr[CR_E1 + 1], cr[CR_E1 + 2]), tx.ys);
@@ -474,12 +493,27 @@ __device__ __forceinline__ float3 face_colour(const float *__restrict__ cr, cons
     tx.ay[0] = tx.u2 + SITE;
     tx.ay[1] = tx.u2 - SITE;
     float Z = 0.f;
+    if (st) {  // learned sites may lie far off: weights relative to the nearest
+        float rmin = CUDART_INF_F;
 #pragma unroll
-    for (int k = 0; k < 4; k++) {
-        const float ax = tx.ax[k & 1], ay = tx.ay[k >> 1];
-        tx.r[k] = sqrt_approx(fmaf(ax, ax, ay * ay));
-        tx.W[k] = __expf(-KAPPA * tx.r[k]);
-        Z += tx.W[k];
+        for (int k = 0; k < 4; k++) {
+            const float ax = tx.u1 - st[2 * k], ay = tx.u2 - st[2 * k + 1];
+            tx.r[k] = sqrt_approx(fmaf(ax, ax, ay * ay));
+            rmin = fminf(rmin, tx.r[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            tx.W[k] = __expf(-KAPPA * (tx.r[k] - rmin));
+            Z += tx.W[k];
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const float ax = tx.ax[k & 1], ay = tx.ay[k >> 1];
+            tx.r[k] = sqrt_approx(fmaf(ax, ax, ay * ay));
+            tx.W[k] = __expf(-KAPPA * tx.r[k]);
+            Z += tx.W[k];
+        }
     }
     const float iz = __fdividef(1.0f, Z);
     float3 c = f3(cr[CR_RGB], cr[CR_RGB + 1], cr[CR_RGB + 2]);
@@ -518,10 +552,11 @@ struct Stage {
     __device__ __forceinline__ int *poff(int b) const {
         return reinterpret_cast<int *>(base + 2 * buf_bytes()) + 2 * BATCH + b * (BATCH + 1);
     }
-    // face displacements [2][BATCH] (displaced scenes only), 16-byte aligned
-    __device__ __forceinline__ float4 *dsp(int b) const {
+    // extended face model [2][BATCH][3] (16-byte aligned): the displacement,
+    // then the four learned site positions (x, y) (scenes with either only)
+    __device__ __forceinline__ float4 *xtr(int b) const {
         return reinterpret_cast<float4 *>(base + ((2 * buf_bytes() + (4 * BATCH + 2) * 4 + 15) & ~(size_t)15)) +
-               b * BATCH;
+               b * BATCH * 3;
     }
 };
 
@@ -542,7 +577,8 @@ __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wai
 // warp 0 also publishes them for the consumers.
 __device__ __forceinline__ void issue_batch(const Stage &sg, int buf, const uint32_t *__restrict__ list, int nb,
                                             const WS &w, int64_t vbase, int K, bool with_nb,
-                                            const float *__restrict__ disp = nullptr) {
+                                            const float *__restrict__ disp = nullptr,
+                                            const float *__restrict__ sites = nullptr) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     int id = 0, np = 0;
     if (lane < nb) {
@@ -560,9 +596,9 @@ __device__ __forceinline__ void issue_batch(const Stage &sg, int buf, const uint
         sg.poff(buf)[lane + 1] = incl;
         if (lane == 0) sg.poff(buf)[0] = 0;
     }
-    // records: nb x (8 + 2 (+ 1 displacement)) chunks over all threads
-    // (uniform trip count: the shuffles need every lane)
-    const int parts = disp ? 11 : 10;
+    // records: nb x (8 + 2 (+ 3 extended)) chunks over all threads (uniform
+    // trip count: the shuffles need every lane)
+    const int parts = (disp || sites) ? 13 : 10;
     const int nrec = nb * parts;
     for (int q0 = 0; q0 < nrec; q0 += TILE_PIX) {
         const int q = q0 + tid;
@@ -574,8 +610,10 @@ __device__ __forceinline__ void issue_batch(const Stage &sg, int buf, const uint
             else if (part < 10)
                 cp_async16(sg.vr(buf) + j * VIEWREC_F + (part - 8) * 4,
                            w.viewrec + (vbase + c) * VIEWREC_F + (part - 8) * 4);
-            else
-                cp_async16(sg.dsp(buf) + j, disp + (int64_t)c * 4);
+            else if (part == 10 && disp)
+                cp_async16(sg.xtr(buf) + 3 * j, disp + (int64_t)c * 4);
+            else if (part > 10 && sites)
+                cp_async16(sg.xtr(buf) + 3 * j + (part - 10), sites + (int64_t)c * 8 + (part - 11) * 4);
         }
     }
     // planes: warp w copies the planes of cells w, w + 8, ...
@@ -610,6 +648,8 @@ struct RenderArgs {
     float *contrib_normal;  // [N] sum of T alpha max(nh.d, 0)^2 per cell, or null
     const float *disp;      // [N][4] face displacement at the texture sites, or null
     float *gdisp;           // [N][4] its gradient (the backward adds into it), or null
+    const float *sites;     // [N][4][2] learned texture / detail site positions, or null
+    float *gsites;          // [N][4][2] their gradient, or null
 };
 
 // Hit masks: one 32-bit word per (warp of the tile, batch, pixel of the
@@ -673,11 +713,11 @@ __device__ __forceinline__ unsigned warp_mask(const Stage &sg, int buf, int nb, 
     return __ballot_sync(0xffffffffu, ov);
 }
 
-__host__ __device__ inline size_t stage_bytes(int K, bool with_nb, bool with_disp = false) {
+__host__ __device__ inline size_t stage_bytes(int K, bool with_nb, bool ext = false) {
     const size_t k = K > 0 ? (size_t)K : 1;
     const size_t buf = (size_t)BATCH * (CELLREC_F + VIEWREC_F) * 4 + BATCH * k * (with_nb ? 24 : 16);
     const size_t ids = 2 * buf + (2 * BATCH + 2 * (BATCH + 1)) * 4;
-    return with_disp ? ((ids + 15) & ~(size_t)15) + 2 * BATCH * 16 : ids;
+    return ext ? ((ids + 15) & ~(size_t)15) + 2 * BATCH * 48 : ids;
 }
 
 __device__ __forceinline__ Stage make_stage(float4 *smem, int K, bool with_nb) {
@@ -693,7 +733,7 @@ __device__ __forceinline__ Stage make_stage(float4 *smem, int K, bool with_nb) {
 // replays (only with a hit-mask region in the workspace); CONTRIB: add each
 // cell's contributions (Sec. 4: T alpha for L_sparse and the pruning EMA,
 // T alpha max(nh.d, 0)^2 for L_normal) over the frame's pixels.
-template <bool STATS, bool REC, bool CONTRIB, bool DISP = false>
+template <bool STATS, bool REC, bool CONTRIB, bool EXT = false>
 __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, int64_t n_tiles,
                                                                  float *__restrict__ rgb_out,
                                                                  float *__restrict__ T_out,
@@ -737,14 +777,14 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, i
     int nhit = 0;  // hits so far (hit recording)
     bool done = !inside || !has_ray;
 
-    const float *disp = DISP ? A.disp : nullptr;
-    if (nbat > 0) issue_batch(sg, 0, A.w.inst_sorted + s, min(BATCH, n), A.w, vbase, A.K, false, disp);
+    const float *disp = EXT ? A.disp : nullptr, *sites = EXT ? A.sites : nullptr;
+    if (nbat > 0) issue_batch(sg, 0, A.w.inst_sorted + s, min(BATCH, n), A.w, vbase, A.K, false, disp, sites);
     for (int k = 0; k < nbat; k++) {
         // every warp is done with batch k-1, whose buffer batch k+1 reuses
         if (__syncthreads_count(!done) == 0) break;
         if (k + 1 < nbat) {
             issue_batch(sg, (k + 1) & 1, A.w.inst_sorted + s + (k + 1) * BATCH, min(BATCH, n - (k + 1) * BATCH),
-                        A.w, vbase, A.K, false, disp);
+                        A.w, vbase, A.K, false, disp, sites);
             cp_async_wait_one();
         } else {
             cp_async_wait_all();
@@ -770,9 +810,12 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, i
                 const int o = sg.poff(buf)[j];
                 np = sg.poff(buf)[j + 1] - o;
                 if (pass)
-                    hit = clip_chord<false, STATS, DISP>(cr, vr, sg.pl(buf) + o, np,
-                                                         A.w.planes_lo + (int64_t)sg.ids(buf)[j] * A.K, ray, ch, seg,
-                                                         pm, DISP ? sg.dsp(buf)[j] : float4{0.f, 0.f, 0.f, 0.f});
+                    hit = clip_chord<false, STATS, EXT>(cr, vr, sg.pl(buf) + o, np,
+                                                        A.w.planes_lo + (int64_t)sg.ids(buf)[j] * A.K, ray, ch, seg,
+                                                        pm, EXT && disp ? sg.xtr(buf)[3 * j] : float4{0.f, 0.f, 0.f, 0.f},
+                                                        EXT && sites ? reinterpret_cast<const float *>(sg.xtr(buf) + 3 * j + 1)
+                                                                     : nullptr,
+                                                        EXT && disp);
             }
             if (STATS && !done) {
                 const unsigned act = __ballot_sync(__activemask(), true);
@@ -812,7 +855,9 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, i
                 nhit++;
             }
             Tex tx;
-            const float3 c = face_colour(cr, seg, ray, tx);
+            const float3 c = face_colour(cr, seg, ray, tx,
+                                         EXT && sites ? reinterpret_cast<const float *>(sg.xtr(buf) + 3 * j + 1)
+                                                      : nullptr);
             const float x = fminf(cr[CR_SIG] * (seg.sb - seg.sa), X_CAP);
             const float ex = __expf(-x);
             const float wgt = T * (1.0f - ex);
@@ -985,7 +1030,7 @@ __device__ __forceinline__ void route_end(float gt, int kind, float s, float den
 
 // MASKS: replay only the (cell, lane) pairs the forward recorded as hits
 // (the hit masks of the current bins); otherwise re-test every listed cell.
-template <bool MASKS, bool DISP = false>
+template <bool MASKS, bool EXT = false>
 __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, int64_t n_tiles,
                                                                  const float *__restrict__ dL_drgb,
                                                                  const float *__restrict__ dL_dT,
@@ -1051,14 +1096,14 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
     const int nbat = (maxlast + BATCH - 1) / BATCH;
     if (nbat > 0)
         issue_batch(stg, (nbat - 1) & 1, list + (nbat - 1) * BATCH, maxlast - (nbat - 1) * BATCH, A.w, vbase, A.K,
-                    true, DISP ? A.disp : nullptr);
+                    true, EXT ? A.disp : nullptr, EXT ? A.sites : nullptr);
     for (int b = nbat - 1; b >= 0; b--) {
         // bit j: the forward found this pixel's segment in cell j non-empty
         const unsigned my_hits = MASKS ? A.w.hitmask[hitmask_slot(A, tile, s, b, warp) + lane] : 0u;
         __syncthreads();  // batch b+1, whose buffer batch b-1 reuses, is done
         if (b > 0) {
             issue_batch(stg, (b - 1) & 1, list + (b - 1) * BATCH, BATCH, A.w, vbase, A.K, true,
-                        DISP ? A.disp : nullptr);
+                        EXT ? A.disp : nullptr, EXT ? A.sites : nullptr);
             cp_async_wait_one();
         } else {
             cp_async_wait_all();
@@ -1080,7 +1125,9 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
             const int cell = stg.ids(buf)[j];
             const float *cr = s_cr + j * CELLREC_F;
             const float *vr = s_vr + j * VIEWREC_F;
-            const float4 dk = DISP ? stg.dsp(buf)[j] : float4{0.f, 0.f, 0.f, 0.f};
+            const bool has_disp = EXT && A.disp;
+            const float4 dk = has_disp ? stg.xtr(buf)[3 * j] : float4{0.f, 0.f, 0.f, 0.f};
+            const float *st = EXT && A.sites ? reinterpret_cast<const float *>(stg.xtr(buf) + 3 * j + 1) : nullptr;
             const int o = poff[j], np = poff[j + 1] - o;
             Seg sg;
             Chord ch;
@@ -1096,16 +1143,17 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
                 }
                 if (mine && sphere_chord<true>(cr, vr, ray, ch, cand)) {
                     if (kk != 0xffffu)
-                        hit = segment_from_kinds<true, DISP>(cr, vr, s_pl + o, A.w.planes_lo + (int64_t)cell * A.K,
-                                                             ray, ch, (int)(kk & 127u) - 3, (int)(kk >> 7) - 3, sg,
-                                                             dk);
+                        hit = segment_from_kinds<true, EXT>(cr, vr, s_pl + o, A.w.planes_lo + (int64_t)cell * A.K,
+                                                            ray, ch, (int)(kk & 127u) - 3, (int)(kk >> 7) - 3, sg,
+                                                            dk, st, has_disp);
                     else  // beyond the recorded hits of this pixel: clip against every plane
-                        hit = clip_chord<true, false, DISP>(cr, vr, s_pl + o, np,
-                                                            A.w.planes_lo + (int64_t)cell * A.K, ray, ch, sg, 0u, dk);
+                        hit = clip_chord<true, false, EXT>(cr, vr, s_pl + o, np,
+                                                           A.w.planes_lo + (int64_t)cell * A.K, ray, ch, sg, 0u, dk, st,
+                                                           has_disp);
                 }
             } else if (mine && sphere_chord<true>(cr, vr, ray, ch, cand)) {
-                hit = clip_chord<true, false, DISP>(cr, vr, s_pl + o, np, A.w.planes_lo + (int64_t)cell * A.K, ray,
-                                                    ch, sg, 0u, dk);
+                hit = clip_chord<true, false, EXT>(cr, vr, s_pl + o, np, A.w.planes_lo + (int64_t)cell * A.K, ray,
+                                                   ch, sg, 0u, dk, st, has_disp);
             }
             if (!__any_sync(0xffffffffu, hit)) continue;
             // Every lane runs the adjoint of this cell.  A lane without a hit
@@ -1126,7 +1174,7 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
             int ja, jb;
             {
                 Tex tx;
-                const float3 c = face_colour(cr, sg, ray, tx);
+                const float3 c = face_colour(cr, sg, ray, tx, st);
                 const float sig = cr[CR_SIG];
                 const float l = sg.sb - sg.sa;
                 const float xr = sig * l;
@@ -1153,12 +1201,17 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
                     sW += tx.W[k] * gW[k];
                 }
                 float gu1 = 0.f, gu2 = 0.f;
+                float gs[8];  // learned sites: r_k = |u - s_k|, so dL/ds_k = -dL/du through logit k
 #pragma unroll
                 for (int k = 0; k < 4; k++) {
                     const float gr = -KAPPA * tx.W[k] * (gW[k] - sW);
                     const float ir = tx.r[k] > 0.f ? gr * rcp_approx(tx.r[k]) : 0.0f;
-                    gu1 = fmaf(ir, tx.ax[k & 1], gu1);
-                    gu2 = fmaf(ir, tx.ay[k >> 1], gu2);
+                    const float dxk = st ? tx.u1 - st[2 * k] : tx.ax[k & 1];
+                    const float dyk = st ? tx.u2 - st[2 * k + 1] : tx.ay[k >> 1];
+                    gu1 = fmaf(ir, dxk, gu1);
+                    gu2 = fmaf(ir, dyk, gu2);
+                    gs[2 * k] = -ir * dxk;
+                    gs[2 * k + 1] = -ir * dyk;
                 }
                 // u = (e1.y, e2.y)/R with e/R stored:  dL/dy, dL/dR, dL/dn via the frame
                 const float3 E1 = f3(cr[CR_E1], cr[CR_E1 + 1], cr[CR_E1 + 2]);
@@ -1188,7 +1241,7 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
                 const float4 *plp = s_pl + o;
                 route_end(gta, sg.ka, sg.sa, sg.dena, sg, ray, cr, plp, nbp, gm, vv, nba, ja);
                 route_end(gtb, sg.kb, sg.sb, sg.denb, sg, ray, cr, plp, nbp, gm, vv, nbb, jb);
-                if (DISP) {
+                if (EXT && has_disp) {
                     // the displaced face end moves with delta like with the offset
                     // (ds/d delta = 1/(d.n)); delta moves with the site displacements
                     // through W, and with u at the base crossing, whose point
@@ -1197,7 +1250,7 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
                     const bool fa = sg.ka == K_FACE, fb = sg.kb == K_FACE;
                     const float fden = dot3(ray.dh, nf);
                     Tex fd;
-                    const float dl = face_delta(cr, sg.q, ray.dh, cr[CR_OFF] - dot3(sg.q, nf), fden, dk, &fd);
+                    const float dl = face_delta(cr, sg.q, ray.dh, cr[CR_OFF] - dot3(sg.q, nf), fden, dk, &fd, st);
                     const float gd = (fa || fb) ? ((fa ? gta : 0.f) + (fb ? gtb : 0.f)) *
                                                       rcp_approx(fa ? sg.dena : sg.denb)
                                                 : 0.f;
@@ -1208,8 +1261,12 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
                         gdk[k] = gd * fd.W[k];
                         const float gr = -KAPPA * gd * fd.W[k] * (dks[k] - dl);
                         const float ir = fd.r[k] > 0.f ? gr * rcp_approx(fd.r[k]) : 0.0f;
-                        gv1 = fmaf(ir, fd.ax[k & 1], gv1);
-                        gv2 = fmaf(ir, fd.ay[k >> 1], gv2);
+                        const float dxk = st ? fd.u1 - st[2 * k] : fd.ax[k & 1];
+                        const float dyk = st ? fd.u2 - st[2 * k + 1] : fd.ay[k >> 1];
+                        gv1 = fmaf(ir, dxk, gv1);
+                        gv2 = fmaf(ir, dyk, gv2);
+                        gs[2 * k] -= ir * dxk;
+                        gs[2 * k + 1] -= ir * dyk;
                     }
                     const float3 gyb = f3(gv1 * E1.x + gv2 * E2.x, gv1 * E1.y + gv2 * E2.y, gv1 * E1.z + gv2 * E2.z);
                     vv[G_R] -= (gv1 * fd.u1 + gv2 * fd.u2) * iR;
@@ -1229,6 +1286,15 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
 #pragma unroll
                         for (int o2 = 16; o2 > 0; o2 >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o2);
                         if (lane == 0 && A.gdisp) atomicAdd(A.gdisp + 4 * (int64_t)cell + k, v);
+                    }
+                }
+                if (EXT && st) {  // the eight site coordinates: summed over the warp, one atomic each
+#pragma unroll
+                    for (int k = 0; k < 8; k++) {
+                        float v = gs[k];
+#pragma unroll
+                        for (int o2 = 16; o2 > 0; o2 >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o2);
+                        if (lane == 0 && A.gsites) atomicAdd(A.gsites + 8 * (int64_t)cell + k, v);
                     }
                 }
                 // m = o - p
@@ -1331,6 +1397,8 @@ static RenderArgs make_args(const pf_scene &s, const Plan &p, const WS &w) {
     A.contrib_normal = nullptr;
     A.disp = s.disp;
     A.gdisp = nullptr;
+    A.sites = s.sites;
+    A.gsites = nullptr;
     return A;
 }
 
@@ -1356,7 +1424,7 @@ cudaError_t launch_render_fwd(const pf_scene &s, const Plan &p, const WS &w, flo
     A.contrib_sparse = contrib_sparse;
     A.contrib_normal = contrib_normal;
     const bool contrib = contrib_sparse != nullptr;
-    const bool disp = s.disp != nullptr;
+    const bool disp = s.disp != nullptr || s.sites != nullptr;  // an extended face model
     if (disp && (contrib || p.stats)) return cudaErrorNotSupported;  // the C API refuses these first
     const size_t smem = disp ? stage_bytes(p.k, false, true) : fwd_smem(p.k);
     cudaError_t e = cudaMemsetAsync(&w.counters->q_fwd, 0, sizeof(unsigned int), st);
@@ -1379,7 +1447,8 @@ cudaError_t launch_render_bwd(const pf_scene &s, const Plan &p, const WS &w, con
     if (p.total_tiles > 0) {
         RenderArgs A = make_args(s, p, w);
         A.gdisp = g.disp;
-        const bool disp = s.disp != nullptr;
+        A.gsites = g.sites;
+        const bool disp = s.disp != nullptr || s.sites != nullptr;  // an extended face model
         const size_t smem = disp ? stage_bytes(p.k, true, true) : bwd_smem(p.k);
         e = cudaMemsetAsync(&w.counters->q_bwd, 0, sizeof(unsigned int), st);
         if (e != cudaSuccess) return e;

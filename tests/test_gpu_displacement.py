@@ -1,6 +1,6 @@
-"""Face displacement (Eq. svdisp, one-step plane shift) on the GPU: forward
-and backward against the FP64 oracle, and the call that refuses a displaced
-scene."""
+"""Face displacement (Eq. svdisp, one-step plane shift) and learned detail-site
+positions (Sec. 3.4) on the GPU: forward and backward against the FP64
+oracle, and the call that refuses such a scene."""
 import numpy as np
 import pytest
 
@@ -18,10 +18,10 @@ def built():
     build.build()
 
 
-def gpu_render(sc, cams, disp):
+def gpu_render(sc, cams, disp, sites=None):
     import torch
     from paper_2604_24994_gb300 import DeviceScene, Renderer
-    ds = DeviceScene.from_numpy(sc, "cuda", disp=disp)
+    ds = DeviceScene.from_numpy(sc, "cuda", disp=disp, sites=sites)
     r = Renderer(ds.n, ds.k, cams)
     rgb, T, last = r.forward(ds)
     torch.cuda.synchronize()
@@ -31,6 +31,22 @@ def gpu_render(sc, cams, disp):
 def random_disp(sc, scale, seed):
     rng = np.random.default_rng(seed)
     return (rng.uniform(-scale, scale, (sc.n, 4)) * sc.R[:, None]).astype(np.float32)
+
+
+def random_sites(sc, spread, seed):
+    rng = np.random.default_rng(seed)
+    base = np.array([[-1, -1], [1, -1], [-1, 1], [1, 1]], np.float64) / 3.0
+    return (base[None] + rng.uniform(-spread, spread, (sc.n, 4, 2))).astype(np.float32)
+
+
+@pytest.mark.parametrize("with_disp", [True, False])
+def test_learned_sites_forward_tiny(tiny, with_disp):
+    sc, cam = tiny
+    disp = random_disp(sc, 0.3, 5) if with_disp else None
+    sites = random_sites(sc, 0.2, 6)
+    rgb, T, last = gpu_render(sc, [cam], disp, sites)
+    rgb_o, T_o = oracle.Oracle(sc, disp=disp, sites=sites).render(cam)
+    assert_close_image(rgb, T, rgb_o, T_o, f"learned sites, displaced={with_disp}")
 
 
 def test_displaced_forward_tiny(tiny):
@@ -68,29 +84,32 @@ def test_zero_displacement_matches_the_plain_forward(tiny):
     assert np.abs(rgb0 - rgb1).max() < 1e-6 and np.abs(T0 - T1).max() < 1e-6
 
 
-@pytest.mark.parametrize("with_masks", [True, False])
-def test_displaced_backward_matches_the_oracle(with_masks):
-    """pf_render_bwd on a displaced scene: every parameter's gradient, the
-    site displacements' included, within 1e-3 relative L2 of the FP64
-    adjoint (replaying the forward's recorded hits, or re-clipping)."""
+@pytest.mark.parametrize("with_masks,with_disp,with_sites", [(True, True, False), (False, True, False),
+                                                             (True, True, True), (False, False, True)])
+def test_displaced_backward_matches_the_oracle(with_masks, with_disp, with_sites):
+    """pf_render_bwd on a displaced scene and / or learned sites: every
+    parameter's gradient, the displacements' and the sites' included, within
+    1e-3 relative L2 of the FP64 adjoint (replaying the forward's recorded
+    hits, or re-clipping)."""
     import torch
     from paper_2604_24994_gb300 import DeviceScene, Renderer
     from tests.test_gpu_backward import check_grads
     rng = np.random.default_rng(31)
     sc = f32(cluster_scene(rng, n=40, spread=0.15, r=(0.06, 0.12), tex_std=0.2))
-    disp = random_disp(sc, 0.35, 4)
+    disp = random_disp(sc, 0.35, 4) if with_disp else None
+    sites = random_sites(sc, 0.2, 7) if with_sites else None
     cams = [inputs.look_at((0.7, 0.2, 0.1), 48, 40, fov_y_deg=40),
             inputs.fisheye_look_at((-0.5, 0.5, 0.3), 33, 29, fov_deg=70.0)]
     npx = sum(c.n_pixels for c in cams)
     gC = rng.normal(size=(npx, 3))
     gT = rng.normal(size=npx)
-    ds = DeviceScene.from_numpy(sc, "cuda", disp=disp)
+    ds = DeviceScene.from_numpy(sc, "cuda", disp=disp, sites=sites)
     r = Renderer(ds.n, ds.k, cams, hit_records=with_masks)
     rgb, T, last = r.forward(ds)
     g = r.backward(ds, torch.from_numpy(gC).float().cuda(), torch.from_numpy(gT).float().cuda(), T, last)
     torch.cuda.synchronize()
     G = {k: v.cpu().numpy().astype(np.float64) for k, v in g.items()}
-    orc = oracle.Oracle(sc, disp=disp)
+    orc = oracle.Oracle(sc, disp=disp, sites=sites)
     Go = None
     o = 0
     for cam in cams:
@@ -99,8 +118,10 @@ def test_displaced_backward_matches_the_oracle(with_masks):
         o += cam.n_pixels
     check_grads(G, Go)
     from tests.gpu_util import rel_l2
-    assert np.linalg.norm(Go["disp"]) > 0
-    assert rel_l2(G["disp"], Go["disp"]) < 1e-3
+    for k in ("disp", "sites"):
+        if k in Go:
+            assert np.linalg.norm(Go[k]) > 0
+            assert rel_l2(G[k].reshape(-1), Go[k].reshape(-1)) < 1e-3, k
 
 
 def test_displaced_scene_refuses_contributions(tiny):
