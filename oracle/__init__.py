@@ -32,8 +32,10 @@ _lib = None
 
 KAPPA = 6.0          # soft-Voronoi sharpness on the face, in units of 1/R
 PARAM_COLS = {"pos": (0, 3), "w": (3, 1), "R": (4, 1), "sigma": (5, 1), "rgb": (6, 3),
-              "normal": (9, 3), "offset": (12, 1), "tex": (13, 12), "disp": (25, 4), "sites": (29, 8)}
-NPAR = 37
+              "normal": (9, 3), "offset": (12, 1), "tex": (13, 12), "disp": (25, 4), "sites": (29, 8),
+              "sv": (37, 192)}
+NPAR = 229
+SV_LAMBDA = 10.0     # sharpness of the spherical-Voronoi site colours
 ACT_SPHERE, ACT_CAMERA, ACT_DIPOLE = -1, -2, -3
 
 
@@ -50,7 +52,8 @@ def build(force: bool = False) -> str:
 class _Scene(C.Structure):
     _fields_ = [("n", C.c_int64)] + [(k, C.POINTER(C.c_double)) for k in
                                      ("pos", "w", "R", "sigma", "rgb", "normal", "offset", "tex", "disp")] + \
-               [("kappa_disp", C.c_double), ("sites", C.POINTER(C.c_double))]
+               [("kappa_disp", C.c_double), ("sites", C.POINTER(C.c_double)), ("sv", C.POINTER(C.c_double)),
+                ("sv_lambda", C.c_double)]
 
 
 class _Camera(C.Structure):
@@ -137,11 +140,15 @@ class Oracle:
     widened to float64 (exactly, for float32 inputs); `params` holds them and
     may be edited in place (finite differences do)."""
 
-    def __init__(self, scene, kappa: float = KAPPA, nthreads: int = 0, disp=None, sites=None):
+    def __init__(self, scene, kappa: float = KAPPA, nthreads: int = 0, disp=None, sites=None, sv=None,
+                 sv_lambda: float = SV_LAMBDA):
         """`disp` [N,4] (or the scene's `disp` attribute): displacement of
         each face at its four texture sites (Eq. svdisp); None for none.
         `sites` [N,4,2] (or the scene's `sites`): learned positions of those
-        sites in units of R; None for the fixed (+-1/3, +-1/3)."""
+        sites in units of R; None for the fixed (+-1/3, +-1/3).  `sv`
+        [N,4,8,6] (or the scene's `sv`): view-dependent site colours, per
+        site eight (axis xyz, rgb) of a spherical-Voronoi function with
+        sharpness `sv_lambda`; None for the constant colours `tex`."""
         self.kappa = float(kappa)
         self.nthreads = int(nthreads)
         self._arrs = {k: np.ascontiguousarray(np.asarray(getattr(scene, k), np.float64))
@@ -154,6 +161,10 @@ class Oracle:
             sites = getattr(scene, "sites", None)
         if sites is not None:
             self._arrs["sites"] = np.ascontiguousarray(np.asarray(sites, np.float64).reshape(-1, 4, 2))
+        if sv is None:
+            sv = getattr(scene, "sv", None)
+        if sv is not None:
+            self._arrs["sv"] = np.ascontiguousarray(np.asarray(sv, np.float64).reshape(-1, 4, 8, 6))
         self.params = self._arrs
         self.n = int(self._arrs["pos"].shape[0])
         s = _Scene()
@@ -161,6 +172,7 @@ class Oracle:
         for k, a in self._arrs.items():
             setattr(s, k, _ptr(a, C.c_double))
         s.kappa_disp = self.kappa
+        s.sv_lambda = float(sv_lambda)
         self._s = s
         self._cands = None      # (beg, end, idx) arrays, kept alive
         self._cs = None
@@ -316,11 +328,13 @@ class Oracle:
                               self.nthreads)
         out = {}
         for k, (c0, w) in PARAM_COLS.items():
-            if k in ("disp", "sites") and k not in self._arrs:
+            if k in ("disp", "sites", "sv") and k not in self._arrs:
                 continue
             out[k] = g[:, c0:c0 + w] if w > 1 else g[:, c0].copy()
             if k == "sites":
                 out[k] = out[k].reshape(-1, 4, 2)
+            if k == "sv":
+                out[k] = out[k].reshape(-1, 4, 8, 6)
         return out
 
     def ray(self, cam, u, v):

@@ -58,6 +58,11 @@ typedef struct {
      * texture / detail sites on the face, [n][4][2], in units of R, in the
      * site order of tex and disp (Sec. 3.4: learnable detail sites) */
     const double *sites;
+    /* optional (NULL: the constant site colours tex): view-dependent site
+     * colours, a spherical-Voronoi function per site (Sec. 3.4): [n][4][8][6],
+     * per site eight (axis xyz, rgb); sharpness sv_lambda */
+    const double *sv;
+    double sv_lambda;
 } orc_scene;
 
 /* model 0: pinhole.  model 1: equidistant fisheye (non-pinhole rasterization,
@@ -317,6 +322,35 @@ static double face_disp(const orc_scene *s, int64_t i, const double *o, const do
     return delta;
 }
 
+/*
+ * Colour of site k of cell i seen along the ray (reading of Sec. 3.4's
+ * spherical-Voronoi radiance): with the outgoing direction wo = -d and the
+ * site's eight axes a_j (normalised) and colours c_j,
+ * c_k(wo) = sum_j P_j c_j, P_j = softmax_j(sv_lambda a_j.wo).
+ * P (optional) receives the eight weights.
+ */
+static void sv_colour(const orc_scene *s, int64_t i, int k, const double *d, double *c, double *P) {
+    const double *q = s->sv + (((int64_t)i * 4 + k) * 8) * 6;
+    double lg[8], mx = -INFINITY, Z = 0.0;
+    for (int j = 0; j < 8; j++) {
+        const double *a = q + 6 * j;
+        double L = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+        lg[j] = -s->sv_lambda * (a[0] * d[0] + a[1] * d[1] + a[2] * d[2]) / L;
+        if (lg[j] > mx) mx = lg[j];
+    }
+    double Pj[8];
+    for (int j = 0; j < 8; j++) {
+        Pj[j] = exp(lg[j] - mx);
+        Z += Pj[j];
+    }
+    c[0] = c[1] = c[2] = 0.0;
+    for (int j = 0; j < 8; j++) {
+        Pj[j] /= Z;
+        for (int ch = 0; ch < 3; ch++) c[ch] += Pj[j] * q[6 * j + 3 + ch];
+    }
+    if (P) memcpy(P, Pj, sizeof Pj);
+}
+
 /* colour of cell i for the segment (Eq. svrad, see header) */
 static void cell_colour(const orc_scene *s, int64_t i, const double *o, const double *d, const orc_seg *sg,
                         double kappa, double *col, double *Wout, double *uout, double *ts_out) {
@@ -341,9 +375,16 @@ static void cell_colour(const orc_scene *s, int64_t i, const double *o, const do
         Z += W[k];
     }
     for (int k = 0; k < 4; k++) W[k] /= Z;
+    double ck[4][3];
+    for (int k = 0; k < 4; k++) {
+        if (s->sv)
+            sv_colour(s, i, k, d, ck[k], NULL);
+        else
+            for (int ch = 0; ch < 3; ch++) ck[k][ch] = (double)s->tex[12 * i + 3 * k + ch];
+    }
     for (int ch = 0; ch < 3; ch++) {
         double v = s->rgb[3 * i + ch];
-        for (int k = 0; k < 4; k++) v += W[k] * (double)s->tex[12 * i + 3 * k + ch];
+        for (int k = 0; k < 4; k++) v += W[k] * ck[k][ch];
         col[ch] = v;
     }
     if (Wout) memcpy(Wout, W, sizeof W);
@@ -561,7 +602,7 @@ int orc_hit_cells(const orc_scene *s, const orc_camera *cam, int64_t npix, const
  * normal 9-11, offset 12, tex 13-24.
  */
 enum { P_POS = 0, P_W = 3, P_R = 4, P_SIG = 5, P_RGB = 6, P_N = 9, P_OFF = 12, P_TEX = 13, P_DISP = 25, P_SITE = 29,
-       NPAR = 37 };
+       P_SV = 37, NPAR = 229 };
 
 typedef struct {
     int32_t cell, col;
@@ -683,7 +724,7 @@ static void route_t(const orc_scene *s, int64_t i, int act, double t, const doub
 
 /*
  * Gradient of L with respect to every cell parameter, given dL/dC [npix][3]
- * and dL/dT_final [npix] for the rendered pixels.  grad [n][37] is
+ * and dL/dT_final [npix] for the rendered pixels.  grad [n][229] is
  * overwritten.  Contributions are summed in pixel order, so the result does
  * not depend on the thread count.
  */
@@ -748,13 +789,42 @@ int orc_render_grad(const orc_scene *s, const orc_cands *cd, const orc_camera *c
                 double cc[3];
                 cell_colour(s, i, o, d, &buf[q], kappa, cc, W, uu, &ts);
                 for (int ch = 0; ch < 3; ch++) push(L, (int32_t)i, P_RGB + ch, gc[ch]);
-                for (int kk = 0; kk < 4; kk++)
-                    for (int ch = 0; ch < 3; ch++) push(L, (int32_t)i, P_TEX + 3 * kk + ch, W[kk] * gc[ch]);
-                /* soft-Voronoi weights -> u */
+                /* site colours: constant (tex), or view dependent (spherical Voronoi) */
                 double gW[4], sW = 0.0;
                 for (int kk = 0; kk < 4; kk++) {
                     gW[kk] = 0.0;
-                    for (int ch = 0; ch < 3; ch++) gW[kk] += (double)s->tex[12 * i + 3 * kk + ch] * gc[ch];
+                    if (!s->sv) {
+                        for (int ch = 0; ch < 3; ch++) {
+                            push(L, (int32_t)i, P_TEX + 3 * kk + ch, W[kk] * gc[ch]);
+                            gW[kk] += (double)s->tex[12 * i + 3 * kk + ch] * gc[ch];
+                        }
+                    } else {
+                        /* c_k = sum_j P_j c_j, P = softmax(lambda a_j.wo / |a_j|), wo = -d */
+                        double ck[3], P[8], gP[8], sP = 0.0;
+                        const double *qv = s->sv + (((int64_t)i * 4 + kk) * 8) * 6;
+                        const int base = P_SV + kk * 48;
+                        sv_colour(s, i, kk, d, ck, P);
+                        for (int ch = 0; ch < 3; ch++) gW[kk] += ck[ch] * gc[ch];
+                        for (int j = 0; j < 8; j++) {
+                            gP[j] = 0.0;
+                            for (int ch = 0; ch < 3; ch++) {
+                                double gck = W[kk] * gc[ch];
+                                push(L, (int32_t)i, base + 6 * j + 3 + ch, P[j] * gck);
+                                gP[j] += gck * qv[6 * j + 3 + ch];
+                            }
+                            sP += P[j] * gP[j];
+                        }
+                        for (int j = 0; j < 8; j++) {
+                            double glg = P[j] * (gP[j] - sP);   /* dL/dlogit_j */
+                            const double *a = qv + 6 * j;
+                            double La = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+                            double ah[3] = {a[0] / La, a[1] / La, a[2] / La};
+                            double ga[3] = {-glg * s->sv_lambda * d[0], -glg * s->sv_lambda * d[1],
+                                            -glg * s->sv_lambda * d[2]};   /* dL/d(a hat), wo = -d */
+                            double pa = dot3(ah, ga);
+                            for (int r = 0; r < 3; r++) push(L, (int32_t)i, base + 6 * j + r, (ga[r] - ah[r] * pa) / La);
+                        }
+                    }
                     sW += W[kk] * gW[kk];
                 }
                 double gu[2] = {0.0, 0.0};

@@ -965,3 +965,102 @@ def test_site_adjoint_matches_central_differences(seed):
             assert abs(fd - gflat[j]) <= 1e-5 * max(1.0, abs(fd)), (key, j, fd, gflat[j])
             checked += 1
     assert checked >= 55
+
+
+# ------------------------------------------- spherical-Voronoi site colours
+
+def sv_from_tex(tex, rng):
+    """Eight random axes per site, every colour equal to the site's tex colour."""
+    n = tex.shape[0]
+    axes = rng.normal(size=(n, 4, 8, 3))
+    cols = np.repeat(tex.reshape(n, 4, 1, 3), 8, axis=2)
+    return np.concatenate([axes, cols], -1)
+
+
+def test_flat_spherical_voronoi_is_the_constant_colour():
+    """A site whose eight spherical-Voronoi colours are all equal has that
+    colour from every direction: the image and every gradient equal the
+    constant-colour render's, and the colour gradients summed over the eight
+    axes equal the tex gradient."""
+    rng = np.random.default_rng(41)
+    sc = cluster_scene(rng, n=9, spread=0.12, r=(0.06, 0.12), tex_std=0.2)
+    sv = sv_from_tex(sc.tex, rng)
+    cam = cam_at([0.55, 0.25, 0.15], 12, 10, fov=40.0)
+    a = oracle.Oracle(sc)
+    b = oracle.Oracle(sc, sv=sv)
+    c1, T1 = a.render(cam)
+    c2, T2 = b.render(cam)
+    np.testing.assert_allclose(c2, c1, atol=1e-12)
+    np.testing.assert_allclose(T2, T1, atol=1e-15)
+    npix = cam.width * cam.height
+    gC = rng.normal(size=(npix, 3))
+    gT = rng.normal(size=npix)
+    Ga = a.render_grad(cam, gC, gT)
+    Gb = b.render_grad(cam, gC, gT)
+    for k in ("pos", "w", "R", "sigma", "rgb", "normal", "offset"):
+        np.testing.assert_allclose(Gb[k], Ga[k], atol=1e-9, err_msg=k)
+    np.testing.assert_allclose(Gb["sv"][..., 3:].sum(2).reshape(sc.n, 12), Ga["tex"], atol=1e-9)
+    np.testing.assert_allclose(Gb["sv"][..., :3], 0.0, atol=1e-9)   # no direction dependence to learn
+
+
+def test_spherical_voronoi_closed_form_along_the_axis():
+    """A ray along +z leaves towards -z.  A site whose axes are +-x, +-y, +-z
+    and two more in the xy-plane weighs them by softmax(lambda a.wo):
+    e^lambda for -z, e^-lambda for +z, 1 for the six others (axes need not be
+    unit: they are normalised).  Through the face centre the four sites weigh
+    1/4 each."""
+    R, sig, off, lam = 0.5, 2.0, 0.1, 3.0
+    sc = make_scene([0, 0, 0], 0.04, R, sig, [0.1, 0.2, 0.3], normal=[0, 0, 1], offset=off)
+    axes = np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1],
+                     [1, 1, 0], [-1, 1, 0]], np.float64) * 2.0
+    rng = np.random.default_rng(3)
+    cols = rng.uniform(0, 1, (4, 8, 3))
+    sv = np.concatenate([np.broadcast_to(axes, (4, 8, 3)), cols], -1)[None]
+    orc = oracle.Oracle(sc, sv=sv, sv_lambda=lam)
+    c, T = orc.render_rays(np.array([[0.0, 0.0, -3.0]]), np.array([[0.0, 0.0, 1.0]]))
+    wgt = np.ones(8)
+    wgt[5] = math.exp(lam)
+    wgt[4] = math.exp(-lam)
+    wgt /= wgt.sum()
+    site_cols = (wgt[None, :, None] * cols).sum(1)          # [4, 3]
+    alpha = 1 - math.exp(-sig * (off + R))
+    np.testing.assert_allclose(c[0], alpha * (np.array([0.1, 0.2, 0.3]) + site_cols.mean(0)), atol=1e-13)
+
+
+@pytest.mark.parametrize("seed", [131, 132])
+def test_spherical_voronoi_adjoint_matches_central_differences(seed):
+    sc = fd_scene(seed)
+    rng = np.random.default_rng(seed + 5)
+    sv = np.concatenate([rng.normal(size=(sc.n, 4, 8, 3)), rng.uniform(0, 1, (sc.n, 4, 8, 3))], -1)
+    sites = default_sites(sc.n) + rng.uniform(-0.1, 0.1, (sc.n, 4, 2))
+    cam = cam_at([0.55, 0.25, 0.15], 10, 10, fov=40.0)
+    orc = oracle.Oracle(sc, sv=sv, sites=sites, sv_lambda=4.0)
+    npix = cam.width * cam.height
+    gC = rng.normal(size=(npix, 3))
+    gT = rng.normal(size=npix)
+    G = orc.render_grad(cam, gC, gT)
+
+    def loss():
+        c, T = orc.render(cam)
+        return float(np.sum(c * gC) + np.sum(T * gT))
+
+    checked = 0
+    for key, arr in orc.params.items():
+        if key == "tex":
+            continue          # unused with view-dependent colours
+        flat = arr.reshape(-1)
+        gflat = np.asarray(G[key]).reshape(-1)
+        nz = np.nonzero(np.abs(gflat) > 1e-8)[0]
+        assert nz.size > 0, key
+        for j in rng.choice(nz, size=min(16 if key == "sv" else 5, nz.size), replace=False):
+            h = 1e-6 if key != "w" else 1e-7
+            old = flat[j]
+            flat[j] = old + h
+            lp = loss()
+            flat[j] = old - h
+            lm = loss()
+            flat[j] = old
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - gflat[j]) <= 1e-5 * max(1.0, abs(fd)), (key, j, fd, gflat[j])
+            checked += 1
+    assert checked >= 50
