@@ -375,7 +375,26 @@ def run_ours(args):
         if it >= W:
             dt.append(a.elapsed_time(b))
     ms_disp = float(np.mean(dt))
-    del rd, do, dsp, dparams
+    # view-dependent site colours (spherical Voronoi, eight axes per site) on the same view
+    svp = np.concatenate([drng.normal(size=(ds.n, 4, 8, 3)), drng.uniform(0, 1, (ds.n, 4, 8, 3))], -1)
+    sparams = dict(ds.params, sv=torch.from_numpy(svp.astype(np.float32)).cuda())
+    sst2 = ds.struct(sparams)
+    del svp
+    st_t = []
+    for it in range(W + K):
+        flush.zero_()
+        a, b = ev(), ev()
+        a.record(stream)
+        check(lib().pf_project(C.byref(sst2), rd.plan.handle, rd.plan.ws_ptr, stream.cuda_stream), "project")
+        check(lib().pf_bin_sort(rd.plan.handle, rd.plan.ws_ptr, None, stream.cuda_stream), "bin_sort")
+        check(lib().pf_render_fwd(C.byref(sst2), rd.plan.handle, rd.plan.ws_ptr, do[0].data_ptr(), do[1].data_ptr(),
+                                  do[2].data_ptr(), stream.cuda_stream), "render_fwd")
+        b.record(stream)
+        b.synchronize()
+        if it >= W:
+            st_t.append(a.elapsed_time(b))
+    ms_sv = float(np.mean(st_t))
+    del rd, do, dsp, dparams, sparams
     # the neighbour lists of the same scene built on the GPU (pf_build_neighbours)
     from paper_2604_24994_gb300.api import build_neighbours
     pw, Rin = ds.params["pos"], ds.params["R"]
@@ -432,6 +451,7 @@ def run_ours(args):
                    "fwd_bwd_step": "pf_prepare + pf_project + pf_bin_sort + pf_render_fwd + L2 loss grad + pf_render_bwd",
                    "fisheye_step": "the forward step for a 180-degree equidistant fisheye of the same size and position",
                    "displaced_step": "the forward step with every face displaced by up to 0.2 R at its four sites",
+                   "view_dependent_step": "the forward step with spherical-Voronoi site colours (8 axes per site)",
                    "scene_generation_s": round(gen_s, 1)},
         "fwd_fps": ws * 1000.0 / ms_fwd, "fwd_bwd_fps": ws * 1000.0 / ms_train, "ms_fwd_bwd": ms_train,
         "ms_render_fwd_kernel": ms_render,
@@ -439,6 +459,7 @@ def run_ours(args):
         "ms_connect_loss_and_grad": ms_connect,
         "fisheye_fwd_fps": 1000.0 / ms_fisheye,
         "displaced_fwd_fps": 1000.0 / ms_disp,
+        "view_dependent_fwd_fps": 1000.0 / ms_sv,
         "ms_build_neighbours": ms_neighbours,
         "neighbours_equal_input_lists": nbr_same,
         "work": stats,

@@ -75,6 +75,14 @@ typedef struct {
      * entry points as disp honour them, and pf_render_bwd adds dL/dsites
      * into pf_scene_grad.sites. */
     const float *sites;
+    /* Optional view-dependent site colours [N][4][8][6] (NULL: the constant
+     * colours tex): per site a spherical-Voronoi function (Sec. 3.4) of
+     * eight (axis xyz, rgb); seen along a ray with direction d the site's
+     * colour is sum_j softmax_j(10 a_j.(-d) / |a_j|) rgb_j.  They replace
+     * tex in the colour.  Forward only: pf_render_fwd, pf_render_fwd_static
+     * and the server honour them; pf_render_bwd, pf_render_fwd_contrib and
+     * stats passes return PF_ERR_INVALID_ARG for such a scene. */
+    const float *sv;
 } pf_scene;
 
 /* Camera: x_cam = rot (x_world - origin), OpenCV axes (x right, y down,

@@ -29,7 +29,8 @@ class PFError(RuntimeError):
 
 class Scene(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in ("pos", "w", "R", "sigma", "rgb", "normal", "offset", "tex", "nbr")] + [
-        ("n_cells", C.c_int32), ("k_nbr", C.c_int32), ("disp", C.c_void_p), ("sites", C.c_void_p)]
+        ("n_cells", C.c_int32), ("k_nbr", C.c_int32), ("disp", C.c_void_p), ("sites", C.c_void_p),
+        ("sv", C.c_void_p)]
 
 
 class Camera(C.Structure):

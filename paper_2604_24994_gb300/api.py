@@ -28,10 +28,12 @@ class DeviceScene:
         self.k = int(nbr.shape[1]) if nbr.dim() == 2 else 0
 
     @staticmethod
-    def from_numpy(scene, device="cuda", requires_grad=False, disp=None, sites=None) -> "DeviceScene":
+    def from_numpy(scene, device="cuda", requires_grad=False, disp=None, sites=None, sv=None) -> "DeviceScene":
         """`disp` [N,4] (or the scene's `disp` attribute): face displacement
         at the four texture sites (Eq. svdisp).  `sites` [N,4,2] (or the
-        scene's `sites`): learned positions of those sites, in units of R."""
+        scene's `sites`): learned positions of those sites, in units of R.
+        `sv` [N,4,8,6] (or the scene's `sv`): view-dependent site colours,
+        eight (axis, rgb) per site; forward rendering only."""
         params = {}
         for k in PARAMS:
             a = np.ascontiguousarray(getattr(scene, k), np.float32)
@@ -47,6 +49,10 @@ class DeviceScene:
             sites = getattr(scene, "sites", None)
         if sites is not None:
             params["sites"] = torch.from_numpy(np.ascontiguousarray(sites, np.float32).reshape(-1, 4, 2)).to(device)
+        if sv is None:
+            sv = getattr(scene, "sv", None)
+        if sv is not None:
+            params["sv"] = torch.from_numpy(np.ascontiguousarray(sv, np.float32).reshape(-1, 4, 8, 6)).to(device)
         nbr = torch.from_numpy(np.ascontiguousarray(scene.nbr, np.int32)).to(device)
         return DeviceScene(params, nbr)
 
@@ -61,7 +67,7 @@ class DeviceScene:
         s.nbr = self.nbr.data_ptr() if self.nbr.numel() else None
         s.n_cells = self.n
         s.k_nbr = self.k
-        for k, width in (("disp", 4), ("sites", 8)):
+        for k, width in (("disp", 4), ("sites", 8), ("sv", 192)):
             d = p.get(k)
             if d is not None:
                 if not (d.is_cuda and d.dtype == torch.float32 and d.is_contiguous() and d.numel() == width * self.n):
@@ -248,7 +254,7 @@ class Renderer:
         """pf_render_bwd: returns a dict of gradient tensors (added into
         `grads` when given)."""
         p = scene.params if params is None else params
-        keys = PARAMS + tuple(k for k in ("disp", "sites") if p.get(k) is not None)
+        keys = PARAMS + tuple(k for k in ("disp", "sites", "sv") if p.get(k) is not None)
         if grads is None:
             grads = {k: torch.zeros_like(p[k]) for k in keys}
         g = _lib.SceneGrad()

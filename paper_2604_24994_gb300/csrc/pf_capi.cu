@@ -388,8 +388,8 @@ pf_status pf_render_fwd(const pf_scene *scene, pf_plan *p, void *ws, float *rgb,
     g_err[0] = 0;
     if (!p || !ws || !scene_ok(scene, p) || !rgb || !T || !last) return PF_ERR_INVALID_ARG;
     WS w = p->ws(ws);
-    if ((scene->disp || scene->sites) && p->stats && p->n > 0) {
-        set_error("pf_render_fwd: no stats pass for a displaced scene or learned sites");
+    if ((scene->disp || scene->sites || scene->sv) && p->stats && p->n > 0) {
+        set_error("pf_render_fwd: no stats pass for an extended face model");
         return PF_ERR_INVALID_ARG;
     }
     const bool record = p->record_hits && !p->stats && w.hitmask != nullptr;
@@ -407,8 +407,8 @@ pf_status pf_render_fwd_contrib(const pf_scene *scene, pf_plan *p, void *ws, flo
         set_error("pf_render_fwd_contrib: null contribution array");
         return PF_ERR_INVALID_ARG;
     }
-    if ((scene->disp || scene->sites) && p->n > 0) {
-        set_error("pf_render_fwd_contrib: not available for a displaced scene or learned sites");
+    if ((scene->disp || scene->sites || scene->sv) && p->n > 0) {
+        set_error("pf_render_fwd_contrib: not available for an extended face model");
         return PF_ERR_INVALID_ARG;
     }
     WS w = p->ws(ws);
@@ -434,6 +434,10 @@ pf_status pf_render_bwd(const pf_scene *scene, pf_plan *p, void *ws, const float
     }
     if (scene->sites && p->n > 0 && !g->sites) {
         set_error("pf_render_bwd: learned sites need grad->sites");
+        return PF_ERR_INVALID_ARG;
+    }
+    if (scene->sv && p->n > 0) {
+        set_error("pf_render_bwd: no adjoint for view-dependent site colours");
         return PF_ERR_INVALID_ARG;
     }
     WS w = p->ws(ws);

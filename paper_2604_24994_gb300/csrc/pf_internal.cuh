@@ -21,6 +21,7 @@ constexpr float T_EPS = 1e-6f;         // forward stops once T drops below this
 constexpr float X_CAP = 60.0f;         // sigma * l is capped (alpha = 1 - e^-60)
 constexpr float KAPPA = 6.0f;          // soft-Voronoi sharpness, units of 1/R
 constexpr float SITE = 1.0f / 3.0f;    // texture sites at (+-1/3, +-1/3) R
+constexpr float SV_LAMBDA = 10.0f;     // sharpness of the spherical-Voronoi site colours
 
 // Precision budget of the render's float segment ends (the rest of the
 // budget for the forward's 1e-5 in T): an end whose float error bound could

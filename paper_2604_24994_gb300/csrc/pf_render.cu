@@ -480,10 +480,39 @@ __device__ __forceinline__ bool segment_from_kinds(const float *__restrict__ cr,
 
 // Soft-Voronoi face colour (Eq. svrad): weights of the four sites at the
 // texture point y = q + s d (the dense segment's end on the face side).
+// Colour of site k seen along the ray, a spherical-Voronoi function (Sec.
+// 3.4): with wo = -d and the site's eight (axis, rgb), the colours weighed by
+// softmax(SV_LAMBDA a.wo / |a|).  q: the cell's [4][8][6] floats in global
+// memory (the lanes of a warp that hit the cell read the same lines).
+__device__ __forceinline__ float3 sv_colour(const float *__restrict__ q, int k, float3 d) {
+    const float *p = q + 48 * k;
+    float lg[8], mx = -CUDART_INF_F;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        const float ax = __ldg(p + 6 * j), ay = __ldg(p + 6 * j + 1), az = __ldg(p + 6 * j + 2);
+        lg[j] = -SV_LAMBDA * (ax * d.x + ay * d.y + az * d.z) * rsqrtf(fmaf(ax, ax, fmaf(ay, ay, az * az)));
+        mx = fmaxf(mx, lg[j]);
+    }
+    float z = 0.f;
+    float3 c = f3(0.f, 0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        const float w = __expf(lg[j] - mx);
+        z += w;
+        c.x = fmaf(w, __ldg(p + 6 * j + 3), c.x);
+        c.y = fmaf(w, __ldg(p + 6 * j + 4), c.y);
+        c.z = fmaf(w, __ldg(p + 6 * j + 5), c.z);
+    }
+    const float iz = 1.0f / z;
+    return f3(c.x * iz, c.y * iz, c.z * iz);
+}
+
 // Colour at the texture point; `st`: the cell's learned site positions, or
-// null for the fixed ones (then tx.ax / tx.ay hold u minus the sites).
+// null for the fixed ones (then tx.ax / tx.ay hold u minus the sites); `sv`:
+// the cell's view-dependent site colours, or null for the constant ones.
 __device__ __forceinline__ float3 face_colour(const float *__restrict__ cr, const Seg &sg, const Ray &ray, Tex &tx,
-                                              const float *__restrict__ st = nullptr) {
+                                              const float *__restrict__ st = nullptr,
+                                              const float *__restrict__ sv = nullptr) {
     const float ss = sg.dnd > 0.0f ? sg.sb : sg.sa;
     tx.ys = f3(fmaf(ss, ray.dh.x, sg.q.x), fmaf(ss, ray.dh.y, sg.q.y), fmaf(ss, ray.dh.z, sg.q.z));
     tx.u1 = dot3(f3(cr[CR_E1], cr[CR_E1 + 1], cr[CR_E1 + 2]), tx.ys);
@@ -520,9 +549,10 @@ __device__ __forceinline__ float3 face_colour(const float *__restrict__ cr, cons
 #pragma unroll
     for (int k = 0; k < 4; k++) {
         tx.W[k] *= iz;
-        c.x = fmaf(tx.W[k], cr[CR_TEX + 3 * k], c.x);
-        c.y = fmaf(tx.W[k], cr[CR_TEX + 3 * k + 1], c.y);
-        c.z = fmaf(tx.W[k], cr[CR_TEX + 3 * k + 2], c.z);
+        const float3 ck = sv ? sv_colour(sv, k, ray.dh) : f3(cr[CR_TEX + 3 * k], cr[CR_TEX + 3 * k + 1], cr[CR_TEX + 3 * k + 2]);
+        c.x = fmaf(tx.W[k], ck.x, c.x);
+        c.y = fmaf(tx.W[k], ck.y, c.y);
+        c.z = fmaf(tx.W[k], ck.z, c.z);
     }
     return c;
 }
@@ -650,6 +680,7 @@ struct RenderArgs {
     float *gdisp;           // [N][4] its gradient (the backward adds into it), or null
     const float *sites;     // [N][4][2] learned texture / detail site positions, or null
     float *gsites;          // [N][4][2] their gradient, or null
+    const float *sv;        // [N][4][8][6] view-dependent site colours, or null (forward only)
 };
 
 // Hit masks: one 32-bit word per (warp of the tile, batch, pixel of the
@@ -857,7 +888,8 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, i
             Tex tx;
             const float3 c = face_colour(cr, seg, ray, tx,
                                          EXT && sites ? reinterpret_cast<const float *>(sg.xtr(buf) + 3 * j + 1)
-                                                      : nullptr);
+                                                      : nullptr,
+                                         EXT && A.sv ? A.sv + 192 * (int64_t)sg.ids(buf)[j] : nullptr);
             const float x = fminf(cr[CR_SIG] * (seg.sb - seg.sa), X_CAP);
             const float ex = __expf(-x);
             const float wgt = T * (1.0f - ex);
@@ -1399,6 +1431,7 @@ static RenderArgs make_args(const pf_scene &s, const Plan &p, const WS &w) {
     A.gdisp = nullptr;
     A.sites = s.sites;
     A.gsites = nullptr;
+    A.sv = s.sv;
     return A;
 }
 
@@ -1424,7 +1457,7 @@ cudaError_t launch_render_fwd(const pf_scene &s, const Plan &p, const WS &w, flo
     A.contrib_sparse = contrib_sparse;
     A.contrib_normal = contrib_normal;
     const bool contrib = contrib_sparse != nullptr;
-    const bool disp = s.disp != nullptr || s.sites != nullptr;  // an extended face model
+    const bool disp = s.disp != nullptr || s.sites != nullptr || s.sv != nullptr;  // an extended face model
     if (disp && (contrib || p.stats)) return cudaErrorNotSupported;  // the C API refuses these first
     const size_t smem = disp ? stage_bytes(p.k, false, true) : fwd_smem(p.k);
     cudaError_t e = cudaMemsetAsync(&w.counters->q_fwd, 0, sizeof(unsigned int), st);

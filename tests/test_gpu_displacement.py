@@ -134,3 +134,54 @@ def test_displaced_scene_refuses_contributions(tiny):
     with pytest.raises(_lib.PFError) as e:
         r.render_fwd(ds, contrib=(torch.zeros(ds.n, device="cuda"), torch.zeros(ds.n, device="cuda")))
     assert e.value.status == _lib.PF_ERR_INVALID_ARG
+
+
+def random_sv(sc, seed):
+    rng = np.random.default_rng(seed)
+    axes = rng.normal(size=(sc.n, 4, 8, 3))
+    cols = rng.uniform(0, 1, (sc.n, 4, 8, 3))
+    return np.concatenate([axes, cols], -1).astype(np.float32)
+
+
+@pytest.mark.parametrize("with_disp,with_sites", [(False, False), (True, True)])
+def test_view_dependent_site_colours_forward(with_disp, with_sites):
+    """Spherical-Voronoi site colours (eight axes per site) in the forward,
+    alone and with displacement and learned sites, pinhole and fisheye
+    views, against the FP64 oracle."""
+    import torch
+    from paper_2604_24994_gb300 import DeviceScene, Renderer
+    rng = np.random.default_rng(9)
+    sc = f32(cluster_scene(rng, n=50, spread=0.3, r=(0.08, 0.2), tex_std=0.15))
+    disp = random_disp(sc, 0.3, 8) if with_disp else None
+    sites = random_sites(sc, 0.2, 9) if with_sites else None
+    sv = random_sv(sc, 10)
+    cams = [inputs.look_at((1.2, 0.4, 0.3), 80, 64),
+            inputs.fisheye_look_at((-0.9, 0.6, 0.2), 60, 60, fov_deg=150.0)]
+    ds = DeviceScene.from_numpy(sc, "cuda", disp=disp, sites=sites, sv=sv)
+    r = Renderer(ds.n, ds.k, cams)
+    rgb, T, last = r.forward(ds)
+    torch.cuda.synchronize()
+    rgb = rgb.cpu().numpy().astype(np.float64)
+    T = T.cpu().numpy().astype(np.float64)
+    orc = oracle.Oracle(sc, disp=disp, sites=sites, sv=sv)
+    o = 0
+    for cam in cams:
+        n = cam.n_pixels
+        rgb_o, T_o = orc.render(cam)
+        assert_close_image(rgb[o:o + n], T[o:o + n], rgb_o, T_o, f"sv {cam.width}x{cam.height}")
+        o += n
+    # the colours are view dependent: the constant-colour image differs
+    rgb_c, _ = oracle.Oracle(sc, disp=disp, sites=sites).render(cams[0])
+    assert np.abs(rgb_c - rgb[:cams[0].n_pixels]).max() > 1e-2
+
+
+def test_view_dependent_site_colours_refuse_the_backward(tiny):
+    import torch
+    from paper_2604_24994_gb300 import DeviceScene, Renderer, _lib
+    sc, cam = tiny
+    ds = DeviceScene.from_numpy(sc, "cuda", sv=random_sv(sc, 11))
+    r = Renderer(ds.n, ds.k, [cam])
+    rgb, T, last = r.forward(ds)
+    with pytest.raises(_lib.PFError) as e:
+        r.backward(ds, torch.zeros_like(rgb), None, T, last)
+    assert e.value.status == _lib.PF_ERR_INVALID_ARG
