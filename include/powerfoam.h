@@ -79,9 +79,10 @@ typedef struct {
      * colours tex): per site a spherical-Voronoi function (Sec. 3.4) of
      * eight (axis xyz, rgb); seen along a ray with direction d the site's
      * colour is sum_j softmax_j(10 a_j.(-d) / |a_j|) rgb_j.  They replace
-     * tex in the colour.  Forward only: pf_render_fwd, pf_render_fwd_static
-     * and the server honour them; pf_render_bwd, pf_render_fwd_contrib and
-     * stats passes return PF_ERR_INVALID_ARG for such a scene. */
+     * tex in the colour.  pf_render_fwd, pf_render_fwd_static, the server
+     * and pf_render_bwd (adding dL/dsv into pf_scene_grad.sv) honour them;
+     * pf_render_fwd_contrib and stats passes return PF_ERR_INVALID_ARG for
+     * such a scene. */
     const float *sv;
 } pf_scene;
 
@@ -110,6 +111,8 @@ typedef struct {
     float *pos, *w, *R, *sigma, *rgb, *normal, *offset, *tex;
     float *disp;  /* [N][4], required when the scene has a displacement, else ignored */
     float *sites; /* [N][4][2], required when the scene has learned sites, else ignored */
+    float *sv;    /* [N][4][8][6], required when the scene has view-dependent site
+                   * colours, else ignored (tex then gets no gradient) */
 } pf_scene_grad;
 
 typedef struct pf_plan pf_plan;

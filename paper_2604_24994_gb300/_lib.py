@@ -40,7 +40,8 @@ class Camera(C.Structure):
 
 
 class SceneGrad(C.Structure):
-    _fields_ = [(k, C.c_void_p) for k in ("pos", "w", "R", "sigma", "rgb", "normal", "offset", "tex", "disp", "sites")]
+    _fields_ = [(k, C.c_void_p) for k in ("pos", "w", "R", "sigma", "rgb", "normal", "offset", "tex", "disp", "sites",
+                                          "sv")]
 
 
 class Stats(C.Structure):

@@ -33,7 +33,7 @@ class DeviceScene:
         at the four texture sites (Eq. svdisp).  `sites` [N,4,2] (or the
         scene's `sites`): learned positions of those sites, in units of R.
         `sv` [N,4,8,6] (or the scene's `sv`): view-dependent site colours,
-        eight (axis, rgb) per site; forward rendering only."""
+        eight (axis, rgb) per site."""
         params = {}
         for k in PARAMS:
             a = np.ascontiguousarray(getattr(scene, k), np.float32)

@@ -436,8 +436,8 @@ pf_status pf_render_bwd(const pf_scene *scene, pf_plan *p, void *ws, const float
         set_error("pf_render_bwd: learned sites need grad->sites");
         return PF_ERR_INVALID_ARG;
     }
-    if (scene->sv && p->n > 0) {
-        set_error("pf_render_bwd: no adjoint for view-dependent site colours");
+    if (scene->sv && p->n > 0 && !g->sv) {
+        set_error("pf_render_bwd: view-dependent site colours need grad->sv");
         return PF_ERR_INVALID_ARG;
     }
     WS w = p->ws(ws);

@@ -680,7 +680,8 @@ struct RenderArgs {
     float *gdisp;           // [N][4] its gradient (the backward adds into it), or null
     const float *sites;     // [N][4][2] learned texture / detail site positions, or null
     float *gsites;          // [N][4][2] their gradient, or null
-    const float *sv;        // [N][4][8][6] view-dependent site colours, or null (forward only)
+    const float *sv;        // [N][4][8][6] view-dependent site colours, or null
+    float *gsv;             // [N][4][8][6] their gradient, or null
 };
 
 // Hit masks: one 32-bit word per (warp of the tile, batch, pixel of the
@@ -1206,7 +1207,8 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
             int ja, jb;
             {
                 Tex tx;
-                const float3 c = face_colour(cr, sg, ray, tx, st);
+                const float *svc = EXT && A.sv ? A.sv + 192 * (int64_t)cell : nullptr;
+                const float3 c = face_colour(cr, sg, ray, tx, st, svc);
                 const float sig = cr[CR_SIG];
                 const float l = sg.sb - sg.sa;
                 const float xr = sig * l;
@@ -1226,11 +1228,70 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
                 float gW[4], sW = 0.f;
 #pragma unroll
                 for (int k = 0; k < 4; k++) {
+                    // the site's colour weight (finalize: the tex gradient, and summed, the rgb one)
                     vv[G_TEX + 3 * k] = tx.W[k] * gc.x;
                     vv[G_TEX + 3 * k + 1] = tx.W[k] * gc.y;
                     vv[G_TEX + 3 * k + 2] = tx.W[k] * gc.z;
-                    gW[k] = cr[CR_TEX + 3 * k] * gc.x + cr[CR_TEX + 3 * k + 1] * gc.y + cr[CR_TEX + 3 * k + 2] * gc.z;
+                    const float3 ck = svc ? sv_colour(svc, k, ray.dh)
+                                          : f3(cr[CR_TEX + 3 * k], cr[CR_TEX + 3 * k + 1], cr[CR_TEX + 3 * k + 2]);
+                    gW[k] = ck.x * gc.x + ck.y * gc.y + ck.z * gc.z;
                     sW += tx.W[k] * gW[k];
+                }
+                if (EXT && svc) {
+                    // spherical-Voronoi site colours c_k = sum_j P_j rgb_j, P = softmax(lambda a_j.wo / |a_j|),
+                    // wo = -d: dL/drgb_j = P_j W_k gc; dL/dlogit_j = P_j (gP_j - sum P gP) with
+                    // gP_j = W_k gc.rgb_j; dL/da_j = (I - a a^T / |a|^2) lambda wo dL/dlogit_j / |a|.
+                    // 48 values per site, summed over the warp in two transposed rounds of 24.
+#pragma unroll 1
+                    for (int k = 0; k < 4; k++) {
+                        const float *pk = svc + 48 * k;
+                        const float3 gck = f3(tx.W[k] * gc.x, tx.W[k] * gc.y, tx.W[k] * gc.z);
+                        float P[8], gP[8], mx = -CUDART_INF_F, z = 0.f, sP = 0.f;
+#pragma unroll
+                        for (int j = 0; j < 8; j++) {
+                            const float ax = __ldg(pk + 6 * j), ay = __ldg(pk + 6 * j + 1), az = __ldg(pk + 6 * j + 2);
+                            P[j] = -SV_LAMBDA * (ax * ray.dh.x + ay * ray.dh.y + az * ray.dh.z) *
+                                   rsqrtf(fmaf(ax, ax, fmaf(ay, ay, az * az)));
+                            mx = fmaxf(mx, P[j]);
+                            gP[j] = gck.x * __ldg(pk + 6 * j + 3) + gck.y * __ldg(pk + 6 * j + 4) +
+                                    gck.z * __ldg(pk + 6 * j + 5);
+                        }
+#pragma unroll
+                        for (int j = 0; j < 8; j++) {
+                            P[j] = __expf(P[j] - mx);
+                            z += P[j];
+                        }
+                        const float iz = 1.0f / z;
+#pragma unroll
+                        for (int j = 0; j < 8; j++) {
+                            P[j] *= iz;
+                            sP = fmaf(P[j], gP[j], sP);
+                        }
+#pragma unroll
+                        for (int h = 0; h < 2; h++) {
+                            float v[32];
+#pragma unroll
+                            for (int jj = 0; jj < 4; jj++) {
+                                const int j = 4 * h + jj;
+                                const float ax = __ldg(pk + 6 * j), ay = __ldg(pk + 6 * j + 1), az = __ldg(pk + 6 * j + 2);
+                                const float ia = rsqrtf(fmaf(ax, ax, fmaf(ay, ay, az * az)));
+                                const float3 ah = f3(ax * ia, ay * ia, az * ia);
+                                const float gl = -SV_LAMBDA * P[j] * (gP[j] - sP);  // times wo = -d below
+                                const float3 ga = f3(gl * ray.dh.x, gl * ray.dh.y, gl * ray.dh.z);
+                                const float pa = dot3(ah, ga);
+                                v[6 * jj] = (ga.x - ah.x * pa) * ia;
+                                v[6 * jj + 1] = (ga.y - ah.y * pa) * ia;
+                                v[6 * jj + 2] = (ga.z - ah.z * pa) * ia;
+                                v[6 * jj + 3] = P[j] * gck.x;
+                                v[6 * jj + 4] = P[j] * gck.y;
+                                v[6 * jj + 5] = P[j] * gck.z;
+                            }
+#pragma unroll
+                            for (int q = 24; q < 32; q++) v[q] = 0.f;
+                            const float sum = warp_transpose_sum(v, lane);
+                            if (lane < 24 && A.gsv) atomicAdd(A.gsv + 192 * (int64_t)cell + 48 * k + 24 * h + lane, sum);
+                        }
+                    }
                 }
                 float gu1 = 0.f, gu2 = 0.f;
                 float gs[8];  // learned sites: r_k = |u - s_k|, so dL/ds_k = -dL/du through logit k
@@ -1382,7 +1443,8 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
 // Accumulators -> parameter gradients.  n = |n| n^:  dL/dn = (I - n^ n^T) dL/dn^ / |n|;
 // rgb enters the colour with weight 1, the texture sites with weights summing to 1.
 __global__ void __launch_bounds__(256) finalize_kernel(int n, const float *__restrict__ acc,
-                                                       const float *__restrict__ cellrec, pf_scene_grad G) {
+                                                       const float *__restrict__ cellrec, pf_scene_grad G,
+                                                       bool view_dependent) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float *a = acc + (int64_t)i * ACC_F;
@@ -1405,9 +1467,11 @@ __global__ void __launch_bounds__(256) finalize_kernel(int n, const float *__res
 #pragma unroll
     for (int k = 0; k < 4; k++) {
         const float t0 = a[G_TEX + 3 * k], t1 = a[G_TEX + 3 * k + 1], t2 = a[G_TEX + 3 * k + 2];
-        G.tex[12 * i + 3 * k] += t0;
-        G.tex[12 * i + 3 * k + 1] += t1;
-        G.tex[12 * i + 3 * k + 2] += t2;
+        if (!view_dependent) {  // (the spherical-Voronoi colours replace tex)
+            G.tex[12 * i + 3 * k] += t0;
+            G.tex[12 * i + 3 * k + 1] += t1;
+            G.tex[12 * i + 3 * k + 2] += t2;
+        }
         r0 += t0;
         r1 += t1;
         r2 += t2;
@@ -1432,6 +1496,7 @@ static RenderArgs make_args(const pf_scene &s, const Plan &p, const WS &w) {
     A.sites = s.sites;
     A.gsites = nullptr;
     A.sv = s.sv;
+    A.gsv = nullptr;
     return A;
 }
 
@@ -1481,7 +1546,8 @@ cudaError_t launch_render_bwd(const pf_scene &s, const Plan &p, const WS &w, con
         RenderArgs A = make_args(s, p, w);
         A.gdisp = g.disp;
         A.gsites = g.sites;
-        const bool disp = s.disp != nullptr || s.sites != nullptr;  // an extended face model
+        A.gsv = g.sv;
+        const bool disp = s.disp != nullptr || s.sites != nullptr || s.sv != nullptr;  // an extended face model
         const size_t smem = disp ? stage_bytes(p.k, true, true) : bwd_smem(p.k);
         e = cudaMemsetAsync(&w.counters->q_bwd, 0, sizeof(unsigned int), st);
         if (e != cudaSuccess) return e;
@@ -1493,7 +1559,7 @@ cudaError_t launch_render_bwd(const pf_scene &s, const Plan &p, const WS &w, con
                                                                                  last);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    finalize_kernel<<<(p.n + 255) / 256, 256, 0, st>>>(p.n, w.acc, w.cellrec, g);
+    finalize_kernel<<<(p.n + 255) / 256, 256, 0, st>>>(p.n, w.acc, w.cellrec, g, s.sv != nullptr);
     return cudaGetLastError();
 }
 

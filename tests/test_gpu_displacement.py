@@ -175,13 +175,38 @@ def test_view_dependent_site_colours_forward(with_disp, with_sites):
     assert np.abs(rgb_c - rgb[:cams[0].n_pixels]).max() > 1e-2
 
 
-def test_view_dependent_site_colours_refuse_the_backward(tiny):
+@pytest.mark.parametrize("with_masks,with_disp", [(True, False), (False, True)])
+def test_view_dependent_site_colours_backward(with_masks, with_disp):
+    """The backward with spherical-Voronoi site colours: every parameter's
+    gradient, the axes' and colours' included, within 1e-3 relative L2 of
+    the FP64 adjoint; tex gets none (the colours replace it)."""
     import torch
-    from paper_2604_24994_gb300 import DeviceScene, Renderer, _lib
-    sc, cam = tiny
-    ds = DeviceScene.from_numpy(sc, "cuda", sv=random_sv(sc, 11))
-    r = Renderer(ds.n, ds.k, [cam])
+    from paper_2604_24994_gb300 import DeviceScene, Renderer
+    from tests.gpu_util import rel_l2
+    rng = np.random.default_rng(33)
+    sc = f32(cluster_scene(rng, n=40, spread=0.15, r=(0.06, 0.12), tex_std=0.2))
+    disp = random_disp(sc, 0.3, 12) if with_disp else None
+    sv = random_sv(sc, 13)
+    cams = [inputs.look_at((0.7, 0.2, 0.1), 48, 40, fov_y_deg=40),
+            inputs.look_at((-0.5, 0.5, 0.3), 33, 21, fov_y_deg=50)]
+    npx = sum(c.n_pixels for c in cams)
+    gC = rng.normal(size=(npx, 3))
+    gT = rng.normal(size=npx)
+    ds = DeviceScene.from_numpy(sc, "cuda", disp=disp, sv=sv)
+    r = Renderer(ds.n, ds.k, cams, hit_records=with_masks)
     rgb, T, last = r.forward(ds)
-    with pytest.raises(_lib.PFError) as e:
-        r.backward(ds, torch.zeros_like(rgb), None, T, last)
-    assert e.value.status == _lib.PF_ERR_INVALID_ARG
+    g = r.backward(ds, torch.from_numpy(gC).float().cuda(), torch.from_numpy(gT).float().cuda(), T, last)
+    torch.cuda.synchronize()
+    G = {k: v.cpu().numpy().astype(np.float64) for k, v in g.items()}
+    orc = oracle.Oracle(sc, disp=disp, sv=sv)
+    Go = None
+    o = 0
+    for cam in cams:
+        gg = orc.render_grad(cam, gC[o:o + cam.n_pixels], gT[o:o + cam.n_pixels])
+        Go = gg if Go is None else {k: Go[k] + gg[k] for k in gg}
+        o += cam.n_pixels
+    for k in ("pos", "w", "R", "sigma", "rgb", "normal", "offset", "sv") + (("disp",) if with_disp else ()):
+        a, b = G[k].reshape(-1), np.asarray(Go[k]).reshape(-1)
+        assert np.linalg.norm(b) > 0, k
+        assert rel_l2(a, b) < 1e-3, (k, rel_l2(a, b))
+    assert np.abs(G["tex"]).max() == 0.0
