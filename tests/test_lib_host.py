@@ -136,3 +136,64 @@ def test_product_path_refuses_to_run_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(_lib, "_lib", None)
     with pytest.raises(RuntimeError, match="CUDA library missing"):
         _lib.lib()
+
+
+def test_neighbour_build_validates_arguments(lib):
+    """pf_build_neighbours refuses bad sizes, null pointers and a small
+    workspace before any device work; the workspace is ~116 bytes per cell."""
+    from paper_2604_24994_gb300 import _lib
+    assert lib.pf_neighbours_workspace_bytes(-1) == 0
+    b = lib.pf_neighbours_workspace_bytes(1_000_000)
+    assert 100e6 < b < 140e6
+    fake = C.c_void_p(4096)
+    args = lambda n, k, nbr=fake, ws_bytes=b: (fake, fake, fake, n, k, nbr, fake, None, None, fake, ws_bytes, None)
+    assert lib.pf_build_neighbours(*args(1_000_000, 65)) == _lib.PF_ERR_INVALID_ARG
+    assert lib.pf_build_neighbours(*args(-1, 8)) == _lib.PF_ERR_INVALID_ARG
+    assert lib.pf_build_neighbours(*args(100, 8, nbr=None)) == _lib.PF_ERR_INVALID_ARG
+    assert lib.pf_build_neighbours(*args(1_000_000, 32, ws_bytes=b - 1)) == _lib.PF_ERR_CAPACITY
+    assert b"workspace" in lib.pf_last_error_message()
+
+
+def test_camera_models(lib):
+    from paper_2604_24994_gb300 import _lib
+    h = C.c_void_p()
+    fe = inputs.fisheye_look_at((3, 0, 0), 64, 48, fov_deg=190.0)
+    assert lib.pf_plan_create(10, 4, _lib.camera_array([fe]), 1, 100, C.byref(h)) == 0
+    lib.pf_plan_destroy(h)
+    bad = _lib.camera_array([fe])
+    bad[0].model = 2
+    assert lib.pf_plan_create(10, 4, bad, 1, 100, C.byref(h)) == _lib.PF_ERR_INVALID_ARG
+
+
+def test_extended_face_model_checks(lib):
+    """Displacement, learned sites and view-dependent colours: misaligned
+    arrays, a stats pass, the contribution forward and a backward without
+    the matching gradient arrays are refused on the host."""
+    from paper_2604_24994_gb300 import _lib
+    h = C.c_void_p()
+    assert lib.pf_plan_create(10, 4, _lib.camera_array([inputs.look_at((3, 0, 0), 32, 32)]), 1, 100,
+                              C.byref(h)) == 0
+    fake = 1 << 20                                       # never dereferenced: every call returns first
+    s = _lib.Scene()
+    for k in ("pos", "w", "R", "sigma", "rgb", "normal", "offset", "tex", "nbr"):
+        setattr(s, k, fake)
+    s.n_cells, s.k_nbr = 10, 4
+    out = C.c_void_p(fake)
+    s.disp = fake + 8                                    # not 16-byte aligned
+    assert lib.pf_render_fwd(C.byref(s), h, out, out, out, out, None) == _lib.PF_ERR_INVALID_ARG
+    assert b"aligned" in lib.pf_last_error_message()
+    s.disp = fake
+    assert lib.pf_plan_enable_stats(h, 1) == 0
+    assert lib.pf_render_fwd(C.byref(s), h, out, out, out, out, None) == _lib.PF_ERR_INVALID_ARG
+    assert lib.pf_plan_enable_stats(h, 0) == 0
+    s.disp, s.sv = None, fake
+    assert lib.pf_render_fwd_contrib(C.byref(s), h, out, out, out, out, out, out, None) == _lib.PF_ERR_INVALID_ARG
+    g = _lib.SceneGrad()
+    for k in ("pos", "w", "R", "sigma", "rgb", "normal", "offset", "tex"):
+        setattr(g, k, fake)
+    for k in ("disp", "sites", "sv"):
+        s.disp = s.sites = s.sv = None
+        setattr(s, k, fake)
+        assert lib.pf_render_bwd(C.byref(s), h, out, out, out, out, out, C.byref(g), None) == _lib.PF_ERR_INVALID_ARG
+        assert k.encode() in lib.pf_last_error_message()
+    lib.pf_plan_destroy(h)
