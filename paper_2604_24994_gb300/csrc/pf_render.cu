@@ -709,10 +709,12 @@ struct Cone {
     float tan_t;
 };
 
-__device__ __forceinline__ Cone warp_cone(const ViewDev &V, int wx, int wy, const Ray &ray) {
+__device__ __forceinline__ Cone warp_cone(const Ray &ray) {
     Cone c;
-    const Ray r0 = pixel_ray(V, wx + 4, wy + 2);   // near the block's centre; the cone is measured from it
-    c.dc = r0.dh;
+    // the ray of pixel (wx + 4, wy + 2), near the block's centre, is lane 20's
+    // own (lanes run x fastest, 8 to a row); the cone is measured from it
+    c.dc = f3(__shfl_sync(0xffffffffu, ray.dh.x, 20), __shfl_sync(0xffffffffu, ray.dh.y, 20),
+              __shfl_sync(0xffffffffu, ray.dh.z, 20));
     const float3 d = ray.dh;
     const float3 x = cross3(d, c.dc);
     const float sn = sqrtf(dot3(x, x));
@@ -791,7 +793,7 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, i
     tile_pixel(V, tile - V.tile_base, px, py, wx, wy);
     const bool inside = px < V.width && py < V.height;
     const Ray ray = pixel_ray(V, px, py);
-    const Cone cone = warp_cone(V, wx, wy, ray);
+    const Cone cone = warp_cone(ray);
     const bool has_ray = pixel_has_ray(V, px, py);
 
     unsigned long long s = A.w.tile_start[tile], e = A.w.tile_start[tile + 1];
@@ -1091,7 +1093,7 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
     tile_pixel(V, tile - V.tile_base, px, py, wx, wy);
     const bool inside = px < V.width && py < V.height;
     const Ray ray = pixel_ray(V, px, py);
-    const Cone cone = warp_cone(V, wx, wy, ray);
+    const Cone cone = warp_cone(ray);
     unsigned long long s = A.w.tile_start[tile], e = A.w.tile_start[tile + 1];
     if (s > A.cap) s = A.cap;
     if (e > A.cap) e = A.cap;
