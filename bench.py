@@ -33,7 +33,8 @@ WORKLOAD_SMALL = "profiling case: the same recipe at 400,000 cells, one 1280x720
 
 # Algorithmic FP32 flops of the forward per counted event (FMA = 2, add /
 # mul / compare / sqrt / exp / reciprocal = 1), counted operation by
-# operation from the render kernel's source; the design doc lists the terms.
+# operation from the render kernel's source; the terms are listed beside
+# each constant.
 FLOPS_PER_CANDIDATE = 15        # cheap sphere test: m x d (9), |v|^2 (5), compare (1)
 FLOPS_PER_PASS = 107            # compensated m x d (51), D (7), tangent check (9), sqrt (1),
                                 # q = d x v (9), m.d (5), camera end (2), face clip (14),
