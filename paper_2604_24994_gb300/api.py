@@ -16,6 +16,7 @@ from . import _lib
 from ._lib import check, lib, ptr
 
 PARAMS = ("pos", "w", "R", "sigma", "rgb", "normal", "offset", "tex")
+EXTRA_PARAMS = ("disp", "sites", "sv")   # optional: face displacement, learned sites, view-dependent colours
 
 
 class DeviceScene:
@@ -254,7 +255,7 @@ class Renderer:
         """pf_render_bwd: returns a dict of gradient tensors (added into
         `grads` when given)."""
         p = scene.params if params is None else params
-        keys = PARAMS + tuple(k for k in ("disp", "sites", "sv") if p.get(k) is not None)
+        keys = PARAMS + tuple(k for k in EXTRA_PARAMS if p.get(k) is not None)
         if grads is None:
             grads = {k: torch.zeros_like(p[k]) for k in keys}
         g = _lib.SceneGrad()
@@ -307,19 +308,21 @@ class Renderer:
 
 
 class RenderFunction(torch.autograd.Function):
-    """(pos, w, R, sigma, rgb, normal, offset, tex) -> (rgb [P,3], T [P]).
+    """(pos, w, R, sigma, rgb, normal, offset, tex[, disp][, sites][, sv]) ->
+    (rgb [P,3], T [P]); `keys` names the parameter tensors that follow.
 
     The backward replays the forward's checkpoint (T, last) tile by tile,
     back to front, through pf_render_bwd."""
 
     @staticmethod
-    def forward(ctx, renderer: Renderer, scene: DeviceScene, *params):
-        pd = dict(zip(PARAMS, [p.detach() for p in params]))
+    def forward(ctx, renderer: Renderer, scene: DeviceScene, keys, *params):
+        pd = dict(zip(keys, [p.detach() for p in params]))
         gen = renderer.bin(scene, pd)
         rgb, T, last = renderer.render_fwd(scene, pd)
         ctx.renderer = renderer
         ctx.scene = scene
         ctx.gen = gen
+        ctx.keys = keys
         ctx.save_for_backward(T, last, *params)
         return rgb, T
 
@@ -327,16 +330,19 @@ class RenderFunction(torch.autograd.Function):
     def backward(ctx, g_rgb, g_T):
         T, last, *params = ctx.saved_tensors
         r = ctx.renderer
-        pd = dict(zip(PARAMS, [p.detach() for p in params]))
+        pd = dict(zip(ctx.keys, [p.detach() for p in params]))
         if r.generation != ctx.gen:  # the workspace was reused: rebuild the same bins
             r.bin(ctx.scene, pd)
         if g_rgb is None:
             g_rgb = torch.zeros((T.shape[0], 3), device=T.device)
         grads = r.backward(ctx.scene, g_rgb, g_T, T, last, pd)
-        return (None, None, *[grads[k] for k in PARAMS])
+        return (None, None, None, *[grads[k] for k in ctx.keys])
 
 
 def render(renderer: Renderer, scene: DeviceScene, params: dict | None = None):
-    """Differentiable render of all the renderer's views: flat rgb [P,3], T [P]."""
+    """Differentiable render of all the renderer's views: flat rgb [P,3], T [P],
+    with gradients for every parameter tensor of the scene (the optional
+    displacement, learned sites and view-dependent colours included)."""
     p = scene.params if params is None else params
-    return RenderFunction.apply(renderer, scene, *[p[k] for k in PARAMS])
+    keys = PARAMS + tuple(k for k in EXTRA_PARAMS if p.get(k) is not None)
+    return RenderFunction.apply(renderer, scene, keys, *[p[k] for k in keys])
