@@ -93,6 +93,8 @@ def lib():
             _lib.orc_bin.argtypes = [P(_Camera), C.c_int64, P(d), P(d), P(d),
                                      P(C.c_int32), P(C.c_uint64)]
             f = C.c_float
+            _lib.orc_contrib_grad.argtypes = [P(_Scene), P(_Cands), P(_Camera), C.c_int64, P(C.c_int32), P(d), P(d),
+                                              P(d), C.c_int]
             _lib.orc_neighbours.argtypes = [P(f), P(f), P(f), C.c_int64, C.c_int32, C.c_int64, P(C.c_int64),
                                             P(C.c_int32), P(f), C.c_int]
         return _lib
@@ -314,6 +316,32 @@ class Oracle:
                           _ptr(nm, C.c_double), self.nthreads)
         return sp, nm
 
+    def contrib_grad(self, cam, w_sparse, w_normal, pix=None) -> dict:
+        """Gradient (float64 dict keyed like render_grad) of
+        sum_i (w_sparse[i] sparse_i + w_normal[i] normal_i) over the pixels,
+        sparse / normal the per-cell contributions of `contrib`."""
+        pixa, npix = self._pix(cam, pix)
+        ws = np.ascontiguousarray(np.broadcast_to(np.asarray(w_sparse, np.float64), (self.n,)))
+        wn = np.ascontiguousarray(np.broadcast_to(np.asarray(w_normal, np.float64), (self.n,)))
+        g = np.zeros((self.n, NPAR), np.float64)
+        lib().orc_contrib_grad(C.byref(self._s), C.byref(self._cs) if self._cs else None,
+                               C.byref(camera_struct(cam)), npix,
+                               _ptr(pixa, C.c_int32) if pixa is not None else None, _ptr(ws, C.c_double),
+                               _ptr(wn, C.c_double), _ptr(g, C.c_double), self.nthreads)
+        return self._split_grad(g)
+
+    def _split_grad(self, g) -> dict:
+        out = {}
+        for k, (c0, w) in PARAM_COLS.items():
+            if k in ("disp", "sites", "sv") and k not in self._arrs:
+                continue
+            out[k] = g[:, c0:c0 + w] if w > 1 else g[:, c0].copy()
+            if k == "sites":
+                out[k] = out[k].reshape(-1, 4, 2)
+            if k == "sv":
+                out[k] = out[k].reshape(-1, 4, 8, 6)
+        return out
+
     def render_grad(self, cam, dL_dC, dL_dT, pix=None) -> dict:
         """dL/d(parameters) (float64 dict keyed like the scene) for upstream
         gradients dL/dC [npix,3] and dL/dT [npix] of the rendered pixels."""
@@ -326,16 +354,7 @@ class Oracle:
                               _ptr(pixa, C.c_int32) if pixa is not None else None, self.kappa,
                               _ptr(gC, C.c_double), _ptr(gT, C.c_double), _ptr(g, C.c_double),
                               self.nthreads)
-        out = {}
-        for k, (c0, w) in PARAM_COLS.items():
-            if k in ("disp", "sites", "sv") and k not in self._arrs:
-                continue
-            out[k] = g[:, c0:c0 + w] if w > 1 else g[:, c0].copy()
-            if k == "sites":
-                out[k] = out[k].reshape(-1, 4, 2)
-            if k == "sv":
-                out[k] = out[k].reshape(-1, 4, 8, 6)
-        return out
+        return self._split_grad(g)
 
     def ray(self, cam, u, v):
         """(origin, unit direction) of pixel (u, v); None where the pixel has

@@ -1040,3 +1040,93 @@ int orc_neighbours(const float *pos, const float *w, const float *R, int64_t n, 
     }
     return 0;
 }
+
+/*
+ * Gradient of L = sum_i (ws_i sparse_i + wn_i normal_i), the per-cell
+ * contributions of orc_cell_contrib (Sec. 4's L_sparse and L_normal with
+ * per-cell weights), with respect to every cell parameter.  Along one ray
+ * the contributions composite the scalar c_k = ws_i + wn_i max(nh.d, 0)^2 of
+ * each segment: L_ray = sum_k T_k alpha_k c_k.  So, as in the colour adjoint,
+ * dL/dx_k (x = sigma l) = T_{k+1} c_k - S_k with S_k the part of the sum
+ * behind segment k, routed to the segment ends; and c_k moves with the unit
+ * normal: dc/dnh = 2 wn max(nh.d, 0) d.  grad [n][NPAR] is overwritten;
+ * contributions are summed in pixel order.
+ */
+int orc_contrib_grad(const orc_scene *s, const orc_cands *cd, const orc_camera *cam, int64_t npix, const int32_t *pix,
+                     const double *ws, const double *wn, double *grad, int nthreads) {
+    clist *lists = calloc((size_t)npix, sizeof(clist));
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+#endif
+    {
+        orc_seg *buf = NULL;
+        int64_t cap = 0;
+        double *alpha = NULL, *Tin = NULL, *cv = NULL;
+        int64_t acap = 0;
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+        for (int64_t k = 0; k < npix; k++) {
+            double u, v, o[3], d[3];
+            pixel_of(cam, k, pix, &u, &v);
+            if (!orc_ray(cam, u, v, o, d)) continue;
+            int64_t n = ray_segments(s, cd, o, d, &buf, &cap);
+            if (n > acap) {
+                acap = n;
+                alpha = realloc(alpha, (size_t)n * sizeof(double));
+                Tin = realloc(Tin, (size_t)n * sizeof(double));
+                cv = realloc(cv, (size_t)n * sizeof(double));
+            }
+            double T = 1.0;
+            for (int64_t q = 0; q < n; q++) {
+                int64_t i = buf[q].cell;
+                double nh[3], nl;
+                unit_normal(s, i, nh, &nl);
+                double nd = dot3(nh, d);
+                alpha[q] = 1.0 - exp(-(double)s->sigma[i] * (buf[q].tb - buf[q].ta));
+                Tin[q] = T;
+                cv[q] = ws[i] + wn[i] * (nd > 0.0 ? nd * nd : 0.0);
+                T *= 1.0 - alpha[q];
+            }
+            clist *L = &lists[k];
+            double S = 0.0;
+            for (int64_t q = n - 1; q >= 0; q--) {
+                int64_t i = buf[q].cell;
+                double sig = s->sigma[i];
+                double l = buf[q].tb - buf[q].ta;
+                double Tout = Tin[q] * (1.0 - alpha[q]);
+                double dLdx = Tout * cv[q] - S;
+                push(L, (int32_t)i, P_SIG, dLdx * l);
+                double gl = dLdx * sig;
+                route_t(s, i, buf[q].act_a, buf[q].ta, o, d, -gl, L);
+                route_t(s, i, buf[q].act_b, buf[q].tb, o, d, gl, L);
+                /* the normal-loss weight: dc/dnh = 2 wn (nh.d) d where nh.d > 0; n = |n| nh */
+                double nh[3], nl;
+                unit_normal(s, i, nh, &nl);
+                double nd = dot3(nh, d);
+                if (nd > 0.0 && wn[i] != 0.0) {
+                    double f = Tin[q] * alpha[q] * 2.0 * wn[i] * nd;
+                    double gnh[3] = {f * d[0], f * d[1], f * d[2]};
+                    double pr = dot3(nh, gnh);
+                    for (int r = 0; r < 3; r++) push(L, (int32_t)i, P_N + r, (gnh[r] - nh[r] * pr) / nl);
+                }
+                S += Tin[q] * alpha[q] * cv[q];
+            }
+        }
+        free(buf);
+        free(alpha);
+        free(Tin);
+        free(cv);
+    }
+    memset(grad, 0, (size_t)s->n * NPAR * sizeof(double));
+    for (int64_t k = 0; k < npix; k++) {
+        for (int64_t q = 0; q < lists[k].n; q++) {
+            orc_contrib *c = &lists[k].c[q];
+            grad[(int64_t)c->cell * NPAR + c->col] += c->v;
+        }
+        free(lists[k].c);
+    }
+    free(lists);
+    return 0;
+}

@@ -1064,3 +1064,61 @@ def test_spherical_voronoi_adjoint_matches_central_differences(seed):
             assert abs(fd - gflat[j]) <= 1e-5 * max(1.0, abs(fd)), (key, j, fd, gflat[j])
             checked += 1
     assert checked >= 50
+
+
+# ------------------------------------------------- contribution-loss adjoint
+
+def test_sparse_loss_of_an_isolated_cell_closed_form():
+    """One cell, one ray through its centre, face outside the ball: the
+    sparse contribution is alpha = 1 - exp(-sigma 2R), so its derivative in
+    sigma is 2R exp(-sigma 2R) and in R it is 2 sigma exp(-sigma 2R)."""
+    R, sig = 0.3, 2.0
+    sc = make_scene([0, 0, 0], 0.04, R, sig, [0.5, 0.5, 0.5])
+    cam = cam_at([-2.0, 0.0, 0.0], 1, 1, fov=1.0)
+    orc = oracle.Oracle(sc)
+    sp, nm = orc.contrib(cam)
+    assert sp[0] == pytest.approx(1 - math.exp(-sig * 2 * R), rel=1e-12)
+    G = orc.contrib_grad(cam, 1.0, 0.0)
+    assert G["sigma"][0] == pytest.approx(2 * R * math.exp(-sig * 2 * R), rel=1e-9)
+    assert G["R"][0] == pytest.approx(2 * sig * math.exp(-sig * 2 * R), rel=1e-6)
+
+
+@pytest.mark.parametrize("seed", [141, 142])
+def test_contribution_adjoint_matches_central_differences(seed):
+    """d/dtheta of sum_i (ws_i sparse_i + wn_i normal_i) equals FP64 central
+    differences of the contributions for every parameter group (the normal
+    weight reaches the normal through max(nh.d, 0)^2)."""
+    sc = fd_scene(seed)
+    rng = np.random.default_rng(seed + 9)
+    disp = rng.uniform(-0.03, 0.03, (sc.n, 4))
+    cam = cam_at([0.55, 0.25, 0.15], 10, 10, fov=40.0)
+    orc = oracle.Oracle(sc, disp=disp)
+    ws = rng.uniform(0.5, 1.5, sc.n)
+    wn = rng.uniform(0.5, 1.5, sc.n)
+    G = orc.contrib_grad(cam, ws, wn)
+
+    def loss():
+        sp, nm = orc.contrib(cam)
+        return float(ws @ sp + wn @ nm)
+
+    checked = 0
+    for key, arr in orc.params.items():
+        if key in ("rgb", "tex"):
+            assert np.abs(G[key]).max() == 0.0      # colours do not enter the contributions
+            continue
+        flat = arr.reshape(-1)
+        gflat = np.asarray(G[key]).reshape(-1)
+        nz = np.nonzero(np.abs(gflat) > 1e-8)[0]
+        assert nz.size > 0, key
+        for j in rng.choice(nz, size=min(6, nz.size), replace=False):
+            h = 1e-6 if key != "w" else 1e-7
+            old = flat[j]
+            flat[j] = old + h
+            lp = loss()
+            flat[j] = old - h
+            lm = loss()
+            flat[j] = old
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - gflat[j]) <= 1e-5 * max(1.0, abs(fd)), (key, j, fd, gflat[j])
+            checked += 1
+    assert checked >= 35
