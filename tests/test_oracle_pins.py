@@ -1122,3 +1122,24 @@ def test_contribution_adjoint_matches_central_differences(seed):
             assert abs(fd - gflat[j]) <= 1e-5 * max(1.0, abs(fd)), (key, j, fd, gflat[j])
             checked += 1
     assert checked >= 35
+
+
+def test_radical_plane_contains_the_intersection_circle():
+    """With R^2 = w (the sphere is the cell's bound), the radical plane of two
+    overlapping spheres contains their intersection circle: a ray through a
+    point of that circle leaves one cell and enters the other exactly there.
+    For disjoint spheres the plane lies outside both, so each cell's segment
+    is its full sphere chord."""
+    r0, r1, L = 1.0, 0.8, 1.5
+    x0 = (L * L + r0 * r0 - r1 * r1) / (2 * L)          # plane of the circle, from the sphere equations
+    rho = math.sqrt(r0 * r0 - x0 * x0)                   # circle radius
+    sc = make_scene([[0, 0, 0], [L, 0, 0]], [r0 * r0, r1 * r1], [r0, r1])
+    orc = oracle.Oracle(sc)
+    segs = seg_dict(orc.ray_segments([-3.0, rho, 0.0], [1.0, 0, 0]))
+    assert segs[0][1] == pytest.approx(3.0 + x0, abs=1e-12)
+    assert segs[1][0] == pytest.approx(3.0 + x0, abs=1e-12)
+    # disjoint: full chords, the plane between them cuts neither
+    sc2 = make_scene([[0, 0, 0], [2.5, 0, 0]], [r0 * r0, r1 * r1], [r0, r1])
+    segs2 = seg_dict(oracle.Oracle(sc2).ray_segments([-3.0, 0.3, 0.0], [1.0, 0, 0]))
+    assert segs2[0][1] - segs2[0][0] == pytest.approx(2 * math.sqrt(r0 * r0 - 0.09), abs=1e-12)
+    assert segs2[1][1] - segs2[1][0] == pytest.approx(2 * math.sqrt(r1 * r1 - 0.09), abs=1e-12)
