@@ -32,9 +32,9 @@ _lib = None
 
 KAPPA = 6.0          # soft-Voronoi sharpness on the face, in units of 1/R
 PARAM_COLS = {"pos": (0, 3), "w": (3, 1), "R": (4, 1), "sigma": (5, 1), "rgb": (6, 3),
-              "normal": (9, 3), "offset": (12, 1), "tex": (13, 12), "disp": (25, 4), "sites": (29, 8),
-              "sv": (37, 192)}
-NPAR = 229
+              "normal": (9, 3), "offset": (12, 1), "tex": (13, 12), "disp": (37, 4), "sites": (45, 8),
+              "sv": (61, 192)}
+NPAR = 445          # the site blocks have room for eight sites
 SV_LAMBDA = 10.0     # sharpness of the spherical-Voronoi site colours
 ACT_SPHERE, ACT_CAMERA, ACT_DIPOLE = -1, -2, -3
 
@@ -53,7 +53,7 @@ class _Scene(C.Structure):
     _fields_ = [("n", C.c_int64)] + [(k, C.POINTER(C.c_double)) for k in
                                      ("pos", "w", "R", "sigma", "rgb", "normal", "offset", "tex", "disp")] + \
                [("kappa_disp", C.c_double), ("sites", C.POINTER(C.c_double)), ("sv", C.POINTER(C.c_double)),
-                ("sv_lambda", C.c_double)]
+                ("sv_lambda", C.c_double), ("nsite", C.c_int32)]
 
 
 class _Camera(C.Structure):
@@ -155,18 +155,23 @@ class Oracle:
         self.nthreads = int(nthreads)
         self._arrs = {k: np.ascontiguousarray(np.asarray(getattr(scene, k), np.float64))
                       for k in ("pos", "w", "R", "sigma", "rgb", "normal", "offset", "tex")}
+        # detail sites per face, from the texture's width: 4 (tex [N,12]) or 8 (tex [N,24])
+        ns = self._arrs["tex"].shape[1] // 3 if self._arrs["tex"].ndim == 2 else 4
+        if ns not in (4, 8):
+            raise ValueError("tex must hold 4 or 8 RGB sites per cell")
+        self.nsite = ns
         if disp is None:
             disp = getattr(scene, "disp", None)
         if disp is not None:
-            self._arrs["disp"] = np.ascontiguousarray(np.asarray(disp, np.float64).reshape(-1, 4))
+            self._arrs["disp"] = np.ascontiguousarray(np.asarray(disp, np.float64).reshape(-1, ns))
         if sites is None:
             sites = getattr(scene, "sites", None)
         if sites is not None:
-            self._arrs["sites"] = np.ascontiguousarray(np.asarray(sites, np.float64).reshape(-1, 4, 2))
+            self._arrs["sites"] = np.ascontiguousarray(np.asarray(sites, np.float64).reshape(-1, ns, 2))
         if sv is None:
             sv = getattr(scene, "sv", None)
         if sv is not None:
-            self._arrs["sv"] = np.ascontiguousarray(np.asarray(sv, np.float64).reshape(-1, 4, 8, 6))
+            self._arrs["sv"] = np.ascontiguousarray(np.asarray(sv, np.float64).reshape(-1, ns, 8, 6))
         self.params = self._arrs
         self.n = int(self._arrs["pos"].shape[0])
         s = _Scene()
@@ -175,6 +180,7 @@ class Oracle:
             setattr(s, k, _ptr(a, C.c_double))
         s.kappa_disp = self.kappa
         s.sv_lambda = float(sv_lambda)
+        s.nsite = ns
         self._s = s
         self._cands = None      # (beg, end, idx) arrays, kept alive
         self._cs = None
@@ -332,14 +338,19 @@ class Oracle:
 
     def _split_grad(self, g) -> dict:
         out = {}
+        per_site = {"tex": 3, "disp": 1, "sites": 2, "sv": 48}
         for k, (c0, w) in PARAM_COLS.items():
             if k in ("disp", "sites", "sv") and k not in self._arrs:
                 continue
+            if k in per_site:
+                w = per_site[k] * self.nsite
             out[k] = g[:, c0:c0 + w] if w > 1 else g[:, c0].copy()
             if k == "sites":
-                out[k] = out[k].reshape(-1, 4, 2)
+                out[k] = out[k].reshape(-1, self.nsite, 2)
             if k == "sv":
-                out[k] = out[k].reshape(-1, 4, 8, 6)
+                out[k] = out[k].reshape(-1, self.nsite, 8, 6)
+            if k == "disp" and self.nsite != 4:
+                out[k] = out[k].reshape(-1, self.nsite)
         return out
 
     def render_grad(self, cam, dL_dC, dL_dT, pix=None) -> dict:

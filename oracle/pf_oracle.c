@@ -51,18 +51,21 @@ typedef struct {
     int64_t n;
     const double *pos, *w, *R, *sigma, *rgb, *normal, *offset, *tex;
     /* optional (NULL: none): displacement of the face at the four texture
-     * sites, [n][4] (Eq. svdisp), with soft-Voronoi sharpness kappa_disp */
+     * sites, [n][nsite] (Eq. svdisp), with soft-Voronoi sharpness kappa_disp */
     const double *disp;
     double kappa_disp;
     /* optional (NULL: the fixed sites (+-1/3, +-1/3)): positions of the four
-     * texture / detail sites on the face, [n][4][2], in units of R, in the
+     * texture / detail sites on the face, [n][nsite][2], in units of R, in the
      * site order of tex and disp (Sec. 3.4: learnable detail sites) */
     const double *sites;
     /* optional (NULL: the constant site colours tex): view-dependent site
-     * colours, a spherical-Voronoi function per site (Sec. 3.4): [n][4][8][6],
+     * colours, a spherical-Voronoi function per site (Sec. 3.4): [n][nsite][8][6],
      * per site eight (axis xyz, rgb); sharpness sv_lambda */
     const double *sv;
     double sv_lambda;
+    /* detail sites per face: 4 (also when 0) or 8; tex is [n][3 nsite], and
+     * disp, sites and sv have nsite sites per cell */
+    int32_t nsite;
 } orc_scene;
 
 /* model 0: pinhole.  model 1: equidistant fisheye (non-pinhole rasterization,
@@ -269,10 +272,22 @@ void orc_onb(const double *n, double *e1, double *e2) { onb(n, e1, e2, NULL, NUL
 /* the four texture sites, in units of R on the face, site-major */
 static const double SITE[4][2] = {{-1.0 / 3.0, -1.0 / 3.0}, {1.0 / 3.0, -1.0 / 3.0}, {-1.0 / 3.0, 1.0 / 3.0}, {1.0 / 3.0, 1.0 / 3.0}};
 
+/* eight fixed sites: the 3 x 3 grid of step 1/3 without its centre, row by row */
+static const double SITE8[8][2] = {{-1.0 / 3.0, -1.0 / 3.0}, {0.0, -1.0 / 3.0}, {1.0 / 3.0, -1.0 / 3.0},
+                                   {-1.0 / 3.0, 0.0},        {1.0 / 3.0, 0.0},  {-1.0 / 3.0, 1.0 / 3.0},
+                                   {0.0, 1.0 / 3.0},         {1.0 / 3.0, 1.0 / 3.0}};
+enum { MAXS = 8 };
+
+static int nsites(const orc_scene *s) { return s->nsite == 8 ? 8 : 4; }
+
 /* site k of cell i: the scene's learned position, else the fixed one */
-static double site_x(const orc_scene *s, int64_t i, int k) { return s->sites ? s->sites[8 * i + 2 * k] : SITE[k][0]; }
+static double site_x(const orc_scene *s, int64_t i, int k) {
+    const int ns = nsites(s);
+    return s->sites ? s->sites[2 * ns * i + 2 * k] : (ns == 8 ? SITE8[k][0] : SITE[k][0]);
+}
 static double site_y(const orc_scene *s, int64_t i, int k) {
-    return s->sites ? s->sites[8 * i + 2 * k + 1] : SITE[k][1];
+    const int ns = nsites(s);
+    return s->sites ? s->sites[2 * ns * i + 2 * k + 1] : (ns == 8 ? SITE8[k][1] : SITE[k][1]);
 }
 
 /*
@@ -289,9 +304,10 @@ static double face_disp(const orc_scene *s, int64_t i, const double *o, const do
     double nh[3], nl, p[3], m[3], y[3], e1[3], e2[3];
     unit_normal(s, i, nh, &nl);
     double den = dot3(nh, d);
+    const int ns = nsites(s);
     if (!s->disp || den == 0.0) {
         if (W)
-            for (int k = 0; k < 4; k++) W[k] = 0.0;
+            for (int k = 0; k < ns; k++) W[k] = 0.0;
         if (tbar) *tbar = 0.0;
         return 0.0;
     }
@@ -302,21 +318,21 @@ static double face_disp(const orc_scene *s, int64_t i, const double *o, const do
     onb(nh, e1, e2, NULL, NULL);
     double R = s->R[i];
     double uu[2] = {dot3(e1, y) / R, dot3(e2, y) / R};
-    double lg[4], mx = -INFINITY, Wk[4], Z = 0.0, delta = 0.0;
-    for (int k = 0; k < 4; k++) {
+    double lg[MAXS], mx = -INFINITY, Wk[MAXS], Z = 0.0, delta = 0.0;
+    for (int k = 0; k < ns; k++) {
         double dx = uu[0] - site_x(s, i, k), dy = uu[1] - site_y(s, i, k);
         lg[k] = -s->kappa_disp * sqrt(dx * dx + dy * dy);
         if (lg[k] > mx) mx = lg[k];
     }
-    for (int k = 0; k < 4; k++) {
+    for (int k = 0; k < ns; k++) {
         Wk[k] = exp(lg[k] - mx);
         Z += Wk[k];
     }
-    for (int k = 0; k < 4; k++) {
+    for (int k = 0; k < ns; k++) {
         Wk[k] /= Z;
-        delta += Wk[k] * s->disp[4 * i + k];
+        delta += Wk[k] * s->disp[(int64_t)ns * i + k];
     }
-    if (W) memcpy(W, Wk, sizeof Wk);
+    if (W) memcpy(W, Wk, sizeof(double) * (size_t)ns);
     if (u) memcpy(u, uu, sizeof uu);
     if (tbar) *tbar = tb;
     return delta;
@@ -330,7 +346,7 @@ static double face_disp(const orc_scene *s, int64_t i, const double *o, const do
  * P (optional) receives the eight weights.
  */
 static void sv_colour(const orc_scene *s, int64_t i, int k, const double *d, double *c, double *P) {
-    const double *q = s->sv + (((int64_t)i * 4 + k) * 8) * 6;
+    const double *q = s->sv + (((int64_t)i * nsites(s) + k) * 8) * 6;
     double lg[8], mx = -INFINITY, Z = 0.0;
     for (int j = 0; j < 8; j++) {
         const double *a = q + 6 * j;
@@ -363,31 +379,32 @@ static void cell_colour(const orc_scene *s, int64_t i, const double *o, const do
     onb(nh, e1, e2, NULL, NULL);
     double R = s->R[i];
     double u[2] = {dot3(e1, y) / R, dot3(e2, y) / R};
-    double lg[4], mx = -INFINITY;
-    for (int k = 0; k < 4; k++) {
+    const int ns = nsites(s);
+    double lg[MAXS], mx = -INFINITY;
+    for (int k = 0; k < ns; k++) {
         double dx = u[0] - site_x(s, i, k), dy = u[1] - site_y(s, i, k);
         lg[k] = -kappa * sqrt(dx * dx + dy * dy);
         if (lg[k] > mx) mx = lg[k];
     }
-    double W[4], Z = 0.0;
-    for (int k = 0; k < 4; k++) {
+    double W[MAXS], Z = 0.0;
+    for (int k = 0; k < ns; k++) {
         W[k] = exp(lg[k] - mx);
         Z += W[k];
     }
-    for (int k = 0; k < 4; k++) W[k] /= Z;
-    double ck[4][3];
-    for (int k = 0; k < 4; k++) {
+    for (int k = 0; k < ns; k++) W[k] /= Z;
+    double ck[MAXS][3];
+    for (int k = 0; k < ns; k++) {
         if (s->sv)
             sv_colour(s, i, k, d, ck[k], NULL);
         else
-            for (int ch = 0; ch < 3; ch++) ck[k][ch] = (double)s->tex[12 * i + 3 * k + ch];
+            for (int ch = 0; ch < 3; ch++) ck[k][ch] = (double)s->tex[3 * ns * i + 3 * k + ch];
     }
     for (int ch = 0; ch < 3; ch++) {
         double v = s->rgb[3 * i + ch];
-        for (int k = 0; k < 4; k++) v += W[k] * ck[k][ch];
+        for (int k = 0; k < ns; k++) v += W[k] * ck[k][ch];
         col[ch] = v;
     }
-    if (Wout) memcpy(Wout, W, sizeof W);
+    if (Wout) memcpy(Wout, W, sizeof(double) * (size_t)ns);
     if (uout) memcpy(uout, u, sizeof u);
     if (ts_out) *ts_out = ts;
 }
@@ -601,8 +618,10 @@ int orc_hit_cells(const orc_scene *s, const orc_camera *cam, int64_t npix, const
  * Parameter columns (25 per cell): pos 0-2, w 3, R 4, sigma 5, rgb 6-8,
  * normal 9-11, offset 12, tex 13-24.
  */
-enum { P_POS = 0, P_W = 3, P_R = 4, P_SIG = 5, P_RGB = 6, P_N = 9, P_OFF = 12, P_TEX = 13, P_DISP = 25, P_SITE = 29,
-       P_SV = 37, NPAR = 229 };
+/* gradient columns; the site blocks have room for eight sites (tex 24, disp 8,
+ * sites 16, sv 384), a four-site scene uses the first half of each */
+enum { P_POS = 0, P_W = 3, P_R = 4, P_SIG = 5, P_RGB = 6, P_N = 9, P_OFF = 12, P_TEX = 13, P_DISP = 37, P_SITE = 45,
+       P_SV = 61, NPAR = 445 };
 
 typedef struct {
     int32_t cell, col;
@@ -648,17 +667,17 @@ static void route_face(const orc_scene *s, int64_t i, double t, const double *o,
     }
     push(L, (int32_t)i, P_OFF, g / nd);
     if (with_disp && s->disp && nd != 0.0) {
-        double W[4], u[2], tb;
+        double W[MAXS], u[2], tb;
         double delta = face_disp(s, i, o, d, W, u, &tb);
         double gd = g / nd; /* dL/ddelta */
         double gu[2] = {0.0, 0.0};
-        for (int k = 0; k < 4; k++) {
+        for (int k = 0; k < nsites(s); k++) {
             push(L, (int32_t)i, P_DISP + k, gd * W[k]);
             /* d delta / d u = sum_k W_k (disp_k - delta) d lg_k / du,  lg_k = -kappa |u - s_k| */
             double dx = u[0] - site_x(s, i, k), dy = u[1] - site_y(s, i, k);
             double rr = sqrt(dx * dx + dy * dy);
             if (rr > 0.0) {
-                double c = gd * W[k] * (s->disp[4 * i + k] - delta) * (-s->kappa_disp) / rr;
+                double c = gd * W[k] * (s->disp[(int64_t)nsites(s) * i + k] - delta) * (-s->kappa_disp) / rr;
                 gu[0] += c * dx;
                 gu[1] += c * dy;
                 /* the logit depends on u - s_k: the site moves opposite to u */
@@ -785,23 +804,24 @@ int orc_render_grad(const orc_scene *s, const orc_cands *cd, const orc_camera *c
                 /* colour: dL/dc = T alpha gC */
                 double wc = Tin[q] * alpha[q];
                 double gc[3] = {wc * gC[0], wc * gC[1], wc * gC[2]};
-                double W[4], uu[2], ts;
+                double W[MAXS], uu[2], ts;
+                const int ns = nsites(s);
                 double cc[3];
                 cell_colour(s, i, o, d, &buf[q], kappa, cc, W, uu, &ts);
                 for (int ch = 0; ch < 3; ch++) push(L, (int32_t)i, P_RGB + ch, gc[ch]);
                 /* site colours: constant (tex), or view dependent (spherical Voronoi) */
-                double gW[4], sW = 0.0;
-                for (int kk = 0; kk < 4; kk++) {
+                double gW[MAXS], sW = 0.0;
+                for (int kk = 0; kk < ns; kk++) {
                     gW[kk] = 0.0;
                     if (!s->sv) {
                         for (int ch = 0; ch < 3; ch++) {
                             push(L, (int32_t)i, P_TEX + 3 * kk + ch, W[kk] * gc[ch]);
-                            gW[kk] += (double)s->tex[12 * i + 3 * kk + ch] * gc[ch];
+                            gW[kk] += (double)s->tex[3 * ns * i + 3 * kk + ch] * gc[ch];
                         }
                     } else {
                         /* c_k = sum_j P_j c_j, P = softmax(lambda a_j.wo / |a_j|), wo = -d */
                         double ck[3], P[8], gP[8], sP = 0.0;
-                        const double *qv = s->sv + (((int64_t)i * 4 + kk) * 8) * 6;
+                        const double *qv = s->sv + (((int64_t)i * ns + kk) * 8) * 6;
                         const int base = P_SV + kk * 48;
                         sv_colour(s, i, kk, d, ck, P);
                         for (int ch = 0; ch < 3; ch++) gW[kk] += ck[ch] * gc[ch];
@@ -828,7 +848,7 @@ int orc_render_grad(const orc_scene *s, const orc_cands *cd, const orc_camera *c
                     sW += W[kk] * gW[kk];
                 }
                 double gu[2] = {0.0, 0.0};
-                for (int kk = 0; kk < 4; kk++) {
+                for (int kk = 0; kk < ns; kk++) {
                     double glog = W[kk] * (gW[kk] - sW);          /* dL/dlogit */
                     double dx = uu[0] - site_x(s, i, kk), dy = uu[1] - site_y(s, i, kk);
                     double r = sqrt(dx * dx + dy * dy);

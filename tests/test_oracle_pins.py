@@ -1143,3 +1143,112 @@ def test_radical_plane_contains_the_intersection_circle():
     segs2 = seg_dict(oracle.Oracle(sc2).ray_segments([-3.0, 0.3, 0.0], [1.0, 0, 0]))
     assert segs2[0][1] - segs2[0][0] == pytest.approx(2 * math.sqrt(r0 * r0 - 0.09), abs=1e-12)
     assert segs2[1][1] - segs2[1][0] == pytest.approx(2 * math.sqrt(r1 * r1 - 0.09), abs=1e-12)
+
+
+# --------------------------------------------------- eight detail sites
+
+SITE8 = np.array([[-1, -1], [0, -1], [1, -1], [-1, 0], [1, 0], [-1, 1], [0, 1], [1, 1]], np.float64) / 3.0
+
+
+def eight_site_scene(sc, tex8):
+    s8 = sc.copy()
+    s8.tex = tex8
+    return s8
+
+
+def test_eight_sites_with_duplicated_positions_reduce_to_four():
+    """Eight detail sites (the paper's configuration) whose second four repeat
+    the first four's positions, colours and displacements: each pair weighs
+    what the single site weighed, so image and gradients equal the four-site
+    scene's (the pairs' gradients summing to the single site's)."""
+    rng = np.random.default_rng(51)
+    sc = cluster_scene(rng, n=9, spread=0.12, r=(0.06, 0.12), tex_std=0.2)
+    sites4 = default_sites(sc.n) + rng.uniform(-0.1, 0.1, (sc.n, 4, 2))
+    disp4 = rng.uniform(-0.03, 0.03, (sc.n, 4))
+    sc8 = eight_site_scene(sc, np.concatenate([sc.tex, sc.tex], 1))
+    o4 = oracle.Oracle(sc, disp=disp4, sites=sites4)
+    o8 = oracle.Oracle(sc8, disp=np.concatenate([disp4, disp4], 1), sites=np.concatenate([sites4, sites4], 1))
+    assert o8.nsite == 8
+    cam = cam_at([0.55, 0.25, 0.15], 12, 10, fov=40.0)
+    c4, T4 = o4.render(cam)
+    c8, T8 = o8.render(cam)
+    np.testing.assert_allclose(c8, c4, atol=1e-12)
+    np.testing.assert_allclose(T8, T4, atol=1e-13)
+    npix = cam.width * cam.height
+    gC = rng.normal(size=(npix, 3))
+    gT = rng.normal(size=npix)
+    G4 = o4.render_grad(cam, gC, gT)
+    G8 = o8.render_grad(cam, gC, gT)
+    for k in ("pos", "w", "R", "sigma", "rgb", "normal", "offset"):
+        np.testing.assert_allclose(G8[k], G4[k], atol=1e-9, err_msg=k)
+    np.testing.assert_allclose(G8["tex"][:, :12] + G8["tex"][:, 12:], G4["tex"], atol=1e-9)
+    np.testing.assert_allclose(G8["disp"][:, :4] + G8["disp"][:, 4:], G4["disp"], atol=1e-9)
+    np.testing.assert_allclose(G8["sites"][:, :4] + G8["sites"][:, 4:], G4["sites"], atol=1e-9)
+
+
+def test_eight_fixed_sites_and_a_symmetric_ring():
+    """The fixed eight sites are the 3 x 3 grid of step R/3 without its
+    centre (explicit positions give the same image); eight sites on a circle
+    around the ray's crossing weigh 1/8 each: the colour is the base plus the
+    mean site colour and the face moves by the mean displacement."""
+    rng = np.random.default_rng(52)
+    sc = cluster_scene(rng, n=6, spread=0.1, r=(0.06, 0.12), tex_std=0.2)
+    sc8 = eight_site_scene(sc, rng.normal(0, 0.1, (sc.n, 24)))
+    cam = cam_at([0.5, 0.2, 0.1], 8, 8, fov=40.0)
+    a = oracle.Oracle(sc8)
+    b = oracle.Oracle(sc8, sites=np.tile(SITE8, (sc.n, 1, 1)))
+    ca, Ta = a.render(cam)
+    cb, Tb = b.render(cam)
+    assert np.array_equal(ca, cb) and np.array_equal(Ta, Tb)
+    R, sig, off = 0.5, 2.0, 0.1
+    tex = rng.uniform(-0.2, 0.2, 24)
+    disp = rng.uniform(-0.03, 0.03, (1, 8))
+    one = make_scene([0, 0, 0], 0.04, R, sig, [0.2, 0.3, 0.4], normal=[0, 0, 1], offset=off)
+    one = eight_site_scene(one, tex[None])
+    x0, y0 = 0.1, 0.05
+    ang = np.arange(8) * (2 * np.pi / 8) + 0.3
+    ring = (np.array([x0, y0]) / R + 0.25 * np.stack([np.cos(ang), np.sin(ang)], 1))[None]
+    orc = oracle.Oracle(one, disp=disp, sites=ring)
+    c, T = orc.render_rays(np.array([[x0, y0, -3.0]]), np.array([[0.0, 0.0, 1.0]]))
+    length = (off + disp.mean()) + math.sqrt(R * R - x0 * x0 - y0 * y0)
+    alpha = 1 - math.exp(-sig * length)
+    assert T[0] == pytest.approx(1 - alpha, rel=1e-12)
+    np.testing.assert_allclose(c[0], alpha * (np.array([0.2, 0.3, 0.4]) + tex.reshape(8, 3).mean(0)), atol=1e-12)
+
+
+def test_eight_site_adjoint_matches_central_differences():
+    sc = fd_scene(153)
+    rng = np.random.default_rng(154)
+    sc8 = eight_site_scene(sc, rng.normal(0, 0.2, (sc.n, 24)))
+    disp = rng.uniform(-0.04, 0.04, (sc.n, 8))
+    sites = np.tile(SITE8, (sc.n, 1, 1)) + rng.uniform(-0.1, 0.1, (sc.n, 8, 2))
+    cam = cam_at([0.55, 0.25, 0.15], 10, 10, fov=40.0)
+    orc = oracle.Oracle(sc8, disp=disp, sites=sites)
+    npix = cam.width * cam.height
+    gC = rng.normal(size=(npix, 3))
+    gT = rng.normal(size=npix)
+    G = orc.render_grad(cam, gC, gT)
+
+    def loss():
+        c, T = orc.render(cam)
+        return float(np.sum(c * gC) + np.sum(T * gT))
+
+    checked = 0
+    for key, arr in orc.params.items():
+        flat = arr.reshape(-1)
+        gflat = np.asarray(G[key]).reshape(-1)
+        assert gflat.size == flat.size, key
+        nz = np.nonzero(np.abs(gflat) > 1e-8)[0]
+        assert nz.size > 0, key
+        for j in rng.choice(nz, size=min(6, nz.size), replace=False):
+            h = 1e-6 if key != "w" else 1e-7
+            old = flat[j]
+            flat[j] = old + h
+            lp = loss()
+            flat[j] = old - h
+            lm = loss()
+            flat[j] = old
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - gflat[j]) <= 1e-5 * max(1.0, abs(fd)), (key, j, fd, gflat[j])
+            checked += 1
+    assert checked >= 50
