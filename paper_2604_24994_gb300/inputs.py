@@ -53,6 +53,11 @@ class Scene:
     tex: np.ndarray
     nbr: np.ndarray
     n_clipped: int = 0          # cells whose R was clipped for list completeness
+    # optional extended face model: displacement [N,4], learned site positions
+    # [N,4,2] (units of R), view-dependent site colours [N,4,8,6]
+    disp: np.ndarray | None = None
+    sites: np.ndarray | None = None
+    sv: np.ndarray | None = None
 
     @property
     def n(self) -> int:
@@ -72,6 +77,16 @@ class Scene:
                                  if isinstance(getattr(self, f.name), np.ndarray)
                                  else getattr(self, f.name))
                         for f in dataclasses.fields(self)})
+
+    FORMAT = "pf-scene-1"
+
+    def save(self, path: str) -> None:
+        """Write the scene to one uncompressed .npz file (the binary scene
+        format: every array under its field name, plus `format` and
+        `n_clipped`); `load_scene` reads it back unchanged."""
+        arrays = {f.name: getattr(self, f.name) for f in dataclasses.fields(self)
+                  if isinstance(getattr(self, f.name), np.ndarray)}
+        np.savez(path, format=np.array(self.FORMAT), n_clipped=np.array(self.n_clipped, np.int64), **arrays)
 
     def subset_params(self, idx) -> "Scene":
         """A scene holding only cells `idx` (neighbour lists dropped)."""
@@ -111,6 +126,15 @@ class Camera:
     @property
     def n_tiles(self) -> int:
         return self.tiles_x * self.tiles_y
+
+
+def load_scene(path: str) -> Scene:
+    """Read a scene written by Scene.save."""
+    with np.load(path, allow_pickle=False) as z:
+        if str(z["format"]) != Scene.FORMAT:
+            raise ValueError(f"{path}: not a {Scene.FORMAT} file")
+        kw = {f.name: z[f.name] for f in dataclasses.fields(Scene) if f.name in z.files and f.name != "n_clipped"}
+        return Scene(n_clipped=int(z["n_clipped"]), **kw)
 
 
 def look_at(origin, width: int, height: int, fov_y_deg: float = 60.0,
