@@ -429,7 +429,7 @@ static int64_t ray_segments(const orc_scene *s, const orc_cands *cd, const doubl
         }
         (*buf)[n++] = sg;
     }
-    qsort(*buf, (size_t)n, sizeof(orc_seg), cmp_seg);
+    if (n > 1) qsort(*buf, (size_t)n, sizeof(orc_seg), cmp_seg);
     return n;
 }
 
