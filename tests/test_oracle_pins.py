@@ -1252,3 +1252,23 @@ def test_eight_site_adjoint_matches_central_differences():
             assert abs(fd - gflat[j]) <= 1e-5 * max(1.0, abs(fd)), (key, j, fd, gflat[j])
             checked += 1
     assert checked >= 50
+
+
+def test_displacement_beyond_the_ball_limits():
+    """The dipole limits with displacement: faces pushed by +2R everywhere
+    lie outside every ball, so the cells render as undipoled cells; pulled by
+    -2R the dense halves miss the balls and nothing is rendered."""
+    rng = np.random.default_rng(61)
+    sc = cluster_scene(rng, n=9, spread=0.12, r=(0.06, 0.12), tex_std=0.2)
+    sc.offset = np.zeros(sc.n)
+    cam = cam_at([0.55, 0.25, 0.15], 10, 8, fov=40.0)
+    up = oracle.Oracle(sc, disp=np.repeat(2 * sc.R[:, None], 4, 1))
+    undipoled = sc.copy()
+    undipoled.offset = 10 * sc.R
+    c1, T1 = up.render(cam)
+    c2, T2 = oracle.Oracle(undipoled).render(cam)
+    np.testing.assert_allclose(c1, c2, atol=1e-12)
+    np.testing.assert_allclose(T1, T2, atol=1e-13)
+    down = oracle.Oracle(sc, disp=np.repeat(-2 * sc.R[:, None], 4, 1))
+    c3, T3 = down.render(cam)
+    assert np.all(T3 == 1.0) and np.all(c3 == 0.0)
