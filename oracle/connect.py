@@ -46,3 +46,28 @@ def connect(pos, R, nbr):
                 gpos[i] += 2 * o * a / d
                 gpos[j] -= 2 * o * a / d
     return loss, gpos, gR
+
+
+def cech_lists(pos, R):
+    """The Cech adjacency of the bounding spheres (Sec. 3.3): for each cell,
+    every other cell whose sphere overlaps its own, |p_i - p_j| < R_i + R_j,
+    by brute force over all pairs (lists padded with -1)."""
+    pos = np.asarray(pos, np.float64)
+    R = np.asarray(R, np.float64)
+    n = pos.shape[0]
+    rows = []
+    for i in range(n):
+        d = np.sqrt(((pos - pos[i]) ** 2).sum(1))
+        js = np.nonzero((d < R[i] + R) & (np.arange(n) != i))[0]
+        rows.append(js)
+    k = max((len(r) for r in rows), default=0)
+    out = np.full((n, k), -1, np.int64)
+    for i, r in enumerate(rows):
+        out[i, :len(r)] = r
+    return out
+
+
+def connect_cech(pos, R):
+    """L_connect over the exact Cech adjacency (the paper's definition):
+    `connect` applied to `cech_lists`."""
+    return connect(pos, R, cech_lists(pos, R))

@@ -1272,3 +1272,21 @@ def test_displacement_beyond_the_ball_limits():
     down = oracle.Oracle(sc, disp=np.repeat(-2 * sc.R[:, None], 4, 1))
     c3, T3 = down.render(cam)
     assert np.all(T3 == 1.0) and np.all(c3 == 0.0)
+
+
+def test_connect_over_the_cech_graph_and_over_lists():
+    """L_connect is defined over the Cech graph (all overlapping bounding
+    spheres).  Where the neighbour lists hold every overlapping pair, the
+    list-based loss equals it; where they do not (K smaller than the number
+    of overlaps), the list-based loss is smaller, never larger."""
+    from oracle.connect import cech_lists, connect, connect_cech
+    from paper_2604_24994_gb300 import inputs
+    sc = inputs.uniform_scene(600, seed=9, r_range=(0.05, 0.12), K=8, box=0.5)
+    full, _, _ = connect_cech(sc.pos, sc.R)
+    lists, _, _ = connect(sc.pos, sc.R, sc.nbr)
+    assert np.all(lists <= full + 1e-15)
+    cl = cech_lists(sc.pos, sc.R)
+    complete = np.array([set(c[c >= 0]) <= set(b[b >= 0]) for c, b in zip(cl, sc.nbr)])
+    assert complete.any() and (~complete).any()       # this scene has both kinds of cells
+    np.testing.assert_allclose(lists[complete], full[complete], rtol=1e-12, atol=0)
+    assert np.all(lists[~complete] < full[~complete])
