@@ -1,8 +1,12 @@
 """GB300 (sm_103a) tile rasterizer for bounded power-diagram cells
 (Power Foam, arxiv 2604.24994): forward render, hand-written adjoint and a
-continuous-batching server behind a C ABI (include/powerfoam.h).
+continuous-batching server behind a C ABI (include/powerfoam.h), with
+pinhole and fisheye views, the optional face displacement, learned detail
+sites and view-dependent site colours, per-cell contributions, the
+connectivity loss, and GPU neighbour lists.
 
     from paper_2604_24994_gb300 import inputs, DeviceScene, Renderer, render
+    from paper_2604_24994_gb300 import build_neighbours, connect_loss
 """
 from . import inputs  # noqa: F401
 
