@@ -31,16 +31,26 @@ WORKLOAD = "capture-shaped scene, 1,000,000 cells (70% Gaussian mixture in the u
 
 WORKLOAD_SMALL = "profiling case: the same recipe at 400,000 cells, one 1280x720 view from (3,0,0)"
 
-# Algorithmic FP32 flops of the forward per counted event (FMA = 2, add /
-# mul / compare / sqrt / exp / reciprocal = 1), counted operation by
-# operation from the render kernel's source; the terms are listed beside
-# each constant.
-FLOPS_PER_CANDIDATE = 15        # cheap sphere test: m x d (9), |v|^2 (5), compare (1)
-FLOPS_PER_PASS = 107            # compensated m x d (51), D (7), tangent check (9), sqrt (1),
+# Algorithmic FP32 work of the forward per counted event, the per-unit
+# figures of the path's cost model: a candidate (a listed cell a pixel
+# examines) costs a sphere test of about 10 flops; a hit (a non-empty
+# segment) about 140: about 9 relevant radical planes x 6, the dipole face
+# 8, the soft-Voronoi texture about 60 and compositing 10.  The event counts
+# come from the render kernel's stats pass over the same frame.
+ALG_FLOPS_PER_CANDIDATE = 10
+ALG_FLOPS_PER_HIT = 140
+
+# The same frame counted operation by operation from the render kernel's
+# source (FMA = 2, add / mul / compare / sqrt / exp / reciprocal = 1),
+# reported beside the algorithmic figure: it includes the work this
+# implementation adds (compensated products, refinement checks, the planes
+# each ray needs on its own).
+IMPL_FLOPS_PER_CANDIDATE = 15   # cheap sphere test: m x d (9), |v|^2 (5), compare (1)
+IMPL_FLOPS_PER_PASS = 107       # compensated m x d (51), D (7), tangent check (9), sqrt (1),
                                 # q = d x v (9), m.d (5), camera end (2), face clip (14),
                                 # emptiness (1), refinement checks (8)
-FLOPS_PER_PLANE = 14            # q.a (5), g - q.a (1), d.a (5), sign test, divide, compare (3)
-FLOPS_PER_HIT = 92              # face point (6), face coordinates (10), site offsets (4),
+IMPL_FLOPS_PER_PLANE = 14       # q.a (5), g - q.a (1), d.a (5), sign test, divide, compare (3)
+IMPL_FLOPS_PER_HIT = 92         # face point (6), face coordinates (10), site offsets (4),
                                 # four sites x (|u - s| 3, sqrt, scale, exp, sum) (28),
                                 # normalise (5), colour (24), compositing (15)
 
@@ -140,6 +150,16 @@ def dist_env():
     return ws, rank, local
 
 
+def bench_config(workload: str, width: int, height: int, n_cells: int, n_nbr: int, ws: int = 1) -> dict:
+    """The workload description both arms print (the same keys and values)."""
+    return {"workload": WORKLOAD if workload == "full" else WORKLOAD_SMALL,
+            "resolution": f"{width}x{height}", "cells": n_cells, "neighbours": n_nbr,
+            "parallelism": f"replicas x{ws}",
+            "l2": "256 MiB buffer written between timed steps (not timed)",
+            "fwd_step": "pf_project + pf_bin_sort + pf_render_fwd (scene resident and prepared)",
+            "fwd_bwd_step": "pf_prepare + pf_project + pf_bin_sort + pf_render_fwd + L2 loss grad + pf_render_bwd"}
+
+
 def make_workload(rank: int = 0, small: bool = False):
     """The 1080p / 1M-cell capture workload, or (small=True) the same recipe
     at 400k cells and 1280x720 for profiler captures."""
@@ -178,14 +198,18 @@ def cpu_baseline(sc, cam, seconds: float = 15.0):
 
 
 def run_reference(args):
+    """The oracle as it stands on this host's cores: each step renders a
+    bounded sample (64 random pixels) of the benchmark frame; frames/s is
+    extrapolated from the time per pixel."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    sc, cam, _ = make_workload(0)
+    small = args.workload == "small"
+    sc, cam, _ = make_workload(0, small=small)
     import oracle
     orc = oracle.Oracle(sc)
     rng = np.random.default_rng(1)
-    per = []
+    per, step_s = [], []
     for step in range(args.warmup + args.steps):
         pix = np.stack([rng.integers(0, cam.width, 64), rng.integers(0, cam.height, 64)], 1).astype(np.int32)
         t0 = time.time()
@@ -194,15 +218,19 @@ def run_reference(args):
         dt = time.time() - t0
         if step >= args.warmup:
             per.append(dt / 64)
+            step_s.append(dt)
     per_px = float(np.mean(per))
     fps = 1.0 / (per_px * cam.width * cam.height)
+    sample = (f"each step 64 random pixels of the {cam.width}x{cam.height} frame (exact prune, OpenMP over "
+              f"pixels); frames/s extrapolated as 1 / (time per pixel x {cam.width * cam.height:,})")
     line = {"impl": "reference", "metric": METRIC, "value": fps, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_px * cam.width * cam.height * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(step_s)) * 1e3,
+            "ms_per_frame_extrapolated": per_px * cam.width * cam.height * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "parallelism": "replicas"},
+            "data": "synthetic",
+            "config": bench_config(args.workload, cam.width, cam.height, sc.n, sc.k, args.gpus),
             "cpu_baseline": {"value": fps, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": f"each step 64 random pixels of the 1920x1080 frame; frames/s "
-                                       f"extrapolated as 1 / (time per pixel x 2,073,600)"},
+                             "sample": sample},
             "e2e": {"value": fps, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -434,26 +462,24 @@ def run_ours(args):
 
     pk = peaks()
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
-    peak_tflops = 152 * 128 * 2 * sm_max * 1e6 / 1e12     # FP32 FMA lanes x 2 flops x clock
-    flops = (stats["candidates"] * FLOPS_PER_CANDIDATE + stats["sphere_pass"] * FLOPS_PER_PASS
-             + stats["planes"] * FLOPS_PER_PLANE + stats["hits"] * FLOPS_PER_HIT)
-    achieved = flops / (ms_render * 1e-3) / 1e12
+    n_sms = torch.cuda.get_device_properties(local).multi_processor_count
+    peak_tflops = n_sms * 128 * 2 * sm_max * 1e6 / 1e12   # FP32 FMA lanes x 2 flops x clock
+    alg_flops = stats["candidates"] * ALG_FLOPS_PER_CANDIDATE + stats["hits"] * ALG_FLOPS_PER_HIT
+    impl_flops = (stats["candidates"] * IMPL_FLOPS_PER_CANDIDATE + stats["sphere_pass"] * IMPL_FLOPS_PER_PASS
+                  + stats["planes"] * IMPL_FLOPS_PER_PLANE + stats["hits"] * IMPL_FLOPS_PER_HIT)
+    achieved = alg_flops / (ms_render * 1e-3) / 1e12
+    achieved_impl = impl_flops / (ms_render * 1e-3) / 1e12
     cpu = cpu_baseline(sc, cam, seconds=args.cpu_seconds) if args.cpu_seconds > 0 else None
     n_cells, n_nbr = ds.n, ds.k
     line = {
         "metric": METRIC, "value": ws * 1000.0 / ms_fwd, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
         "ms_per_step": ms_fwd, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 (FP64 geometry)", "data": "synthetic",
-        "config": {"workload": WORKLOAD if args.workload == "full" else WORKLOAD_SMALL,
-                   "resolution": f"{cam.width}x{cam.height}", "cells": n_cells, "neighbours": n_nbr,
-                   "instances": n_inst, "parallelism": f"replicas x{ws}",
-                   "l2": "256 MiB buffer written between timed steps (not timed)",
-                   "fwd_step": "pf_project + pf_bin_sort + pf_render_fwd (scene resident and prepared)",
-                   "fwd_bwd_step": "pf_prepare + pf_project + pf_bin_sort + pf_render_fwd + L2 loss grad + pf_render_bwd",
-                   "fisheye_step": "the forward step for a 180-degree equidistant fisheye of the same size and position",
-                   "displaced_step": "the forward step with every face displaced by up to 0.2 R at its four sites",
-                   "view_dependent_step": "the forward step with spherical-Voronoi site colours (8 axes per site)",
-                   "scene_generation_s": round(gen_s, 1)},
+        "config": bench_config(args.workload, cam.width, cam.height, n_cells, n_nbr, ws),
+        "instances": n_inst, "scene_generation_s": round(gen_s, 1),
+        "side_steps": {"fisheye_step": "the forward step for a 180-degree equidistant fisheye of the same size and position",
+                       "displaced_step": "the forward step with every face displaced by up to 0.2 R at its four sites",
+                       "view_dependent_step": "the forward step with spherical-Voronoi site colours (8 axes per site)"},
         "fwd_fps": ws * 1000.0 / ms_fwd, "fwd_bwd_fps": ws * 1000.0 / ms_train, "ms_fwd_bwd": ms_train,
         "ms_render_fwd_kernel": ms_render,
         "ms_render_fwd_contrib_kernel": ms_render_contrib,
@@ -467,7 +493,12 @@ def run_ours(args):
         "roofline": {"bound": "alu", "kernel": "render_fwd_kernel", "achieved": achieved, "peak": peak_tflops,
                      "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                      "traffic": measured_traffic() if args.workload == "full" else None,
-                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz (unit counts and max clock)"},
+                     "work": f"{ALG_FLOPS_PER_CANDIDATE} flops x {stats['candidates']} candidates + "
+                             f"{ALG_FLOPS_PER_HIT} flops x {stats['hits']} hits = {alg_flops:.4g} flops per launch",
+                     "peak_source": f"{n_sms} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz (unit counts and "
+                                    f"max clock; no FP32 figure is measured)",
+                     "implementation_count": {"flops": impl_flops, "achieved": achieved_impl,
+                                              "frac": achieved_impl / peak_tflops}},
         "e2e": {"value": ws * 1000.0 / ms_e2e, "unit": UNIT, "h2d_bytes_per_step": 184,
                 "d2h_bytes_per_step": r.plan.pixels * 16},
         "gpu_launches": K * kernels_fwd,
@@ -648,7 +679,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--workload", default="full", choices=["full", "small", "large"])
-    ap.add_argument("--serve-seconds", type=float, default=20.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-budget-gb", type=float, default=40.0)
     ap.add_argument("--no-serve", action="store_true")

@@ -331,27 +331,31 @@ void pf_serve_destroy(pf_server *srv);
  * Forward render of one small view WITHOUT a workspace and without any
  * device allocation (no cudaMalloc, cudaFree or allocating library call).
  * The paper has no counterpart: this exists for callers that cannot
- * allocate device memory (a host that owns the whole memory budget, a
- * real-time loop that forbids allocation, code running while a stream
- * capture is open).  The caller still passes the scene (device pointers),
- * the camera (host struct) and device outputs rgb [W*H,3], T [W*H],
- * last [W*H], exactly as for pf_render_fwd with a one-view plan; the
- * results are the same.
+ * allocate device memory (a host that has given its whole memory budget to
+ * another allocator, a real-time loop that forbids allocation).  The caller
+ * still passes the scene (device pointers), the camera (host struct) and
+ * device outputs rgb [W*H,3], T [W*H], last [W*H], exactly as for
+ * pf_render_fwd with a one-view plan; the results are the same.
  *
  * The scratch is one file-scope __device__ array of PF_STATIC_SCRATCH_BYTES
- * that every GPU loading the library keeps until the process exits.  Limits
- * (larger requests return PF_ERR_INVALID_ARG, or PF_ERR_CAPACITY when the
- * instance count is exceeded, with a message from pf_last_error_message):
- * at most PF_STATIC_MAX_CELLS cells, PF_STATIC_MAX_K neighbours, an image of
- * at most PF_STATIC_MAX_SIDE x PF_STATIC_MAX_SIDE pixels and
- * PF_STATIC_MAX_INSTANCES (cell, tile) pairs.
+ * that every GPU loading the library keeps until the process exits.  With
+ * CUDA's lazy module loading it is reserved inside the first call on a
+ * device, so that call commits device memory and can fail with
+ * out-of-memory (PF_ERR_CUDA): make it before giving the device's memory
+ * away.  Each call looks up the array's address on the current device
+ * (cudaGetSymbolAddress).  Limits (larger requests return
+ * PF_ERR_INVALID_ARG, or PF_ERR_CAPACITY when the instance count is
+ * exceeded, with a message from pf_last_error_message): at most
+ * PF_STATIC_MAX_CELLS cells, PF_STATIC_MAX_K neighbours, an image of at most
+ * PF_STATIC_MAX_SIDE x PF_STATIC_MAX_SIDE pixels and PF_STATIC_MAX_INSTANCES
+ * (cell, tile) pairs.
  *
- * The first call on a device looks up the array's address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
  * Every call reuses the same array and clears what must start at zero;
  * calls that overlap on the GPU (different streams or threads) race on it
  * and must be serialised by the caller.  The call synchronises `stream`
- * once, after binning, to check the instance count.
+ * once, after binning, to check the instance count; on a stream that is
+ * being captured into a CUDA graph it returns PF_ERR_INVALID_ARG without
+ * enqueuing anything.
  */
 #define PF_STATIC_MAX_CELLS 4096
 #define PF_STATIC_MAX_K 32

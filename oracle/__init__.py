@@ -427,24 +427,19 @@ def tile_lists(rect: np.ndarray, key: np.ndarray, tiles_x: int, tiles_y: int):
     """Per-tile cell lists from the CPU binning: for tile t, the cells whose
     rectangle covers it, sorted by (key, cell index).  Returns (start [T+1],
     cells [n_instances]) in CSR form."""
-    n = rect.shape[0]
     nt = tiles_x * tiles_y
-    tiles = []
-    cells = []
-    for i in range(n):
-        x0, y0, x1, y1 = rect[i]
-        if x0 > x1 or y0 > y1:
-            continue
-        ys, xs = np.mgrid[y0:y1 + 1, x0:x1 + 1]
-        t = (ys * tiles_x + xs).ravel()
-        tiles.append(t)
-        cells.append(np.full(t.size, i, np.int64))
-    if tiles:
-        tiles = np.concatenate(tiles)
-        cells = np.concatenate(cells)
-    else:
-        tiles = np.zeros(0, np.int64)
-        cells = np.zeros(0, np.int64)
+    rect = np.asarray(rect, np.int64)
+    x0, y0, x1, y1 = rect[:, 0], rect[:, 1], rect[:, 2], rect[:, 3]
+    live = np.nonzero((x0 <= x1) & (y0 <= y1))[0]
+    wd = (x1 - x0 + 1)[live]
+    ht = (y1 - y0 + 1)[live]
+    cnt = wd * ht
+    total = int(cnt.sum())
+    # every (cell, tile) pair of every rectangle, row by row
+    cells = np.repeat(live, cnt)
+    k = np.arange(total, dtype=np.int64) - np.repeat(np.cumsum(cnt) - cnt, cnt)
+    w_rep = np.repeat(wd, cnt)
+    tiles = (np.repeat(y0[live], cnt) + k // w_rep) * tiles_x + np.repeat(x0[live], cnt) + k % w_rep
     order = np.lexsort((cells, key[cells], tiles))
     tiles = tiles[order]
     cells = cells[order]

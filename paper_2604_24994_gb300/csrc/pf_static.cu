@@ -5,24 +5,30 @@
 //
 // Who needs this: code that must not allocate device memory at all, for
 // example a host that hands its whole memory budget to another allocator,
-// a real-time loop where an allocation (or the caching allocator growing)
-// is not allowed, or a caller in a context that forbids cudaMalloc (such as
-// an ongoing stream capture).  Such a caller still owns and passes its
-// scene, camera and output buffers.
+// or a real-time loop where an allocation (or the caching allocator
+// growing) is not allowed.  Such a caller still owns and passes its scene,
+// camera and output buffers.
 //
 // Costs and rules:
-//   - The array is PF_STATIC_SCRATCH_BYTES (8.5 MiB).  Every GPU that
-//     loads this library reserves it until the process exits.
-//   - The first call on a device looks up the array's device address with
-//     cudaGetSymbolAddress (host code cannot use the array's name as a
-//     device pointer).  Make that first call before any stream capture.
+//   - The array is PF_STATIC_SCRATCH_BYTES (8.5 MiB).  It is reserved on a
+//     device when the library's module is loaded there, which with CUDA's
+//     lazy module loading happens inside the first call on that device
+//     (its cudaGetSymbolAddress).  So the first call commits device memory
+//     and can fail with out-of-memory: make it before handing the device's
+//     memory to another allocator.  The array then stays until the process
+//     exits.
+//   - Host code cannot use the array's name as a device pointer: every call
+//     looks up its device address on the current device with
+//     cudaGetSymbolAddress (cheap once the module is loaded) and passes
+//     that address to the kernels.  Looking it up each time keeps the call
+//     correct after a cudaDeviceReset, which may place the array elsewhere.
 //   - All calls share the one array and it keeps the previous call's data.
 //     Everything that has to start at zero is cleared on every call.  Calls
 //     that overlap on the GPU (other streams, other threads) race on it:
 //     serialise them.
-//   - The call synchronises `stream` once (to check the instance count).
-#include <mutex>
-
+//   - The call synchronises `stream` once (to check the instance count),
+//     so it cannot run while `stream` is being captured into a CUDA graph;
+//     it returns PF_ERR_INVALID_ARG in that case without enqueuing work.
 #include "pf_internal.cuh"
 
 namespace pf {
@@ -31,26 +37,12 @@ constexpr size_t STATIC_SCRATCH_BYTES = PF_STATIC_SCRATCH_BYTES;
 
 static __device__ __align__(256) unsigned char g_static_scratch[STATIC_SCRATCH_BYTES];
 
-static std::mutex g_static_mu;
-static void *g_static_ptr[128];
-
-// Device address of the array on the current device (looked up once per device).
+// Device address of the array on the current device.
 static pf_status static_scratch(void **out) {
-    int dev = 0;
-    pf_status s = cuda_status(cudaGetDevice(&dev), "pf_render_fwd_static: cudaGetDevice");
+    void *p = nullptr;
+    pf_status s = cuda_status(cudaGetSymbolAddress(&p, g_static_scratch), "pf_render_fwd_static: cudaGetSymbolAddress");
     if (s) return s;
-    if (dev < 0 || dev >= 128) {
-        set_error("pf_render_fwd_static: device %d out of range", dev);
-        return PF_ERR_INVALID_ARG;
-    }
-    std::lock_guard<std::mutex> lk(g_static_mu);
-    if (!g_static_ptr[dev]) {
-        void *p = nullptr;
-        s = cuda_status(cudaGetSymbolAddress(&p, g_static_scratch), "pf_render_fwd_static: cudaGetSymbolAddress");
-        if (s) return s;
-        g_static_ptr[dev] = p;
-    }
-    *out = g_static_ptr[dev];
+    *out = p;
     return PF_OK;
 }
 
@@ -93,11 +85,19 @@ extern "C" pf_status pf_render_fwd_static(const pf_scene *scene, const pf_camera
         set_error("pf_render_fwd_static: layout %llu bytes exceeds the static scratch", (unsigned long long)p.L.total);
         return PF_ERR_CAPACITY;
     }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    pf_status s = cuda_status(cudaStreamIsCapturing(st, &cap), "pf_render_fwd_static: cudaStreamIsCapturing");
+    if (s) return s;
+    if (cap != cudaStreamCaptureStatusNone) {
+        set_error("pf_render_fwd_static: the stream is being captured; this call synchronises it and cannot be "
+                  "captured");
+        return PF_ERR_INVALID_ARG;
+    }
     void *base = nullptr;
-    pf_status s = static_scratch(&base);
+    s = static_scratch(&base);
     if (s) return s;
     WS w = p.ws(base);
-    cudaStream_t st = (cudaStream_t)stream;
     // the view constants: pageable copy, done before cudaMemcpyAsync returns
     s = cuda_status(cudaMemcpyAsync(w.views, &view_host, sizeof view_host, cudaMemcpyHostToDevice, st),
                     "pf_render_fwd_static: views");

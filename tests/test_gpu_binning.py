@@ -1,0 +1,131 @@
+"""Bit-exact binning where the tile lists are long: every per-tile sort path
+of pf_bin_sort (lists of at most 2048 entries sorted in 24 KB of shared
+memory, 2049-16384 in 192 KB by the persistent kernel, longer lists in
+global memory) against the CPU binning (oracle.bin + oracle.tile_lists),
+plus the render of those tiles against the FP64 oracle.
+
+The scene puts, for every pixel of two chosen tiles, a column of cells
+along the pixel's ray.  Each sphere projects to about 0.3 px around its
+pixel centre, so each cell lands in exactly one tile, and one tile lists
+20,480 cells, the other 6,144.  Weights are tied to the bound radii
+(w = R^2) and the balls are disjoint, so no radical plane cuts any ball
+(Sec. 3.2: with tied weights a plane cuts a ball only where the balls
+overlap) and empty neighbour lists are complete: the oracle, which clips
+against every site, renders the same cells."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_24994_gb300 import inputs
+from tests.gpu_util import assert_close_image, pixel_index
+from tests.oracle_util import f32, make_scene, random_dirs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2604_24994_gb300 import build
+    build.build()
+
+
+def column_scene(cam, tiles, per_column, seed=0):
+    rng = np.random.default_rng(seed)
+    ray = oracle.Oracle(make_scene(np.zeros((1, 3)), [0.0], [0.0])).ray
+    pos, R = [], []
+    for (tx, ty), m in zip(tiles, per_column):
+        for v in range(ty * 16, ty * 16 + 16):
+            for u in range(tx * 16, tx * 16 + 16):
+                o, d = ray(cam, u, v)
+                t = 2.0 * (1.0 + rng.uniform(0.0, 0.05))
+                for _ in range(m):
+                    r = 0.3 * t / cam.fy            # about 0.3 px at this distance
+                    pos.append(o + t * d)
+                    R.append(r)
+                    t += 2.2 * r                     # the next ball starts past this one
+    pos = np.array(pos)
+    R = np.array(R)
+    n = len(R)
+    sigma = np.exp(rng.normal(0.0, 1.0, n))
+    rgb = rng.uniform(0, 1, (n, 3))
+    nrm = random_dirs(rng, n)
+    off = rng.uniform(-1, 1, n) * R
+    tex = rng.normal(0, 0.1, (n, 12))
+    sc = make_scene(pos, R * R, R, sigma, rgb, nrm, off, tex)
+    s = sc.copy()
+    for k in s.PARAMS:
+        setattr(s, k, np.ascontiguousarray(np.asarray(getattr(s, k)), np.float32))
+    # tied weights (from the float32 radii) and no neighbour lists
+    s.w = (s.R.astype(np.float64) ** 2).astype(np.float32)
+    s.nbr = np.zeros((n, 0), np.int32)
+    return s
+
+
+def compare_bins(r, sc, cam):
+    ts, cells, keys, rects = r.read_bins()
+    orc = oracle.Oracle(sc)
+    rect_o, key_o = orc.bin(cam)
+    assert np.array_equal(keys[:sc.n], key_o)
+    empty_o = (rect_o[:, 0] > rect_o[:, 2]) | (rect_o[:, 1] > rect_o[:, 3])
+    rg = rects[:sc.n].astype(np.int64)
+    empty_g = (rg[:, 0] > rg[:, 2]) | (rg[:, 1] > rg[:, 3])
+    assert np.array_equal(empty_o, empty_g)
+    assert np.array_equal(rg[~empty_o], rect_o[~empty_o])
+    st_o, cells_o = oracle.tile_lists(rect_o, key_o, cam.tiles_x, cam.tiles_y)
+    assert np.array_equal(ts.astype(np.int64), st_o)
+    assert np.array_equal(cells[:st_o[-1]].astype(np.int64), cells_o)
+    return np.diff(st_o)
+
+
+def test_long_tile_lists_bit_exact_and_rendered():
+    import torch
+    from paper_2604_24994_gb300 import DeviceScene, Renderer
+    cam = inputs.look_at((3.0, 0.0, 0.0), 640, 360)
+    tiles = [(19, 10), (23, 6)]
+    sc = column_scene(cam, tiles, [80, 24])
+    ds = DeviceScene.from_numpy(sc, "cuda")
+    r = Renderer(ds.n, ds.k, [cam])
+    rgb, T, last = r.forward(ds)
+    torch.cuda.synchronize()
+    lens = compare_bins(r, sc, cam)
+    assert lens.max() == 256 * 80 > 16384            # the global-memory sort
+    assert ((lens > 2048) & (lens <= 16384)).sum() == 1   # the 192 KB shared-memory sort
+    # the rendered tiles against the oracle (every pixel of both tiles, and some empty ones)
+    pix = np.array([(u, v) for tx, ty in tiles for v in range(ty * 16, ty * 16 + 16)
+                    for u in range(tx * 16, tx * 16 + 16)] + [(0, 0), (639, 359), (300, 10)], np.int32)
+    orc = oracle.Oracle(sc)
+    orc.prune_for(cam, pix)
+    rgb_o, T_o, nseg = orc.render(cam, pix, return_nseg=True)
+    idx = pixel_index([cam], 0, pix)
+    rgb = rgb.cpu().numpy().astype(np.float64)
+    T = T.cpu().numpy().astype(np.float64)
+    assert_close_image(rgb[idx], T[idx], rgb_o, T_o, "long lists")
+    # every ray crosses its whole column; the dense halves keep about three quarters of the chords
+    assert nseg[:256].mean() > 40 and nseg[256:512].mean() > 12
+
+
+def test_long_tile_lists_across_views_and_capacity_growth():
+    """The same columns seen by two views of one plan, starting from a
+    capacity far too small (the plan grows and re-bins)."""
+    import torch
+    from paper_2604_24994_gb300 import DeviceScene, Renderer
+    cam = inputs.look_at((3.0, 0.0, 0.0), 640, 360)
+    sc = column_scene(cam, [(10, 12)], [70], seed=1)
+    cam2 = inputs.look_at((3.0, 0.2, -0.1), 320, 200, target=(0.0, 0.2, -0.1))
+    ds = DeviceScene.from_numpy(sc, "cuda")
+    r = Renderer(ds.n, ds.k, [cam, cam2], capacity=1024)
+    r.forward(ds)
+    torch.cuda.synchronize()
+    ts, cells, keys, rects = r.read_bins()
+    orc = oracle.Oracle(sc)
+    base = 0
+    for v, c in enumerate((cam, cam2)):
+        rect_o, key_o = orc.bin(c)
+        st_o, cells_o = oracle.tile_lists(rect_o, key_o, c.tiles_x, c.tiles_y)
+        nt = c.tiles_x * c.tiles_y
+        st_g = ts[base:base + nt + 1].astype(np.int64) - int(ts[base])
+        assert np.array_equal(st_g, st_o)
+        assert np.array_equal(cells[int(ts[base]):int(ts[base + nt])].astype(np.int64), cells_o)
+        assert np.array_equal(keys[v * sc.n:(v + 1) * sc.n], key_o)
+        base += nt
+    assert np.diff(oracle.tile_lists(*orc.bin(cam), cam.tiles_x, cam.tiles_y)[0]).max() == 256 * 70

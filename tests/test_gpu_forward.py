@@ -42,8 +42,8 @@ def test_forward_tiny_full_frame(tiny):
     rgb, T, last = gpu_forward(sc, [cam])
     rgb_o, T_o = oracle.Oracle(sc).render(cam)
     assert_close_image(rgb, T, rgb_o, T_o, "tiny 128x128")
-    assert np.all(T < 1) or True
-    assert (last > 0).sum() > 1000
+    assert np.all(T[last == 0] == 1.0)     # no contributing cell: nothing composited
+    assert (last > 0).sum() > 1000 and (T < 1).sum() > 1000
 
 
 def test_forward_ragged_inside_multiview():

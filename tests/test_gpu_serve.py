@@ -74,6 +74,37 @@ def test_results_same_alone_and_in_the_mix(scene, graphs):
     srv.close()
 
 
+def test_served_images_match_the_oracle(scene):
+    """Every request of a mixed-resolution burst, served in continuous
+    batches (graphs on), against the FP64 oracle on sampled pixels."""
+    import torch
+    import oracle
+    from paper_2604_24994_gb300.serve import Server
+    from tests.gpu_util import assert_close_image, sample_pixels
+    sc, ds = scene
+    cams = mixed_cameras(12, seed=4)
+    srv = Server(ds, 1 << 30, max_batch_views=4, slots=2, use_graphs=True)
+    outs, ids = [], []
+    for cam in cams:
+        rgb = torch.full((cam.n_pixels, 3), float("nan"), device="cuda")
+        T = torch.full((cam.n_pixels,), float("nan"), device="cuda")
+        outs.append((rgb, T))
+        ids.append(srv.submit(cam, rgb, T))
+    for rid in ids:
+        srv.wait(rid, 60000)
+    rep = srv.report()
+    srv.close()
+    assert rep["completed"] == len(cams) and rep["mean_batch_views"] >= 1.0
+    orc = oracle.Oracle(sc)
+    for v, (cam, (rgb, T)) in enumerate(zip(cams, outs)):
+        pix = sample_pixels(cam, 40, seed=v)
+        orc.prune_for(cam, pix)
+        rgb_o, T_o = orc.render(cam, pix)
+        idx = pix[:, 1] * cam.width + pix[:, 0]
+        assert_close_image(rgb.cpu().numpy().astype(np.float64)[idx], T.cpu().numpy().astype(np.float64)[idx],
+                           rgb_o, T_o, f"served request {v} ({cam.width}x{cam.height})")
+
+
 def test_admission_by_memory_and_back_pressure(scene):
     import torch
     from paper_2604_24994_gb300 import _lib

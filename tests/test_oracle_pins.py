@@ -401,6 +401,22 @@ def test_compositing_matches_marching_on_ten_cells():
 
 # ------------------------------------------------------------------ gradients
 
+def richardson_central(flat, j, h, loss):
+    """d loss / d flat[j] by FP64 central differences at steps h and h/2,
+    combined by Richardson extrapolation, (4 D(h/2) - D(h)) / 3, which
+    cancels the h^2 term of the central difference's error.  flat[j] is
+    restored."""
+    old = flat[j]
+
+    def central(step):
+        flat[j] = old + step
+        lp = loss()
+        flat[j] = old - step
+        lm = loss()
+        flat[j] = old
+        return (lp - lm) / (2 * step)
+    return (4.0 * central(0.5 * h) - central(h)) / 3.0
+
 def fd_scene(seed):
     rng = np.random.default_rng(seed)
     return cluster_scene(rng, n=9, spread=0.12, r=(0.06, 0.12), tex_std=0.2)
@@ -434,14 +450,8 @@ def test_adjoint_matches_central_differences(seed):
         assert nz.size > 0, key
         for j in rng.choice(nz, size=min(6, nz.size), replace=False):
             h = scale[key] * 1e-3
-            old = flat[j]
-            flat[j] = old + h
-            lp = loss()
-            flat[j] = old - h
-            lm = loss()
-            flat[j] = old
-            fd = (lp - lm) / (2 * h)
-            assert abs(fd - gflat[j]) <= 1e-5 * max(1.0, abs(fd)), (key, j, fd, gflat[j])
+            fd = richardson_central(flat, j, h, loss)
+            assert abs(fd - gflat[j]) <= 1e-6 * max(1.0, abs(fd)), (key, j, fd, gflat[j])
             checked += 1
     assert checked >= 40
 
@@ -874,14 +884,8 @@ def test_displacement_adjoint_matches_central_differences(seed):
         assert nz.size > 0, key
         for j in rng.choice(nz, size=min(6, nz.size), replace=False):
             h = scale[key] * 1e-3
-            old = flat[j]
-            flat[j] = old + h
-            lp = loss()
-            flat[j] = old - h
-            lm = loss()
-            flat[j] = old
-            fd = (lp - lm) / (2 * h)
-            assert abs(fd - gflat[j]) <= 1e-5 * max(1.0, abs(fd)), (key, j, fd, gflat[j])
+            fd = richardson_central(flat, j, h, loss)
+            assert abs(fd - gflat[j]) <= 1e-6 * max(1.0, abs(fd)), (key, j, fd, gflat[j])
             checked += 1
     assert checked >= 45
 
@@ -955,14 +959,8 @@ def test_site_adjoint_matches_central_differences(seed):
         assert nz.size > 0, key
         for j in rng.choice(nz, size=min(6 if key != "sites" else 12, nz.size), replace=False):
             h = scale[key] * 1e-3
-            old = flat[j]
-            flat[j] = old + h
-            lp = loss()
-            flat[j] = old - h
-            lm = loss()
-            flat[j] = old
-            fd = (lp - lm) / (2 * h)
-            assert abs(fd - gflat[j]) <= 1e-5 * max(1.0, abs(fd)), (key, j, fd, gflat[j])
+            fd = richardson_central(flat, j, h, loss)
+            assert abs(fd - gflat[j]) <= 1e-6 * max(1.0, abs(fd)), (key, j, fd, gflat[j])
             checked += 1
     assert checked >= 55
 
@@ -1054,14 +1052,8 @@ def test_spherical_voronoi_adjoint_matches_central_differences(seed):
         assert nz.size > 0, key
         for j in rng.choice(nz, size=min(16 if key == "sv" else 5, nz.size), replace=False):
             h = 1e-6 if key != "w" else 1e-7
-            old = flat[j]
-            flat[j] = old + h
-            lp = loss()
-            flat[j] = old - h
-            lm = loss()
-            flat[j] = old
-            fd = (lp - lm) / (2 * h)
-            assert abs(fd - gflat[j]) <= 1e-5 * max(1.0, abs(fd)), (key, j, fd, gflat[j])
+            fd = richardson_central(flat, j, h, loss)
+            assert abs(fd - gflat[j]) <= 1e-6 * max(1.0, abs(fd)), (key, j, fd, gflat[j])
             checked += 1
     assert checked >= 50
 
@@ -1112,14 +1104,8 @@ def test_contribution_adjoint_matches_central_differences(seed):
         assert nz.size > 0, key
         for j in rng.choice(nz, size=min(6, nz.size), replace=False):
             h = 1e-6 if key != "w" else 1e-7
-            old = flat[j]
-            flat[j] = old + h
-            lp = loss()
-            flat[j] = old - h
-            lm = loss()
-            flat[j] = old
-            fd = (lp - lm) / (2 * h)
-            assert abs(fd - gflat[j]) <= 1e-5 * max(1.0, abs(fd)), (key, j, fd, gflat[j])
+            fd = richardson_central(flat, j, h, loss)
+            assert abs(fd - gflat[j]) <= 1e-6 * max(1.0, abs(fd)), (key, j, fd, gflat[j])
             checked += 1
     assert checked >= 35
 
@@ -1242,14 +1228,8 @@ def test_eight_site_adjoint_matches_central_differences():
         assert nz.size > 0, key
         for j in rng.choice(nz, size=min(6, nz.size), replace=False):
             h = 1e-6 if key != "w" else 1e-7
-            old = flat[j]
-            flat[j] = old + h
-            lp = loss()
-            flat[j] = old - h
-            lm = loss()
-            flat[j] = old
-            fd = (lp - lm) / (2 * h)
-            assert abs(fd - gflat[j]) <= 1e-5 * max(1.0, abs(fd)), (key, j, fd, gflat[j])
+            fd = richardson_central(flat, j, h, loss)
+            assert abs(fd - gflat[j]) <= 1e-6 * max(1.0, abs(fd)), (key, j, fd, gflat[j])
             checked += 1
     assert checked >= 50
 
