@@ -359,6 +359,18 @@ def run_ours(args):
         if it >= W:
             cc.append(a.elapsed_time(b))
     ms_connect = float(np.mean(cc))
+    # the same loss over the exact Cech adjacency (every overlapping pair of bounding spheres)
+    from paper_2604_24994_gb300.api import connect_loss_cech
+    cc = []
+    for it in range(W + K):
+        a, b = ev(), ev()
+        a.record(stream)
+        connect_loss_cech(ds.params["pos"], ds.params["R"])
+        b.record(stream)
+        b.synchronize()
+        if it >= W:
+            cc.append(a.elapsed_time(b))
+    ms_connect_cech = float(np.mean(cc))
     # a 180-degree equidistant fisheye view of the same scene through the same kernels
     from paper_2604_24994_gb300 import inputs as _inputs
     fcam = _inputs.fisheye_look_at(tuple(np.asarray(cam.origin)), cam.width, cam.height, fov_deg=180.0)
@@ -388,7 +400,7 @@ def run_ours(args):
     dparams = dict(ds.params, disp=dsp)
     dst = ds.struct(dparams)
     rd = Renderer(ds.n, ds.k, [cam], hit_records=False)
-    rd.bin(ds, sync=True)
+    rd.bin(ds, params=dparams, sync=True)   # prepare prunes planes against the displaced face
     do = rd.render_fwd(ds, params=dparams)
     dt = []
     for it in range(W + K):
@@ -423,7 +435,31 @@ def run_ours(args):
         if it >= W:
             st_t.append(a.elapsed_time(b))
     ms_sv = float(np.mean(st_t))
-    del rd, do, dsp, dparams, sparams
+    # eight detail sites per face (Sec. 3.4's main configuration): 24 texture values, displacements up to
+    # 0.2 R and learned positions (the fixed 3 x 3 grid without its centre, jittered) at every site
+    grid8 = np.array([[-1, -1], [0, -1], [1, -1], [-1, 0], [1, 0], [-1, 1], [0, 1], [1, 1]], np.float32) / 3.0
+    e8 = dict(ds.params,
+              tex=torch.from_numpy(drng.normal(0, 0.1, (ds.n, 24)).astype(np.float32)).cuda(),
+              disp=torch.from_numpy((drng.uniform(-0.2, 0.2, (ds.n, 8)) * sc.R[:, None]).astype(np.float32)).cuda(),
+              sites=torch.from_numpy((grid8[None] + drng.uniform(-0.1, 0.1, (ds.n, 8, 2))).astype(np.float32)).cuda())
+    est = ds.struct(e8)
+    assert est.n_sites == 8
+    rd.bin(ds, params=e8, sync=True)
+    e8_t = []
+    for it in range(W + K):
+        flush.zero_()
+        a, b = ev(), ev()
+        a.record(stream)
+        check(lib().pf_project(C.byref(est), rd.plan.handle, rd.plan.ws_ptr, stream.cuda_stream), "project")
+        check(lib().pf_bin_sort(rd.plan.handle, rd.plan.ws_ptr, None, stream.cuda_stream), "bin_sort")
+        check(lib().pf_render_fwd(C.byref(est), rd.plan.handle, rd.plan.ws_ptr, do[0].data_ptr(), do[1].data_ptr(),
+                                  do[2].data_ptr(), stream.cuda_stream), "render_fwd")
+        b.record(stream)
+        b.synchronize()
+        if it >= W:
+            e8_t.append(a.elapsed_time(b))
+    ms_e8 = float(np.mean(e8_t))
+    del rd, do, dsp, dparams, sparams, e8, est
     # the neighbour lists of the same scene built on the GPU (pf_build_neighbours)
     from paper_2604_24994_gb300.api import build_neighbours
     pw, Rin = ds.params["pos"], ds.params["R"]
@@ -479,14 +515,18 @@ def run_ours(args):
         "instances": n_inst, "scene_generation_s": round(gen_s, 1),
         "side_steps": {"fisheye_step": "the forward step for a 180-degree equidistant fisheye of the same size and position",
                        "displaced_step": "the forward step with every face displaced by up to 0.2 R at its four sites",
-                       "view_dependent_step": "the forward step with spherical-Voronoi site colours (8 axes per site)"},
+                       "view_dependent_step": "the forward step with spherical-Voronoi site colours (8 axes per site)",
+                       "eight_site_step": "the forward step with eight detail sites per face: 24 texture values, "
+                                          "displacements up to 0.2 R and learned positions"},
         "fwd_fps": ws * 1000.0 / ms_fwd, "fwd_bwd_fps": ws * 1000.0 / ms_train, "ms_fwd_bwd": ms_train,
         "ms_render_fwd_kernel": ms_render,
         "ms_render_fwd_contrib_kernel": ms_render_contrib,
         "ms_connect_loss_and_grad": ms_connect,
+        "ms_connect_cech_loss_and_grad": ms_connect_cech,
         "fisheye_fwd_fps": 1000.0 / ms_fisheye,
         "displaced_fwd_fps": 1000.0 / ms_disp,
         "view_dependent_fwd_fps": 1000.0 / ms_sv,
+        "eight_site_fwd_fps": 1000.0 / ms_e8,
         "ms_build_neighbours": ms_neighbours,
         "neighbours_equal_input_lists": nbr_same,
         "work": stats,

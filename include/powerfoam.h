@@ -84,6 +84,16 @@ typedef struct {
      * pf_render_fwd_contrib and stats passes return PF_ERR_INVALID_ARG for
      * such a scene. */
     const float *sv;
+    /* Detail sites per face (Sec. 3.4; the paper's main configuration has
+     * eight): 0 or 4 for four, 8 for eight.  With eight, tex is [N,24],
+     * disp [N][8], sites [N][8][2] and sv [N][8][8][6]; the fixed sites are
+     * the 3 x 3 grid of step 1/3 (units of R) without its centre, row by row:
+     * (-1,-1), (0,-1), (1,-1), (-1,0), (1,0), (-1,1), (0,1), (1,1) / 3.
+     * pf_render_fwd, pf_render_fwd_static, the server and pf_render_bwd (its
+     * tex, disp, sites and sv gradients have the same shapes) take either;
+     * pf_render_fwd_contrib and stats passes return PF_ERR_INVALID_ARG for
+     * eight. */
+    int32_t n_sites;
 } pf_scene;
 
 /* Camera: x_cam = rot (x_world - origin), OpenCV axes (x right, y down,
@@ -253,13 +263,40 @@ pf_status pf_render_bwd(const pf_scene *scene, pf_plan *plan, void *ws, const fl
 /*
  * Connectivity loss of Sec. 4 / appendix (L_connect) over the neighbour
  * lists, which stand in for the Cech adjacency (pairs whose bounding spheres
- * do not overlap add nothing):
+ * do not overlap add nothing; pf_connect_cech below sums over the exact
+ * adjacency):
  *   loss[i] = sum_{j in nbr(i)} max(R_i + R_j - |p_i - p_j|, 0)^2     (written)
  * With grad_pos [N,3] and grad_R [N] (both or neither) it ADDS the gradient
  * of sum_i loss[i] with respect to the sites and the bound radii.  Uses only
  * pos, R, nbr, n_cells and k_nbr of the scene; device pointers; no plan.
  */
 pf_status pf_connect(const pf_scene *scene, float *loss, float *grad_pos, float *grad_R, void *stream);
+
+/*
+ * Connectivity loss of Sec. 4 / appendix (L_connect) over the exact Cech
+ * adjacency of the bounding spheres: for every cell i, every j != i whose
+ * sphere overlaps cell i's, |p_i - p_j| < R_i + R_j,
+ *   loss[i] = sum_{j in Cech(i)} max(R_i + R_j - |p_i - p_j|, 0)^2   (written)
+ * With grad_pos [N,3] and grad_R [N] (both or neither) it ADDS the gradient
+ * of sum_i loss[i]: each overlapping pair appears in L(i) and in L(j), so
+ * dR_i gets 4 o and dp_i gets 4 o (p_j - p_i) / d per pair, with
+ * o = R_i + R_j - d > 0 and d = |p_j - p_i| (coincident sites add no
+ * direction).  The pairs are found by a radix tree over the sites' Morton
+ * codes refit with the spheres' boxes (the step the paper does with GPU
+ * collision detection, Sec. 3.3); each pair's value is computed in FP64 from
+ * the float inputs and each cell gathers its own sums (no atomics).
+ * pos [N][3], R [N] (negative radii count as 0): device float32.  loss [N],
+ * grad_pos, grad_R: device float32.  status: device uint32, optional: 1 if a
+ * tree walk ran out of stack or steps (not expected below
+ * PF_NEIGHBOURS_MAX_CELLS).  ws: device workspace of at least
+ * pf_connect_cech_workspace_bytes(N) bytes (about 116 bytes per cell).
+ * Errors: PF_ERR_INVALID_ARG (size, null pointer, only one gradient),
+ * PF_ERR_CAPACITY (workspace too small).  Asynchronous on `stream`, no
+ * allocation, no host synchronisation.
+ */
+uint64_t pf_connect_cech_workspace_bytes(int32_t n_cells);
+pf_status pf_connect_cech(const float *pos, const float *R, int32_t n_cells, float *loss, float *grad_pos,
+                          float *grad_R, uint32_t *status, void *ws, uint64_t ws_bytes, void *stream);
 
 /*
  * Copy the binning results to HOST buffers (synchronises `stream`), for

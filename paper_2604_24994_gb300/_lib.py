@@ -30,7 +30,7 @@ class PFError(RuntimeError):
 class Scene(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in ("pos", "w", "R", "sigma", "rgb", "normal", "offset", "tex", "nbr")] + [
         ("n_cells", C.c_int32), ("k_nbr", C.c_int32), ("disp", C.c_void_p), ("sites", C.c_void_p),
-        ("sv", C.c_void_p)]
+        ("sv", C.c_void_p), ("n_sites", C.c_int32)]
 
 
 class Camera(C.Structure):
@@ -74,6 +74,8 @@ def _sig(lib):
         "pf_read_bins": ([V, V, V, V, V, V, V], st),
         "pf_neighbours_workspace_bytes": ([I32], U64),
         "pf_build_neighbours": ([V, V, V, I32, I32, V, V, V, V, V, U64, V], st),
+        "pf_connect_cech_workspace_bytes": ([I32], U64),
+        "pf_connect_cech": ([V, V, I32, V, V, V, V, V, U64, V], st),
     }
     for name, (args, res) in spec.items():
         f = getattr(lib, name)

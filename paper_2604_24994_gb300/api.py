@@ -27,15 +27,20 @@ class DeviceScene:
         self.nbr = nbr
         self.n = int(params["pos"].shape[0])
         self.k = int(nbr.shape[1]) if nbr.dim() == 2 else 0
+        # detail sites per face (Sec. 3.4): 4, or 8 when tex holds 24 values per cell
+        self.n_sites = 8 if params["tex"].numel() == 24 * self.n and self.n > 0 else 4
 
     @staticmethod
     def from_numpy(scene, device="cuda", requires_grad=False, disp=None, sites=None, sv=None) -> "DeviceScene":
-        """`disp` [N,4] (or the scene's `disp` attribute): face displacement
-        at the four texture sites (Eq. svdisp).  `sites` [N,4,2] (or the
+        """`disp` [N,S] (or the scene's `disp` attribute): face displacement
+        at the S texture sites (Eq. svdisp).  `sites` [N,S,2] (or the
         scene's `sites`): learned positions of those sites, in units of R.
-        `sv` [N,4,8,6] (or the scene's `sv`): view-dependent site colours,
-        eight (axis, rgb) per site."""
+        `sv` [N,S,8,6] (or the scene's `sv`): view-dependent site colours,
+        eight (axis, rgb) per site.  S, the detail sites per face, is 4, or 8
+        when the scene's tex is [N,24]."""
         params = {}
+        tex = np.asarray(scene.tex)
+        ns = 8 if tex.ndim == 2 and tex.shape[1] == 24 else 4
         for k in PARAMS:
             a = np.ascontiguousarray(getattr(scene, k), np.float32)
             t = torch.from_numpy(a).to(device)
@@ -45,15 +50,15 @@ class DeviceScene:
         if disp is None:
             disp = getattr(scene, "disp", None)
         if disp is not None:
-            params["disp"] = torch.from_numpy(np.ascontiguousarray(disp, np.float32).reshape(-1, 4)).to(device)
+            params["disp"] = torch.from_numpy(np.ascontiguousarray(disp, np.float32).reshape(scene.n, ns)).to(device)
         if sites is None:
             sites = getattr(scene, "sites", None)
         if sites is not None:
-            params["sites"] = torch.from_numpy(np.ascontiguousarray(sites, np.float32).reshape(-1, 4, 2)).to(device)
+            params["sites"] = torch.from_numpy(np.ascontiguousarray(sites, np.float32).reshape(scene.n, ns, 2)).to(device)
         if sv is None:
             sv = getattr(scene, "sv", None)
         if sv is not None:
-            params["sv"] = torch.from_numpy(np.ascontiguousarray(sv, np.float32).reshape(-1, 4, 8, 6)).to(device)
+            params["sv"] = torch.from_numpy(np.ascontiguousarray(sv, np.float32).reshape(scene.n, ns, 8, 6)).to(device)
         nbr = torch.from_numpy(np.ascontiguousarray(scene.nbr, np.int32)).to(device)
         return DeviceScene(params, nbr)
 
@@ -68,7 +73,9 @@ class DeviceScene:
         s.nbr = self.nbr.data_ptr() if self.nbr.numel() else None
         s.n_cells = self.n
         s.k_nbr = self.k
-        for k, width in (("disp", 4), ("sites", 8), ("sv", 192)):
+        ns = 8 if p["tex"].numel() == 24 * self.n and self.n > 0 else 4
+        s.n_sites = ns
+        for k, width in (("disp", ns), ("sites", 2 * ns), ("sv", 48 * ns)):
             d = p.get(k)
             if d is not None:
                 if not (d.is_cuda and d.dtype == torch.float32 and d.is_contiguous() and d.numel() == width * self.n):
@@ -87,6 +94,30 @@ def connect_loss(scene: DeviceScene, grad: bool = True):
     gR = torch.zeros_like(p["R"]) if grad else None
     check(lib().pf_connect(C.byref(scene.struct()), loss.data_ptr(), gp.data_ptr() if grad else None,
                            gR.data_ptr() if grad else None, _stream()), "pf_connect")
+    return loss, gp, gR
+
+
+def connect_loss_cech(pos, R, grad: bool = True):
+    """pf_connect_cech: the per-cell connectivity loss [N] over the exact
+    Cech adjacency (every pair of overlapping bounding spheres, Sec. 4 /
+    appendix) and, if grad, the gradients (dL/dpos [N,3], dL/dR [N]) of its
+    sum; otherwise (loss, None, None).  pos [N,3], R [N]: float32 CUDA
+    tensors."""
+    n = int(pos.shape[0])
+    for t in (pos, R):
+        if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
+            raise ValueError("connect_loss_cech: float32 contiguous CUDA tensors expected")
+    dev = pos.device
+    loss = torch.empty(n, dtype=torch.float32, device=dev)
+    gp = torch.zeros_like(pos) if grad else None
+    gR = torch.zeros_like(R) if grad else None
+    ws_bytes = int(lib().pf_connect_cech_workspace_bytes(n))
+    ws = torch.empty(max(ws_bytes, 256), dtype=torch.uint8, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    check(lib().pf_connect_cech(pos.data_ptr(), R.data_ptr(), n, loss.data_ptr(), ptr(gp), ptr(gR),
+                                status.data_ptr(), ws.data_ptr(), ws_bytes, _stream()), "pf_connect_cech")
+    if int(status.item()):
+        raise RuntimeError("pf_connect_cech: a tree walk ran out of stack or steps")
     return loss, gp, gR
 
 

@@ -201,6 +201,10 @@ bool scene_ok(const pf_scene *s, const Plan *p) {
         set_error("tex, disp and sites must be 16-byte aligned");
         return false;
     }
+    if (s->n_sites != 0 && s->n_sites != 4 && s->n_sites != 8) {
+        set_error("n_sites must be 0 or 4 (four detail sites) or 8, not %d", s->n_sites);
+        return false;
+    }
     return true;
 }
 
@@ -388,7 +392,7 @@ pf_status pf_render_fwd(const pf_scene *scene, pf_plan *p, void *ws, float *rgb,
     g_err[0] = 0;
     if (!p || !ws || !scene_ok(scene, p) || !rgb || !T || !last) return PF_ERR_INVALID_ARG;
     WS w = p->ws(ws);
-    if ((scene->disp || scene->sites || scene->sv) && p->stats && p->n > 0) {
+    if (ext_face(*scene) && p->stats && p->n > 0) {
         set_error("pf_render_fwd: no stats pass for an extended face model");
         return PF_ERR_INVALID_ARG;
     }
@@ -407,7 +411,7 @@ pf_status pf_render_fwd_contrib(const pf_scene *scene, pf_plan *p, void *ws, flo
         set_error("pf_render_fwd_contrib: null contribution array");
         return PF_ERR_INVALID_ARG;
     }
-    if ((scene->disp || scene->sites || scene->sv) && p->n > 0) {
+    if (ext_face(*scene) && p->n > 0) {
         set_error("pf_render_fwd_contrib: not available for an extended face model");
         return PF_ERR_INVALID_ARG;
     }

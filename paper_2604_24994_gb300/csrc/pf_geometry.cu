@@ -148,8 +148,12 @@ __global__ void __launch_bounds__(256) prepare_kernel(pf_scene s, const float4 *
     // the face as a witness at its widest: a displaced face (Eq. svdisp) moves
     // by a convex combination of the site displacements, at most their maximum
     float face_off = s.offset[i];
-    if (s.disp)
-        face_off += fmaxf(fmaxf(s.disp[4 * i], s.disp[4 * i + 1]), fmaxf(s.disp[4 * i + 2], s.disp[4 * i + 3]));
+    if (s.disp) {
+        const int ns = scene_sites(s);
+        float mx = s.disp[(int64_t)ns * i];
+        for (int k = 1; k < ns; k++) mx = fmaxf(mx, s.disp[(int64_t)ns * i + k]);
+        face_off += mx;
+    }
     if (!empty) cnt = drop_implied_planes(planes + (int64_t)i * K, planes_lo + (int64_t)i * K,
                                           plane_nb + (int64_t)i * K, cnt, make_float4(nx, ny, nz, face_off), Rf);
     // nearest planes first: they cut the most of the ball, so a warp whose
@@ -177,10 +181,14 @@ __global__ void __launch_bounds__(256) prepare_kernel(pf_scene s, const float4 *
     cr[1] = make_float4(e1x, e1y, e1z, Rf);
     cr[2] = make_float4(e2x, e2y, e2z, s.sigma[i]);
     cr[3] = make_float4(s.rgb[3 * i], s.rgb[3 * i + 1], s.rgb[3 * i + 2], __int_as_float(empty ? 1 : 0));
-    const float4 *tx = reinterpret_cast<const float4 *>(s.tex + (int64_t)i * 12);
-    cr[4] = tx[0];
-    cr[5] = tx[1];
-    cr[6] = tx[2];
+    if (s.n_sites == 8) {  // eight sites: the renderer stages tex [N,24] beside the record
+        cr[4] = cr[5] = cr[6] = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+        const float4 *tx = reinterpret_cast<const float4 *>(s.tex + (int64_t)i * 12);
+        cr[4] = tx[0];
+        cr[5] = tx[1];
+        cr[6] = tx[2];
+    }
     cr[7] = make_float4((float)(nxd - (double)nx), (float)(nyd - (double)ny), (float)(nzd - (double)nz),
                         (float)(n2 * inl));
 }

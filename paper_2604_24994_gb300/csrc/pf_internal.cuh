@@ -174,6 +174,14 @@ SceneLayout make_scene_layout(int32_t n, int32_t k);
 // ------------------------------------------------------------------ helpers
 __host__ __device__ inline uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
 
+// Detail sites per face of a scene (Sec. 3.4): 4, or 8.
+__host__ __device__ inline int scene_sites(const pf_scene &s) { return s.n_sites == 8 ? 8 : 4; }
+// An extended face model: displacement, learned sites, view-dependent site
+// colours or eight sites (the renderer's EXT kernels).
+__host__ __device__ inline bool ext_face(const pf_scene &s) {
+    return s.disp != nullptr || s.sites != nullptr || s.sv != nullptr || s.n_sites == 8;
+}
+
 void set_error(const char *fmt, ...);
 pf_status cuda_status(cudaError_t e, const char *what);
 bool camera_ok(const pf_camera &c);

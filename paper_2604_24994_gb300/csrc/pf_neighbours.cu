@@ -570,10 +570,181 @@ __global__ void __launch_bounds__(NB_QT) nb_exact_kernel(const float4 *__restric
     nb_emit(set.t, set.j, set.m, k, i, R_in, nbr, R_out, P);
 }
 
+// ------------------------------------------- Cech adjacency: L_connect
+// The connectivity loss of Sec. 4 / appendix sums over the Cech adjacency
+// of the bounding spheres: every j whose sphere overlaps cell i's.  The same
+// Morton-ordered radix tree, refit with the spheres' boxes, answers "which
+// spheres overlap sphere i" for every i; the pairs found are the exact
+// adjacency (the box test is conservative), and each cell gathers its own
+// loss and gradient (no atomics: the pair (i, j) is met from both sides).
+
+// Leaves: the site and radius (sorted copy) and the sphere's box, rounded
+// outwards; internal nodes: the union of their children's boxes.
+__global__ void __launch_bounds__(NB_T) cc_refit_kernel(const float *__restrict__ pos, const float *__restrict__ R,
+                                                        const uint32_t *__restrict__ val, int64_t n,
+                                                        const int32_t *__restrict__ child,
+                                                        const int32_t *__restrict__ parent,
+                                                        float4 *__restrict__ box, unsigned int *__restrict__ flag,
+                                                        float4 *__restrict__ site, NbParams *__restrict__ P) {
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const uint32_t i = val[s];
+    const float r = fmaxf(R[i], 0.0f);
+    const float4 p = make_float4(pos[3 * (int64_t)i], pos[3 * (int64_t)i + 1], pos[3 * (int64_t)i + 2], r);
+    site[s] = p;
+    const int64_t leaf = n - 1 + s;
+    box[2 * leaf] = make_float4(__fsub_rd(p.x, r), __fsub_rd(p.y, r), __fsub_rd(p.z, r), 0.0f);
+    box[2 * leaf + 1] = make_float4(__fadd_ru(p.x, r), __fadd_ru(p.y, r), __fadd_ru(p.z, r), 0.0f);
+    if (n < 2) return;
+    int64_t node = parent[leaf];
+    for (int up = 0; node >= 0; up++) {
+        if (up >= 2 * NB_STACK) {
+            atomicOr(&P->stack_overflow, 1u);
+            return;
+        }
+        __threadfence();
+        if (atomicAdd(&flag[node], 1u) == 0u) return;  // the sibling subtree is not done yet
+        const int64_t a = child[2 * node], b = child[2 * node + 1];
+        const float4 alo = __ldcg(&box[2 * a]), ahi = __ldcg(&box[2 * a + 1]);
+        const float4 blo = __ldcg(&box[2 * b]), bhi = __ldcg(&box[2 * b + 1]);
+        box[2 * node] = make_float4(fminf(alo.x, blo.x), fminf(alo.y, blo.y), fminf(alo.z, blo.z), 0.0f);
+        box[2 * node + 1] = make_float4(fmaxf(ahi.x, bhi.x), fmaxf(ahi.y, bhi.y), fmaxf(ahi.z, bhi.z), 0.0f);
+        node = parent[node];
+    }
+}
+
+// Can sphere (pi.xyz, pi.w) meet the box?  Conservative: the squared
+// distance from the centre to the box against R^2 with a relative margin
+// far above the float rounding of these few operations (NaN admits).
+__device__ __forceinline__ bool cc_box_hit(float4 pi, float4 lo, float4 hi) {
+    const float ax = fmaxf(fmaxf(lo.x - pi.x, pi.x - hi.x), 0.0f);
+    const float ay = fmaxf(fmaxf(lo.y - pi.y, pi.y - hi.y), 0.0f);
+    const float az = fmaxf(fmaxf(lo.z - pi.z, pi.z - hi.z), 0.0f);
+    const float D2 = ax * ax + ay * ay + az * az;
+    return !(D2 > pi.w * pi.w * (1.0f + 1e-5f) + 1e-30f);
+}
+
+// One pair in FP64 from the float inputs: o = R_i + R_j - |p_j - p_i|; if
+// o > 0 the loss gets o^2, and the gradient of the loss summed over cells
+// (where the pair appears twice, in L(i) and in L(j)) gets 4 o for R_i and
+// 4 o (p_j - p_i) / d for p_i (no direction when the sites coincide).
+struct CcAcc {
+    double loss = 0.0, gx = 0.0, gy = 0.0, gz = 0.0, gr = 0.0;
+    unsigned int pairs = 0;
+    __device__ __forceinline__ void pair(float4 pi, float4 pj) {
+        const double dx = (double)pj.x - (double)pi.x, dy = (double)pj.y - (double)pi.y,
+                     dz = (double)pj.z - (double)pi.z;
+        const double d = sqrt(dx * dx + dy * dy + dz * dz);
+        const double o = ((double)pi.w + (double)pj.w) - d;
+        if (!(o > 0.0)) return;
+        pairs++;
+        loss += o * o;
+        gr += 4.0 * o;
+        if (d > 0.0) {
+            const double f = 4.0 * o / d;
+            gx += f * dx;
+            gy += f * dy;
+            gz += f * dz;
+        }
+    }
+};
+
+__global__ void __launch_bounds__(NB_QT) cc_query_kernel(const float4 *__restrict__ site,
+                                                         const uint32_t *__restrict__ val, int64_t n,
+                                                         const int32_t *__restrict__ child,
+                                                         const int2 *__restrict__ rng,
+                                                         const float4 *__restrict__ box, float *__restrict__ loss,
+                                                         float *__restrict__ gpos, float *__restrict__ gR,
+                                                         NbParams *__restrict__ P) {
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const uint32_t i = val[s];
+    const float4 pi = site[s];
+    CcAcc acc;
+    if (n >= 2) {
+        int32_t stack[NB_STACK];
+        int sp = 0;
+        stack[sp++] = 0;
+        for (int64_t pops = 0; sp > 0; pops++) {
+            if (pops >= n) {  // a tree has n - 1 internal nodes, each taken at most once
+                atomicOr(&P->stack_overflow, 1u);
+                break;
+            }
+            const int64_t node = stack[--sp];
+            for (int e = 0; e < 2; e++) {
+                const int64_t c = child[2 * node + e];
+                if (!cc_box_hit(pi, box[2 * c], box[2 * c + 1])) continue;
+                int64_t lo_q, hi_q;
+                if (c >= n - 1) {  // one site
+                    lo_q = hi_q = c - (n - 1);
+                } else {
+                    const int2 r = rng[c];
+                    if (r.y - r.x >= NB_BUCKET) {
+                        if (sp < NB_STACK) stack[sp++] = (int32_t)c;
+                        else atomicOr(&P->stack_overflow, 1u);
+                        continue;
+                    }
+                    lo_q = r.x;
+                    hi_q = r.y;
+                }
+                for (int64_t q = lo_q; q <= hi_q; q++)
+                    if (q != s) acc.pair(pi, site[q]);
+            }
+        }
+    }
+    loss[i] = (float)acc.loss;
+    if (gpos) {
+        gpos[3 * (int64_t)i] += (float)acc.gx;
+        gpos[3 * (int64_t)i + 1] += (float)acc.gy;
+        gpos[3 * (int64_t)i + 2] += (float)acc.gz;
+        gR[i] += (float)acc.gr;
+    }
+}
+
 __global__ void nb_finish_kernel(const NbParams *__restrict__ P, uint32_t *__restrict__ n_clipped,
                                  uint32_t *__restrict__ status) {
     if (n_clipped) *n_clipped = P->clipped;
     if (status) *status = P->stack_overflow;
+}
+
+// Steps 1-3 of the build, shared by the neighbour lists and the Cech
+// query: bounding box, Morton codes, stable radix sort (the sorted codes and
+// site ids end in code0 / val0), the radix tree, and the refit's arrival
+// flags and parent links reset.
+static cudaError_t nb_sort_and_tree(const float *pos, int64_t n, const NbLayout &L, char *b, cudaStream_t st) {
+    NbParams *P = (NbParams *)(b + L.params);
+    uint32_t *code0 = (uint32_t *)(b + L.code0), *val0 = (uint32_t *)(b + L.val0);
+    uint32_t *code1 = (uint32_t *)(b + L.code1), *val1 = (uint32_t *)(b + L.val1);
+    uint32_t *hist = (uint32_t *)(b + L.hist), *scan_tmp = (uint32_t *)(b + L.scan_tmp);
+    int32_t *parent = (int32_t *)(b + L.parent), *child = (int32_t *)(b + L.child);
+    int2 *rng = (int2 *)(b + L.rng);
+    unsigned int *flag = (unsigned int *)(b + L.flag);
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned grid_n = (unsigned)((n + NB_T - 1) / NB_T);
+    nb_init_kernel<<<1, 1, 0, st>>>(P);
+    cudaError_t e = cudaMemsetAsync(flag, 0, 4 * (size_t)n, st);
+    if (!e) e = cudaMemsetAsync(parent, 0xff, 4 * (size_t)(2 * n), st);  // -1: the refit walk stops there
+    if (e) return e;
+    const unsigned grid_bb = (unsigned)std::min<int64_t>((int64_t)2 * sms, (int64_t)grid_n);
+    nb_bbox_kernel<<<grid_bb, NB_T, 0, st>>>(pos, n, P);
+    nb_morton_kernel<<<grid_n, NB_T, 0, st>>>(pos, n, P, code0, val0);
+    uint32_t *ci = code0, *vi = val0, *co = code1, *vo = val1;
+    for (int shift = 0; shift < 32; shift += 8) {
+        nb_hist_kernel<<<(unsigned)L.nblk, NB_T, 0, st>>>(ci, n, shift, hist, L.nblk);
+        e = exclusive_scan(hist, L.hist_n, scan_tmp, nullptr, nullptr, 0, st);
+        if (e) return e;
+        nb_scatter_kernel<<<(unsigned)L.nblk, NB_T, 0, st>>>(ci, vi, n, shift, hist, L.nblk, co, vo);
+        uint32_t *tc = ci, *tv = vi;
+        ci = co;
+        vi = vo;
+        co = tc;
+        vo = tv;
+    }
+    // four passes: the sorted keys are back in code0 / val0
+    if (n >= 2) nb_tree_kernel<<<(unsigned)((n - 1 + NB_T - 1) / NB_T), NB_T, 0, st>>>(code0, n, child, parent, rng);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -614,39 +785,15 @@ extern "C" pf_status pf_build_neighbours(const float *pos, const float *w, const
     }
     char *b = (char *)ws;
     NbParams *P = (NbParams *)(b + L.params);
-    uint32_t *code0 = (uint32_t *)(b + L.code0), *val0 = (uint32_t *)(b + L.val0);
-    uint32_t *code1 = (uint32_t *)(b + L.code1), *val1 = (uint32_t *)(b + L.val1);
-    uint32_t *hist = (uint32_t *)(b + L.hist), *scan_tmp = (uint32_t *)(b + L.scan_tmp);
+    uint32_t *val0 = (uint32_t *)(b + L.val0);
     int32_t *parent = (int32_t *)(b + L.parent), *child = (int32_t *)(b + L.child);
     int2 *rng = (int2 *)(b + L.rng);
     float4 *box = (float4 *)(b + L.box), *site = (float4 *)(b + L.site);
     unsigned int *flag = (unsigned int *)(b + L.flag);
 
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = nb_sort_and_tree(pos, n, L, b, st);
+    if (e) return cuda_status(e, "pf_build_neighbours: tree");
     const unsigned grid_n = (unsigned)((n + NB_T - 1) / NB_T);
-    nb_init_kernel<<<1, 1, 0, st>>>(P);
-    cudaError_t e = cudaMemsetAsync(flag, 0, 4 * (size_t)n, st);
-    if (!e) e = cudaMemsetAsync(parent, 0xff, 4 * (size_t)(2 * n), st);  // -1: the refit walk stops there
-    if (e) return cuda_status(e, "pf_build_neighbours: memset");
-    const unsigned grid_bb = (unsigned)std::min<int64_t>((int64_t)2 * sms, (int64_t)grid_n);
-    nb_bbox_kernel<<<grid_bb, NB_T, 0, st>>>(pos, n, P);
-    nb_morton_kernel<<<grid_n, NB_T, 0, st>>>(pos, n, P, code0, val0);
-    uint32_t *ci = code0, *vi = val0, *co = code1, *vo = val1;
-    for (int shift = 0; shift < 32; shift += 8) {
-        nb_hist_kernel<<<(unsigned)L.nblk, NB_T, 0, st>>>(ci, n, shift, hist, L.nblk);
-        e = exclusive_scan(hist, L.hist_n, scan_tmp, nullptr, nullptr, 0, st);
-        if (e) return cuda_status(e, "pf_build_neighbours: scan");
-        nb_scatter_kernel<<<(unsigned)L.nblk, NB_T, 0, st>>>(ci, vi, n, shift, hist, L.nblk, co, vo);
-        uint32_t *tc = ci, *tv = vi;
-        ci = co;
-        vi = vo;
-        co = tc;
-        vo = tv;
-    }
-    // four passes: the sorted keys are back in code0 / val0
-    if (n >= 2) nb_tree_kernel<<<(unsigned)((n - 1 + NB_T - 1) / NB_T), NB_T, 0, st>>>(code0, n, child, parent, rng);
     nb_refit_kernel<<<grid_n, NB_T, 0, st>>>(pos, w, val0, n, child, parent, box, flag, site, P);
     uint8_t *redo = (uint8_t *)(b + L.redo);
     e = cudaMemsetAsync(redo, 0, (size_t)n, st);
@@ -664,4 +811,53 @@ extern "C" pf_status pf_build_neighbours(const float *pos, const float *w, const
                                                        P);
     if (n_clipped || status) nb_finish_kernel<<<1, 1, 0, st>>>(P, n_clipped, status);
     return cuda_status(cudaGetLastError(), "pf_build_neighbours");
+}
+
+extern "C" uint64_t pf_connect_cech_workspace_bytes(int32_t n_cells) {
+    return n_cells < 0 ? 0 : nb_layout(n_cells).total;
+}
+
+extern "C" pf_status pf_connect_cech(const float *pos, const float *R, int32_t n_cells, float *loss,
+                                     float *grad_pos, float *grad_R, uint32_t *status, void *ws, uint64_t ws_bytes,
+                                     void *stream) {
+    set_error("%s", "");
+    if (n_cells < 0 || n_cells > PF_NEIGHBOURS_MAX_CELLS) {
+        set_error("pf_connect_cech: %d cells outside [0, %d]", n_cells, PF_NEIGHBOURS_MAX_CELLS);
+        return PF_ERR_INVALID_ARG;
+    }
+    if ((grad_pos == nullptr) != (grad_R == nullptr)) {
+        set_error("pf_connect_cech: grad_pos and grad_R are given together or not at all");
+        return PF_ERR_INVALID_ARG;
+    }
+    const int64_t n = n_cells;
+    if (n > 0 && (!pos || !R || !loss || !ws)) {
+        set_error("pf_connect_cech: null pointer");
+        return PF_ERR_INVALID_ARG;
+    }
+    const NbLayout L = nb_layout(n);
+    if (n > 0 && ws_bytes < L.total) {
+        set_error("pf_connect_cech: workspace %llu bytes < %llu", (unsigned long long)ws_bytes,
+                  (unsigned long long)L.total);
+        return PF_ERR_CAPACITY;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n == 0) {
+        cudaError_t e = status ? cudaMemsetAsync(status, 0, sizeof(uint32_t), st) : cudaSuccess;
+        return cuda_status(e, "pf_connect_cech");
+    }
+    char *b = (char *)ws;
+    NbParams *P = (NbParams *)(b + L.params);
+    uint32_t *val0 = (uint32_t *)(b + L.val0);
+    int32_t *parent = (int32_t *)(b + L.parent), *child = (int32_t *)(b + L.child);
+    int2 *rng = (int2 *)(b + L.rng);
+    float4 *box = (float4 *)(b + L.box), *site = (float4 *)(b + L.site);
+    unsigned int *flag = (unsigned int *)(b + L.flag);
+    cudaError_t e = nb_sort_and_tree(pos, n, L, b, st);
+    if (e) return cuda_status(e, "pf_connect_cech: tree");
+    const unsigned grid_n = (unsigned)((n + NB_T - 1) / NB_T);
+    cc_refit_kernel<<<grid_n, NB_T, 0, st>>>(pos, R, val0, n, child, parent, box, flag, site, P);
+    cc_query_kernel<<<(unsigned)((n + NB_QT - 1) / NB_QT), NB_QT, 0, st>>>(site, val0, n, child, rng, box, loss,
+                                                                           grad_pos, grad_R, P);
+    if (status) nb_finish_kernel<<<1, 1, 0, st>>>(P, nullptr, status);
+    return cuda_status(cudaGetLastError(), "pf_connect_cech");
 }

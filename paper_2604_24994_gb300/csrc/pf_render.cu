@@ -220,13 +220,29 @@ __device__ __forceinline__ bool sphere_chord(const float *__restrict__ cr, const
 }
 
 // Face coordinates of a point y (relative to the site) and the soft-Voronoi
-// weights of the four texture sites there.
-struct Tex {
+// weights of the NS texture sites there.
+template <int NS>
+struct TexT {
     float3 ys;
     float u1, u2;
-    float ax[2], ay[2];     // u - site offsets: ax[0] = u1 + 1/3, ax[1] = u1 - 1/3
-    float r[4], W[4];
+    float ax[2], ay[2];     // u - site offsets of the four fixed sites: ax[0] = u1 + 1/3, ax[1] = u1 - 1/3
+    float r[NS], W[NS];
 };
+using Tex = TexT<4>;
+
+// The fixed detail sites, in units of R: four at (+-1/3, +-1/3), site-major
+// (-,-), (+,-), (-,+), (+,+); eight on the 3 x 3 grid of step 1/3 without its
+// centre, row by row.
+template <int NS>
+__device__ __forceinline__ float site_x(int k) {
+    if (NS == 4) return (k & 1) ? SITE : -SITE;
+    return k < 3 ? (float)(k - 1) * SITE : (k == 3 ? -SITE : (k == 4 ? SITE : (float)(k - 6) * SITE));
+}
+template <int NS>
+__device__ __forceinline__ float site_y(int k) {
+    if (NS == 4) return (k >> 1) ? SITE : -SITE;
+    return k < 3 ? -SITE : (k < 5 ? 0.0f : SITE);
+}
 
 // Displacement of the face for this ray (Eq. svdisp, one-step plane shift):
 // the ray crosses the base face at s = num / fden from its closest approach,
@@ -289,18 +305,63 @@ __device__ __forceinline__ float face_delta(const float *__restrict__ cr, float3
     return (w0 * dk.x + w1 * dk.y + w2 * dk.z + w3 * dk.w) / z;
 }
 
+// face_delta over eight sites (the fixed grid or learned positions st
+// [8][2]): the same one-step plane shift, the weights taken relative to the
+// nearest site; dk: the eight site displacements.
+__device__ __forceinline__ float face_delta8(const float *__restrict__ cr, float3 q, float3 dh, float num, float fden,
+                                             const float *__restrict__ dk, TexT<8> *tx = nullptr,
+                                             const float *__restrict__ st = nullptr) {
+    if (!(fabsf(fden) > 0.0f)) {
+        if (tx) *tx = TexT<8>{};
+        return 0.0f;
+    }
+    const float big = 1e6f * cr[CR_R];
+    const float s = fminf(fmaxf(num / fden, -big), big);
+    const float3 y = f3(fmaf(s, dh.x, q.x), fmaf(s, dh.y, q.y), fmaf(s, dh.z, q.z));
+    const float u0 = dot3(f3(cr[CR_E1], cr[CR_E1 + 1], cr[CR_E1 + 2]), y);
+    const float u1 = dot3(f3(cr[CR_E2], cr[CR_E2 + 1], cr[CR_E2 + 2]), y);
+    float r[8], rmin = CUDART_INF_F;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        const float ax = u0 - (st ? st[2 * k] : site_x<8>(k)), ay = u1 - (st ? st[2 * k + 1] : site_y<8>(k));
+        r[k] = sqrtf(ax * ax + ay * ay);
+        rmin = fminf(rmin, r[k]);
+    }
+    float w[8], z = 0.f, dl = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        w[k] = __expf(-KAPPA * (r[k] - rmin));
+        z += w[k];
+        dl = fmaf(w[k], dk[k], dl);
+    }
+    if (tx) {
+        const float iz = 1.0f / z;
+        tx->ys = y;
+        tx->u1 = u0;
+        tx->u2 = u1;
+        tx->ax[0] = tx->ax[1] = tx->ay[0] = tx->ay[1] = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            tx->r[k] = r[k];
+            tx->W[k] = w[k] * iz;
+        }
+    }
+    return dl / z;
+}
+
 // Clip the chord with the cell's radical planes pl[0..np), the dipole face,
 // then refine near-parallel ends.  False if the segment is empty.  NEED sets
 // sg.nplanes to the planes this ray needs on its own (up to the one that
 // empties its segment) instead of the planes the warp evaluated.  EXT:
 // an extended face model; with has_disp the face moves by the ray's
 // displacement (face_delta, from dk and the sites st).
-template <bool GRAD, bool NEED = false, bool EXT = false>
+template <bool GRAD, bool NEED = false, bool EXT = false, int NS = 4>
 __device__ __forceinline__ bool clip_chord(const float *__restrict__ cr, const float *__restrict__ vr,
                                            const float4 *__restrict__ pl, int np,
                                            const float4 *__restrict__ lo_glob, const Ray &ray, const Chord &ch,
                                            Seg &sg, unsigned lanes = 0u, float4 dk = float4{0.f, 0.f, 0.f, 0.f},
-                                           const float *__restrict__ st = nullptr, bool has_disp = false) {
+                                           const float *__restrict__ st = nullptr, bool has_disp = false,
+                                           const float *__restrict__ dk8 = nullptr) {
     const float3 dh = ray.dh, q = ch.q;
     const float R = cr[CR_R];
     const float sig = cr[CR_SIG];
@@ -323,7 +384,8 @@ __device__ __forceinline__ bool clip_chord(const float *__restrict__ cr, const f
         float num = foff - dot3(q, n);
         fden = dot3(dh, n);
         if (EXT && has_disp) {
-            const float dl = face_delta(cr, q, dh, num, fden, dk, nullptr, st);
+            const float dl = NS == 8 ? face_delta8(cr, q, dh, num, fden, dk8, nullptr, st)
+                                     : face_delta(cr, q, dh, num, fden, dk, nullptr, st);
             foff += dl;
             num += dl;
         }
@@ -411,13 +473,14 @@ __device__ __forceinline__ bool clip_chord(const float *__restrict__ cr, const f
 // The segment of a recorded hit from its active constraints (ka, kb): the
 // same float expressions as clip_chord for those two constraints and the
 // face, then the same refinement, so the ends equal the forward's.
-template <bool GRAD, bool EXT = false>
+template <bool GRAD, bool EXT = false, int NS = 4>
 __device__ __forceinline__ bool segment_from_kinds(const float *__restrict__ cr, const float *__restrict__ vr,
                                                    const float4 *__restrict__ pl,
                                                    const float4 *__restrict__ lo_glob, const Ray &ray,
                                                    const Chord &ch, int ka, int kb, Seg &sg,
                                                    float4 dk = float4{0.f, 0.f, 0.f, 0.f},
-                                                   const float *__restrict__ st = nullptr, bool has_disp = false) {
+                                                   const float *__restrict__ st = nullptr, bool has_disp = false,
+                                                   const float *__restrict__ dk8 = nullptr) {
     const float3 dh = ray.dh, q = ch.q;
     const float R = cr[CR_R];
     const float sig = cr[CR_SIG];
@@ -427,7 +490,8 @@ __device__ __forceinline__ bool segment_from_kinds(const float *__restrict__ cr,
     float fnum = foff - dot3(q, n);
     const float fden = dot3(dh, n);
     if (EXT && has_disp) {  // the forward's displaced face, the same expressions
-        const float dl = face_delta(cr, q, dh, fnum, fden, dk, nullptr, st);
+        const float dl = NS == 8 ? face_delta8(cr, q, dh, fnum, fden, dk8, nullptr, st)
+                                 : face_delta(cr, q, dh, fnum, fden, dk, nullptr, st);
         foff += dl;
         fnum += dl;
     }
@@ -510,9 +574,11 @@ __device__ __forceinline__ float3 sv_colour(const float *__restrict__ q, int k, 
 // Colour at the texture point; `st`: the cell's learned site positions, or
 // null for the fixed ones (then tx.ax / tx.ay hold u minus the sites); `sv`:
 // the cell's view-dependent site colours, or null for the constant ones.
-__device__ __forceinline__ float3 face_colour(const float *__restrict__ cr, const Seg &sg, const Ray &ray, Tex &tx,
+template <int NS>
+__device__ __forceinline__ float3 face_colour(const float *__restrict__ cr, const Seg &sg, const Ray &ray, TexT<NS> &tx,
                                               const float *__restrict__ st = nullptr,
-                                              const float *__restrict__ sv = nullptr) {
+                                              const float *__restrict__ sv = nullptr,
+                                              const float *__restrict__ tex = nullptr) {
     const float ss = sg.dnd > 0.0f ? sg.sb : sg.sa;
     tx.ys = f3(fmaf(ss, ray.dh.x, sg.q.x), fmaf(ss, ray.dh.y, sg.q.y), fmaf(ss, ray.dh.z, sg.q.z));
     tx.u1 = dot3(f3(cr[CR_E1], cr[CR_E1 + 1], cr[CR_E1 + 2]), tx.ys);
@@ -522,16 +588,16 @@ __device__ __forceinline__ float3 face_colour(const float *__restrict__ cr, cons
     tx.ay[0] = tx.u2 + SITE;
     tx.ay[1] = tx.u2 - SITE;
     float Z = 0.f;
-    if (st) {  // learned sites may lie far off: weights relative to the nearest
+    if (st || NS != 4) {  // learned sites may lie far off: weights relative to the nearest
         float rmin = CUDART_INF_F;
 #pragma unroll
-        for (int k = 0; k < 4; k++) {
-            const float ax = tx.u1 - st[2 * k], ay = tx.u2 - st[2 * k + 1];
+        for (int k = 0; k < NS; k++) {
+            const float ax = tx.u1 - (st ? st[2 * k] : site_x<NS>(k)), ay = tx.u2 - (st ? st[2 * k + 1] : site_y<NS>(k));
             tx.r[k] = sqrt_approx(fmaf(ax, ax, ay * ay));
             rmin = fminf(rmin, tx.r[k]);
         }
 #pragma unroll
-        for (int k = 0; k < 4; k++) {
+        for (int k = 0; k < NS; k++) {
             tx.W[k] = __expf(-KAPPA * (tx.r[k] - rmin));
             Z += tx.W[k];
         }
@@ -546,10 +612,11 @@ __device__ __forceinline__ float3 face_colour(const float *__restrict__ cr, cons
     }
     const float iz = __fdividef(1.0f, Z);
     float3 c = f3(cr[CR_RGB], cr[CR_RGB + 1], cr[CR_RGB + 2]);
+    const float *tc = tex ? tex : cr + CR_TEX;  // eight sites: tex staged beside the record
 #pragma unroll
-    for (int k = 0; k < 4; k++) {
+    for (int k = 0; k < NS; k++) {
         tx.W[k] *= iz;
-        const float3 ck = sv ? sv_colour(sv, k, ray.dh) : f3(cr[CR_TEX + 3 * k], cr[CR_TEX + 3 * k + 1], cr[CR_TEX + 3 * k + 2]);
+        const float3 ck = sv ? sv_colour(sv, k, ray.dh) : f3(tc[3 * k], tc[3 * k + 1], tc[3 * k + 2]);
         c.x = fmaf(tx.W[k], ck.x, c.x);
         c.y = fmaf(tx.W[k], ck.y, c.y);
         c.z = fmaf(tx.W[k], ck.z, c.z);
@@ -566,6 +633,7 @@ struct Stage {
     char *base;        // dynamic shared memory
     int K;
     bool with_nb;
+    int xw;            // float4s per cell in the extended face model region (3, or 12 for eight sites)
     // per buffer: cell records [BATCH][CELLREC_F], view records [BATCH][VIEWREC_F],
     // planes [BATCH * K], plane neighbours [BATCH * K]; then ids [2][BATCH], poff [2][BATCH + 1]
     __device__ __forceinline__ size_t kk() const { return K > 0 ? (size_t)K : 1; }
@@ -582,11 +650,13 @@ struct Stage {
     __device__ __forceinline__ int *poff(int b) const {
         return reinterpret_cast<int *>(base + 2 * buf_bytes()) + 2 * BATCH + b * (BATCH + 1);
     }
-    // extended face model [2][BATCH][3] (16-byte aligned): the displacement,
-    // then the four learned site positions (x, y) (scenes with either only)
+    // extended face model [2][BATCH][xw] (16-byte aligned).  Four sites: the
+    // displacement, then the four learned site positions (x, y) (scenes with
+    // either only).  Eight sites: the texture (24 floats), the displacement
+    // (8), the learned positions (16).
     __device__ __forceinline__ float4 *xtr(int b) const {
         return reinterpret_cast<float4 *>(base + ((2 * buf_bytes() + (4 * BATCH + 2) * 4 + 15) & ~(size_t)15)) +
-               b * BATCH * 3;
+               b * BATCH * xw;
     }
 };
 
@@ -608,7 +678,8 @@ __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wai
 __device__ __forceinline__ void issue_batch(const Stage &sg, int buf, const uint32_t *__restrict__ list, int nb,
                                             const WS &w, int64_t vbase, int K, bool with_nb,
                                             const float *__restrict__ disp = nullptr,
-                                            const float *__restrict__ sites = nullptr) {
+                                            const float *__restrict__ sites = nullptr,
+                                            const float *__restrict__ tex8 = nullptr) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     int id = 0, np = 0;
     if (lane < nb) {
@@ -626,9 +697,9 @@ __device__ __forceinline__ void issue_batch(const Stage &sg, int buf, const uint
         sg.poff(buf)[lane + 1] = incl;
         if (lane == 0) sg.poff(buf)[0] = 0;
     }
-    // records: nb x (8 + 2 (+ 3 extended)) chunks over all threads (uniform
-    // trip count: the shuffles need every lane)
-    const int parts = (disp || sites) ? 13 : 10;
+    // records: nb x (8 + 2 (+ 3, or 12 with eight sites, extended)) chunks
+    // over all threads (uniform trip count: the shuffles need every lane)
+    const int parts = tex8 ? 22 : ((disp || sites) ? 13 : 10);
     const int nrec = nb * parts;
     for (int q0 = 0; q0 < nrec; q0 += TILE_PIX) {
         const int q = q0 + tid;
@@ -640,7 +711,15 @@ __device__ __forceinline__ void issue_batch(const Stage &sg, int buf, const uint
             else if (part < 10)
                 cp_async16(sg.vr(buf) + j * VIEWREC_F + (part - 8) * 4,
                            w.viewrec + (vbase + c) * VIEWREC_F + (part - 8) * 4);
-            else if (part == 10 && disp)
+            else if (tex8) {  // eight sites: texture 6, displacement 2, positions 4 granules
+                const int e = part - 10;
+                if (e < 6)
+                    cp_async16(sg.xtr(buf) + 12 * j + e, tex8 + (int64_t)c * 24 + e * 4);
+                else if (e < 8 && disp)
+                    cp_async16(sg.xtr(buf) + 12 * j + e, disp + (int64_t)c * 8 + (e - 6) * 4);
+                else if (e >= 8 && sites)
+                    cp_async16(sg.xtr(buf) + 12 * j + e, sites + (int64_t)c * 16 + (e - 8) * 4);
+            } else if (part == 10 && disp)
                 cp_async16(sg.xtr(buf) + 3 * j, disp + (int64_t)c * 4);
             else if (part > 10 && sites)
                 cp_async16(sg.xtr(buf) + 3 * j + (part - 10), sites + (int64_t)c * 8 + (part - 11) * 4);
@@ -680,8 +759,10 @@ struct RenderArgs {
     float *gdisp;           // [N][4] its gradient (the backward adds into it), or null
     const float *sites;     // [N][4][2] learned texture / detail site positions, or null
     float *gsites;          // [N][4][2] their gradient, or null
-    const float *sv;        // [N][4][8][6] view-dependent site colours, or null
-    float *gsv;             // [N][4][8][6] their gradient, or null
+    const float *sv;        // [N][S][8][6] view-dependent site colours, or null
+    float *gsv;             // [N][S][8][6] their gradient, or null
+    const float *tex8;      // eight sites: the texture [N][24] (four: in the cell record), else null
+    float *gtex8;           // eight sites: its gradient (the backward adds into it), else null
 };
 
 // Hit masks: one 32-bit word per (warp of the tile, batch, pixel of the
@@ -747,18 +828,19 @@ __device__ __forceinline__ unsigned warp_mask(const Stage &sg, int buf, int nb, 
     return __ballot_sync(0xffffffffu, ov);
 }
 
-__host__ __device__ inline size_t stage_bytes(int K, bool with_nb, bool ext = false) {
+__host__ __device__ inline size_t stage_bytes(int K, bool with_nb, bool ext = false, int xw = 3) {
     const size_t k = K > 0 ? (size_t)K : 1;
     const size_t buf = (size_t)BATCH * (CELLREC_F + VIEWREC_F) * 4 + BATCH * k * (with_nb ? 24 : 16);
     const size_t ids = 2 * buf + (2 * BATCH + 2 * (BATCH + 1)) * 4;
-    return ext ? ((ids + 15) & ~(size_t)15) + 2 * BATCH * 48 : ids;
+    return ext ? ((ids + 15) & ~(size_t)15) + 2 * BATCH * 16 * (size_t)xw : ids;
 }
 
-__device__ __forceinline__ Stage make_stage(float4 *smem, int K, bool with_nb) {
+__device__ __forceinline__ Stage make_stage(float4 *smem, int K, bool with_nb, int xw = 3) {
     Stage sg;
     sg.base = reinterpret_cast<char *>(smem);
     sg.K = K;
     sg.with_nb = with_nb;
+    sg.xw = xw;
     return sg;
 }
 
@@ -767,14 +849,15 @@ __device__ __forceinline__ Stage make_stage(float4 *smem, int K, bool with_nb) {
 // replays (only with a hit-mask region in the workspace); CONTRIB: add each
 // cell's contributions (Sec. 4: T alpha for L_sparse and the pruning EMA,
 // T alpha max(nh.d, 0)^2 for L_normal) over the frame's pixels.
-template <bool STATS, bool REC, bool CONTRIB, bool EXT = false>
+template <bool STATS, bool REC, bool CONTRIB, bool EXT = false, int NS = 4>
 __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, int64_t n_tiles,
                                                                  float *__restrict__ rgb_out,
                                                                  float *__restrict__ T_out,
                                                                  uint32_t *__restrict__ last_out) {
     extern __shared__ float4 smem4[];
     __shared__ int64_t s_q, s_slot;
-    const Stage sg = make_stage(smem4, A.K, false);
+    constexpr int XW = NS == 8 ? 12 : 3;  // float4s of extended face model per staged cell
+    const Stage sg = make_stage(smem4, A.K, false, XW);
     const int lane = threadIdx.x & 31;
     unsigned long long st_cand = 0, st_hit = 0, st_pl = 0, st_ref = 0, st_pass = 0;
     unsigned long long st_wcand = 0, st_wpass = 0, st_whit = 0;  // per warp (lane 0 counts)
@@ -812,13 +895,15 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, i
     bool done = !inside || !has_ray;
 
     const float *disp = EXT ? A.disp : nullptr, *sites = EXT ? A.sites : nullptr;
-    if (nbat > 0) issue_batch(sg, 0, A.w.inst_sorted + s, min(BATCH, n), A.w, vbase, A.K, false, disp, sites);
+    const float *tex8 = NS == 8 ? A.tex8 : nullptr;
+    if (nbat > 0)
+        issue_batch(sg, 0, A.w.inst_sorted + s, min(BATCH, n), A.w, vbase, A.K, false, disp, sites, tex8);
     for (int k = 0; k < nbat; k++) {
         // every warp is done with batch k-1, whose buffer batch k+1 reuses
         if (__syncthreads_count(!done) == 0) break;
         if (k + 1 < nbat) {
             issue_batch(sg, (k + 1) & 1, A.w.inst_sorted + s + (k + 1) * BATCH, min(BATCH, n - (k + 1) * BATCH),
-                        A.w, vbase, A.K, false, disp, sites);
+                        A.w, vbase, A.K, false, disp, sites, tex8);
             cp_async_wait_one();
         } else {
             cp_async_wait_all();
@@ -840,16 +925,18 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, i
             bool hit = false;
             Seg seg;
             int np = 0;
+            // the cell's extended face model in shared memory: four sites,
+            // displacement then positions; eight, texture, displacement, positions
+            const float *xj = EXT ? reinterpret_cast<const float *>(sg.xtr(buf) + XW * j) : nullptr;
+            const float *st = EXT && sites ? xj + (NS == 8 ? 32 : 4) : nullptr;
             if (pm) {
                 const int o = sg.poff(buf)[j];
                 np = sg.poff(buf)[j + 1] - o;
                 if (pass)
-                    hit = clip_chord<false, STATS, EXT>(cr, vr, sg.pl(buf) + o, np,
-                                                        A.w.planes_lo + (int64_t)sg.ids(buf)[j] * A.K, ray, ch, seg,
-                                                        pm, EXT && disp ? sg.xtr(buf)[3 * j] : float4{0.f, 0.f, 0.f, 0.f},
-                                                        EXT && sites ? reinterpret_cast<const float *>(sg.xtr(buf) + 3 * j + 1)
-                                                                     : nullptr,
-                                                        EXT && disp);
+                    hit = clip_chord<false, STATS, EXT, NS>(
+                        cr, vr, sg.pl(buf) + o, np, A.w.planes_lo + (int64_t)sg.ids(buf)[j] * A.K, ray, ch, seg, pm,
+                        EXT && disp && NS == 4 ? sg.xtr(buf)[3 * j] : float4{0.f, 0.f, 0.f, 0.f}, st, EXT && disp,
+                        NS == 8 ? xj + 24 : nullptr);
             }
             if (STATS && !done) {
                 const unsigned act = __ballot_sync(__activemask(), true);
@@ -888,11 +975,10 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, i
                         (uint16_t)((seg.ka + 3) | ((seg.kb + 3) << 7));
                 nhit++;
             }
-            Tex tx;
-            const float3 c = face_colour(cr, seg, ray, tx,
-                                         EXT && sites ? reinterpret_cast<const float *>(sg.xtr(buf) + 3 * j + 1)
-                                                      : nullptr,
-                                         EXT && A.sv ? A.sv + 192 * (int64_t)sg.ids(buf)[j] : nullptr);
+            TexT<NS> tx;
+            const float3 c = face_colour<NS>(cr, seg, ray, tx, st,
+                                             EXT && A.sv ? A.sv + 48 * NS * (int64_t)sg.ids(buf)[j] : nullptr,
+                                             NS == 8 ? xj : nullptr);
             const float x = fminf(cr[CR_SIG] * (seg.sb - seg.sa), X_CAP);
             const float ex = __expf(-x);
             const float wgt = T * (1.0f - ex);
@@ -1065,7 +1151,7 @@ __device__ __forceinline__ void route_end(float gt, int kind, float s, float den
 
 // MASKS: replay only the (cell, lane) pairs the forward recorded as hits
 // (the hit masks of the current bins); otherwise re-test every listed cell.
-template <bool MASKS, bool EXT = false>
+template <bool MASKS, bool EXT = false, int NS = 4>
 __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, int64_t n_tiles,
                                                                  const float *__restrict__ dL_drgb,
                                                                  const float *__restrict__ dL_dT,
@@ -1074,7 +1160,8 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
     extern __shared__ float4 smem4[];
     __shared__ int s_maxlast;
     __shared__ int64_t s_q;
-    const Stage stg = make_stage(smem4, A.K, true);
+    constexpr int XW = NS == 8 ? 12 : 3;  // float4s of extended face model per staged cell
+    const Stage stg = make_stage(smem4, A.K, true, XW);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool overflow = A.w.counters->overflow != 0;
 
@@ -1131,14 +1218,14 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
     const int nbat = (maxlast + BATCH - 1) / BATCH;
     if (nbat > 0)
         issue_batch(stg, (nbat - 1) & 1, list + (nbat - 1) * BATCH, maxlast - (nbat - 1) * BATCH, A.w, vbase, A.K,
-                    true, EXT ? A.disp : nullptr, EXT ? A.sites : nullptr);
+                    true, EXT ? A.disp : nullptr, EXT ? A.sites : nullptr, NS == 8 ? A.tex8 : nullptr);
     for (int b = nbat - 1; b >= 0; b--) {
         // bit j: the forward found this pixel's segment in cell j non-empty
         const unsigned my_hits = MASKS ? A.w.hitmask[hitmask_slot(A, tile, s, b, warp) + lane] : 0u;
         __syncthreads();  // batch b+1, whose buffer batch b-1 reuses, is done
         if (b > 0) {
             issue_batch(stg, (b - 1) & 1, list + (b - 1) * BATCH, BATCH, A.w, vbase, A.K, true,
-                        EXT ? A.disp : nullptr, EXT ? A.sites : nullptr);
+                        EXT ? A.disp : nullptr, EXT ? A.sites : nullptr, NS == 8 ? A.tex8 : nullptr);
             cp_async_wait_one();
         } else {
             cp_async_wait_all();
@@ -1161,8 +1248,11 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
             const float *cr = s_cr + j * CELLREC_F;
             const float *vr = s_vr + j * VIEWREC_F;
             const bool has_disp = EXT && A.disp;
-            const float4 dk = has_disp ? stg.xtr(buf)[3 * j] : float4{0.f, 0.f, 0.f, 0.f};
-            const float *st = EXT && A.sites ? reinterpret_cast<const float *>(stg.xtr(buf) + 3 * j + 1) : nullptr;
+            // the cell's extended face model in shared memory (see Stage::xtr)
+            const float *xj = EXT ? reinterpret_cast<const float *>(stg.xtr(buf) + XW * j) : nullptr;
+            const float4 dk = has_disp && NS == 4 ? stg.xtr(buf)[3 * j] : float4{0.f, 0.f, 0.f, 0.f};
+            const float *dk8 = NS == 8 && has_disp ? xj + 24 : nullptr;
+            const float *st = EXT && A.sites ? xj + (NS == 8 ? 32 : 4) : nullptr;
             const int o = poff[j], np = poff[j + 1] - o;
             Seg sg;
             Chord ch;
@@ -1178,17 +1268,18 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
                 }
                 if (mine && sphere_chord<true>(cr, vr, ray, ch, cand)) {
                     if (kk != 0xffffu)
-                        hit = segment_from_kinds<true, EXT>(cr, vr, s_pl + o, A.w.planes_lo + (int64_t)cell * A.K,
-                                                            ray, ch, (int)(kk & 127u) - 3, (int)(kk >> 7) - 3, sg,
-                                                            dk, st, has_disp);
+                        hit = segment_from_kinds<true, EXT, NS>(cr, vr, s_pl + o,
+                                                                A.w.planes_lo + (int64_t)cell * A.K, ray, ch,
+                                                                (int)(kk & 127u) - 3, (int)(kk >> 7) - 3, sg, dk, st,
+                                                                has_disp, dk8);
                     else  // beyond the recorded hits of this pixel: clip against every plane
-                        hit = clip_chord<true, false, EXT>(cr, vr, s_pl + o, np,
-                                                           A.w.planes_lo + (int64_t)cell * A.K, ray, ch, sg, 0u, dk, st,
-                                                           has_disp);
+                        hit = clip_chord<true, false, EXT, NS>(cr, vr, s_pl + o, np,
+                                                               A.w.planes_lo + (int64_t)cell * A.K, ray, ch, sg, 0u, dk,
+                                                               st, has_disp, dk8);
                 }
             } else if (mine && sphere_chord<true>(cr, vr, ray, ch, cand)) {
-                hit = clip_chord<true, false, EXT>(cr, vr, s_pl + o, np, A.w.planes_lo + (int64_t)cell * A.K, ray,
-                                                   ch, sg, 0u, dk, st, has_disp);
+                hit = clip_chord<true, false, EXT, NS>(cr, vr, s_pl + o, np, A.w.planes_lo + (int64_t)cell * A.K,
+                                                       ray, ch, sg, 0u, dk, st, has_disp, dk8);
             }
             if (!__any_sync(0xffffffffu, hit)) continue;
             // Every lane runs the adjoint of this cell.  A lane without a hit
@@ -1208,9 +1299,9 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
             float nba[4], nbb[4];
             int ja, jb;
             {
-                Tex tx;
-                const float *svc = EXT && A.sv ? A.sv + 192 * (int64_t)cell : nullptr;
-                const float3 c = face_colour(cr, sg, ray, tx, st, svc);
+                TexT<NS> tx;
+                const float *svc = EXT && A.sv ? A.sv + 48 * NS * (int64_t)cell : nullptr;
+                const float3 c = face_colour<NS>(cr, sg, ray, tx, st, svc, NS == 8 ? xj : nullptr);
                 const float sig = cr[CR_SIG];
                 const float l = sg.sb - sg.sa;
                 const float xr = sig * l;
@@ -1227,17 +1318,36 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
                 const float wc = hit ? Tbefore * alpha : 0.0f;
                 const float3 gc = f3(wc * g.x, wc * g.y, wc * g.z);
                 // texture values and soft-Voronoi weights
-                float gW[4], sW = 0.f;
+                float gW[NS], sW = 0.f;
+                float gt8[NS == 8 ? 32 : 1];  // eight sites: the texture gradient, routed to memory below
+                const float *tc = NS == 8 ? xj : cr + CR_TEX;
 #pragma unroll
-                for (int k = 0; k < 4; k++) {
+                for (int k = 0; k < NS; k++) {
                     // the site's colour weight (finalize: the tex gradient, and summed, the rgb one)
-                    vv[G_TEX + 3 * k] = tx.W[k] * gc.x;
-                    vv[G_TEX + 3 * k + 1] = tx.W[k] * gc.y;
-                    vv[G_TEX + 3 * k + 2] = tx.W[k] * gc.z;
-                    const float3 ck = svc ? sv_colour(svc, k, ray.dh)
-                                          : f3(cr[CR_TEX + 3 * k], cr[CR_TEX + 3 * k + 1], cr[CR_TEX + 3 * k + 2]);
+                    if constexpr (NS == 4) {
+                        vv[G_TEX + 3 * k] = tx.W[k] * gc.x;
+                        vv[G_TEX + 3 * k + 1] = tx.W[k] * gc.y;
+                        vv[G_TEX + 3 * k + 2] = tx.W[k] * gc.z;
+                    } else {
+                        gt8[3 * k] = tx.W[k] * gc.x;
+                        gt8[3 * k + 1] = tx.W[k] * gc.y;
+                        gt8[3 * k + 2] = tx.W[k] * gc.z;
+                    }
+                    const float3 ck = svc ? sv_colour(svc, k, ray.dh) : f3(tc[3 * k], tc[3 * k + 1], tc[3 * k + 2]);
                     gW[k] = ck.x * gc.x + ck.y * gc.y + ck.z * gc.z;
                     sW += tx.W[k] * gW[k];
+                }
+                if constexpr (NS == 8) {
+                    // the site weights sum to one: the rgb gradient is gc (finalize adds it);
+                    // the 24 texture values are summed over the warp, one atomic each
+#pragma unroll
+                    for (int q = 0; q < 12; q++) vv[G_TEX + q] = q < 3 ? (q == 0 ? gc.x : (q == 1 ? gc.y : gc.z)) : 0.f;
+                    if (!svc) {
+#pragma unroll
+                        for (int q = 24; q < 32; q++) gt8[q] = 0.f;
+                        const float sum = warp_transpose_sum(gt8, lane);
+                        if (lane < 24 && A.gtex8) atomicAdd(A.gtex8 + 24 * (int64_t)cell + lane, sum);
+                    }
                 }
                 if (EXT && svc) {
                     // spherical-Voronoi site colours c_k = sum_j P_j rgb_j, P = softmax(lambda a_j.wo / |a_j|),
@@ -1245,7 +1355,7 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
                     // gP_j = W_k gc.rgb_j; dL/da_j = (I - a a^T / |a|^2) lambda wo dL/dlogit_j / |a|.
                     // 48 values per site, summed over the warp in two transposed rounds of 24.
 #pragma unroll 1
-                    for (int k = 0; k < 4; k++) {
+                    for (int k = 0; k < NS; k++) {
                         const float *pk = svc + 48 * k;
                         const float3 gck = f3(tx.W[k] * gc.x, tx.W[k] * gc.y, tx.W[k] * gc.z);
                         float P[8], gP[8], mx = -CUDART_INF_F, z = 0.f, sP = 0.f;
@@ -1291,18 +1401,19 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
 #pragma unroll
                             for (int q = 24; q < 32; q++) v[q] = 0.f;
                             const float sum = warp_transpose_sum(v, lane);
-                            if (lane < 24 && A.gsv) atomicAdd(A.gsv + 192 * (int64_t)cell + 48 * k + 24 * h + lane, sum);
+                            if (lane < 24 && A.gsv)
+                                atomicAdd(A.gsv + 48 * NS * (int64_t)cell + 48 * k + 24 * h + lane, sum);
                         }
                     }
                 }
                 float gu1 = 0.f, gu2 = 0.f;
-                float gs[8];  // learned sites: r_k = |u - s_k|, so dL/ds_k = -dL/du through logit k
+                float gs[2 * NS];  // learned sites: r_k = |u - s_k|, so dL/ds_k = -dL/du through logit k
 #pragma unroll
-                for (int k = 0; k < 4; k++) {
+                for (int k = 0; k < NS; k++) {
                     const float gr = -KAPPA * tx.W[k] * (gW[k] - sW);
                     const float ir = tx.r[k] > 0.f ? gr * rcp_approx(tx.r[k]) : 0.0f;
-                    const float dxk = st ? tx.u1 - st[2 * k] : tx.ax[k & 1];
-                    const float dyk = st ? tx.u2 - st[2 * k + 1] : tx.ay[k >> 1];
+                    const float dxk = st ? tx.u1 - st[2 * k] : (NS == 4 ? tx.ax[k & 1] : tx.u1 - site_x<NS>(k));
+                    const float dyk = st ? tx.u2 - st[2 * k + 1] : (NS == 4 ? tx.ay[k >> 1] : tx.u2 - site_y<NS>(k));
                     gu1 = fmaf(ir, dxk, gu1);
                     gu2 = fmaf(ir, dyk, gu2);
                     gs[2 * k] = -ir * dxk;
@@ -1336,6 +1447,9 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
                 const float4 *plp = s_pl + o;
                 route_end(gta, sg.ka, sg.sa, sg.dena, sg, ray, cr, plp, nbp, gm, vv, nba, ja);
                 route_end(gtb, sg.kb, sg.sb, sg.denb, sg, ray, cr, plp, nbp, gm, vv, nbb, jb);
+                float gdk[NS];  // the site displacements' gradients
+#pragma unroll
+                for (int k = 0; k < NS; k++) gdk[k] = 0.f;
                 if (EXT && has_disp) {
                     // the displaced face end moves with delta like with the offset
                     // (ds/d delta = 1/(d.n)); delta moves with the site displacements
@@ -1344,20 +1458,24 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
                     const float3 nf = f3(cr[CR_N], cr[CR_N + 1], cr[CR_N + 2]);
                     const bool fa = sg.ka == K_FACE, fb = sg.kb == K_FACE;
                     const float fden = dot3(ray.dh, nf);
-                    Tex fd;
-                    const float dl = face_delta(cr, sg.q, ray.dh, cr[CR_OFF] - dot3(sg.q, nf), fden, dk, &fd, st);
+                    TexT<NS> fd;
+                    float dl;
+                    if constexpr (NS == 8)
+                        dl = face_delta8(cr, sg.q, ray.dh, cr[CR_OFF] - dot3(sg.q, nf), fden, dk8, &fd, st);
+                    else
+                        dl = face_delta(cr, sg.q, ray.dh, cr[CR_OFF] - dot3(sg.q, nf), fden, dk, &fd, st);
                     const float gd = (fa || fb) ? ((fa ? gta : 0.f) + (fb ? gtb : 0.f)) *
                                                       rcp_approx(fa ? sg.dena : sg.denb)
                                                 : 0.f;
-                    const float dks[4] = {dk.x, dk.y, dk.z, dk.w};
-                    float gdk[4], gv1 = 0.f, gv2 = 0.f;
+                    const float dk4[4] = {dk.x, dk.y, dk.z, dk.w};
+                    float gv1 = 0.f, gv2 = 0.f;
 #pragma unroll
-                    for (int k = 0; k < 4; k++) {
+                    for (int k = 0; k < NS; k++) {
                         gdk[k] = gd * fd.W[k];
-                        const float gr = -KAPPA * gd * fd.W[k] * (dks[k] - dl);
+                        const float gr = -KAPPA * gd * fd.W[k] * ((NS == 8 ? dk8[k] : dk4[k & 3]) - dl);
                         const float ir = fd.r[k] > 0.f ? gr * rcp_approx(fd.r[k]) : 0.0f;
-                        const float dxk = st ? fd.u1 - st[2 * k] : fd.ax[k & 1];
-                        const float dyk = st ? fd.u2 - st[2 * k + 1] : fd.ay[k >> 1];
+                        const float dxk = st ? fd.u1 - st[2 * k] : (NS == 4 ? fd.ax[k & 1] : fd.u1 - site_x<NS>(k));
+                        const float dyk = st ? fd.u2 - st[2 * k + 1] : (NS == 4 ? fd.ay[k >> 1] : fd.u2 - site_y<NS>(k));
                         gv1 = fmaf(ir, dxk, gv1);
                         gv2 = fmaf(ir, dyk, gv2);
                         gs[2 * k] -= ir * dxk;
@@ -1374,22 +1492,39 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
                     gm.x += gyb.x - id2 * nf.x;
                     gm.y += gyb.y - id2 * nf.y;
                     gm.z += gyb.z - id2 * nf.z;
-                    // the four site displacements: summed over the warp, one atomic each
+                    if (NS == 4) {  // the four site displacements: summed over the warp, one atomic each
 #pragma unroll
-                    for (int k = 0; k < 4; k++) {
-                        float v = gdk[k];
+                        for (int k = 0; k < NS; k++) {
+                            float v = gdk[k];
 #pragma unroll
-                        for (int o2 = 16; o2 > 0; o2 >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o2);
-                        if (lane == 0 && A.gdisp) atomicAdd(A.gdisp + 4 * (int64_t)cell + k, v);
+                            for (int o2 = 16; o2 > 0; o2 >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o2);
+                            if (lane == 0 && A.gdisp) atomicAdd(A.gdisp + 4 * (int64_t)cell + k, v);
+                        }
                     }
                 }
-                if (EXT && st) {  // the eight site coordinates: summed over the warp, one atomic each
+                if (NS == 4 && EXT && st) {  // the eight site coordinates: summed over the warp, one atomic each
 #pragma unroll
-                    for (int k = 0; k < 8; k++) {
+                    for (int k = 0; k < 2 * NS; k++) {
                         float v = gs[k];
 #pragma unroll
                         for (int o2 = 16; o2 > 0; o2 >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o2);
                         if (lane == 0 && A.gsites) atomicAdd(A.gsites + 8 * (int64_t)cell + k, v);
+                    }
+                }
+                if constexpr (NS == 8) {
+                    // eight displacements and sixteen site coordinates in one transposed warp sum
+                    if (has_disp || st) {
+                        float e[32];
+#pragma unroll
+                        for (int q = 0; q < 8; q++) e[q] = has_disp ? gdk[q] : 0.f;
+#pragma unroll
+                        for (int q = 0; q < 16; q++) e[8 + q] = st ? gs[q] : 0.f;
+#pragma unroll
+                        for (int q = 24; q < 32; q++) e[q] = 0.f;
+                        const float sum = warp_transpose_sum(e, lane);
+                        if (lane < 8 && has_disp && A.gdisp) atomicAdd(A.gdisp + 8 * (int64_t)cell + lane, sum);
+                        if (lane >= 8 && lane < 24 && st && A.gsites)
+                            atomicAdd(A.gsites + 16 * (int64_t)cell + (lane - 8), sum);
                     }
                 }
                 // m = o - p
@@ -1446,7 +1581,7 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
 // rgb enters the colour with weight 1, the texture sites with weights summing to 1.
 __global__ void __launch_bounds__(256) finalize_kernel(int n, const float *__restrict__ acc,
                                                        const float *__restrict__ cellrec, pf_scene_grad G,
-                                                       bool view_dependent) {
+                                                       bool view_dependent, int nsite) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float *a = acc + (int64_t)i * ACC_F;
@@ -1465,6 +1600,12 @@ __global__ void __launch_bounds__(256) finalize_kernel(int n, const float *__res
     G.normal[3 * i + 1] += (gy - ny * pr) * inl;
     G.normal[3 * i + 2] += (gz - nz * pr) * inl;
     G.offset[i] += a[G_OFF];
+    if (nsite == 8) {  // eight sites: the backward added tex itself and left the rgb gradient here
+        G.rgb[3 * i] += a[G_TEX];
+        G.rgb[3 * i + 1] += a[G_TEX + 1];
+        G.rgb[3 * i + 2] += a[G_TEX + 2];
+        return;
+    }
     float r0 = 0.f, r1 = 0.f, r2 = 0.f;
 #pragma unroll
     for (int k = 0; k < 4; k++) {
@@ -1499,6 +1640,8 @@ static RenderArgs make_args(const pf_scene &s, const Plan &p, const WS &w) {
     A.gsites = nullptr;
     A.sv = s.sv;
     A.gsv = nullptr;
+    A.tex8 = scene_sites(s) == 8 ? s.tex : nullptr;
+    A.gtex8 = nullptr;
     return A;
 }
 
@@ -1524,12 +1667,15 @@ cudaError_t launch_render_fwd(const pf_scene &s, const Plan &p, const WS &w, flo
     A.contrib_sparse = contrib_sparse;
     A.contrib_normal = contrib_normal;
     const bool contrib = contrib_sparse != nullptr;
-    const bool disp = s.disp != nullptr || s.sites != nullptr || s.sv != nullptr;  // an extended face model
+    const bool disp = ext_face(s);  // an extended face model
+    const bool eight = scene_sites(s) == 8;
     if (disp && (contrib || p.stats)) return cudaErrorNotSupported;  // the C API refuses these first
-    const size_t smem = disp ? stage_bytes(p.k, false, true) : fwd_smem(p.k);
+    const size_t smem = disp ? stage_bytes(p.k, false, true, eight ? 12 : 3) : fwd_smem(p.k);
     cudaError_t e = cudaMemsetAsync(&w.counters->q_fwd, 0, sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
-    auto k = disp      ? (record ? render_fwd_kernel<false, true, false, true> : render_fwd_kernel<false, false, false, true>)
+    auto k = disp && eight ? (record ? render_fwd_kernel<false, true, false, true, 8>
+                                     : render_fwd_kernel<false, false, false, true, 8>)
+             : disp    ? (record ? render_fwd_kernel<false, true, false, true> : render_fwd_kernel<false, false, false, true>)
              : contrib ? (record ? render_fwd_kernel<false, true, true> : render_fwd_kernel<false, false, true>)
              : p.stats ? render_fwd_kernel<true, false, false>
                        : (record ? render_fwd_kernel<false, true, false> : render_fwd_kernel<false, false, false>);
@@ -1549,19 +1695,22 @@ cudaError_t launch_render_bwd(const pf_scene &s, const Plan &p, const WS &w, con
         A.gdisp = g.disp;
         A.gsites = g.sites;
         A.gsv = g.sv;
-        const bool disp = s.disp != nullptr || s.sites != nullptr || s.sv != nullptr;  // an extended face model
-        const size_t smem = disp ? stage_bytes(p.k, true, true) : bwd_smem(p.k);
+        const bool disp = ext_face(s);  // an extended face model
+        const bool eight = scene_sites(s) == 8;
+        A.gtex8 = eight ? g.tex : nullptr;
+        const size_t smem = disp ? stage_bytes(p.k, true, true, eight ? 12 : 3) : bwd_smem(p.k);
         e = cudaMemsetAsync(&w.counters->q_bwd, 0, sizeof(unsigned int), st);
         if (e != cudaSuccess) return e;
         const bool m = use_masks && w.hitmask;
-        auto kern = disp ? (m ? render_bwd_kernel<true, true> : render_bwd_kernel<false, true>)
-                         : (m ? render_bwd_kernel<true> : render_bwd_kernel<false>);
+        auto kern = disp && eight ? (m ? render_bwd_kernel<true, true, 8> : render_bwd_kernel<false, true, 8>)
+                    : disp        ? (m ? render_bwd_kernel<true, true> : render_bwd_kernel<false, true>)
+                                  : (m ? render_bwd_kernel<true> : render_bwd_kernel<false>);
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         kern<<<persistent_grid(kern, smem, p.total_tiles), TILE_PIX, smem, st>>>(A, p.total_tiles, dL_drgb, dL_dT, T,
                                                                                  last);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    finalize_kernel<<<(p.n + 255) / 256, 256, 0, st>>>(p.n, w.acc, w.cellrec, g, s.sv != nullptr);
+    finalize_kernel<<<(p.n + 255) / 256, 256, 0, st>>>(p.n, w.acc, w.cellrec, g, s.sv != nullptr, scene_sites(s));
     return cudaGetLastError();
 }
 

@@ -10,8 +10,9 @@ that those decisions are close:
 - grazing rays: each cell's sphere is placed so that one pixel ray passes at
   R (1 + eps) from the site, eps from -1e-3 to +1e-4 (|D| -> 0 from both sides);
 - near-parallel planes and faces: pairs of equal-weight sites straddle a
-  pixel ray so that their radical plane contains the ray direction up to a
-  tilt of 0 to 1e-4, and dipole faces are set parallel to the ray the same way;
+  pixel ray so that their radical plane is parallel to the ray up to a tilt
+  of 0 to 1e-4, at 1e-4 to 3e-3 of the pair's half distance from it, and
+  dipole faces are set parallel to the ray the same way;
 - far cameras: cells of radius 5e-4 to 2e-3 seen from 1,000 to 30,000 radii
   through a narrow field of view.
 
@@ -77,7 +78,15 @@ def grazing_scene(cam, rng):
 
 
 def near_parallel_scene(cam, rng):
+    """Pairs of equal-weight sites straddle a pixel ray so that their radical
+    plane (the bisector) is parallel to the ray up to a tilt of 0 to 1e-4 and
+    lies at a small offset from it (1e-4 to 3e-3 of the pair's half
+    distance); one site of each pair has its dipole face set the same way.
+    The offsets are kept well above the float32 rounding of the inputs, so
+    each ray lies on a definite side of every such plane (an offset at the
+    inputs' rounding level would be a tie, which either side may take)."""
     tilts = [0.0, 1e-7, 1e-6, 1e-5, 1e-4]
+    offs = [1e-4, -1e-4, 1e-3, -1e-3, 3e-3, -3e-3]
     pos, R, nrm, off = [], [], [], []
     us = np.linspace(8, cam.width - 9, 4).astype(int)
     vs = np.linspace(8, cam.height - 9, 3).astype(int)
@@ -89,19 +98,20 @@ def near_parallel_scene(cam, rng):
             e = perp(d, rng)
             h = rng.uniform(0.03, 0.06)
             tilt = tilts[k % len(tilts)] * (1 if k % 2 else -1)
-            # equal weights: the radical plane is the bisector, through x0
-            # with normal e + tilt d, i.e. containing the ray up to the tilt
+            # equal weights: the bisector has normal a = e + tilt d and passes
+            # through the pair's midpoint, offs * h from the ray along a
             a = e + tilt * d
             a /= np.linalg.norm(a)
-            for s in (1.0, -1.0):
-                pos.append(x0 + s * h * a)
+            mid = x0 + offs[k % len(offs)] * h * a
+            for sgn in (1.0, -1.0):
+                pos.append(mid + sgn * h * a)
                 rr = rng.uniform(1.4, 2.0) * h
                 R.append(rr)
-                # the pair's faces: one parallel to the ray through x0, one far away
+                # one face parallel to the ray (up to a tilt), offs * R from it; one far away
                 f = perp(d, rng) + tilts[(k + 2) % len(tilts)] * d
                 f /= np.linalg.norm(f)
-                nrm.append(f if s > 0 else rng.normal(size=3))
-                off.append(float(np.dot(f, x0 - pos[-1])) if s > 0 else 10 * rr)
+                nrm.append(f if sgn > 0 else rng.normal(size=3))
+                off.append(float(np.dot(f, x0 - pos[-1])) + offs[(k + 3) % len(offs)] * rr if sgn > 0 else 10 * rr)
             k += 1
     pos = np.array(pos)
     n = len(pos)

@@ -110,7 +110,7 @@ def test_static_entry_extended_face_model(lib):
     result as the workspace path."""
     from paper_2604_24994_gb300 import DeviceScene
     rng = np.random.default_rng(11)
-    sc = f32(cluster_scene(rng, n=40, spread=0.3, r=(0.06, 0.15), tex_std=0.2))
+    sc = f32(cluster_scene(rng, n=30, spread=0.3, r=(0.06, 0.15), tex_std=0.2))   # all-pairs lists: K = 29
     disp = (rng.uniform(-0.2, 0.2, (sc.n, 4)) * sc.R[:, None]).astype(np.float32)
     sites = rng.uniform(-0.5, 0.5, (sc.n, 4, 2)).astype(np.float32)
     ds = DeviceScene.from_numpy(sc, "cuda", disp=disp, sites=sites)
