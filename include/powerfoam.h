@@ -62,10 +62,10 @@ typedef struct {
      * moved by delta = sum_k W_k(u) disp[i][k], with the soft-Voronoi
      * weights of the texture (Eq. svdisp, one-step plane shift); a ray
      * parallel to the face sees no displacement.  pf_render_fwd (also
-     * recording hits), pf_render_fwd_static, the server and pf_render_bwd
-     * (which then adds dL/ddisp into pf_scene_grad.disp) honour it;
-     * pf_render_fwd_contrib and stats passes return PF_ERR_INVALID_ARG for a
-     * displaced scene. */
+     * recording hits), pf_render_fwd_contrib, pf_render_fwd_static, the
+     * server and pf_render_bwd (which then adds dL/ddisp into
+     * pf_scene_grad.disp) honour it; stats passes return PF_ERR_INVALID_ARG
+     * for a displaced scene. */
     const float *disp;
     /* Optional learned detail-site positions [N][4][2] (NULL: the fixed
      * sites (-1/3,-1/3), (1/3,-1/3), (-1/3,1/3), (1/3,1/3); 16-byte
@@ -79,19 +79,19 @@ typedef struct {
      * colours tex): per site a spherical-Voronoi function (Sec. 3.4) of
      * eight (axis xyz, rgb); seen along a ray with direction d the site's
      * colour is sum_j softmax_j(10 a_j.(-d) / |a_j|) rgb_j.  They replace
-     * tex in the colour.  pf_render_fwd, pf_render_fwd_static, the server
-     * and pf_render_bwd (adding dL/dsv into pf_scene_grad.sv) honour them;
-     * pf_render_fwd_contrib and stats passes return PF_ERR_INVALID_ARG for
-     * such a scene. */
+     * tex in the colour.  pf_render_fwd, pf_render_fwd_contrib,
+     * pf_render_fwd_static, the server and pf_render_bwd (adding dL/dsv into
+     * pf_scene_grad.sv) honour them; stats passes return PF_ERR_INVALID_ARG
+     * for such a scene. */
     const float *sv;
     /* Detail sites per face (Sec. 3.4; the paper's main configuration has
      * eight): 0 or 4 for four, 8 for eight.  With eight, tex is [N,24],
      * disp [N][8], sites [N][8][2] and sv [N][8][8][6]; the fixed sites are
      * the 3 x 3 grid of step 1/3 (units of R) without its centre, row by row:
      * (-1,-1), (0,-1), (1,-1), (-1,0), (1,0), (-1,1), (0,1), (1,1) / 3.
-     * pf_render_fwd, pf_render_fwd_static, the server and pf_render_bwd (its
-     * tex, disp, sites and sv gradients have the same shapes) take either;
-     * pf_render_fwd_contrib and stats passes return PF_ERR_INVALID_ARG for
+     * pf_render_fwd, pf_render_fwd_contrib, pf_render_fwd_static, the
+     * server and pf_render_bwd (its tex, disp, sites and sv gradients have the
+     * same shapes) take either; stats passes return PF_ERR_INVALID_ARG for
      * eight. */
     int32_t n_sites;
 } pf_scene;
@@ -243,7 +243,8 @@ pf_status pf_render_fwd(const pf_scene *scene, pf_plan *plan, void *ws, float *r
  *   contrib_normal[i] += sum over rays of T alpha max(nh_i . d, 0)^2   (L_normal)
  * Arrays [N] on the device, zeroed by the caller for a fresh sum.  Segments
  * behind a pixel's early termination (T < 1e-6) are not counted.  Records
- * hits like pf_render_fwd; does not count stats.
+ * hits like pf_render_fwd; does not count stats.  Takes every face model
+ * (displacement, learned or eight sites, view-dependent colours).
  */
 pf_status pf_render_fwd_contrib(const pf_scene *scene, pf_plan *plan, void *ws, float *rgb, float *T, uint32_t *last,
                                 float *contrib_sparse, float *contrib_normal, void *stream);
@@ -259,6 +260,24 @@ pf_status pf_render_fwd_contrib(const pf_scene *scene, pf_plan *plan, void *ws, 
  */
 pf_status pf_render_bwd(const pf_scene *scene, pf_plan *plan, void *ws, const float *dL_drgb, const float *dL_dT,
                         const float *T, const uint32_t *last, const pf_scene_grad *grad, void *stream);
+
+/*
+ * pf_render_bwd for a loss that also holds the per-cell contributions of
+ * pf_render_fwd_contrib (Sec. 4: L_sparse and L_normal are functions of
+ * them; the caller's weights are their derivatives):
+ *   L = L_image(rgb, T) + sum_i (w_sparse[i] sparse_i + w_normal[i] normal_i),
+ *   sparse_i = sum over rays of T alpha,  normal_i = sum of T alpha max(nh_i.d, 0)^2,
+ * the same sums as pf_render_fwd_contrib over the plan's views.  dL_drgb,
+ * dL_dT, T and last as for pf_render_bwd (pass zeros in dL_drgb for the
+ * contributions' gradient alone); w_sparse, w_normal: device [N].  Along a
+ * ray the contributions composite the scalar w_sparse + w_normal
+ * max(nh.d, 0)^2 like a colour channel, so the same replay gives their
+ * gradient for every parameter the segments depend on, plus the normal's
+ * share through max(nh.d, 0)^2.  ADDS into `grad`.  Errors as pf_render_bwd.
+ */
+pf_status pf_render_bwd_contrib(const pf_scene *scene, pf_plan *plan, void *ws, const float *dL_drgb,
+                                const float *dL_dT, const float *T, const uint32_t *last, const float *w_sparse,
+                                const float *w_normal, const pf_scene_grad *grad, void *stream);
 
 /*
  * Connectivity loss of Sec. 4 / appendix (L_connect) over the neighbour

@@ -71,6 +71,7 @@ def _sig(lib):
         "pf_render_fwd_contrib": ([P(Scene), V, V, V, V, V, V, V, V], st),
         "pf_connect": ([P(Scene), V, V, V, V], st),
         "pf_render_bwd": ([P(Scene), V, V, V, V, V, V, P(SceneGrad), V], st),
+        "pf_render_bwd_contrib": ([P(Scene), V, V, V, V, V, V, V, V, P(SceneGrad), V], st),
         "pf_read_bins": ([V, V, V, V, V, V, V], st),
         "pf_neighbours_workspace_bytes": ([I32], U64),
         "pf_build_neighbours": ([V, V, V, I32, I32, V, V, V, V, V, U64, V], st),

@@ -282,9 +282,13 @@ class Renderer:
         self.bin(scene, params, sync=sync)
         return self.render_fwd(scene, params)
 
-    def backward(self, scene: DeviceScene, dL_drgb, dL_dT, T, last, params: dict | None = None, grads=None):
+    def backward(self, scene: DeviceScene, dL_drgb, dL_dT, T, last, params: dict | None = None, grads=None,
+                 contrib_weights=None):
         """pf_render_bwd: returns a dict of gradient tensors (added into
-        `grads` when given)."""
+        `grads` when given).  With contrib_weights=(w_sparse [N], w_normal
+        [N]) it is pf_render_bwd_contrib: the loss also holds
+        sum_i w_sparse[i] sparse_i + w_normal[i] normal_i over the per-cell
+        contributions of render_fwd(contrib=...)."""
         p = scene.params if params is None else params
         keys = PARAMS + tuple(k for k in EXTRA_PARAMS if p.get(k) is not None)
         if grads is None:
@@ -295,9 +299,18 @@ class Renderer:
         dL_drgb = dL_drgb.contiguous().float()
         dL_dT = None if dL_dT is None else dL_dT.contiguous().float()
         P = self.plan
-        check(lib().pf_render_bwd(C.byref(scene.struct(params)), P.handle, P.ws_ptr, dL_drgb.data_ptr(),
-                                  ptr(dL_dT), T.data_ptr(), last.data_ptr(), C.byref(g), _stream()),
-              "pf_render_bwd")
+        if contrib_weights is None:
+            check(lib().pf_render_bwd(C.byref(scene.struct(params)), P.handle, P.ws_ptr, dL_drgb.data_ptr(),
+                                      ptr(dL_dT), T.data_ptr(), last.data_ptr(), C.byref(g), _stream()),
+                  "pf_render_bwd")
+        else:
+            ws_, wn_ = (w.contiguous().float() for w in contrib_weights)
+            for t in (ws_, wn_):
+                if not (t.is_cuda and t.numel() == P.n):
+                    raise ValueError("contribution weights must be float32 CUDA tensors of N cells")
+            check(lib().pf_render_bwd_contrib(C.byref(scene.struct(params)), P.handle, P.ws_ptr, dL_drgb.data_ptr(),
+                                              ptr(dL_dT), T.data_ptr(), last.data_ptr(), ws_.data_ptr(),
+                                              wn_.data_ptr(), C.byref(g), _stream()), "pf_render_bwd_contrib")
         return grads
 
     def stats(self):

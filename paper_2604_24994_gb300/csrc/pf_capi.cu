@@ -411,10 +411,6 @@ pf_status pf_render_fwd_contrib(const pf_scene *scene, pf_plan *p, void *ws, flo
         set_error("pf_render_fwd_contrib: null contribution array");
         return PF_ERR_INVALID_ARG;
     }
-    if (ext_face(*scene) && p->n > 0) {
-        set_error("pf_render_fwd_contrib: not available for an extended face model");
-        return PF_ERR_INVALID_ARG;
-    }
     WS w = p->ws(ws);
     const bool record = p->record_hits && w.hitmask != nullptr;
     pf_status s = cuda_status(launch_render_fwd(*scene, *p, w, rgb, T, last, record, (cudaStream_t)stream,
@@ -424,30 +420,48 @@ pf_status pf_render_fwd_contrib(const pf_scene *scene, pf_plan *p, void *ws, flo
     return s;
 }
 
-pf_status pf_render_bwd(const pf_scene *scene, pf_plan *p, void *ws, const float *dL_drgb, const float *dL_dT,
-                        const float *T, const uint32_t *last, const pf_scene_grad *g, void *stream) {
+static pf_status render_bwd(const char *who, const pf_scene *scene, pf_plan *p, void *ws, const float *dL_drgb,
+                            const float *dL_dT, const float *T, const uint32_t *last, const float *w_sparse,
+                            const float *w_normal, const pf_scene_grad *g, void *stream) {
     g_err[0] = 0;
     if (!p || !ws || !scene_ok(scene, p) || !dL_drgb || !T || !last || !g) return PF_ERR_INVALID_ARG;
     if (p->n > 0 && (!g->pos || !g->w || !g->R || !g->sigma || !g->rgb || !g->normal || !g->offset || !g->tex)) {
-        set_error("pf_render_bwd: null gradient pointer");
+        set_error("%s: null gradient pointer", who);
         return PF_ERR_INVALID_ARG;
     }
     if (scene->disp && p->n > 0 && !g->disp) {
-        set_error("pf_render_bwd: a displaced scene needs grad->disp");
+        set_error("%s: a displaced scene needs grad->disp", who);
         return PF_ERR_INVALID_ARG;
     }
     if (scene->sites && p->n > 0 && !g->sites) {
-        set_error("pf_render_bwd: learned sites need grad->sites");
+        set_error("%s: learned sites need grad->sites", who);
         return PF_ERR_INVALID_ARG;
     }
     if (scene->sv && p->n > 0 && !g->sv) {
-        set_error("pf_render_bwd: view-dependent site colours need grad->sv");
+        set_error("%s: view-dependent site colours need grad->sv", who);
         return PF_ERR_INVALID_ARG;
     }
     WS w = p->ws(ws);
-    return cuda_status(
-        launch_render_bwd(*scene, *p, w, dL_drgb, dL_dT, T, last, *g, p->masks_valid, (cudaStream_t)stream),
-        "pf_render_bwd");
+    return cuda_status(launch_render_bwd(*scene, *p, w, dL_drgb, dL_dT, T, last, *g, p->masks_valid,
+                                         (cudaStream_t)stream, w_sparse, w_normal),
+                       who);
+}
+
+pf_status pf_render_bwd(const pf_scene *scene, pf_plan *p, void *ws, const float *dL_drgb, const float *dL_dT,
+                        const float *T, const uint32_t *last, const pf_scene_grad *g, void *stream) {
+    return render_bwd("pf_render_bwd", scene, p, ws, dL_drgb, dL_dT, T, last, nullptr, nullptr, g, stream);
+}
+
+pf_status pf_render_bwd_contrib(const pf_scene *scene, pf_plan *p, void *ws, const float *dL_drgb,
+                                const float *dL_dT, const float *T, const uint32_t *last, const float *w_sparse,
+                                const float *w_normal, const pf_scene_grad *g, void *stream) {
+    if (p && p->n > 0 && (!w_sparse || !w_normal)) {
+        g_err[0] = 0;
+        set_error("pf_render_bwd_contrib: null contribution weights");
+        return PF_ERR_INVALID_ARG;
+    }
+    return render_bwd("pf_render_bwd_contrib", scene, p, ws, dL_drgb, dL_dT, T, last, w_sparse, w_normal, g,
+                      stream);
 }
 
 pf_status pf_connect(const pf_scene *scene, float *loss, float *grad_pos, float *grad_R, void *stream) {

@@ -199,6 +199,7 @@ cudaError_t launch_render_fwd(const pf_scene &s, const Plan &p, const WS &w, flo
                               float *contrib_normal = nullptr);
 cudaError_t launch_render_bwd(const pf_scene &s, const Plan &p, const WS &w, const float *dL_drgb,
                               const float *dL_dT, const float *T, const uint32_t *last, const pf_scene_grad &g,
-                              bool use_masks, cudaStream_t st);
+                              bool use_masks, cudaStream_t st, const float *w_sparse = nullptr,
+                              const float *w_normal = nullptr);
 
 }  // namespace pf

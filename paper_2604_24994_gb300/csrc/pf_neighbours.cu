@@ -632,6 +632,10 @@ struct CcAcc {
     double loss = 0.0, gx = 0.0, gy = 0.0, gz = 0.0, gr = 0.0;
     unsigned int pairs = 0;
     __device__ __forceinline__ void pair(float4 pi, float4 pj) {
+        // float screen first: pairs farther apart than R_i + R_j by more than
+        // the screen's rounding (far below its 1e-5 relative margin) add nothing
+        const float fx = pj.x - pi.x, fy = pj.y - pi.y, fz = pj.z - pi.z, rs = pi.w + pj.w;
+        if (fx * fx + fy * fy + fz * fz > rs * rs * (1.0f + 1e-5f) + 1e-30f) return;
         const double dx = (double)pj.x - (double)pi.x, dy = (double)pj.y - (double)pi.y,
                      dz = (double)pj.z - (double)pi.z;
         const double d = sqrt(dx * dx + dy * dy + dz * dz);

@@ -763,6 +763,8 @@ struct RenderArgs {
     float *gsv;             // [N][S][8][6] their gradient, or null
     const float *tex8;      // eight sites: the texture [N][24] (four: in the cell record), else null
     float *gtex8;           // eight sites: its gradient (the backward adds into it), else null
+    const float *w_sparse;  // [N] upstream weights of the contributions' adjoint (pf_render_bwd_contrib), or null
+    const float *w_normal;  // [N]
 };
 
 // Hit masks: one 32-bit word per (warp of the tile, batch, pixel of the
@@ -1151,7 +1153,12 @@ __device__ __forceinline__ void route_end(float gt, int kind, float s, float den
 
 // MASKS: replay only the (cell, lane) pairs the forward recorded as hits
 // (the hit masks of the current bins); otherwise re-test every listed cell.
-template <bool MASKS, bool EXT = false, int NS = 4>
+// CONTRIB: also the adjoint of sum_i (w_sparse[i] sparse_i + w_normal[i]
+// normal_i), the per-cell contributions of pf_render_fwd_contrib (Sec. 4's
+// L_sparse / L_normal): along a ray they composite the scalar
+// q_k = w_sparse + w_normal max(nh.d, 0)^2 like a fourth colour channel whose
+// upstream gradient is 1, and q_k itself moves with the unit normal.
+template <bool MASKS, bool EXT = false, int NS = 4, bool CONTRIB = false>
 __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, int64_t n_tiles,
                                                                  const float *__restrict__ dL_drgb,
                                                                  const float *__restrict__ dL_dT,
@@ -1209,6 +1216,7 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
     const int maxlast = s_maxlast;
 
     float Tafter = Tf;
+    float accQ = 0.f;  // CONTRIB: the contribution scalar composited behind the current cell
     float3 accC = f3(0.f, 0.f, 0.f);
     float *acc = A.w.acc;
     const uint32_t *list = A.w.inst_sorted + s;
@@ -1312,6 +1320,12 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
                 // x = sigma l, alpha = 1 - e^-x:  dL/dx = g.(T_{k+1} c - S_k) - gT T_final
                 float dLdx = g.x * (Tafter * c.x - accC.x) + g.y * (Tafter * c.y - accC.y) +
                              g.z * (Tafter * c.z - accC.z) - gT * Tf;
+                float qk = 0.f, ndq = 0.f;
+                if (CONTRIB) {
+                    ndq = dot3(f3(cr[CR_N], cr[CR_N + 1], cr[CR_N + 2]), ray.dh);
+                    qk = __ldg(A.w_sparse + cell) + __ldg(A.w_normal + cell) * (ndq > 0.0f ? ndq * ndq : 0.0f);
+                    dLdx += Tafter * qk - accQ;
+                }
                 if (xr > X_CAP || !hit) dLdx = 0.f;
                 vv[G_SIG] = dLdx * l;
                 const float gl = dLdx * sig;
@@ -1437,6 +1451,12 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
                 vv[G_P + 2] = 0.f;
                 vv[G_W] = 0.f;
                 vv[G_OFF] = 0.f;
+                if (CONTRIB && ndq > 0.0f) {  // d(max(nh.d, 0)^2)/d nh = 2 (nh.d) d, weighted T alpha w_normal
+                    const float gq = wc * __ldg(A.w_normal + cell) * 2.0f * ndq;
+                    vv[G_N] = fmaf(gq, ray.dh.x, vv[G_N]);
+                    vv[G_N + 1] = fmaf(gq, ray.dh.y, vv[G_N + 1]);
+                    vv[G_N + 2] = fmaf(gq, ray.dh.z, vv[G_N + 2]);
+                }
                 // the texture point moves with its segment end: y_s = m + t_s d
                 float3 gm = gy;
                 const float gts = dot3(gy, ray.dh);
@@ -1534,6 +1554,7 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
                 accC.x = fmaf(wc, c.x, accC.x);
                 accC.y = fmaf(wc, c.y, accC.y);
                 accC.z = fmaf(wc, c.z, accC.z);
+                if (CONTRIB) accQ = fmaf(wc, qk, accQ);
                 if (hit) Tafter = Tbefore;
             }
             // neighbour gradients: fold into the warp sum when the warp agrees on j
@@ -1642,6 +1663,8 @@ static RenderArgs make_args(const pf_scene &s, const Plan &p, const WS &w) {
     A.gsv = nullptr;
     A.tex8 = scene_sites(s) == 8 ? s.tex : nullptr;
     A.gtex8 = nullptr;
+    A.w_sparse = nullptr;
+    A.w_normal = nullptr;
     return A;
 }
 
@@ -1669,13 +1692,19 @@ cudaError_t launch_render_fwd(const pf_scene &s, const Plan &p, const WS &w, flo
     const bool contrib = contrib_sparse != nullptr;
     const bool disp = ext_face(s);  // an extended face model
     const bool eight = scene_sites(s) == 8;
-    if (disp && (contrib || p.stats)) return cudaErrorNotSupported;  // the C API refuses these first
+    if (disp && p.stats) return cudaErrorNotSupported;  // the C API refuses this first
     const size_t smem = disp ? stage_bytes(p.k, false, true, eight ? 12 : 3) : fwd_smem(p.k);
     cudaError_t e = cudaMemsetAsync(&w.counters->q_fwd, 0, sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
-    auto k = disp && eight ? (record ? render_fwd_kernel<false, true, false, true, 8>
-                                     : render_fwd_kernel<false, false, false, true, 8>)
-             : disp    ? (record ? render_fwd_kernel<false, true, false, true> : render_fwd_kernel<false, false, false, true>)
+    auto k = disp && eight
+                 ? (contrib ? (record ? render_fwd_kernel<false, true, true, true, 8>
+                                      : render_fwd_kernel<false, false, true, true, 8>)
+                            : (record ? render_fwd_kernel<false, true, false, true, 8>
+                                      : render_fwd_kernel<false, false, false, true, 8>))
+             : disp ? (contrib ? (record ? render_fwd_kernel<false, true, true, true>
+                                         : render_fwd_kernel<false, false, true, true>)
+                               : (record ? render_fwd_kernel<false, true, false, true>
+                                         : render_fwd_kernel<false, false, false, true>))
              : contrib ? (record ? render_fwd_kernel<false, true, true> : render_fwd_kernel<false, false, true>)
              : p.stats ? render_fwd_kernel<true, false, false>
                        : (record ? render_fwd_kernel<false, true, false> : render_fwd_kernel<false, false, false>);
@@ -1686,7 +1715,7 @@ cudaError_t launch_render_fwd(const pf_scene &s, const Plan &p, const WS &w, flo
 
 cudaError_t launch_render_bwd(const pf_scene &s, const Plan &p, const WS &w, const float *dL_drgb,
                               const float *dL_dT, const float *T, const uint32_t *last, const pf_scene_grad &g,
-                              bool use_masks, cudaStream_t st) {
+                              bool use_masks, cudaStream_t st, const float *w_sparse, const float *w_normal) {
     if (p.n == 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(w.acc, 0, sizeof(float) * ACC_F * (size_t)p.n, st);
     if (e != cudaSuccess) return e;
@@ -1702,9 +1731,16 @@ cudaError_t launch_render_bwd(const pf_scene &s, const Plan &p, const WS &w, con
         e = cudaMemsetAsync(&w.counters->q_bwd, 0, sizeof(unsigned int), st);
         if (e != cudaSuccess) return e;
         const bool m = use_masks && w.hitmask;
-        auto kern = disp && eight ? (m ? render_bwd_kernel<true, true, 8> : render_bwd_kernel<false, true, 8>)
-                    : disp        ? (m ? render_bwd_kernel<true, true> : render_bwd_kernel<false, true>)
-                                  : (m ? render_bwd_kernel<true> : render_bwd_kernel<false>);
+        const bool cq = w_sparse != nullptr;  // the contributions' adjoint too
+        A.w_sparse = w_sparse;
+        A.w_normal = w_normal;
+        auto kern =
+            cq ? (disp && eight ? (m ? render_bwd_kernel<true, true, 8, true> : render_bwd_kernel<false, true, 8, true>)
+                  : disp        ? (m ? render_bwd_kernel<true, true, 4, true> : render_bwd_kernel<false, true, 4, true>)
+                                : (m ? render_bwd_kernel<true, false, 4, true> : render_bwd_kernel<false, false, 4, true>))
+               : (disp && eight ? (m ? render_bwd_kernel<true, true, 8> : render_bwd_kernel<false, true, 8>)
+                  : disp        ? (m ? render_bwd_kernel<true, true> : render_bwd_kernel<false, true>)
+                                : (m ? render_bwd_kernel<true> : render_bwd_kernel<false>));
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         kern<<<persistent_grid(kern, smem, p.total_tiles), TILE_PIX, smem, st>>>(A, p.total_tiles, dL_drgb, dL_dT, T,
                                                                                  last);

@@ -152,3 +152,93 @@ def test_connect_cech_degenerate_inputs():
         l, gp, gR = cech_gpu(pos, R)
         if len(R):
             check_cech(pos, R, l, gp, gR)
+
+
+def ext_scene(kind, seed):
+    """A clipping cluster with an extended face model: four sites with
+    displacement and learned positions, or eight sites with displacement."""
+    rng = np.random.default_rng(seed)
+    sc = f32(cluster_scene(rng, n=40, spread=0.15, r=(0.06, 0.12), tex_std=0.2))
+    if kind is None:
+        return sc, {}
+    ns = 8 if kind == "eight" else 4
+    if ns == 8:
+        sc.tex = rng.normal(0, 0.2, (sc.n, 24)).astype(np.float32)
+    disp = (rng.uniform(-0.3, 0.3, (sc.n, ns)) * sc.R[:, None]).astype(np.float32)
+    extra = {"disp": disp}
+    if ns == 4:
+        base = np.array([[-1, -1], [1, -1], [-1, 1], [1, 1]], np.float64) / 3.0
+        extra["sites"] = (base[None] + rng.uniform(-0.2, 0.2, (sc.n, 4, 2))).astype(np.float32)
+    return sc, extra
+
+
+@pytest.mark.parametrize("kind", ["disp4", "eight"])
+def test_contributions_extended_face_model(kind):
+    """pf_render_fwd_contrib on displaced faces with learned sites, and with
+    eight detail sites, against oracle.contrib (Sec. 4's per-cell terms)."""
+    import torch
+    from paper_2604_24994_gb300 import DeviceScene, Renderer
+    sc, extra = ext_scene(kind, 41)
+    cams = [inputs.look_at((0.8, 0.3, 0.2), 40, 32, fov_y_deg=45), inputs.look_at((-0.6, 0.4, 0.5), 24, 36)]
+    ds = DeviceScene.from_numpy(sc, "cuda", **extra)
+    r = Renderer(ds.n, ds.k, cams)
+    r.bin(ds)
+    cs = torch.zeros(ds.n, device="cuda")
+    cn = torch.zeros(ds.n, device="cuda")
+    rgb, T, last = r.render_fwd(ds, contrib=(cs, cn))
+    rgb2, T2, last2 = r.render_fwd(ds)
+    torch.cuda.synchronize()
+    assert torch.equal(rgb, rgb2) and torch.equal(T, T2) and torch.equal(last, last2)
+    orc = oracle.Oracle(sc, **extra)
+    sp = sum(orc.contrib(c)[0] for c in cams)
+    nm = sum(orc.contrib(c)[1] for c in cams)
+    assert (sp > 0).sum() > 10
+    check(cs.double().cpu().numpy(), sp, "sparse")
+    check(cn.double().cpu().numpy(), nm, "normal")
+
+
+@pytest.mark.parametrize("with_masks,kind", [(True, None), (False, None), (True, "disp4"), (False, "eight"),
+                                             (True, "eight")])
+def test_contribution_adjoint_matches_oracle(with_masks, kind):
+    """pf_render_bwd_contrib: the gradient of an image loss plus
+    sum_i w_sparse[i] sparse_i + w_normal[i] normal_i (the contributions of
+    L_sparse / L_normal) against the FP64 adjoints orc render_grad +
+    contrib_grad, 1e-3 relative L2 per tensor, replaying recorded hits or
+    re-clipping; also the contributions' gradient alone (zero image
+    gradient)."""
+    import torch
+    from paper_2604_24994_gb300 import DeviceScene, Renderer
+    from tests.gpu_util import rel_l2
+    sc, extra = ext_scene(kind, 43)
+    rng = np.random.default_rng(44)
+    cams = [inputs.look_at((0.7, 0.2, 0.1), 48, 40, fov_y_deg=40), inputs.look_at((-0.5, 0.5, 0.3), 33, 21)]
+    npx = sum(c.n_pixels for c in cams)
+    ws = rng.normal(size=sc.n)
+    wn = rng.normal(size=sc.n)
+    ds = DeviceScene.from_numpy(sc, "cuda", **extra)
+    orc = oracle.Oracle(sc, **extra)
+    for image in (True, False):
+        gC = rng.normal(size=(npx, 3)) if image else np.zeros((npx, 3))
+        gT = rng.normal(size=npx) if image else np.zeros(npx)
+        r = Renderer(ds.n, ds.k, cams, hit_records=with_masks)
+        rgb, T, last = r.forward(ds)
+        g = r.backward(ds, torch.from_numpy(gC).float().cuda(), torch.from_numpy(gT).float().cuda(), T, last,
+                       contrib_weights=(torch.from_numpy(ws).float().cuda(), torch.from_numpy(wn).float().cuda()))
+        torch.cuda.synchronize()
+        G = {k: v.cpu().numpy().astype(np.float64) for k, v in g.items()}
+        Go = None
+        o = 0
+        for cam in cams:
+            gg = orc.contrib_grad(cam, ws, wn)
+            if image:
+                gi = orc.render_grad(cam, gC[o:o + cam.n_pixels], gT[o:o + cam.n_pixels])
+                gg = {k: gg[k] + gi[k] for k in gg}
+            Go = gg if Go is None else {k: Go[k] + gg[k] for k in gg}
+            o += cam.n_pixels
+        for k in Go:
+            b = np.asarray(Go[k]).reshape(-1)
+            a = G[k].reshape(-1)
+            if np.linalg.norm(b) == 0:
+                assert np.abs(a).max() < 1e-6, k
+                continue
+            assert rel_l2(a, b) < 1e-3, (k, image, rel_l2(a, b))
