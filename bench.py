@@ -627,7 +627,7 @@ def serve_bench(args, local: int):
                        f"{args.serve_budget_gb:.0f} GB tile/sort budget",
            "scene_generation_s": round(gen_s, 1)}
     keep = ("p50_ms", "p99_ms", "mean_ms", "requests_per_s", "mpix_per_s", "mean_batch_views", "completed",
-            "rejected", "graph_replays")
+            "rejected", "batches", "graph_replays", "graph_updates")
     for name, opts in (("batched", batched), ("plain", plain)):
         rep_open = run(opts, True)
         rep_sat = run(opts, False)

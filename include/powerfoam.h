@@ -341,8 +341,9 @@ pf_status pf_read_bins(pf_plan *plan, void *ws, uint32_t *tile_start, uint32_t *
  * up to max_batch_views.  A batch is projected, binned and rendered as one
  * multi-view plan with one persistent render launch; requests that arrive
  * while other batches run are admitted as slots free up, so their work
- * overlaps on the GPU.  With use_graphs the launch sequence of each batch
- * shape is captured once per slot and replayed.  Results are the same as
+ * overlaps on the GPU.  With use_graphs each batch's launch sequence runs
+ * as a CUDA graph: a slot keeps one executable graph per view count, replays
+ * it for a repeated batch shape and updates it in place for a new one.  Results are the same as
  * rendering each view alone with pf_render_fwd.
  *
  * The scene pointers and the pool must stay valid until pf_serve_destroy.
@@ -354,15 +355,19 @@ pf_status pf_read_bins(pf_plan *plan, void *ws, uint32_t *tile_start, uint32_t *
 typedef struct {
     int32_t max_batch_views; /* views per batch, 1..256 */
     int32_t slots;           /* batches in flight, 1..16 */
-    int32_t use_graphs;      /* capture and replay each batch shape */
+    int32_t use_graphs;      /* run each batch as a CUDA graph (replayed or updated per slot) */
     int32_t max_queue;       /* queued requests before submit returns PF_ERR_BUSY */
 } pf_serve_opts;
 
 typedef struct {
+    /* graph_replays: batches that replayed their slot's graph as it was (the
+     * same batch shape); graph_updates: batches written into an existing
+     * graph of their view count (cudaGraphExecUpdate, no instantiation) */
     uint64_t submitted, completed, rejected, batches, graph_replays, requeued;
     double p50_ms, p99_ms, mean_ms, max_ms; /* submit -> result written */
     double elapsed_s;                        /* first submit -> last completion */
     double requests_per_s, mpix_per_s, mean_batch_views;
+    uint64_t graph_updates;
 } pf_serve_report;
 
 typedef struct pf_server pf_server;

@@ -11,7 +11,9 @@
 // render launch whose CTAs take tiles of every view from a shared queue;
 // each view writes straight into its request's output buffers.  Batches on
 // different slots overlap on the GPU.  With use_graphs, the launch sequence
-// of each (slot, batch shape) is captured once and replayed; the cameras and
+// of a batch is captured into a CUDA graph: each slot keeps one executable
+// graph per view count, replayed as it is for a repeated batch shape and
+// updated in place (cudaGraphExecUpdate) for a new one; the cameras and
 // output pointers it reads live in the slot's pinned buffer.  Completion is
 // signalled by a host function at the end of the batch's stream.
 //
@@ -67,7 +69,8 @@ struct Slot {
     std::atomic<int> finished{0};
     double t_finished = 0;
     bool busy = false;
-    std::map<std::string, cudaGraphExec_t> graphs;
+    // one executable graph per view count, and the batch shape it holds now
+    std::map<int, std::pair<std::string, cudaGraphExec_t>> graphs;
 };
 
 struct Server {
@@ -90,7 +93,8 @@ struct Server {
     double t_stop = -1;
     // statistics
     std::vector<double> lat;
-    uint64_t submitted = 0, completed = 0, rejected = 0, batches = 0, batch_views = 0, replays = 0, requeued = 0;
+    uint64_t submitted = 0, completed = 0, rejected = 0, batches = 0, batch_views = 0, replays = 0, requeued = 0,
+             updates = 0;
     double pixels_done = 0, t_first = -1, t_last = 0;
 };
 
@@ -175,29 +179,48 @@ static cudaError_t launch_batch(Server &S, Slot &sl, uint64_t cap) {
     }
     sl.finished.store(0);
     if (!S.opts.use_graphs) return enqueue_batch(S, sl, p);
+    // Each slot keeps one executable graph per view count.  A batch of the
+    // shape (resolutions in order, capacity) that graph holds replays it as
+    // it is.  A batch of another shape with the same number of views has the
+    // same launch sequence with other grid sizes and arguments: it is
+    // captured (cheap) and written into that executable graph with
+    // cudaGraphExecUpdate, with no new instantiation; only a first batch of
+    // its view count, or an update the runtime refuses, instantiates.
     const std::string key = signature(sl.batch, cap);
-    auto it = sl.graphs.find(key);
-    if (it == sl.graphs.end()) {
-        cudaGraph_t g = nullptr;
-        cudaGraphExec_t ex = nullptr;
-        cudaError_t e = cudaStreamBeginCapture(sl.stream, cudaStreamCaptureModeThreadLocal);
-        if (e != cudaSuccess) return e;
-        e = enqueue_batch(S, sl, p);
-        cudaError_t e2 = cudaStreamEndCapture(sl.stream, &g);
-        if (e != cudaSuccess) return e;
-        if (e2 != cudaSuccess) return e2;
-        e = cudaGraphInstantiate(&ex, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) return e;
-        if (sl.graphs.size() >= 64) {  // bounded cache
-            cudaGraphExecDestroy(sl.graphs.begin()->second);
-            sl.graphs.erase(sl.graphs.begin());
-        }
-        it = sl.graphs.emplace(key, ex).first;
-    } else {
+    const int nv = (int)sl.batch.size();
+    auto it = sl.graphs.find(nv);
+    if (it != sl.graphs.end() && it->second.first == key) {
         S.replays++;
+        return cudaGraphLaunch(it->second.second, sl.stream);
     }
-    return cudaGraphLaunch(it->second, sl.stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(sl.stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    e = enqueue_batch(S, sl, p);
+    cudaError_t e2 = cudaStreamEndCapture(sl.stream, &g);
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return e;
+    }
+    if (e2 != cudaSuccess) return e2;
+    if (it != sl.graphs.end()) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(it->second.second, g, &info) == cudaSuccess) {
+            cudaGraphDestroy(g);
+            it->second.first = key;
+            S.updates++;
+            return cudaGraphLaunch(it->second.second, sl.stream);
+        }
+        cudaGetLastError();  // a refused update leaves no error behind
+        cudaGraphExecDestroy(it->second.second);
+        sl.graphs.erase(it);
+    }
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return e;
+    sl.graphs[nv] = std::make_pair(key, ex);
+    return cudaGraphLaunch(ex, sl.stream);
 }
 
 // Complete finished batches (lock held).
@@ -448,6 +471,7 @@ pf_status pf_serve_stats(pf_server *S, pf_serve_report *out) {
     out->rejected = S->rejected;
     out->batches = S->batches;
     out->graph_replays = S->replays;
+    out->graph_updates = S->updates;
     out->requeued = S->requeued;
     out->mean_batch_views = S->batches ? (double)S->batch_views / S->batches : 0;
     if (!S->lat.empty()) {
@@ -474,6 +498,7 @@ pf_status pf_serve_reset_stats(pf_server *S) {
     std::lock_guard<std::mutex> lk(S->mu);
     S->lat.clear();
     S->submitted = S->completed = S->rejected = S->batches = S->batch_views = S->replays = S->requeued = 0;
+    S->updates = 0;
     S->pixels_done = 0;
     S->t_first = -1;
     S->t_last = 0;
@@ -495,7 +520,7 @@ void pf_serve_destroy(pf_server *S) {
     }
     for (Slot *sl : S->slots) {
         if (sl->stream) cudaStreamSynchronize(sl->stream);
-        for (auto &kv : sl->graphs) cudaGraphExecDestroy(kv.second);
+        for (auto &kv : sl->graphs) cudaGraphExecDestroy(kv.second.second);
         if (sl->stream) cudaStreamDestroy(sl->stream);
         if (sl->views_pinned) cudaFreeHost(sl->views_pinned);
         if (sl->ctr_pinned) cudaFreeHost(sl->ctr_pinned);

@@ -20,7 +20,7 @@ class ServeReport(C.Structure):
     _fields_ = [(k, C.c_uint64) for k in ("submitted", "completed", "rejected", "batches", "graph_replays",
                                            "requeued")] + \
                [(k, C.c_double) for k in ("p50_ms", "p99_ms", "mean_ms", "max_ms", "elapsed_s", "requests_per_s",
-                                          "mpix_per_s", "mean_batch_views")]
+                                          "mpix_per_s", "mean_batch_views")] + [("graph_updates", C.c_uint64)]
 
 
 def _sig():

@@ -1,6 +1,7 @@
-"""Face displacement (Eq. svdisp, one-step plane shift) and learned detail-site
-positions (Sec. 3.4) on the GPU: forward and backward against the FP64
-oracle, and the call that refuses such a scene."""
+"""Face displacement (Eq. svdisp, one-step plane shift), learned detail-site
+positions, spherical-Voronoi site colours and eight detail sites per face
+(Sec. 3.4) on the GPU: forward and backward against the FP64 oracle, and
+the call that refuses such a scene (a counting pass)."""
 import numpy as np
 import pytest
 
@@ -124,15 +125,18 @@ def test_displaced_backward_matches_the_oracle(with_masks, with_disp, with_sites
             assert rel_l2(G[k].reshape(-1), Go[k].reshape(-1)) < 1e-3, k
 
 
-def test_displaced_scene_refuses_contributions(tiny):
-    import torch
+def test_displaced_scene_refuses_a_stats_pass(tiny):
+    """The work counters cover the plain face model only: a counting forward
+    of a displaced scene is refused on the host (contributions are not:
+    tests/test_gpu_contrib.py checks them for every face model)."""
     from paper_2604_24994_gb300 import DeviceScene, Renderer, _lib
     sc, cam = tiny
     ds = DeviceScene.from_numpy(sc, "cuda", disp=random_disp(sc, 0.2, 3))
     r = Renderer(ds.n, ds.k, [cam])
-    r.forward(ds)
+    r.bin(ds)
+    r.enable_stats(True)
     with pytest.raises(_lib.PFError) as e:
-        r.render_fwd(ds, contrib=(torch.zeros(ds.n, device="cuda"), torch.zeros(ds.n, device="cuda")))
+        r.render_fwd(ds)
     assert e.value.status == _lib.PF_ERR_INVALID_ARG
 
 

@@ -67,10 +67,22 @@ def test_results_same_alone_and_in_the_mix(scene, graphs):
             srv.wait(srv.submit(cam, rgb, T), 60000)
             rgb0, T0 = alone(ds, cam)
             assert np.abs(rgb.cpu().numpy() - rgb0).max() < RGB_TOL
+    # the same view again and again, one at a time: an exact replay of the slot's graph
+    for rnd in range(3):
+        rgb = torch.empty((cams[0].n_pixels, 3), device="cuda")
+        T = torch.empty(cams[0].n_pixels, device="cuda")
+        srv.wait(srv.submit(cams[0], rgb, T), 60000)
+        rgb0, T0 = alone(ds, cams[0])
+        assert np.abs(rgb.cpu().numpy() - rgb0).max() < RGB_TOL
     rep = srv.report()
-    assert rep["completed"] == 2 * len(cams) + 6
+    assert rep["completed"] == 2 * len(cams) + 9
     if graphs:
-        assert rep["graph_replays"] > 0
+        # new shapes of a seen view count update the slot's graph in place; repeats replay it
+        assert rep["graph_updates"] > 0 and rep["graph_replays"] > 0
+        # only the first batch of each view count on each slot instantiates (2 slots x up to 4 views)
+        assert rep["graph_updates"] + rep["graph_replays"] >= rep["batches"] - 2 * 4
+    else:
+        assert rep["graph_updates"] == 0 and rep["graph_replays"] == 0
     srv.close()
 
 
