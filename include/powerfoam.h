@@ -144,6 +144,10 @@ typedef struct {
     uint64_t warp_candidates;
     uint64_t warp_passes;
     uint64_t warp_hits;
+    /* nonzero if a bounded wait of the forward's shared-memory pipeline ran
+     * out since the last pf_bin_sort (the image is then incomplete); always
+     * 0 in correct operation, read whether or not stats are enabled */
+    uint64_t wait_errors;
 } pf_stats;
 
 const char *pf_status_string(pf_status s);

@@ -46,7 +46,7 @@ class SceneGrad(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [(k, C.c_uint64) for k in ("instances", "candidates", "hits", "planes", "refined", "sphere_pass",
-                                                     "warp_candidates", "warp_passes", "warp_hits")]
+                                                     "warp_candidates", "warp_passes", "warp_hits", "wait_errors")]
 
 
 def _sig(lib):

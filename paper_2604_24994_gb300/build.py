@@ -18,8 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpowerfoam.so")
-SOURCES = ["pf_capi.cu", "pf_geometry.cu", "pf_binsort.cu", "pf_render.cu", "pf_static.cu", "pf_serve.cu",
-           "pf_neighbours.cu"]
+SOURCES = ["pf_capi.cu", "pf_geometry.cu", "pf_binsort.cu", "pf_render.cu", "pf_render_pipe.cu", "pf_static.cu",
+           "pf_serve.cu", "pf_neighbours.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler",
               "-fPIC,-ffp-contract=off,-O2", "-I" + INCLUDE]

@@ -342,6 +342,7 @@ pf_status pf_plan_read_stats(pf_plan *p, void *ws, pf_stats *out, void *stream) 
     out->warp_candidates = c.stats[5];
     out->warp_passes = c.stats[6];
     out->warp_hits = c.stats[7];
+    out->wait_errors = c.wait_errors;
     return PF_OK;
 }
 

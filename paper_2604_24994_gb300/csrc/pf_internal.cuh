@@ -93,7 +93,7 @@ struct Counters {
     unsigned int overflow;          // 1 if total_inst > capacity
     unsigned int q_fwd;             // next entry of tile_order for the forward's CTAs
     unsigned int q_bwd;             // same for the backward
-    unsigned int pad;
+    unsigned int wait_errors;       // nonzero if a bounded wait of the pipelined forward ran out
     unsigned long long stats[8];    // pf_stats fields after `instances`
 };
 
@@ -197,6 +197,11 @@ cudaError_t launch_bin_sort(const Plan &p, const WS &w, cudaStream_t st);
 cudaError_t launch_render_fwd(const pf_scene &s, const Plan &p, const WS &w, float *rgb, float *T, uint32_t *last,
                               bool record, cudaStream_t st, float *contrib_sparse = nullptr,
                               float *contrib_normal = nullptr);
+// The pipelined forward (pf_render_pipe.cu): the plain face model without
+// hit recording, stats or contributions.
+bool pipe_applies(const pf_scene &s, const Plan &p, bool record, bool contrib);
+cudaError_t launch_render_fwd_pipe(const pf_scene &s, const Plan &p, const WS &w, float *rgb, float *T,
+                                   uint32_t *last, cudaStream_t st);
 cudaError_t launch_render_bwd(const pf_scene &s, const Plan &p, const WS &w, const float *dL_drgb,
                               const float *dL_dT, const float *T, const uint32_t *last, const pf_scene_grad &g,
                               bool use_masks, cudaStream_t st, const float *w_sparse = nullptr,

@@ -12,7 +12,9 @@ import pytest
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(ROOT, "paper_2604_24994_gb300", "csrc")
-UNITS = ["pf_capi", "pf_geometry", "pf_binsort", "pf_render", "pf_static", "pf_serve", "pf_neighbours"]
+from paper_2604_24994_gb300.build import SOURCES  # noqa: E402  (the library's translation units)
+
+UNITS = [u[:-3] for u in SOURCES]
 
 
 def test_capi_host_code_is_clean_under_asan(tmp_path):

@@ -1,0 +1,76 @@
+"""The pipelined forward (the plain face model without hit recording: the
+benchmark's forward step, the server and the static entry point) against
+the batch-staged forward that records hits, which the other parity tests pin
+to the FP64 oracle: the same per-pixel arithmetic in the same list order, so
+rgb, T and last must agree bit for bit.  The scenes cover early termination
+(near-opaque cells), batches cut short by the stage's plane budget (cells with
+up to 39 kept planes), several views of different sizes in one plan, a
+camera inside the cells, long tile lists, and the capture workload at 720p.
+Every run must leave the pipeline's wait-error word at zero."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_24994_gb300 import inputs
+from tests.gpu_util import assert_close_image
+from tests.oracle_util import cluster_scene, f32
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2604_24994_gb300 import build
+    build.build()
+
+
+def both(sc, cams):
+    import torch
+    from paper_2604_24994_gb300 import DeviceScene, Renderer
+    ds = DeviceScene.from_numpy(sc, "cuda")
+    out = []
+    for rec in (True, False):
+        r = Renderer(ds.n, ds.k, cams, hit_records=rec)
+        rgb, T, last = r.forward(ds)
+        torch.cuda.synchronize()
+        assert r.stats()["wait_errors"] == 0
+        out.append((rgb.cpu().numpy(), T.cpu().numpy(), last.cpu().numpy()))
+    (a, b) = out
+    for x, y, name in zip(a, b, ("rgb", "T", "last")):
+        assert np.array_equal(x, y), name
+    return b
+
+
+def test_tiny_and_multiview(tiny):
+    sc, cam = tiny
+    rgb, T, last = both(sc, [cam])
+    rgb_o, T_o = oracle.Oracle(sc).render(cam)
+    assert_close_image(rgb.astype(np.float64), T.astype(np.float64), rgb_o, T_o, "tiny, pipelined")
+    rng = np.random.default_rng(5)
+    sc = f32(cluster_scene(rng, n=60, spread=0.4, r=(0.08, 0.25), tex_std=0.15))
+    both(sc, [inputs.look_at((1.4, 0.3, 0.2), 100, 75),
+              inputs.look_at((0.05, 0.02, 0.0), 37, 29, target=(1.0, 0.5, 0.1)),
+              inputs.fisheye_look_at((-0.9, -0.9, 0.6), 40, 33, fov_deg=160.0)])
+
+
+def test_plane_budget_cuts_batches_and_early_termination():
+    """A dense cluster with all-pairs lists: cells keep many planes, so the
+    stage's plane budget cuts batches short; near-opaque densities end most
+    pixels early."""
+    rng = np.random.default_rng(8)
+    sc = cluster_scene(rng, n=40, spread=0.1, r=(0.08, 0.14), tex_std=0.2)
+    sc.sigma = sc.sigma * 20.0
+    sc = f32(sc)
+    cam = inputs.look_at((0.7, 0.2, 0.1), 64, 48, fov_y_deg=40)
+    rgb, T, last = both(sc, [cam])
+    rgb_o, T_o = oracle.Oracle(sc).render(cam)
+    assert_close_image(rgb.astype(np.float64), T.astype(np.float64), rgb_o, T_o, "opaque cluster, pipelined")
+    assert (T < 1e-6).sum() > 100
+
+
+def test_long_lists_and_capture_720p():
+    from tests.test_gpu_binning import column_scene
+    cam = inputs.look_at((3.0, 0.0, 0.0), 640, 360)
+    both(column_scene(cam, [(19, 10), (23, 6)], [80, 24]), [cam])
+    sc = inputs.capture_scene(400_000, seed=0, K=32)
+    both(sc, [inputs.capture_camera(1280, 720)])

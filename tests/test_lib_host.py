@@ -166,9 +166,10 @@ def test_camera_models(lib):
 
 
 def test_extended_face_model_checks(lib):
-    """Displacement, learned sites and view-dependent colours: misaligned
-    arrays, a stats pass, the contribution forward and a backward without
-    the matching gradient arrays are refused on the host."""
+    """Displacement, learned sites, view-dependent colours and the site
+    count: misaligned arrays, a stats pass, a site count other than 4 or 8,
+    a contribution adjoint without its weights and a backward without the
+    matching gradient arrays are refused on the host."""
     from paper_2604_24994_gb300 import _lib
     h = C.c_void_p()
     assert lib.pf_plan_create(10, 4, _lib.camera_array([inputs.look_at((3, 0, 0), 32, 32)]), 1, 100,
@@ -186,11 +187,21 @@ def test_extended_face_model_checks(lib):
     assert lib.pf_plan_enable_stats(h, 1) == 0
     assert lib.pf_render_fwd(C.byref(s), h, out, out, out, out, None) == _lib.PF_ERR_INVALID_ARG
     assert lib.pf_plan_enable_stats(h, 0) == 0
-    s.disp, s.sv = None, fake
-    assert lib.pf_render_fwd_contrib(C.byref(s), h, out, out, out, out, out, out, None) == _lib.PF_ERR_INVALID_ARG
+    s.disp = None
+    s.n_sites = 5
+    assert lib.pf_render_fwd(C.byref(s), h, out, out, out, out, None) == _lib.PF_ERR_INVALID_ARG
+    assert b"n_sites" in lib.pf_last_error_message()
+    s.n_sites = 8
+    assert lib.pf_plan_enable_stats(h, 1) == 0          # eight sites: no stats pass either
+    assert lib.pf_render_fwd(C.byref(s), h, out, out, out, out, None) == _lib.PF_ERR_INVALID_ARG
+    assert lib.pf_plan_enable_stats(h, 0) == 0
+    s.n_sites = 0
     g = _lib.SceneGrad()
     for k in ("pos", "w", "R", "sigma", "rgb", "normal", "offset", "tex"):
         setattr(g, k, fake)
+    assert lib.pf_render_bwd_contrib(C.byref(s), h, out, out, out, out, out, None, None, C.byref(g),
+                                     None) == _lib.PF_ERR_INVALID_ARG
+    assert b"contribution weights" in lib.pf_last_error_message()
     for k in ("disp", "sites", "sv"):
         s.disp = s.sites = s.sv = None
         setattr(s, k, fake)
