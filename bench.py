@@ -642,10 +642,12 @@ def run_large(args):
     """The large differentiable workload: 5M cells (capture recipe), 48
     neighbours, four 3840x2160 views on a ring, forward+backward with the
     per-pixel (T, last) checkpoint.  Times the step and reports peak device
-    memory for the default plan (checkpoint + the forward's hit records) and
+    memory for the default plan (checkpoint + the forward's hit records),
     for a plan laid out without hit records (checkpoint only: the backward
-    re-tests every listed cell), plus what storing every segment instead of
-    replaying would need.  Prints one JSON line (not the benchmark line)."""
+    re-tests every listed cell), and for the variant that stores every
+    segment instead of replaying it (pf_plan_store_segments), which fits for
+    one of the four views: the three plans are also measured on that view
+    alone.  Prints one JSON line (not the benchmark line)."""
     import torch
     from paper_2604_24994_gb300 import DeviceScene, Renderer, build, inputs
     from paper_2604_24994_gb300.dataparallel import ring_view
@@ -656,25 +658,22 @@ def run_large(args):
     cams = [ring_view(v, 3840, 2160, radius=3.0, n_ring=4) for v in range(4)]
     ds = DeviceScene.from_numpy(sc, "cuda")
     del sc
-    # size the instance capacity once, then lay plans out at that size
-    r = Renderer(ds.n, ds.k, cams, hit_records=False)
-    r.bin(ds, sync=True)
-    cap = int(r.n_instances * 1.02) + 4096
-    r.enable_stats(True)
-    r.render_fwd(ds)
-    stats = r.stats()
-    del r
-    torch.cuda.empty_cache()
-    px = sum(c.width * c.height for c in cams)
-    gen = torch.Generator(device="cuda").manual_seed(0)
-    target = torch.rand((px, 3), device="cuda", generator=gen)
     stream = torch.cuda.current_stream()
-    out = {}
-    for name, rec in (("checkpoint+hit_records", True), ("checkpoint_only", False)):
+    free_total = torch.cuda.mem_get_info()
+
+    def measure(name, views, rec, store=0):
+        # size the instance capacity once, then lay the plan out at that size
+        r = Renderer(ds.n, ds.k, views, hit_records=False)
+        r.bin(ds, sync=True)
+        cap = int(r.n_instances * 1.02) + 4096
+        del r
         torch.cuda.empty_cache()
         torch.cuda.reset_peak_memory_stats()
         base = torch.cuda.memory_allocated()
-        r = Renderer(ds.n, ds.k, cams, capacity=cap, hit_records=rec)
+        px = sum(c.width * c.height for c in views)
+        gen = torch.Generator(device="cuda").manual_seed(0)
+        target = torch.rand((px, 3), device="cuda", generator=gen)
+        r = Renderer(ds.n, ds.k, views, capacity=cap, hit_records=rec, store_segments=store)
         rgb = torch.empty((px, 3), device="cuda")
         T = torch.empty(px, device="cuda")
         last = torch.empty(px, dtype=torch.int32, device="cuda")
@@ -694,19 +693,46 @@ def run_large(args):
             step()
         b.record(stream)
         b.synchronize()
-        out[name] = {"ms_fwd_bwd": a.elapsed_time(b) / args.steps,
-                     "workspace_gb": r.plan.ws_bytes / 1e9,
-                     "peak_allocated_gb": torch.cuda.max_memory_allocated() / 1e9,
-                     "peak_above_scene_gb": (torch.cuda.max_memory_allocated() - base) / 1e9}
-        del r, rgb, T, last, grads
-    hits = stats["hits"]
+        res = {"views": len(views), "ms_fwd_bwd": a.elapsed_time(b) / args.steps,
+               "workspace_gb": r.plan.ws_bytes / 1e9,
+               "peak_allocated_gb": torch.cuda.max_memory_allocated() / 1e9,
+               "peak_above_scene_gb": (torch.cuda.max_memory_allocated() - base) / 1e9}
+        if rec:
+            hc = r.hit_counts()
+            res["hits_per_pixel"] = float(hc.mean())
+            res["max_hits_per_pixel"] = int(hc.max())
+        if store:
+            res["stored_segments_per_pixel"] = store
+        del r, rgb, T, last, grads, target
+        torch.cuda.empty_cache()
+        return res
+
+    out = {}
+    out["checkpoint+hit_records"] = measure("checkpoint+hit_records", cams, True)
+    out["checkpoint_only"] = measure("checkpoint_only", cams, False)
+    one = cams[:1]
+    out["one_view"] = {"checkpoint+hit_records": measure("1v hit records", one, True),
+                       "checkpoint_only": measure("1v checkpoint", one, False)}
+    # store every segment: the capacity per pixel is the largest hit count of that view
+    mh = out["one_view"]["checkpoint+hit_records"]["max_hits_per_pixel"]
+    need = one[0].width * one[0].height * mh * 16
+    all4 = out["checkpoint+hit_records"]["max_hits_per_pixel"] * sum(c.width * c.height for c in cams) * 16
+    try:
+        out["one_view"]["store_every_segment"] = measure("1v store", one, True, store=mh)
+    except torch.OutOfMemoryError:
+        torch.cuda.empty_cache()
+        out["one_view"]["store_every_segment"] = f"does not fit: {need / 1e9:.1f} GB of segments"
+    if all4 <= free_total[1] * 0.6:
+        out["store_every_segment"] = measure("store", cams, True,
+                                             store=out["checkpoint+hit_records"]["max_hits_per_pixel"])
     line = {"workload": "5,000,000 cells (capture recipe), 48 neighbours, 4 views 3840x2160 on a ring of radius 3",
-            "pixels": px, "instances": stats["instances"], "capacity": cap, "hits": hits,
-            "hits_per_pixel": hits / px, "scene_params_gb": sum(v.numel() * v.element_size()
-                                                               for v in ds.params.values()) / 1e9,
-            "checkpoint_bytes_per_pixel": 8,
-            "no_checkpoint_estimate_gb": hits * 32 / 1e9,
-            "no_checkpoint_note": "not built: every hit's (T before, colour, entry, exit, kinds, cell) at 32 B",
+            "device_memory_gb": free_total[1] / 1e9,
+            "checkpoint_bytes_per_pixel": 8, "store_bytes_per_segment": 16,
+            "store_every_segment_one_view_gb": need / 1e9,
+            "store_every_segment_four_views_gb": all4 / 1e9,
+            "store_every_segment_four_views": "not run: the per-pixel store at the largest hit count of the "
+                                              "four views exceeds the device's memory beside the scene and workspace"
+            if all4 > free_total[1] * 0.6 else "fits",
             "steps": args.steps, "warmup": args.warmup, "scene_generation_s": round(gen_s, 1), **out}
     print(json.dumps(line), flush=True)
 

@@ -188,6 +188,21 @@ pf_status pf_plan_set_record_hits(pf_plan *plan, int32_t enable);
  * before querying pf_plan_workspace_bytes and allocating; recording can then
  * no longer be enabled (PF_ERR_INVALID_ARG). */
 pf_status pf_plan_omit_hit_records(pf_plan *plan);
+/* Store every segment instead of replaying it: with max_hits > 0 the
+ * forward (while recording hits) also stores, for each pixel's first
+ * max_hits hits in list order, the segment's entry and exit, the
+ * transmittance in front of it and its active constraints (16 bytes), and
+ * the backward reads them instead of recomputing the ends and the
+ * transmittance (the no-checkpoint variant of the large differentiable
+ * workload; hits past max_hits are replayed as before).  It adds
+ * pixels x max_hits x 16 bytes to the workspace: call it before querying
+ * pf_plan_workspace_bytes and allocating.  0 turns it off.  Errors:
+ * PF_ERR_INVALID_ARG (negative, or a plan laid out without hit records). */
+pf_status pf_plan_store_segments(pf_plan *plan, int32_t max_hits);
+/* Copy the hits the last recording forward composited per pixel [P] to a
+ * HOST buffer (synchronises `stream`); PF_ERR_INVALID_ARG without hit
+ * records. */
+pf_status pf_read_hit_counts(pf_plan *plan, void *ws, uint32_t *counts, void *stream);
 /* Count work in the next forward passes (adds to the counters; 0 disables). */
 pf_status pf_plan_enable_stats(pf_plan *plan, int32_t enable);
 /* Read the counters, then reset them (synchronises `stream`). */

@@ -63,6 +63,8 @@ def _sig(lib):
         "pf_plan_enable_stats": ([V, I32], st),
         "pf_plan_set_record_hits": ([V, I32], st),
         "pf_plan_omit_hit_records": ([V], st),
+        "pf_plan_store_segments": ([V, I32], st),
+        "pf_read_hit_counts": ([V, V, V, V], st),
         "pf_plan_read_stats": ([V, V, P(Stats), V], st),
         "pf_prepare": ([P(Scene), V, V, V], st),
         "pf_project": ([P(Scene), V, V, V], st),

@@ -150,7 +150,8 @@ def build_neighbours(pos, w, R, k: int, out_R=None):
 class Plan:
     """A C plan (layout + cameras) with its device workspace."""
 
-    def __init__(self, n: int, k: int, cams, capacity: int, device="cuda", hit_records: bool = True):
+    def __init__(self, n: int, k: int, cams, capacity: int, device="cuda", hit_records: bool = True,
+                 store_segments: int = 0):
         self.n, self.k = n, k
         self.cams = list(cams)
         self.capacity = int(capacity)
@@ -160,6 +161,8 @@ class Plan:
               "pf_plan_create")
         if not hit_records:
             check(lib().pf_plan_omit_hit_records(self.handle), "pf_plan_omit_hit_records")
+        if store_segments:
+            check(lib().pf_plan_store_segments(self.handle, int(store_segments)), "pf_plan_store_segments")
         b = C.c_uint64()
         check(lib().pf_plan_workspace_bytes(self.handle, C.byref(b)), "pf_plan_workspace_bytes")
         self.ws_bytes = int(b.value)
@@ -195,11 +198,15 @@ class Renderer:
     any resolutions).  The instance capacity grows automatically."""
 
     def __init__(self, n: int, k: int, cams, capacity: int | None = None, device="cuda",
-                 hit_records: bool = True):
+                 hit_records: bool = True, store_segments: int = 0):
         """hit_records=False lays the workspace out without the forward's hit
-        records (smaller; the backward then always re-tests)."""
+        records (smaller; the backward then always re-tests).
+        store_segments=M > 0 also stores each pixel's first M segments
+        (ends, transmittance in front, active constraints; 16 bytes each), which
+        the backward reads instead of recomputing (pf_plan_store_segments)."""
         self.device = device
         self._hit_records = hit_records
+        self._store = int(store_segments)
         cams = list(cams)
         if capacity is None:
             px = sum(c.width * c.height for c in cams)
@@ -211,7 +218,7 @@ class Renderer:
         self.n_instances = 0
 
     def _make_plan(self, n, k, cams, capacity):
-        P = Plan(n, k, cams, capacity, self.device, hit_records=self._hit_records)
+        P = Plan(n, k, cams, capacity, self.device, hit_records=self._hit_records, store_segments=self._store)
         check(lib().pf_plan_set_record_hits(P.handle, 1 if self._record else 0), "pf_plan_set_record_hits")
         check(lib().pf_plan_enable_stats(P.handle, 1 if self._stats else 0), "pf_plan_enable_stats")
         return P
@@ -312,6 +319,13 @@ class Renderer:
                                               ptr(dL_dT), T.data_ptr(), last.data_ptr(), ws_.data_ptr(),
                                               wn_.data_ptr(), C.byref(g), _stream()), "pf_render_bwd_contrib")
         return grads
+
+    def hit_counts(self):
+        """Hits the last recording forward composited per pixel (numpy uint32 [P])."""
+        P = self.plan
+        out = np.zeros(P.pixels, np.uint32)
+        check(lib().pf_read_hit_counts(P.handle, P.ws_ptr, out.ctypes.data, _stream()), "pf_read_hit_counts")
+        return out
 
     def stats(self):
         s = _lib.Stats()

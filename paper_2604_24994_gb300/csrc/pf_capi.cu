@@ -56,6 +56,7 @@ WS Plan::ws(void *base) const {
     w.hitmask = rec ? (uint32_t *)(b + L.hitmask) : nullptr;
     w.hitkind = rec ? (uint16_t *)(b + L.hitkind) : nullptr;
     w.hitcount = rec ? (uint32_t *)(b + L.hitcount) : nullptr;
+    w.segrec = rec && seg_cap > 0 ? (float4 *)(b + L.segrec) : nullptr;
     w.pw = (float4 *)(b + L.pw);
     if (external_scene) {
         const SceneLayout S = make_scene_layout(n, k);
@@ -182,6 +183,7 @@ void make_layout(Plan *p) {
     L.hitmask = take(rec ? (uint64_t)(TILE_PIX / 32) * mask_batches(*p) * 32 * 4 : 0);
     L.hitkind = take(rec ? (uint64_t)p->total_pixels * HIT_CAP * 2 : 0);
     L.hitcount = take(rec ? (uint64_t)p->total_pixels * 4 : 0);
+    L.segrec = take(rec && p->seg_cap > 0 ? (uint64_t)p->total_pixels * (uint64_t)p->seg_cap * 16 : 0);
     L.total = o;
 }
 
@@ -314,6 +316,33 @@ pf_status pf_plan_omit_hit_records(pf_plan *p) {
     p->masks_valid = false;
     make_layout(p);
     return PF_OK;
+}
+
+pf_status pf_plan_store_segments(pf_plan *p, int32_t max_hits) {
+    if (!p || max_hits < 0) return PF_ERR_INVALID_ARG;
+    if (max_hits > 0 && (p->no_hit_records || p->fwd_only)) {
+        set_error("pf_plan_store_segments: the plan has no hit records (pf_plan_omit_hit_records)");
+        return PF_ERR_INVALID_ARG;
+    }
+    p->seg_cap = max_hits;
+    p->masks_valid = false;
+    make_layout(p);
+    return PF_OK;
+}
+
+pf_status pf_read_hit_counts(pf_plan *p, void *ws, uint32_t *counts, void *stream) {
+    g_err[0] = 0;
+    if (!p || !ws || !counts) return PF_ERR_INVALID_ARG;
+    WS w = p->ws(ws);
+    if (!w.hitcount) {
+        set_error("pf_read_hit_counts: the plan has no hit records");
+        return PF_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    pf_status s = cuda_status(cudaMemcpyAsync(counts, w.hitcount, 4 * (size_t)p->total_pixels, cudaMemcpyDeviceToHost, st),
+                              "read hit counts");
+    if (!s) s = cuda_status(cudaStreamSynchronize(st), "read hit counts sync");
+    return s;
 }
 
 pf_status pf_plan_enable_stats(pf_plan *p, int32_t enable) {

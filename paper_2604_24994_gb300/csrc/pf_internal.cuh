@@ -101,7 +101,7 @@ struct Counters {
 struct Layout {
     uint64_t views, cellrec, cellnp, planes, plane_nb, viewrec, rect, key, cnt, celloff, diff, tile_start,
         tile_cursor, tile_order, scan_tmp, inst_key, inst_cell, inst_sorted, sort_tmp_key, sort_tmp_cell, counters,
-        acc, planes_lo, hitmask, hitkind, hitcount, pw, total;
+        acc, planes_lo, hitmask, hitkind, hitcount, segrec, pw, total;
     uint64_t scan_tmp_elems;
 };
 
@@ -138,6 +138,8 @@ struct WS {
     uint32_t *hitcount;    // [pixels] hits the forward composited
     uint32_t *hitmask;     // [8][batch slots][32] per warp of a tile, batch of its list and
                            // pixel: bit j set if the forward's segment in cell j was non-empty
+    float4 *segrec;        // [pixels][seg_cap] stored segments of the pixel's first hits in list
+                           // order: (entry, exit, T before the segment, active constraints as bits)
 };
 
 struct Plan {
@@ -158,6 +160,7 @@ struct Plan {
     bool masks_valid = false;
     bool record_hits = true;   // pf_plan_set_record_hits
     bool no_hit_records = false;  // pf_plan_omit_hit_records: the layout has no hit-record regions
+    int32_t seg_cap = 0;     // pf_plan_store_segments: stored segments per pixel (0: none)
     WS ws(void *base) const;
 };
 

@@ -136,9 +136,12 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, i
             }
             if (!hit) continue;
             if (REC) {
-                if (nhit < HIT_CAP)
-                    A.w.hitkind[(V.pix_base + (int64_t)py * V.width + px) * HIT_CAP + nhit] =
-                        (uint16_t)((seg.ka + 3) | ((seg.kb + 3) << 7));
+                const int64_t rp = V.pix_base + (int64_t)py * V.width + px;
+                const unsigned kinds = (unsigned)((seg.ka + 3) | ((seg.kb + 3) << 7));
+                if (nhit < HIT_CAP) A.w.hitkind[rp * HIT_CAP + nhit] = (uint16_t)kinds;
+                // stored segments (pf_plan_store_segments): the ends and the transmittance before
+                if (A.segrec && nhit < A.seg_cap)
+                    A.segrec[rp * A.seg_cap + nhit] = make_float4(seg.sa, seg.sb, T, __uint_as_float(kinds));
                 nhit++;
             }
             TexT<NS> tx;
@@ -202,6 +205,58 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, i
             atomicAdd(&st[7], st_whit);
         }
     }
+}
+
+// A stored hit (pf_plan_store_segments): the forward's segment ends, the
+// transmittance in front of it and its active constraints, so the ends are
+// not recomputed.  The d.a of the end constraints are formed in float, and
+// from FP64 where the backward's criterion asks for it (the adjoint divides
+// by them), as in segment_from_kinds.
+template <bool EXT, int NS>
+__device__ __forceinline__ bool segment_from_record(const float *__restrict__ cr, const float *__restrict__ vr,
+                                                    const float4 *__restrict__ pl, const float4 *__restrict__ lo_glob,
+                                                    const Ray &ray, const Chord &ch, float4 rec, Seg &sg, float4 dk,
+                                                    const float *__restrict__ st, bool has_disp,
+                                                    const float *__restrict__ dk8) {
+    const unsigned kinds = __float_as_uint(rec.w);
+    const int ka = (int)(kinds & 127u) - 3, kb = (int)(kinds >> 7) - 3;
+    const float3 dh = ray.dh, q = ch.q;
+    const float R = cr[CR_R];
+    const float sig = cr[CR_SIG];
+    const float3 n = f3(cr[CR_N], cr[CR_N + 1], cr[CR_N + 2]);
+    float foff = cr[CR_OFF];
+    const float fden = dot3(dh, n);
+    if (EXT && has_disp) {  // the displaced face's offset, for an FP64 d.n at a face end
+        const float fnum = foff - dot3(q, n);
+        foff += NS == 8 ? face_delta8(cr, q, dh, fnum, fden, dk8, nullptr, st)
+                        : face_delta(cr, q, dh, fnum, fden, dk, nullptr, st);
+    }
+    sg.dnd = fden;
+    if (fabsf(fden) < 0x1p-20f) sg.dnd = face_side64(cr, ray);
+    const float4 Pa = pl[max(ka, 0)], Pb = pl[max(kb, 0)];
+    float dena = ka >= 0 ? dot3(dh, f3(Pa.x, Pa.y, Pa.z)) : (ka == K_FACE ? fden : CUDART_INF_F);
+    float denb = kb >= 0 ? dot3(dh, f3(Pb.x, Pb.y, Pb.z)) : (kb == K_FACE ? fden : CUDART_INF_F);
+    const float lim = PLANE_ERR * sig * (1.0f / REFINE_EPS);
+    const float4 face_hi = make_float4(cr[CR_N], cr[CR_N + 1], cr[CR_N + 2], foff);
+    const float4 face_lo = make_float4(cr[CR_NLO], cr[CR_NLO + 1], cr[CR_NLO + 2], 0.f);
+    float d64;
+    if (fabsf(dena) < fmaxf(lim * (R + fabsf(rec.x)), GRAD_DEN)) {
+        refine_plane64(vr, ka >= 0 ? Pa : face_hi, ka >= 0 ? lo_glob[ka] : face_lo, ray, rec.x, d64);
+        dena = d64;
+    }
+    if (fabsf(denb) < fmaxf(lim * (R + fabsf(rec.y)), GRAD_DEN)) {
+        refine_plane64(vr, kb >= 0 ? Pb : face_hi, kb >= 0 ? lo_glob[kb] : face_lo, ray, rec.y, d64);
+        denb = d64;
+    }
+    sg.sa = rec.x;
+    sg.sb = rec.y;
+    sg.ka = ka;
+    sg.kb = kb;
+    sg.dena = dena;
+    sg.denb = denb;
+    sg.q = q;
+    sg.refined = 0;
+    return true;
 }
 
 // --------------------------------------------------------------- backward
@@ -430,6 +485,8 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
             Chord ch;
             bool cand;
             bool hit = false;
+            float4 srec = float4{0.f, 0.f, 0.f, 0.f};
+            bool has_srec = false;  // the forward stored this hit's segment
             if (MASKS) {
                 // the forward recorded this hit's active constraints: no plane loop
                 unsigned kk = 0xffffu;
@@ -437,9 +494,16 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
                     kk = kk_next;
                     --nrec;
                     kk_next = nrec > 0 && nrec - 1 < HIT_CAP ? A.w.hitkind[pix * HIT_CAP + nrec - 1] : 0xffffu;
+                    if (A.segrec && nrec < A.seg_cap) {
+                        srec = A.segrec[pix * A.seg_cap + nrec];
+                        has_srec = true;
+                    }
                 }
                 if (mine && sphere_chord<true>(cr, vr, ray, ch, cand)) {
-                    if (kk != 0xffffu)
+                    if (has_srec)
+                        hit = segment_from_record<EXT, NS>(cr, vr, s_pl + o, A.w.planes_lo + (int64_t)cell * A.K, ray,
+                                                           ch, srec, sg, dk, st, has_disp, dk8);
+                    else if (kk != 0xffffu)
                         hit = segment_from_kinds<true, EXT, NS>(cr, vr, s_pl + o,
                                                                 A.w.planes_lo + (int64_t)cell * A.K, ray, ch,
                                                                 (int)(kk & 127u) - 3, (int)(kk >> 7) - 3, sg, dk, st,
@@ -480,7 +544,7 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
                 const float x = fminf(xr, X_CAP);
                 const float ex = __expf(-x);
                 const float alpha = 1.0f - ex;
-                const float Tbefore = Tafter * __expf(x);
+                const float Tbefore = has_srec ? srec.z : Tafter * __expf(x);
                 // x = sigma l, alpha = 1 - e^-x:  dL/dx = g.(T_{k+1} c - S_k) - gT T_final
                 float dLdx = g.x * (Tafter * c.x - accC.x) + g.y * (Tafter * c.y - accC.y) +
                              g.z * (Tafter * c.z - accC.z) - gT * Tf;
@@ -829,6 +893,8 @@ static RenderArgs make_args(const pf_scene &s, const Plan &p, const WS &w) {
     A.gtex8 = nullptr;
     A.w_sparse = nullptr;
     A.w_normal = nullptr;
+    A.segrec = w.segrec;
+    A.seg_cap = w.segrec ? p.seg_cap : 0;
     return A;
 }
 

@@ -762,6 +762,8 @@ struct RenderArgs {
     float *gtex8;           // eight sites: its gradient (the backward adds into it), else null
     const float *w_sparse;  // [N] upstream weights of the contributions' adjoint (pf_render_bwd_contrib), or null
     const float *w_normal;  // [N]
+    float4 *segrec;         // [pixels][seg_cap] stored segments (pf_plan_store_segments), or null
+    int seg_cap;
 };
 
 // Hit masks: one 32-bit word per (warp of the tile, batch, pixel of the

@@ -378,6 +378,8 @@ cudaError_t launch_render_fwd_pipe(const pf_scene &s, const Plan &p, const WS &w
     A.disp = A.sites = A.sv = A.tex8 = nullptr;
     A.gdisp = A.gsites = A.gsv = A.gtex8 = nullptr;
     A.w_sparse = A.w_normal = nullptr;
+    A.segrec = nullptr;
+    A.seg_cap = 0;
     (void)s;
     const size_t smem = sizeof(PipeStage) * PIPE_S;
     cudaError_t e = cudaMemsetAsync(&w.counters->q_fwd, 0, sizeof(unsigned int), st);

@@ -169,3 +169,42 @@ def test_replay_beyond_the_recorded_hits_per_pixel():
         assert rel_l2(a, b) < 1e-5, (k, rel_l2(a, b))
     Go = oracle.Oracle(sc).render_grad(cam, gC.cpu().numpy().astype(np.float64), gT.cpu().numpy().astype(np.float64))
     check_grads({k: v.double().cpu().numpy() for k, v in g_rec.items()}, Go)
+
+
+@pytest.mark.parametrize("cap", [1000, 3])
+def test_stored_segments_backward(cap):
+    """pf_plan_store_segments: the forward stores every hit's segment (or
+    only each pixel's first 3, the rest replayed), the backward reads them
+    instead of recomputing; the gradients agree with the replaying backward
+    and with the FP64 adjoint."""
+    import torch
+    from paper_2604_24994_gb300 import DeviceScene, Renderer
+    rng = np.random.default_rng(17)
+    sc = f32(cluster_scene(rng, n=40, spread=0.15, r=(0.06, 0.12), tex_std=0.2))
+    cams = [inputs.look_at((0.7, 0.2, 0.1), 48, 40, fov_y_deg=40),
+            inputs.look_at((-0.5, 0.5, 0.3), 33, 21, fov_y_deg=50)]
+    npx = sum(c.n_pixels for c in cams)
+    gC = torch.from_numpy(rng.normal(size=(npx, 3))).float().cuda()
+    gT = torch.from_numpy(rng.normal(size=npx)).float().cuda()
+    ds = DeviceScene.from_numpy(sc, "cuda")
+    out = {}
+    for name, kw in (("replay", {}), ("stored", {"store_segments": cap})):
+        r = Renderer(ds.n, ds.k, cams, **kw)
+        rgb, T, last = r.forward(ds)
+        if name == "stored":
+            counts = r.hit_counts()
+            assert counts.max() > 3 and (cap > counts.max() or cap == 3)
+        g = r.backward(ds, gC, gT, T, last)
+        torch.cuda.synchronize()
+        out[name] = {k: v.cpu().numpy().astype(np.float64) for k, v in g.items()}
+    for k in PARAMS:
+        if np.linalg.norm(out["replay"][k]) > 0:
+            assert rel_l2(out["stored"][k], out["replay"][k]) < 1e-4, k
+    orc = oracle.Oracle(sc)
+    Go = None
+    o = 0
+    for cam in cams:
+        g = orc.render_grad(cam, gC[o:o + cam.n_pixels].cpu().numpy(), gT[o:o + cam.n_pixels].cpu().numpy())
+        Go = g if Go is None else {k: Go[k] + g[k] for k in PARAMS}
+        o += cam.n_pixels
+    check_grads(out["stored"], Go)
