@@ -55,9 +55,9 @@ IMPL_FLOPS_PER_HIT = 92         # face point (6), face coordinates (10), site of
                                 # normalise (5), colour (24), compositing (15)
 
 
-TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "render_fwd_dram_1080p_1M.md")
-TRAFFIC_SOURCES = ("paper_2604_24994_gb300/csrc/pf_render.cu", "paper_2604_24994_gb300/csrc/pf_internal.cuh",
-                   "include/powerfoam.h")
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "render_fwd_pipe_dram_1080p_1M.md")
+TRAFFIC_SOURCES = ("paper_2604_24994_gb300/csrc/pf_render_pipe.cu", "paper_2604_24994_gb300/csrc/pf_render_common.cuh",
+                   "paper_2604_24994_gb300/csrc/pf_internal.cuh", "include/powerfoam.h")
 
 
 def render_source_digest():
@@ -70,7 +70,7 @@ def render_source_digest():
 
 
 def measured_traffic():
-    """DRAM bytes (read + write) of one render_fwd_kernel launch on this
+    """DRAM bytes (read + write) of one render_fwd_pipe_kernel launch on this
     workload from the committed ncu summary, or None when the kernel's
     sources changed since those counters were taken."""
     try:
@@ -530,7 +530,7 @@ def run_ours(args):
         "ms_build_neighbours": ms_neighbours,
         "neighbours_equal_input_lists": nbr_same,
         "work": stats,
-        "roofline": {"bound": "alu", "kernel": "render_fwd_kernel", "achieved": achieved, "peak": peak_tflops,
+        "roofline": {"bound": "alu", "kernel": "render_fwd_pipe_kernel", "achieved": achieved, "peak": peak_tflops,
                      "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                      "traffic": measured_traffic() if args.workload == "full" else None,
                      "work": f"{ALG_FLOPS_PER_CANDIDATE} flops x {stats['candidates']} candidates + "
