@@ -377,7 +377,9 @@ __device__ __forceinline__ void route_end(float gt, int kind, float s, float den
 // L_sparse / L_normal): along a ray they composite the scalar
 // q_k = w_sparse + w_normal max(nh.d, 0)^2 like a fourth colour channel whose
 // upstream gradient is 1, and q_k itself moves with the unit normal.
-template <bool MASKS, bool EXT = false, int NS = 4, bool CONTRIB = false>
+// STORE: read the segments the forward stored (pf_plan_store_segments)
+// instead of recomputing their ends and the transmittance.
+template <bool MASKS, bool EXT = false, int NS = 4, bool CONTRIB = false, bool STORE = false>
 __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, int64_t n_tiles,
                                                                  const float *__restrict__ dL_drgb,
                                                                  const float *__restrict__ dL_dT,
@@ -494,13 +496,13 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
                     kk = kk_next;
                     --nrec;
                     kk_next = nrec > 0 && nrec - 1 < HIT_CAP ? A.w.hitkind[pix * HIT_CAP + nrec - 1] : 0xffffu;
-                    if (A.segrec && nrec < A.seg_cap) {
+                    if (STORE && A.segrec && nrec < A.seg_cap) {
                         srec = A.segrec[pix * A.seg_cap + nrec];
                         has_srec = true;
                     }
                 }
                 if (mine && sphere_chord<true>(cr, vr, ray, ch, cand)) {
-                    if (has_srec)
+                    if (STORE && has_srec)
                         hit = segment_from_record<EXT, NS>(cr, vr, s_pl + o, A.w.planes_lo + (int64_t)cell * A.K, ray,
                                                            ch, srec, sg, dk, st, has_disp, dk8);
                     else if (kk != 0xffffu)
@@ -544,7 +546,7 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
                 const float x = fminf(xr, X_CAP);
                 const float ex = __expf(-x);
                 const float alpha = 1.0f - ex;
-                const float Tbefore = has_srec ? srec.z : Tafter * __expf(x);
+                const float Tbefore = STORE && has_srec ? srec.z : Tafter * __expf(x);
                 // x = sigma l, alpha = 1 - e^-x:  dL/dx = g.(T_{k+1} c - S_k) - gT T_final
                 float dLdx = g.x * (Tafter * c.x - accC.x) + g.y * (Tafter * c.y - accC.y) +
                              g.z * (Tafter * c.z - accC.z) - gT * Tf;
@@ -953,8 +955,10 @@ cudaError_t launch_render_bwd(const pf_scene &s, const Plan &p, const WS &w, con
         const bool cq = w_sparse != nullptr;  // the contributions' adjoint too
         A.w_sparse = w_sparse;
         A.w_normal = w_normal;
+        const bool store = m && w.segrec != nullptr && !disp && !cq;  // stored segments to read
         auto kern =
-            cq ? (disp && eight ? (m ? render_bwd_kernel<true, true, 8, true> : render_bwd_kernel<false, true, 8, true>)
+            store ? render_bwd_kernel<true, false, 4, false, true>
+            : cq ? (disp && eight ? (m ? render_bwd_kernel<true, true, 8, true> : render_bwd_kernel<false, true, 8, true>)
                   : disp        ? (m ? render_bwd_kernel<true, true, 4, true> : render_bwd_kernel<false, true, 4, true>)
                                 : (m ? render_bwd_kernel<true, false, 4, true> : render_bwd_kernel<false, false, 4, true>))
                : (disp && eight ? (m ? render_bwd_kernel<true, true, 8> : render_bwd_kernel<false, true, 8>)

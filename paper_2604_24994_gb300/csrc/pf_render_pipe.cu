@@ -71,6 +71,17 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
     return false;
 }
 
+// Wait for batch k's stage (phase parity `parity`) unless the batch is known
+// never to come (*stop <= k).  1: filled, 0: no such batch, -1: the wait ran out.
+__device__ __forceinline__ int mbar_wait_or_stop(uint64_t *bar, unsigned parity, const int *stop, int k) {
+    for (int it = 0; it < PIPE_SPIN; it++) {
+        if (mbar_test(bar, parity)) return 1;
+        if (*(const volatile int *)stop <= k) return 0;
+        if (it > 64) __nanosleep(128);
+    }
+    return -1;
+}
+
 // size bytes from global src to shared dst, completing on bar (16-byte
 // aligned addresses, size a multiple of 16)
 __device__ __forceinline__ void bulk_copy(void *dst, const void *src, unsigned size, uint64_t *bar) {
@@ -89,6 +100,8 @@ struct PipeShared {
     int next;                  // list index where the next batch starts
     int abort;                 // a wait ran out
     int ndone;                 // warps whose every pixel is done (T below T_EPS, or no pixel)
+    int stop;                  // no batch of this tile from this index on will be issued
+    int pad_;
     int64_t q;                 // the tile taken from the queue
 };
 
@@ -186,6 +199,7 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_pipe_kernel(RenderArgs
             S.q = S.abort ? n_tiles : (int64_t)atomicAdd(&A.w.counters->q_fwd, 1u);
             for (int b = 0; b < PIPE_S; b++) S.consumed[b] = 0;
             S.ndone = 0;
+            S.stop = 0x7fffffff;
         }
         __syncthreads();
         if (S.q >= n_tiles) break;
@@ -212,6 +226,8 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_pipe_kernel(RenderArgs
                 if (next < n) {
                     next = pipe_issue(stage[b], &S.full[b], list, n, next, A.w, vbase, A.K);
                     if (lane == 0) S.fills[b]++;
+                } else if (lane == 0 && S.stop > b) {
+                    S.stop = b;
                 }
             }
             if (lane == 0) {
@@ -233,22 +249,33 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_pipe_kernel(RenderArgs
         bool done = !inside || !has_ray;
         bool warp_done = false;  // counted in S.ndone
         bool more = n > 0;
+        // Every warp consumes every batch that is issued, done or not (a warp that
+        // left early would leave a stage without its eighth arrival, and the batch
+        // another warp waits for would never be refilled).  Once every warp is done
+        // the refilling warp issues no further batch and publishes where the tile
+        // stops; a warp waiting for a batch from there on leaves the loop.
         for (int k = 0; more; k++) {
             if (!warp_done && __all_sync(0xffffffffu, done)) {
                 warp_done = true;
                 if (lane == 0) atomicAdd(&S.ndone, 1);
             }
-            // every pixel of the tile is done: nothing in the rest of the list matters
-            if (*(volatile int *)&S.ndone == PIPE_WARPS) break;
             const int sidx = k % PIPE_S;
             PipeStage &st = stage[sidx];
-            if (!mbar_wait(&S.full[sidx], ((f0 >> sidx) + (unsigned)(k / PIPE_S)) & 1u)) {
+            int got = 1;
+            if (lane == 0)
+                got = mbar_wait_or_stop(&S.full[sidx], ((f0 >> sidx) + (unsigned)(k / PIPE_S)) & 1u, &S.stop, k);
+            got = __shfl_sync(0xffffffffu, got, 0);
+            if (got == 0) break;  // the tile stops before batch k
+            if (got < 0) {
                 if (lane == 0) {
                     atomicOr(&A.w.counters->wait_errors, 1u);
                     atomicExch(&S.abort, 1);
                 }
                 break;
             }
+            // the other lanes observe the completed phase too (acquire for the stage's data)
+            if (lane != 0) mbar_test(&S.full[sidx], ((f0 >> sidx) + (unsigned)(k / PIPE_S)) & 1u);
+            __syncwarp();
             const int nb = st.nb, lo = st.lo;
             more = lo + nb < n;
             if (!warp_done) {
@@ -326,13 +353,16 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_pipe_kernel(RenderArgs
                 }
                 const int next = *(volatile int *)&S.next;
                 int after = next;
-                if (next < n && !*(volatile int *)&S.abort && *(volatile int *)&S.ndone < PIPE_WARPS) {
+                const bool go = next < n && !*(volatile int *)&S.abort &&
+                                *(volatile int *)&S.ndone < PIPE_WARPS && *(volatile int *)&S.stop > b;
+                if (go) {
                     after = pipe_issue(st, &S.full[sidx], list, n, next, A.w, vbase, A.K);
                     if (lane == 0) S.fills[sidx]++;
                 }
                 __syncwarp();
                 if (lane == 0) {
                     S.next = after;
+                    if (!go && S.stop > b) *(volatile int *)&S.stop = b;  // no batch from b on
                     __threadfence_block();
                     *(volatile int *)&S.issued = b + 1;
                 }

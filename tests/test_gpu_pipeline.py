@@ -74,3 +74,20 @@ def test_long_lists_and_capture_720p():
     both(column_scene(cam, [(19, 10), (23, 6)], [80, 24]), [cam])
     sc = inputs.capture_scene(400_000, seed=0, K=32)
     both(sc, [inputs.capture_camera(1280, 720)])
+
+
+def test_early_termination_across_random_views():
+    """Near-opaque cells seen from inside the capture recipe's shell by
+    random cameras of mixed sizes, one plan per view and one multi-view plan
+    (as the server batches them): most tiles end early, where the warps of a
+    tile finish at different batches; the pipeline must neither hang (its
+    bounded waits report in wait_errors) nor change a pixel."""
+    sc = inputs.capture_scene(200_000, seed=4, K=32)
+    sc.sigma = (sc.sigma * 30.0).astype(np.float32)
+    rng = np.random.default_rng(12)
+    sizes = [(160, 90), (320, 180), (200, 200), (97, 61)]
+    cams = inputs.random_sphere_cameras(rng, 8, 1.6, 3.0, sizes, [0.25] * 4)
+    for cam in cams[:4]:
+        rgb, T, last = both(sc, [cam])
+        assert (T < 1e-6).mean() > 0.05
+    both(sc, cams)
