@@ -261,10 +261,11 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_pipe_kernel(RenderArgs
             }
             const int sidx = k % PIPE_S;
             PipeStage &st = stage[sidx];
-            int got = 1;
-            if (lane == 0)
-                got = mbar_wait_or_stop(&S.full[sidx], ((f0 >> sidx) + (unsigned)(k / PIPE_S)) & 1u, &S.stop, k);
-            got = __shfl_sync(0xffffffffu, got, 0);
+            // every lane waits itself (each observes the phase: acquire for the stage's
+            // data); a batch that never comes cannot also complete, so the lanes agree
+            // unless one of them ran out of polls
+            const int got = __reduce_min_sync(
+                0xffffffffu, mbar_wait_or_stop(&S.full[sidx], ((f0 >> sidx) + (unsigned)(k / PIPE_S)) & 1u, &S.stop, k));
             if (got == 0) break;  // the tile stops before batch k
             if (got < 0) {
                 if (lane == 0) {
@@ -273,9 +274,6 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_pipe_kernel(RenderArgs
                 }
                 break;
             }
-            // the other lanes observe the completed phase too (acquire for the stage's data)
-            if (lane != 0) mbar_test(&S.full[sidx], ((f0 >> sidx) + (unsigned)(k / PIPE_S)) & 1u);
-            __syncwarp();
             const int nb = st.nb, lo = st.lo;
             more = lo + nb < n;
             if (!warp_done) {
