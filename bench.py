@@ -197,6 +197,27 @@ def cpu_baseline(sc, cam, seconds: float = 15.0):
                       f"OpenMP over pixels); frames/s = 1 / (time per pixel x 2,073,600)"}
 
 
+def cpu_tile_baseline(sc, cam, t_stop: float = 1e-6):
+    """Second, labelled CPU baseline: the oracle's full-frame FP64 renderer
+    over per-tile lists and the scene's K-neighbour lists (the tiled
+    renderer's own math, with its stop at T < 1e-6).  Timed: the CPU binning
+    (single thread), the per-tile list sort (numpy) and the render (OpenMP
+    over tiles); the neighbour lists are scene data, loaded before."""
+    import oracle
+    orc = oracle.Oracle(sc)
+    orc.set_neighbour_lists(sc.nbr)
+    t0 = time.time()
+    rect, key = orc.bin(cam)
+    start, cells = oracle.tile_lists(rect, key, cam.tiles_x, cam.tiles_y)
+    t1 = time.time()
+    orc.render_tiles(cam, start, cells, t_stop=t_stop)
+    t2 = time.time()
+    return {"value": 1.0 / (t2 - t0), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle tile-list renderer",
+            "s_bin_and_lists": round(t1 - t0, 3), "s_render": round(t2 - t1, 3),
+            "sample": f"the full {cam.width}x{cam.height} frame: CPU binning, per-tile lists in painter order, "
+                      f"each listed cell clipped against its {sc.k} neighbours in FP64, stop at T < {t_stop:g}"}
+
+
 def run_reference(args):
     """The oracle as it stands on this host's cores: each step renders a
     bounded sample (64 random pixels) of the benchmark frame; frames/s is
@@ -506,6 +527,7 @@ def run_ours(args):
     achieved = alg_flops / (ms_render * 1e-3) / 1e12
     achieved_impl = impl_flops / (ms_render * 1e-3) / 1e12
     cpu = cpu_baseline(sc, cam, seconds=args.cpu_seconds) if args.cpu_seconds > 0 else None
+    cpu_tiles = cpu_tile_baseline(sc, cam) if args.cpu_seconds > 0 else None
     n_cells, n_nbr = ds.n, ds.k
     line = {
         "metric": METRIC, "value": ws * 1000.0 / ms_fwd, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
@@ -544,6 +566,7 @@ def run_ours(args):
         "gpu_launches": K * kernels_fwd,
         "clocks": clocks,
         "cpu_baseline": cpu,
+        "cpu_baseline_tile_lists": cpu_tiles,
     }
     del r, ds, flush, grads, target, host_rgb, host_T, rgb, T, last
     torch.cuda.empty_cache()

@@ -97,6 +97,8 @@ def lib():
                                               P(d), C.c_int]
             _lib.orc_neighbours.argtypes = [P(f), P(f), P(f), C.c_int64, C.c_int32, C.c_int64, P(C.c_int64),
                                             P(C.c_int32), P(f), C.c_int]
+            _lib.orc_render_tiles.argtypes = [P(_Scene), P(_Cands), P(_Camera), P(C.c_int64), P(C.c_int32),
+                                              C.c_int64, P(C.c_int32), d, d, P(d), P(d), P(C.c_int32), C.c_int]
         return _lib
 
 
@@ -257,6 +259,26 @@ class Oracle:
         cs.idx = _ptr(idx, C.c_int32)
         self._cs = cs
 
+    def set_neighbour_lists(self, nbr):
+        """Candidate lists from a neighbour array [N,K] (-1 padded): cell i
+        is clipped against its K listed sites only, as the tiled renderer
+        clips it."""
+        nbr = np.asarray(nbr, np.int64)
+        n = self.n
+        valid = (nbr >= 0) & (nbr != np.arange(n)[:, None])
+        cnt = valid.sum(1)
+        end = np.cumsum(cnt).astype(np.int64)
+        beg = (end - cnt).astype(np.int64)
+        idx = nbr[valid].astype(np.int32)
+        if idx.size == 0:
+            idx = np.zeros(1, np.int32)
+        self._cands = (beg, end, idx)
+        cs = _Cands()
+        cs.beg = _ptr(beg, C.c_int64)
+        cs.end = _ptr(end, C.c_int64)
+        cs.idx = _ptr(idx, C.c_int32)
+        self._cs = cs
+
     def render_rays(self, o, d):
         """rgb [n,3] and T [n] for explicit rays (o [n,3], unit d [n,3])."""
         o = np.ascontiguousarray(np.asarray(o, np.float64).reshape(-1, 3))
@@ -401,6 +423,29 @@ class Oracle:
         lib().orc_cell_colour(C.byref(self._s), int(i), _ptr(o, C.c_double), _ptr(d, C.c_double),
                               float(ta), float(tb), self.kappa, _ptr(col, C.c_double))
         return col
+
+    def render_tiles(self, cam, start, cells, tiles=None, t_stop: float = 0.0, return_nseg: bool = False):
+        """Full-frame render over per-tile lists (CSR `start`, `cells`, from
+        tile_lists): each pixel composites its tile's cells in list order,
+        each clipped against the current candidate lists; a ray stops once
+        T < t_stop.  `tiles`: indices of the tiles to render (None: all).
+        Returns row-major rgb [H*W,3], T [H*W] (and nseg), NaN outside the
+        rendered tiles."""
+        npx = cam.width * cam.height
+        rgb = np.full((npx, 3), np.nan)
+        T = np.full(npx, np.nan)
+        nseg = np.full(npx, -1, np.int32)
+        start = np.ascontiguousarray(start, np.int64)
+        cells = np.ascontiguousarray(cells, np.int32)
+        if cells.size == 0:
+            cells = np.zeros(1, np.int32)
+        tl = None if tiles is None else np.ascontiguousarray(tiles, np.int32)
+        lib().orc_render_tiles(C.byref(self._s), C.byref(self._cs) if self._cs else None,
+                               C.byref(camera_struct(cam)), _ptr(start, C.c_int64), _ptr(cells, C.c_int32),
+                               0 if tl is None else tl.size, None if tl is None else _ptr(tl, C.c_int32),
+                               self.kappa, float(t_stop), _ptr(rgb, C.c_double), _ptr(T, C.c_double),
+                               _ptr(nseg, C.c_int32), self.nthreads)
+        return (rgb, T, nseg) if return_nseg else (rgb, T)
 
     def bin(self, cam):
         """CPU binning: tile rectangles [N,4] (tx0, ty0, tx1, ty1; empty when

@@ -1150,3 +1150,61 @@ int orc_contrib_grad(const orc_scene *s, const orc_cands *cd, const orc_camera *
     free(lists);
     return 0;
 }
+
+/*
+ * Full-frame renderer over per-tile lists (the CPU counterpart of the tiled
+ * renderer, Sec. 3.4): every pixel of a tile walks the tile's cell list in
+ * the given order (the painter order of Sec. 3.4: ascending power distance
+ * from the camera centre, then cell index), clips each listed cell's ray
+ * segment against that cell's candidates (its K neighbour list when `cd`
+ * holds one), and composites the non-empty segments in list order:
+ *   C = sum_k T_k alpha_k c_k,  T_{k+1} = T_k (1 - alpha_k).
+ * A ray stops once T < t_stop (t_stop = 0: never).  In a power diagram the
+ * segments of one ray are disjoint and the painter order is their order
+ * along the ray, so with complete lists this equals orc_render.
+ *
+ * tile_start [ntx*nty+1], tile_cells: CSR lists, tile t = ty*ntx + tx of
+ * ORC_TILE x ORC_TILE pixels.  tiles: ntile indices to render (NULL: all).
+ * out_rgb [H*W][3], out_T [H*W], out_nseg [H*W] (nullable): row-major,
+ * written for the pixels of the rendered tiles only.  OpenMP over tiles.
+ */
+int orc_render_tiles(const orc_scene *s, const orc_cands *cd, const orc_camera *cam, const int64_t *tile_start,
+                     const int32_t *tile_cells, int64_t ntile, const int32_t *tiles, double kappa, double t_stop,
+                     double *out_rgb, double *out_T, int32_t *out_nseg, int nthreads) {
+    const int64_t ntx = (cam->width + ORC_TILE - 1) / ORC_TILE;
+    const int64_t nty = (cam->height + ORC_TILE - 1) / ORC_TILE;
+    if (!tiles) ntile = ntx * nty;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int64_t q = 0; q < ntile; q++) {
+        const int64_t t = tiles ? (int64_t)tiles[q] : q;
+        if (t < 0 || t >= ntx * nty) continue;
+        const int64_t tx = t % ntx, ty = t / ntx;
+        for (int64_t v = ty * ORC_TILE; v < (ty + 1) * ORC_TILE && v < cam->height; v++) {
+            for (int64_t u = tx * ORC_TILE; u < (tx + 1) * ORC_TILE && u < cam->width; u++) {
+                const int64_t k = v * cam->width + u;
+                double o[3], d[3], C[3] = {0.0, 0.0, 0.0}, T = 1.0;
+                int32_t nseg = 0;
+                if (orc_ray(cam, (double)u, (double)v, o, d)) {
+                    for (int64_t e = tile_start[t]; e < tile_start[t + 1] && !(T < t_stop); e++) {
+                        const int64_t i = tile_cells[e];
+                        orc_seg sg;
+                        if (!cell_segment(s, cd, i, o, d, &sg)) continue;
+                        double surv = exp(-s->sigma[i] * (sg.tb - sg.ta));
+                        double col[3];
+                        cell_colour(s, i, o, d, &sg, kappa, col, NULL, NULL, NULL);
+                        for (int ch = 0; ch < 3; ch++) C[ch] += T * (1.0 - surv) * col[ch];
+                        T *= surv;
+                        nseg++;
+                    }
+                }
+                for (int ch = 0; ch < 3; ch++) out_rgb[3 * k + ch] = C[ch];
+                out_T[k] = T;
+                if (out_nseg) out_nseg[k] = nseg;
+            }
+        }
+    }
+    return 0;
+}

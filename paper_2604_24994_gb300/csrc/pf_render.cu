@@ -81,7 +81,6 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, i
         while (mask) {
             const int j = __ffs(mask) - 1;
             mask &= mask - 1;
-            if (__all_sync(0xffffffffu, done)) break;
             const float *cr = sg.cr(buf) + j * CELLREC_F;
             const float *vr = sg.vr(buf) + j * VIEWREC_F;
             Chord ch;

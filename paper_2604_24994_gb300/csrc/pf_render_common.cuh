@@ -369,6 +369,8 @@ __device__ __forceinline__ bool clip_chord(const float *__restrict__ cr, const f
         ka = K_CAMERA;
     }
     sg.refined = ch.refined;
+    // d.a of the constraint at each end, carried along (+inf for sphere and camera ends)
+    float dena = CUDART_INF_F, denb = CUDART_INF_F;
     // the dipole's dense half n.y <= offset first (it removes about half of
     // the ball): a bound from below when d.n < 0 (sign bit, so -0 counts as
     // below), from above otherwise; d.n = +-0 gives +-inf or NaN, which moves
@@ -392,8 +394,10 @@ __device__ __forceinline__ bool clip_chord(const float *__restrict__ cr, const f
         const bool ub = !ent && t < sb;
         sa = ua ? t : sa;
         ka = ua ? K_FACE : ka;
+        dena = ua ? fden : dena;
         sb = ub ? t : sb;
         kb = ub ? K_FACE : kb;
+        denb = ub ? fden : denb;
         sg.dnd = fden;
         if (fabsf(fden) < 0x1p-20f) sg.dnd = face_side64(cr, ray);
     }
@@ -416,8 +420,10 @@ __device__ __forceinline__ bool clip_chord(const float *__restrict__ cr, const f
             const bool ub = !ent && t < sb;
             sa = ua ? t : sa;
             ka = ua ? k + u : ka;
+            dena = ua ? den : dena;
             sb = ub ? t : sb;
             kb = ub ? k + u : kb;
+            denb = ub ? den : denb;
             if (NEED && need == np && !(sb > sa)) need = k + u + 1;
         }
         if (lanes && !__any_sync(lanes, sb > sa)) {
@@ -426,11 +432,6 @@ __device__ __forceinline__ bool clip_chord(const float *__restrict__ cr, const f
         }
     }
     sg.nplanes = NEED ? need : min(k, np);
-    // d.a of the constraints at the ends (+inf for sphere / camera ends); a
-    // cell without planes reads some other slot of the batch and discards it
-    const float4 Pa = pl[max(ka, 0)], Pb = pl[max(kb, 0)];
-    float dena = ka >= 0 ? dot3(dh, f3(Pa.x, Pa.y, Pa.z)) : (ka == K_FACE ? fden : CUDART_INF_F);
-    float denb = kb >= 0 ? dot3(dh, f3(Pb.x, Pb.y, Pb.z)) : (kb == K_FACE ? fden : CUDART_INF_F);
     if (!(sb > sa)) return false;
     // near-parallel plane or face at an end: recompute that end in FP64
     const float lim = PLANE_ERR * sig * (1.0f / REFINE_EPS);

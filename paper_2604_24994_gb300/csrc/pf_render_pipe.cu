@@ -281,7 +281,6 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_pipe_kernel(RenderArgs
                 while (mask) {
                     const int j = __ffs(mask) - 1;
                     mask &= mask - 1;
-                    if (__all_sync(0xffffffffu, done)) break;
                     const float *cr = st.cr + j * CELLREC_F;
                     const float *vr = st.vr + j * VIEWREC_F;
                     Chord ch;

@@ -1,7 +1,10 @@
 """Parity at the benchmark's full sizes, in the benchmark's launch
 configuration: sampled outputs the oracle computes one by one.
 
-- capture workload: 1M cells, 1920x1080 (forward, sampled pixels);
+- capture workload: 1M cells, 1920x1080 (forward): sampled pixels against
+  the brute-force oracle, then every pixel of the frame against the
+  oracle's FP64 tile-list renderer (pinned to the brute-force oracle on the
+  CPU), and the bins bit for bit;
 - training workload: 100k cells on a ring of eight views; its gradients
   for an L2 loss against a target rendered from a perturbed copy, at
   64x64, against the oracle's adjoint (1e-3 relative L2 per tensor) and
@@ -66,6 +69,13 @@ def test_capture_workload_1080p_sampled_pixels():
     assert np.array_equal(ts.astype(np.int64), st_o)
     assert np.array_equal(cells[:st_o[-1]].astype(np.int64), cells_o)
     assert st_o[-1] > 3_000_000 and np.diff(st_o).max() > 2048   # the large-list sort ran too
+    # every pixel of the frame: the oracle's FP64 renderer over the same tile
+    # lists and neighbour lists, stopping where the kernel stops (T < 1e-6)
+    orc.clear_candidates()
+    orc.set_neighbour_lists(sc.nbr)
+    rgb_f, T_f = orc.render_tiles(cam, st_o, cells_o, t_stop=1e-6)
+    assert_close_image(rgb, T, rgb_f, T_f, "capture 1080p, full frame")
+    np.testing.assert_allclose(rgb_f[idx], rgb_o, rtol=0, atol=1e-5)
 
 
 @pytest.fixture(scope="module")
