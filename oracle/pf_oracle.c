@@ -913,14 +913,17 @@ int orc_render_grad(const orc_scene *s, const orc_cands *cd, const orc_camera *c
  * the painter key pow(o, p_i) (Sec. 3.2; Thm. power_painter orders cells by
  * the power distance of the camera centre).
  *
- * The rectangle is the exact image-plane bounding box of the projected
- * sphere (the tangent lines from the camera centre in the x-z and y-z
- * planes, slopes (X Z -+ r sqrt(X^2 + Z^2 - r^2)) / (Z^2 - r^2)), widened by
- * 1e-6 px, and clipped to the image.  A sphere that reaches the plane
- * z = 0 gets the whole image unless it lies entirely outside a side plane
- * of the view frustum.  Every step is one IEEE operation
- * in double precision, in the order written (the library evaluates the same
- * rule), so the tile sets can be compared bit for bit.
+ * The rectangle is the image-plane bounding box of the projected sphere
+ * (the tangent lines from the camera centre in the x-z and y-z planes,
+ * slopes (X Z -+ r sqrt(X^2 + Z^2 - r^2)) / (Z^2 - r^2)), clipped to the
+ * image.  For a centre at camera depth Z > 2 r it is evaluated in float from
+ * X, Y, Z rounded to float and widened by e = 2^-18 (|f| (|X| / Z + 1) + |c|)
+ * pixels per axis (twice a bound on that evaluation's rounding error, about
+ * 32 ulps of those magnitudes); nearer spheres take the same box in double,
+ * widened by 1e-6 px.  A sphere that reaches the plane z = 0 gets the whole
+ * image unless it lies entirely outside a side plane of the view frustum.
+ * Every step is one IEEE operation, in the order written (the library
+ * evaluates the same rule), so the tile sets can be compared bit for bit.
  * ------------------------------------------------------------------------ */
 #define ORC_TILE 16
 
@@ -951,6 +954,29 @@ void orc_bin_cell(const orc_camera *cam, const double *pos, const double *w, con
     if (Z + r <= 0.0) return; /* entirely behind the camera */
     double W = cam->width, H = cam->height;
     double ulo = -INFINITY, uhi = INFINITY, vlo = -INFINITY, vhi = INFINITY;
+    double a0, a1, b0, b1;
+    if (Z > 2.0 * r) {
+        /* well in front: the same box in float, widened by its rounding bound */
+        float Xf = (float)X, Yf = (float)Y, Zf = (float)Z, rf = (float)r;
+        float fxf = (float)cam->fx, fyf = (float)cam->fy, cxf = (float)cam->cx, cyf = (float)cam->cy;
+        float rr = rf * rf, zz = Zf * Zf;
+        float izr = 1.0f / (zz - rr);
+        float sx = sqrtf((Xf * Xf + zz) - rr);
+        float sy = sqrtf((Yf * Yf + zz) - rr);
+        float xz = Xf * Zf, yz = Yf * Zf;
+        float rsx = rf * sx, rsy = rf * sy;
+        float flo = fxf * ((xz - rsx) * izr) + cxf;
+        float fhi = fxf * ((xz + rsx) * izr) + cxf;
+        float glo = fyf * ((yz - rsy) * izr) + cyf;
+        float ghi = fyf * ((yz + rsy) * izr) + cyf;
+        float ex = 0x1p-18f * (fabsf(fxf) * (fabsf(Xf) / Zf + 1.0f) + fabsf(cxf));
+        float ey = 0x1p-18f * (fabsf(fyf) * (fabsf(Yf) / Zf + 1.0f) + fabsf(cyf));
+        a0 = ceilf((flo - 0.5f) - ex);
+        a1 = floorf((fhi - 0.5f) + ex);
+        b0 = ceilf((glo - 0.5f) - ey);
+        b1 = floorf((ghi - 0.5f) + ey);
+        goto clip;
+    }
     if (Z > r) {
         /* tangent lines from the camera centre to the sphere's x-z and y-z circles */
         double rr = r * r;
@@ -974,8 +1000,11 @@ void orc_bin_cell(const orc_camera *cam, const double *pos, const double *w, con
         if (ku * Z - Y > r * sqrt(1.0 + ku * ku)) return;
     }
     /* pixel centres u + 0.5 inside [ulo, uhi], widened by 1e-6 px */
-    double a0 = orc_ceil((ulo - 0.5) - 1e-6), a1 = orc_floor((uhi - 0.5) + 1e-6);
-    double b0 = orc_ceil((vlo - 0.5) - 1e-6), b1 = orc_floor((vhi - 0.5) + 1e-6);
+    a0 = orc_ceil((ulo - 0.5) - 1e-6);
+    a1 = orc_floor((uhi - 0.5) + 1e-6);
+    b0 = orc_ceil((vlo - 0.5) - 1e-6);
+    b1 = orc_floor((vhi - 0.5) + 1e-6);
+clip:
     if (a0 < 0.0) a0 = 0.0;
     if (b0 < 0.0) b0 = 0.0;
     if (a1 > W - 1.0) a1 = W - 1.0;

@@ -9,8 +9,8 @@
 //      finds its cell by binary search, its tile inside the cell's
 //      rectangle, and takes a slot in the tile's bucket;
 //   4. one CTA per tile sorts the bucket by (key, cell): a bitonic network
-//      in shared memory (24 KB for up to 2048 entries, 192 KB for up to
-//      16384), or in global memory for larger buckets.
+//      in 24 KB of shared memory for up to 2048 entries, a radix sort in
+//      208 KB for up to 16384, a bitonic network in global memory beyond.
 // The result does not depend on the order of the atomic slot grabs: the
 // composite key (key, cell) is unique.
 #include "pf_internal.cuh"
@@ -21,20 +21,35 @@ constexpr int SCAN_T = 1024;         // threads per scan block
 constexpr int SCAN_E = 2 * SCAN_T;   // elements per scan block
 
 // --------------------------------------------------------------- tile counts
-__global__ void tile_counts_kernel(const ViewDev *__restrict__ views, int32_t *__restrict__ diff,
-                                   uint32_t *__restrict__ tile_cnt) {
+// One CTA per view: the 2D difference grid becomes per-tile counts by an
+// inclusive prefix along rows (one warp per row, 32 columns per step, a
+// shuffle scan and a carry) and then along columns (one lane per column,
+// coalesced row by row).
+constexpr int TC_T = 1024;
+
+__global__ void __launch_bounds__(TC_T) tile_counts_kernel(const ViewDev *__restrict__ views, int32_t *__restrict__ diff,
+                                                          uint32_t *__restrict__ tile_cnt) {
     const ViewDev &V = views[blockIdx.x];
     const int gw = V.tiles_x + 1, gh = V.tiles_y + 1;
     int32_t *g = diff + V.diff_base;
-    for (int y = threadIdx.x; y < gh; y += blockDim.x) {  // prefix along rows
-        int32_t acc = 0;
-        for (int x = 0; x < gw; x++) {
-            acc += g[y * gw + x];
-            g[y * gw + x] = acc;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int y = warp; y < gh; y += TC_T / 32) {
+        int32_t carry = 0;
+        for (int x0 = 0; x0 < gw; x0 += 32) {
+            const int x = x0 + lane;
+            int32_t v = x < gw ? g[y * gw + x] : 0;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int32_t u = __shfl_up_sync(0xffffffffu, v, d);
+                if (lane >= d) v += u;
+            }
+            v += carry;
+            if (x < gw) g[y * gw + x] = v;
+            carry = __shfl_sync(0xffffffffu, v, 31);
         }
     }
     __syncthreads();
-    for (int x = threadIdx.x; x < gw; x += blockDim.x) {  // then along columns
+    for (int x = threadIdx.x; x < gw; x += TC_T) {
         int32_t acc = 0;
         for (int y = 0; y < gh; y++) {
             acc += g[y * gw + x];
@@ -42,7 +57,7 @@ __global__ void tile_counts_kernel(const ViewDev *__restrict__ views, int32_t *_
         }
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < V.tiles_x * V.tiles_y; t += blockDim.x) {
+    for (int t = threadIdx.x; t < V.tiles_x * V.tiles_y; t += TC_T) {
         const int y = t / V.tiles_x, x = t - y * V.tiles_x;
         tile_cnt[V.tile_base + t] = (uint32_t)g[y * gw + x];
     }
@@ -156,40 +171,70 @@ __device__ __forceinline__ int find_view(const ViewDev *views, int nv, int64_t t
     return lo;
 }
 
-__global__ void __launch_bounds__(256) expand_kernel(const ViewDev *__restrict__ views, int64_t N, int64_t VN,
-                                                     const uint32_t *__restrict__ celloff,
-                                                     const ushort4 *__restrict__ rect,
-                                                     const unsigned long long *__restrict__ key,
-                                                     const uint32_t *__restrict__ tile_start,
-                                                     uint32_t *__restrict__ tile_cursor,
-                                                     const Counters *__restrict__ ctr, unsigned long long cap,
-                                                     unsigned long long *__restrict__ inst_key,
-                                                     uint32_t *__restrict__ inst_cell) {
+// Instances in chunks of EXP_T * EXP_I consecutive indices per CTA step:
+// two threads find the (view, cell) of the chunk's first and last instance
+// by binary search over the first-instance offsets in global memory; when
+// the cells between them fit, their offsets are staged in shared memory and
+// every instance finds its cell there.
+constexpr int EXP_T = 256, EXP_I = 4, EXP_CAP = 4096;
+
+// last c in [lo, hi] with off(c) <= k (off non-decreasing, off(lo) <= k)
+template <typename Off>
+__device__ __forceinline__ int64_t last_le(Off off, int64_t lo, int64_t hi, unsigned long long k) {
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if ((unsigned long long)off(mid) <= k) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(EXP_T) expand_kernel(const ViewDev *__restrict__ views, int64_t N, int64_t VN,
+                                                       const uint32_t *__restrict__ celloff,
+                                                       const ushort4 *__restrict__ rect,
+                                                       const unsigned long long *__restrict__ key,
+                                                       const uint32_t *__restrict__ tile_start,
+                                                       uint32_t *__restrict__ tile_cursor,
+                                                       const Counters *__restrict__ ctr, unsigned long long cap,
+                                                       unsigned long long *__restrict__ inst_key,
+                                                       uint32_t *__restrict__ inst_cell) {
+    __shared__ uint32_t soff[EXP_CAP];
+    __shared__ int64_t range[2];
     const unsigned long long total = ctr->total_inst;
     const unsigned long long lim = total < cap ? total : cap;
-    for (unsigned long long k = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; k < lim;
-         k += (unsigned long long)gridDim.x * blockDim.x) {
-        // last (view, cell) whose first instance is <= k
-        int64_t lo = 0, hi = VN - 1;
-        while (lo < hi) {
-            const int64_t mid = (lo + hi + 1) >> 1;
-            if ((unsigned long long)celloff[mid] <= k) lo = mid; else hi = mid - 1;
+    constexpr unsigned long long CH = (unsigned long long)EXP_T * EXP_I;
+    auto goff = [&](int64_t c) { return celloff[c]; };
+    for (unsigned long long k0 = (unsigned long long)blockIdx.x * CH; k0 < lim;
+         k0 += (unsigned long long)gridDim.x * CH) {
+        const unsigned long long k1 = (k0 + CH < lim ? k0 + CH : lim) - 1;
+        if (threadIdx.x == 0) range[0] = last_le(goff, 0, VN - 1, k0);
+        if (threadIdx.x == 32) range[1] = last_le(goff, 0, VN - 1, k1);
+        __syncthreads();
+        const int64_t lo = range[0], hi = range[1];
+        const bool staged = hi - lo + 1 <= EXP_CAP;
+        if (staged)
+            for (int64_t q = threadIdx.x; q <= hi - lo; q += EXP_T) soff[q] = celloff[lo + q];
+        __syncthreads();
+        for (int r = 0; r < EXP_I; r++) {
+            const unsigned long long k = k0 + (unsigned long long)r * EXP_T + threadIdx.x;
+            if (k > k1) break;
+            const int64_t c = staged ? last_le([&](int64_t x) { return soff[x - lo]; }, lo, hi, k)
+                                     : last_le(goff, lo, hi, k);
+            const int v = (int)(c / N);
+            const uint32_t cell = (uint32_t)(c - (int64_t)v * N);
+            const ushort4 rc = rect[c];
+            const uint32_t local = (uint32_t)(k - celloff[c]);
+            const uint32_t w = (uint32_t)(rc.z - rc.x + 1);
+            const uint32_t ty = rc.y + local / w, tx = rc.x + local % w;
+            const ViewDev &V = views[v];
+            const int64_t tile = V.tile_base + (int64_t)ty * V.tiles_x + tx;
+            const uint32_t slot = atomicAdd(&tile_cursor[tile], 1u);
+            const unsigned long long pos = (unsigned long long)tile_start[tile] + slot;
+            if (pos < cap) {
+                inst_key[pos] = key[c];
+                inst_cell[pos] = cell;
+            }
         }
-        const int64_t c = lo;
-        const int v = (int)(c / N);
-        const uint32_t cell = (uint32_t)(c - (int64_t)v * N);
-        const ushort4 r = rect[c];
-        const uint32_t local = (uint32_t)(k - celloff[c]);
-        const uint32_t w = (uint32_t)(r.z - r.x + 1);
-        const uint32_t ty = r.y + local / w, tx = r.x + local % w;
-        const ViewDev &V = views[v];
-        const int64_t tile = V.tile_base + (int64_t)ty * V.tiles_x + tx;
-        const uint32_t slot = atomicAdd(&tile_cursor[tile], 1u);
-        const unsigned long long pos = (unsigned long long)tile_start[tile] + slot;
-        if (pos < cap) {
-            inst_key[pos] = key[c];
-            inst_cell[pos] = cell;
-        }
+        __syncthreads();  // soff and range are rewritten for the next chunk
     }
 }
 
@@ -240,6 +285,142 @@ __device__ void bitonic_sort(KeyArr keys, CellArr cells, int n) {
     }
 }
 
+// Stable LSD radix sort of one tile's list in shared memory, 4-bit digits.
+// The 64-bit keys stay in place (keys[q] = key of bucket entry q); 16-bit
+// entry indices move between ia and ib.  Thread t owns the contiguous
+// entries [t E, (t + 1) E), E = ceil(n / NT) <= 32, so the order of equal
+// digits is (thread, position) order, the list order before the pass.
+// Digit positions where every key has the same bits are skipped.  Equal
+// keys end in bucket order, which the atomic slot grabs made arbitrary: a
+// final pass puts each run of equal keys in cell order.  gkey / cells:
+// the bucket in global memory; keys: n words, ia / ib: n entries, cnt:
+// 16 NT counters, red: 2 NT / 32 words of shared memory.  Returns the
+// array (ia or ib) that holds the sorted entry order.
+template <int NT>
+__device__ uint16_t *radix_sort_tile(int n, const unsigned long long *__restrict__ gkey,
+                                     const uint32_t *__restrict__ cells, unsigned long long *keys, uint16_t *ia,
+                                     uint16_t *ib, uint16_t *cnt, unsigned long long *red) {
+    constexpr int NW = NT / 32;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    // bits that differ between keys: OR ^ AND over the list
+    unsigned long long o = 0ull, a = ~0ull;
+    for (int q = t; q < n; q += NT) {
+        const unsigned long long k = gkey[q];
+        keys[q] = k;
+        o |= k;
+        a &= k;
+        ia[q] = (uint16_t)q;
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        o |= __shfl_xor_sync(0xffffffffu, o, d);
+        a &= __shfl_xor_sync(0xffffffffu, a, d);
+    }
+    if (lane == 0) {
+        red[warp] = o;
+        red[NW + warp] = a;
+    }
+    __syncthreads();
+    unsigned long long vo = 0ull, va = ~0ull;
+#pragma unroll
+    for (int w = 0; w < NW; w++) {
+        vo |= red[w];
+        va &= red[NW + w];
+    }
+    const unsigned long long vary = vo ^ va;
+    __syncthreads();  // red is reused by the scans
+    const int E = (n + NT - 1) / NT;
+    const int b = min(n, t * E), e = min(n, b + E);
+    for (int sh = 0; sh < 64; sh += 4) {
+        if (((vary >> sh) & 15ull) == 0ull) continue;  // the same for every thread
+        // this thread's digit counts, eight bits each (E <= 32)
+        unsigned long long c0 = 0ull, c1 = 0ull;
+        for (int i = b; i < e; i++) {
+            const unsigned dg = (unsigned)(keys[ia[i]] >> sh) & 15u;
+            if (dg < 8)
+                c0 += 1ull << (8 * dg);
+            else
+                c1 += 1ull << (8 * (dg - 8));
+        }
+#pragma unroll
+        for (int dg = 0; dg < 16; dg++)
+            cnt[dg * NT + t] = (uint16_t)(((dg < 8 ? c0 >> (8 * dg) : c1 >> (8 * (dg - 8)))) & 0xffull);
+        __syncthreads();
+        // exclusive scan of cnt in (digit, thread) order: 16 entries per thread
+        uint16_t *mine = cnt + 16 * t;
+        unsigned run = 0;
+#pragma unroll
+        for (int r = 0; r < 16; r++) run += mine[r];
+        unsigned incl = run;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += y;
+        }
+        if (lane == 31) red[warp] = incl;
+        __syncthreads();
+        unsigned before = incl - run;
+        for (int w = 0; w < warp; w++) before += (unsigned)red[w];
+#pragma unroll
+        for (int r = 0; r < 16; r++) {
+            const unsigned x = mine[r];
+            mine[r] = (uint16_t)before;
+            before += x;
+        }
+        __syncthreads();
+        for (int i = b; i < e; i++) {
+            const uint16_t x = ia[i];
+            const unsigned dg = (unsigned)(keys[x] >> sh) & 15u;
+            const unsigned pos = cnt[dg * NT + t];
+            cnt[dg * NT + t] = (uint16_t)(pos + 1u);
+            ib[pos] = x;
+        }
+        __syncthreads();
+        uint16_t *sw = ia;
+        ia = ib;
+        ib = sw;
+    }
+    // runs of equal keys into cell order (insertion sort by the run's first thread)
+    bool tie = false;
+    for (int q = t; q + 1 < n; q += NT) tie |= keys[ia[q]] == keys[ia[q + 1]];
+    if (__syncthreads_or(tie)) {
+        for (int q = t; q + 1 < n; q += NT) {
+            const unsigned long long k = keys[ia[q]];
+            if (k != keys[ia[q + 1]] || (q > 0 && keys[ia[q - 1]] == k)) continue;
+            int r = q + 2;
+            while (r < n && keys[ia[r]] == k) r++;
+            for (int i = q + 1; i < r; i++) {
+                const uint16_t x = ia[i];
+                const uint32_t cx = cells[x];
+                int j = i - 1;
+                while (j >= q && cells[ia[j]] > cx) {
+                    ia[j + 1] = ia[j];
+                    j--;
+                }
+                ia[j + 1] = x;
+            }
+        }
+        __syncthreads();
+    }
+    return ia;
+}
+
+// Shared memory of a sorting CTA: keys [CAP] (8 B), two entry-index arrays
+// [CAP] (2 B each; the bitonic path keeps cells [CAP] (4 B) there), digit
+// counters [16 NT] (2 B), reduction words [2 NT / 32] (8 B).
+template <int CAP, int NT>
+struct SortSmem {
+    static constexpr size_t keys = 0, ia = keys + (size_t)CAP * 8, ib = ia + (size_t)CAP * 2,
+                            cnt = ib + (size_t)CAP * 2, red = cnt + (size_t)16 * NT * 2,
+                            bytes = red + (size_t)2 * (NT / 32) * 8;
+};
+
+// Lists of at most this many entries take the bitonic network, longer ones
+// the radix sort (measured on GB300: the 256 thread CTA sorts lists of up
+// to 2048 entries faster with the network, the 512 thread CTA lists of
+// 2049-16384 entries three times faster with the radix sort).
+constexpr int BITONIC_MAX = 2048;
+
 // One CTA per tile.  Variant <LO, CAP>: buckets with LO < n <= CAP are
 // sorted in shared memory; with GLOBAL, buckets above CAP are sorted in
 // place in the global scratch arrays.
@@ -247,7 +428,8 @@ template <int LO, int CAP, int NT, bool GLOBAL>
 __device__ __forceinline__ void sort_tile(int64_t t, const uint32_t *__restrict__ tile_start, unsigned long long cap,
                                           const unsigned long long *inst_key, const uint32_t *inst_cell,
                                           uint32_t *__restrict__ inst_sorted, unsigned long long *tmp_key,
-                                          uint32_t *tmp_cell, unsigned long long *sk, uint32_t *sc) {
+                                          uint32_t *tmp_cell, char *smem) {
+    using L = SortSmem<CAP, NT>;
     unsigned long long s = tile_start[t], e = tile_start[t + 1];
     if (s > cap) s = cap;
     if (e > cap) e = cap;
@@ -257,7 +439,9 @@ __device__ __forceinline__ void sort_tile(int64_t t, const uint32_t *__restrict_
         if (threadIdx.x == 0) inst_sorted[s] = inst_cell[s];
         return;
     }
-    if (n <= CAP) {
+    unsigned long long *sk = reinterpret_cast<unsigned long long *>(smem + L::keys);
+    if (n <= BITONIC_MAX) {
+        uint32_t *sc = reinterpret_cast<uint32_t *>(smem + L::ia);
         for (int q = threadIdx.x; q < n; q += NT) {
             sk[q] = inst_key[s + q];
             sc[q] = inst_cell[s + q];
@@ -265,6 +449,12 @@ __device__ __forceinline__ void sort_tile(int64_t t, const uint32_t *__restrict_
         __syncthreads();
         bitonic_sort(sk, sc, (int)n);
         for (int q = threadIdx.x; q < n; q += NT) inst_sorted[s + q] = sc[q];
+    } else if (CAP > BITONIC_MAX && n <= CAP) {
+        const uint16_t *ord = radix_sort_tile<NT>(
+            (int)n, inst_key + s, inst_cell + s, sk, reinterpret_cast<uint16_t *>(smem + L::ia),
+            reinterpret_cast<uint16_t *>(smem + L::ib), reinterpret_cast<uint16_t *>(smem + L::cnt),
+            reinterpret_cast<unsigned long long *>(smem + L::red));
+        for (int q = threadIdx.x; q < n; q += NT) inst_sorted[s + q] = inst_cell[s + ord[q]];
     } else if (GLOBAL) {
         unsigned long long *gk = tmp_key + s;
         uint32_t *gc = tmp_cell + s;
@@ -285,14 +475,13 @@ __global__ void __launch_bounds__(NT) sort_small_tiles_kernel(const uint32_t *__
                                                               const unsigned long long *inst_key,
                                                               const uint32_t *inst_cell,
                                                               uint32_t *__restrict__ inst_sorted) {
-    extern __shared__ unsigned long long sk[];
-    uint32_t *sc = reinterpret_cast<uint32_t *>(sk + CAP);
+    extern __shared__ unsigned long long smem_sort[];
     unsigned long long s = tile_start[blockIdx.x], e = tile_start[blockIdx.x + 1];
     if (s > cap) s = cap;
     if (e > cap) e = cap;
     if (e - s > (unsigned long long)CAP) return;  // the persistent kernel sorts it
     sort_tile<0, CAP, NT, false>(blockIdx.x, tile_start, cap, inst_key, inst_cell, inst_sorted, nullptr, nullptr,
-                                 sk, sc);
+                                 reinterpret_cast<char *>(smem_sort));
 }
 
 // Persistent CTAs over the render order (tiles by decreasing list length,
@@ -307,16 +496,15 @@ __global__ void __launch_bounds__(NT) sort_large_tiles_kernel(const uint32_t *__
                                                               const uint32_t *inst_cell,
                                                               uint32_t *__restrict__ inst_sorted,
                                                               unsigned long long *tmp_key, uint32_t *tmp_cell) {
-    extern __shared__ unsigned long long sk[];
-    uint32_t *sc = reinterpret_cast<uint32_t *>(sk + CAP);
+    extern __shared__ unsigned long long smem_sort[];
     for (int64_t i = blockIdx.x; i < T; i += gridDim.x) {
         const int64_t t = order[i];
         unsigned long long s = tile_start[t], e = tile_start[t + 1];
         if (s > cap) s = cap;
         if (e > cap) e = cap;
         if (e - s < (unsigned long long)LO) break;  // the same for every thread of the CTA
-        sort_tile<LO, CAP, NT, true>(t, tile_start, cap, inst_key, inst_cell, inst_sorted, tmp_key, tmp_cell, sk,
-                                     sc);
+        sort_tile<LO, CAP, NT, true>(t, tile_start, cap, inst_key, inst_cell, inst_sorted, tmp_key, tmp_cell,
+                                     reinterpret_cast<char *>(smem_sort));
         __syncthreads();  // shared memory is reused by the next list
     }
 }
@@ -359,7 +547,7 @@ cudaError_t launch_bin_sort(const Plan &p, const WS &w, cudaStream_t st) {
     // per-tile counts into tile_start[0..T), then exclusive scan over T+1 entries
     e = cudaMemsetAsync(w.tile_start + T, 0, sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
-    tile_counts_kernel<<<p.nv, 256, 0, st>>>(w.views, w.diff, w.tile_start);
+    tile_counts_kernel<<<p.nv, TC_T, 0, st>>>(w.views, w.diff, w.tile_start);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     e = exclusive_scan(w.tile_start, T + 1, w.scan_tmp, nullptr, nullptr, 0, st);
     if (e != cudaSuccess) return e;
@@ -376,7 +564,7 @@ cudaError_t launch_bin_sort(const Plan &p, const WS &w, cudaStream_t st) {
         int dev = 0, sms = 148;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        expand_kernel<<<sms * 8, 256, 0, st>>>(w.views, p.n, VN, w.celloff, w.rect, w.key, w.tile_start,
+        expand_kernel<<<sms * 8, EXP_T, 0, st>>>(w.views, p.n, VN, w.celloff, w.rect, w.key, w.tile_start,
                                                  w.tile_cursor, w.counters, p.cap, w.inst_key, w.inst_cell);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
@@ -385,11 +573,13 @@ cudaError_t launch_bin_sort(const Plan &p, const WS &w, cudaStream_t st) {
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (T > 0) {
-        // small buckets (<= 2048) in 24 KB of shared memory, large ones in 192 KB
+        // small buckets (<= 2048) in 24 KB of shared memory (bitonic), large ones in 208 KB (radix)
         constexpr int SMALL = 2048, LARGE = 16384;
         auto ks = sort_small_tiles_kernel<SMALL, 256>;
         auto kl = sort_large_tiles_kernel<SMALL, LARGE, 512>;
-        const size_t ss = (size_t)SMALL * 12, sl = (size_t)LARGE * 12;
+        static_assert(SMALL <= BITONIC_MAX, "the small-list kernel sorts with the bitonic network only");
+        const size_t ss = (size_t)SMALL * 12, sl = SortSmem<LARGE, 512>::bytes;
+        cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
         cudaFuncSetAttribute(kl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sl);
         ks<<<(unsigned)T, 256, ss, st>>>(w.tile_start, p.cap, w.inst_key, w.inst_cell, w.inst_sorted);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -199,14 +199,19 @@ __global__ void __launch_bounds__(256) prepare_kernel(pf_scene s, const float4 *
 // Painter key: pow(o, p_i) = |p_i - o|^2 - w_i in FP64 (Thm. power_painter),
 // mapped to order-preserving unsigned bits.
 //
-// Tile rectangle: the exact image-plane bounding box of the sphere (p_i,
-// R_i), from the tangent lines through the camera centre in the camera's
-// x-z and y-z planes, widened by 1e-6 px, covering every pixel whose centre
-// lies inside it.  A sphere reaching z <= 0 gets the whole image unless it
-// lies entirely outside one side plane of the frustum; one entirely behind
-// is dropped.  Every operation is an explicitly rounded IEEE double
-// operation (no contraction), so a CPU evaluating the same rule in the same
-// order gets the same rectangles bit for bit.
+// Tile rectangle: the image-plane bounding box of the sphere (p_i, R_i),
+// from the tangent lines through the camera centre in the camera's x-z and
+// y-z planes, covering every pixel whose centre lies inside it.  For a
+// sphere well in front of the camera plane (camera-frame Z > 2 R) the box
+// is evaluated in float from the camera-frame centre rounded to float, and
+// widened by 2^-18 (|f| (|X| / Z + 1) + |c|) pixels per axis, a bound on the
+// float evaluation's rounding (about 32 ulps of those magnitudes); closer
+// spheres take the same box in double, widened by 1e-6 px.  A sphere
+// reaching z <= 0 gets the whole image unless it lies entirely outside one
+// side plane of the frustum; one entirely behind is dropped.  Every
+// operation is an explicitly rounded IEEE operation (no contraction), so a
+// CPU evaluating the same rule in the same order gets the same rectangles
+// bit for bit.
 //
 // Site offset m = o - p_i is stored as a float pair (hi + lo ~ 48 bits) for
 // the renderer's compensated products; Rt^2 is a conservative radius^2 for
@@ -244,9 +249,10 @@ __global__ void __launch_bounds__(256) project_kernel(pf_scene s, const ViewDev 
         const float hx = __double2float_rn(mx), hy = __double2float_rn(my), hz = __double2float_rn(mz);
         const float lx = __double2float_rn(mx - (double)hx), ly = __double2float_rn(my - (double)hy),
                     lz = __double2float_rn(mz - (double)hz);
-        const double mlen = sqrt(mx * mx + my * my + mz * mz);
-        const double Rt = (double)s.R[i] * (1.0 + 0x1p-20) + mlen * 0x1p-20;
-        const float rt2 = __double2float_ru(Rt * Rt * (1.0 + 0x1p-20));
+        // |m| only sets the margin 2^-20 |m| of the bound radius: float is plenty
+        const float mlen = sqrtf(fmaf(hx, hx, fmaf(hy, hy, hz * hz)));
+        const float Rt = __fmaf_ru(mlen, 0x1p-19f, __fmul_ru(s.R[i], 1.0f + 0x1p-20f));
+        const float rt2 = __fmul_ru(__fmul_ru(Rt, Rt), 1.0f + 0x1p-20f);
         float4 *vr = reinterpret_cast<float4 *>(viewrec + idx * VIEWREC_F);
         vr[0] = make_float4(hx, hy, hz, rt2);
         vr[1] = make_float4(lx, ly, lz, sphere_refine_threshold(s.R[i], s.sigma[i]));
@@ -262,6 +268,8 @@ __global__ void __launch_bounds__(256) project_kernel(pf_scene s, const ViewDev 
     bool vis = !(DADD(Z, r) <= 0.0);
     const double W = V.width, H = V.height;
     double ulo = -CUDART_INF, uhi = CUDART_INF, vlo = -CUDART_INF, vhi = CUDART_INF;
+    bool fast = false;                  // the float box below
+    float fa0 = 0.f, fa1 = 0.f, fb0 = 0.f, fb1 = 0.f;
     if (V.model == PF_FISHEYE) {
         // equidistant fisheye: the directions that meet the sphere form a cap
         // of angular radius asin(r/|c|) around c; its pixels lie in the box
@@ -309,6 +317,31 @@ __global__ void __launch_bounds__(256) project_kernel(pf_scene s, const ViewDev 
             vlo = V.cy + V.fy * yl;
             vhi = V.cy + V.fy * yh;
         }
+    } else if (vis && Z > DMUL(2.0, r)) {
+        // well in front: the tangent-line box in float, widened by its rounding bound
+        fast = true;
+        const float Xf = __double2float_rn(X), Yf = __double2float_rn(Y), Zf = __double2float_rn(Z);
+        const float rf = s.R[i];
+        const float fxf = __double2float_rn(V.fx), fyf = __double2float_rn(V.fy);
+        const float cxf = __double2float_rn(V.cx), cyf = __double2float_rn(V.cy);
+        const float rr = __fmul_rn(rf, rf), zz = __fmul_rn(Zf, Zf);
+        const float izr = __fdiv_rn(1.0f, __fsub_rn(zz, rr));
+        const float sx = __fsqrt_rn(__fsub_rn(__fadd_rn(__fmul_rn(Xf, Xf), zz), rr));
+        const float sy = __fsqrt_rn(__fsub_rn(__fadd_rn(__fmul_rn(Yf, Yf), zz), rr));
+        const float xz = __fmul_rn(Xf, Zf), yz = __fmul_rn(Yf, Zf);
+        const float rsx = __fmul_rn(rf, sx), rsy = __fmul_rn(rf, sy);
+        const float flo = __fadd_rn(__fmul_rn(fxf, __fmul_rn(__fsub_rn(xz, rsx), izr)), cxf);
+        const float fhi = __fadd_rn(__fmul_rn(fxf, __fmul_rn(__fadd_rn(xz, rsx), izr)), cxf);
+        const float glo = __fadd_rn(__fmul_rn(fyf, __fmul_rn(__fsub_rn(yz, rsy), izr)), cyf);
+        const float ghi = __fadd_rn(__fmul_rn(fyf, __fmul_rn(__fadd_rn(yz, rsy), izr)), cyf);
+        const float ex = __fmul_rn(0x1p-18f, __fadd_rn(__fmul_rn(fabsf(fxf), __fadd_rn(__fdiv_rn(fabsf(Xf), Zf), 1.0f)),
+                                                       fabsf(cxf)));
+        const float ey = __fmul_rn(0x1p-18f, __fadd_rn(__fmul_rn(fabsf(fyf), __fadd_rn(__fdiv_rn(fabsf(Yf), Zf), 1.0f)),
+                                                       fabsf(cyf)));
+        fa0 = ceilf(__fsub_rn(__fsub_rn(flo, 0.5f), ex));
+        fa1 = floorf(__fadd_rn(__fsub_rn(fhi, 0.5f), ex));
+        fb0 = ceilf(__fsub_rn(__fsub_rn(glo, 0.5f), ey));
+        fb1 = floorf(__fadd_rn(__fsub_rn(ghi, 0.5f), ey));
     } else if (vis && Z > r) {
         // tangent lines from the camera centre to the sphere's x-z and y-z circles
         const double rr = DMUL(r, r);
@@ -331,8 +364,18 @@ __global__ void __launch_bounds__(256) project_kernel(pf_scene s, const ViewDev 
         if (DSUB(DMUL(V.ku, Z), Y) > DMUL(r, V.sku)) vis = false;
     }
     if (vis) {
-        double a0 = ceil(DSUB(DSUB(ulo, 0.5), 1e-6)), a1 = floor(DADD(DSUB(uhi, 0.5), 1e-6));
-        double b0 = ceil(DSUB(DSUB(vlo, 0.5), 1e-6)), b1 = floor(DADD(DSUB(vhi, 0.5), 1e-6));
+        double a0, a1, b0, b1;
+        if (fast) {  // whole numbers (or +-inf) in float: exact in double
+            a0 = fa0;
+            a1 = fa1;
+            b0 = fb0;
+            b1 = fb1;
+        } else {
+            a0 = ceil(DSUB(DSUB(ulo, 0.5), 1e-6));
+            a1 = floor(DADD(DSUB(uhi, 0.5), 1e-6));
+            b0 = ceil(DSUB(DSUB(vlo, 0.5), 1e-6));
+            b1 = floor(DADD(DSUB(vhi, 0.5), 1e-6));
+        }
         if (a0 < 0.0) a0 = 0.0;
         if (b0 < 0.0) b0 = 0.0;
         if (a1 > W - 1.0) a1 = W - 1.0;

@@ -129,3 +129,37 @@ def test_long_tile_lists_across_views_and_capacity_growth():
         assert np.array_equal(keys[v * sc.n:(v + 1) * sc.n], key_o)
         base += nt
     assert np.diff(oracle.tile_lists(*orc.bin(cam), cam.tiles_x, cam.tiles_y)[0]).max() == 256 * 70
+
+
+def test_equal_keys_in_every_sort_path_bit_exact():
+    """Cells duplicated (same site, weight and radius, so the same key) in
+    lists that take each radix sort: 488 and 1,944 entries (256 threads,
+    32 KB of shared memory), 11,674 (512 threads, 208 KB).  Equal keys must come
+    out in cell-index order, as in the CPU binning, whatever order the
+    atomic bucket fill left them in."""
+    import torch
+    from paper_2604_24994_gb300 import DeviceScene, Renderer
+    cam = inputs.look_at((3.0, 0.0, 0.0), 640, 360)
+    tiles = [(5, 5), (30, 15), (14, 9)]
+    base = column_scene(cam, tiles, [1, 4, 24], seed=2)
+    n0 = base.n
+    rng = np.random.default_rng(5)
+    # every other cell once more, every fifth cell twice more, appended in a shuffled order
+    extra = np.concatenate([np.arange(0, n0, 2), np.arange(0, n0, 5), np.arange(0, n0, 5)])
+    extra = extra[rng.permutation(extra.size)]
+    src = np.concatenate([np.arange(n0), extra])
+    sc = base.copy()
+    for k in sc.PARAMS:
+        setattr(sc, k, np.ascontiguousarray(np.asarray(getattr(base, k))[src]))
+    sc.w = np.ascontiguousarray(base.w[src])
+    sc.nbr = np.zeros((src.size, 0), np.int32)
+    ds = DeviceScene.from_numpy(sc, "cuda")
+    r = Renderer(ds.n, ds.k, [cam])
+    r.forward(ds)
+    torch.cuda.synchronize()
+    lens = compare_bins(r, sc, cam)
+    # each cell lies in one tile: its column's
+    tile_of = np.repeat(np.arange(3), [256 * 1, 256 * 4, 256 * 24])[src]
+    want = np.bincount(tile_of)
+    assert sorted(lens[lens > 0].tolist()) == sorted(want.tolist())
+    assert 256 < want[0] <= 2048 and 256 < want[1] <= 2048 and 2048 < want[2] <= 16384
