@@ -930,6 +930,11 @@ int orc_render_grad(const orc_scene *s, const orc_cands *cd, const orc_camera *c
 static double orc_ceil(double x) { return ceil(x); }
 static double orc_floor(double x) { return floor(x); }
 
+/* widening of one edge of the float box (pixels): 2^-17 (|f| ((1 + k^2) L1z + az) + |c0|) */
+static float orc_box_margin(float f, float c0, float k, float L1z, float az) {
+    return 0x1p-17f * (fabsf(f) * ((1.0f + k * k) * L1z + az) + fabsf(c0));
+}
+
 /* rect[4] = {tx0, ty0, tx1, ty1} (empty: tx0 > tx1), key = order-preserving bits of pow */
 void orc_bin_cell(const orc_camera *cam, const double *pos, const double *w, const double *R, int64_t i,
                   int32_t *rect, uint64_t *key) {
@@ -942,41 +947,60 @@ void orc_bin_cell(const orc_camera *cam, const double *pos, const double *w, con
     memcpy(&bits, &pw, 8);
     *key = (bits >> 63) ? ~bits : (bits | 0x8000000000000000ULL);
 
+    rect[0] = 1;
+    rect[1] = 1;
+    rect[2] = 0;
+    rect[3] = 0;
+    double W = cam->width, H = cam->height;
+    double ulo = -INFINITY, uhi = INFINITY, vlo = -INFINITY, vhi = INFINITY;
+    double a0, a1, b0, b1;
+    {
+        /* m = o - p as a float pair (two-sum of the origin's float high part
+         * and -p, plus its low part), then the camera-frame centre in float */
+        float hm[3];
+        for (int c = 0; c < 3; c++) {
+            float p = (float)pos[3 * i + c];
+            float a = (float)cam->origin[c];
+            float ol = (float)(cam->origin[c] - (double)a);
+            float s0 = a - p;
+            float bb = s0 - a;
+            float e0 = (a - (s0 - bb)) + (-p - bb);
+            float t0 = e0 + ol;
+            hm[c] = s0 + t0;
+        }
+        float Mf[9];
+        for (int k = 0; k < 9; k++) Mf[k] = (float)cam->rot[k];
+        float Xf = -((Mf[0] * hm[0] + Mf[1] * hm[1]) + Mf[2] * hm[2]);
+        float Yf = -((Mf[3] * hm[0] + Mf[4] * hm[1]) + Mf[5] * hm[2]);
+        float Zf = -((Mf[6] * hm[0] + Mf[7] * hm[1]) + Mf[8] * hm[2]);
+        float rf = (float)R[i];
+        if (Zf > 2.0f * rf && Zf * 1024.0f > fabsf(Xf) + fabsf(Yf)) {
+            /* well in front, within 89.9 degrees of the axis: the box in
+             * float, each edge widened by a bound on its rounding error */
+            float fxf = (float)cam->fx, fyf = (float)cam->fy, cxf = (float)cam->cx, cyf = (float)cam->cy;
+            float rr = rf * rf, zz = Zf * Zf;
+            float izr = 1.0f / (zz - rr);
+            float sx = sqrtf((Xf * Xf + zz) - rr);
+            float sy = sqrtf((Yf * Yf + zz) - rr);
+            float xz = Xf * Zf, yz = Yf * Zf;
+            float rsx = rf * sx, rsy = rf * sy;
+            float kxl = (xz - rsx) * izr, kxh = (xz + rsx) * izr;
+            float kyl = (yz - rsy) * izr, kyh = (yz + rsy) * izr;
+            float L1z = ((fabsf(Xf) + fabsf(Yf)) + Zf) / Zf;
+            float axz = fabsf(Xf) / Zf + 1.0f, ayz = fabsf(Yf) / Zf + 1.0f;
+            a0 = ceilf(((fxf * kxl + cxf) - 0.5f) - orc_box_margin(fxf, cxf, kxl, L1z, axz));
+            a1 = floorf(((fxf * kxh + cxf) - 0.5f) + orc_box_margin(fxf, cxf, kxh, L1z, axz));
+            b0 = ceilf(((fyf * kyl + cyf) - 0.5f) - orc_box_margin(fyf, cyf, kyl, L1z, ayz));
+            b1 = floorf(((fyf * kyh + cyf) - 0.5f) + orc_box_margin(fyf, cyf, kyh, L1z, ayz));
+            goto clip;
+        }
+    }
     const double *M = cam->rot;
     double X = (M[0] * dx + M[1] * dy) + M[2] * dz;
     double Y = (M[3] * dx + M[4] * dy) + M[5] * dz;
     double Z = (M[6] * dx + M[7] * dy) + M[8] * dz;
     double r = R[i];
-    rect[0] = 1;
-    rect[1] = 1;
-    rect[2] = 0;
-    rect[3] = 0;
     if (Z + r <= 0.0) return; /* entirely behind the camera */
-    double W = cam->width, H = cam->height;
-    double ulo = -INFINITY, uhi = INFINITY, vlo = -INFINITY, vhi = INFINITY;
-    double a0, a1, b0, b1;
-    if (Z > 2.0 * r) {
-        /* well in front: the same box in float, widened by its rounding bound */
-        float Xf = (float)X, Yf = (float)Y, Zf = (float)Z, rf = (float)r;
-        float fxf = (float)cam->fx, fyf = (float)cam->fy, cxf = (float)cam->cx, cyf = (float)cam->cy;
-        float rr = rf * rf, zz = Zf * Zf;
-        float izr = 1.0f / (zz - rr);
-        float sx = sqrtf((Xf * Xf + zz) - rr);
-        float sy = sqrtf((Yf * Yf + zz) - rr);
-        float xz = Xf * Zf, yz = Yf * Zf;
-        float rsx = rf * sx, rsy = rf * sy;
-        float flo = fxf * ((xz - rsx) * izr) + cxf;
-        float fhi = fxf * ((xz + rsx) * izr) + cxf;
-        float glo = fyf * ((yz - rsy) * izr) + cyf;
-        float ghi = fyf * ((yz + rsy) * izr) + cyf;
-        float ex = 0x1p-18f * (fabsf(fxf) * (fabsf(Xf) / Zf + 1.0f) + fabsf(cxf));
-        float ey = 0x1p-18f * (fabsf(fyf) * (fabsf(Yf) / Zf + 1.0f) + fabsf(cyf));
-        a0 = ceilf((flo - 0.5f) - ex);
-        a1 = floorf((fhi - 0.5f) + ex);
-        b0 = ceilf((glo - 0.5f) - ey);
-        b1 = floorf((ghi - 0.5f) + ey);
-        goto clip;
-    }
     if (Z > r) {
         /* tangent lines from the camera centre to the sphere's x-z and y-z circles */
         double rr = r * r;

@@ -21,6 +21,16 @@ constexpr int SCAN_T = 1024;         // threads per scan block
 constexpr int SCAN_E = 2 * SCAN_T;   // elements per scan block
 
 // --------------------------------------------------------------- tile counts
+// The DIFF_REP copies of the difference grids summed into the first.
+__global__ void __launch_bounds__(256) diff_sum_kernel(int32_t *__restrict__ diff, int64_t total) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        int32_t v = 0;
+#pragma unroll
+        for (int r = 0; r < DIFF_REP; r++) v += diff[total * r + q];
+        diff[q] = v;
+    }
+}
+
 // One CTA per view: the 2D difference grid becomes per-tile counts by an
 // inclusive prefix along rows (one warp per row, 32 columns per step, a
 // shuffle scan and a carry) and then along columns (one lane per column,
@@ -176,7 +186,7 @@ __device__ __forceinline__ int find_view(const ViewDev *views, int nv, int64_t t
 // by binary search over the first-instance offsets in global memory; when
 // the cells between them fit, their offsets are staged in shared memory and
 // every instance finds its cell there.
-constexpr int EXP_T = 256, EXP_I = 4, EXP_CAP = 4096;
+constexpr int EXP_T = 256, EXP_I = 4, EXP_CAP = 4096, EXP_NV = 64;
 
 // last c in [lo, hi] with off(c) <= k (off non-decreasing, off(lo) <= k)
 template <typename Off>
@@ -199,6 +209,15 @@ __global__ void __launch_bounds__(EXP_T) expand_kernel(const ViewDev *__restrict
                                                        uint32_t *__restrict__ inst_cell) {
     __shared__ uint32_t soff[EXP_CAP];
     __shared__ int64_t range[2];
+    // each view's first tile and tiles per row (of the first EXP_NV views)
+    __shared__ int64_t vtb[EXP_NV];
+    __shared__ int32_t vtx[EXP_NV];
+    const int nv = (int)(VN / N);
+    for (int q = threadIdx.x; q < nv && q < EXP_NV; q += EXP_T) {
+        vtb[q] = views[q].tile_base;
+        vtx[q] = views[q].tiles_x;
+    }
+    __syncthreads();
     const unsigned long long total = ctr->total_inst;
     const unsigned long long lim = total < cap ? total : cap;
     constexpr unsigned long long CH = (unsigned long long)EXP_T * EXP_I;
@@ -225,8 +244,8 @@ __global__ void __launch_bounds__(EXP_T) expand_kernel(const ViewDev *__restrict
             const uint32_t local = (uint32_t)(k - celloff[c]);
             const uint32_t w = (uint32_t)(rc.z - rc.x + 1);
             const uint32_t ty = rc.y + local / w, tx = rc.x + local % w;
-            const ViewDev &V = views[v];
-            const int64_t tile = V.tile_base + (int64_t)ty * V.tiles_x + tx;
+            const int64_t tile = v < EXP_NV ? vtb[v] + (int64_t)ty * vtx[v] + tx
+                                            : views[v].tile_base + (int64_t)ty * views[v].tiles_x + tx;
             const uint32_t slot = atomicAdd(&tile_cursor[tile], 1u);
             const unsigned long long pos = (unsigned long long)tile_start[tile] + slot;
             if (pos < cap) {
@@ -547,6 +566,11 @@ cudaError_t launch_bin_sort(const Plan &p, const WS &w, cudaStream_t st) {
     // per-tile counts into tile_start[0..T), then exclusive scan over T+1 entries
     e = cudaMemsetAsync(w.tile_start + T, 0, sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
+    if (p.total_diff > 0) {
+        const int64_t nb = (p.total_diff + 255) / 256;
+        diff_sum_kernel<<<(unsigned)(nb < 1024 ? nb : 1024), 256, 0, st>>>(w.diff, p.total_diff);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     tile_counts_kernel<<<p.nv, TC_T, 0, st>>>(w.views, w.diff, w.tile_start);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     e = exclusive_scan(w.tile_start, T + 1, w.scan_tmp, nullptr, nullptr, 0, st);

@@ -121,6 +121,15 @@ void fill_views(Plan *p, const pf_camera *cams) {
         d.skr = sqrt(1.0 + d.kr * d.kr);
         d.sku = sqrt(1.0 + d.ku * d.ku);
         d.skd = sqrt(1.0 + d.kd * d.kd);
+        for (int k = 0; k < 9; k++) d.rotf[k] = (float)c.rot[k];
+        d.fxf = (float)c.fx;
+        d.fyf = (float)c.fy;
+        d.cxf = (float)c.cx;
+        d.cyf = (float)c.cy;
+        for (int k = 0; k < 3; k++) {
+            d.ohi[k] = (float)c.origin[k];
+            d.olo[k] = (float)(c.origin[k] - (double)d.ohi[k]);
+        }
         d.width = c.width;
         d.height = c.height;
         d.model = c.model;
@@ -163,7 +172,7 @@ void make_layout(Plan *p) {
     L.key = take(nv * n * 8);
     L.cnt = take(nv * n * 4);
     L.celloff = take(nv * n * 4);
-    L.diff = take((uint64_t)p->total_diff * 4);
+    L.diff = take((uint64_t)p->total_diff * 4 * DIFF_REP);
     L.tile_start = take((T + 1) * 4);
     L.tile_cursor = take(T * 4);
     L.tile_order = take(T * 4);

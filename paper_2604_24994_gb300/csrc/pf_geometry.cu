@@ -224,17 +224,47 @@ __global__ void __launch_bounds__(256) prepare_kernel(pf_scene s, const float4 *
 #define DDIV __ddiv_rn
 #define DSQRT __dsqrt_rn
 
+// Widening (pixels) of one edge of the float tile box: 2^-17 (|f| ((1 + k^2)
+// |c|_1 / Z + |X| / Z + 1) + |c0|) for an edge of slope k, focal length f and
+// principal point c0, with |c|_1 / Z = (|X| + |Y| + Z) / Z.  It bounds, with a
+// factor of four to spare, the float error of the edge: about 32 ulps of
+// |f| (|X| / Z + 1) from evaluating the tangent slopes (Z > 2 R keeps
+// Z^2 - R^2 >= 3 Z^2 / 4), and 23 ulps of |f| (1 + k^2) |c|_1 / Z from the
+// camera-frame centre's own rounding (about 10 ulps of |c|_1, moving the
+// slope by (1 + k^2) times the angle it subtends).
+__device__ __forceinline__ float box_margin(float f, float c0, float k, float L1z, float az) {
+    return __fmul_rn(0x1p-17f,
+                     __fadd_rn(__fmul_rn(fabsf(f), __fadd_rn(__fmul_rn(__fadd_rn(1.0f, __fmul_rn(k, k)), L1z), az)),
+                               fabsf(c0)));
+}
+
 __global__ void __launch_bounds__(256) project_kernel(pf_scene s, const ViewDev *__restrict__ views, int nv,
                                                       const float *__restrict__ cellrec, float *__restrict__ viewrec,
                                                       ushort4 *__restrict__ rect_out,
                                                       unsigned long long *__restrict__ key_out,
-                                                      uint32_t *__restrict__ cnt_out, int32_t *__restrict__ diff) {
+                                                      uint32_t *__restrict__ cnt_out, int32_t *__restrict__ diff,
+                                                      int64_t diff_total) {
     const int64_t N = s.n_cells;
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // the views of this block's cells (one or two unless the scene has fewer
+    // cells than the block has threads), staged in shared memory: every
+    // thread reads some thirty of their fields
+    __shared__ ViewDev sv[2];
+    const int64_t first = (int64_t)blockIdx.x * blockDim.x;
+    const int v0 = (int)(first / N);
+    const int v1 = (int)min((int64_t)nv - 1, (first + blockDim.x - 1) / N);
+    const bool staged = v1 - v0 < 2;
+    if (staged) {
+        constexpr int WORDS = (int)(sizeof(ViewDev) / 4);
+        static_assert(sizeof(ViewDev) % 4 == 0, "ViewDev is copied as 32-bit words");
+        for (int q = threadIdx.x; q < WORDS * (v1 - v0 + 1); q += blockDim.x)
+            reinterpret_cast<uint32_t *>(sv)[q] = reinterpret_cast<const uint32_t *>(views + v0)[q];
+    }
+    __syncthreads();
+    const int64_t idx = first + threadIdx.x;
     if (idx >= N * nv) return;
     const int v = (int)(idx / N);
     const int64_t i = idx - (int64_t)v * N;
-    const ViewDev &V = views[v];
+    const ViewDev &V = staged ? sv[v - v0] : views[v];
     const double px = s.pos[3 * i], py = s.pos[3 * i + 1], pz = s.pos[3 * i + 2];
     const double dx = DSUB(px, V.origin[0]);
     const double dy = DSUB(py, V.origin[1]);
@@ -243,34 +273,77 @@ __global__ void __launch_bounds__(256) project_kernel(pf_scene s, const ViewDev 
     unsigned long long bits = (unsigned long long)__double_as_longlong(pw);
     key_out[idx] = (bits >> 63) ? ~bits : (bits | 0x8000000000000000ull);
 
-    // camera-relative offset m = o - p as a float pair
+    // camera-relative offset m = o - p as a float pair: Knuth's two-sum of
+    // the origin's high part and -p, then the origin's low part added
+    float hm[3], lm[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const float p = s.pos[3 * i + c];
+        const float a = V.ohi[c];
+        const float s0 = __fsub_rn(a, p);
+        const float bb = __fsub_rn(s0, a);
+        const float e0 = __fadd_rn(__fsub_rn(a, __fsub_rn(s0, bb)), __fsub_rn(-p, bb));
+        const float t0 = __fadd_rn(e0, V.olo[c]);
+        hm[c] = __fadd_rn(s0, t0);
+        lm[c] = __fsub_rn(t0, __fsub_rn(hm[c], s0));
+    }
     {
-        const double mx = -dx, my = -dy, mz = -dz;
-        const float hx = __double2float_rn(mx), hy = __double2float_rn(my), hz = __double2float_rn(mz);
-        const float lx = __double2float_rn(mx - (double)hx), ly = __double2float_rn(my - (double)hy),
-                    lz = __double2float_rn(mz - (double)hz);
-        // |m| only sets the margin 2^-20 |m| of the bound radius: float is plenty
-        const float mlen = sqrtf(fmaf(hx, hx, fmaf(hy, hy, hz * hz)));
+        // |m| only sets the margin 2^-19 |m| of the bound radius: float is plenty
+        const float mlen = sqrtf(fmaf(hm[0], hm[0], fmaf(hm[1], hm[1], hm[2] * hm[2])));
         const float Rt = __fmaf_ru(mlen, 0x1p-19f, __fmul_ru(s.R[i], 1.0f + 0x1p-20f));
         const float rt2 = __fmul_ru(__fmul_ru(Rt, Rt), 1.0f + 0x1p-20f);
         float4 *vr = reinterpret_cast<float4 *>(viewrec + idx * VIEWREC_F);
-        vr[0] = make_float4(hx, hy, hz, rt2);
-        vr[1] = make_float4(lx, ly, lz, sphere_refine_threshold(s.R[i], s.sigma[i]));
+        vr[0] = make_float4(hm[0], hm[1], hm[2], rt2);
+        vr[1] = make_float4(lm[0], lm[1], lm[2], sphere_refine_threshold(s.R[i], s.sigma[i]));
     }
 
     ushort4 rc = make_ushort4(1, 1, 0, 0);
     uint32_t count = 0;
-    const double *M = V.rot;
-    const double X = DADD(DADD(DMUL(M[0], dx), DMUL(M[1], dy)), DMUL(M[2], dz));
-    const double Y = DADD(DADD(DMUL(M[3], dx), DMUL(M[4], dy)), DMUL(M[5], dz));
-    const double Z = DADD(DADD(DMUL(M[6], dx), DMUL(M[7], dy)), DMUL(M[8], dz));
-    const double r = s.R[i];
-    bool vis = !(DADD(Z, r) <= 0.0);
+    // camera-frame centre in float from the rounded offset (d = -m)
+    const float *Mf = V.rotf;
+    const float Xf = -__fadd_rn(__fadd_rn(__fmul_rn(Mf[0], hm[0]), __fmul_rn(Mf[1], hm[1])), __fmul_rn(Mf[2], hm[2]));
+    const float Yf = -__fadd_rn(__fadd_rn(__fmul_rn(Mf[3], hm[0]), __fmul_rn(Mf[4], hm[1])), __fmul_rn(Mf[5], hm[2]));
+    const float Zf = -__fadd_rn(__fadd_rn(__fmul_rn(Mf[6], hm[0]), __fmul_rn(Mf[7], hm[1])), __fmul_rn(Mf[8], hm[2]));
+    const float rf = s.R[i];
     const double W = V.width, H = V.height;
     double ulo = -CUDART_INF, uhi = CUDART_INF, vlo = -CUDART_INF, vhi = CUDART_INF;
-    bool fast = false;                  // the float box below
+    // well in front of the camera and within 89.9 degrees of its axis: the
+    // float tile box below; otherwise the double one from the double centre
+    const bool fast = V.model != PF_FISHEYE && Zf > __fmul_rn(2.0f, rf) &&
+                      __fmul_rn(Zf, 1024.0f) > __fadd_rn(fabsf(Xf), fabsf(Yf));
+    bool vis = true;
     float fa0 = 0.f, fa1 = 0.f, fb0 = 0.f, fb1 = 0.f;
-    if (V.model == PF_FISHEYE) {
+    double X = 0.0, Y = 0.0, Z = 0.0;
+    const double r = rf;
+    if (fast) {
+        const float rr = __fmul_rn(rf, rf), zz = __fmul_rn(Zf, Zf);
+        const float izr = __fdiv_rn(1.0f, __fsub_rn(zz, rr));
+        const float sx = __fsqrt_rn(__fsub_rn(__fadd_rn(__fmul_rn(Xf, Xf), zz), rr));
+        const float sy = __fsqrt_rn(__fsub_rn(__fadd_rn(__fmul_rn(Yf, Yf), zz), rr));
+        const float xz = __fmul_rn(Xf, Zf), yz = __fmul_rn(Yf, Zf);
+        const float rsx = __fmul_rn(rf, sx), rsy = __fmul_rn(rf, sy);
+        const float kxl = __fmul_rn(__fsub_rn(xz, rsx), izr), kxh = __fmul_rn(__fadd_rn(xz, rsx), izr);
+        const float kyl = __fmul_rn(__fsub_rn(yz, rsy), izr), kyh = __fmul_rn(__fadd_rn(yz, rsy), izr);
+        const float L1z = __fdiv_rn(__fadd_rn(__fadd_rn(fabsf(Xf), fabsf(Yf)), Zf), Zf);
+        const float axz = __fadd_rn(__fdiv_rn(fabsf(Xf), Zf), 1.0f), ayz = __fadd_rn(__fdiv_rn(fabsf(Yf), Zf), 1.0f);
+        fa0 = ceilf(__fsub_rn(__fsub_rn(__fadd_rn(__fmul_rn(V.fxf, kxl), V.cxf), 0.5f),
+                              box_margin(V.fxf, V.cxf, kxl, L1z, axz)));
+        fa1 = floorf(__fadd_rn(__fsub_rn(__fadd_rn(__fmul_rn(V.fxf, kxh), V.cxf), 0.5f),
+                               box_margin(V.fxf, V.cxf, kxh, L1z, axz)));
+        fb0 = ceilf(__fsub_rn(__fsub_rn(__fadd_rn(__fmul_rn(V.fyf, kyl), V.cyf), 0.5f),
+                              box_margin(V.fyf, V.cyf, kyl, L1z, ayz)));
+        fb1 = floorf(__fadd_rn(__fsub_rn(__fadd_rn(__fmul_rn(V.fyf, kyh), V.cyf), 0.5f),
+                               box_margin(V.fyf, V.cyf, kyh, L1z, ayz)));
+    } else {
+        const double *M = V.rot;
+        X = DADD(DADD(DMUL(M[0], dx), DMUL(M[1], dy)), DMUL(M[2], dz));
+        Y = DADD(DADD(DMUL(M[3], dx), DMUL(M[4], dy)), DMUL(M[5], dz));
+        Z = DADD(DADD(DMUL(M[6], dx), DMUL(M[7], dy)), DMUL(M[8], dz));
+        vis = !(DADD(Z, r) <= 0.0);
+    }
+    if (fast) {
+        // the box is fa0..fb1
+    } else if (V.model == PF_FISHEYE) {
         // equidistant fisheye: the directions that meet the sphere form a cap
         // of angular radius asin(r/|c|) around c; its pixels lie in the box
         // of the annular sector theta in [thc - b, thc + b], phi in
@@ -317,31 +390,6 @@ __global__ void __launch_bounds__(256) project_kernel(pf_scene s, const ViewDev 
             vlo = V.cy + V.fy * yl;
             vhi = V.cy + V.fy * yh;
         }
-    } else if (vis && Z > DMUL(2.0, r)) {
-        // well in front: the tangent-line box in float, widened by its rounding bound
-        fast = true;
-        const float Xf = __double2float_rn(X), Yf = __double2float_rn(Y), Zf = __double2float_rn(Z);
-        const float rf = s.R[i];
-        const float fxf = __double2float_rn(V.fx), fyf = __double2float_rn(V.fy);
-        const float cxf = __double2float_rn(V.cx), cyf = __double2float_rn(V.cy);
-        const float rr = __fmul_rn(rf, rf), zz = __fmul_rn(Zf, Zf);
-        const float izr = __fdiv_rn(1.0f, __fsub_rn(zz, rr));
-        const float sx = __fsqrt_rn(__fsub_rn(__fadd_rn(__fmul_rn(Xf, Xf), zz), rr));
-        const float sy = __fsqrt_rn(__fsub_rn(__fadd_rn(__fmul_rn(Yf, Yf), zz), rr));
-        const float xz = __fmul_rn(Xf, Zf), yz = __fmul_rn(Yf, Zf);
-        const float rsx = __fmul_rn(rf, sx), rsy = __fmul_rn(rf, sy);
-        const float flo = __fadd_rn(__fmul_rn(fxf, __fmul_rn(__fsub_rn(xz, rsx), izr)), cxf);
-        const float fhi = __fadd_rn(__fmul_rn(fxf, __fmul_rn(__fadd_rn(xz, rsx), izr)), cxf);
-        const float glo = __fadd_rn(__fmul_rn(fyf, __fmul_rn(__fsub_rn(yz, rsy), izr)), cyf);
-        const float ghi = __fadd_rn(__fmul_rn(fyf, __fmul_rn(__fadd_rn(yz, rsy), izr)), cyf);
-        const float ex = __fmul_rn(0x1p-18f, __fadd_rn(__fmul_rn(fabsf(fxf), __fadd_rn(__fdiv_rn(fabsf(Xf), Zf), 1.0f)),
-                                                       fabsf(cxf)));
-        const float ey = __fmul_rn(0x1p-18f, __fadd_rn(__fmul_rn(fabsf(fyf), __fadd_rn(__fdiv_rn(fabsf(Yf), Zf), 1.0f)),
-                                                       fabsf(cyf)));
-        fa0 = ceilf(__fsub_rn(__fsub_rn(flo, 0.5f), ex));
-        fa1 = floorf(__fadd_rn(__fsub_rn(fhi, 0.5f), ex));
-        fb0 = ceilf(__fsub_rn(__fsub_rn(glo, 0.5f), ey));
-        fb1 = floorf(__fadd_rn(__fsub_rn(ghi, 0.5f), ey));
     } else if (vis && Z > r) {
         // tangent lines from the camera centre to the sphere's x-z and y-z circles
         const double rr = DMUL(r, r);
@@ -386,7 +434,7 @@ __global__ void __launch_bounds__(256) project_kernel(pf_scene s, const ViewDev 
             count = (uint32_t)(x1 - x0 + 1) * (uint32_t)(y1 - y0 + 1);
             // 2D difference grid: +1 at (x0,y0), -1 at (x1+1,y0) and (x0,y1+1), +1 at (x1+1,y1+1)
             const int gw = V.tiles_x + 1;
-            int32_t *g = diff + V.diff_base;
+            int32_t *g = diff + diff_total * (int64_t)((blockIdx.x * 8 + (threadIdx.x >> 5)) % DIFF_REP) + V.diff_base;
             atomicAdd(&g[y0 * gw + x0], 1);
             atomicAdd(&g[y0 * gw + x1 + 1], -1);
             atomicAdd(&g[(y1 + 1) * gw + x0], -1);
@@ -456,14 +504,14 @@ cudaError_t launch_prepare(const pf_scene &s, const Plan &p, const WS &w, cudaSt
 }
 
 cudaError_t launch_project(const pf_scene &s, const Plan &p, const WS &w, cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(w.diff, 0, sizeof(int32_t) * (size_t)p.total_diff, st);
+    cudaError_t e = cudaMemsetAsync(w.diff, 0, sizeof(int32_t) * (size_t)p.total_diff * DIFF_REP, st);
     if (e != cudaSuccess) return e;
     const int64_t total = (int64_t)p.n * p.nv;
     if (total == 0) return cudaSuccess;
     const int threads = 256;
     const int64_t blocks = (total + threads - 1) / threads;
     project_kernel<<<(unsigned)blocks, threads, 0, st>>>(s, w.views, p.nv, w.cellrec, w.viewrec, w.rect, w.key,
-                                                         w.cnt, w.diff);
+                                                         w.cnt, w.diff, p.total_diff);
     return cudaGetLastError();
 }
 

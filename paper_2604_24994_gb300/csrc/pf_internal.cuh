@@ -68,6 +68,11 @@ enum : int {
     G_USED = 22
 };
 
+// Copies of the per-view 2D difference grids that the projection's
+// atomics are spread over (warp w of block b adds into copy (8 b + w) mod
+// DIFF_REP); the tile-count pass sums them.
+constexpr int DIFF_REP = 16;
+
 // Per-view constants on the device.
 struct ViewDev {
     double rot[9];
@@ -76,6 +81,9 @@ struct ViewDev {
     double ifx, ify;          // 1/fx, 1/fy
     double kl, kr, ku, kd;    // image-edge slopes x/z, y/z of the frustum side planes
     double skl, skr, sku, skd; // sqrt(1 + k^2) of each
+    float rotf[9];            // rot, fx, fy, cx, cy rounded to float (the float tile box)
+    float fxf, fyf, cxf, cyf;
+    float ohi[3], olo[3];     // origin as a float pair: ohi = (float)origin, olo = (float)(origin - ohi)
     int32_t width, height;
     int32_t tiles_x, tiles_y;
     int32_t model;            // PF_PINHOLE or PF_FISHEYE

@@ -1270,3 +1270,63 @@ def test_connect_over_the_cech_graph_and_over_lists():
     assert complete.any() and (~complete).any()       # this scene has both kinds of cells
     np.testing.assert_allclose(lists[complete], full[complete], rtol=1e-12, atol=0)
     assert np.all(lists[~complete] < full[~complete])
+
+
+@pytest.mark.parametrize("dist,fov,seed", [(3.0, 90.0, 11), (60.0, 4.0, 12)])
+def test_float_tile_box_contains_the_exact_box(dist, fov, seed):
+    """The CPU binning evaluates the tile box of a sphere well in front of
+    the camera in float, widened by a bound on its rounding.  Against the
+    exact box (the tangent-line formula in FP64 from the same float32
+    inputs) over 200k spheres, from just past the float path's Z > 2R limit
+    to Z = 50 R and past the image edges: every tile of the exact box is in
+    the rectangle, and the rectangle is at most one tile wider."""
+    from paper_2604_24994_gb300.inputs import look_at
+    rng = np.random.default_rng(seed)
+    cam = look_at([dist, 0.4, -0.3], 333, 211, fov_y_deg=fov)
+    n = 200_000
+    Mr = np.asarray(cam.rot, np.float64)
+    o = np.asarray(cam.origin, np.float64)
+    # camera-frame centres: depth, then image-plane offset up to 1.3x the half field
+    tanv = np.tan(np.radians(fov) / 2)
+    Z = dist * rng.uniform(0.05, 1.5, n)
+    R = Z / rng.uniform(2.02, 50.0, n)
+    xy = rng.uniform(-1.3, 1.3, (n, 2)) * tanv * np.array([cam.width / cam.height, 1.0]) * Z[:, None]
+    # half of them placed so that the left (or right) edge of the exact box lies
+    # within 2e-3 px of the last (first) pixel centre of a tile, where an edge
+    # moved by rounding would change the tile
+    h = n // 2
+    tile = rng.integers(1, cam.width // 16 - 1, h)
+    left = rng.random(h) < 0.5
+    target = np.where(left, 16 * tile - 0.5, 16 * tile + 0.5) + rng.uniform(-2e-3, 2e-3, h)
+    kt = (target - cam.cx) / cam.fx
+    Xh = kt * Z[:h]
+    for _ in range(8):          # X with the tangent slope atan(kt) -+ asin(R / |(X, Z)|) equal to kt
+        al = np.arcsin(R[:h] / np.hypot(Xh, Z[:h]))
+        Xh = Z[:h] * np.tan(np.arctan(kt) + np.where(left, al, -al))
+    xy[:h, 0] = Xh
+    pc = np.stack([xy[:, 0], xy[:, 1], Z], 1)
+    pos = (o + pc @ Mr).astype(np.float32).astype(np.float64)
+    R = R.astype(np.float32).astype(np.float64)
+    sc = make_scene(pos, R * R, R)
+    rect, _ = oracle.Oracle(sc).bin(cam)
+    d = (pos - o) @ Mr.T
+    X, Y, Z = d[:, 0], d[:, 1], d[:, 2]
+    sel = Z > 2.0 * R * (1 + 1e-3)
+    zz = Z * Z - R * R
+    sx = np.sqrt(X * X + zz)
+    sy = np.sqrt(Y * Y + zz)
+    box = np.stack([cam.fx * (X * Z - R * sx) / zz + cam.cx, cam.fy * (Y * Z - R * sy) / zz + cam.cy,
+                    cam.fx * (X * Z + R * sx) / zz + cam.cx, cam.fy * (Y * Z + R * sy) / zz + cam.cy], 1)
+    a0 = np.maximum(np.ceil(box[:, 0] - 0.5), 0)
+    b0 = np.maximum(np.ceil(box[:, 1] - 0.5), 0)
+    a1 = np.minimum(np.floor(box[:, 2] - 0.5), cam.width - 1)
+    b1 = np.minimum(np.floor(box[:, 3] - 0.5), cam.height - 1)
+    live = sel & (a0 <= a1) & (b0 <= b1)
+    assert live.sum() > n // 4
+    ex = np.stack([a0 // 16, b0 // 16, a1 // 16, b1 // 16], 1)[live]
+    r = rect[live].astype(np.int64)
+    assert np.all(r[:, 0] <= ex[:, 0]) and np.all(r[:, 1] <= ex[:, 1])
+    assert np.all(r[:, 2] >= ex[:, 2]) and np.all(r[:, 3] >= ex[:, 3])
+    assert np.all(r[:, 0] >= ex[:, 0] - 1) and np.all(r[:, 2] <= ex[:, 2] + 1)
+    m16 = (box[live][:, [0, 2]] - 0.5) % 16.0
+    assert (np.minimum(np.abs(m16 - 15.0), np.abs(m16)) < 2e-3).sum() > n // 10
