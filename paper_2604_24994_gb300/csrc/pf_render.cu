@@ -905,7 +905,8 @@ static size_t bwd_smem(int K) { return stage_bytes(K, true); }
 cudaError_t launch_render_fwd(const pf_scene &s, const Plan &p, const WS &w, float *rgb, float *T, uint32_t *last,
                               bool record, cudaStream_t st, float *contrib_sparse, float *contrib_normal) {
     if (p.total_tiles == 0) return cudaSuccess;
-    if (pipe_applies(s, p, record, contrib_sparse != nullptr)) return launch_render_fwd_pipe(s, p, w, rgb, T, last, st);
+    if (pipe_applies(s, p, record, contrib_sparse != nullptr))
+        return launch_render_fwd_pipe(s, p, w, rgb, T, last, record, st);
     RenderArgs A = make_args(s, p, w);
     A.contrib_sparse = contrib_sparse;
     A.contrib_normal = contrib_normal;

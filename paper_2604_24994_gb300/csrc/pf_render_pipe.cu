@@ -168,6 +168,7 @@ __device__ __forceinline__ unsigned pipe_mask(const PipeStage &st, int nb, const
     return __ballot_sync(0xffffffffu, ov);
 }
 
+template <bool REC>
 __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_pipe_kernel(RenderArgs A, int64_t n_tiles,
                                                                       float *__restrict__ rgb_out,
                                                                       float *__restrict__ T_out,
@@ -246,6 +247,13 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_pipe_kernel(RenderArgs
         float T = 1.0f;
         float3 C = f3(0.f, 0.f, 0.f);
         uint32_t last = 0;
+        // REC: this lane's hit bits of the 32-entry list groups hg and hg + 1
+        // (a batch of at most 32 cells spans at most two), written to the hit
+        // masks as the batches move past them; hit records in list order
+        unsigned hb0 = 0u, hb1 = 0u;
+        int hg = 0, pend = 0, nhit = 0;
+        const int64_t s_slot = (int64_t)(s0 / BATCH) + tile;
+        const int64_t rp = V.pix_base + (int64_t)py * V.width + px;
         bool done = !inside || !has_ray;
         bool warp_done = false;  // counted in S.ndone
         bool more = n > 0;
@@ -275,6 +283,15 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_pipe_kernel(RenderArgs
                 break;
             }
             const int nb = st.nb, lo = st.lo;
+            if (REC) {
+                if ((lo >> 5) > hg) {  // group hg is complete: the next batches start past it
+                    A.w.hitmask[((int64_t)warp * A.mask_batches + s_slot + hg) * 32 + lane] = hb0;
+                    hb0 = hb1;
+                    hb1 = 0u;
+                    hg++;
+                }
+                pend = lo + nb;
+            }
             more = lo + nb < n;
             if (!warp_done) {
                 unsigned mask = pipe_mask(st, nb, cone);
@@ -297,6 +314,16 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_pipe_kernel(RenderArgs
                                                     ray, ch, seg, pm);
                     }
                     if (!hit) continue;
+                    if (REC) {
+                        const int idx = lo + j;
+                        if ((idx >> 5) == hg)
+                            hb0 |= 1u << (idx & 31);
+                        else
+                            hb1 |= 1u << (idx & 31);
+                        if (nhit < HIT_CAP)
+                            A.w.hitkind[rp * HIT_CAP + nhit] = (uint16_t)((seg.ka + 3) | ((seg.kb + 3) << 7));
+                        nhit++;
+                    }
                     Tex tx;
                     const float3 c = face_colour<4>(cr, seg, ray, tx);
                     const float x = fminf(cr[CR_SIG] * (seg.sb - seg.sa), X_CAP);
@@ -366,6 +393,10 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_pipe_kernel(RenderArgs
             }
             if (*(volatile int *)&S.abort) break;
         }
+        if (REC && pend > 0) {  // the last one or two groups of the batches consumed
+            A.w.hitmask[((int64_t)warp * A.mask_batches + s_slot + hg) * 32 + lane] = hb0;
+            if (((pend - 1) >> 5) > hg) A.w.hitmask[((int64_t)warp * A.mask_batches + s_slot + hg + 1) * 32 + lane] = hb1;
+        }
         if (inside) {
             const int64_t lp = (int64_t)py * V.width + px;
             if (V.out_rgb) {  // per-view outputs (serving)
@@ -381,6 +412,7 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_pipe_kernel(RenderArgs
                 rgb_out[3 * pix + 2] = C.z;
                 T_out[pix] = T;
                 last_out[pix] = last;
+                if (REC) A.w.hitcount[pix] = (uint32_t)nhit;
             }
         }
     }
@@ -389,18 +421,19 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_pipe_kernel(RenderArgs
 }
 
 bool pipe_applies(const pf_scene &s, const Plan &p, bool record, bool contrib) {
-    return !ext_face(s) && !record && !contrib && !p.stats;
+    // hit recording without stored segments (those take the batch-staged kernel)
+    return !ext_face(s) && !contrib && !p.stats && !(record && p.seg_cap > 0);
 }
 
 cudaError_t launch_render_fwd_pipe(const pf_scene &s, const Plan &p, const WS &w, float *rgb, float *T,
-                                   uint32_t *last, cudaStream_t st) {
+                                   uint32_t *last, bool record, cudaStream_t st) {
     RenderArgs A;
     A.w = w;
     A.nv = p.nv;
     A.n = p.n;
     A.K = p.k;
     A.cap = p.cap;
-    A.mask_batches = 0;
+    A.mask_batches = record ? mask_batches(p) : 0;
     A.contrib_sparse = A.contrib_normal = nullptr;
     A.disp = A.sites = A.sv = A.tex8 = nullptr;
     A.gdisp = A.gsites = A.gsv = A.gtex8 = nullptr;
@@ -411,9 +444,9 @@ cudaError_t launch_render_fwd_pipe(const pf_scene &s, const Plan &p, const WS &w
     const size_t smem = sizeof(PipeStage) * PIPE_S;
     cudaError_t e = cudaMemsetAsync(&w.counters->q_fwd, 0, sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
-    cudaFuncSetAttribute(render_fwd_pipe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    render_fwd_pipe_kernel<<<persistent_grid(render_fwd_pipe_kernel, smem, p.total_tiles), TILE_PIX, smem, st>>>(
-        A, p.total_tiles, rgb, T, last);
+    auto k = record ? render_fwd_pipe_kernel<true> : render_fwd_pipe_kernel<false>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<persistent_grid(k, smem, p.total_tiles), TILE_PIX, smem, st>>>(A, p.total_tiles, rgb, T, last);
     return cudaGetLastError();
 }
 

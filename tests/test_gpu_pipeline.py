@@ -1,12 +1,15 @@
-"""The pipelined forward (the plain face model without hit recording: the
-benchmark's forward step, the server and the static entry point) against
-the batch-staged forward that records hits, which the other parity tests pin
-to the FP64 oracle: the same per-pixel arithmetic in the same list order, so
-rgb, T and last must agree bit for bit.  The scenes cover early termination
-(near-opaque cells), batches cut short by the stage's plane budget (cells with
-up to 39 kept planes), several views of different sizes in one plan, a
-camera inside the cells, long tile lists, and the capture workload at 720p.
-Every run must leave the pipeline's wait-error word at zero."""
+"""The pipelined forward (the plain face model, with or without hit
+recording: the benchmark's forward and forward+backward steps, the server
+and the static entry point) against the batch-staged forward (the variant
+that counts work, and the one that stores every segment), which the other
+parity tests pin to the FP64 oracle: the same per-pixel arithmetic in the
+same list order, so rgb, T and last must agree bit for bit, and both
+recording forwards must count the same hits per pixel.  The scenes cover
+early termination (near-opaque cells), batches cut short by the stage's
+plane budget (cells with up to 39 kept planes), several views of different
+sizes in one plan, a camera inside the cells, long tile lists, and the
+capture workload at 720p.  Every run must leave the pipeline's wait-error
+word at zero."""
 import numpy as np
 import pytest
 
@@ -28,17 +31,27 @@ def both(sc, cams):
     import torch
     from paper_2604_24994_gb300 import DeviceScene, Renderer
     ds = DeviceScene.from_numpy(sc, "cuda")
-    out = []
-    for rec in (True, False):
-        r = Renderer(ds.n, ds.k, cams, hit_records=rec)
+    out = {}
+    runs = (("staged", dict(hit_records=False), True),            # counts work: batch-staged
+            ("staged_rec", dict(hit_records=True, store_segments=1), False),  # stores segments: batch-staged
+            ("pipe_rec", dict(hit_records=True), False),
+            ("pipe", dict(hit_records=False), False))
+    for name, kw, stats in runs:
+        r = Renderer(ds.n, ds.k, cams, **kw)
+        if stats:
+            r.enable_stats(True)
         rgb, T, last = r.forward(ds)
         torch.cuda.synchronize()
         assert r.stats()["wait_errors"] == 0
-        out.append((rgb.cpu().numpy(), T.cpu().numpy(), last.cpu().numpy()))
-    (a, b) = out
-    for x, y, name in zip(a, b, ("rgb", "T", "last")):
-        assert np.array_equal(x, y), name
-    return b
+        hc = r.hit_counts() if kw["hit_records"] else None
+        out[name] = (rgb.cpu().numpy(), T.cpu().numpy(), last.cpu().numpy(),
+                     None if hc is None else np.asarray(hc.cpu() if hasattr(hc, "cpu") else hc))
+    ref = out["staged"]
+    for name in ("staged_rec", "pipe_rec", "pipe"):
+        for x, y, what in zip(out[name][:3], ref[:3], ("rgb", "T", "last")):
+            assert np.array_equal(x, y), (name, what)
+    assert np.array_equal(out["pipe_rec"][3], out["staged_rec"][3]), "hit counts"
+    return out["pipe"][:3]
 
 
 def test_tiny_and_multiview(tiny):
