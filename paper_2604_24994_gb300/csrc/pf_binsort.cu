@@ -487,19 +487,22 @@ __device__ __forceinline__ void sort_tile(int64_t t, const uint32_t *__restrict_
     }
 }
 
-// One CTA per tile for the lists of at most CAP entries.
+// One CTA per tile for the lists of at most CAP entries, CTAs in the render
+// order (longest lists first, so that the last wave holds the short ones).
 template <int CAP, int NT>
-__global__ void __launch_bounds__(NT) sort_small_tiles_kernel(const uint32_t *__restrict__ tile_start,
+__global__ void __launch_bounds__(NT) sort_small_tiles_kernel(const uint32_t *__restrict__ order,
+                                                              const uint32_t *__restrict__ tile_start,
                                                               unsigned long long cap,
                                                               const unsigned long long *inst_key,
                                                               const uint32_t *inst_cell,
                                                               uint32_t *__restrict__ inst_sorted) {
     extern __shared__ unsigned long long smem_sort[];
-    unsigned long long s = tile_start[blockIdx.x], e = tile_start[blockIdx.x + 1];
+    const int64_t tt = order[blockIdx.x];
+    unsigned long long s = tile_start[tt], e = tile_start[tt + 1];
     if (s > cap) s = cap;
     if (e > cap) e = cap;
     if (e - s > (unsigned long long)CAP) return;  // the persistent kernel sorts it
-    sort_tile<0, CAP, NT, false>(blockIdx.x, tile_start, cap, inst_key, inst_cell, inst_sorted, nullptr, nullptr,
+    sort_tile<0, CAP, NT, false>(tt, tile_start, cap, inst_key, inst_cell, inst_sorted, nullptr, nullptr,
                                  reinterpret_cast<char *>(smem_sort));
 }
 
@@ -605,7 +608,7 @@ cudaError_t launch_bin_sort(const Plan &p, const WS &w, cudaStream_t st) {
         const size_t ss = (size_t)SMALL * 12, sl = SortSmem<LARGE, 512>::bytes;
         cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
         cudaFuncSetAttribute(kl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sl);
-        ks<<<(unsigned)T, 256, ss, st>>>(w.tile_start, p.cap, w.inst_key, w.inst_cell, w.inst_sorted);
+        ks<<<(unsigned)T, 256, ss, st>>>(w.tile_order, w.tile_start, p.cap, w.inst_key, w.inst_cell, w.inst_sorted);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         int dev = 0, sms = 148;
         cudaGetDevice(&dev);

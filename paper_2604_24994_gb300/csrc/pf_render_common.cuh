@@ -49,6 +49,15 @@ __device__ __forceinline__ float sqrt_approx(float x) {
     asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
+// 2^x by the hardware approximation (ex2.approx, about 2 ulp); the soft-
+// Voronoi weights exp(-kappa r) = 2^(r * KAPPA_LOG2E) take one multiply.
+__device__ __forceinline__ float exp2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+constexpr float KAPPA_LOG2E = (float)(-(double)KAPPA * 1.4426950408889634);
+
 __device__ __forceinline__ float3 cross3(float3 a, float3 b) {
     return f3(fmaf(a.y, b.z, -a.z * b.y), fmaf(a.z, b.x, -a.x * b.z), fmaf(a.x, b.y, -a.y * b.x));
 }
@@ -596,7 +605,7 @@ __device__ __forceinline__ float3 face_colour(const float *__restrict__ cr, cons
         }
 #pragma unroll
         for (int k = 0; k < NS; k++) {
-            tx.W[k] = __expf(-KAPPA * (tx.r[k] - rmin));
+            tx.W[k] = exp2_approx((tx.r[k] - rmin) * KAPPA_LOG2E);
             Z += tx.W[k];
         }
     } else {
@@ -604,22 +613,23 @@ __device__ __forceinline__ float3 face_colour(const float *__restrict__ cr, cons
         for (int k = 0; k < 4; k++) {
             const float ax = tx.ax[k & 1], ay = tx.ay[k >> 1];
             tx.r[k] = sqrt_approx(fmaf(ax, ax, ay * ay));
-            tx.W[k] = __expf(-KAPPA * tx.r[k]);
+            tx.W[k] = exp2_approx(tx.r[k] * KAPPA_LOG2E);
             Z += tx.W[k];
         }
     }
     const float iz = __fdividef(1.0f, Z);
-    float3 c = f3(cr[CR_RGB], cr[CR_RGB + 1], cr[CR_RGB + 2]);
+    // the weighted site colours summed unnormalised, then scaled once
+    float3 c = f3(0.f, 0.f, 0.f);
     const float *tc = tex ? tex : cr + CR_TEX;  // eight sites: tex staged beside the record
 #pragma unroll
     for (int k = 0; k < NS; k++) {
-        tx.W[k] *= iz;
         const float3 ck = sv ? sv_colour(sv, k, ray.dh) : f3(tc[3 * k], tc[3 * k + 1], tc[3 * k + 2]);
         c.x = fmaf(tx.W[k], ck.x, c.x);
         c.y = fmaf(tx.W[k], ck.y, c.y);
         c.z = fmaf(tx.W[k], ck.z, c.z);
+        tx.W[k] *= iz;  // the normalised weights, for the adjoint
     }
-    return c;
+    return f3(fmaf(c.x, iz, cr[CR_RGB]), fmaf(c.y, iz, cr[CR_RGB + 1]), fmaf(c.z, iz, cr[CR_RGB + 2]));
 }
 
 // ------------------------------------------------------------ batch staging
