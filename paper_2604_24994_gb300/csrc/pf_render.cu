@@ -259,6 +259,10 @@ __device__ __forceinline__ bool segment_from_record(const float *__restrict__ cr
 }
 
 // --------------------------------------------------------------- backward
+// A cell that at most this many lanes of a warp hit adds each lane's
+// gradients with atomics; more hit lanes sum them over the warp first.
+constexpr int BWD_DIRECT_LANES = 6;
+
 // Sum v[0..31] over the warp with each lane ending up holding one index:
 // after five exchange rounds lane l holds sum_lanes v[l] (31 shuffles).
 __device__ __forceinline__ float warp_transpose_sum(float (&v)[32], int lane) {
@@ -785,6 +789,29 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
                 accC.z = fmaf(wc, c.z, accC.z);
                 if (CONTRIB) accQ = fmaf(wc, qk, accQ);
                 if (hit) Tafter = Tbefore;
+            }
+            // few hit lanes: each adds its own values (cheaper than the transposed sum;
+            // measured at 1080p / 1M: 6.63 -> 6.44 ms, best at up to six lanes)
+            if (__popc(__ballot_sync(0xffffffffu, hit)) <= BWD_DIRECT_LANES) {
+                if (hit) {
+#pragma unroll
+                    for (int q = 0; q < G_USED; q++) atomicAdd(acc + (int64_t)cell * ACC_F + q, vv[q]);
+                    if (ja >= 0) {
+                        float *d = acc + (int64_t)ja * ACC_F;
+                        atomicAdd(d + G_P, nba[0]);
+                        atomicAdd(d + G_P + 1, nba[1]);
+                        atomicAdd(d + G_P + 2, nba[2]);
+                        atomicAdd(d + G_W, nba[3]);
+                    }
+                    if (jb >= 0) {
+                        float *d = acc + (int64_t)jb * ACC_F;
+                        atomicAdd(d + G_P, nbb[0]);
+                        atomicAdd(d + G_P + 1, nbb[1]);
+                        atomicAdd(d + G_P + 2, nbb[2]);
+                        atomicAdd(d + G_W, nbb[3]);
+                    }
+                }
+                continue;
             }
             // neighbour gradients: fold into the warp sum when the warp agrees on j
             const unsigned ma = __ballot_sync(0xffffffffu, ja >= 0);
