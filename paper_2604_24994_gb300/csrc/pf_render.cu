@@ -65,16 +65,14 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_kernel(RenderArgs A, i
     if (nbat > 0)
         issue_batch(sg, 0, A.w.inst_sorted + s, min(BATCH, n), A.w, vbase, A.K, false, disp, sites, tex8);
     for (int k = 0; k < nbat; k++) {
-        // every warp is done with batch k-1, whose buffer batch k+1 reuses
+        // one barrier per batch: this thread's copies of batch k have landed, so
+        // after it everyone's have, and every warp is done with batch k-1, whose
+        // buffer batch k+1 (in flight while batch k is shaded) reuses
+        cp_async_wait_all();
         if (__syncthreads_count(!done) == 0) break;
-        if (k + 1 < nbat) {
+        if (k + 1 < nbat)
             issue_batch(sg, (k + 1) & 1, A.w.inst_sorted + s + (k + 1) * BATCH, min(BATCH, n - (k + 1) * BATCH),
                         A.w, vbase, A.K, false, disp, sites, tex8);
-            cp_async_wait_one();
-        } else {
-            cp_async_wait_all();
-        }
-        __syncthreads();
         const int buf = k & 1, nb = min(BATCH, n - k * BATCH);
         unsigned mask = warp_mask(sg, buf, nb, cone);
         unsigned my_hits = 0;  // bit j: this pixel's segment in cell j of the batch is non-empty
@@ -454,15 +452,14 @@ __global__ void __launch_bounds__(TILE_PIX, 3) render_bwd_kernel(RenderArgs A, i
     for (int b = nbat - 1; b >= 0; b--) {
         // bit j: the forward found this pixel's segment in cell j non-empty
         const unsigned my_hits = MASKS ? A.w.hitmask[hitmask_slot(A, tile, s, b, warp) + lane] : 0u;
-        __syncthreads();  // batch b+1, whose buffer batch b-1 reuses, is done
-        if (b > 0) {
+        // one barrier per batch: this thread's copies of batch b have landed, so
+        // after it everyone's have, and batch b+1 (whose buffer batch b-1 reuses)
+        // is done; batch b-1's copies are in flight while batch b is replayed
+        cp_async_wait_all();
+        __syncthreads();
+        if (b > 0)
             issue_batch(stg, (b - 1) & 1, list + (b - 1) * BATCH, BATCH, A.w, vbase, A.K, true,
                         EXT ? A.disp : nullptr, EXT ? A.sites : nullptr, NS == 8 ? A.tex8 : nullptr);
-            cp_async_wait_one();
-        } else {
-            cp_async_wait_all();
-        }
-        __syncthreads();
         const int buf = b & 1, lo = b * BATCH, nb = min(BATCH, maxlast - lo);
         unsigned mask = MASKS ? __reduce_or_sync(0xffffffffu, my_hits) : warp_mask(stg, buf, nb, cone);
         const float *s_cr = stg.cr(buf);
