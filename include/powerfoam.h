@@ -221,10 +221,13 @@ pf_status pf_plan_read_stats(pf_plan *plan, void *ws, pf_stats *out, void *strea
 pf_status pf_prepare(const pf_scene *scene, pf_plan *plan, void *ws, void *stream);
 
 /*
- * Per view and cell, in FP64: the camera-relative site offset (stored as a
- * float pair), the painter key pow(o, p_i) (Thm. power_painter: ordering by
- * power distance from the camera centre is a valid painter's order), and
- * the exact screen bounding box of the sphere, as a 16x16 tile rectangle.
+ * Per view and cell: the camera-relative site offset as a float pair (an
+ * error-free two-sum of the origin's float pair and the site), the painter
+ * key pow(o, p_i) in FP64 (Thm. power_painter: ordering by power distance
+ * from the camera centre is a valid painter's order), and the screen
+ * bounding box of the sphere as a 16x16 tile rectangle: in float, widened by
+ * a bound on its rounding, for a sphere well in front of the camera, in FP64
+ * otherwise.  The rectangle covers every pixel whose ray meets the sphere.
  */
 pf_status pf_project(const pf_scene *scene, pf_plan *plan, void *ws, void *stream);
 
