@@ -55,3 +55,35 @@ def f32(scene):
     if s.nbr.shape[1] == 0 and s.n > 1:
         s.nbr = np.array([[j for j in range(s.n) if j != i] for i in range(s.n)], np.int32)
     return s
+
+
+def border_box_scene(dist, fov, seed, n):
+    """Spheres seen by a 333x211 camera at distance `dist` (vertical field
+    `fov`): camera depths Z from 0.05 to 1.5 dist, radii Z / U(2.02, 50) (the
+    float tile box's domain, Z > 2R, from just past its limit), image-plane
+    offsets up to 1.3x the half field; half of them placed so that the left
+    (or right) edge of the exact box lies within 2e-3 px of the last (first)
+    pixel centre of a tile, where an edge moved by rounding would change the
+    tile.  Positions and radii are float32 values."""
+    rng = np.random.default_rng(seed)
+    cam = look_at([dist, 0.4, -0.3], 333, 211, fov_y_deg=fov)
+    Mr = np.asarray(cam.rot, np.float64)
+    o = np.asarray(cam.origin, np.float64)
+    tanv = np.tan(np.radians(fov) / 2)
+    Z = dist * rng.uniform(0.05, 1.5, n)
+    R = Z / rng.uniform(2.02, 50.0, n)
+    xy = rng.uniform(-1.3, 1.3, (n, 2)) * tanv * np.array([cam.width / cam.height, 1.0]) * Z[:, None]
+    h = n // 2
+    tile = rng.integers(1, cam.width // 16 - 1, h)
+    left = rng.random(h) < 0.5
+    target = np.where(left, 16 * tile - 0.5, 16 * tile + 0.5) + rng.uniform(-2e-3, 2e-3, h)
+    kt = (target - cam.cx) / cam.fx
+    Xh = kt * Z[:h]
+    for _ in range(8):          # X with the tangent slope atan(kt) -+ asin(R / |(X, Z)|) equal to kt
+        al = np.arcsin(R[:h] / np.hypot(Xh, Z[:h]))
+        Xh = Z[:h] * np.tan(np.arctan(kt) + np.where(left, al, -al))
+    xy[:h, 0] = Xh
+    pc = np.stack([xy[:, 0], xy[:, 1], Z], 1)
+    pos = (o + pc @ Mr).astype(np.float32).astype(np.float64)
+    R = R.astype(np.float32).astype(np.float64)
+    return make_scene(pos, R * R, R), cam

@@ -37,6 +37,45 @@ def test_binning_bit_exact_tiny(tiny):
     assert r.n_instances == st_o[-1] > 0
 
 
+@pytest.mark.parametrize("dist,fov,seed", [(3.0, 90.0, 11), (60.0, 4.0, 12)])
+def test_binning_bit_exact_float_box_at_tile_borders(dist, fov, seed):
+    """The tile boxes of spheres whose box edges sit within 2e-3 px of tile
+    borders (the float box of the tile rule, Z > 2R), plus spheres near and
+    across the camera plane (the FP64 box and the frustum test): rectangles
+    and keys bit for bit against the CPU binning (the per-tile lists follow
+    from them; the other binning tests compare those)."""
+    import torch
+    from paper_2604_24994_gb300 import DeviceScene, Renderer
+    from tests.oracle_util import border_box_scene
+    sc, cam = border_box_scene(dist, fov, seed, 60_000)
+    rng = np.random.default_rng(seed + 100)
+    # 4,000 more: camera depth between -R and 2R (near / across the camera plane)
+    m = 4000
+    Mr = np.asarray(cam.rot, np.float64)
+    o = np.asarray(cam.origin, np.float64)
+    R2 = dist * rng.uniform(0.002, 0.05, m)
+    Z2 = R2 * rng.uniform(-1.0, 2.0, m)
+    xy2 = rng.normal(0, 1, (m, 2)) * dist * 0.05
+    pos2 = (o + np.stack([xy2[:, 0], xy2[:, 1], Z2], 1) @ Mr).astype(np.float32).astype(np.float64)
+    R2 = R2.astype(np.float32).astype(np.float64)
+    sc = make_scene(np.concatenate([sc.pos, pos2]), np.concatenate([sc.w, R2 * R2]), np.concatenate([sc.R, R2]))
+    for k in sc.PARAMS:    # float32 parameters, no neighbour lists (only the bins are compared)
+        setattr(sc, k, np.ascontiguousarray(np.asarray(getattr(sc, k)), np.float32))
+    ds = DeviceScene.from_numpy(sc, "cuda")
+    r = Renderer(ds.n, ds.k, [cam])
+    r.bin(ds)
+    torch.cuda.synchronize()
+    ts, cells, keys, rects = r.read_bins()
+    orc = oracle.Oracle(sc)
+    rect_o, key_o = orc.bin(cam)
+    assert np.array_equal(keys[:sc.n], key_o)
+    empty = (rect_o[:, 0] > rect_o[:, 2]) | (rect_o[:, 1] > rect_o[:, 3])
+    rg = rects[:sc.n].astype(np.int64)
+    assert np.array_equal(empty, (rg[:, 0] > rg[:, 2]) | (rg[:, 1] > rg[:, 3]))
+    assert np.array_equal(rg[~empty], rect_o[~empty])
+    assert (~empty[-m:]).sum() > m // 8      # many of the near spheres reach the image
+
+
 def test_forward_tiny_full_frame(tiny):
     sc, cam = tiny
     rgb, T, last = gpu_forward(sc, [cam])

@@ -1280,34 +1280,12 @@ def test_float_tile_box_contains_the_exact_box(dist, fov, seed):
     inputs) over 200k spheres, from just past the float path's Z > 2R limit
     to Z = 50 R and past the image edges: every tile of the exact box is in
     the rectangle, and the rectangle is at most one tile wider."""
-    from paper_2604_24994_gb300.inputs import look_at
-    rng = np.random.default_rng(seed)
-    cam = look_at([dist, 0.4, -0.3], 333, 211, fov_y_deg=fov)
+    from tests.oracle_util import border_box_scene
     n = 200_000
+    sc, cam = border_box_scene(dist, fov, seed, n)
+    pos, R = sc.pos, sc.R
     Mr = np.asarray(cam.rot, np.float64)
     o = np.asarray(cam.origin, np.float64)
-    # camera-frame centres: depth, then image-plane offset up to 1.3x the half field
-    tanv = np.tan(np.radians(fov) / 2)
-    Z = dist * rng.uniform(0.05, 1.5, n)
-    R = Z / rng.uniform(2.02, 50.0, n)
-    xy = rng.uniform(-1.3, 1.3, (n, 2)) * tanv * np.array([cam.width / cam.height, 1.0]) * Z[:, None]
-    # half of them placed so that the left (or right) edge of the exact box lies
-    # within 2e-3 px of the last (first) pixel centre of a tile, where an edge
-    # moved by rounding would change the tile
-    h = n // 2
-    tile = rng.integers(1, cam.width // 16 - 1, h)
-    left = rng.random(h) < 0.5
-    target = np.where(left, 16 * tile - 0.5, 16 * tile + 0.5) + rng.uniform(-2e-3, 2e-3, h)
-    kt = (target - cam.cx) / cam.fx
-    Xh = kt * Z[:h]
-    for _ in range(8):          # X with the tangent slope atan(kt) -+ asin(R / |(X, Z)|) equal to kt
-        al = np.arcsin(R[:h] / np.hypot(Xh, Z[:h]))
-        Xh = Z[:h] * np.tan(np.arctan(kt) + np.where(left, al, -al))
-    xy[:h, 0] = Xh
-    pc = np.stack([xy[:, 0], xy[:, 1], Z], 1)
-    pos = (o + pc @ Mr).astype(np.float32).astype(np.float64)
-    R = R.astype(np.float32).astype(np.float64)
-    sc = make_scene(pos, R * R, R)
     rect, _ = oracle.Oracle(sc).bin(cam)
     d = (pos - o) @ Mr.T
     X, Y, Z = d[:, 0], d[:, 1], d[:, 2]
