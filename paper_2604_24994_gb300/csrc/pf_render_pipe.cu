@@ -1,7 +1,9 @@
-// pf_render_fwd for the plain face model without hit recording, stats or
-// contributions (rendering a view: the benchmark's forward step, the server,
-// the static entry point): the same per-pixel segments and compositing as
-// render_fwd_kernel (Sec. 3.1-3.3), fed by a shared-memory ring instead of
+// pf_render_fwd for the plain face model and the extended one with four
+// detail sites, with or without hit recording (rendering a view: the
+// benchmark's forward and training steps, the server, the static entry
+// point; stats, contributions, stored segments and eight sites keep
+// render_fwd_kernel): the same per-pixel segments and compositing as
+// render_fwd_kernel (Sec. 3.1-3.4), fed by a shared-memory ring instead of
 // double buffers behind CTA barriers.
 //
 // The tile's sorted list is cut into batches of at most 32 cells whose kept
@@ -9,7 +11,8 @@
 // most K <= 64 planes, so every batch holds at least one cell).  PIPE_S
 // stages hold consecutive batches.  One warp fills a stage: one lane per
 // cell issues cp.async.bulk copies of the cell's 128-byte record, its
-// 32-byte view record and its planes (16 bytes each), all completing on the
+// 32-byte view record, its planes (16 bytes each) and, for the extended
+// face model, its displacement and site rows, all completing on the
 // stage's mbarrier, whose expected transaction count the warp sets first.
 // Each warp waits for a stage's barrier, shades the batch, and signals that
 // it is done with the stage; the last of the eight warps to do so refills
@@ -29,16 +32,27 @@ constexpr int PIPE_PLANES = 320;          // planes one stage holds
 constexpr int PIPE_WARPS = TILE_PIX / 32; // warps per CTA, all of them shade
 constexpr int PIPE_SPIN = 1 << 22;        // polls before a wait gives up (about a second)
 
+// XW: float4s of extended face model per cell (0: the plain model; 3: four
+// sites, displacement then positions, as in the batch-staged kernel's
+// stages).
+template <int XW>
 struct PipeStage {
     float cr[BATCH * CELLREC_F];   // cell records
     float vr[BATCH * VIEWREC_F];   // (view, cell) records
     float4 pl[PIPE_PLANES];        // the cells' kept planes, back to back
+    float4 xt[XW > 0 ? BATCH * XW : 1];  // the cells' extended face model
     int ids[BATCH];                // cell indices
     int poff[BATCH + 1];           // first plane of each cell in pl
     int nb, lo;                    // cells in the batch, list index of its first cell
     int pad_[2];
 };
-static_assert(sizeof(PipeStage) % 16 == 0, "stages must stay 16-byte aligned");
+static_assert(sizeof(PipeStage<0>) % 16 == 0 && sizeof(PipeStage<3>) % 16 == 0,
+              "stages must stay 16-byte aligned");
+
+// The extended face model's arrays (null where the scene has none).
+struct PipeExt {
+    const float *disp, *sites;
+};
 
 __device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -108,8 +122,11 @@ struct PipeShared {
 // Issue the batch starting at list index `next` (< n) into stage `st`, by
 // the calling warp; returns the index after it.  Lanes take the next 32
 // entries; the prefix of them whose planes fit the stage forms the batch.
-__device__ __forceinline__ int pipe_issue(PipeStage &st, uint64_t *full, const uint32_t *__restrict__ list, int n,
-                                          int next, const WS &w, int64_t vbase, int K) {
+// With XW > 0 each cell's extended face model rows come along (16-byte
+// aligned rows of 16 and 32 bytes, as the batch-staged kernel's copies need).
+template <int XW>
+__device__ __forceinline__ int pipe_issue(PipeStage<XW> &st, uint64_t *full, const uint32_t *__restrict__ list, int n,
+                                          int next, const WS &w, int64_t vbase, int K, const PipeExt &x) {
     const int lane = threadIdx.x & 31;
     int id = 0, np = 0;
     const bool valid = next + lane < n;
@@ -138,19 +155,29 @@ __device__ __forceinline__ int pipe_issue(PipeStage &st, uint64_t *full, const u
     // the stage's previous contents were read through the generic proxy
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncwarp();
-    if (lane == 0) mbar_arrive_expect_tx(full, (unsigned)(nb * (CELLREC_F + VIEWREC_F) * 4 + planes * 16));
+    // bytes of one cell's extended rows: displacement 16, positions 32
+    constexpr unsigned DISP_B = 16u, SITE_B = 32u;
+    const unsigned xb = XW > 0 ? (x.disp ? DISP_B : 0u) + (x.sites ? SITE_B : 0u) : 0u;
+    if (lane == 0)
+        mbar_arrive_expect_tx(full, (unsigned)(nb * ((CELLREC_F + VIEWREC_F) * 4 + xb) + planes * 16));
     __syncwarp();
     if (take) {
         bulk_copy(st.cr + lane * CELLREC_F, w.cellrec + (int64_t)id * CELLREC_F, CELLREC_F * 4, full);
         bulk_copy(st.vr + lane * VIEWREC_F, w.viewrec + (vbase + id) * VIEWREC_F, VIEWREC_F * 4, full);
         if (np > 0) bulk_copy(st.pl + (incl - np), w.planes + (int64_t)id * K, (unsigned)np * 16u, full);
+        if (XW == 3) {
+            float4 *xr = st.xt + 3 * lane;
+            if (x.disp) bulk_copy(xr, x.disp + (int64_t)id * 4, DISP_B, full);
+            if (x.sites) bulk_copy(xr + 1, x.sites + (int64_t)id * 8, SITE_B, full);
+        }
     }
     return next + nb;
 }
 
 // Ballot of the batch's cells whose sphere can meet the warp's cone (the
 // test of warp_mask, on a stage).
-__device__ __forceinline__ unsigned pipe_mask(const PipeStage &st, int nb, const Cone &cone) {
+template <int XW>
+__device__ __forceinline__ unsigned pipe_mask(const PipeStage<XW> &st, int nb, const Cone &cone) {
     const int lane = threadIdx.x & 31;
     bool ov = false;
     if (lane < nb) {
@@ -168,14 +195,20 @@ __device__ __forceinline__ unsigned pipe_mask(const PipeStage &st, int nb, const
     return __ballot_sync(0xffffffffu, ov);
 }
 
-template <bool REC>
+// REC: record hits for the backward.  EXT: the extended face model with
+// four detail sites (displacement, learned site positions, view-dependent
+// site colours), as in the batch-staged kernel.
+template <bool REC, bool EXT = false, int NS = 4>
 __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_pipe_kernel(RenderArgs A, int64_t n_tiles,
                                                                       float *__restrict__ rgb_out,
                                                                       float *__restrict__ T_out,
                                                                       uint32_t *__restrict__ last_out) {
+    static_assert(NS == 4, "eight detail sites take the batch-staged kernel");
+    constexpr int XW = EXT ? 3 : 0;
     extern __shared__ float4 smem4[];
     __shared__ PipeShared S;
-    PipeStage *stage = reinterpret_cast<PipeStage *>(smem4);
+    PipeStage<XW> *stage = reinterpret_cast<PipeStage<XW> *>(smem4);
+    const PipeExt xm{EXT ? A.disp : nullptr, EXT ? A.sites : nullptr};
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
         for (int s = 0; s < PIPE_S; s++) {
@@ -225,7 +258,7 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_pipe_kernel(RenderArgs
             int next = 0;
             for (int b = 0; b < PIPE_S; b++) {
                 if (next < n) {
-                    next = pipe_issue(stage[b], &S.full[b], list, n, next, A.w, vbase, A.K);
+                    next = pipe_issue<XW>(stage[b], &S.full[b], list, n, next, A.w, vbase, A.K, xm);
                     if (lane == 0) S.fills[b]++;
                 } else if (lane == 0 && S.stop > b) {
                     S.stop = b;
@@ -268,7 +301,7 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_pipe_kernel(RenderArgs
                 if (lane == 0) atomicAdd(&S.ndone, 1);
             }
             const int sidx = k % PIPE_S;
-            PipeStage &st = stage[sidx];
+            PipeStage<XW> &st = stage[sidx];
             // every lane waits itself (each observes the phase: acquire for the stage's
             // data); a batch that never comes cannot also complete, so the lanes agree
             // unless one of them ran out of polls
@@ -306,12 +339,17 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_pipe_kernel(RenderArgs
                     const unsigned pm = __ballot_sync(0xffffffffu, pass);
                     bool hit = false;
                     Seg seg;
+                    // the cell's extended face model in the stage: displacement, then positions
+                    const float *xj = EXT ? reinterpret_cast<const float *>(st.xt + XW * j) : nullptr;
+                    const float *sj = EXT && xm.sites ? xj + 4 : nullptr;
                     if (pm) {
                         const int o = st.poff[j];
                         const int np = st.poff[j + 1] - o;
                         if (pass)
-                            hit = clip_chord<false>(cr, vr, st.pl + o, np, A.w.planes_lo + (int64_t)st.ids[j] * A.K,
-                                                    ray, ch, seg, pm);
+                            hit = clip_chord<false, false, EXT, NS>(
+                                cr, vr, st.pl + o, np, A.w.planes_lo + (int64_t)st.ids[j] * A.K, ray, ch, seg, pm,
+                                EXT && xm.disp && NS == 4 ? st.xt[3 * j] : float4{0.f, 0.f, 0.f, 0.f}, sj,
+                                EXT && xm.disp, nullptr);
                     }
                     if (!hit) continue;
                     if (REC) {
@@ -324,8 +362,10 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_pipe_kernel(RenderArgs
                             A.w.hitkind[rp * HIT_CAP + nhit] = (uint16_t)((seg.ka + 3) | ((seg.kb + 3) << 7));
                         nhit++;
                     }
-                    Tex tx;
-                    const float3 c = face_colour<4>(cr, seg, ray, tx);
+                    TexT<NS> tx;
+                    const float3 c = face_colour<NS>(cr, seg, ray, tx, sj,
+                                                     EXT && A.sv ? A.sv + 48 * NS * (int64_t)st.ids[j] : nullptr,
+                                                     nullptr);
                     const float x = fminf(cr[CR_SIG] * (seg.sb - seg.sa), X_CAP);
                     const float ex = __expf(-x);
                     const float wgt = T * (1.0f - ex);
@@ -380,7 +420,7 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_pipe_kernel(RenderArgs
                 const bool go = next < n && !*(volatile int *)&S.abort &&
                                 *(volatile int *)&S.ndone < PIPE_WARPS && *(volatile int *)&S.stop > b;
                 if (go) {
-                    after = pipe_issue(st, &S.full[sidx], list, n, next, A.w, vbase, A.K);
+                    after = pipe_issue<XW>(st, &S.full[sidx], list, n, next, A.w, vbase, A.K, xm);
                     if (lane == 0) S.fills[sidx]++;
                 }
                 __syncwarp();
@@ -421,8 +461,22 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_pipe_kernel(RenderArgs
 }
 
 bool pipe_applies(const pf_scene &s, const Plan &p, bool record, bool contrib) {
-    // hit recording without stored segments (those take the batch-staged kernel)
-    return !ext_face(s) && !contrib && !p.stats && !(record && p.seg_cap > 0);
+    // the plain face model and the extended one with four sites; hit recording
+    // without stored segments.  Stored segments, contributions, work counts and
+    // eight sites take the batch-staged kernel (eight sites' 192-byte rows make
+    // a stage 16.5 KB, and at three CTAs per SM the ring measured 7% slower).
+    return scene_sites(s) != 8 && !contrib && !p.stats && !(record && p.seg_cap > 0);
+}
+
+template <bool REC, bool EXT, int NS>
+static cudaError_t launch_pipe(const RenderArgs &A, const Plan &p, float *rgb, float *T, uint32_t *last,
+                               cudaStream_t st) {
+    constexpr int XW = EXT ? 3 : 0;
+    const size_t smem = sizeof(PipeStage<XW>) * PIPE_S;
+    auto k = render_fwd_pipe_kernel<REC, EXT, NS>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<persistent_grid(k, smem, p.total_tiles), TILE_PIX, smem, st>>>(A, p.total_tiles, rgb, T, last);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_render_fwd_pipe(const pf_scene &s, const Plan &p, const WS &w, float *rgb, float *T,
@@ -435,19 +489,21 @@ cudaError_t launch_render_fwd_pipe(const pf_scene &s, const Plan &p, const WS &w
     A.cap = p.cap;
     A.mask_batches = record ? mask_batches(p) : 0;
     A.contrib_sparse = A.contrib_normal = nullptr;
-    A.disp = A.sites = A.sv = A.tex8 = nullptr;
+    A.disp = s.disp;
+    A.sites = s.sites;
+    A.sv = s.sv;
+    A.tex8 = nullptr;
     A.gdisp = A.gsites = A.gsv = A.gtex8 = nullptr;
     A.w_sparse = A.w_normal = nullptr;
     A.segrec = nullptr;
     A.seg_cap = 0;
-    (void)s;
-    const size_t smem = sizeof(PipeStage) * PIPE_S;
     cudaError_t e = cudaMemsetAsync(&w.counters->q_fwd, 0, sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
-    auto k = record ? render_fwd_pipe_kernel<true> : render_fwd_pipe_kernel<false>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k<<<persistent_grid(k, smem, p.total_tiles), TILE_PIX, smem, st>>>(A, p.total_tiles, rgb, T, last);
-    return cudaGetLastError();
+    if (scene_sites(s) == 8) return cudaErrorNotSupported;  // pipe_applies excludes it
+    if (!ext_face(s)) return record ? launch_pipe<true, false, 4>(A, p, rgb, T, last, st)
+                                    : launch_pipe<false, false, 4>(A, p, rgb, T, last, st);
+    return record ? launch_pipe<true, true, 4>(A, p, rgb, T, last, st)
+                  : launch_pipe<false, true, 4>(A, p, rgb, T, last, st);
 }
 
 }  // namespace pf

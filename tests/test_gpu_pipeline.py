@@ -27,16 +27,23 @@ def built():
     build.build()
 
 
-def both(sc, cams):
+def both(sc, cams, **ext):
+    """Render with every variant; `ext`: the extended face model's arrays
+    (disp, sites, sv) for DeviceScene.from_numpy.  The work-counting run is
+    refused for the extended model, so those scenes compare with the
+    segment-storing one only."""
     import torch
     from paper_2604_24994_gb300 import DeviceScene, Renderer
-    ds = DeviceScene.from_numpy(sc, "cuda")
+    ds = DeviceScene.from_numpy(sc, "cuda", **ext)
+    extended = any(v is not None for v in ext.values()) or np.asarray(sc.tex).shape[1] == 24
     out = {}
     runs = (("staged", dict(hit_records=False), True),            # counts work: batch-staged
             ("staged_rec", dict(hit_records=True, store_segments=1), False),  # stores segments: batch-staged
             ("pipe_rec", dict(hit_records=True), False),
             ("pipe", dict(hit_records=False), False))
     for name, kw, stats in runs:
+        if stats and extended:
+            continue
         r = Renderer(ds.n, ds.k, cams, **kw)
         if stats:
             r.enable_stats(True)
@@ -44,9 +51,8 @@ def both(sc, cams):
         torch.cuda.synchronize()
         assert r.stats()["wait_errors"] == 0
         hc = r.hit_counts() if kw["hit_records"] else None
-        out[name] = (rgb.cpu().numpy(), T.cpu().numpy(), last.cpu().numpy(),
-                     None if hc is None else np.asarray(hc.cpu() if hasattr(hc, "cpu") else hc))
-    ref = out["staged"]
+        out[name] = (rgb.cpu().numpy(), T.cpu().numpy(), last.cpu().numpy(), hc)
+    ref = out["staged_rec"] if extended else out["staged"]
     for name in ("staged_rec", "pipe_rec", "pipe"):
         for x, y, what in zip(out[name][:3], ref[:3], ("rgb", "T", "last")):
             assert np.array_equal(x, y), (name, what)
@@ -104,3 +110,38 @@ def test_early_termination_across_random_views():
         rgb, T, last = both(sc, [cam])
         assert (T < 1e-6).mean() > 0.05
     both(sc, cams)
+
+
+def test_extended_face_models():
+    """Displaced faces with learned site positions, and view-dependent site
+    colours: the pipelined kernel's stages carry each cell's extended rows,
+    and the image equals the batch-staged kernel's bit for bit (and the
+    oracle's within tolerance).  Eight detail sites take the batch-staged
+    kernel in every variant; the same comparisons hold."""
+    rng = np.random.default_rng(21)
+    sc = f32(cluster_scene(rng, n=50, spread=0.3, r=(0.08, 0.2), tex_std=0.15))
+    disp = (rng.uniform(-0.3, 0.3, (sc.n, 4)) * sc.R[:, None]).astype(np.float32)
+    base = np.array([[-1, -1], [1, -1], [-1, 1], [1, 1]], np.float64) / 3.0
+    sites = (base[None] + rng.uniform(-0.2, 0.2, (sc.n, 4, 2))).astype(np.float32)
+    sv = np.concatenate([rng.normal(size=(sc.n, 4, 8, 3)), rng.uniform(0, 1, (sc.n, 4, 8, 3))], -1).astype(np.float32)
+    cams = [inputs.look_at((1.2, 0.4, 0.3), 80, 64),
+            inputs.fisheye_look_at((-0.9, 0.6, 0.2), 60, 60, fov_deg=150.0)]
+    rgb, T, _ = both(sc, cams, disp=disp, sites=sites)
+    orc = oracle.Oracle(sc, disp=disp, sites=sites)
+    n0 = cams[0].n_pixels
+    rgb_o, T_o = orc.render(cams[0])
+    assert_close_image(rgb[:n0].astype(np.float64), T[:n0].astype(np.float64), rgb_o, T_o, "displaced, pipelined")
+    both(sc, cams, sv=sv)
+    both(sc, cams, disp=disp, sites=sites, sv=sv)
+    # eight sites: texture [N,24], displacement [N,8], positions [N,8,2], colours [N,8,8,6]
+    sc8 = sc.copy()
+    sc8.tex = rng.normal(0, 0.2, (sc.n, 24)).astype(np.float32)
+    disp8 = (rng.uniform(-0.3, 0.3, (sc.n, 8)) * sc.R[:, None]).astype(np.float32)
+    grid = np.array([[-1, -1], [0, -1], [1, -1], [-1, 0], [1, 0], [-1, 1], [0, 1], [1, 1]], np.float64) / 3.0
+    sites8 = (grid[None] + rng.uniform(-0.15, 0.15, (sc.n, 8, 2))).astype(np.float32)
+    sv8 = np.concatenate([rng.normal(size=(sc.n, 8, 8, 3)), rng.uniform(0, 1, (sc.n, 8, 8, 3))], -1).astype(np.float32)
+    rgb, T, _ = both(sc8, cams, disp=disp8, sites=sites8)
+    rgb_o, T_o = oracle.Oracle(sc8, disp=disp8, sites=sites8).render(cams[0])
+    assert_close_image(rgb[:n0].astype(np.float64), T[:n0].astype(np.float64), rgb_o, T_o, "eight sites, pipelined")
+    both(sc8, cams)
+    both(sc8, cams, disp=disp8, sites=sites8, sv=sv8)
