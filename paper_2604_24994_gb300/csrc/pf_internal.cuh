@@ -212,7 +212,8 @@ cudaError_t launch_render_fwd(const pf_scene &s, const Plan &p, const WS &w, flo
 // hit recording, stats or contributions.
 bool pipe_applies(const pf_scene &s, const Plan &p, bool record, bool contrib);
 cudaError_t launch_render_fwd_pipe(const pf_scene &s, const Plan &p, const WS &w, float *rgb, float *T,
-                                   uint32_t *last, bool record, cudaStream_t st);
+                                   uint32_t *last, bool record, cudaStream_t st, float *contrib_sparse,
+                                   float *contrib_normal);
 cudaError_t launch_render_bwd(const pf_scene &s, const Plan &p, const WS &w, const float *dL_drgb,
                               const float *dL_dT, const float *T, const uint32_t *last, const pf_scene_grad &g,
                               bool use_masks, cudaStream_t st, const float *w_sparse = nullptr,

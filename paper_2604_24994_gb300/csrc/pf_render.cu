@@ -930,7 +930,7 @@ cudaError_t launch_render_fwd(const pf_scene &s, const Plan &p, const WS &w, flo
                               bool record, cudaStream_t st, float *contrib_sparse, float *contrib_normal) {
     if (p.total_tiles == 0) return cudaSuccess;
     if (pipe_applies(s, p, record, contrib_sparse != nullptr))
-        return launch_render_fwd_pipe(s, p, w, rgb, T, last, record, st);
+        return launch_render_fwd_pipe(s, p, w, rgb, T, last, record, st, contrib_sparse, contrib_normal);
     RenderArgs A = make_args(s, p, w);
     A.contrib_sparse = contrib_sparse;
     A.contrib_normal = contrib_normal;

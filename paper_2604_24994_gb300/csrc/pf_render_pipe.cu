@@ -198,7 +198,10 @@ __device__ __forceinline__ unsigned pipe_mask(const PipeStage<XW> &st, int nb, c
 // REC: record hits for the backward.  EXT: the extended face model with
 // four detail sites (displacement, learned site positions, view-dependent
 // site colours), as in the batch-staged kernel.
-template <bool REC, bool EXT = false, int NS = 4>
+// CONTRIB: also add the per-cell contributions (Sec. 4's L_sparse and
+// L_normal terms) into A.contrib_sparse / A.contrib_normal, as the
+// batch-staged kernel does.
+template <bool REC, bool EXT = false, int NS = 4, bool CONTRIB = false>
 __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_pipe_kernel(RenderArgs A, int64_t n_tiles,
                                                                       float *__restrict__ rgb_out,
                                                                       float *__restrict__ T_out,
@@ -351,6 +354,22 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_pipe_kernel(RenderArgs
                                 EXT && xm.disp && NS == 4 ? st.xt[3 * j] : float4{0.f, 0.f, 0.f, 0.f}, sj,
                                 EXT && xm.disp, nullptr);
                     }
+                    if (CONTRIB && __any_sync(0xffffffffu, hit)) {
+                        // T alpha and T alpha max(nh.d, 0)^2 of the hit lanes, summed over the
+                        // warp in 2^-24 fixed point, one atomic per value and cell
+                        unsigned qw = 0u, qn = 0u;
+                        if (hit) {
+                            const float cw = T * (1.0f - __expf(-fminf(cr[CR_SIG] * (seg.sb - seg.sa), X_CAP)));
+                            const float nd = dot3(f3(cr[CR_N], cr[CR_N + 1], cr[CR_N + 2]), ray.dh);
+                            qw = __float2uint_rn(cw * 0x1p24f);
+                            qn = __float2uint_rn((nd > 0.0f ? cw * nd * nd : 0.0f) * 0x1p24f);
+                        }
+                        qw = __reduce_add_sync(0xffffffffu, qw);
+                        qn = __reduce_add_sync(0xffffffffu, qn);
+                        if (lane < 2)
+                            atomicAdd((lane ? A.contrib_normal : A.contrib_sparse) + st.ids[j],
+                                      (float)(lane ? qn : qw) * 0x1p-24f);
+                    }
                     if (!hit) continue;
                     if (REC) {
                         const int idx = lo + j;
@@ -461,26 +480,35 @@ __global__ void __launch_bounds__(TILE_PIX, 4) render_fwd_pipe_kernel(RenderArgs
 }
 
 bool pipe_applies(const pf_scene &s, const Plan &p, bool record, bool contrib) {
-    // the plain face model and the extended one with four sites; hit recording
-    // without stored segments.  Stored segments, contributions, work counts and
-    // eight sites take the batch-staged kernel (eight sites' 192-byte rows make
-    // a stage 16.5 KB, and at three CTAs per SM the ring measured 7% slower).
-    return scene_sites(s) != 8 && !contrib && !p.stats && !(record && p.seg_cap > 0);
+    // the plain face model and the extended one with four sites, with or without
+    // hit recording and contributions.  Stored segments, work counts and eight
+    // sites take the batch-staged kernel (eight sites' 192-byte rows make a
+    // stage 16.5 KB, and at three CTAs per SM the ring measured 7% slower).
+    (void)contrib;
+    return scene_sites(s) != 8 && !p.stats && !(record && p.seg_cap > 0);
 }
 
-template <bool REC, bool EXT, int NS>
+template <bool REC, bool EXT, int NS, bool CONTRIB>
 static cudaError_t launch_pipe(const RenderArgs &A, const Plan &p, float *rgb, float *T, uint32_t *last,
                                cudaStream_t st) {
     constexpr int XW = EXT ? 3 : 0;
     const size_t smem = sizeof(PipeStage<XW>) * PIPE_S;
-    auto k = render_fwd_pipe_kernel<REC, EXT, NS>;
+    auto k = render_fwd_pipe_kernel<REC, EXT, NS, CONTRIB>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<persistent_grid(k, smem, p.total_tiles), TILE_PIX, smem, st>>>(A, p.total_tiles, rgb, T, last);
     return cudaGetLastError();
 }
 
+template <bool REC, bool CONTRIB>
+static cudaError_t launch_pipe_model(const pf_scene &s, const RenderArgs &A, const Plan &p, float *rgb, float *T,
+                                     uint32_t *last, cudaStream_t st) {
+    return ext_face(s) ? launch_pipe<REC, true, 4, CONTRIB>(A, p, rgb, T, last, st)
+                       : launch_pipe<REC, false, 4, CONTRIB>(A, p, rgb, T, last, st);
+}
+
 cudaError_t launch_render_fwd_pipe(const pf_scene &s, const Plan &p, const WS &w, float *rgb, float *T,
-                                   uint32_t *last, bool record, cudaStream_t st) {
+                                   uint32_t *last, bool record, cudaStream_t st, float *contrib_sparse,
+                                   float *contrib_normal) {
     RenderArgs A;
     A.w = w;
     A.nv = p.nv;
@@ -488,7 +516,8 @@ cudaError_t launch_render_fwd_pipe(const pf_scene &s, const Plan &p, const WS &w
     A.K = p.k;
     A.cap = p.cap;
     A.mask_batches = record ? mask_batches(p) : 0;
-    A.contrib_sparse = A.contrib_normal = nullptr;
+    A.contrib_sparse = contrib_sparse;
+    A.contrib_normal = contrib_normal;
     A.disp = s.disp;
     A.sites = s.sites;
     A.sv = s.sv;
@@ -500,10 +529,11 @@ cudaError_t launch_render_fwd_pipe(const pf_scene &s, const Plan &p, const WS &w
     cudaError_t e = cudaMemsetAsync(&w.counters->q_fwd, 0, sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
     if (scene_sites(s) == 8) return cudaErrorNotSupported;  // pipe_applies excludes it
-    if (!ext_face(s)) return record ? launch_pipe<true, false, 4>(A, p, rgb, T, last, st)
-                                    : launch_pipe<false, false, 4>(A, p, rgb, T, last, st);
-    return record ? launch_pipe<true, true, 4>(A, p, rgb, T, last, st)
-                  : launch_pipe<false, true, 4>(A, p, rgb, T, last, st);
+    const bool contrib = contrib_sparse != nullptr;
+    if (contrib) return record ? launch_pipe_model<true, true>(s, A, p, rgb, T, last, st)
+                               : launch_pipe_model<false, true>(s, A, p, rgb, T, last, st);
+    return record ? launch_pipe_model<true, false>(s, A, p, rgb, T, last, st)
+                  : launch_pipe_model<false, false>(s, A, p, rgb, T, last, st);
 }
 
 }  // namespace pf

@@ -145,3 +145,31 @@ def test_extended_face_models():
     assert_close_image(rgb[:n0].astype(np.float64), T[:n0].astype(np.float64), rgb_o, T_o, "eight sites, pipelined")
     both(sc8, cams)
     both(sc8, cams, disp=disp8, sites=sites8, sv=sv8)
+
+
+def test_contributions_pipelined_and_staged(tiny):
+    """Per-cell contributions (sum of T alpha, and of T alpha max(n.d, 0)^2)
+    from the pipelined forward equal the batch-staged forward's (the one that
+    stores segments), up to the order of the float atomics, and the images
+    are equal bit for bit; with displaced faces too."""
+    import torch
+    from paper_2604_24994_gb300 import DeviceScene, Renderer
+    sc, cam = tiny
+    rng = np.random.default_rng(4)
+    for ext in ({}, {"disp": (rng.uniform(-0.2, 0.2, (sc.n, 4)) * sc.R[:, None]).astype(np.float32)}):
+        ds = DeviceScene.from_numpy(sc, "cuda", **ext)
+        res = []
+        for kw in (dict(hit_records=True, store_segments=1), dict(hit_records=True), dict(hit_records=False)):
+            r = Renderer(ds.n, ds.k, [cam], **kw)
+            r.bin(ds)
+            cs = torch.zeros(ds.n, device="cuda")
+            cn = torch.zeros(ds.n, device="cuda")
+            rgb, T, last = r.render_fwd(ds, contrib=(cs, cn))
+            torch.cuda.synchronize()
+            assert r.stats()["wait_errors"] == 0
+            res.append((rgb.cpu().numpy(), T.cpu().numpy(), cs.cpu().numpy(), cn.cpu().numpy()))
+        for got in res[1:]:
+            assert np.array_equal(got[0], res[0][0]) and np.array_equal(got[1], res[0][1])
+            np.testing.assert_allclose(got[2], res[0][2], rtol=1e-5, atol=1e-6)
+            np.testing.assert_allclose(got[3], res[0][3], rtol=1e-5, atol=1e-6)
+        assert res[0][2].sum() > 1.0
