@@ -304,32 +304,63 @@ __device__ void bitonic_sort(KeyArr keys, CellArr cells, int n) {
     }
 }
 
-// Stable LSD radix sort of one tile's list in shared memory, 4-bit digits.
-// The 64-bit keys stay in place (keys[q] = key of bucket entry q); 16-bit
-// entry indices move between ia and ib.  Thread t owns the contiguous
-// entries [t E, (t + 1) E), E = ceil(n / NT) <= 32, so the order of equal
-// digits is (thread, position) order, the list order before the pass.
-// Digit positions where every key has the same bits are skipped.  Equal
-// keys end in bucket order, which the atomic slot grabs made arbitrary: a
-// final pass puts each run of equal keys in cell order.  gkey / cells:
-// the bucket in global memory; keys: n words, ia / ib: n entries, cnt:
-// 16 NT counters, red: 2 NT / 32 words of shared memory.  Returns the
-// array (ia or ib) that holds the sorted entry order.
-template <int NT>
-__device__ uint16_t *radix_sort_tile(int n, const unsigned long long *__restrict__ gkey,
-                                     const uint32_t *__restrict__ cells, unsigned long long *keys, uint16_t *ia,
-                                     uint16_t *ib, uint16_t *cnt, unsigned long long *red) {
-    constexpr int NW = NT / 32;
+// One stable counting pass over a 4-bit digit: entries move from ia to ib,
+// dig(x) is entry x's digit.
+template <int NT, typename Dig>
+__device__ __forceinline__ void radix_pass(int b, int e, const uint16_t *ia, uint16_t *ib, uint16_t *cnt,
+                                           unsigned long long *red, Dig dig) {
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    // bits that differ between keys: OR ^ AND over the list
-    unsigned long long o = 0ull, a = ~0ull;
-    for (int q = t; q < n; q += NT) {
-        const unsigned long long k = gkey[q];
-        keys[q] = k;
-        o |= k;
-        a &= k;
-        ia[q] = (uint16_t)q;
+    // this thread's digit counts, eight bits each (E <= 32)
+    unsigned long long c0 = 0ull, c1 = 0ull;
+    for (int i = b; i < e; i++) {
+        const unsigned dg = dig(ia[i]);
+        if (dg < 8)
+            c0 += 1ull << (8 * dg);
+        else
+            c1 += 1ull << (8 * (dg - 8));
     }
+#pragma unroll
+    for (int dg = 0; dg < 16; dg++)
+        cnt[dg * NT + t] = (uint16_t)(((dg < 8 ? c0 >> (8 * dg) : c1 >> (8 * (dg - 8)))) & 0xffull);
+    __syncthreads();
+    // exclusive scan of cnt in (digit, thread) order: 16 entries per thread
+    uint16_t *mine = cnt + 16 * t;
+    unsigned run = 0;
+#pragma unroll
+    for (int r = 0; r < 16; r++) run += mine[r];
+    unsigned incl = run;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
+    }
+    if (lane == 31) red[warp] = incl;
+    __syncthreads();
+    unsigned before = incl - run;
+    for (int w = 0; w < warp; w++) before += (unsigned)red[w];
+#pragma unroll
+    for (int r = 0; r < 16; r++) {
+        const unsigned x = mine[r];
+        mine[r] = (uint16_t)before;
+        before += x;
+    }
+    __syncthreads();
+    for (int i = b; i < e; i++) {
+        const uint16_t x = ia[i];
+        const unsigned dg = dig(x);
+        const unsigned pos = cnt[dg * NT + t];
+        cnt[dg * NT + t] = (uint16_t)(pos + 1u);
+        ib[pos] = x;
+    }
+    __syncthreads();
+}
+
+// OR ^ AND of v over the CTA: the bits in which the values differ.
+template <int NT>
+__device__ __forceinline__ unsigned long long varying_bits(unsigned long long o, unsigned long long a,
+                                                           unsigned long long *red) {
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
         o |= __shfl_xor_sync(0xffffffffu, o, d);
@@ -346,81 +377,116 @@ __device__ uint16_t *radix_sort_tile(int n, const unsigned long long *__restrict
         vo |= red[w];
         va &= red[NW + w];
     }
-    const unsigned long long vary = vo ^ va;
     __syncthreads();  // red is reused by the scans
+    return vo ^ va;
+}
+
+// Lists whose equal keys form more than this many adjacent pairs are sorted
+// again with the cell index as the low-order part of the key (the insertion
+// fix-up below is quadratic in a run's length).
+constexpr int TIE_INSERT_MAX = 64;
+
+// The rare path of radix_sort_tile: the list sorted again from bucket order,
+// the cell index's varying digits first and then the key's, so that equal
+// keys end in cell order.  Out of line: it keeps the common path's registers.
+template <int NT>
+static __device__ __noinline__ uint16_t *radix_resort_with_cells(int n, const uint32_t *__restrict__ cells,
+                                                                 const unsigned long long *keys, uint16_t *ia,
+                                                                 uint16_t *ib, uint16_t *cnt,
+                                                                 unsigned long long *red,
+                                                                 unsigned long long vary) {
+    const int t = threadIdx.x;
     const int E = (n + NT - 1) / NT;
     const int b = min(n, t * E), e = min(n, b + E);
-    for (int sh = 0; sh < 64; sh += 4) {
-        if (((vary >> sh) & 15ull) == 0ull) continue;  // the same for every thread
-        // this thread's digit counts, eight bits each (E <= 32)
-        unsigned long long c0 = 0ull, c1 = 0ull;
-        for (int i = b; i < e; i++) {
-            const unsigned dg = (unsigned)(keys[ia[i]] >> sh) & 15u;
-            if (dg < 8)
-                c0 += 1ull << (8 * dg);
-            else
-                c1 += 1ull << (8 * (dg - 8));
-        }
-#pragma unroll
-        for (int dg = 0; dg < 16; dg++)
-            cnt[dg * NT + t] = (uint16_t)(((dg < 8 ? c0 >> (8 * dg) : c1 >> (8 * (dg - 8)))) & 0xffull);
-        __syncthreads();
-        // exclusive scan of cnt in (digit, thread) order: 16 entries per thread
-        uint16_t *mine = cnt + 16 * t;
-        unsigned run = 0;
-#pragma unroll
-        for (int r = 0; r < 16; r++) run += mine[r];
-        unsigned incl = run;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const unsigned y = __shfl_up_sync(0xffffffffu, incl, d);
-            if (lane >= d) incl += y;
-        }
-        if (lane == 31) red[warp] = incl;
-        __syncthreads();
-        unsigned before = incl - run;
-        for (int w = 0; w < warp; w++) before += (unsigned)red[w];
-#pragma unroll
-        for (int r = 0; r < 16; r++) {
-            const unsigned x = mine[r];
-            mine[r] = (uint16_t)before;
-            before += x;
-        }
-        __syncthreads();
-        for (int i = b; i < e; i++) {
-            const uint16_t x = ia[i];
-            const unsigned dg = (unsigned)(keys[x] >> sh) & 15u;
-            const unsigned pos = cnt[dg * NT + t];
-            cnt[dg * NT + t] = (uint16_t)(pos + 1u);
-            ib[pos] = x;
-        }
-        __syncthreads();
+    unsigned long long co = 0ull, ca = ~0ull;
+    for (int q = t; q < n; q += NT) {
+        ia[q] = (uint16_t)q;
+        co |= cells[q];
+        ca &= cells[q];
+    }
+    const unsigned long long cvary = varying_bits<NT>(co, ca, red);
+    for (int sh = 0; sh < 32; sh += 4) {
+        if (((cvary >> sh) & 15ull) == 0ull) continue;
+        radix_pass<NT>(b, e, ia, ib, cnt, red, [cells, sh](uint16_t x) { return (cells[x] >> sh) & 15u; });
         uint16_t *sw = ia;
         ia = ib;
         ib = sw;
     }
-    // runs of equal keys into cell order (insertion sort by the run's first thread)
-    bool tie = false;
-    for (int q = t; q + 1 < n; q += NT) tie |= keys[ia[q]] == keys[ia[q + 1]];
-    if (__syncthreads_or(tie)) {
-        for (int q = t; q + 1 < n; q += NT) {
-            const unsigned long long k = keys[ia[q]];
-            if (k != keys[ia[q + 1]] || (q > 0 && keys[ia[q - 1]] == k)) continue;
-            int r = q + 2;
-            while (r < n && keys[ia[r]] == k) r++;
-            for (int i = q + 1; i < r; i++) {
-                const uint16_t x = ia[i];
-                const uint32_t cx = cells[x];
-                int j = i - 1;
-                while (j >= q && cells[ia[j]] > cx) {
-                    ia[j + 1] = ia[j];
-                    j--;
-                }
-                ia[j + 1] = x;
-            }
-        }
-        __syncthreads();
+    for (int sh = 0; sh < 64; sh += 4) {
+        if (((vary >> sh) & 15ull) == 0ull) continue;
+        radix_pass<NT>(b, e, ia, ib, cnt, red, [keys, sh](uint16_t x) { return (unsigned)(keys[x] >> sh) & 15u; });
+        uint16_t *sw = ia;
+        ia = ib;
+        ib = sw;
     }
+    return ia;
+}
+
+// Stable LSD radix sort of one tile's list in shared memory, 4-bit digits.
+// The 64-bit keys stay in place (keys[q] = key of bucket entry q); 16-bit
+// entry indices move between ia and ib.  Thread t owns the contiguous
+// entries [t E, (t + 1) E), E = ceil(n / NT) <= 32, so the order of equal
+// digits is (thread, position) order, the list order before the pass.
+// Digit positions where every key has the same bits are skipped.  Equal
+// keys end in bucket order, which the atomic slot grabs made arbitrary: a
+// final pass puts each run of equal keys in cell order (by insertion when
+// they are few, else by sorting again with the cell index's digits first).
+// gkey / cells: the bucket in global memory; keys: n words, ia / ib: n entries, cnt:
+// 16 NT counters, red: 2 NT / 32 words of shared memory.  Returns the
+// array (ia or ib) that holds the sorted entry order.
+template <int NT>
+__device__ uint16_t *radix_sort_tile(int n, const unsigned long long *__restrict__ gkey,
+                                     const uint32_t *__restrict__ cells, unsigned long long *keys, uint16_t *ia,
+                                     uint16_t *ib, uint16_t *cnt, unsigned long long *red) {
+    const int t = threadIdx.x;
+    unsigned long long o = 0ull, a = ~0ull;
+    for (int q = t; q < n; q += NT) {
+        const unsigned long long k = gkey[q];
+        keys[q] = k;
+        o |= k;
+        a &= k;
+        ia[q] = (uint16_t)q;
+    }
+    const unsigned long long vary = varying_bits<NT>(o, a, red);
+    const int E = (n + NT - 1) / NT;
+    const int b = min(n, t * E), e = min(n, b + E);
+    for (int sh = 0; sh < 64; sh += 4) {
+        if (((vary >> sh) & 15ull) == 0ull) continue;  // the same for every thread
+        radix_pass<NT>(b, e, ia, ib, cnt, red, [keys, sh](uint16_t x) { return (unsigned)(keys[x] >> sh) & 15u; });
+        uint16_t *sw = ia;
+        ia = ib;
+        ib = sw;
+    }
+    // equal keys end in bucket order; put them in cell order
+    int mine = 0;
+    for (int q = t; q + 1 < n; q += NT) mine += keys[ia[q]] == keys[ia[q + 1]];
+    if (!__syncthreads_or(mine > 0)) return ia;
+    unsigned long long *tot = red;  // the CTA's count of adjacent equal pairs
+    if (t == 0) *tot = 0ull;
+    __syncthreads();
+    if (mine) atomicAdd(tot, (unsigned long long)mine);
+    __syncthreads();
+    const int nties = (int)*tot;
+    __syncthreads();
+    if (nties > TIE_INSERT_MAX) return radix_resort_with_cells<NT>(n, cells, keys, ia, ib, cnt, red, vary);
+    // few ties: each run of equal keys into cell order (insertion sort by its first thread)
+    for (int q = t; q + 1 < n; q += NT) {
+        const unsigned long long k = keys[ia[q]];
+        if (k != keys[ia[q + 1]] || (q > 0 && keys[ia[q - 1]] == k)) continue;
+        int r = q + 2;
+        while (r < n && keys[ia[r]] == k) r++;
+        for (int i = q + 1; i < r; i++) {
+            const uint16_t x = ia[i];
+            const uint32_t cx = cells[x];
+            int j = i - 1;
+            while (j >= q && cells[ia[j]] > cx) {
+                ia[j + 1] = ia[j];
+                j--;
+            }
+            ia[j + 1] = x;
+        }
+    }
+    __syncthreads();
     return ia;
 }
 

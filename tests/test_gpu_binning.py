@@ -134,24 +134,29 @@ def test_long_tile_lists_across_views_and_capacity_growth():
 def test_equal_keys_in_every_sort_path_bit_exact():
     """Cells duplicated (same site, weight and radius, so the same key) in
     lists that take each radix sort: 488 and 1,944 entries (256 threads,
-    32 KB of shared memory), 11,674 (512 threads, 208 KB).  Equal keys must come
-    out in cell-index order, as in the CPU binning, whatever order the
-    atomic bucket fill left them in."""
+    32 KB of shared memory; there the bitonic network orders (key, cell)),
+    11,674 entries with thousands of equal keys (512 threads, 208 KB: sorted
+    again with the cell index's digits first) and 2,570 entries with ten
+    (the insertion fix-up).  Equal keys must come out in cell-index order,
+    as in the CPU binning, whatever order the atomic bucket fill left them
+    in."""
     import torch
     from paper_2604_24994_gb300 import DeviceScene, Renderer
     cam = inputs.look_at((3.0, 0.0, 0.0), 640, 360)
-    tiles = [(5, 5), (30, 15), (14, 9)]
-    base = column_scene(cam, tiles, [1, 4, 24], seed=2)
-    n0 = base.n
+    tiles = [(5, 5), (30, 15), (14, 9), (35, 3)]
+    per = [1, 4, 24, 10]
+    base = column_scene(cam, tiles, per, seed=2)
+    n3 = 256 * (1 + 4 + 24)          # cells of the first three tiles
     rng = np.random.default_rng(5)
-    # every other cell once more, every fifth cell twice more, appended in a shuffled order
-    extra = np.concatenate([np.arange(0, n0, 2), np.arange(0, n0, 5), np.arange(0, n0, 5)])
+    # the first three tiles: every other cell once more, every fifth twice more;
+    # the fourth: ten of its cells once more; all appended in a shuffled order
+    extra = np.concatenate([np.arange(0, n3, 2), np.arange(0, n3, 5), np.arange(0, n3, 5),
+                            n3 + rng.choice(256 * 10, 10, replace=False)])
     extra = extra[rng.permutation(extra.size)]
-    src = np.concatenate([np.arange(n0), extra])
+    src = np.concatenate([np.arange(base.n), extra])
     sc = base.copy()
     for k in sc.PARAMS:
         setattr(sc, k, np.ascontiguousarray(np.asarray(getattr(base, k))[src]))
-    sc.w = np.ascontiguousarray(base.w[src])
     sc.nbr = np.zeros((src.size, 0), np.int32)
     ds = DeviceScene.from_numpy(sc, "cuda")
     r = Renderer(ds.n, ds.k, [cam])
@@ -159,7 +164,8 @@ def test_equal_keys_in_every_sort_path_bit_exact():
     torch.cuda.synchronize()
     lens = compare_bins(r, sc, cam)
     # each cell lies in one tile: its column's
-    tile_of = np.repeat(np.arange(3), [256 * 1, 256 * 4, 256 * 24])[src]
+    tile_of = np.repeat(np.arange(4), [256 * p for p in per])[src]
     want = np.bincount(tile_of)
     assert sorted(lens[lens > 0].tolist()) == sorted(want.tolist())
     assert 256 < want[0] <= 2048 and 256 < want[1] <= 2048 and 2048 < want[2] <= 16384
+    assert want[3] == 2570
