@@ -555,6 +555,10 @@ __device__ __forceinline__ void sort_tile(int64_t t, const uint32_t *__restrict_
 
 // One CTA per tile for the lists of at most CAP entries, CTAs in the render
 // order (longest lists first, so that the last wave holds the short ones).
+// Launched as a programmatic dependent of the long-list kernel, so the two
+// run side by side (they write disjoint ranges of inst_sorted); the last CTA
+// waits for that kernel's completion before it exits, so this kernel's
+// completion, which the next launch on the stream waits for, implies both.
 template <int CAP, int NT>
 __global__ void __launch_bounds__(NT) sort_small_tiles_kernel(const uint32_t *__restrict__ order,
                                                               const uint32_t *__restrict__ tile_start,
@@ -567,9 +571,10 @@ __global__ void __launch_bounds__(NT) sort_small_tiles_kernel(const uint32_t *__
     unsigned long long s = tile_start[tt], e = tile_start[tt + 1];
     if (s > cap) s = cap;
     if (e > cap) e = cap;
-    if (e - s > (unsigned long long)CAP) return;  // the persistent kernel sorts it
-    sort_tile<0, CAP, NT, false>(tt, tile_start, cap, inst_key, inst_cell, inst_sorted, nullptr, nullptr,
-                                 reinterpret_cast<char *>(smem_sort));
+    if (e - s <= (unsigned long long)CAP)  // longer lists: the persistent kernel sorts them
+        sort_tile<0, CAP, NT, false>(tt, tile_start, cap, inst_key, inst_cell, inst_sorted, nullptr, nullptr,
+                                     reinterpret_cast<char *>(smem_sort));
+    if (blockIdx.x == gridDim.x - 1) asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 // Persistent CTAs over the render order (tiles by decreasing list length,
@@ -585,6 +590,7 @@ __global__ void __launch_bounds__(NT) sort_large_tiles_kernel(const uint32_t *__
                                                               uint32_t *__restrict__ inst_sorted,
                                                               unsigned long long *tmp_key, uint32_t *tmp_cell) {
     extern __shared__ unsigned long long smem_sort[];
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");  // the short-list sort may start now
     for (int64_t i = blockIdx.x; i < T; i += gridDim.x) {
         const int64_t t = order[i];
         unsigned long long s = tile_start[t], e = tile_start[t + 1];
@@ -598,7 +604,8 @@ __global__ void __launch_bounds__(NT) sort_large_tiles_kernel(const uint32_t *__
 }
 
 // Render order: tiles by decreasing list length (bucketed by length / 4),
-// so that persistent render CTAs start with the heaviest tiles.
+// so that persistent render CTAs start with the heaviest tiles.  One CTA of
+// 1024 threads, one per length bucket.
 __global__ void __launch_bounds__(1024) tile_order_kernel(const uint32_t *__restrict__ tile_start, int64_t T,
                                                           unsigned long long cap, uint32_t *__restrict__ order) {
     constexpr int NB = 1024;
@@ -614,13 +621,27 @@ __global__ void __launch_bounds__(1024) tile_order_kernel(const uint32_t *__rest
     };
     for (int64_t t = threadIdx.x; t < T; t += blockDim.x) atomicAdd(&hist[bucket(t)], 1u);
     __syncthreads();
-    if (threadIdx.x == 0) {  // 1024 buckets: a serial scan is cheap
-        uint32_t acc = 0;
-        for (int b = 0; b < NB; b++) {
-            const uint32_t x = hist[b];
-            hist[b] = acc;
-            acc += x;
+    {  // exclusive scan of the 1024 buckets, one per thread: warp scans, then a scan of the warp sums
+        __shared__ uint32_t wsum[NB / 32];
+        const int b = threadIdx.x, lane = b & 31;
+        const uint32_t x = hist[b];
+        uint32_t v = x;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
         }
+        if (lane == 31) wsum[b >> 5] = v;
+        __syncthreads();
+        if (b < NB / 32) {
+            uint32_t u = wsum[b];
+            for (int o = 1; o < NB / 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, u, o);
+                if (lane >= o) u += y;
+            }
+            wsum[b] = u;
+        }
+        __syncthreads();
+        hist[b] = v - x + ((b >> 5) ? wsum[(b >> 5) - 1] : 0u);
     }
     __syncthreads();
     for (int64_t t = threadIdx.x; t < T; t += blockDim.x) order[atomicAdd(&hist[bucket(t)], 1u)] = (uint32_t)t;
@@ -674,8 +695,8 @@ cudaError_t launch_bin_sort(const Plan &p, const WS &w, cudaStream_t st) {
         const size_t ss = (size_t)SMALL * 12, sl = SortSmem<LARGE, 512>::bytes;
         cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
         cudaFuncSetAttribute(kl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sl);
-        ks<<<(unsigned)T, 256, ss, st>>>(w.tile_order, w.tile_start, p.cap, w.inst_key, w.inst_cell, w.inst_sorted);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        // the long lists first (a few persistent CTAs, one per SM), the short
+        // ones beside them on the SMs that the first kernel leaves free
         int dev = 0, sms = 148;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -683,6 +704,19 @@ cudaError_t launch_bin_sort(const Plan &p, const WS &w, cudaStream_t st) {
                                                             w.inst_cell, w.inst_sorted, w.sort_tmp_key,
                                                             w.sort_tmp_cell);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.gridDim = dim3((unsigned)T);
+        cfg.blockDim = dim3(256);
+        cfg.dynamicSmemBytes = ss;
+        cfg.stream = st;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, ks, (const uint32_t *)w.tile_order, (const uint32_t *)w.tile_start, p.cap,
+                               (const unsigned long long *)w.inst_key, (const uint32_t *)w.inst_cell, w.inst_sorted);
+        if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
