@@ -590,7 +590,7 @@ def serve_bench(args, local: int):
     from paper_2604_24994_gb300.serve import Server
 
     t0 = time.time()
-    n_cells = 2_000_000 if args.workload == "full" else 400_000
+    n_cells = 2_000_000 if args.workload in ("full", "serve") else 400_000
     sc = inputs.capture_scene(n_cells, seed=0, K=32)
     gen_s = time.time() - t0
     ds = DeviceScene.from_numpy(sc, "cuda")
@@ -600,7 +600,8 @@ def serve_bench(args, local: int):
     n_req = int(rate * dur * 1.2) + 64
     arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
     arrivals = arrivals[arrivals < dur]
-    cams = inputs.random_sphere_cameras(rng, len(arrivals) + 400, 2.0, 6.0, SERVE_SIZES, SERVE_PROBS)
+    cams = inputs.random_sphere_cameras(rng, max(len(arrivals), args.serve_burst) + 400, 2.0, 6.0, SERVE_SIZES,
+                                        SERVE_PROBS)
     ring = {}
     for (w, h) in SERVE_SIZES:  # output buffers, reused round-robin
         ring[(w, h)] = [(torch.empty((w * h, 3), device="cuda"), torch.empty(w * h, device="cuda"))
@@ -633,7 +634,7 @@ def serve_bench(args, local: int):
                 if st == 0:
                     ids.append(rid)
         else:  # closed loop: a burst that keeps every slot busy
-            for cam in cams[:300]:
+            for cam in cams[:args.serve_burst]:
                 ids.append(srv.submit(cam, *outputs(cam)))
         for i in ids:
             srv.wait(i, 600000)
@@ -659,6 +660,17 @@ def serve_bench(args, local: int):
                                                             "mean_batch_views")},
                      "opts": opts}
     return out
+
+
+def run_serve_only(args):
+    """The serving workload alone (both servers, open loop for
+    --serve-seconds, then a closed-loop burst of --serve-burst requests):
+    one JSON line, not the benchmark line."""
+    import torch
+    from paper_2604_24994_gb300 import build
+    torch.cuda.set_device(0)
+    build.build()
+    print(json.dumps({"workload": "serve", "serve": serve_bench(args, 0)}), flush=True)
 
 
 def run_large(args):
@@ -767,16 +779,19 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="full", choices=["full", "small", "large"])
+    ap.add_argument("--workload", default="full", choices=["full", "small", "large", "serve"])
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-budget-gb", type=float, default=40.0)
+    ap.add_argument("--serve-burst", type=int, default=300)
     ap.add_argument("--no-serve", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "large":
         run_large(args)
+    elif args.workload == "serve":
+        run_serve_only(args)
     else:
         run_ours(args)
 

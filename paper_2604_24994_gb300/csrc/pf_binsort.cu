@@ -506,15 +506,179 @@ struct SortSmem {
 // 2049-16384 entries three times faster with the radix sort).
 constexpr int BITONIC_MAX = 2048;
 
+// A list of 2 <= m <= CAP entries in global memory (keys gk, cells gc),
+// sorted in shared memory by (key, cell); its cells in order to out.
+template <int CAP, int NT>
+__device__ void sort_run_shared(int m, const unsigned long long *gk, const uint32_t *gc, uint32_t *out,
+                                char *smem) {
+    using L = SortSmem<CAP, NT>;
+    unsigned long long *sk = reinterpret_cast<unsigned long long *>(smem + L::keys);
+    if (m <= BITONIC_MAX) {
+        uint32_t *sc = reinterpret_cast<uint32_t *>(smem + L::ia);
+        for (int q = threadIdx.x; q < m; q += NT) {
+            sk[q] = gk[q];
+            sc[q] = gc[q];
+        }
+        __syncthreads();
+        bitonic_sort(sk, sc, m);
+        for (int q = threadIdx.x; q < m; q += NT) out[q] = sc[q];
+    } else if constexpr (CAP > BITONIC_MAX) {
+        const uint16_t *ord = radix_sort_tile<NT>(
+            m, gk, gc, sk, reinterpret_cast<uint16_t *>(smem + L::ia), reinterpret_cast<uint16_t *>(smem + L::ib),
+            reinterpret_cast<uint16_t *>(smem + L::cnt), reinterpret_cast<unsigned long long *>(smem + L::red));
+        for (int q = threadIdx.x; q < m; q += NT) out[q] = gc[ord[q]];
+    }
+    __syncthreads();  // shared memory is reused by the next list
+}
+
+// ------------------------------------------------ lists above CAP entries
+// A list too long for shared memory is split by the 8 most significant bits
+// in which its keys differ: a counting pass, then every entry moves to its
+// bucket in the other pair of global arrays (same offsets; the order within
+// a bucket does not matter).  The buckets partition the key range in order,
+// so runs of consecutive buckets holding at most CAP entries in all are
+// each sorted in shared memory as one list, completely by (key, cell), and
+// the runs end to end are the sorted list.  A bucket above CAP is split
+// again by the next 8 bits (at most 8 levels: each consumes 8 key bits); one
+// whose keys are all equal, or that finds the stack full, is sorted in place
+// in global memory by the bitonic network.
+constexpr int BIG_DIG = 8, BIG_NB = 1 << BIG_DIG, BIG_STACK = 128;
+
+struct BigSeg {
+    uint32_t off, m;  // first entry (from the list's start) and length
+    int buf, depth;   // where its entries are (0: instance arrays, 1: scratch arrays); splits above it
+};
+struct BigRun {
+    uint32_t start, m;  // first entry (from the segment's start) and length
+    int global, pad;    // 1: one bucket above CAP, sorted in global memory
+};
+
+// Shared memory after SortSmem: bucket counts and cursors, the runs of the
+// current split, the stack of buckets still to split, two counters.
+struct BigSmem {
+    static constexpr size_t hist = 0, cur = hist + BIG_NB * 4, run = cur + BIG_NB * 4,
+                            stk = run + (BIG_NB + 1) * sizeof(BigRun), ctl = stk + BIG_STACK * sizeof(BigSeg),
+                            bytes = ctl + 16;
+};
+
+template <int CAP, int NT>
+static __device__ __forceinline__ void sort_long_list(uint32_t n, unsigned long long *k0, uint32_t *c0,
+                                                   unsigned long long *k1, uint32_t *c1, uint32_t *out,
+                                                   char *smem) {
+    using L = SortSmem<CAP, NT>;
+    char *xs = smem + L::bytes;
+    uint32_t *hist = reinterpret_cast<uint32_t *>(xs + BigSmem::hist);
+    uint32_t *cur = reinterpret_cast<uint32_t *>(xs + BigSmem::cur);
+    BigRun *run = reinterpret_cast<BigRun *>(xs + BigSmem::run);
+    BigSeg *stk = reinterpret_cast<BigSeg *>(xs + BigSmem::stk);
+    int *ctl = reinterpret_cast<int *>(xs + BigSmem::ctl);
+    unsigned long long *red = reinterpret_cast<unsigned long long *>(smem + L::red);
+    const int t = threadIdx.x, lane = t & 31;
+    const uint32_t w0 = (uint32_t)(t & ~31);  // this warp's first entry of each round
+    if (t == 0) stk[0] = BigSeg{0u, n, 0, 0};
+    int sp = 1;  // the same in every thread
+    for (int guard = 0; sp > 0 && guard < (1 << 20); guard++) {
+        __syncthreads();  // the stack written by thread 0 is visible
+        const BigSeg g = stk[--sp];
+        unsigned long long *sk = (g.buf ? k1 : k0) + g.off, *dk = (g.buf ? k0 : k1) + g.off;
+        uint32_t *sc = (g.buf ? c1 : c0) + g.off, *dc = (g.buf ? c0 : c1) + g.off;
+        uint32_t *o = out + g.off;
+        unsigned long long vo = 0ull, va = ~0ull;
+        for (uint32_t q = t; q < g.m; q += NT) {
+            const unsigned long long k = sk[q];
+            vo |= k;
+            va &= k;
+        }
+        const unsigned long long vary = varying_bits<NT>(vo, va, red);  // also: every thread has read g
+        if (vary == 0ull || g.depth >= 8) {  // all keys equal: the cells decide
+            bitonic_sort(sk, sc, (int)g.m);
+            for (uint32_t q = t; q < g.m; q += NT) o[q] = sc[q];
+            continue;
+        }
+        const int hb = 63 - __clzll((long long)vary);
+        const int sh = hb >= BIG_DIG - 1 ? hb - (BIG_DIG - 1) : 0;
+        for (int d = t; d < BIG_NB; d += NT) hist[d] = 0u;
+        __syncthreads();
+        // counts: rounds of 32 consecutive entries per warp, one atomic per digit and round
+        for (uint32_t q0 = w0; q0 < g.m; q0 += NT) {
+            const uint32_t q = q0 + lane;
+            const unsigned d = q < g.m ? (unsigned)(sk[q] >> sh) & (BIG_NB - 1) : 0xffffffffu;
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            if (d != 0xffffffffu && lane == __ffs(peers) - 1) atomicAdd(&hist[d], (unsigned)__popc(peers));
+        }
+        __syncthreads();
+        if (t == 0) {  // bucket offsets, the runs, and the buckets to split again
+            uint32_t acc = 0u, rs = 0u, rm = 0u;
+            int nr = 0;
+            for (int d = 0; d < BIG_NB; d++) {
+                const uint32_t c = hist[d];
+                cur[d] = acc;
+                if (c > (uint32_t)CAP) {
+                    if (rm) run[nr++] = BigRun{rs, rm, 0, 0};
+                    rm = 0u;
+                    if (sp < BIG_STACK)
+                        stk[sp++] = BigSeg{g.off + acc, c, g.buf ^ 1, g.depth + 1};
+                    else
+                        run[nr++] = BigRun{acc, c, 1, 0};
+                } else if (c) {
+                    if (rm + c > (uint32_t)CAP) {
+                        run[nr++] = BigRun{rs, rm, 0, 0};
+                        rm = 0u;
+                    }
+                    if (!rm) rs = acc;
+                    rm += c;
+                }
+                acc += c;
+            }
+            if (rm) run[nr++] = BigRun{rs, rm, 0, 0};
+            ctl[0] = nr;
+            ctl[1] = sp;
+        }
+        __syncthreads();
+        const int nr = ctl[0];
+        sp = ctl[1];
+        // every entry to its bucket: a rank among the round's equal digits after the bucket's cursor
+        for (uint32_t q0 = w0; q0 < g.m; q0 += NT) {
+            const uint32_t q = q0 + lane;
+            const bool ok = q < g.m;
+            const unsigned long long k = ok ? sk[q] : 0ull;
+            const uint32_t c = ok ? sc[q] : 0u;
+            const unsigned d = ok ? (unsigned)(k >> sh) & (BIG_NB - 1) : 0xffffffffu;
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            const int leader = __ffs(peers) - 1;
+            uint32_t base = 0u;
+            if (ok && lane == leader) base = atomicAdd(&cur[d], (unsigned)__popc(peers));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (ok) {
+                const uint32_t pos = base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+                dk[pos] = k;
+                dc[pos] = c;
+            }
+        }
+        __syncthreads();  // the moved entries are visible to the CTA
+        for (int r = 0; r < nr; r++) {
+            const BigRun R = run[r];
+            if (R.global) {
+                bitonic_sort(dk + R.start, dc + R.start, (int)R.m);
+                for (uint32_t q = t; q < R.m; q += NT) o[R.start + q] = dc[R.start + q];
+            } else if (R.m == 1u) {
+                if (t == 0) o[R.start] = dc[R.start];
+            } else {
+                sort_run_shared<CAP, NT>((int)R.m, dk + R.start, dc + R.start, o + R.start, smem);
+            }
+        }
+    }
+}
+
 // One CTA per tile.  Variant <LO, CAP>: buckets with LO < n <= CAP are
-// sorted in shared memory; with GLOBAL, buckets above CAP are sorted in
-// place in the global scratch arrays.
+// sorted in shared memory; with GLOBAL, buckets above CAP by splitting
+// them (sort_long_list), with the global scratch arrays beside the
+// instance arrays.
 template <int LO, int CAP, int NT, bool GLOBAL>
 __device__ __forceinline__ void sort_tile(int64_t t, const uint32_t *__restrict__ tile_start, unsigned long long cap,
                                           const unsigned long long *inst_key, const uint32_t *inst_cell,
                                           uint32_t *__restrict__ inst_sorted, unsigned long long *tmp_key,
                                           uint32_t *tmp_cell, char *smem) {
-    using L = SortSmem<CAP, NT>;
     unsigned long long s = tile_start[t], e = tile_start[t + 1];
     if (s > cap) s = cap;
     if (e > cap) e = cap;
@@ -524,32 +688,14 @@ __device__ __forceinline__ void sort_tile(int64_t t, const uint32_t *__restrict_
         if (threadIdx.x == 0) inst_sorted[s] = inst_cell[s];
         return;
     }
-    unsigned long long *sk = reinterpret_cast<unsigned long long *>(smem + L::keys);
-    if (n <= BITONIC_MAX) {
-        uint32_t *sc = reinterpret_cast<uint32_t *>(smem + L::ia);
-        for (int q = threadIdx.x; q < n; q += NT) {
-            sk[q] = inst_key[s + q];
-            sc[q] = inst_cell[s + q];
-        }
-        __syncthreads();
-        bitonic_sort(sk, sc, (int)n);
-        for (int q = threadIdx.x; q < n; q += NT) inst_sorted[s + q] = sc[q];
-    } else if (CAP > BITONIC_MAX && n <= CAP) {
-        const uint16_t *ord = radix_sort_tile<NT>(
-            (int)n, inst_key + s, inst_cell + s, sk, reinterpret_cast<uint16_t *>(smem + L::ia),
-            reinterpret_cast<uint16_t *>(smem + L::ib), reinterpret_cast<uint16_t *>(smem + L::cnt),
-            reinterpret_cast<unsigned long long *>(smem + L::red));
-        for (int q = threadIdx.x; q < n; q += NT) inst_sorted[s + q] = inst_cell[s + ord[q]];
-    } else if (GLOBAL) {
-        unsigned long long *gk = tmp_key + s;
-        uint32_t *gc = tmp_cell + s;
-        for (int64_t q = threadIdx.x; q < n; q += NT) {
-            gk[q] = inst_key[s + q];
-            gc[q] = inst_cell[s + q];
-        }
-        __syncthreads();
-        bitonic_sort(gk, gc, (int)n);
-        for (int64_t q = threadIdx.x; q < n; q += NT) inst_sorted[s + q] = gc[q];
+    if (n <= CAP) {
+        sort_run_shared<CAP, NT>((int)n, inst_key + s, inst_cell + s, inst_sorted + s, smem);
+    } else if constexpr (GLOBAL) {
+        // the instance arrays are scratch once the lists are sorted: the
+        // splits move entries between them and the scratch arrays
+        sort_long_list<CAP, NT>((uint32_t)n, const_cast<unsigned long long *>(inst_key) + s,
+                                const_cast<uint32_t *>(inst_cell) + s, tmp_key + s, tmp_cell + s, inst_sorted + s,
+                                smem);
     }
 }
 
@@ -687,12 +833,13 @@ cudaError_t launch_bin_sort(const Plan &p, const WS &w, cudaStream_t st) {
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (T > 0) {
-        // small buckets (<= 2048) in 24 KB of shared memory (bitonic), large ones in 208 KB (radix)
+        // small buckets (<= 2048) in 24 KB of shared memory (bitonic), large ones in 208 KB (radix;
+        // above 16384 entries split by their leading key bits first, with 6.5 KB more)
         constexpr int SMALL = 2048, LARGE = 16384;
         auto ks = sort_small_tiles_kernel<SMALL, 256>;
         auto kl = sort_large_tiles_kernel<SMALL, LARGE, 512>;
         static_assert(SMALL <= BITONIC_MAX, "the small-list kernel sorts with the bitonic network only");
-        const size_t ss = (size_t)SMALL * 12, sl = SortSmem<LARGE, 512>::bytes;
+        const size_t ss = (size_t)SMALL * 12, sl = SortSmem<LARGE, 512>::bytes + BigSmem::bytes;
         cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
         cudaFuncSetAttribute(kl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sl);
         // the long lists first (a few persistent CTAs, one per SM), the short

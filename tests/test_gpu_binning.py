@@ -169,3 +169,37 @@ def test_equal_keys_in_every_sort_path_bit_exact():
     assert sorted(lens[lens > 0].tolist()) == sorted(want.tolist())
     assert 256 < want[0] <= 2048 and 256 < want[1] <= 2048 and 2048 < want[2] <= 16384
     assert want[3] == 2570
+
+
+def test_lists_above_shared_memory_split_bit_exact():
+    """Lists longer than the 16,384 entries a CTA sorts in shared memory are
+    split by their leading key bits first.  Two such lists: 20,480 distinct
+    keys with every third cell duplicated (27,307 entries: equal keys inside
+    the shared-memory runs), and 6,144 keys plus one cell repeated 17,000
+    times (23,144 entries: a bucket of 17,001 equal keys that no split can
+    shorten, ordered by cell index alone).  Bit-exact against the CPU
+    binning."""
+    import torch
+    from paper_2604_24994_gb300 import DeviceScene, Renderer
+    cam = inputs.look_at((3.0, 0.0, 0.0), 640, 360)
+    tiles = [(19, 10), (23, 6)]
+    per = [80, 24]
+    base = column_scene(cam, tiles, per, seed=3)
+    na = 256 * per[0]
+    rng = np.random.default_rng(7)
+    extra = np.concatenate([np.arange(0, na, 3), np.full(17000, na + 1000)])
+    extra = extra[rng.permutation(extra.size)]
+    src = np.concatenate([np.arange(base.n), extra])
+    sc = base.copy()
+    for k in sc.PARAMS:
+        setattr(sc, k, np.ascontiguousarray(np.asarray(getattr(base, k))[src]))
+    sc.nbr = np.zeros((src.size, 0), np.int32)
+    ds = DeviceScene.from_numpy(sc, "cuda")
+    r = Renderer(ds.n, ds.k, [cam])
+    r.forward(ds)
+    torch.cuda.synchronize()
+    lens = compare_bins(r, sc, cam)
+    tile_of = np.repeat(np.arange(2), [256 * p for p in per])[src]
+    want = np.bincount(tile_of)
+    assert sorted(lens[lens > 0].tolist()) == sorted(want.tolist())
+    assert want.tolist() == [27307, 23144]
