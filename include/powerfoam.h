@@ -233,8 +233,8 @@ pf_status pf_project(const pf_scene *scene, pf_plan *plan, void *ws, void *strea
 
 /*
  * Duplicate every (cell, tile) pair, group by tile and sort each tile's list
- * by (key, cell index) (Sec. 3.2: a global sort by depth "similar to 3DGS",
- * here by power distance).  If n_instances is non-NULL the call
+ * by (key, cell index) (Sec. 3.2: all instances sorted by depth, as Gaussian
+ * splatting does; here by power distance).  If n_instances is non-NULL the call
  * synchronises the stream and returns the instance count; then
  * PF_ERR_CAPACITY means the plan's capacity was too small (*n_instances is
  * the size needed; re-plan and repeat pf_prepare/pf_project/pf_bin_sort).
