@@ -7,10 +7,13 @@
 //      its first instance index;
 //   3. one thread per instance (load-balanced: big cells do not serialise)
 //      finds its cell by binary search, its tile inside the cell's
-//      rectangle, and takes a slot in the tile's bucket;
+//      rectangle, and takes a slot in the tile's bucket; the tiles are put
+//      in render order (longest lists first);
 //   4. one CTA per tile sorts the bucket by (key, cell): a bitonic network
-//      in 24 KB of shared memory for up to 2048 entries, a radix sort in
-//      208 KB for up to 16384, a bitonic network in global memory beyond.
+//      in 24 KB of shared memory for up to 2048 entries; persistent CTAs,
+//      running beside that kernel, a radix sort in 208 KB for up to 16384,
+//      and beyond that a split by the leading key bits into runs of at most
+//      16384 entries, each sorted in shared memory.
 // The result does not depend on the order of the atomic slot grabs: the
 // composite key (key, cell) is unique.
 #include "pf_internal.cuh"
