@@ -493,6 +493,28 @@ def test_binning_is_conservative_and_keys_ordered(tiny):
     assert np.array_equal(np.argsort(key, kind="stable"), np.argsort(pw, kind="stable"))
 
 
+def test_tile_lists_equal_a_per_tile_brute_force():
+    """The CPU tile lists (CSR, sorted per tile by (key, cell)), the
+    reference of the bit-exact GPU binning tests, against a plain loop over
+    tiles and cells: rectangles of every size, empty ones, ones on the grid
+    border, and keys with many ties."""
+    rng = np.random.default_rng(11)
+    tx, ty, n = 7, 5, 300
+    x0 = rng.integers(0, tx, n)
+    y0 = rng.integers(0, ty, n)
+    x1 = np.minimum(x0 + rng.integers(-1, 4, n), tx - 1)   # -1: an empty rectangle
+    y1 = np.minimum(y0 + rng.integers(-1, 3, n), ty - 1)
+    rect = np.stack([x0, y0, x1, y1], 1).astype(np.int32)
+    key = rng.integers(0, 40, n).astype(np.uint64) << np.uint64(40)    # ties among the keys
+    start, cells = oracle.tile_lists(rect, key, tx, ty)
+    assert start[0] == 0 and start[-1] == cells.size and start.size == tx * ty + 1
+    for t in range(tx * ty):
+        u, v = t % tx, t // tx
+        want = [i for i in range(n) if x0[i] <= u <= x1[i] and y0[i] <= v <= y1[i]]
+        want.sort(key=lambda i: (int(key[i]), i))
+        assert cells[start[t]:start[t + 1]].tolist() == want, t
+
+
 def test_binning_rect_is_tight():
     """For a sphere in front of the camera the rectangle is the tile cover
     of its projected extent: sampled silhouette points reach every edge."""
