@@ -319,9 +319,9 @@ def run_ours(args):
         return g
 
     grads = {k: torch.zeros_like(v) for k, v in ds.params.items()}
-    # library kernels per forward step: project, tile counts, 2 scans x 3, expand, tile order,
-    # 2 tile sorts (shared-memory sizes), render
-    kernels_fwd = 1 + 1 + 6 + 1 + 1 + 2 + 1
+    # library kernels per forward step: project, the difference grids' sum, tile counts,
+    # 2 scans x 3, expand, tile order, 2 tile sorts (shared-memory sizes), render
+    kernels_fwd = 1 + 1 + 1 + 6 + 1 + 1 + 2 + 1
 
     def timed(fn, k, warm, per_kernel=None):
         for _ in range(warm):
