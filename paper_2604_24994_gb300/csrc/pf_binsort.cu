@@ -837,7 +837,7 @@ cudaError_t launch_bin_sort(const Plan &p, const WS &w, cudaStream_t st) {
     }
     if (T > 0) {
         // small buckets (<= 2048) in 24 KB of shared memory (bitonic), large ones in 208 KB (radix;
-        // above 16384 entries split by their leading key bits first, with 6.5 KB more)
+        // above 16384 entries split by their leading key bits first, with 8 KB more)
         constexpr int SMALL = 2048, LARGE = 16384;
         auto ks = sort_small_tiles_kernel<SMALL, 256>;
         auto kl = sort_large_tiles_kernel<SMALL, LARGE, 512>;
