@@ -705,7 +705,8 @@ __device__ __forceinline__ void sort_tile(int64_t t, const uint32_t *__restrict_
 // One CTA per tile for the lists of at most CAP entries, CTAs in the render
 // order (longest lists first, so that the last wave holds the short ones).
 // Launched as a programmatic dependent of the long-list kernel, so the two
-// run side by side (they write disjoint ranges of inst_sorted); the last CTA
+// run side by side (each touches only its own tiles' ranges of the
+// instance, scratch and sorted arrays); the last CTA
 // waits for that kernel's completion before it exits, so this kernel's
 // completion, which the next launch on the stream waits for, implies both.
 template <int CAP, int NT>
